@@ -1,0 +1,809 @@
+/*
+ * rm_oracle.c -- CPU oracle for the RenderMap pose-cost path (Ryde & Ding, arXiv 1702.06813).
+ *
+ * TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's CPU-baseline leg
+ * are its only callers. It is deliberately plain and slow: one loop per step, no blocking,
+ * no fusion. It shares no code with the CUDA library.
+ *
+ * What it computes, and where the paper defines it:
+ *  - Sec. III.A: the map is a triangle mesh of the interfaces between free, occupied and
+ *    unknown space, each face labelled FO / FU / UO; it is rendered into a z-buffer image.
+ *  - Eq. 1: E(X) = C(R(T(X)), Z_s), R(Y) the z-buffer rendered from camera pose Y.
+ *  - Table I: the per-pixel reward / penalty from the map class, the scan class and
+ *    dz = d(p_r) - d(p_s) with the inlier threshold eps = 0.1 m; the cost is the sum over
+ *    all pixels (Sec. III.B).
+ *  - Sec. III.C names derivative-based and derivative-free optimisers; this oracle adds the
+ *    least-squares surrogate whose Levenberg-Marquardt step the library runs (a reading, not
+ *    the paper's own optimiser), with the pose derivative of the ray-plane depth.
+ *
+ * The z-buffer follows a written FP32 arithmetic contract so that the CPU and the GPU pick
+ * the same triangle for every pixel: fixed operation order, IEEE add / mul / div / fma,
+ * round-to-nearest-even. Build with -ffp-contract=off so that the compiler fuses nothing.
+ */
+#include "rm_oracle.h"
+
+#include <float.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define KEY_EMPTY 0xFFFFFFFFFFFFFFFFull
+#define GUARD_PX 2097152.0f /* 2^21 pixels: snapped coordinates stay below 2^29 */
+
+/* ------------------------------------------------------------------------------------- */
+/* map preparation and pose                                                              */
+/* ------------------------------------------------------------------------------------- */
+
+void orc_recentre(const float *v, int64_t V, double centre[3], float *out) {
+  for (int a = 0; a < 3; ++a) {
+    double lo = INFINITY, hi = -INFINITY;
+    for (int64_t k = 0; k < V; ++k) {
+      double x = (double)v[3 * k + a];
+      if (x < lo) lo = x;
+      if (x > hi) hi = x;
+    }
+    centre[a] = V > 0 ? 0.5 * (lo + hi) : 0.0;
+  }
+  for (int64_t k = 0; k < V; ++k)
+    for (int a = 0; a < 3; ++a) out[3 * k + a] = (float)((double)v[3 * k + a] - centre[a]);
+}
+
+/* Eq. 1's T(X) maps the observer pose to the camera pose; here the caller passes the camera
+ * pose directly. M = inverse of (R, t - centre): rotation R^T, translation -R^T (t - c). */
+void orc_pose_matrix(const double T[16], const double c[3], float M[12]) {
+  double t0 = T[3] - c[0], t1 = T[7] - c[1], t2 = T[11] - c[2];
+  for (int i = 0; i < 3; ++i) {
+    double r0 = T[0 * 4 + i], r1 = T[1 * 4 + i], r2 = T[2 * 4 + i]; /* column i of R */
+    double s = r0 * t0;
+    s = s + r1 * t1;
+    s = s + r2 * t2;
+    M[4 * i + 0] = (float)r0;
+    M[4 * i + 1] = (float)r1;
+    M[4 * i + 2] = (float)r2;
+    M[4 * i + 3] = (float)(-s);
+  }
+}
+
+void orc_transform(const float M[12], const float *v, int64_t V, float *vc) {
+  for (int64_t k = 0; k < V; ++k) {
+    float x = v[3 * k], y = v[3 * k + 1], z = v[3 * k + 2];
+    for (int r = 0; r < 3; ++r)
+      vc[3 * k + r] = fmaf(M[4 * r], x, fmaf(M[4 * r + 1], y, fmaf(M[4 * r + 2], z, M[4 * r + 3])));
+  }
+}
+
+/* ------------------------------------------------------------------------------------- */
+/* the z-buffer (Sec. III.A render; depth buffer as in Sec. III)                          */
+/* ------------------------------------------------------------------------------------- */
+
+typedef struct { float nx, ny, nz, d, A, B, C; } plane32;
+
+/* Camera-space plane of a triangle from its stored vertex order. */
+static void plane_of(const float *a, const float *b, const float *c, const orc_cam *cam,
+                     plane32 *p) {
+  float e1x = b[0] - a[0], e1y = b[1] - a[1], e1z = b[2] - a[2];
+  float e2x = c[0] - a[0], e2y = c[1] - a[1], e2z = c[2] - a[2];
+  p->nx = fmaf(e1y, e2z, -(e1z * e2y));
+  p->ny = fmaf(e1z, e2x, -(e1x * e2z));
+  p->nz = fmaf(e1x, e2y, -(e1y * e2x));
+  p->d = fmaf(p->nx, a[0], fmaf(p->ny, a[1], p->nz * a[2]));
+  if (cam->model == 0) {
+    p->A = p->nx / cam->fx;
+    p->B = p->ny / cam->fy;
+    p->C = fmaf(-p->A, cam->cx, fmaf(-p->B, cam->cy, p->nz));
+  } else {
+    p->A = p->B = p->C = 0.0f;
+  }
+}
+
+static float depth_at(const plane32 *p, const orc_cam *cam, int i, int j) {
+  float den;
+  if (cam->model == 0) {
+    float px = (float)i + 0.5f, py = (float)j + 0.5f;
+    den = fmaf(p->A, px, fmaf(p->B, py, p->C));
+  } else {
+    const float *r = cam->rays + 3 * ((int64_t)j * cam->width + i);
+    den = fmaf(p->nx, r[0], fmaf(p->ny, r[1], p->nz * r[2]));
+  }
+  return p->d / den;
+}
+
+static void deposit(const plane32 *pl, const orc_cam *cam, int i, int j, uint32_t id,
+                    uint64_t *keys, int32_t *frags, orc_stats *st) {
+  int64_t pix = (int64_t)j * cam->width + i;
+  if (frags) frags[pix] += 1;
+  st->n_fragments += 1;
+  float t = depth_at(pl, cam, i, j);
+  if (t >= cam->near_m && t <= cam->far_m) {
+    uint32_t bits;
+    memcpy(&bits, &t, 4);
+    uint64_t key = ((uint64_t)bits << 32) | (uint64_t)id;
+    if (key < keys[pix]) keys[pix] = key;
+  }
+}
+
+/* Pinhole: project and snap to 1/256 pixel, round half to even. */
+static int snap(const orc_cam *cam, float X, float Y, float Z, int32_t *xi, int32_t *yi) {
+  float xs = fmaf(cam->fx, X / Z, cam->cx);
+  float ys = fmaf(cam->fy, Y / Z, cam->cy);
+  if (!(fabsf(xs) <= GUARD_PX && fabsf(ys) <= GUARD_PX)) return 0;
+  *xi = (int32_t)lrintf(xs * 256.0f);
+  *yi = (int32_t)lrintf(ys * 256.0f);
+  return 1;
+}
+
+/* One snapped triangle: integer edge functions, top-left fill rule, sample at pixel centres
+ * (256 i + 128, 256 j + 128); single sample, no anti-aliasing (Sec. V renders with AA off). */
+static void raster_snapped(int32_t x[3], int32_t y[3], const plane32 *pl, uint32_t id,
+                           const orc_cam *cam, uint64_t *keys, int32_t *frags, int brute,
+                           orc_stats *st) {
+  int64_t area = (int64_t)(x[1] - x[0]) * (y[2] - y[0]) - (int64_t)(y[1] - y[0]) * (x[2] - x[0]);
+  if (area == 0) return;
+  if (area < 0) {
+    int32_t tx = x[1], ty = y[1];
+    x[1] = x[2]; y[1] = y[2];
+    x[2] = tx; y[2] = ty;
+  }
+  int64_t dx[3], dy[3], bias[3];
+  for (int e = 0; e < 3; ++e) {
+    int b = (e + 1) % 3;
+    dx[e] = (int64_t)x[b] - x[e];
+    dy[e] = (int64_t)y[b] - y[e];
+    bias[e] = (dy[e] < 0 || (dy[e] == 0 && dx[e] > 0)) ? 0 : -1; /* top or left edge */
+  }
+  int64_t i0 = 0, i1 = cam->width - 1, j0 = 0, j1 = cam->height - 1;
+  if (!brute) {
+    int64_t xmin = x[0], xmax = x[0], ymin = y[0], ymax = y[0];
+    for (int k = 1; k < 3; ++k) {
+      if (x[k] < xmin) xmin = x[k];
+      if (x[k] > xmax) xmax = x[k];
+      if (y[k] < ymin) ymin = y[k];
+      if (y[k] > ymax) ymax = y[k];
+    }
+    int64_t a0 = (xmin + 127) >> 8, a1 = (xmax - 128) >> 8;
+    int64_t b0 = (ymin + 127) >> 8, b1 = (ymax - 128) >> 8;
+    if (a0 > i0) i0 = a0;
+    if (a1 < i1) i1 = a1;
+    if (b0 > j0) j0 = b0;
+    if (b1 < j1) j1 = b1;
+  }
+  for (int64_t j = j0; j <= j1; ++j) {
+    int64_t py = 256 * j + 128;
+    for (int64_t i = i0; i <= i1; ++i) {
+      int64_t px = 256 * i + 128;
+      int in = 1;
+      for (int e = 0; e < 3 && in; ++e) {
+        int64_t E = dx[e] * (py - y[e]) - dy[e] * (px - x[e]);
+        if (E + bias[e] < 0) in = 0;
+      }
+      if (in) deposit(pl, cam, (int)i, (int)j, id, keys, frags, st);
+    }
+  }
+}
+
+/* Near-plane cut of edge (a, b), a being the endpoint with the lower vertex index. */
+static void near_cut(const float *a, const float *b, float near_m, float *out) {
+  float s = (near_m - a[2]) / (b[2] - a[2]);
+  out[0] = fmaf(s, b[0] - a[0], a[0]);
+  out[1] = fmaf(s, b[1] - a[1], a[1]);
+  out[2] = near_m;
+}
+
+static void raster_pinhole(const float *vc, const int32_t *f, uint32_t id, const orc_cam *cam,
+                           uint64_t *keys, int32_t *frags, int brute, orc_stats *st) {
+  const float *v[3] = {vc + 3 * (int64_t)f[0], vc + 3 * (int64_t)f[1], vc + 3 * (int64_t)f[2]};
+  plane32 pl;
+  plane_of(v[0], v[1], v[2], cam, &pl);
+  int in[3], nin = 0;
+  for (int k = 0; k < 3; ++k) {
+    in[k] = v[k][2] >= cam->near_m;
+    nin += in[k];
+  }
+  if (nin == 0) return;
+  float poly[4][3];
+  int n = 0;
+  if (nin == 3) {
+    for (int k = 0; k < 3; ++k) memcpy(poly[n++], v[k], sizeof(float) * 3);
+  } else {
+    st->n_clipped += 1;
+    for (int k = 0; k < 3; ++k) {
+      int m = (k + 1) % 3;
+      if (in[k]) memcpy(poly[n++], v[k], sizeof(float) * 3);
+      if (in[k] != in[m]) {
+        if (f[k] < f[m]) near_cut(v[k], v[m], cam->near_m, poly[n++]);
+        else near_cut(v[m], v[k], cam->near_m, poly[n++]);
+      }
+    }
+  }
+  int32_t sx[4], sy[4];
+  for (int k = 0; k < n; ++k) {
+    if (!snap(cam, poly[k][0], poly[k][1], poly[k][2], &sx[k], &sy[k])) {
+      st->n_guard_culled += 1;
+      return;
+    }
+  }
+  int32_t x[3] = {sx[0], sx[1], sx[2]}, y[3] = {sy[0], sy[1], sy[2]};
+  raster_snapped(x, y, &pl, id, cam, keys, frags, brute, st);
+  if (n == 4) {
+    int32_t x2[3] = {sx[0], sx[2], sx[3]}, y2[3] = {sy[0], sy[2], sy[3]};
+    raster_snapped(x2, y2, &pl, id, cam, keys, frags, brute, st);
+  }
+}
+
+/* ---- ray-table (panoramic) model: coverage by cone side tests ---- */
+
+static void cross3f(const float *p, const float *q, float *c) {
+  c[0] = fmaf(p[1], q[2], -(p[2] * q[1]));
+  c[1] = fmaf(p[2], q[0], -(p[0] * q[2]));
+  c[2] = fmaf(p[0], q[1], -(p[1] * q[0]));
+}
+
+static float dot3f(const float *p, const float *q) {
+  return fmaf(p[0], q[0], fmaf(p[1], q[1], p[2] * q[2]));
+}
+
+static double clampd(double x, double lo, double hi) { return x < lo ? lo : (x > hi ? hi : x); }
+
+/* Pixel rectangle (columns may wrap) that can hold rays inside the triangle's cone, from the
+ * table's parametric layout in FP64 with a two-pixel margin. Returns 0 if empty. */
+static int sph_bounds(const float *v0, const float *v1, const float *v2, const orc_cam *cam,
+                      int64_t *i0, int64_t *ni, int64_t *j0, int64_t *j1) {
+  double d[3][3];
+  const float *vv[3] = {v0, v1, v2};
+  for (int k = 0; k < 3; ++k) {
+    double n = sqrt((double)vv[k][0] * vv[k][0] + (double)vv[k][1] * vv[k][1] +
+                    (double)vv[k][2] * vv[k][2]);
+    if (!(n > 0)) return 0;
+    for (int a = 0; a < 3; ++a) d[k][a] = vv[k][a] / n;
+  }
+  /* normal sides of the cone (orientation-corrected) */
+  double cr[3][3], det;
+  for (int k = 0; k < 3; ++k) {
+    const double *p = d[k], *q = d[(k + 1) % 3];
+    cr[k][0] = p[1] * q[2] - p[2] * q[1];
+    cr[k][1] = p[2] * q[0] - p[0] * q[2];
+    cr[k][2] = p[0] * q[1] - p[1] * q[0];
+  }
+  det = d[0][0] * cr[1][0] + d[0][1] * cr[1][1] + d[0][2] * cr[1][2];
+  if (det == 0) return 0;
+  double sg = det > 0 ? 1.0 : -1.0;
+  int has_up = 1, has_dn = 1; /* up = (0,-1,0), down = (0,1,0) */
+  for (int k = 0; k < 3; ++k) {
+    if (-sg * cr[k][1] < -1e-9) has_up = 0;
+    if (sg * cr[k][1] < -1e-9) has_dn = 0;
+  }
+  double el_hi = -M_PI / 2, el_lo = M_PI / 2;
+  for (int k = 0; k < 3; ++k) {
+    double e = asin(clampd(-d[k][1], -1, 1));
+    if (e > el_hi) el_hi = e;
+    if (e < el_lo) el_lo = e;
+  }
+  for (int k = 0; k < 3; ++k) { /* extrema of elevation along each great-circle arc */
+    const double *a = d[k], *b = d[(k + 1) % 3];
+    double c[3] = {cr[k][0], cr[k][1], cr[k][2]};
+    double cn = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+    if (!(cn > 1e-15)) continue;
+    for (int a2 = 0; a2 < 3; ++a2) c[a2] /= cn;
+    double up[3] = {0, -1, 0};
+    double s = up[1] * c[1];
+    double u[3] = {up[0] - s * c[0], up[1] - s * c[1], up[2] - s * c[2]};
+    double un = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    if (!(un > 1e-15)) continue;
+    for (int a2 = 0; a2 < 3; ++a2) u[a2] /= un;
+    for (int sgn = -1; sgn <= 1; sgn += 2) {
+      double w[3] = {sgn * u[0], sgn * u[1], sgn * u[2]};
+      double aw[3] = {a[1] * w[2] - a[2] * w[1], a[2] * w[0] - a[0] * w[2], a[0] * w[1] - a[1] * w[0]};
+      double wb[3] = {w[1] * b[2] - w[2] * b[1], w[2] * b[0] - w[0] * b[2], w[0] * b[1] - w[1] * b[0]};
+      if (aw[0] * c[0] + aw[1] * c[1] + aw[2] * c[2] >= -1e-12 &&
+          wb[0] * c[0] + wb[1] * c[1] + wb[2] * c[2] >= -1e-12) {
+        double e = asin(clampd(-w[1], -1, 1));
+        if (e > el_hi) el_hi = e;
+        if (e < el_lo) el_lo = e;
+      }
+    }
+  }
+  if (has_up) el_hi = M_PI / 2;
+  if (has_dn) el_lo = -M_PI / 2;
+  double m_el = 2.0 * cam->el_step, m_az = 2.0 * cam->az_step;
+  double jlo = ceil((cam->el0 - el_hi - m_el) / cam->el_step);
+  double jhi = floor((cam->el0 - el_lo + m_el) / cam->el_step);
+  if (jlo < 0) jlo = 0;
+  if (jhi > cam->height - 1) jhi = cam->height - 1;
+  if (jlo > jhi) return 0;
+  *j0 = (int64_t)jlo;
+  *j1 = (int64_t)jhi;
+  if (has_up || has_dn) {
+    *i0 = 0;
+    *ni = cam->width;
+    return 1;
+  }
+  double az[3];
+  for (int k = 0; k < 3; ++k) az[k] = atan2(d[k][0], d[k][2]);
+  /* smallest circular arc holding the three azimuths: drop the largest gap */
+  double s0 = az[0], s1 = az[1], s2 = az[2], t;
+  if (s0 > s1) { t = s0; s0 = s1; s1 = t; }
+  if (s1 > s2) { t = s1; s1 = s2; s2 = t; }
+  if (s0 > s1) { t = s0; s0 = s1; s1 = t; }
+  double g01 = s1 - s0, g12 = s2 - s1, g20 = s0 + 2 * M_PI - s2;
+  double lo, hi;
+  if (g20 >= g01 && g20 >= g12) { lo = s0; hi = s2; }
+  else if (g01 >= g12) { lo = s1; hi = s0 + 2 * M_PI; }
+  else { lo = s2; hi = s1 + 2 * M_PI; }
+  double ilo = ceil((lo - m_az - cam->az0) / cam->az_step - 0.5);
+  double ihi = floor((hi + m_az - cam->az0) / cam->az_step - 0.5);
+  if (ihi - ilo + 1 >= cam->width) {
+    *i0 = 0;
+    *ni = cam->width;
+  } else {
+    int64_t a = (int64_t)ilo % cam->width;
+    if (a < 0) a += cam->width;
+    *i0 = a;
+    *ni = (int64_t)(ihi - ilo) + 1;
+  }
+  return 1;
+}
+
+static void raster_raytable(const float *vc, const int32_t *f, uint32_t id, const orc_cam *cam,
+                            uint64_t *keys, int32_t *frags, int brute, orc_stats *st) {
+  const float *v[3] = {vc + 3 * (int64_t)f[0], vc + 3 * (int64_t)f[1], vc + 3 * (int64_t)f[2]};
+  plane32 pl;
+  plane_of(v[0], v[1], v[2], cam, &pl);
+  float c12[3];
+  cross3f(v[1], v[2], c12);
+  float det = dot3f(v[0], c12);
+  if (det == 0.0f || det != det) return;
+  float side[3][3], sig[3];
+  for (int k = 0; k < 3; ++k) {
+    int m = (k + 1) % 3;
+    int lo = f[k] < f[m] ? k : m, hi = f[k] < f[m] ? m : k;
+    cross3f(v[lo], v[hi], side[k]);
+    sig[k] = (det > 0.0f ? 1.0f : -1.0f) * (lo == k ? 1.0f : -1.0f);
+  }
+  int64_t i0 = 0, ni = cam->width, j0 = 0, j1 = cam->height - 1;
+  if (!brute && !sph_bounds(v[0], v[1], v[2], cam, &i0, &ni, &j0, &j1)) return;
+  for (int64_t j = j0; j <= j1; ++j) {
+    for (int64_t q = 0; q < ni; ++q) {
+      int64_t i = (i0 + q) % cam->width;
+      const float *r = cam->rays + 3 * (j * cam->width + i);
+      int in = 1;
+      for (int k = 0; k < 3 && in; ++k) {
+        float s = dot3f(r, side[k]);
+        if (!(sig[k] * s > 0.0f || (s == 0.0f && sig[k] > 0.0f))) in = 0;
+      }
+      if (in) deposit(&pl, cam, (int)i, (int)j, id, keys, frags, st);
+    }
+  }
+}
+
+int orc_zbuffer(const float *vc, const int32_t *faces, int64_t T, const orc_cam *cam,
+                uint64_t *keys, int32_t *frags, int brute, orc_stats *st) {
+  int64_t P = (int64_t)cam->width * cam->height;
+  orc_stats local = {0, 0, 0};
+  for (int64_t p = 0; p < P; ++p) keys[p] = KEY_EMPTY;
+  if (frags) memset(frags, 0, sizeof(int32_t) * P);
+  for (int64_t k = 0; k < T; ++k) {
+    const int32_t *f = faces + 3 * k;
+    if (cam->model == 0) raster_pinhole(vc, f, (uint32_t)k, cam, keys, frags, brute, &local);
+    else raster_raytable(vc, f, (uint32_t)k, cam, keys, frags, brute, &local);
+  }
+  if (st) *st = local;
+  return 0;
+}
+
+int orc_render(const float *vr, int64_t V, const double centre[3], const int32_t *faces,
+               int64_t T, const double Twc[16], const orc_cam *cam, uint64_t *keys,
+               int32_t *frags, int brute, orc_stats *st) {
+  float M[12];
+  orc_pose_matrix(Twc, centre, M);
+  float *vc = (float *)malloc(sizeof(float) * 3 * (V > 0 ? V : 1));
+  if (!vc) return -1;
+  orc_transform(M, vr, V, vc);
+  int rc = orc_zbuffer(vc, faces, T, cam, keys, frags, brute, st);
+  free(vc);
+  return rc;
+}
+
+/* ------------------------------------------------------------------------------------- */
+/* FP64 geometry of the winners                                                           */
+/* ------------------------------------------------------------------------------------- */
+
+static void ray64(const orc_cam *cam, int i, int j, double r[3]) {
+  if (cam->model == 0) {
+    r[0] = ((double)i + 0.5 - (double)cam->cx) / (double)cam->fx;
+    r[1] = ((double)j + 0.5 - (double)cam->cy) / (double)cam->fy;
+    r[2] = 1.0;
+  } else {
+    const float *q = cam->rays + 3 * ((int64_t)j * cam->width + i);
+    r[0] = q[0];
+    r[1] = q[1];
+    r[2] = q[2];
+  }
+}
+
+/* Camera-frame plane n_c . p = d_c of triangle k in FP64 at pose T. */
+static void plane64(const float *v, const int32_t *faces, int64_t k, const double T[16],
+                    double n[3], double *d) {
+  const float *a = v + 3 * (int64_t)faces[3 * k], *b = v + 3 * (int64_t)faces[3 * k + 1],
+              *c = v + 3 * (int64_t)faces[3 * k + 2];
+  double e1[3] = {(double)b[0] - a[0], (double)b[1] - a[1], (double)b[2] - a[2]};
+  double e2[3] = {(double)c[0] - a[0], (double)c[1] - a[1], (double)c[2] - a[2]};
+  double nw[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
+                  e1[0] * e2[1] - e1[1] * e2[0]};
+  double q[3] = {(double)a[0] - T[3], (double)a[1] - T[7], (double)a[2] - T[11]};
+  *d = nw[0] * q[0] + nw[1] * q[1] + nw[2] * q[2];
+  for (int i = 0; i < 3; ++i) n[i] = T[0 * 4 + i] * nw[0] + T[1 * 4 + i] * nw[1] + T[2 * 4 + i] * nw[2];
+}
+
+void orc_depth_exact(const float *v, const int32_t *faces, const double Twc[16],
+                     const orc_cam *cam, const uint64_t *keys, double *depth) {
+  for (int j = 0; j < cam->height; ++j)
+    for (int i = 0; i < cam->width; ++i) {
+      int64_t p = (int64_t)j * cam->width + i;
+      if (keys[p] == KEY_EMPTY) {
+        depth[p] = NAN;
+        continue;
+      }
+      double n[3], d, r[3];
+      plane64(v, faces, (int64_t)(keys[p] & 0xFFFFFFFFu), Twc, n, &d);
+      ray64(cam, i, j, r);
+      depth[p] = d / (n[0] * r[0] + n[1] * r[1] + n[2] * r[2]);
+    }
+}
+
+void orc_barycentrics(const float *v, const int32_t *faces, const double T[16],
+                      const orc_cam *cam, const uint64_t *keys, double *bary) {
+  for (int j = 0; j < cam->height; ++j)
+    for (int i = 0; i < cam->width; ++i) {
+      int64_t p = (int64_t)j * cam->width + i;
+      if (keys[p] == KEY_EMPTY) {
+        bary[2 * p] = bary[2 * p + 1] = NAN;
+        continue;
+      }
+      int64_t k = (int64_t)(keys[p] & 0xFFFFFFFFu);
+      double w[3][3];
+      for (int m = 0; m < 3; ++m) { /* vertices in the camera frame */
+        const float *a = v + 3 * (int64_t)faces[3 * k + m];
+        double q[3] = {(double)a[0] - T[3], (double)a[1] - T[7], (double)a[2] - T[11]};
+        for (int c = 0; c < 3; ++c) w[m][c] = T[0 * 4 + c] * q[0] + T[1 * 4 + c] * q[1] + T[2 * 4 + c] * q[2];
+      }
+      double r[3];
+      ray64(cam, i, j, r);
+      double e1[3], e2[3], n[3];
+      for (int c = 0; c < 3; ++c) {
+        e1[c] = w[1][c] - w[0][c];
+        e2[c] = w[2][c] - w[0][c];
+      }
+      n[0] = e1[1] * e2[2] - e1[2] * e2[1];
+      n[1] = e1[2] * e2[0] - e1[0] * e2[2];
+      n[2] = e1[0] * e2[1] - e1[1] * e2[0];
+      double t = (n[0] * w[0][0] + n[1] * w[0][1] + n[2] * w[0][2]) /
+                 (n[0] * r[0] + n[1] * r[1] + n[2] * r[2]);
+      double h[3] = {t * r[0] - w[0][0], t * r[1] - w[0][1], t * r[2] - w[0][2]};
+      double nn = n[0] * n[0] + n[1] * n[1] + n[2] * n[2];
+      double c1[3] = {h[1] * e2[2] - h[2] * e2[1], h[2] * e2[0] - h[0] * e2[2], h[0] * e2[1] - h[1] * e2[0]};
+      double c2[3] = {e1[1] * h[2] - e1[2] * h[1], e1[2] * h[0] - e1[0] * h[2], e1[0] * h[1] - e1[1] * h[0]};
+      bary[2 * p] = (c1[0] * n[0] + c1[1] * n[1] + c1[2] * n[2]) / nn;
+      bary[2 * p + 1] = (c2[0] * n[0] + c2[1] * n[1] + c2[2] * n[2]) / nn;
+    }
+}
+
+/* ------------------------------------------------------------------------------------- */
+/* Table I and the least-squares surrogate                                                */
+/* ------------------------------------------------------------------------------------- */
+
+int orc_table1(int mc, int sc, float dz, float eps) {
+  if (mc == 0 && sc == 0) return fabsf(dz) <= eps ? 0 : 1;
+  if (mc == 0 && sc == 1) return dz > 0.0f ? 2 : 3;
+  if (mc == 1 && sc == 0) return dz <= 0.0f ? 4 : 5;
+  return -1; /* FU/FU, UO row, NaN row, NaN column: ignore */
+}
+
+/* Truncated-L2 residual of one pixel. On return *active says whether r varies with the pose
+ * (then d r / d t = *sgn), and *w is the cell weight; 0 is returned for ignored cells. */
+static double ls_residual(int outcome, float dz32, double dz, float eps, const orc_params *prm,
+                          int *active, double *sgn, double *w) {
+  *active = 0;
+  *sgn = 0.0;
+  switch (outcome) {
+    case 0: /* FO/FO inlier */
+      *w = prm->w_fofo;
+      *active = 1;
+      *sgn = 1.0;
+      return dz;
+    case 1: /* FO/FO outlier: truncated */
+      *w = prm->w_fofo;
+      return (double)eps;
+    case 2: /* FO map behind the FU scan interface: consistent */
+      *w = prm->w_fofu;
+      return 0.0;
+    case 3: /* FO map inside the scan's free space */
+      *w = prm->w_fofu;
+      if (-dz32 < eps) {
+        *active = 1;
+        *sgn = -1.0;
+        return -dz;
+      }
+      return (double)eps;
+    case 4: /* scan surface beyond the map's FU interface: consistent */
+      *w = prm->w_fufo;
+      return 0.0;
+    case 5: /* scan surface inside the map's free space */
+      *w = prm->w_fufo;
+      if (dz32 < eps) {
+        *active = 1;
+        *sgn = 1.0;
+        return dz;
+      }
+      return (double)eps;
+    default:
+      *w = 0.0;
+      return 0.0;
+  }
+}
+
+static int scan_class_of(const float *sd, const uint8_t *sc, int64_t p) {
+  float d = sd[p];
+  int c = sc[p];
+  if (c > 1 || !(fabsf(d) <= FLT_MAX)) return 2;
+  return c;
+}
+
+/* d t / d xi for twist xi = (rho, phi) under T <- T exp(xi^): -n/(n.r) and -t (r x n)/(n.r). */
+static void depth_jacobian(const double n[3], const double r[3], double t, double J[6]) {
+  double nr = n[0] * r[0] + n[1] * r[1] + n[2] * r[2];
+  double rxn[3] = {r[1] * n[2] - r[2] * n[1], r[2] * n[0] - r[0] * n[2], r[0] * n[1] - r[1] * n[0]};
+  for (int a = 0; a < 3; ++a) {
+    J[a] = -n[a] / nr;
+    J[3 + a] = -t * rxn[a] / nr;
+  }
+}
+
+int orc_cost(const float *v, const float *vr, int64_t V, const double centre[3],
+             const int32_t *faces, const uint8_t *labels, int64_t T, const double Twc[16],
+             const orc_cam *cam, const float *scan_depth, const uint8_t *scan_class,
+             const orc_params *prm, int residual_exact, int64_t counts[6], double *e_ls,
+             double grad[6], double jtj[21], int8_t *outcome, double *resid) {
+  int64_t P = (int64_t)cam->width * cam->height;
+  uint64_t *keys = (uint64_t *)malloc(sizeof(uint64_t) * (P > 0 ? P : 1));
+  if (!keys) return -1;
+  orc_render(vr, V, centre, faces, T, Twc, cam, keys, NULL, 0, NULL);
+  for (int k = 0; k < 6; ++k) counts[k] = 0;
+  double E = 0.0, g[6] = {0}, H[36] = {0};
+  for (int j = 0; j < cam->height; ++j)
+    for (int i = 0; i < cam->width; ++i) {
+      int64_t p = (int64_t)j * cam->width + i;
+      uint64_t key = keys[p];
+      int mc = key == KEY_EMPTY ? 3 : (int)labels[key & 0xFFFFFFFFu];
+      int sc = scan_class_of(scan_depth, scan_class, p);
+      float t32 = 0.0f;
+      if (key != KEY_EMPTY) {
+        uint32_t bits = (uint32_t)(key >> 32);
+        memcpy(&t32, &bits, 4);
+      }
+      float dz32 = t32 - scan_depth[p];
+      int oc = (mc == 3 || sc == 2) ? -1 : orc_table1(mc, sc, dz32, prm->eps);
+      if (outcome) outcome[p] = (int8_t)oc;
+      if (resid) resid[p] = 0.0;
+      if (oc < 0) continue;
+      counts[oc] += 1;
+      double n[3], d, r[3];
+      plane64(v, faces, (int64_t)(key & 0xFFFFFFFFu), Twc, n, &d);
+      ray64(cam, i, j, r);
+      double t64 = d / (n[0] * r[0] + n[1] * r[1] + n[2] * r[2]);
+      double dz = (residual_exact ? t64 : (double)t32) - (double)scan_depth[p];
+      int active;
+      double sgn, w;
+      double res = ls_residual(oc, dz32, dz, prm->eps, prm, &active, &sgn, &w);
+      if (resid) resid[p] = res;
+      E += 0.5 * w * res * res;
+      if (active) {
+        double J[6];
+        depth_jacobian(n, r, t64, J);
+        for (int a = 0; a < 6; ++a) {
+          J[a] *= sgn;
+          g[a] += w * res * J[a];
+        }
+        for (int a = 0; a < 6; ++a)
+          for (int b = 0; b < 6; ++b) H[6 * a + b] += w * J[a] * J[b];
+      }
+    }
+  free(keys);
+  *e_ls = E;
+  for (int a = 0; a < 6; ++a) grad[a] = g[a];
+  int q = 0;
+  for (int a = 0; a < 6; ++a)
+    for (int b = a; b < 6; ++b) jtj[q++] = H[6 * a + b];
+  return 0;
+}
+
+/* ------------------------------------------------------------------------------------- */
+/* SE(3)                                                                                  */
+/* ------------------------------------------------------------------------------------- */
+
+void orc_se3_right(const double T[16], const double xi[6], double out[16]) {
+  const double *rho = xi, *phi = xi + 3;
+  double th2 = phi[0] * phi[0] + phi[1] * phi[1] + phi[2] * phi[2], th = sqrt(th2);
+  double A, B, C; /* sin t / t, (1 - cos t)/t^2, (t - sin t)/t^3 */
+  if (th < 1e-4) {
+    A = 1.0 - th2 / 6.0 + th2 * th2 / 120.0;
+    B = 0.5 - th2 / 24.0 + th2 * th2 / 720.0;
+    C = 1.0 / 6.0 - th2 / 120.0 + th2 * th2 / 5040.0;
+  } else {
+    A = sin(th) / th;
+    B = (1.0 - cos(th)) / th2;
+    C = (th - sin(th)) / (th2 * th);
+  }
+  double K[9] = {0, -phi[2], phi[1], phi[2], 0, -phi[0], -phi[1], phi[0], 0};
+  double K2[9];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double s = 0;
+      for (int k = 0; k < 3; ++k) s += K[3 * i + k] * K[3 * k + j];
+      K2[3 * i + j] = s;
+    }
+  double R[9], Vm[9];
+  for (int i = 0; i < 9; ++i) {
+    double I = (i % 4 == 0) ? 1.0 : 0.0;
+    R[i] = I + A * K[i] + B * K2[i];
+    Vm[i] = I + B * K[i] + C * K2[i];
+  }
+  double t[3];
+  for (int i = 0; i < 3; ++i) t[i] = Vm[3 * i] * rho[0] + Vm[3 * i + 1] * rho[1] + Vm[3 * i + 2] * rho[2];
+  double E[16] = {R[0], R[1], R[2], t[0], R[3], R[4], R[5], t[1], R[6], R[7], R[8], t[2], 0, 0, 0, 1};
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      double s = 0;
+      for (int k = 0; k < 4; ++k) s += T[4 * i + k] * E[4 * k + j];
+      out[4 * i + j] = s;
+    }
+}
+
+double orc_cost_frozen(const float *v, const float *vr, int64_t V, const double centre[3],
+                       const int32_t *faces, const uint8_t *labels, int64_t T,
+                       const double Twc[16], const orc_cam *cam, const float *scan_depth,
+                       const uint8_t *scan_class, const orc_params *prm, const double xi[6]) {
+  int64_t P = (int64_t)cam->width * cam->height;
+  uint64_t *keys = (uint64_t *)malloc(sizeof(uint64_t) * (P > 0 ? P : 1));
+  if (!keys) return NAN;
+  orc_render(vr, V, centre, faces, T, Twc, cam, keys, NULL, 0, NULL);
+  double Tp[16];
+  orc_se3_right(Twc, xi, Tp);
+  double E = 0.0;
+  for (int j = 0; j < cam->height; ++j)
+    for (int i = 0; i < cam->width; ++i) {
+      int64_t p = (int64_t)j * cam->width + i;
+      uint64_t key = keys[p];
+      if (key == KEY_EMPTY) continue;
+      int mc = (int)labels[key & 0xFFFFFFFFu];
+      int sc = scan_class_of(scan_depth, scan_class, p);
+      if (sc == 2) continue;
+      float t32;
+      uint32_t bits = (uint32_t)(key >> 32);
+      memcpy(&t32, &bits, 4);
+      float dz32 = t32 - scan_depth[p];
+      int oc = orc_table1(mc, sc, dz32, prm->eps);
+      if (oc < 0) continue;
+      double n[3], d, r[3];
+      plane64(v, faces, (int64_t)(key & 0xFFFFFFFFu), Tp, n, &d);
+      ray64(cam, i, j, r);
+      double dz = d / (n[0] * r[0] + n[1] * r[1] + n[2] * r[2]) - (double)scan_depth[p];
+      int active;
+      double sgn, w;
+      /* activity is decided by the FP32 dz of the unperturbed pose: cells stay frozen */
+      double res = ls_residual(oc, dz32, dz, prm->eps, prm, &active, &sgn, &w);
+      E += 0.5 * w * res * res;
+    }
+  free(keys);
+  return E;
+}
+
+/* ------------------------------------------------------------------------------------- */
+/* Levenberg-Marquardt                                                                    */
+/* ------------------------------------------------------------------------------------- */
+
+/* Solve (H + lambda diag H) x = -g by Cholesky; returns 0 if not positive definite. */
+static int lm_solve(const double jtj[21], const double g[6], double lambda, double x[6]) {
+  double A[36], L[36] = {0};
+  int q = 0;
+  for (int a = 0; a < 6; ++a)
+    for (int b = a; b < 6; ++b) {
+      A[6 * a + b] = A[6 * b + a] = jtj[q++];
+    }
+  for (int a = 0; a < 6; ++a) A[7 * a] += lambda * A[7 * a];
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j <= i; ++j) {
+      double s = A[6 * i + j];
+      for (int k = 0; k < j; ++k) s -= L[6 * i + k] * L[6 * j + k];
+      if (i == j) {
+        if (!(s > 0)) return 0;
+        L[7 * i] = sqrt(s);
+      } else {
+        L[6 * i + j] = s / L[7 * j];
+      }
+    }
+  double y[6];
+  for (int i = 0; i < 6; ++i) {
+    double s = -g[i];
+    for (int k = 0; k < i; ++k) s -= L[6 * i + k] * y[k];
+    y[i] = s / L[7 * i];
+  }
+  for (int i = 5; i >= 0; --i) {
+    double s = y[i];
+    for (int k = i + 1; k < 6; ++k) s -= L[6 * k + i] * x[k];
+    x[i] = s / L[7 * i];
+  }
+  return 1;
+}
+
+int orc_align(const float *v, const float *vr, int64_t V, const double centre[3],
+              const int32_t *faces, const uint8_t *labels, int64_t T, const double Twc0[16],
+              const orc_cam *cam, const float *scan_depth, const uint8_t *scan_class,
+              const orc_params *prm, const orc_lm *lm, double Twc_out[16],
+              orc_lm_report *rep) {
+  double Tc[16], Tn[16];
+  memcpy(Tc, Twc0, sizeof(Tc));
+  int64_t cnt[6], cnt_n[6];
+  double E, g[6], H[21], En, gn[6], Hn[21];
+  orc_cost(v, vr, V, centre, faces, labels, T, Tc, cam, scan_depth, scan_class, prm, 0, cnt, &E,
+           g, H, NULL, NULL);
+  memset(rep, 0, sizeof(*rep));
+  rep->e_ls_initial = E;
+  rep->e_table_initial = cnt[1] + cnt[3] + cnt[5] - cnt[0] - cnt[2] - cnt[4];
+  double lambda = lm->lambda0;
+  int it;
+  for (it = 0; it < lm->max_iters; ++it) {
+    double dx[6];
+    if (!lm_solve(H, g, lambda, dx)) {
+      lambda *= lm->lambda_up;
+      continue;
+    }
+    double nrm = 0;
+    for (int a = 0; a < 6; ++a) nrm += dx[a] * dx[a];
+    if (sqrt(nrm) < lm->step_tol) {
+      rep->converged = 1;
+      break;
+    }
+    orc_se3_right(Tc, dx, Tn);
+    orc_cost(v, vr, V, centre, faces, labels, T, Tn, cam, scan_depth, scan_class, prm, 0, cnt_n,
+             &En, gn, Hn, NULL, NULL);
+    if (En < E) {
+      memcpy(Tc, Tn, sizeof(Tc));
+      E = En;
+      memcpy(g, gn, sizeof(g));
+      memcpy(H, Hn, sizeof(H));
+      memcpy(cnt, cnt_n, sizeof(cnt));
+      lambda /= lm->lambda_down;
+      rep->accepted += 1;
+    } else {
+      lambda *= lm->lambda_up;
+    }
+  }
+  rep->iters = it;
+  rep->e_ls_final = E;
+  rep->e_table_final = cnt[1] + cnt[3] + cnt[5] - cnt[0] - cnt[2] - cnt[4];
+  memcpy(Twc_out, Tc, sizeof(Tc));
+  return 0;
+}
+
+int orc_cost_batch(const float *v, const float *vr, int64_t V, const double centre[3],
+                   const int32_t *faces, const uint8_t *labels, int64_t T, const double *Twc,
+                   int N, const orc_cam *cam, const float *scan_depth,
+                   const uint8_t *scan_class, const orc_params *prm, int64_t *counts,
+                   double *e_ls, double *grad, double *jtj) {
+  int threads = 1;
+#ifdef _OPENMP
+#pragma omp parallel
+  {
+#pragma omp single
+    threads = omp_get_num_threads();
+  }
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+  for (int k = 0; k < N; ++k)
+    orc_cost(v, vr, V, centre, faces, labels, T, Twc + 16 * k, cam, scan_depth, scan_class, prm,
+             0, counts + 6 * k, e_ls + k, grad + 6 * k, jtj + 21 * k, NULL, NULL);
+  return threads;
+}

@@ -1,0 +1,125 @@
+/*
+ * rm_oracle.h -- CPU oracle for the RenderMap pose-cost path (Ryde & Ding, arXiv 1702.06813).
+ *
+ * TEST INFRASTRUCTURE ONLY. Only the tests, the smoke check and the benchmark's CPU-baseline
+ * leg may call this library. It shares no code, header, table or constant with the CUDA
+ * library; both are written from the paper and from the same written arithmetic contract
+ * for the z-buffer (the FP32 steps that decide which triangle a pixel sees).
+ *
+ * Every pointer is host memory. Layouts are dense, row major, C order.
+ */
+#ifndef RM_ORACLE_H
+#define RM_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Camera. model 0: pinhole, ray of pixel (i,j) = ((i+.5-cx)/fx, (j+.5-cy)/fy, 1), depth is z.
+ * model 1: ray table, `rays` holds H*W*3 float32 unit rays (camera frame), depth is range;
+ * az0/az_step/el0/el_step describe the table's layout (column i at azimuth az0+az_step*(i+.5),
+ * row j at elevation el0-el_step*j) and only serve to bound the pixels a triangle can cover. */
+typedef struct {
+  int32_t model, width, height, pad_;
+  float fx, fy, cx, cy;
+  float az0, az_step, el0, el_step;
+  float near_m, far_m;
+  const float *rays;
+} orc_cam;
+
+typedef struct {
+  float eps;                 /* Table I inlier threshold (0.1 m) */
+  float w_fofo, w_fofu, w_fufo; /* per-cell weights of the least-squares surrogate */
+} orc_params;
+
+typedef struct {
+  int64_t n_clipped;         /* triangles cut by the near plane */
+  int64_t n_guard_culled;    /* triangles dropped: a vertex projects beyond the guard band */
+  int64_t n_fragments;       /* covered (triangle, pixel) pairs before the depth test */
+} orc_stats;
+
+/* Map preparation: centre = midpoint of the FP64 bounding box of the FP32 vertices,
+ * out = float(v - centre). */
+void orc_recentre(const float *v, int64_t V, double centre[3], float *out);
+
+/* World-to-camera FP32 3x4 matrix from a camera-to-world FP64 pose and the map centre. */
+void orc_pose_matrix(const double Twc[16], const double centre[3], float M[12]);
+
+/* Camera-space FP32 vertices: vc = M * [v;1] in the contract's operation order. */
+void orc_transform(const float M[12], const float *v, int64_t V, float *vc);
+
+/* Z-buffer of camera-space geometry. keys: H*W uint64 (bits(depth)<<32 | tri id),
+ * 0xFFFF..FF where nothing is hit. frags (optional): per-pixel count of covering triangles
+ * before the depth test. brute != 0 tests every pixel against every triangle. */
+int orc_zbuffer(const float *vc, const int32_t *faces, int64_t T, const orc_cam *cam,
+                uint64_t *keys, int32_t *frags, int brute, orc_stats *st);
+
+/* Full render from a pose: recentred vertices + centre + pose -> keys. */
+int orc_render(const float *vr, int64_t V, const double centre[3], const int32_t *faces,
+               int64_t T, const double Twc[16], const orc_cam *cam, uint64_t *keys,
+               int32_t *frags, int brute, orc_stats *st);
+
+/* FP64 ray-plane depth of every pixel's winner, from the ORIGINAL vertices and the FP64
+ * pose; NaN where keys holds no hit. */
+void orc_depth_exact(const float *v, const int32_t *faces, const double Twc[16],
+                     const orc_cam *cam, const uint64_t *keys, double *depth);
+
+/* Barycentrics (b1, b2) of the ray-plane hit on the winner, FP64; NaN where no hit. */
+void orc_barycentrics(const float *v, const int32_t *faces, const double Twc[16],
+                      const orc_cam *cam, const uint64_t *keys, double *bary);
+
+/* Table I outcome of one pixel: returns -1 ignore, else 0..5 =
+ * {FO/FO reward, FO/FO penalty, FO/FU reward, FO/FU penalty, FU/FO reward, FU/FO penalty}.
+ * map_class 0 FO, 1 FU, 2 UO, 3 NaN; scan_class 0 FO, 1 FU, 2 NaN. */
+int orc_table1(int map_class, int scan_class, float dz, float eps);
+
+/* Cost of one pose. counts[6] per outcome; e_ls = 1/2 sum w r^2; grad[6] = sum w r J;
+ * jtj[21] = upper triangle (row major) of sum w J J^T. Twist xi = (rho, phi), right
+ * perturbation T <- T exp(xi^). outcome (optional, H*W int8) per-pixel outcome code;
+ * resid (optional, H*W double) per-pixel residual. residual_exact != 0 takes residuals from
+ * the FP64 depth instead of the z-buffer's FP32 depth. */
+int orc_cost(const float *v, const float *vr, int64_t V, const double centre[3],
+             const int32_t *faces, const uint8_t *labels, int64_t T, const double Twc[16],
+             const orc_cam *cam, const float *scan_depth, const uint8_t *scan_class,
+             const orc_params *prm, int residual_exact, int64_t counts[6], double *e_ls,
+             double grad[6], double jtj[21], int8_t *outcome, double *resid);
+
+/* Frozen-visibility cost: the z-buffer winners and residual cells of pose Twc, with every
+ * winner's plane re-intersected in FP64 at pose Twc * exp(xi^). */
+double orc_cost_frozen(const float *v, const float *vr, int64_t V, const double centre[3],
+                       const int32_t *faces, const uint8_t *labels, int64_t T,
+                       const double Twc[16], const orc_cam *cam, const float *scan_depth,
+                       const uint8_t *scan_class, const orc_params *prm, const double xi[6]);
+
+/* SE(3) exponential, out = Twc * exp(xi^). */
+void orc_se3_right(const double Twc[16], const double xi[6], double out[16]);
+
+/* Levenberg-Marquardt on the least-squares surrogate (FP64, Cholesky 6x6). */
+typedef struct {
+  int32_t max_iters; int32_t pad_;
+  double lambda0, lambda_up, lambda_down, step_tol;
+} orc_lm;
+typedef struct {
+  int32_t iters, accepted, converged, pad_;
+  double e_ls_initial, e_ls_final;
+  int64_t e_table_initial, e_table_final;
+} orc_lm_report;
+int orc_align(const float *v, const float *vr, int64_t V, const double centre[3],
+              const int32_t *faces, const uint8_t *labels, int64_t T, const double Twc0[16],
+              const orc_cam *cam, const float *scan_depth, const uint8_t *scan_class,
+              const orc_params *prm, const orc_lm *lm, double Twc_out[16],
+              orc_lm_report *rep);
+
+/* Cost of N poses (OpenMP over poses when built with it): e_ls[N], counts[N*6], grad[N*6],
+ * jtj[N*21]. Returns the number of threads used. */
+int orc_cost_batch(const float *v, const float *vr, int64_t V, const double centre[3],
+                   const int32_t *faces, const uint8_t *labels, int64_t T, const double *Twc,
+                   int N, const orc_cam *cam, const float *scan_depth,
+                   const uint8_t *scan_class, const orc_params *prm, int64_t *counts,
+                   double *e_ls, double *grad, double *jtj);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
