@@ -1,0 +1,335 @@
+#!/usr/bin/env python3
+"""Throughput of the RenderMap pose-cost hot path on one GB300 (or N, one replica each).
+
+One step = the whole hot path for one batch: render the labelled 1M-triangle map's z-buffer
+from each of 256 candidate poses at 640x480, apply Table I per pixel with the truncated
+least-squares residual, and reduce the adjoint gradient and Gauss-Newton matrix per pose
+(rm_cost_grad). Metric: pose evaluations per second. Prints ONE JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pose evals/s (render+residual+grad) 640x480, 1M tris; % of HBM roofline"
+UNIT = "pose evals/s"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
+
+
+def args_():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--poses", type=int, default=256)
+    ap.add_argument("--seed", type=int, default=3000)
+    ap.add_argument("--cpu-sample", type=int, default=32, help="poses in the oracle's timed sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return p, "measured"
+    except OSError:
+        return PEAKS_FALLBACK, "fallback"
+
+
+def algorithmic_bytes(V, T, P):
+    """Bytes one pose evaluation must touch: vertices 12 V, faces + labels 13 T, scan 5 P."""
+    return {"k_vertex_pinhole": 12 * V, "k_setup_pinhole": 13 * T, "k_raster": 5 * P,
+            "k_reduce": 0, "total": 12 * V + 13 * T + 5 * P}
+
+
+class Clocks:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"] + (["-i", self.uuid] if self.uuid else []),
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(w, sample):
+    import oracle
+    oracle.build()
+    om = oracle.OracleMap(w["mesh"].vertices, w["mesh"].faces, w["mesh"].labels)
+    sd, sc = w["scan"]
+    poses = w["poses"][:sample]
+    om.cost_batch(poses[:1], w["cam"], sd, sc)  # page in
+    t0 = time.perf_counter()
+    out = om.cost_batch(poses, w["cam"], sd, sc)
+    dt = time.perf_counter() - t0
+    return {"value": len(poses) / dt, "unit": UNIT, "cores": int(out["threads"]), "kind": "oracle",
+            "sample": f"{len(poses)} of the {len(w['poses'])} candidate poses, full 640x480 render + "
+                      f"Table I + FP64 gradient each, OpenMP over poses ({dt:.1f} s wall)"}
+
+
+def run_reference(a):
+    """The oracle timed as it stands, same workload and metric (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import synth
+    w = synth.workload_headline(a.seed, a.poses)
+    import oracle
+    oracle.build()
+    om = oracle.OracleMap(w["mesh"].vertices, w["mesh"].faces, w["mesh"].labels)
+    sd, sc = w["scan"]
+    per_step = max(1, min(a.cpu_sample, 16))
+    steps = max(1, min(a.steps, 3))
+    for k in range(max(0, min(a.warmup, 1))):
+        om.cost_batch(w["poses"][:per_step], w["cam"], sd, sc)
+    t0 = time.perf_counter()
+    threads = 1
+    for k in range(steps):
+        sel = w["poses"][(k * per_step) % len(w["poses"]):][:per_step]
+        threads = om.cost_batch(sel, w["cam"], sd, sc)["threads"]
+    dt = time.perf_counter() - t0
+    v = steps * per_step / dt
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus,
+        "steps": steps, "warmup": a.warmup, "ms_per_step": 1e3 * dt / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w["name"], "poses_per_step": per_step},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": int(threads), "kind": "oracle",
+                         "sample": f"{per_step} poses per step of the {len(w['poses'])}-pose batch"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def main():
+    a = args_()
+    if a.impl == "reference":
+        run_reference(a)
+        return
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    import __graft_entry__
+    __graft_entry__.build_library()
+    import ctypes
+
+    import paper_1702_06813_gb300 as rm
+    from paper_1702_06813_gb300 import _native as N
+    import synth
+
+    w = synth.workload_headline(a.seed + 17 * rank, a.poses)
+    mesh, cam = w["mesh"], w["cam"]
+    gm = rm.Map(mesh.vertices, mesh.faces, mesh.labels)
+    intr = rm.Intrinsics.from_camera(cam)
+    scan = rm.Scan.make(intr, *w["scan"])
+    poses = torch.as_tensor(w["poses"].reshape(-1, 16), dtype=torch.float64, device="cuda")
+    n = poses.shape[0]
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
+
+    def step():
+        return rm.cost_grad(gm, scan, poses)
+
+    for _ in range(max(3, a.warmup)):
+        out = step()
+    torch.cuda.synchronize()
+    tune = gm.get_tuning()
+
+    def timed(fn, k_steps, profile=False):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k_steps)]
+        barrier()
+        torch.cuda.synchronize()
+        if profile:
+            gm.profile(True)
+        for k in range(k_steps):
+            flush.fill_(k & 0xFF)
+            evs[k][0].record(stream)
+            fn()
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = sum(e0.elapsed_time(e1) for e0, e1 in evs)
+        prof = None
+        if profile:
+            prof = gm.profile_read()
+            gm.profile(False)
+        return ms, prof
+
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        pass
+    for attempt in range(2):
+        clk = Clocks(uuid)
+        clk.start()
+        ms, prof = timed(step, a.steps, profile=True)
+        clocks = clk.stop()
+        bad = {"hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"} & set(clocks["reasons"])
+        if not bad:
+            break
+    clocks["remeasured"] = attempt > 0
+    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms = float(ms_t.item())
+    ms_per_step = ms / a.steps
+    value = world * n * a.steps / (ms * 1e-3)
+
+    # plain form: one pose per call
+    def plain():
+        for i in range(n):
+            rm.cost_grad(gm, scan, poses[i:i + 1])
+    plain_steps = max(1, min(3, a.steps))
+    ms_plain, _ = timed(plain, plain_steps)
+    plain_value = n * plain_steps / (ms_plain * 1e-3)
+
+    # end to end through the C ABI with pinned host buffers
+    hp = torch.empty((n, 16), dtype=torch.float64).pin_memory()
+    hp.copy_(torch.as_tensor(w["poses"].reshape(-1, 16)))
+    hd = torch.as_tensor(w["scan"][0]).pin_memory()
+    hc = torch.as_tensor(w["scan"][1]).pin_memory()
+    o_counts = torch.empty((n, 6), dtype=torch.int64).pin_memory()
+    o_et = torch.empty(n, dtype=torch.int64).pin_memory()
+    o_els = torch.empty(n, dtype=torch.float64).pin_memory()
+    o_g = torch.empty((n, 6), dtype=torch.float64).pin_memory()
+    o_h = torch.empty((n, 21), dtype=torch.float64).pin_memory()
+    cs = N.rm_scan(intr.c(), hd.data_ptr(), hc.data_ptr())
+    cout = N.rm_cost_out(o_counts.data_ptr(), o_et.data_ptr(), o_els.data_ptr(), o_g.data_ptr(), o_h.data_ptr())
+    prm = rm.cost_params()
+    sp = ctypes.c_void_p(stream.cuda_stream)
+
+    def e2e_step():
+        N.check(N.lib().rm_cost_grad(gm.handle, ctypes.byref(cs), ctypes.c_void_p(hp.data_ptr()), n,
+                                     ctypes.byref(prm), ctypes.byref(cout), sp))
+
+    for _ in range(2):
+        e2e_step()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = world * n * a.steps / float(e2e_t.item())
+    h2d = hp.numel() * 8 + hd.numel() * 4 + hc.numel()
+    d2h = n * (6 * 8 + 8 + 8 + 6 * 8 + 21 * 8)
+    # sanity: the e2e numbers equal the device path's
+    ok = bool(torch.equal(o_counts, out["counts"].cpu()) and torch.equal(o_els, out["e_ls"].cpu()))
+
+    # roofline of the dominant kernel
+    P = cam.width * cam.height
+    ab = algorithmic_bytes(mesh.n_verts, mesh.n_tris, P)
+    pk, pk_kind = peaks()
+    kern = prof["kernels"]
+    dom = max(kern, key=lambda k: kern[k][1])
+    launches, tot = kern[dom]
+    per_launch_poses = n * a.steps / launches
+    avg_s = tot * 1e-3 / launches
+    achieved = ab[dom] * per_launch_poses / avg_s / 1e9
+    share = {k: round(v[1] / sum(x[1] for x in kern.values()), 4) for k, v in kern.items()}
+    step_frac = ab["total"] * (n * a.steps) / (ms * 1e-3) / 1e9 / pk["hbm_gbs"]
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+        "warmup": max(3, a.warmup), "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w["name"], "poses_per_gpu": n, "triangles": mesh.n_tris,
+                   "vertices": mesh.n_verts, "image": [cam.width, cam.height],
+                   "l2": "flushed between timed steps (256 MiB write)",
+                   "tile": list(tune["tile"]), "bin_capacity": tune["bin_capacity"],
+                   "plain_one_pose_per_call_evals_per_s": plain_value,
+                   "batched_over_plain": value / plain_value,
+                   "algorithmic_mb_per_eval": ab["total"] / 1e6,
+                   "step_hbm_roofline_frac": step_frac,
+                   "kernel_share": share, "e2e_matches_device": ok},
+        "clocks": clocks,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(prof["launches"] // a.steps) * a.steps,
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": pk["hbm_gbs"],
+                     "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "traffic": None,
+                     "peak_kind": pk_kind, "avg_launch_ms": avg_s * 1e3,
+                     "poses_per_launch": per_launch_poses},
+    }
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, a.cpu_sample)
+    if rank == 0:
+        print(json.dumps(line))
+    gm.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

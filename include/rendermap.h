@@ -1,0 +1,219 @@
+/*
+ * rendermap.h -- C ABI of the GB300 RenderMap pose-cost library (librendermap.so).
+ *
+ * The library evaluates how well a 6-DoF sensor pose aligns an observed range image with a
+ * labelled triangle-mesh map, following Ryde & Ding, "RenderMap: Exploiting the Link Between
+ * Perception and Rendering for Dense Mapping" (arXiv 1702.06813):
+ *   - the map is the mesh of the interfaces between free, occupied and unknown space, each
+ *     face labelled free-occupied (FO), free-unknown (FU) or unknown-occupied (UO) (Sec. III.A,
+ *     Fig. 3);
+ *   - E(X) = C(R(T(X)), Z_s) (Eq. 1): render the map's z-buffer R from the camera pose and
+ *     compare it per pixel with the scan Z_s;
+ *   - the comparison is Table I (Sec. III.B), summed over all pixels.
+ * On top of the paper's cost the library computes a truncated least-squares surrogate with
+ * the same cells and thresholds, its derivative with respect to a pose twist, and
+ * Levenberg-Marquardt steps on it (the paper's Sec. III.C optimiser is derivative-free).
+ *
+ * All work runs in CUDA kernels for sm_103a on the calling thread's current device.
+ *
+ * Conventions
+ *  - Pose: 16 doubles, row-major 4x4 camera-to-world transform T_wc (p_w = R p_c + t).
+ *  - Camera frame: x right, y down, z forward. Pinhole rays of pixel (i, j) are
+ *    ((i + .5 - cx)/fx, (j + .5 - cy)/fy, 1), so pinhole depth is z-depth; ray-table rays are
+ *    unit vectors, so ray-table depth is range.
+ *  - Images are row-major H x W (pixel (i, j) at index j*W + i), one image per pose.
+ *  - Twist: xi = (rho, phi) (translation first), right perturbation T <- T exp(xi^).
+ *  - Packed symmetric 6x6: the 21 entries of the upper triangle, row major
+ *    ((0,0),(0,1),...,(0,5),(1,1),...,(5,5)).
+ *  - Pointers marked "host or device" may point to either; the library finds out with
+ *    cudaPointerGetAttributes. Host outputs make the call wait for the stream.
+ *
+ * Errors: every entry point returns an rm_status. Nothing crosses the ABI as an exception and
+ * no kernel traps: device-side problems (a full bin, a wait that ran out) are recorded in a
+ * status word that the call reads back. rm_last_error() gives a message for the calling
+ * thread's last failure.
+ *
+ * Threading: calls on one map are serialised by the map (they share its scratch memory).
+ * Different maps may be used from different threads concurrently.
+ */
+#ifndef RENDERMAP_H
+#define RENDERMAP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RM_OK = 0,
+  RM_EINVAL = 1,     /* bad argument: null pointer, size, index, label or non-finite input */
+  RM_ENOMEM = 2,     /* device memory allocation failed */
+  RM_ECUDA = 3,      /* a CUDA runtime call failed (message in rm_last_error) */
+  RM_EOVERFLOW = 4,  /* a screen-tile bin overflowed and could not be grown */
+  RM_ETIMEOUT = 5,   /* a bounded device-side wait gave up */
+  RM_ENOTCONV = 6    /* rm_align stopped at max_iters without meeting step_tol */
+} rm_status;
+
+/* Face labels (Sec. III.A): the interface a map face lies on. */
+enum { RM_LABEL_FO = 0, RM_LABEL_FU = 1, RM_LABEL_UO = 2 };
+/* Scan pixel classes (Sec. III.B): a return (FO), no return drawn at the sensor's maximum
+ * range (FU, Sec. III.A), or a dead pixel (NaN). A scan pixel whose depth is not finite, or
+ * whose class byte is above 2, counts as NaN. */
+enum { RM_SCAN_FO = 0, RM_SCAN_FU = 1, RM_SCAN_NAN = 2 };
+/* Table I outcomes, the index into every counts[6] array. */
+enum {
+  RM_FOFO_REWARD = 0,   /* map FO, scan FO, |dz| <= eps  : -1 */
+  RM_FOFO_PENALTY = 1,  /* map FO, scan FO, |dz| >  eps  : +1 */
+  RM_FOFU_REWARD = 2,   /* map FO, scan FU, dz > 0       : -1 */
+  RM_FOFU_PENALTY = 3,  /* map FO, scan FU, dz <= 0      : +1 */
+  RM_FUFO_REWARD = 4,   /* map FU, scan FO, dz <= 0      : -1 */
+  RM_FUFO_PENALTY = 5   /* map FU, scan FO, dz > 0       : +1 */
+};
+enum { RM_PINHOLE = 0, RM_RAYTABLE = 1 };
+
+typedef struct {
+  int32_t model;            /* RM_PINHOLE or RM_RAYTABLE */
+  int32_t width, height;    /* pixels, 1..16384 */
+  int32_t reserved;         /* 0 */
+  float fx, fy, cx, cy;     /* pinhole focal lengths and principal point, pixels */
+  /* RM_RAYTABLE layout: column i looks at azimuth az0 + az_step*(i + .5), row j at elevation
+   * el0 - el_step*j (radians; azimuth from +z toward +x, elevation toward -y). The layout only
+   * bounds which pixels a triangle may cover; coverage and depth use `rays`. */
+  float az0, az_step, el0, el_step;
+  float near_m;             /* render clip: only depths >= near_m are kept (> 0) */
+  float far_m;              /* and <= far_m (INFINITY allowed) */
+  const float *rays;        /* RM_RAYTABLE only: H*W*3 float32 unit rays, camera frame, host
+                               or device; each ray within 0.5 px of the layout above */
+} rm_intrinsics;
+
+/* Observed scan Z_s (Eq. 1): depth and class per pixel, same layout and size as `intr`. */
+typedef struct {
+  rm_intrinsics intr;
+  const float *depth;       /* H*W float32 metres (z-depth / range), host or device */
+  const uint8_t *cls;       /* H*W uint8 RM_SCAN_*, host or device */
+} rm_scan;
+
+typedef struct {
+  float eps;                /* Table I inlier threshold, metres (the paper's 0.1) */
+  float w_fofo, w_fofu, w_fufo; /* weights of the least-squares surrogate per Table I row/col */
+} rm_cost_params;
+
+/* Per-pose outputs of rm_cost / rm_cost_grad; any pointer may be NULL; host or device. */
+typedef struct {
+  int64_t *counts;          /* N*6 pixels per Table I outcome (RM_FOFO_REWARD ...) */
+  int64_t *e_table;         /* N   Table I cost: penalties minus rewards (Sec. III.B) */
+  double *e_ls;             /* N   1/2 sum w r^2 of the truncated least-squares surrogate */
+  double *grad;             /* N*6 d e_ls / d xi = sum w r J (rm_cost_grad only) */
+  double *jtj;              /* N*21 packed sum w J J^T (rm_cost_grad only) */
+} rm_cost_out;
+
+/* Execution knobs; a zeroed struct (or NULL) means "library defaults / autotuned". */
+typedef struct {
+  int32_t tile_w, tile_h;   /* screen tile, pixels: 16x16, 32x16 or 32x32 */
+  int32_t bin_capacity;     /* triangle records per tile bin (grown on overflow) */
+  int32_t wave_poses;       /* poses processed together per kernel wave */
+  int32_t async_status;     /* 1: do not read the device status back (graph capture);
+                               check it later with rm_status_sync */
+  int32_t reserved[3];
+} rm_tuning;
+
+typedef struct {
+  int32_t max_iters;        /* LM iterations (each one render+residual+gradient) */
+  int32_t reserved;
+  double lambda0;           /* initial damping (1e-3) */
+  double lambda_up, lambda_down; /* damping factor on reject / accept (10, 10) */
+  double step_tol;          /* stop when |delta xi| < step_tol */
+} rm_align_params;
+
+typedef struct {
+  int32_t iters, accepted, converged, reserved;
+  double e_ls_initial, e_ls_final;
+  int64_t e_table_initial, e_table_final;
+} rm_align_report;
+
+typedef struct rm_map rm_map;
+
+/* Build a map from host arrays: vertices V*3 float32 (world, metres), faces T*3 int32
+ * (indices into vertices), labels T uint8 (RM_LABEL_*). The map copies everything to the
+ * device, re-centres the vertices on their bounding-box centre (in FP64, rounded back to
+ * FP32; poses are shifted to match) and precomputes unit face normals. Ownership: the
+ * caller keeps its arrays; *out is released with rm_map_destroy.
+ * Errors: RM_EINVAL for null pointers, negative sizes, T >= 2^31, an index outside [0, V),
+ * a label above 2 or a non-finite vertex; RM_ENOMEM; RM_ECUDA. (Sec. III.A, Fig. 3.) */
+rm_status rm_map_create(const float *vertices, int64_t n_vertices, const int32_t *faces,
+                        const uint8_t *labels, int64_t n_faces, rm_map **out);
+void rm_map_destroy(rm_map *map);
+/* Sizes and the re-centring offset of a map (any output may be NULL). */
+rm_status rm_map_info(const rm_map *map, int64_t *n_vertices, int64_t *n_faces,
+                      double centre[3]);
+rm_status rm_map_set_tuning(rm_map *map, const rm_tuning *tuning);
+rm_status rm_map_get_tuning(const rm_map *map, rm_tuning *tuning);
+
+/* R(Y) of Eq. 1: the z-buffer of the map seen from each of N poses. The z-buffer keeps, per
+ * pixel, the nearest triangle under the library's FP32 rasterisation contract (8-bit
+ * sub-pixel snapping, top-left fill rule, one sample at the pixel centre, no anti-aliasing
+ * as in Sec. V; ties go to the lower triangle id).
+ * depth: N*H*W float32, NaN where the ray hits nothing (the paper's NaN, Sec. III.B);
+ * tri_id: optional N*H*W int32, -1 where nothing is hit;
+ * bary: optional N*H*W*2 float32 barycentrics (b1, b2) of the hit on that triangle.
+ * All outputs host or device; `poses` host or device. stream: a cudaStream_t or NULL. */
+rm_status rm_render_depth(rm_map *map, const double *poses, int32_t n_poses,
+                          const rm_intrinsics *intr, float *depth, int32_t *tri_id,
+                          float *bary, void *stream);
+
+/* E(X) of Eq. 1 with C from Table I (Sec. III.B) for N poses against one scan, plus the
+ * least-squares surrogate: counts, e_table and e_ls in `out` (grad / jtj ignored). */
+rm_status rm_cost(rm_map *map, const rm_scan *scan, const double *poses, int32_t n_poses,
+                  const rm_cost_params *params, const rm_cost_out *out, void *stream);
+
+/* As rm_cost, plus the adjoint: the gradient of e_ls with respect to the pose twist and the
+ * Gauss-Newton matrix sum w J J^T, from the ray-plane depth t = d_c / (n_c . r):
+ * dt/drho = -n_c / (n_c . r), dt/dphi = -t (r x n_c) / (n_c . r). */
+rm_status rm_cost_grad(rm_map *map, const rm_scan *scan, const double *poses,
+                       int32_t n_poses, const rm_cost_params *params, const rm_cost_out *out,
+                       void *stream);
+
+/* Pose retraction used by the Levenberg-Marquardt step and by autograd bindings:
+ * out_k = poses_k exp(twists_k^) in FP64 on the device (N*16 doubles out), and optionally
+ * jr (N*36, row major) = the SE(3) right Jacobian J_r(twist_k), with which
+ * d e(T exp(xi)) / d xi = J_r(xi)^T grad. poses N*16, twists N*6; all host or device.
+ * Uses stream-ordered device scratch when any pointer is on the host, and then waits. */
+rm_status rm_pose_retract(const double *poses, const double *twists, int32_t n_poses,
+                          double *out, double *jr, void *stream);
+
+/* Levenberg-Marquardt alignment of one scan from init_pose (16 doubles, host or device):
+ * each iteration renders, evaluates the surrogate and its gradient, solves
+ * (H + lambda diag H) delta = -g in FP64 on the device, and accepts T exp(delta^) if e_ls
+ * drops. pose_out (16 doubles) and rep (optional) are host or device / host.
+ * Returns RM_ENOTCONV (with pose_out valid) when max_iters is reached first. */
+rm_status rm_align(rm_map *map, const rm_scan *scan, const double *init_pose,
+                   const rm_cost_params *params, const rm_align_params *lm, double *pose_out,
+                   rm_align_report *rep, void *stream);
+
+/* Per-kernel timing, recorded with CUDA events on the launch stream around every kernel
+ * the map launches while enabled. rm_profile(map, 1) clears the record and starts, 0 stops.
+ * rm_profile_read waits for the recorded events and fills up to `cap` entries (one per
+ * kernel kind: k_vertex_pinhole, k_setup_pinhole, k_raster, k_reduce), *n with the count, and
+ * *launches (optional) with the number of kernels launched since recording started. */
+typedef struct {
+  char name[48];
+  int64_t launches;
+  double total_ms;
+} rm_kernel_time;
+rm_status rm_profile(rm_map *map, int32_t enable);
+rm_status rm_profile_read(rm_map *map, rm_kernel_time *out, int32_t cap, int32_t *n,
+                          int64_t *launches);
+
+/* Reads and clears the map's device status word after work queued with async_status = 1;
+ * returns RM_OK, RM_EOVERFLOW or RM_ETIMEOUT. */
+rm_status rm_status_sync(rm_map *map, void *stream);
+
+/* Message for the calling thread's last non-RM_OK status ("" if none). */
+const char *rm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RENDERMAP_H */

@@ -1,0 +1,10 @@
+"""GB300-native RenderMap pose-cost engine (Ryde & Ding, arXiv 1702.06813).
+
+The map is a labelled triangle mesh of the free/occupied/unknown interfaces (Sec. III.A); a
+pose is scored by rendering the map's z-buffer from it and comparing it per pixel with an
+observed range image by Table I (Sec. III.B, Eq. 1). All of it runs in hand-written sm_103a
+CUDA kernels behind the C ABI of include/rendermap.h; this package is the thin binding.
+"""
+from .rendermap import (Intrinsics, Map, RenderMapCost, Scan, align, cost, cost_grad,  # noqa: F401
+                        cost_params, pose_retract, render_depth, OUTCOMES, RM_PINHOLE, RM_RAYTABLE)
+from ._native import RenderMapError, exported_symbols  # noqa: F401

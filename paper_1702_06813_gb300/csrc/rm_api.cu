@@ -1,0 +1,722 @@
+// rm_api.cu -- the C ABI declared in include/rendermap.h.
+//
+// Host-side runtime: map upload (FP64 re-centring, face normals), a per-map scratch arena
+// carved per call, host/device pointer handling, wave scheduling of poses, bin-capacity
+// growth on overflow, the device status word and the Levenberg-Marquardt driver.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "rendermap.h"
+#include "rm_kernels.cuh"
+
+using rmk::DevCam;
+using rmk::TileGeom;
+using rmk::TriRec;
+using rmk::WaveArgs;
+
+namespace {
+
+thread_local std::string g_err;
+
+rm_status fail(rm_status s, const std::string &msg) {
+  g_err = msg;
+  return s;
+}
+
+#define RM_CK(call)                                                                       \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(e_ == cudaErrorMemoryAllocation ? RM_ENOMEM : RM_ECUDA,                 \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                   \
+  } while (0)
+
+#define RM_TRY(expr)               \
+  do {                             \
+    rm_status s_ = (expr);         \
+    if (s_ != RM_OK) return s_;    \
+  } while (0)
+
+bool on_device(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Sequential carving of one allocation.
+struct Carver {
+  char *base;
+  size_t off = 0;
+  template <class T>
+  T *take(size_t n) {
+    off = align_up(off, 256);
+    T *p = reinterpret_cast<T *>(base ? base + off : nullptr);
+    off += sizeof(T) * std::max<size_t>(n, 1);
+    return p;
+  }
+};
+
+}  // namespace
+
+struct rm_map {
+  int device = 0;
+  int64_t V = 0, T = 0;
+  double centre[3] = {0, 0, 0};
+  float4 *d_v = nullptr;
+  int4 *d_faces = nullptr;
+  float4 *d_planes = nullptr;
+  char *arena = nullptr;
+  size_t arena_bytes = 0;
+  unsigned *d_status = nullptr;
+  unsigned *h_status = nullptr;
+  rm_tuning tuning{};
+  int cap = 2048;
+  std::mutex mu;
+  // profiling: events recorded around each kernel of each wave while enabled
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_free;
+  std::vector<std::array<cudaEvent_t, 5>> ev_pending;
+  double prof_ms[4] = {0, 0, 0, 0};
+  long long prof_n[4] = {0, 0, 0, 0};
+  long long launches = 0;  // kernels launched since the last rm_profile(map, 1)
+};
+
+namespace {
+
+rm_status ensure_arena(rm_map *m, size_t bytes, cudaStream_t s) {
+  if (bytes <= m->arena_bytes) return RM_OK;
+  RM_CK(cudaStreamSynchronize(s));
+  if (m->arena) RM_CK(cudaFree(m->arena));
+  m->arena = nullptr;
+  m->arena_bytes = 0;
+  size_t want = align_up(bytes + bytes / 8, 1 << 20);
+  RM_CK(cudaMalloc(&m->arena, want));
+  m->arena_bytes = want;
+  return RM_OK;
+}
+
+rm_status check_intr(const rm_intrinsics *in) {
+  if (!in) return fail(RM_EINVAL, "intrinsics is NULL");
+  if (in->width < 1 || in->height < 1 || in->width > 16384 || in->height > 16384)
+    return fail(RM_EINVAL, "image size must be 1..16384");
+  if (!(in->near_m > 0.0f) || !(in->far_m >= in->near_m))
+    return fail(RM_EINVAL, "need 0 < near_m <= far_m");
+  if (in->model == RM_PINHOLE) {
+    if (!(std::isfinite(in->fx) && std::isfinite(in->fy) && in->fx != 0.0f && in->fy != 0.0f &&
+          std::isfinite(in->cx) && std::isfinite(in->cy)))
+      return fail(RM_EINVAL, "pinhole fx, fy must be finite and non-zero, cx, cy finite");
+    return RM_OK;
+  }
+  if (in->model == RM_RAYTABLE) return fail(RM_EINVAL, "ray-table camera model is not built yet");
+  return fail(RM_EINVAL, "unknown camera model");
+}
+
+TileGeom make_tiles(const rm_map *m, const rm_intrinsics *in) {
+  TileGeom tg;
+  tg.tw = m->tuning.tile_w > 0 ? m->tuning.tile_w : 32;
+  tg.th = m->tuning.tile_h > 0 ? m->tuning.tile_h : 32;
+  tg.ntx = (in->width + tg.tw - 1) / tg.tw;
+  tg.nty = (in->height + tg.th - 1) / tg.th;
+  tg.ntiles = tg.ntx * tg.nty;
+  tg.cap = m->cap;
+  return tg;
+}
+
+DevCam make_cam(const rm_intrinsics *in, const float *d_rays) {
+  DevCam c;
+  c.model = in->model;
+  c.W = in->width;
+  c.H = in->height;
+  c.pad = 0;
+  c.fx = in->fx;
+  c.fy = in->fy;
+  c.cx = in->cx;
+  c.cy = in->cy;
+  c.az0 = in->az0;
+  c.az_step = in->az_step;
+  c.el0 = in->el0;
+  c.el_step = in->el_step;
+  c.near_m = in->near_m;
+  c.far_m = in->far_m;
+  c.rays = d_rays;
+  return c;
+}
+
+int wave_size(const rm_map *m, int n, const TileGeom &tg) {
+  if (m->tuning.wave_poses > 0) return std::min(n, m->tuning.wave_poses);
+  // keep per-wave scratch near 2 GiB
+  size_t per = (size_t)m->V * 24 + (size_t)tg.ntiles * ((size_t)tg.cap * sizeof(TriRec) + 8 * 40);
+  size_t w = std::max<size_t>(1, (size_t(2) << 30) / std::max<size_t>(per, 1));
+  return (int)std::min<size_t>(std::min<size_t>(w, 64), (size_t)n);
+}
+
+rm_status take_events(rm_map *m, cudaEvent_t *ev) {
+  for (int k = 0; k < 5; ++k) {
+    if (m->ev_free.empty()) {
+      cudaEvent_t e;
+      RM_CK(cudaEventCreate(&e));
+      m->ev_free.push_back(e);
+    }
+    ev[k] = m->ev_free.back();
+    m->ev_free.pop_back();
+  }
+  return RM_OK;
+}
+
+rm_status drain_events(rm_map *m) {
+  for (auto &ev : m->ev_pending) {
+    RM_CK(cudaEventSynchronize(ev[4]));
+    for (int k = 0; k < 4; ++k) {
+      float ms = 0.0f;
+      RM_CK(cudaEventElapsedTime(&ms, ev[k], ev[k + 1]));
+      m->prof_ms[k] += ms;
+      m->prof_n[k] += 1;
+    }
+    for (auto e : ev) m->ev_free.push_back(e);
+  }
+  m->ev_pending.clear();
+  return RM_OK;
+}
+
+// One wave, with events around its kernels when profiling.
+rm_status wave(rm_map *m, const WaveArgs &a, int mode, cudaStream_t s) {
+  cudaEvent_t ev[5];
+  if (m->prof) RM_TRY(take_events(m, ev));
+  RM_CK(rmk::launch_wave(a, mode, s, m->prof ? ev : nullptr));
+  m->launches += rmk::wave_kernel_launches(a, mode);
+  if (m->prof) m->ev_pending.push_back({ev[0], ev[1], ev[2], ev[3], ev[4]});
+  return RM_OK;
+}
+
+// Read back and clear the device status word.
+rm_status read_status(rm_map *m, cudaStream_t s, unsigned *out) {
+  RM_CK(cudaMemcpyAsync(m->h_status, m->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  RM_CK(cudaMemsetAsync(m->d_status, 0, sizeof(unsigned), s));
+  RM_CK(cudaStreamSynchronize(s));
+  *out = *m->h_status;
+  return RM_OK;
+}
+
+rm_status copy_out(void *dst, const void *src, size_t bytes, cudaStream_t s, bool *host_out) {
+  if (!dst || bytes == 0) return RM_OK;
+  bool dev = on_device(dst);
+  if (!dev) *host_out = true;
+  RM_CK(cudaMemcpyAsync(dst, src, bytes, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  return RM_OK;
+}
+
+// Shared driver of rm_render_depth / rm_cost / rm_cost_grad.
+struct EvalReq {
+  const rm_intrinsics *intr;
+  const rm_scan *scan;
+  const double *poses;
+  int n;
+  const rm_cost_params *prm;
+  int mode;
+  const rm_cost_out *out;
+  float *depth;
+  int32_t *tri_id;
+  float *bary;
+};
+
+rm_status run_eval(rm_map *m, const EvalReq &r, cudaStream_t s) {
+  const rm_intrinsics *in = r.intr;
+  RM_TRY(check_intr(in));
+  if (r.n < 0) return fail(RM_EINVAL, "n_poses < 0");
+  if (!r.poses && r.n > 0) return fail(RM_EINVAL, "poses is NULL");
+  if (r.mode == rmk::kRender && !r.depth && r.n > 0) return fail(RM_EINVAL, "depth is NULL");
+  if (r.mode != rmk::kRender) {
+    if (!r.scan || !r.scan->depth || !r.scan->cls) return fail(RM_EINVAL, "scan or its arrays NULL");
+    if (!r.prm) return fail(RM_EINVAL, "params is NULL");
+    if (!(r.prm->eps >= 0.0f)) return fail(RM_EINVAL, "eps must be >= 0");
+  }
+  if (r.n == 0) return RM_OK;
+  RM_CK(cudaSetDevice(m->device));
+  const long long P = (long long)in->width * in->height;
+  const bool host_poses = !on_device(r.poses);
+  const bool host_scan = r.mode != rmk::kRender && !on_device(r.scan->depth);
+  const bool host_cls = r.mode != rmk::kRender && !on_device(r.scan->cls);
+  const bool dev_depth = r.mode == rmk::kRender && on_device(r.depth);
+  const bool dev_id = r.tri_id && on_device(r.tri_id);
+  const bool dev_bary = r.bary && on_device(r.bary);
+
+  for (int attempt = 0;; ++attempt) {
+    TileGeom tg = make_tiles(m, in);
+    const int nw = wave_size(m, r.n, tg);
+    // ---- plan the arena
+    Carver plan{nullptr};
+    plan.take<double>(16 * (size_t)r.n);
+    plan.take<float>(12 * (size_t)r.n);
+    if (host_scan) plan.take<float>(P);
+    if (host_cls) plan.take<uint8_t>(P);
+    plan.take<long long>(6 * (size_t)r.n);
+    plan.take<long long>(r.n);
+    plan.take<double>(r.n);
+    plan.take<double>(6 * (size_t)r.n);
+    plan.take<double>(21 * (size_t)r.n);
+    if (r.mode == rmk::kRender) {
+      if (!dev_depth) plan.take<float>(P * r.n);
+      if (r.tri_id && !dev_id) plan.take<int>(P * r.n);
+      if (r.bary && !dev_bary) plan.take<float>(2 * P * r.n);
+    }
+    plan.take<float4>((size_t)m->V * nw);
+    plan.take<int2>((size_t)m->V * nw);
+    plan.take<int>((size_t)tg.ntiles * nw);
+    plan.take<TriRec>((size_t)tg.ntiles * tg.cap * nw);
+    plan.take<double>((size_t)tg.ntiles * rmk::kNumVals * nw);
+    RM_TRY(ensure_arena(m, plan.off, s));
+    // ---- carve it
+    Carver cv{m->arena};
+    double *d_poses = cv.take<double>(16 * (size_t)r.n);
+    float *d_M = cv.take<float>(12 * (size_t)r.n);
+    const float *d_sd = nullptr;
+    const uint8_t *d_sc = nullptr;
+    if (r.mode != rmk::kRender) {
+      d_sd = host_scan ? cv.take<float>(P) : r.scan->depth;
+      d_sc = host_cls ? cv.take<uint8_t>(P) : r.scan->cls;
+    }
+    long long *d_counts = cv.take<long long>(6 * (size_t)r.n);
+    long long *d_etable = cv.take<long long>(r.n);
+    double *d_els = cv.take<double>(r.n);
+    double *d_grad = cv.take<double>(6 * (size_t)r.n);
+    double *d_jtj = cv.take<double>(21 * (size_t)r.n);
+    float *d_depth = nullptr;
+    int *d_id = nullptr;
+    float *d_bary = nullptr;
+    if (r.mode == rmk::kRender) {
+      d_depth = dev_depth ? r.depth : cv.take<float>(P * r.n);
+      if (r.tri_id) d_id = dev_id ? r.tri_id : cv.take<int>(P * r.n);
+      if (r.bary) d_bary = dev_bary ? r.bary : cv.take<float>(2 * P * r.n);
+    }
+    float4 *d_vc = cv.take<float4>((size_t)m->V * nw);
+    int2 *d_vs = cv.take<int2>((size_t)m->V * nw);
+    int *d_bcount = cv.take<int>((size_t)tg.ntiles * nw);
+    TriRec *d_bins = cv.take<TriRec>((size_t)tg.ntiles * tg.cap * nw);
+    double *d_partial = cv.take<double>((size_t)tg.ntiles * rmk::kNumVals * nw);
+    // ---- inputs
+    RM_CK(cudaMemcpyAsync(d_poses, r.poses, sizeof(double) * 16 * r.n,
+                          host_poses ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+    if (host_scan) RM_CK(cudaMemcpyAsync((void *)d_sd, r.scan->depth, sizeof(float) * P, cudaMemcpyHostToDevice, s));
+    if (host_cls) RM_CK(cudaMemcpyAsync((void *)d_sc, r.scan->cls, P, cudaMemcpyHostToDevice, s));
+    RM_CK(rmk::launch_pose_to_m(d_poses, r.n, m->centre[0], m->centre[1], m->centre[2], d_M, s));
+    m->launches += 1;
+    // ---- waves
+    WaveArgs a{};
+    a.cam = make_cam(in, nullptr);
+    a.tg = tg;
+    a.V = (int)m->V;
+    a.T = m->T;
+    a.v = m->d_v;
+    a.faces = m->d_faces;
+    a.planes = m->d_planes;
+    a.Ms = d_M;
+    a.vc = d_vc;
+    a.vs = d_vs;
+    a.counts = d_bcount;
+    a.bins = d_bins;
+    a.partial = d_partial;
+    a.status = m->d_status;
+    a.skip = nullptr;
+    a.scan_depth = d_sd;
+    a.scan_cls = d_sc;
+    if (r.prm) a.prm = {r.prm->eps, r.prm->w_fofo, r.prm->w_fofu, r.prm->w_fufo};
+    a.res_counts = d_counts;
+    a.res_etable = d_etable;
+    a.res_els = d_els;
+    a.res_grad = d_grad;
+    a.res_jtj = d_jtj;
+    a.depth = d_depth;
+    a.tri_id = d_id;
+    a.bary = d_bary;
+    for (int w0 = 0; w0 < r.n; w0 += nw) {
+      a.wave_base = w0;
+      a.n_poses = std::min(nw, r.n - w0);
+      RM_TRY(wave(m, a, r.mode, s));
+    }
+    // ---- outputs
+    bool host_out = false;
+    if (r.mode == rmk::kRender) {
+      if (!dev_depth) RM_TRY(copy_out(r.depth, d_depth, sizeof(float) * P * r.n, s, &host_out));
+      if (r.tri_id && !dev_id) RM_TRY(copy_out(r.tri_id, d_id, sizeof(int) * P * r.n, s, &host_out));
+      if (r.bary && !dev_bary) RM_TRY(copy_out(r.bary, d_bary, sizeof(float) * 2 * P * r.n, s, &host_out));
+    } else if (r.out) {
+      RM_TRY(copy_out(r.out->counts, d_counts, sizeof(long long) * 6 * r.n, s, &host_out));
+      RM_TRY(copy_out(r.out->e_table, d_etable, sizeof(long long) * r.n, s, &host_out));
+      RM_TRY(copy_out(r.out->e_ls, d_els, sizeof(double) * r.n, s, &host_out));
+      if (r.mode == rmk::kCostGrad) {
+        RM_TRY(copy_out(r.out->grad, d_grad, sizeof(double) * 6 * r.n, s, &host_out));
+        RM_TRY(copy_out(r.out->jtj, d_jtj, sizeof(double) * 21 * r.n, s, &host_out));
+      }
+    }
+    if (m->tuning.async_status) {
+      if (host_out) RM_CK(cudaStreamSynchronize(s));
+      return RM_OK;
+    }
+    unsigned st = 0;
+    RM_TRY(read_status(m, s, &st));
+    if (st & rmk::kStatusTimeout) return fail(RM_ETIMEOUT, "a device-side wait ran out of time");
+    if (st & rmk::kStatusOverflow) {
+      if (m->cap >= (1 << 22) || attempt > 12)
+        return fail(RM_EOVERFLOW, "screen-tile bin overflow at the largest capacity");
+      m->cap *= 2;
+      continue;
+    }
+    return RM_OK;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *rm_last_error(void) { return g_err.c_str(); }
+
+rm_status rm_map_create(const float *vertices, int64_t n_vertices, const int32_t *faces,
+                        const uint8_t *labels, int64_t n_faces, rm_map **out) {
+  if (!out) return fail(RM_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n_vertices < 0 || n_faces < 0) return fail(RM_EINVAL, "negative size");
+  if (n_vertices >= (1ll << 31) || n_faces >= (1ll << 31)) return fail(RM_EINVAL, "too many vertices or faces (>= 2^31)");
+  if ((n_vertices > 0 && !vertices) || (n_faces > 0 && (!faces || !labels)))
+    return fail(RM_EINVAL, "null array");
+  if (on_device(vertices) || on_device(faces) || on_device(labels))
+    return fail(RM_EINVAL, "rm_map_create takes host arrays");
+  for (int64_t k = 0; k < 3 * n_vertices; ++k)
+    if (!std::isfinite(vertices[k])) return fail(RM_EINVAL, "non-finite vertex coordinate");
+  for (int64_t k = 0; k < 3 * n_faces; ++k)
+    if (faces[k] < 0 || faces[k] >= n_vertices) return fail(RM_EINVAL, "face index out of range");
+  for (int64_t k = 0; k < n_faces; ++k)
+    if (labels[k] > 2) return fail(RM_EINVAL, "label above 2");
+
+  rm_map *m = new rm_map();
+  cudaGetDevice(&m->device);
+  m->V = n_vertices;
+  m->T = n_faces;
+  // re-centre on the FP64 bounding-box centre
+  for (int a = 0; a < 3; ++a) {
+    double lo = INFINITY, hi = -INFINITY;
+    for (int64_t k = 0; k < n_vertices; ++k) {
+      double x = vertices[3 * k + a];
+      lo = std::min(lo, x);
+      hi = std::max(hi, x);
+    }
+    m->centre[a] = n_vertices > 0 ? 0.5 * (lo + hi) : 0.0;
+  }
+  std::vector<float4> hv(std::max<int64_t>(n_vertices, 1));
+  for (int64_t k = 0; k < n_vertices; ++k)
+    hv[k] = make_float4((float)((double)vertices[3 * k] - m->centre[0]),
+                        (float)((double)vertices[3 * k + 1] - m->centre[1]),
+                        (float)((double)vertices[3 * k + 2] - m->centre[2]), 0.0f);
+  std::vector<int4> hf(std::max<int64_t>(n_faces, 1));
+  std::vector<float4> hp(std::max<int64_t>(n_faces, 1));
+  for (int64_t k = 0; k < n_faces; ++k) {
+    int i0 = faces[3 * k], i1 = faces[3 * k + 1], i2 = faces[3 * k + 2];
+    hf[k] = make_int4(i0, i1, i2, labels[k]);
+    const float4 &a = hv[i0], &b = hv[i1], &c = hv[i2];
+    double e1[3] = {(double)b.x - a.x, (double)b.y - a.y, (double)b.z - a.z};
+    double e2[3] = {(double)c.x - a.x, (double)c.y - a.y, (double)c.z - a.z};
+    double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+    double nn = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    if (nn > 0) for (double &x : n) x /= nn;
+    float lab;
+    int li = labels[k];
+    std::memcpy(&lab, &li, 4);
+    hp[k] = make_float4((float)n[0], (float)n[1], (float)n[2], lab);
+  }
+  auto cleanup = [&](rm_status s) {
+    rm_map_destroy(m);
+    return s;
+  };
+  cudaError_t e;
+  if ((e = cudaMalloc(&m->d_v, sizeof(float4) * hv.size())) != cudaSuccess ||
+      (e = cudaMalloc(&m->d_faces, sizeof(int4) * hf.size())) != cudaSuccess ||
+      (e = cudaMalloc(&m->d_planes, sizeof(float4) * hp.size())) != cudaSuccess ||
+      (e = cudaMalloc(&m->d_status, sizeof(unsigned))) != cudaSuccess ||
+      (e = cudaMallocHost(&m->h_status, sizeof(unsigned))) != cudaSuccess ||
+      (e = cudaMemcpy(m->d_v, hv.data(), sizeof(float4) * hv.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(m->d_faces, hf.data(), sizeof(int4) * hf.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(m->d_planes, hp.data(), sizeof(float4) * hp.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemset(m->d_status, 0, sizeof(unsigned))) != cudaSuccess)
+    return cleanup(fail(e == cudaErrorMemoryAllocation ? RM_ENOMEM : RM_ECUDA,
+                        std::string("map upload: ") + cudaGetErrorString(e)));
+  *out = m;
+  return RM_OK;
+}
+
+void rm_map_destroy(rm_map *m) {
+  if (!m) return;
+  cudaSetDevice(m->device);
+  cudaDeviceSynchronize();
+  cudaFree(m->d_v);
+  cudaFree(m->d_faces);
+  cudaFree(m->d_planes);
+  cudaFree(m->arena);
+  cudaFree(m->d_status);
+  if (m->h_status) cudaFreeHost(m->h_status);
+  for (auto &ev : m->ev_pending)
+    for (auto e : ev) cudaEventDestroy(e);
+  for (auto e : m->ev_free) cudaEventDestroy(e);
+  delete m;
+}
+
+rm_status rm_map_info(const rm_map *m, int64_t *nv, int64_t *nf, double centre[3]) {
+  if (!m) return fail(RM_EINVAL, "map is NULL");
+  if (nv) *nv = m->V;
+  if (nf) *nf = m->T;
+  if (centre) for (int a = 0; a < 3; ++a) centre[a] = m->centre[a];
+  return RM_OK;
+}
+
+rm_status rm_map_set_tuning(rm_map *m, const rm_tuning *t) {
+  if (!m) return fail(RM_EINVAL, "map is NULL");
+  std::lock_guard<std::mutex> lk(m->mu);
+  rm_tuning z{};
+  const rm_tuning &u = t ? *t : z;
+  bool ok_tile = (u.tile_w == 0 && u.tile_h == 0) || (u.tile_w == 32 && u.tile_h == 32) ||
+                 (u.tile_w == 32 && u.tile_h == 16) || (u.tile_w == 16 && u.tile_h == 16);
+  if (!ok_tile) return fail(RM_EINVAL, "tile must be 16x16, 32x16 or 32x32");
+  if (u.bin_capacity < 0 || u.wave_poses < 0) return fail(RM_EINVAL, "negative tuning value");
+  m->tuning = u;
+  if (u.bin_capacity > 0) m->cap = u.bin_capacity;
+  return RM_OK;
+}
+
+rm_status rm_map_get_tuning(const rm_map *m, rm_tuning *t) {
+  if (!m || !t) return fail(RM_EINVAL, "NULL argument");
+  *t = m->tuning;
+  t->bin_capacity = m->cap;
+  if (t->tile_w == 0) {
+    t->tile_w = 32;
+    t->tile_h = 32;
+  }
+  return RM_OK;
+}
+
+rm_status rm_render_depth(rm_map *m, const double *poses, int32_t n, const rm_intrinsics *intr,
+                          float *depth, int32_t *tri_id, float *bary, void *stream) {
+  if (!m) return fail(RM_EINVAL, "map is NULL");
+  std::lock_guard<std::mutex> lk(m->mu);
+  EvalReq r{intr, nullptr, poses, n, nullptr, rmk::kRender, nullptr, depth, tri_id, bary};
+  return run_eval(m, r, (cudaStream_t)stream);
+}
+
+rm_status rm_cost(rm_map *m, const rm_scan *scan, const double *poses, int32_t n,
+                  const rm_cost_params *prm, const rm_cost_out *out, void *stream) {
+  if (!m) return fail(RM_EINVAL, "map is NULL");
+  if (!scan) return fail(RM_EINVAL, "scan is NULL");
+  std::lock_guard<std::mutex> lk(m->mu);
+  EvalReq r{&scan->intr, scan, poses, n, prm, rmk::kCost, out, nullptr, nullptr, nullptr};
+  return run_eval(m, r, (cudaStream_t)stream);
+}
+
+rm_status rm_cost_grad(rm_map *m, const rm_scan *scan, const double *poses, int32_t n,
+                       const rm_cost_params *prm, const rm_cost_out *out, void *stream) {
+  if (!m) return fail(RM_EINVAL, "map is NULL");
+  if (!scan) return fail(RM_EINVAL, "scan is NULL");
+  std::lock_guard<std::mutex> lk(m->mu);
+  EvalReq r{&scan->intr, scan, poses, n, prm, rmk::kCostGrad, out, nullptr, nullptr, nullptr};
+  return run_eval(m, r, (cudaStream_t)stream);
+}
+
+rm_status rm_pose_retract(const double *poses, const double *twists, int32_t n, double *out,
+                          double *jr, void *stream) {
+  if (n < 0) return fail(RM_EINVAL, "n < 0");
+  if (n == 0) return RM_OK;
+  if (!poses || !twists || !out) return fail(RM_EINVAL, "NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool dp = on_device(poses), dt = on_device(twists), dout = on_device(out);
+  const bool djr = jr && on_device(jr);
+  if (dp && dt && dout && (!jr || djr)) {
+    RM_CK(rmk::launch_retract(poses, twists, n, out, jr, s));
+    return RM_OK;
+  }
+  double *buf = nullptr;
+  size_t per = 16 + 6 + 16 + 36;
+  RM_CK(cudaMallocAsync((void **)&buf, sizeof(double) * per * n, s));
+  double *bp = buf, *bt = buf + 16 * (size_t)n, *bo = bt + 6 * (size_t)n, *bj = bo + 16 * (size_t)n;
+  rm_status st = RM_OK;
+  auto run = [&]() -> rm_status {
+    RM_CK(cudaMemcpyAsync(bp, poses, sizeof(double) * 16 * n, dp ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    RM_CK(cudaMemcpyAsync(bt, twists, sizeof(double) * 6 * n, dt ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    RM_CK(rmk::launch_retract(bp, bt, n, bo, jr ? bj : nullptr, s));
+    RM_CK(cudaMemcpyAsync(out, bo, sizeof(double) * 16 * n, dout ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    if (jr) RM_CK(cudaMemcpyAsync(jr, bj, sizeof(double) * 36 * n, djr ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    RM_CK(cudaStreamSynchronize(s));
+    return RM_OK;
+  };
+  st = run();
+  cudaFreeAsync(buf, s);
+  return st;
+}
+
+rm_status rm_profile(rm_map *m, int32_t enable) {
+  if (!m) return fail(RM_EINVAL, "map is NULL");
+  std::lock_guard<std::mutex> lk(m->mu);
+  RM_TRY(drain_events(m));
+  if (enable) {
+    for (int k = 0; k < 4; ++k) {
+      m->prof_ms[k] = 0.0;
+      m->prof_n[k] = 0;
+    }
+    m->launches = 0;
+  }
+  m->prof = enable != 0;
+  return RM_OK;
+}
+
+rm_status rm_profile_read(rm_map *m, rm_kernel_time *out, int32_t cap, int32_t *n,
+                          int64_t *launches) {
+  if (!m || (cap > 0 && !out)) return fail(RM_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> lk(m->mu);
+  RM_TRY(drain_events(m));
+  static const char *names[4] = {"k_vertex_pinhole", "k_setup_pinhole", "k_raster", "k_reduce"};
+  int k = 0;
+  for (int q = 0; q < 4 && k < cap; ++q) {
+    if (m->prof_n[q] == 0) continue;
+    std::memset(out[k].name, 0, sizeof(out[k].name));
+    std::strncpy(out[k].name, names[q], sizeof(out[k].name) - 1);
+    out[k].launches = m->prof_n[q];
+    out[k].total_ms = m->prof_ms[q];
+    ++k;
+  }
+  if (n) *n = k;
+  if (launches) *launches = m->launches;
+  return RM_OK;
+}
+
+rm_status rm_status_sync(rm_map *m, void *stream) {
+  if (!m) return fail(RM_EINVAL, "map is NULL");
+  std::lock_guard<std::mutex> lk(m->mu);
+  unsigned st = 0;
+  RM_TRY(read_status(m, (cudaStream_t)stream, &st));
+  if (st & rmk::kStatusTimeout) return fail(RM_ETIMEOUT, "a device-side wait ran out of time");
+  if (st & rmk::kStatusOverflow) return fail(RM_EOVERFLOW, "screen-tile bin overflow");
+  return RM_OK;
+}
+
+rm_status rm_align(rm_map *m, const rm_scan *scan, const double *init_pose,
+                   const rm_cost_params *prm, const rm_align_params *lm, double *pose_out,
+                   rm_align_report *rep, void *stream) {
+  if (!m) return fail(RM_EINVAL, "map is NULL");
+  if (!scan || !scan->depth || !scan->cls) return fail(RM_EINVAL, "scan or its arrays NULL");
+  if (!init_pose || !pose_out || !prm || !lm) return fail(RM_EINVAL, "NULL argument");
+  if (lm->max_iters < 0 || lm->max_iters > 100000) return fail(RM_EINVAL, "max_iters out of range");
+  std::lock_guard<std::mutex> lk(m->mu);
+  cudaStream_t s = (cudaStream_t)stream;
+  const rm_intrinsics *in = &scan->intr;
+  RM_TRY(check_intr(in));
+  RM_CK(cudaSetDevice(m->device));
+  const long long P = (long long)in->width * in->height;
+  const bool host_scan = !on_device(scan->depth), host_cls = !on_device(scan->cls);
+  for (int attempt = 0;; ++attempt) {
+    TileGeom tg = make_tiles(m, in);
+    Carver plan{nullptr};
+    plan.take<rmk::LMState>(1);
+    plan.take<double>(16);
+    plan.take<float>(12);
+    plan.take<int>(1);
+    if (host_scan) plan.take<float>(P);
+    if (host_cls) plan.take<uint8_t>(P);
+    plan.take<long long>(6);
+    plan.take<long long>(1);
+    plan.take<double>(1);
+    plan.take<double>(6);
+    plan.take<double>(21);
+    plan.take<float4>(m->V);
+    plan.take<int2>(m->V);
+    plan.take<int>(tg.ntiles);
+    plan.take<TriRec>((size_t)tg.ntiles * tg.cap);
+    plan.take<double>((size_t)tg.ntiles * rmk::kNumVals);
+    RM_TRY(ensure_arena(m, plan.off, s));
+    Carver cv{m->arena};
+    rmk::LMState *d_st = cv.take<rmk::LMState>(1);
+    double *d_T0 = cv.take<double>(16);
+    float *d_M = cv.take<float>(12);
+    int *d_skip = cv.take<int>(1);
+    const float *d_sd = host_scan ? cv.take<float>(P) : scan->depth;
+    const uint8_t *d_sc = host_cls ? cv.take<uint8_t>(P) : scan->cls;
+    long long *d_counts = cv.take<long long>(6);
+    long long *d_etable = cv.take<long long>(1);
+    double *d_els = cv.take<double>(1);
+    double *d_grad = cv.take<double>(6);
+    double *d_jtj = cv.take<double>(21);
+    WaveArgs a{};
+    a.cam = make_cam(in, nullptr);
+    a.tg = tg;
+    a.V = (int)m->V;
+    a.T = m->T;
+    a.n_poses = 1;
+    a.wave_base = 0;
+    a.v = m->d_v;
+    a.faces = m->d_faces;
+    a.planes = m->d_planes;
+    a.Ms = d_M;
+    a.vc = cv.take<float4>(m->V);
+    a.vs = cv.take<int2>(m->V);
+    a.counts = cv.take<int>(tg.ntiles);
+    a.bins = cv.take<TriRec>((size_t)tg.ntiles * tg.cap);
+    a.partial = cv.take<double>((size_t)tg.ntiles * rmk::kNumVals);
+    a.status = m->d_status;
+    a.skip = d_skip;
+    a.scan_depth = d_sd;
+    a.scan_cls = d_sc;
+    a.prm = {prm->eps, prm->w_fofo, prm->w_fofu, prm->w_fufo};
+    a.res_counts = d_counts;
+    a.res_etable = d_etable;
+    a.res_els = d_els;
+    a.res_grad = d_grad;
+    a.res_jtj = d_jtj;
+    RM_CK(cudaMemcpyAsync(d_T0, init_pose, sizeof(double) * 16,
+                          on_device(init_pose) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    if (host_scan) RM_CK(cudaMemcpyAsync((void *)d_sd, scan->depth, sizeof(float) * P, cudaMemcpyHostToDevice, s));
+    if (host_cls) RM_CK(cudaMemcpyAsync((void *)d_sc, scan->cls, P, cudaMemcpyHostToDevice, s));
+    rmk::LMArgs la{lm->lambda0, lm->lambda_up, lm->lambda_down, lm->step_tol,
+                   m->centre[0], m->centre[1], m->centre[2]};
+    RM_CK(rmk::launch_lm_init(d_st, d_T0, la, d_M, d_skip, s));
+    RM_TRY(wave(m, a, rmk::kCostGrad, s));
+    RM_CK(rmk::launch_lm_take_initial(d_st, d_counts, d_els, d_grad, d_jtj, s));
+    for (int it = 0; it < lm->max_iters; ++it) {
+      RM_CK(rmk::launch_lm_propose(d_st, la, d_M, d_skip, s));
+      RM_TRY(wave(m, a, rmk::kCostGrad, s));
+      RM_CK(rmk::launch_lm_accept(d_st, la, d_counts, d_els, d_grad, d_jtj, d_skip, s));
+    }
+    rmk::LMState hs;
+    RM_CK(cudaMemcpyAsync(&hs, d_st, sizeof(hs), cudaMemcpyDeviceToHost, s));
+    unsigned st = 0;
+    RM_TRY(read_status(m, s, &st));  // synchronises the stream
+    if (st & rmk::kStatusTimeout) return fail(RM_ETIMEOUT, "a device-side wait ran out of time");
+    if (st & rmk::kStatusOverflow) {
+      if (m->cap >= (1 << 22) || attempt > 12)
+        return fail(RM_EOVERFLOW, "screen-tile bin overflow at the largest capacity");
+      m->cap *= 2;
+      continue;
+    }
+    if (on_device(pose_out)) RM_CK(cudaMemcpy(pose_out, hs.T, sizeof(double) * 16, cudaMemcpyHostToDevice));
+    else std::memcpy(pose_out, hs.T, sizeof(double) * 16);
+    if (rep) {
+      rep->iters = hs.iters;
+      rep->accepted = hs.accepted;
+      rep->converged = hs.converged;
+      rep->reserved = 0;
+      rep->e_ls_initial = hs.e_ls0;
+      rep->e_ls_final = hs.e;
+      rep->e_table_initial = hs.e_table0;
+      rep->e_table_final = hs.e_table;
+    }
+    return hs.converged ? RM_OK : fail(RM_ENOTCONV, "max_iters reached before step_tol");
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,116 @@
+// rm_internal.cuh -- device-side data layout and the FP32 rasterisation contract.
+//
+// The z-buffer of Sec. III (R(Y) in Eq. 1) must pick, for every pixel, exactly the triangle
+// the CPU reference picks. Every step that feeds coverage or the depth key therefore uses
+// IEEE round-to-nearest intrinsics in a fixed order (no contraction left to the compiler):
+//   vertex:   X = fma(M00, x, fma(M01, y, fma(M02, z, M03)))        (rows 1, 2 alike)
+//   project:  xs = fma(fx, X / Z, cx); xi = rint(xs * 256)           (8 sub-pixel bits)
+//   near cut: s = (near - a.z) / (b.z - a.z), a = lower vertex index; P = a + s (b - a)
+//   plane:    n = (v1 - v0) x (v2 - v0), d = n . v0 (camera frame, stored vertex order)
+//   depth:    pinhole  t = d / fma(A, i + .5, fma(B, j + .5, C)), A = nx/fx, B = ny/fy,
+//                      C = fma(-A, cx, fma(-B, cy, nz));  ray table t = d / (n . r)
+//   key:      (bits(t) << 32) | triangle id, kept iff near <= t <= far, minimum wins.
+// Coverage is decided on the snapped integer coordinates with int64 edge functions and
+// the top-left rule, so it is exact.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rmk {
+
+constexpr float kGuardPx = 2097152.0f;           // 2^21 px: snapped |x| < 2^29
+constexpr unsigned long long kKeyEmpty = ~0ull;
+constexpr int kSentinel = (int)0x80000000;       // vs.x of a vertex that cannot be snapped
+constexpr int kNumVals = 34;                      // counts 6 | e_ls | grad 6 | jtj 21
+constexpr unsigned kStatusOverflow = 1u;
+constexpr unsigned kStatusTimeout = 2u;
+constexpr int kThreads = 256;                     // raster CTA
+constexpr int kChunk = 256;                       // triangle records staged per TMA copy
+constexpr int kLargePixels = 48;                  // bbox-in-tile pixels above which a
+                                                  // triangle is rasterised by the whole CTA
+
+struct DevCam {
+  int model, W, H, pad;
+  float fx, fy, cx, cy;
+  float az0, az_step, el0, el_step;
+  float near_m, far_m;
+  const float *rays;  // ray-table model: device H*W*3
+};
+
+struct TileGeom {
+  int tw, th;          // tile size in pixels
+  int ntx, nty;        // tiles per row / column
+  int ntiles;
+  int cap;             // records per bin
+};
+
+// One snapped triangle (or near-clipped piece) in a screen-tile bin, 48 bytes.
+struct __align__(16) TriRec {
+  int x0, y0, x1, y1, x2, y2;  // 1/256 px, winding normalised so the doubled area is > 0
+  float A, B, C, d;            // depth plane, see the contract above
+  unsigned id;                 // parent triangle id
+  int pad;
+};
+static_assert(sizeof(TriRec) == 48, "record layout");
+
+// ---------------------------------------------------------------- contract helpers
+
+__device__ __forceinline__ float3 xform(const float *M, float x, float y, float z) {
+  float X = __fmaf_rn(M[0], x, __fmaf_rn(M[1], y, __fmaf_rn(M[2], z, M[3])));
+  float Y = __fmaf_rn(M[4], x, __fmaf_rn(M[5], y, __fmaf_rn(M[6], z, M[7])));
+  float Z = __fmaf_rn(M[8], x, __fmaf_rn(M[9], y, __fmaf_rn(M[10], z, M[11])));
+  return make_float3(X, Y, Z);
+}
+
+__device__ __forceinline__ bool snap(const DevCam &c, float X, float Y, float Z, int &xi,
+                                     int &yi) {
+  float xs = __fmaf_rn(c.fx, __fdiv_rn(X, Z), c.cx);
+  float ys = __fmaf_rn(c.fy, __fdiv_rn(Y, Z), c.cy);
+  if (!(fabsf(xs) <= kGuardPx && fabsf(ys) <= kGuardPx)) return false;
+  xi = __float2int_rn(__fmul_rn(xs, 256.0f));
+  yi = __float2int_rn(__fmul_rn(ys, 256.0f));
+  return true;
+}
+
+struct PlaneN {
+  float nx, ny, nz, d;
+};
+
+__device__ __forceinline__ PlaneN plane_n(float3 a, float3 b, float3 c) {
+  float e1x = __fsub_rn(b.x, a.x), e1y = __fsub_rn(b.y, a.y), e1z = __fsub_rn(b.z, a.z);
+  float e2x = __fsub_rn(c.x, a.x), e2y = __fsub_rn(c.y, a.y), e2z = __fsub_rn(c.z, a.z);
+  PlaneN p;
+  p.nx = __fmaf_rn(e1y, e2z, -__fmul_rn(e1z, e2y));
+  p.ny = __fmaf_rn(e1z, e2x, -__fmul_rn(e1x, e2z));
+  p.nz = __fmaf_rn(e1x, e2y, -__fmul_rn(e1y, e2x));
+  p.d = __fmaf_rn(p.nx, a.x, __fmaf_rn(p.ny, a.y, __fmul_rn(p.nz, a.z)));
+  return p;
+}
+
+// Pinhole depth plane folded into pixel coordinates.
+__device__ __forceinline__ void fold_pinhole(const DevCam &c, const PlaneN &p, float &A,
+                                             float &B, float &C) {
+  A = __fdiv_rn(p.nx, c.fx);
+  B = __fdiv_rn(p.ny, c.fy);
+  C = __fmaf_rn(-A, c.cx, __fmaf_rn(-B, c.cy, p.nz));
+}
+
+__device__ __forceinline__ float depth_pinhole(float A, float B, float C, float d, int i,
+                                               int j) {
+  float px = __fadd_rn(__int2float_rn(i), 0.5f);
+  float py = __fadd_rn(__int2float_rn(j), 0.5f);
+  return __fdiv_rn(d, __fmaf_rn(A, px, __fmaf_rn(B, py, C)));
+}
+
+__device__ __forceinline__ float3 near_cut(float3 a, float3 b, float near_m) {
+  float s = __fdiv_rn(__fsub_rn(near_m, a.z), __fsub_rn(b.z, a.z));
+  return make_float3(__fmaf_rn(s, __fsub_rn(b.x, a.x), a.x), __fmaf_rn(s, __fsub_rn(b.y, a.y), a.y),
+                     near_m);
+}
+
+__device__ __forceinline__ unsigned long long make_key(float t, unsigned id) {
+  return ((unsigned long long)__float_as_uint(t) << 32) | (unsigned long long)id;
+}
+
+}  // namespace rmk

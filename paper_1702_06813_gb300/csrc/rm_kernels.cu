@@ -1,0 +1,826 @@
+// rm_kernels.cu -- the pose-cost hot path on sm_103a.
+//
+// Per pose (one wave of poses at a time, blockIdx.y = pose within the wave):
+//   k_pose_to_m   camera-to-world FP64 pose -> world-to-camera FP32 3x4 (Eq. 1's T(X) -> Y)
+//   k_vertex      camera-space vertices and their 1/256-px snapped projections
+//   k_setup       per triangle: near-plane cut, cull, depth plane, append to screen-tile bins
+//   k_raster      one CTA per (pose, tile): bins staged into shared memory with bulk (TMA)
+//                 copies, integer edge functions with the top-left rule, 64-bit
+//                 depth|id z-test by shared-memory atomicMin (the z-buffer R(Y) of Sec. III);
+//                 then the fused epilogue: Table I per pixel (Sec. III.B), the truncated
+//                 least-squares residual, its pose Jacobian, and a fixed-order reduction
+//   k_reduce      per pose: fixed-order sum of the per-tile partials
+#include <cfloat>
+#include <cmath>
+
+#include "rm_kernels.cuh"
+
+namespace rmk {
+
+// ------------------------------------------------------------------ PTX helpers
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long *b, unsigned n) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(n) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// One-dimensional bulk copy global -> this CTA's shared memory, completion counted in bytes
+// on `bar`. Both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes,
+                                         unsigned long long *bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(unsigned long long *bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on a phase of `bar`: gives up after about 2^31 cycles (~1 s).
+__device__ __noinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
+  long long t0 = clock64();
+  while (!mbar_try(bar, parity)) {
+    if (clock64() - t0 > (1ll << 31)) return false;
+  }
+  return true;
+}
+
+// ------------------------------------------------------------------ pose -> matrix
+
+// M = inverse of (R, t - c) rounded to FP32: rotation R^T, translation -R^T (t - c), the
+// translation summed in FP64 as ((r0 t0 + r1 t1) + r2 t2) without fused multiply-add.
+__device__ __forceinline__ void pose_to_m(const double *T, double cx, double cy, double cz,
+                                          float *M) {
+  double t0 = __dsub_rn(T[3], cx), t1 = __dsub_rn(T[7], cy), t2 = __dsub_rn(T[11], cz);
+  for (int i = 0; i < 3; ++i) {
+    double r0 = T[i], r1 = T[4 + i], r2 = T[8 + i];
+    double s = __dmul_rn(r0, t0);
+    s = __dadd_rn(s, __dmul_rn(r1, t1));
+    s = __dadd_rn(s, __dmul_rn(r2, t2));
+    M[4 * i + 0] = __double2float_rn(r0);
+    M[4 * i + 1] = __double2float_rn(r1);
+    M[4 * i + 2] = __double2float_rn(r2);
+    M[4 * i + 3] = __double2float_rn(-s);
+  }
+}
+
+__global__ void k_pose_to_m(const double *poses, int n, double cx, double cy, double cz,
+                            float *Ms) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) pose_to_m(poses + 16 * (long long)k, cx, cy, cz, Ms + 12 * (long long)k);
+}
+
+cudaError_t launch_pose_to_m(const double *poses, int n, double cx, double cy, double cz,
+                             float *Ms, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_pose_to_m<<<(n + 127) / 128, 128, 0, s>>>(poses, n, cx, cy, cz, Ms);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ vertices
+
+__global__ void __launch_bounds__(256) k_vertex_pinhole(WaveArgs a) {
+  if (a.skip && *a.skip) return;
+  const int q = blockIdx.y;
+  const float *Mg = a.Ms + 12 * (long long)(a.wave_base + q);
+  float M[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) M[k] = Mg[k];
+  float4 *vc = a.vc + (long long)q * a.V;
+  int2 *vs = a.vs + (long long)q * a.V;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < a.V; k += gridDim.x * blockDim.x) {
+    float4 v = a.v[k];
+    float3 c = xform(M, v.x, v.y, v.z);
+    vc[k] = make_float4(c.x, c.y, c.z, 0.0f);
+    int2 s = make_int2(kSentinel, 1);  // behind the near plane
+    if (c.z >= a.cam.near_m) {
+      int xi, yi;
+      s = snap(a.cam, c.x, c.y, c.z, xi, yi) ? make_int2(xi, yi) : make_int2(kSentinel, 2);
+    }
+    vs[k] = s;
+  }
+}
+
+// ------------------------------------------------------------------ triangle setup + binning
+
+__device__ __forceinline__ void emit_piece(int x0, int y0, int x1, int y1, int x2, int y2,
+                                           float A, float B, float C, float d, unsigned id,
+                                           const WaveArgs &a, int *counts, TriRec *bins) {
+  long long area = (long long)(x1 - x0) * (y2 - y0) - (long long)(y1 - y0) * (x2 - x0);
+  if (area == 0) return;
+  if (area < 0) {
+    int t = x1; x1 = x2; x2 = t;
+    t = y1; y1 = y2; y2 = t;
+  }
+  const int W = a.cam.W, H = a.cam.H;
+  int xmin = min(x0, min(x1, x2)), xmax = max(x0, max(x1, x2));
+  int ymin = min(y0, min(y1, y2)), ymax = max(y0, max(y1, y2));
+  int i0 = max((xmin + 127) >> 8, 0), i1 = min((xmax - 128) >> 8, W - 1);
+  int j0 = max((ymin + 127) >> 8, 0), j1 = min((ymax - 128) >> 8, H - 1);
+  if (i0 > i1 || j0 > j1) return;
+  const TileGeom &tg = a.tg;
+  int tx0 = i0 / tg.tw, tx1 = i1 / tg.tw, ty0 = j0 / tg.th, ty1 = j1 / tg.th;
+  int4 w0 = make_int4(x0, y0, x1, y1);
+  int4 w1 = make_int4(x2, y2, __float_as_int(A), __float_as_int(B));
+  int4 w2 = make_int4(__float_as_int(C), __float_as_int(d), (int)id, 0);
+  for (int ty = ty0; ty <= ty1; ++ty)
+    for (int tx = tx0; tx <= tx1; ++tx) {
+      int tile = ty * tg.ntx + tx;
+      int slot = atomicAdd(&counts[tile], 1);
+      if (slot < tg.cap) {
+        int4 *dst = reinterpret_cast<int4 *>(bins + (long long)tile * tg.cap + slot);
+        dst[0] = w0;
+        dst[1] = w1;
+        dst[2] = w2;
+      } else {
+        atomicOr(a.status, kStatusOverflow);
+      }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_setup_pinhole(WaveArgs a) {
+  if (a.skip && *a.skip) return;
+  const int q = blockIdx.y;
+  const float4 *vc = a.vc + (long long)q * a.V;
+  const int2 *vs = a.vs + (long long)q * a.V;
+  int *counts = a.counts + (long long)q * a.tg.ntiles;
+  TriRec *bins = a.bins + (long long)q * a.tg.ntiles * a.tg.cap;
+  const int W = a.cam.W, H = a.cam.H;
+  const float near_m = a.cam.near_m;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < a.T;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int4 f = a.faces[k];
+    const int2 s0 = vs[f.x], s1 = vs[f.y], s2 = vs[f.z];
+    if (s0.x != kSentinel && s1.x != kSentinel && s2.x != kSentinel) {
+      // all three in front of the near plane and inside the guard band
+      int xmin = min(s0.x, min(s1.x, s2.x)), xmax = max(s0.x, max(s1.x, s2.x));
+      int ymin = min(s0.y, min(s1.y, s2.y)), ymax = max(s0.y, max(s1.y, s2.y));
+      if (max((xmin + 127) >> 8, 0) > min((xmax - 128) >> 8, W - 1)) continue;
+      if (max((ymin + 127) >> 8, 0) > min((ymax - 128) >> 8, H - 1)) continue;
+      const float4 p0 = vc[f.x], p1 = vc[f.y], p2 = vc[f.z];
+      PlaneN pl = plane_n(make_float3(p0.x, p0.y, p0.z), make_float3(p1.x, p1.y, p1.z),
+                          make_float3(p2.x, p2.y, p2.z));
+      float A, B, C;
+      fold_pinhole(a.cam, pl, A, B, C);
+      emit_piece(s0.x, s0.y, s1.x, s1.y, s2.x, s2.y, A, B, C, pl.d, (unsigned)k, a, counts, bins);
+      continue;
+    }
+    // slow path: near-plane cut and/or guard band
+    const int idx[3] = {f.x, f.y, f.z};
+    float3 v[3];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      float4 p = vc[idx[m]];
+      v[m] = make_float3(p.x, p.y, p.z);
+    }
+    bool in[3];
+    int nin = 0;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      in[m] = v[m].z >= near_m;
+      nin += in[m];
+    }
+    if (nin == 0 || nin == 3) continue;  // all behind, or a vertex beyond the guard band
+    PlaneN pl = plane_n(v[0], v[1], v[2]);
+    float A, B, C;
+    fold_pinhole(a.cam, pl, A, B, C);
+    float3 poly[4];
+    int n = 0;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      int nx = (m + 1) % 3;
+      if (in[m]) poly[n++] = v[m];
+      if (in[m] != in[nx]) poly[n++] = idx[m] < idx[nx] ? near_cut(v[m], v[nx], near_m)
+                                                        : near_cut(v[nx], v[m], near_m);
+    }
+    int sx[4], sy[4];
+    bool ok = true;
+    for (int m = 0; m < n; ++m) ok = ok && snap(a.cam, poly[m].x, poly[m].y, poly[m].z, sx[m], sy[m]);
+    if (!ok) continue;
+    emit_piece(sx[0], sy[0], sx[1], sy[1], sx[2], sy[2], A, B, C, pl.d, (unsigned)k, a, counts, bins);
+    if (n == 4)
+      emit_piece(sx[0], sy[0], sx[2], sy[2], sx[3], sy[3], A, B, C, pl.d, (unsigned)k, a, counts,
+                 bins);
+  }
+}
+
+// ------------------------------------------------------------------ raster + epilogue
+
+struct EdgeSet {
+  long long dx[3], dy[3];
+  int xa[3], ya[3];
+  int bias[3];
+};
+
+__device__ __forceinline__ void edge_setup(const TriRec &r, EdgeSet &e) {
+  const int x[3] = {r.x0, r.x1, r.x2}, y[3] = {r.y0, r.y1, r.y2};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    int b = k == 2 ? 0 : k + 1;
+    e.dx[k] = (long long)x[b] - x[k];
+    e.dy[k] = (long long)y[b] - y[k];
+    e.xa[k] = x[k];
+    e.ya[k] = y[k];
+    e.bias[k] = (e.dy[k] < 0 || (e.dy[k] == 0 && e.dx[k] > 0)) ? 0 : -1;  // top-left
+  }
+}
+
+__device__ __forceinline__ bool covers(const EdgeSet &e, int i, int j) {
+  const long long px = 256ll * i + 128, py = 256ll * j + 128;
+  bool in = true;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    long long E = e.dx[k] * (py - e.ya[k]) - e.dy[k] * (px - e.xa[k]);
+    in = in && (E + e.bias[k] >= 0);
+  }
+  return in;
+}
+
+__device__ __forceinline__ void tri_rect(const TriRec &r, int ox, int oy, int xe, int ye,
+                                         int &i0, int &i1, int &j0, int &j1) {
+  int xmin = min(r.x0, min(r.x1, r.x2)), xmax = max(r.x0, max(r.x1, r.x2));
+  int ymin = min(r.y0, min(r.y1, r.y2)), ymax = max(r.y0, max(r.y1, r.y2));
+  i0 = max((xmin + 127) >> 8, ox);
+  i1 = min((xmax - 128) >> 8, xe);
+  j0 = max((ymin + 127) >> 8, oy);
+  j1 = min((ymax - 128) >> 8, ye);
+}
+
+template <int TW>
+__device__ __forceinline__ void deposit(unsigned long long *zk, const TriRec &r, int i, int j,
+                                        int ox, int oy, float near_m, float far_m) {
+  float t = depth_pinhole(r.A, r.B, r.C, r.d, i, j);
+  if (t >= near_m && t <= far_m) atomicMin(&zk[(j - oy) * TW + (i - ox)], make_key(t, r.id));
+}
+
+template <int TW, int TH, int MODE>
+__global__ void __launch_bounds__(kThreads) k_raster(WaveArgs a) {
+  constexpr int NP = TW * TH;
+  __shared__ unsigned long long zk[NP];
+  __shared__ __align__(128) TriRec stage[2][kChunk];
+  __shared__ __align__(8) unsigned long long bar[2];
+  __shared__ int lq[kChunk];
+  __shared__ int lq_n;
+  __shared__ int s_abort;
+  __shared__ float red[kThreads / 32][28];
+  __shared__ int redc[kThreads / 32][6];
+
+  if (a.skip && *a.skip) return;
+  const int tid = threadIdx.x;
+  const int tile = blockIdx.x, q = blockIdx.y, g = a.wave_base + q;
+  const int ox = (tile % a.tg.ntx) * TW, oy = (tile / a.tg.ntx) * TH;
+  const int W = a.cam.W, H = a.cam.H;
+  const int xe = min(ox + TW, W) - 1, ye = min(oy + TH, H) - 1;
+  const float near_m = a.cam.near_m, far_m = a.cam.far_m;
+
+  for (int p = tid; p < NP; p += kThreads) zk[p] = kKeyEmpty;
+  const long long bin = (long long)q * a.tg.ntiles + tile;
+  const int n = min(a.counts[bin], a.tg.cap);
+  const TriRec *recs = a.bins + bin * a.tg.cap;
+  const int nchunks = (n + kChunk - 1) / kChunk;
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    lq_n = 0;
+    s_abort = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (tid == 0 && nchunks > 0) bulk_g2s(stage[0], recs, (unsigned)(min(kChunk, n) * sizeof(TriRec)), &bar[0]);
+
+  for (int c = 0; c < nchunks; ++c) {
+    const int buf = c & 1;
+    if (tid == 0 && c + 1 < nchunks) {
+      fence_async_smem();
+      bulk_g2s(stage[buf ^ 1], recs + (long long)(c + 1) * kChunk,
+               (unsigned)(min(kChunk, n - (c + 1) * kChunk) * sizeof(TriRec)), &bar[buf ^ 1]);
+    }
+    if (!mbar_wait(&bar[buf], (c >> 1) & 1)) s_abort = 1;
+    __syncthreads();
+    if (s_abort) {
+      if (tid == 0) {
+        atomicOr(a.status, kStatusTimeout);
+        if (c + 1 < nchunks) mbar_wait(&bar[buf ^ 1], ((c + 1) >> 1) & 1);
+      }
+      return;
+    }
+    const int cnt = min(kChunk, n - c * kChunk);
+    if (tid < cnt) {
+      const TriRec &r = stage[buf][tid];
+      int i0, i1, j0, j1;
+      tri_rect(r, ox, oy, xe, ye, i0, i1, j0, j1);
+      if (i0 <= i1 && j0 <= j1) {
+        if ((i1 - i0 + 1) * (j1 - j0 + 1) > kLargePixels) {
+          lq[atomicAdd(&lq_n, 1)] = tid;
+        } else {
+          EdgeSet e;
+          edge_setup(r, e);
+          for (int j = j0; j <= j1; ++j)
+            for (int i = i0; i <= i1; ++i)
+              if (covers(e, i, j)) deposit<TW>(zk, r, i, j, ox, oy, near_m, far_m);
+        }
+      }
+    }
+    __syncthreads();
+    const int nl = lq_n;
+    for (int k = 0; k < nl; ++k) {
+      const TriRec &r = stage[buf][lq[k]];
+      int i0, i1, j0, j1;
+      tri_rect(r, ox, oy, xe, ye, i0, i1, j0, j1);
+      const int bw = i1 - i0 + 1, npx = bw * (j1 - j0 + 1);
+      EdgeSet e;
+      edge_setup(r, e);
+      for (int p = tid; p < npx; p += kThreads) {
+        int i = i0 + p % bw, j = j0 + p / bw;
+        if (covers(e, i, j)) deposit<TW>(zk, r, i, j, ox, oy, near_m, far_m);
+      }
+    }
+    __syncthreads();
+    if (tid == 0) lq_n = 0;
+  }
+  __syncthreads();
+
+  const long long P = (long long)W * H;
+  if (MODE == kRender) {
+    for (int p = tid; p < NP; p += kThreads) {
+      const int i = ox + p % TW, j = oy + p / TW;
+      if (i > xe || j > ye) continue;
+      const long long pix = (long long)g * P + (long long)j * W + i;
+      const unsigned long long key = zk[p];
+      if (key == kKeyEmpty) {
+        a.depth[pix] = __int_as_float(0x7fc00000);
+        if (a.tri_id) a.tri_id[pix] = -1;
+        if (a.bary) {
+          a.bary[2 * pix] = __int_as_float(0x7fc00000);
+          a.bary[2 * pix + 1] = __int_as_float(0x7fc00000);
+        }
+        continue;
+      }
+      const unsigned id = (unsigned)key;
+      const float t = __uint_as_float((unsigned)(key >> 32));
+      a.depth[pix] = t;
+      if (a.tri_id) a.tri_id[pix] = (int)id;
+      if (a.bary) {
+        const int4 f = a.faces[id];
+        const float4 *vc = a.vc + (long long)q * a.V;
+        const float4 v0 = vc[f.x], v1 = vc[f.y], v2 = vc[f.z];
+        const float rx = (i + 0.5f - a.cam.cx) / a.cam.fx, ry = (j + 0.5f - a.cam.cy) / a.cam.fy;
+        const float hx = t * rx - v0.x, hy = t * ry - v0.y, hz = t - v0.z;
+        const float e1x = v1.x - v0.x, e1y = v1.y - v0.y, e1z = v1.z - v0.z;
+        const float e2x = v2.x - v0.x, e2y = v2.y - v0.y, e2z = v2.z - v0.z;
+        const float nx = e1y * e2z - e1z * e2y, ny = e1z * e2x - e1x * e2z, nz = e1x * e2y - e1y * e2x;
+        const float nn = nx * nx + ny * ny + nz * nz;
+        const float c1x = hy * e2z - hz * e2y, c1y = hz * e2x - hx * e2z, c1z = hx * e2y - hy * e2x;
+        const float c2x = e1y * hz - e1z * hy, c2y = e1z * hx - e1x * hz, c2z = e1x * hy - e1y * hx;
+        a.bary[2 * pix] = (c1x * nx + c1y * ny + c1z * nz) / nn;
+        a.bary[2 * pix + 1] = (c2x * nx + c2y * ny + c2z * nz) / nn;
+      }
+    }
+    return;
+  }
+
+  // ---- fused Table I + least-squares residual (+ adjoint) epilogue
+  int cnt6[6] = {0, 0, 0, 0, 0, 0};
+  float acc[28];
+#pragma unroll
+  for (int k = 0; k < 28; ++k) acc[k] = 0.0f;
+  const float *Mg = a.Ms + 12 * (long long)g;
+  float R[9];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    R[3 * k] = Mg[4 * k];
+    R[3 * k + 1] = Mg[4 * k + 1];
+    R[3 * k + 2] = Mg[4 * k + 2];
+  }
+  const float eps = a.prm.eps;
+  for (int p = tid; p < NP; p += kThreads) {
+    const int i = ox + p % TW, j = oy + p / TW;
+    if (i > xe || j > ye) continue;
+    const unsigned long long key = zk[p];
+    if (key == kKeyEmpty) continue;  // map NaN row: ignore
+    const long long pix = (long long)j * W + i;
+    const float sd = a.scan_depth[pix];
+    const int sc = a.scan_cls[pix];
+    if (sc > 1 || !(fabsf(sd) <= FLT_MAX)) continue;  // scan NaN column: ignore
+    const unsigned id = (unsigned)key;
+    const float t = __uint_as_float((unsigned)(key >> 32));
+    const float4 pl = a.planes[id];
+    const int mc = __float_as_int(pl.w);
+    if (mc > 1) continue;  // unknown-occupied row: ignore
+    const float dz = __fsub_rn(t, sd);
+    int oc;
+    if (mc == 0) oc = sc == 0 ? (fabsf(dz) <= eps ? 0 : 1) : (dz > 0.0f ? 2 : 3);
+    else if (sc == 0) oc = dz <= 0.0f ? 4 : 5;
+    else continue;  // FU / FU: ignore
+    cnt6[oc] += 1;
+    float r, w, sgn = 0.0f;
+    switch (oc) {
+      case 0: w = a.prm.w_fofo; r = dz; sgn = 1.0f; break;
+      case 1: w = a.prm.w_fofo; r = eps; break;
+      case 2: w = a.prm.w_fofu; r = 0.0f; break;
+      case 3:
+        w = a.prm.w_fofu;
+        if (-dz < eps) { r = -dz; sgn = -1.0f; } else { r = eps; }
+        break;
+      case 4: w = a.prm.w_fufo; r = 0.0f; break;
+      default:
+        w = a.prm.w_fufo;
+        if (dz < eps) { r = dz; sgn = 1.0f; } else { r = eps; }
+        break;
+    }
+    acc[0] += 0.5f * w * r * r;
+    if (MODE == kCostGrad && sgn != 0.0f) {
+      const float rx = (i + 0.5f - a.cam.cx) / a.cam.fx, ry = (j + 0.5f - a.cam.cy) / a.cam.fy;
+      const float nx = R[0] * pl.x + R[1] * pl.y + R[2] * pl.z;
+      const float ny = R[3] * pl.x + R[4] * pl.y + R[5] * pl.z;
+      const float nz = R[6] * pl.x + R[7] * pl.y + R[8] * pl.z;
+      const float inv = 1.0f / (nx * rx + ny * ry + nz);
+      const float s = sgn * inv;
+      float J[6];
+      J[0] = -nx * s;
+      J[1] = -ny * s;
+      J[2] = -nz * s;
+      J[3] = -t * (ry * nz - ny) * s;
+      J[4] = -t * (nx - rx * nz) * s;
+      J[5] = -t * (rx * ny - ry * nx) * s;
+      const float wr = w * r;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) acc[1 + k] += wr * J[k];
+      int qk = 7;
+#pragma unroll
+      for (int u = 0; u < 6; ++u)
+#pragma unroll
+        for (int v = u; v < 6; ++v) acc[qk++] += w * J[u] * J[v];
+    }
+  }
+  // fixed-order reduction: warp butterflies (FP32), then FP64 over warps
+#pragma unroll
+  for (int k = 0; k < 28; ++k) {
+    float v = acc[k];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    acc[k] = v;
+  }
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    int v = cnt6[k];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    cnt6[k] = v;
+  }
+  const int warp = tid >> 5, lane = tid & 31;
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < 28; ++k) red[warp][k] = acc[k];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) redc[warp][k] = cnt6[k];
+  }
+  __syncthreads();
+  if (tid < kNumVals) {
+    double s = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) s += tid < 6 ? (double)redc[w][tid] : (double)red[w][tid - 6];
+    a.partial[bin * kNumVals + tid] = s;
+  }
+}
+
+__global__ void k_reduce(WaveArgs a) {
+  if (a.skip && *a.skip) return;
+  __shared__ double vals[kNumVals];
+  const int q = blockIdx.x, g = a.wave_base + q, k = threadIdx.x;
+  if (k < kNumVals) {
+    const double *p = a.partial + (long long)q * a.tg.ntiles * kNumVals + k;
+    double s = 0.0;
+    for (int t = 0; t < a.tg.ntiles; ++t) s += p[(long long)t * kNumVals];
+    vals[k] = s;
+  }
+  __syncthreads();
+  if (k < 6 && a.res_counts) a.res_counts[6 * (long long)g + k] = (long long)vals[k];
+  if (k == 6 && a.res_els) a.res_els[g] = vals[6];
+  if (k >= 7 && k < 13 && a.res_grad) a.res_grad[6 * (long long)g + (k - 7)] = vals[k];
+  if (k >= 13 && k < kNumVals && a.res_jtj) a.res_jtj[21 * (long long)g + (k - 13)] = vals[k];
+  if (k == 0 && a.res_etable)
+    a.res_etable[g] = (long long)(vals[1] + vals[3] + vals[5]) - (long long)(vals[0] + vals[2] + vals[4]);
+}
+
+// ------------------------------------------------------------------ launch
+
+template <int TW, int TH>
+static cudaError_t launch_raster(const WaveArgs &a, int mode, cudaStream_t s) {
+  dim3 grid(a.tg.ntiles, a.n_poses);
+  if (mode == kRender) k_raster<TW, TH, kRender><<<grid, kThreads, 0, s>>>(a);
+  else if (mode == kCost) k_raster<TW, TH, kCost><<<grid, kThreads, 0, s>>>(a);
+  else k_raster<TW, TH, kCostGrad><<<grid, kThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wave(const WaveArgs &a, int mode, cudaStream_t s, cudaEvent_t *ev) {
+  cudaError_t e;
+  e = cudaMemsetAsync(a.counts, 0, sizeof(int) * (size_t)a.tg.ntiles * a.n_poses, s);
+  if (e != cudaSuccess) return e;
+  if (ev && (e = cudaEventRecord(ev[0], s)) != cudaSuccess) return e;
+  if (a.V > 0) {
+    dim3 gv((a.V + 255) / 256, a.n_poses);
+    k_vertex_pinhole<<<gv, 256, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (ev && (e = cudaEventRecord(ev[1], s)) != cudaSuccess) return e;
+  if (a.T > 0) {
+    long long blocks = (a.T + 255) / 256;
+    dim3 gs((unsigned)(blocks < 65535 ? blocks : 65535), a.n_poses);
+    k_setup_pinhole<<<gs, 256, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (ev && (e = cudaEventRecord(ev[2], s)) != cudaSuccess) return e;
+  if (a.tg.tw == 32 && a.tg.th == 32) e = launch_raster<32, 32>(a, mode, s);
+  else if (a.tg.tw == 32 && a.tg.th == 16) e = launch_raster<32, 16>(a, mode, s);
+  else e = launch_raster<16, 16>(a, mode, s);
+  if (e != cudaSuccess) return e;
+  if (ev && (e = cudaEventRecord(ev[3], s)) != cudaSuccess) return e;
+  if (mode != kRender) {
+    k_reduce<<<a.n_poses, 64, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (ev && (e = cudaEventRecord(ev[4], s)) != cudaSuccess) return e;
+  return cudaSuccess;
+}
+
+int wave_kernel_launches(const WaveArgs &a, int mode) {
+  return (a.V > 0) + (a.T > 0) + 1 + (mode != kRender);
+}
+
+// ------------------------------------------------------------------ Levenberg-Marquardt
+
+__device__ void se3_right_dev(const double *T, const double *xi, double *out) {
+  const double *rho = xi, *phi = xi + 3;
+  const double th2 = phi[0] * phi[0] + phi[1] * phi[1] + phi[2] * phi[2], th = sqrt(th2);
+  double A, B, C;
+  if (th < 1e-4) {
+    A = 1.0 - th2 / 6.0 + th2 * th2 / 120.0;
+    B = 0.5 - th2 / 24.0 + th2 * th2 / 720.0;
+    C = 1.0 / 6.0 - th2 / 120.0 + th2 * th2 / 5040.0;
+  } else {
+    double sn, cs;
+    sincos(th, &sn, &cs);
+    A = sn / th;
+    B = (1.0 - cs) / th2;
+    C = (th - sn) / (th2 * th);
+  }
+  const double K[9] = {0, -phi[2], phi[1], phi[2], 0, -phi[0], -phi[1], phi[0], 0};
+  double K2[9];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double s = 0;
+      for (int k = 0; k < 3; ++k) s += K[3 * i + k] * K[3 * k + j];
+      K2[3 * i + j] = s;
+    }
+  double E[16];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      const double I = i == j ? 1.0 : 0.0;
+      E[4 * i + j] = I + A * K[3 * i + j] + B * K2[3 * i + j];
+    }
+  for (int i = 0; i < 3; ++i) {
+    double t = 0;
+    for (int j = 0; j < 3; ++j) {
+      const double I = i == j ? 1.0 : 0.0;
+      t += (I + B * K[3 * i + j] + C * K2[3 * i + j]) * rho[j];
+    }
+    E[4 * i + 3] = t;
+  }
+  E[12] = E[13] = E[14] = 0.0;
+  E[15] = 1.0;
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      double s = 0;
+      for (int k = 0; k < 4; ++k) s += T[4 * i + k] * E[4 * k + j];
+      out[4 * i + j] = s;
+    }
+}
+
+// hat(v) into a row-major 3x3
+__device__ __forceinline__ void hat3(const double *v, double *K) {
+  K[0] = 0; K[1] = -v[2]; K[2] = v[1];
+  K[3] = v[2]; K[4] = 0; K[5] = -v[0];
+  K[6] = -v[1]; K[7] = v[0]; K[8] = 0;
+}
+
+__device__ __forceinline__ void mm3(const double *A, const double *B, double *C) {
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double s = 0;
+      for (int k = 0; k < 3; ++k) s += A[3 * i + k] * B[3 * k + j];
+      C[3 * i + j] = s;
+    }
+}
+
+// SE(3) left Jacobian for xi = (rho, phi) (translation first), 6x6 row major:
+// [[J(phi), Q(rho, phi)], [0, J(phi)]] with
+// J = I + (1 - cos t)/t^2 P + (t - sin t)/t^3 P^2 and
+// Q = 1/2 R + (t - sin t)/t^3 (PR + RP + PRP)
+//     + (t^2 + 2 cos t - 2)/(2 t^4) (PPR + RPP - 3 PRP)
+//     + (2t - 3 sin t + t cos t)/(2 t^5) (PRPP + PPRP),   P = phi^, R = rho^.
+__device__ void se3_left_jacobian(const double *xi, double *J6) {
+  const double *rho = xi, *phi = xi + 3;
+  const double t2 = phi[0] * phi[0] + phi[1] * phi[1] + phi[2] * phi[2], t = sqrt(t2);
+  double a, b, c, d;
+  if (t < 1e-3) {
+    a = 0.5 - t2 / 24.0 + t2 * t2 / 720.0;
+    b = 1.0 / 6.0 - t2 / 120.0 + t2 * t2 / 5040.0;
+    c = 1.0 / 24.0 - t2 / 720.0 + t2 * t2 / 40320.0;
+    d = 1.0 / 120.0 - t2 / 2520.0;
+  } else {
+    double sn, cs;
+    sincos(t, &sn, &cs);
+    a = (1.0 - cs) / t2;
+    b = (t - sn) / (t2 * t);
+    c = (t2 + 2.0 * cs - 2.0) / (2.0 * t2 * t2);
+    d = (2.0 * t - 3.0 * sn + t * cs) / (2.0 * t2 * t2 * t);
+  }
+  double P[9], R[9], PP[9], PR[9], RP[9], PRP[9], PPR[9], RPP[9], PRPP[9], PPRP[9];
+  hat3(phi, P);
+  hat3(rho, R);
+  mm3(P, P, PP);
+  mm3(P, R, PR);
+  mm3(R, P, RP);
+  mm3(PR, P, PRP);
+  mm3(PP, R, PPR);
+  mm3(R, PP, RPP);
+  mm3(PRP, P, PRPP);
+  mm3(PP, RP, PPRP);
+  for (int i = 0; i < 36; ++i) J6[i] = 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      const int k = 3 * i + j;
+      const double I = i == j ? 1.0 : 0.0;
+      const double Jr = I + a * P[k] + b * PP[k];
+      const double Q = 0.5 * R[k] + b * (PR[k] + RP[k] + PRP[k]) +
+                       c * (PPR[k] + RPP[k] - 3.0 * PRP[k]) + d * (PRPP[k] + PPRP[k]);
+      J6[6 * i + j] = Jr;
+      J6[6 * (i + 3) + (j + 3)] = Jr;
+      J6[6 * i + (j + 3)] = Q;
+    }
+}
+
+// out_k = T_k exp(xi_k^); jr_k (optional) = right Jacobian J_r(xi) = J_l(-xi).
+__global__ void k_retract(const double *T, const double *xi, int n, double *out, double *jr) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  se3_right_dev(T + 16 * (long long)k, xi + 6 * (long long)k, out + 16 * (long long)k);
+  if (jr) {
+    double m[6];
+    for (int u = 0; u < 6; ++u) m[u] = -xi[6 * (long long)k + u];
+    se3_left_jacobian(m, jr + 36 * (long long)k);
+  }
+}
+
+cudaError_t launch_retract(const double *T, const double *xi, int n, double *out, double *jr,
+                           cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_retract<<<(n + 63) / 64, 64, 0, s>>>(T, xi, n, out, jr);
+  return cudaGetLastError();
+}
+
+// (H + lambda diag H) x = -g by Cholesky in FP64; false if not positive definite.
+__device__ bool lm_solve_dev(const double *jtj, const double *g, double lambda, double *x) {
+  double A[36], L[36];
+  int q = 0;
+  for (int u = 0; u < 6; ++u)
+    for (int v = u; v < 6; ++v) {
+      A[6 * u + v] = jtj[q];
+      A[6 * v + u] = jtj[q];
+      ++q;
+    }
+  for (int u = 0; u < 36; ++u) L[u] = 0.0;
+  for (int u = 0; u < 6; ++u) A[7 * u] += lambda * A[7 * u];
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j <= i; ++j) {
+      double s = A[6 * i + j];
+      for (int k = 0; k < j; ++k) s -= L[6 * i + k] * L[6 * j + k];
+      if (i == j) {
+        if (!(s > 0.0)) return false;
+        L[7 * i] = sqrt(s);
+      } else {
+        L[6 * i + j] = s / L[7 * j];
+      }
+    }
+  double y[6];
+  for (int i = 0; i < 6; ++i) {
+    double s = -g[i];
+    for (int k = 0; k < i; ++k) s -= L[6 * i + k] * y[k];
+    y[i] = s / L[7 * i];
+  }
+  for (int i = 5; i >= 0; --i) {
+    double s = y[i];
+    for (int k = i + 1; k < 6; ++k) s -= L[6 * k + i] * x[k];
+    x[i] = s / L[7 * i];
+  }
+  return true;
+}
+
+__global__ void k_lm_init(LMState *st, const double *T0, LMArgs a, float *M, int *skip) {
+  for (int k = 0; k < 16; ++k) st->T[k] = st->Tc[k] = T0[k];
+  st->lambda = a.lambda0;
+  st->iters = st->accepted = st->converged = st->done = 0;
+  st->have_candidate = 1;
+  pose_to_m(T0, a.cx, a.cy, a.cz, M);
+  *skip = 0;
+}
+
+__global__ void k_lm_take_initial(LMState *st, const long long *counts, const double *els,
+                                  const double *grad, const double *jtj) {
+  st->e = els[0];
+  st->e_ls0 = els[0];
+  for (int k = 0; k < 6; ++k) st->g[k] = grad[k];
+  for (int k = 0; k < 21; ++k) st->H[k] = jtj[k];
+  st->e_table = (counts[1] + counts[3] + counts[5]) - (counts[0] + counts[2] + counts[4]);
+  st->e_table0 = st->e_table;
+}
+
+__global__ void k_lm_propose(LMState *st, LMArgs a, float *M, int *skip) {
+  if (st->done) {
+    *skip = 1;
+    return;
+  }
+  double dx[6];
+  if (!lm_solve_dev(st->H, st->g, st->lambda, dx)) {
+    st->lambda *= a.lambda_up;
+    st->iters += 1;
+    *skip = 1;
+    return;
+  }
+  double nrm = 0.0;
+  for (int k = 0; k < 6; ++k) nrm += dx[k] * dx[k];
+  if (sqrt(nrm) < a.step_tol) {
+    st->done = 1;
+    st->converged = 1;
+    *skip = 1;
+    return;
+  }
+  se3_right_dev(st->T, dx, st->Tc);
+  pose_to_m(st->Tc, a.cx, a.cy, a.cz, M);
+  *skip = 0;
+}
+
+__global__ void k_lm_accept(LMState *st, LMArgs a, const long long *counts, const double *els,
+                            const double *grad, const double *jtj, int *skip) {
+  if (*skip) return;
+  st->iters += 1;
+  if (els[0] < st->e) {
+    for (int k = 0; k < 16; ++k) st->T[k] = st->Tc[k];
+    st->e = els[0];
+    for (int k = 0; k < 6; ++k) st->g[k] = grad[k];
+    for (int k = 0; k < 21; ++k) st->H[k] = jtj[k];
+    st->e_table = (counts[1] + counts[3] + counts[5]) - (counts[0] + counts[2] + counts[4]);
+    st->lambda /= a.lambda_down;
+    st->accepted += 1;
+  } else {
+    st->lambda *= a.lambda_up;
+  }
+}
+
+cudaError_t launch_lm_init(LMState *st, const double *T0, const LMArgs &a, float *M, int *skip,
+                           cudaStream_t s) {
+  k_lm_init<<<1, 1, 0, s>>>(st, T0, a, M, skip);
+  return cudaGetLastError();
+}
+cudaError_t launch_lm_take_initial(LMState *st, const long long *counts, const double *els,
+                                   const double *grad, const double *jtj, cudaStream_t s) {
+  k_lm_take_initial<<<1, 1, 0, s>>>(st, counts, els, grad, jtj);
+  return cudaGetLastError();
+}
+cudaError_t launch_lm_propose(LMState *st, const LMArgs &a, float *M, int *skip, cudaStream_t s) {
+  k_lm_propose<<<1, 1, 0, s>>>(st, a, M, skip);
+  return cudaGetLastError();
+}
+cudaError_t launch_lm_accept(LMState *st, const LMArgs &a, const long long *counts,
+                             const double *els, const double *grad, const double *jtj, int *skip,
+                             cudaStream_t s) {
+  k_lm_accept<<<1, 1, 0, s>>>(st, a, counts, els, grad, jtj, skip);
+  return cudaGetLastError();
+}
+
+}  // namespace rmk

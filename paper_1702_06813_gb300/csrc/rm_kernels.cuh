@@ -1,0 +1,90 @@
+// rm_kernels.cuh -- launch interface between the C-ABI layer and the CUDA kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "rm_internal.cuh"
+
+namespace rmk {
+
+struct CostParams {
+  float eps, w_fofo, w_fofu, w_fufo;
+};
+
+// Per-wave scratch and per-call buffers handed to the kernels.
+struct WaveArgs {
+  DevCam cam;
+  TileGeom tg;
+  int V;
+  long long T;
+  int n_poses;        // poses in this wave
+  int wave_base;      // global index of the wave's first pose
+  const float4 *v;    // map vertices (re-centred), w unused
+  const int4 *faces;  // i0, i1, i2, label
+  const float4 *planes;  // unit world normal, label bits in w
+  const float *Ms;    // 12 floats per global pose (world -> camera, FP32)
+  float4 *vc;         // wave: V camera-space vertices per pose
+  int2 *vs;           // wave: V snapped vertices per pose (pinhole)
+  int *counts;        // wave: ntiles per pose
+  TriRec *bins;       // wave: ntiles * cap per pose
+  double *partial;    // wave: ntiles * kNumVals per pose
+  unsigned *status;   // device status word
+  const int *skip;    // optional: non-zero means "skip this evaluation" (LM control)
+  // cost inputs
+  const float *scan_depth;
+  const uint8_t *scan_cls;
+  CostParams prm;
+  // per-pose results (global pose index): counts[6] e_table e_ls grad[6] jtj[21]
+  long long *res_counts;
+  long long *res_etable;
+  double *res_els;
+  double *res_grad;
+  double *res_jtj;
+  // render outputs (global pose index)
+  float *depth;
+  int *tri_id;
+  float *bary;
+};
+
+enum Mode { kRender = 0, kCost = 1, kCostGrad = 2 };
+
+cudaError_t launch_pose_to_m(const double *poses, int n, double cx, double cy, double cz,
+                             float *Ms, cudaStream_t s);
+// ev (optional, 5 events): recorded before the vertex kernel, then after the vertex, setup,
+// raster and reduce kernels, on stream s.
+cudaError_t launch_wave(const WaveArgs &a, int mode, cudaStream_t s, cudaEvent_t *ev = nullptr);
+int wave_kernel_launches(const WaveArgs &a, int mode);
+cudaError_t launch_retract(const double *T, const double *xi, int n, double *out, double *jr,
+                           cudaStream_t s);
+
+// Levenberg-Marquardt state on the device (one pose).
+struct LMState {
+  double T[16];        // current pose
+  double Tc[16];       // candidate pose
+  double e, g[6], H[21];
+  double lambda;
+  long long e_table;
+  double e_ls0;
+  long long e_table0;
+  int iters, accepted, converged, done;
+  int have_candidate;
+  int pad;
+};
+
+struct LMArgs {
+  double lambda0, lambda_up, lambda_down, step_tol;
+  double cx, cy, cz;   // map centre
+};
+
+cudaError_t launch_lm_init(LMState *st, const double *T0, const LMArgs &a, float *M,
+                           int *skip, cudaStream_t s);
+cudaError_t launch_lm_take_initial(LMState *st, const long long *counts, const double *els,
+                                   const double *grad, const double *jtj, cudaStream_t s);
+cudaError_t launch_lm_propose(LMState *st, const LMArgs &a, float *M, int *skip,
+                              cudaStream_t s);
+cudaError_t launch_lm_accept(LMState *st, const LMArgs &a, const long long *counts,
+                             const double *els, const double *grad, const double *jtj,
+                             int *skip, cudaStream_t s);
+
+}  // namespace rmk

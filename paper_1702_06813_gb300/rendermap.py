@@ -1,0 +1,257 @@
+"""PyTorch-facing wrappers of the C ABI (include/rendermap.h).
+
+Torch supplies device memory and the current CUDA stream; every step of the pose-cost path
+runs in librendermap's kernels. Inputs may be numpy arrays or torch tensors (host or CUDA);
+results come back as CUDA tensors unless ``host=True``.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _native as N
+from ._native import check, lib
+
+RM_PINHOLE, RM_RAYTABLE = N.RM_PINHOLE, N.RM_RAYTABLE
+OUTCOMES = ("fofo_reward", "fofo_penalty", "fofu_reward", "fofu_penalty", "fufo_reward",
+            "fufo_penalty")
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _dev_tensor(x, dtype, device="cuda"):
+    if isinstance(x, torch.Tensor):
+        return x.to(device=device, dtype=dtype).contiguous()
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=dtype, device=device)
+
+
+@dataclass
+class Intrinsics:
+    """Camera model of include/rendermap.h (pinhole, or a ray table for panoramic sensors)."""
+    model: int
+    width: int
+    height: int
+    fx: float = 0.0
+    fy: float = 0.0
+    cx: float = 0.0
+    cy: float = 0.0
+    az0: float = 0.0
+    az_step: float = 0.0
+    el0: float = 0.0
+    el_step: float = 0.0
+    near: float = 0.1
+    far: float = math.inf
+    rays: torch.Tensor | None = None  # (H, W, 3) float32 on the device for RM_RAYTABLE
+
+    @staticmethod
+    def from_camera(cam, device="cuda") -> "Intrinsics":
+        """From any object with the attributes of synth.Camera."""
+        model = RM_PINHOLE if cam.model == "pinhole" else RM_RAYTABLE
+        rays = None
+        if model == RM_RAYTABLE:
+            rays = _dev_tensor(cam.ray_table_f32(), torch.float32, device)
+        return Intrinsics(model, cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy, cam.az0,
+                          cam.az_step, cam.el0, cam.el_step, cam.near, cam.far, rays)
+
+    def c(self) -> N.rm_intrinsics:
+        return N.rm_intrinsics(self.model, self.width, self.height, 0, self.fx, self.fy, self.cx,
+                               self.cy, self.az0, self.az_step, self.el0, self.el_step, self.near,
+                               self.far, None if self.rays is None else self.rays.data_ptr())
+
+
+@dataclass
+class Scan:
+    """Observed scan Z_s of Eq. 1: per-pixel depth (float32) and class (uint8)."""
+    intr: Intrinsics
+    depth: torch.Tensor
+    cls: torch.Tensor
+
+    @staticmethod
+    def make(intr: Intrinsics, depth, cls, device="cuda") -> "Scan":
+        return Scan(intr, _dev_tensor(depth, torch.float32, device), _dev_tensor(cls, torch.uint8, device))
+
+    def c(self) -> N.rm_scan:
+        return N.rm_scan(self.intr.c(), self.depth.data_ptr(), self.cls.data_ptr())
+
+
+def cost_params(eps=0.1, w_fofo=1.0, w_fofu=1.0, w_fufo=1.0) -> N.rm_cost_params:
+    return N.rm_cost_params(eps, w_fofo, w_fofu, w_fufo)
+
+
+class Map:
+    """A labelled triangle-mesh map (Sec. III.A) resident on the GPU."""
+
+    def __init__(self, vertices, faces, labels):
+        v = np.ascontiguousarray(vertices.cpu().numpy() if isinstance(vertices, torch.Tensor) else vertices,
+                                 dtype=np.float32).reshape(-1, 3)
+        f = np.ascontiguousarray(faces.cpu().numpy() if isinstance(faces, torch.Tensor) else faces,
+                                 dtype=np.int32).reshape(-1, 3)
+        lab = np.ascontiguousarray(labels.cpu().numpy() if isinstance(labels, torch.Tensor) else labels,
+                                   dtype=np.uint8).reshape(-1)
+        if lab.shape[0] != f.shape[0]:
+            raise ValueError("one label per face")
+        h = ctypes.c_void_p()
+        check(lib().rm_map_create(v.ctypes.data_as(ctypes.c_void_p), v.shape[0],
+                                  f.ctypes.data_as(ctypes.c_void_p), lab.ctypes.data_as(ctypes.c_void_p),
+                                  f.shape[0], ctypes.byref(h)))
+        self._h = h
+        self.n_vertices, self.n_faces = v.shape[0], f.shape[0]
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("map is closed")
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            lib().rm_map_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def centre(self) -> np.ndarray:
+        c = np.zeros(3)
+        check(lib().rm_map_info(self.handle, None, None, c.ctypes.data_as(ctypes.c_void_p)))
+        return c
+
+    def set_tuning(self, tile=(0, 0), bin_capacity=0, wave_poses=0, async_status=False):
+        t = N.rm_tuning(tile[0], tile[1], bin_capacity, wave_poses, int(async_status))
+        check(lib().rm_map_set_tuning(self.handle, ctypes.byref(t)))
+
+    def profile(self, enable: bool):
+        """Start (clearing the record) or stop per-kernel event timing on this map."""
+        check(lib().rm_profile(self.handle, int(enable)))
+
+    def profile_read(self) -> dict:
+        """{kernel: (launches, total_ms)} recorded so far, plus the kernel launch count."""
+        arr = (N.rm_kernel_time * 8)()
+        n = ctypes.c_int32()
+        launches = ctypes.c_int64()
+        check(lib().rm_profile_read(self.handle, arr, 8, ctypes.byref(n), ctypes.byref(launches)))
+        out = {arr[k].name.decode(): (arr[k].launches, arr[k].total_ms) for k in range(n.value)}
+        return {"kernels": out, "launches": launches.value}
+
+    def get_tuning(self) -> dict:
+        t = N.rm_tuning()
+        check(lib().rm_map_get_tuning(self.handle, ctypes.byref(t)))
+        return {"tile": (t.tile_w, t.tile_h), "bin_capacity": t.bin_capacity,
+                "wave_poses": t.wave_poses, "async_status": bool(t.async_status)}
+
+
+def _poses(poses, device="cuda"):
+    p = _dev_tensor(poses, torch.float64, device).reshape(-1, 16)
+    return p, p.shape[0]
+
+
+def render_depth(m: Map, poses, intr: Intrinsics, want_id=True, want_bary=False):
+    """R(Y) of Eq. 1 for each pose: depth (N,H,W) float32 NaN-for-miss, tri_id (N,H,W) int32,
+    bary (N,H,W,2) float32."""
+    p, n = _poses(poses)
+    depth = torch.empty((n, intr.height, intr.width), dtype=torch.float32, device="cuda")
+    ids = torch.empty_like(depth, dtype=torch.int32) if want_id else None
+    bary = torch.empty((n, intr.height, intr.width, 2), dtype=torch.float32, device="cuda") if want_bary else None
+    ci = intr.c()
+    check(lib().rm_render_depth(m.handle, _ptr(p), n, ctypes.byref(ci), _ptr(depth), _ptr(ids),
+                                _ptr(bary), _stream()))
+    return {"depth": depth, "tri_id": ids, "bary": bary}
+
+
+def _cost(fn, m, scan, poses, params, grad):
+    p, n = _poses(poses)
+    counts = torch.empty((n, 6), dtype=torch.int64, device="cuda")
+    etab = torch.empty(n, dtype=torch.int64, device="cuda")
+    els = torch.empty(n, dtype=torch.float64, device="cuda")
+    g = torch.empty((n, 6), dtype=torch.float64, device="cuda") if grad else None
+    h = torch.empty((n, 21), dtype=torch.float64, device="cuda") if grad else None
+    out = N.rm_cost_out(counts.data_ptr(), etab.data_ptr(), els.data_ptr(),
+                        None if g is None else g.data_ptr(), None if h is None else h.data_ptr())
+    cs = scan.c()
+    prm = params if params is not None else cost_params()
+    check(fn(m.handle, ctypes.byref(cs), _ptr(p), n, ctypes.byref(prm), ctypes.byref(out), _stream()))
+    res = {"counts": counts, "e_table": etab, "e_ls": els}
+    if grad:
+        res["grad"] = g
+        res["jtj"] = h
+    return res
+
+
+def cost(m: Map, scan: Scan, poses, params=None):
+    """Table I cost (counts per outcome and E_table) and the least-squares surrogate e_ls."""
+    return _cost(lib().rm_cost, m, scan, poses, params, False)
+
+
+def cost_grad(m: Map, scan: Scan, poses, params=None):
+    """cost() plus d e_ls / d xi and the packed Gauss-Newton matrix."""
+    return _cost(lib().rm_cost_grad, m, scan, poses, params, True)
+
+
+def pose_retract(poses, twists, with_jacobian=False):
+    """poses * exp(twists^) (and the SE(3) right Jacobians), computed on the device."""
+    p, n = _poses(poses)
+    t = _dev_tensor(twists, torch.float64).reshape(-1, 6)
+    if t.shape[0] != n:
+        raise ValueError("one twist per pose")
+    out = torch.empty((n, 16), dtype=torch.float64, device="cuda")
+    jr = torch.empty((n, 36), dtype=torch.float64, device="cuda") if with_jacobian else None
+    check(lib().rm_pose_retract(_ptr(p), _ptr(t), n, _ptr(out), _ptr(jr), _stream()))
+    out = out.reshape(n, 4, 4)
+    return (out, jr.reshape(n, 6, 6)) if with_jacobian else out
+
+
+def align(m: Map, scan: Scan, init_pose, params=None, max_iters=50, lambda0=1e-3, lambda_up=10.0,
+          lambda_down=10.0, step_tol=1e-8):
+    """Levenberg-Marquardt alignment on the device; returns (pose 4x4 float64 numpy, report)."""
+    p, _ = _poses(init_pose)
+    out = np.empty(16)
+    rep = N.rm_align_report()
+    lm = N.rm_align_params(max_iters, 0, lambda0, lambda_up, lambda_down, step_tol)
+    cs = scan.c()
+    prm = params if params is not None else cost_params()
+    st = lib().rm_align(m.handle, ctypes.byref(cs), _ptr(p), ctypes.byref(prm), ctypes.byref(lm),
+                        out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(rep), _stream())
+    if st not in (N.RM_OK, N.RM_ENOTCONV):
+        check(st)
+    report = {f: getattr(rep, f) for f, _ in N.rm_align_report._fields_ if f != "reserved"}
+    report["status"] = N.STATUS_NAMES[st]
+    return out.reshape(4, 4), report
+
+
+class RenderMapCost(torch.autograd.Function):
+    """e_ls(pose * exp(xi^)) as a differentiable function of the twist xi (6,) float64.
+
+    forward: retraction and the fused render + Table I + least-squares + adjoint kernels;
+    backward: grad_output * J_r(xi)^T g, g the adjoint gradient at the retracted pose.
+    Usage: RenderMapCost.apply(xi, pose, map, scan, params) -> scalar tensor.
+    """
+
+    @staticmethod
+    def forward(ctx, xi, pose, m, scan, params=None):
+        pose_t = _dev_tensor(pose, torch.float64).reshape(1, 16)
+        xi_d = xi.detach().to(device="cuda", dtype=torch.float64).reshape(1, 6)
+        p, jr = pose_retract(pose_t, xi_d, with_jacobian=True)
+        res = cost_grad(m, scan, p.reshape(1, 16), params)
+        ctx.save_for_backward(res["grad"][0], jr[0])
+        ctx.xi_device = xi.device
+        return res["e_ls"][0].to(xi.device)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        g, jr = ctx.saved_tensors
+        gx = jr.transpose(0, 1) @ g
+        return (grad_out.to(gx.device) * gx).to(ctx.xi_device), None, None, None, None

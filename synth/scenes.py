@@ -520,3 +520,22 @@ def cam_lidar_1024x64():
     return Camera("spherical", 1024, 64, az0=-math.pi, az_step=2 * math.pi / 1024,
                   el0=math.radians(15.0), el_step=math.radians(40.0) / 63, near=1.0,
                   range_min=1.0, range_max=80.0)
+
+
+# --------------------------------------------------------------------------------------
+# named workloads
+# --------------------------------------------------------------------------------------
+
+def workload_headline(seed=3000, n_poses=256):
+    """Candidate-pose batch on a 1M-triangle cluttered room (800k FO + 200k FU faces), one
+    640x480 Kinect-shaped scan (fx = fy = 525, 0.5-4.5 m, noise 0.5% of depth) and n_poses
+    poses drawn around the true pose with sigma 10 cm / 5 deg."""
+    mesh = room_mesh(seed, size=(10.0, 8.0, 3.0), n_boxes=120, n_slabs=12, target_fo=800_000,
+                     target_fu=200_000, n_panels=250)
+    cam = cam_kinect_640x480()
+    r = np.random.Generator(np.random.PCG64(seed + 1))
+    gt = room_pose(r, mesh)
+    depth, cls = synth_scan(mesh, cam, gt, r, sigma_rel=0.005)
+    poses = perturb_gauss(gt, r, 0.10, 5.0, n_poses)
+    return dict(name="room-1M-640x480-256poses", mesh=mesh, cam=cam, gt=gt, scan=(depth, cls),
+                poses=poses)

@@ -1,0 +1,306 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI.
+
+Visibility (triangle ids and depth keys) and Table I counts must match bit for bit; the
+least-squares cost within 1e-5 relative; gradient and Gauss-Newton matrix within 1e-3
+relative of the oracle's FP64 values; LM poses within 1 mm / 0.01 deg.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+import pytest
+
+import cases
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - the gpu marker is deselected on CPU
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1702_06813_gb300 as rm  # noqa: E402
+from paper_1702_06813_gb300 import build as rmbuild  # noqa: E402
+
+rmbuild.build()
+
+EPS_REL_COST = 1e-5
+EPS_REL_GRAD = 1e-3
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+def _same_render(gpu, orc):
+    ids = _np(gpu["tri_id"])
+    depth = _np(gpu["depth"])
+    assert np.array_equal(ids, orc["tri_id"]), f"{np.sum(ids != orc['tri_id'])} pixels differ in tri id"
+    both = ~np.isnan(orc["depth"])
+    assert np.array_equal(np.isnan(depth), ~both)
+    assert np.array_equal(depth[both].view(np.uint32), orc["depth"][both].view(np.uint32))
+
+
+def _check_cost(g, o, k=0, grad=True):
+    assert np.array_equal(_np(g["counts"])[k], o["counts"])
+    assert int(_np(g["e_table"])[k]) == o["e_table"]
+    e = float(_np(g["e_ls"])[k])
+    assert abs(e - o["e_ls"]) <= EPS_REL_COST * abs(o["e_ls"]) + 1e-12
+    if grad:
+        gg = _np(g["grad"])[k]
+        assert np.linalg.norm(gg - o["grad"]) <= EPS_REL_GRAD * np.linalg.norm(o["grad"]) + 1e-9
+        hh = _np(g["jtj"])[k]
+        assert np.linalg.norm(hh - o["jtj"]) <= EPS_REL_GRAD * np.linalg.norm(o["jtj"]) + 1e-9
+
+
+@pytest.fixture(scope="module")
+def c1():
+    c = cases.config1(seed=1000)
+    om = oracle.OracleMap(c["mesh"].vertices, c["mesh"].faces, c["mesh"].labels)
+    gm = rm.Map(c["mesh"].vertices, c["mesh"].faces, c["mesh"].labels)
+    intr = rm.Intrinsics.from_camera(c["cam"])
+    scan = rm.Scan.make(intr, *c["scan"])
+    return dict(c, om=om, gm=gm, intr=intr, gscan=scan)
+
+
+# ---------------------------------------------------------------------------------------
+# visibility
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("tile", [(32, 32), (32, 16), (16, 16)])
+def test_render_bit_exact_config1(c1, tile):
+    c1["gm"].set_tuning(tile=tile)
+    r = cases.rng(5)
+    poses = [c1["gt"], c1["start"]] + [synth.room_pose(r, c1["mesh"]) for _ in range(4)]
+    g = rm.render_depth(c1["gm"], np.stack(poses), c1["intr"])
+    for k, P in enumerate(poses):
+        o = c1["om"].render(P, c1["cam"])
+        _same_render({"tri_id": g["tri_id"][k], "depth": g["depth"][k]}, o)
+    c1["gm"].set_tuning()
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_render_bit_exact_triangle_soup_with_near_cuts(seed):
+    """Random camera-frame triangles (many cut by the near plane, some huge, some off
+    screen) at an odd image size that leaves ragged tiles."""
+    cam = cases.small_pinhole(w=75, h=53, f=50.0)
+    vc, f = cases.random_tris(seed, 400)
+    om = oracle.OracleMap(vc, f, np.zeros(len(f), np.uint8))
+    o = om.render(np.eye(4), cam)
+    assert o["stats"]["clipped"] > 0
+    gm = rm.Map(vc, f, np.zeros(len(f), np.uint8))
+    g = rm.render_depth(gm, np.eye(4)[None], rm.Intrinsics.from_camera(cam))
+    _same_render({"tri_id": g["tri_id"][0], "depth": g["depth"][0]}, o)
+
+
+def test_render_watertight_plane_gpu():
+    cam = cases.small_pinhole(w=96, h=72, f=70.0)
+    v, f = cases.plane_grid(41, 29, (-4, -4, 1.0), (8, 0, 3.0), (0, 8, 2.0), jitter=0.2, seed=9)
+    om = oracle.OracleMap(v, f, np.zeros(len(f), np.uint8))
+    o = om.render(np.eye(4), cam, frags=True)
+    assert np.all(o["frags"] == 1)
+    gm = rm.Map(v, f, np.zeros(len(f), np.uint8))
+    g = rm.render_depth(gm, np.eye(4)[None], rm.Intrinsics.from_camera(cam))
+    _same_render({"tri_id": g["tri_id"][0], "depth": g["depth"][0]}, o)
+    assert not np.isnan(_np(g["depth"])).any()
+
+
+def test_render_barycentrics(c1):
+    g = rm.render_depth(c1["gm"], c1["gt"][None], c1["intr"], want_bary=True)
+    o = c1["om"].render(c1["gt"], c1["cam"])
+    b64 = c1["om"].barycentrics(c1["gt"], c1["cam"], o["keys"])
+    bg = _np(g["bary"][0])
+    hit = ~np.isnan(o["depth"])
+    # FP32 barycentrics from camera-frame vertices of magnitude ~5 m: |error| ~ 1e-4 at most
+    assert np.nanmax(np.abs(bg[hit] - b64[hit])) < 2e-3
+    assert np.isnan(bg[~hit]).all()
+
+
+def test_render_bin_overflow_retry(c1):
+    """A tiny starting bin capacity overflows; the library grows it and the result is exact."""
+    c1["gm"].set_tuning(tile=(32, 32), bin_capacity=8)
+    g = rm.render_depth(c1["gm"], c1["gt"][None], c1["intr"])
+    assert c1["gm"].get_tuning()["bin_capacity"] > 8
+    o = c1["om"].render(c1["gt"], c1["cam"])
+    _same_render({"tri_id": g["tri_id"][0], "depth": g["depth"][0]}, o)
+    c1["gm"].set_tuning()
+
+
+def test_render_empty_and_away():
+    cam = cases.small_pinhole()
+    intr = rm.Intrinsics.from_camera(cam)
+    gm = rm.Map(np.zeros((0, 3), np.float32), np.zeros((0, 3), np.int32), np.zeros(0, np.uint8))
+    g = rm.render_depth(gm, np.eye(4)[None], intr)
+    assert torch.isnan(g["depth"]).all() and (g["tri_id"] == -1).all()
+    v, f = cases.plane_grid(3, 3, (-1, -1, -2.0), (2, 0, 0), (0, 2, 0))
+    gm = rm.Map(v, f, np.zeros(len(f), np.uint8))
+    g = rm.render_depth(gm, np.eye(4)[None], intr)
+    assert torch.isnan(g["depth"]).all()
+
+
+def test_render_one_pixel_image(c1):
+    cam = dataclasses.replace(c1["cam"], width=1, height=1, cx=0.5, cy=0.5)
+    g = rm.render_depth(c1["gm"], c1["gt"][None], rm.Intrinsics.from_camera(cam))
+    o = c1["om"].render(c1["gt"], cam)
+    _same_render({"tri_id": g["tri_id"][0], "depth": g["depth"][0]}, o)
+
+
+# ---------------------------------------------------------------------------------------
+# cost and adjoint
+# ---------------------------------------------------------------------------------------
+
+def test_cost_grad_parity_config1(c1):
+    r = cases.rng(6)
+    poses = [c1["gt"], c1["start"]] + [synth.perturb_fixed(c1["gt"], r, 0.1, 4.0) for _ in range(4)]
+    sd, sc = c1["scan"]
+    g = rm.cost_grad(c1["gm"], c1["gscan"], np.stack(poses))
+    gc = rm.cost(c1["gm"], c1["gscan"], np.stack(poses))
+    for k, P in enumerate(poses):
+        o = c1["om"].cost(P, c1["cam"], sd, sc)
+        _check_cost(g, o, k)
+        _check_cost(gc, o, k, grad=False)
+
+
+def test_cost_parity_weights_and_eps(c1):
+    prm = rm.cost_params(eps=0.05, w_fofo=1.0, w_fofu=2.5, w_fufo=0.5)
+    oprm = oracle.make_params(eps=0.05, w_fofo=1.0, w_fofu=2.5, w_fufo=0.5)
+    sd, sc = c1["scan"]
+    g = rm.cost_grad(c1["gm"], c1["gscan"], c1["start"][None], prm)
+    o = c1["om"].cost(c1["start"], c1["cam"], sd, sc, params=oprm)
+    _check_cost(g, o)
+
+
+def test_cost_parity_with_fu_faces_and_nan_scan():
+    c = cases.config2(seed=2200, target_fo=60_000, target_fu=15_000)
+    cam = dataclasses.replace(c["cam"], width=213, height=161, fx=175.0, fy=175.0, cx=106.5, cy=80.5)
+    mesh = c["mesh"]
+    r = cases.rng(9)
+    sd, sc = synth.synth_scan(mesh, cam, c["gt"], r, sigma_rel=0.005, dropout=0.05, dropout_as_nan=True)
+    om = oracle.OracleMap(mesh.vertices, mesh.faces, mesh.labels)
+    gm = rm.Map(mesh.vertices, mesh.faces, mesh.labels)
+    scan = rm.Scan.make(rm.Intrinsics.from_camera(cam), sd, sc)
+    poses = [c["gt"], c["start"], synth.perturb_fixed(c["gt"], r, 0.2, 5.0)]
+    g = rm.cost_grad(gm, scan, np.stack(poses))
+    tot = np.zeros(6, np.int64)
+    for k, P in enumerate(poses):
+        o = om.cost(P, cam, sd, sc)
+        _check_cost(g, o, k)
+        tot += o["counts"]
+    assert np.all(tot > 0)   # every Table I outcome was exercised
+
+
+def test_cost_host_buffers_match_device(c1):
+    """Host (numpy) scan and poses through the same ABI give the same numbers."""
+    import ctypes
+    from paper_1702_06813_gb300 import _native as N
+    sd, sc = c1["scan"]
+    intr = c1["intr"]
+    scan = N.rm_scan(intr.c(), sd.ctypes.data, sc.ctypes.data)
+    poses = np.ascontiguousarray(np.stack([c1["gt"], c1["start"]]))
+    counts = np.zeros((2, 6), np.int64)
+    etab = np.zeros(2, np.int64)
+    els = np.zeros(2)
+    grad = np.zeros((2, 6))
+    jtj = np.zeros((2, 21))
+    out = N.rm_cost_out(counts.ctypes.data, etab.ctypes.data, els.ctypes.data, grad.ctypes.data, jtj.ctypes.data)
+    prm = rm.cost_params()
+    N.check(N.lib().rm_cost_grad(c1["gm"].handle, ctypes.byref(scan), poses.ctypes.data_as(ctypes.c_void_p), 2,
+                                 ctypes.byref(prm), ctypes.byref(out), None))
+    g = rm.cost_grad(c1["gm"], c1["gscan"], poses)
+    assert np.array_equal(counts, _np(g["counts"]))
+    assert np.array_equal(els, _np(g["e_ls"]))
+    assert np.array_equal(grad, _np(g["grad"]))
+
+
+def test_batched_waves_equal_single_calls(c1):
+    r = cases.rng(10)
+    poses = np.stack([synth.perturb_fixed(c1["gt"], r, 0.1, 3.0) for _ in range(7)])
+    c1["gm"].set_tuning(wave_poses=3)
+    gb = rm.cost_grad(c1["gm"], c1["gscan"], poses)
+    c1["gm"].set_tuning()
+    for k in range(7):
+        g1 = rm.cost_grad(c1["gm"], c1["gscan"], poses[k:k + 1])
+        assert torch.equal(gb["counts"][k], g1["counts"][0])
+        assert torch.equal(gb["e_ls"][k], g1["e_ls"][0])
+        assert torch.equal(gb["grad"][k], g1["grad"][0])
+
+
+def test_gradient_matches_oracle_frozen_fd(c1):
+    """The GPU adjoint against central differences of the oracle's FP64 frozen cost."""
+    sd, sc = c1["scan"]
+    P = c1["start"]
+    g = _np(rm.cost_grad(c1["gm"], c1["gscan"], P[None])["grad"])[0]
+    h = 1e-5
+    fd = np.zeros(6)
+    for a in range(6):
+        xi = np.zeros(6)
+        xi[a] = h
+        fd[a] = (c1["om"].cost_frozen(P, c1["cam"], sd, sc, xi) - c1["om"].cost_frozen(P, c1["cam"], sd, sc, -xi)) / (2 * h)
+    assert np.linalg.norm(g - fd) <= EPS_REL_GRAD * np.linalg.norm(fd)
+
+
+def test_autograd_function(c1):
+    P = c1["start"]
+    sd, sc = c1["scan"]
+    for xi0 in [np.zeros(6), np.array([0.01, -0.02, 0.015, 0.01, -0.005, 0.02])]:
+        xi = torch.tensor(xi0, dtype=torch.float64, requires_grad=True)
+        e = rm.RenderMapCost.apply(xi, P, c1["gm"], c1["gscan"], None)
+        e.backward()
+        # the oracle at the retracted pose, and FD through the oracle's frozen cost
+        Pr = oracle.se3_right(P, xi0)
+        o = c1["om"].cost(Pr, c1["cam"], sd, sc)
+        assert abs(e.item() - o["e_ls"]) <= EPS_REL_COST * o["e_ls"]
+        # exact chain rule: d e(P exp(xi))/d xi = J_r(xi)^T g(P exp(xi))
+        g_or = o["grad"]
+        _, jr = rm.pose_retract(P[None], xi0[None], with_jacobian=True)
+        want = _np(jr[0]).T @ g_or
+        assert np.linalg.norm(_np(xi.grad) - want) <= EPS_REL_GRAD * np.linalg.norm(want)
+
+
+def test_retraction_and_right_jacobian():
+    from scipy.spatial.transform import Rotation
+    r = cases.rng(11)
+    T = synth.pose_from(np.array([1.0, -2.0, 0.5]), 0.3, 0.1, -0.2)
+    for _ in range(4):
+        xi = r.normal(scale=0.4, size=6)
+        out, jr = rm.pose_retract(T[None], xi[None], with_jacobian=True)
+        assert np.allclose(_np(out[0]), oracle.se3_right(T, xi), atol=1e-12)
+        # columns of J_r: exp(xi)^-1 exp(xi + h e_k) ~ exp(J_r h e_k)
+        E0 = oracle.se3_right(np.eye(4), xi)
+        for k in range(6):
+            h = 1e-6
+            d = np.zeros(6)
+            d[k] = h
+            D = np.linalg.inv(E0) @ oracle.se3_right(np.eye(4), xi + d)
+            col = np.concatenate([D[:3, 3], Rotation.from_matrix(D[:3, :3]).as_rotvec()]) / h
+            assert np.allclose(col, _np(jr[0])[:, k], atol=2e-5)
+
+
+# ---------------------------------------------------------------------------------------
+# Levenberg-Marquardt on the device
+# ---------------------------------------------------------------------------------------
+
+def _pose_gap(a, b):
+    from scipy.spatial.transform import Rotation
+    dt = np.linalg.norm(a[:3, 3] - b[:3, 3])
+    da = math.degrees(Rotation.from_matrix(a[:3, :3].T @ b[:3, :3]).magnitude())
+    return dt, da
+
+
+def test_align_matches_oracle_config1(c1):
+    sd, sc = c1["scan"]
+    gt = synth.pose_from(c1["gt"][:3, 3], 0.7, math.radians(20.0), 0.0)
+    start = synth.perturb_fixed(gt, cases.rng(12), 0.05, 2.0)
+    # noisy scan of the world from the tilted pose
+    sd, sc = synth.synth_scan(c1["mesh"], c1["cam"], gt, cases.rng(13), sigma_abs=0.01, dropout=0.05)
+    scan = rm.Scan.make(c1["intr"], sd, sc)
+    pg, rep = rm.align(c1["gm"], scan, start, max_iters=50, step_tol=1e-7)
+    po, orep = c1["om"].align(start, c1["cam"], sd, sc, max_iters=50, step_tol=1e-7)
+    dt, da = _pose_gap(pg, po)
+    assert dt < 1e-3 and da < 1e-2, (dt, da, rep, orep)
+    assert rep["e_ls_final"] < rep["e_ls_initial"]
+    dgt, agt = _pose_gap(pg, gt)
+    assert dgt < 0.01 and agt < 0.5
