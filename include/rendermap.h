@@ -195,7 +195,7 @@ rm_status rm_align(rm_map *map, const rm_scan *scan, const double *init_pose,
 /* Per-kernel timing, recorded with CUDA events on the launch stream around every kernel
  * the map launches while enabled. rm_profile(map, 1) clears the record and starts, 0 stops.
  * rm_profile_read waits for the recorded events and fills up to `cap` entries (one per
- * kernel kind: k_vertex_pinhole, k_setup_pinhole, k_raster, k_reduce), *n with the count, and
+ * kernel kind: k_cull, k_setup, k_raster, k_reduce), *n with the count, and
  * *launches (optional) with the number of kernels launched since recording started. */
 typedef struct {
   char name[48];

@@ -77,6 +77,12 @@ struct rm_map {
   float4 *d_v = nullptr;
   int4 *d_faces = nullptr;
   float4 *d_planes = nullptr;
+  int n_clusters = 0;
+  int4 *d_cl_info = nullptr;
+  float4 *d_cl_sphere = nullptr;
+  int *d_cl_verts = nullptr;
+  uchar4 *d_cl_tris = nullptr;
+  int *d_cl_ids = nullptr;
   char *arena = nullptr;
   size_t arena_bytes = 0;
   unsigned *d_status = nullptr;
@@ -94,6 +100,118 @@ struct rm_map {
 };
 
 namespace {
+
+// 21-bit spread for a 63-bit Morton key.
+uint64_t spread21(uint64_t x) {
+  x &= 0x1fffff;
+  x = (x | x << 32) & 0x1f00000000ffffull;
+  x = (x | x << 16) & 0x1f0000ff0000ffull;
+  x = (x | x << 8) & 0x100f00f00f00f00full;
+  x = (x | x << 4) & 0x10c30c30c30c30c3ull;
+  x = (x | x << 2) & 0x1249249249249249ull;
+  return x;
+}
+
+struct Clusters {
+  std::vector<int4> info;
+  std::vector<float4> sphere;
+  std::vector<int> verts;
+  std::vector<uchar4> tris;
+  std::vector<int> ids;
+};
+
+// Clusters of at most 64 triangles over at most 64 distinct vertices, grown greedily along
+// the Morton order of the face centroids, each with an FP64 bounding sphere rounded outward.
+void build_clusters(const std::vector<float4> &hv, const int32_t *faces, int64_t T, Clusters &cl) {
+  if (T == 0) return;
+  double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  std::vector<double> cen(3 * (size_t)T);
+  for (int64_t k = 0; k < T; ++k)
+    for (int a = 0; a < 3; ++a) {
+      double c = 0.0;
+      for (int m = 0; m < 3; ++m) {
+        const float4 &v = hv[faces[3 * k + m]];
+        c += a == 0 ? v.x : (a == 1 ? v.y : v.z);
+      }
+      c /= 3.0;
+      cen[3 * k + a] = c;
+      lo[a] = std::min(lo[a], c);
+      hi[a] = std::max(hi[a], c);
+    }
+  std::vector<std::pair<uint64_t, int>> order((size_t)T);
+  for (int64_t k = 0; k < T; ++k) {
+    uint64_t key = 0;
+    for (int a = 0; a < 3; ++a) {
+      double ext = hi[a] - lo[a];
+      double u = ext > 0 ? (cen[3 * k + a] - lo[a]) / ext : 0.0;
+      key |= spread21((uint64_t)std::min(2097151.0, std::max(0.0, u * 2097151.0))) << a;
+    }
+    order[k] = {key, (int)k};
+  }
+  std::sort(order.begin(), order.end());
+  int loc[64];
+  int nv = 0, nt = 0, voff = 0, toff = 0;
+  auto flush = [&]() {
+    if (nt == 0) return;
+    double bl[3] = {INFINITY, INFINITY, INFINITY}, bh[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int k = 0; k < nv; ++k) {
+      const float4 &v = hv[loc[k]];
+      const double p[3] = {v.x, v.y, v.z};
+      for (int a = 0; a < 3; ++a) {
+        bl[a] = std::min(bl[a], p[a]);
+        bh[a] = std::max(bh[a], p[a]);
+      }
+    }
+    const float c32[3] = {(float)(0.5 * (bl[0] + bh[0])), (float)(0.5 * (bl[1] + bh[1])),
+                          (float)(0.5 * (bl[2] + bh[2]))};
+    double r = 0.0;
+    for (int k = 0; k < nv; ++k) {
+      const float4 &v = hv[loc[k]];
+      const double d[3] = {(double)v.x - c32[0], (double)v.y - c32[1], (double)v.z - c32[2]};
+      r = std::max(r, std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]));
+    }
+    float r32 = (float)(r * (1.0 + 1e-6) + 1e-7);
+    while ((double)r32 < r) r32 = std::nextafter(r32, INFINITY);
+    cl.info.push_back(make_int4(voff, toff, nv, nt));
+    cl.sphere.push_back(make_float4(c32[0], c32[1], c32[2], r32));
+    for (int k = 0; k < nv; ++k) cl.verts.push_back(loc[k]);
+    voff += nv;
+    toff += nt;
+    nv = nt = 0;
+  };
+  for (const auto &o : order) {
+    const int32_t *f = faces + 3 * (int64_t)o.second;
+    int li[3], fresh = 0;
+    for (int m = 0; m < 3; ++m) {
+      li[m] = -1;
+      for (int k = 0; k < nv; ++k)
+        if (loc[k] == f[m]) li[m] = k;
+      for (int q = 0; q < m; ++q)
+        if (li[m] < 0 && f[q] == f[m]) li[m] = -2 - q;  // repeated index within the face
+      fresh += li[m] == -1;
+    }
+    if (nt + 1 > 64 || nv + fresh > 64) {
+      flush();
+      for (int m = 0; m < 3; ++m) {
+        li[m] = -1;
+        for (int q = 0; q < m; ++q)
+          if (f[q] == f[m]) li[m] = -2 - q;
+      }
+    }
+    for (int m = 0; m < 3; ++m) {
+      if (li[m] == -1) {
+        loc[nv] = f[m];
+        li[m] = nv++;
+      } else if (li[m] <= -2) {
+        li[m] = li[-2 - li[m]];
+      }
+    }
+    cl.tris.push_back(make_uchar4((unsigned char)li[0], (unsigned char)li[1], (unsigned char)li[2], 0));
+    cl.ids.push_back(o.second);
+    ++nt;
+  }
+  flush();
+}
 
 rm_status ensure_arena(rm_map *m, size_t bytes, cudaStream_t s) {
   if (bytes <= m->arena_bytes) return RM_OK;
@@ -157,9 +275,18 @@ DevCam make_cam(const rm_intrinsics *in, const float *d_rays) {
 int wave_size(const rm_map *m, int n, const TileGeom &tg) {
   if (m->tuning.wave_poses > 0) return std::min(n, m->tuning.wave_poses);
   // keep per-wave scratch near 2 GiB
-  size_t per = (size_t)m->V * 24 + (size_t)tg.ntiles * ((size_t)tg.cap * sizeof(TriRec) + 8 * 40);
+  size_t per = (size_t)m->n_clusters * 4 + (size_t)tg.ntiles * ((size_t)tg.cap * sizeof(TriRec) + 8 * 40);
   size_t w = std::max<size_t>(1, (size_t(2) << 30) / std::max<size_t>(per, 1));
   return (int)std::min<size_t>(std::min<size_t>(w, 64), (size_t)n);
+}
+
+void set_clusters(const rm_map *m, WaveArgs &a) {
+  a.n_clusters = m->n_clusters;
+  a.cl_info = m->d_cl_info;
+  a.cl_sphere = m->d_cl_sphere;
+  a.cl_verts = m->d_cl_verts;
+  a.cl_tris = m->d_cl_tris;
+  a.cl_ids = m->d_cl_ids;
 }
 
 rm_status take_events(rm_map *m, cudaEvent_t *ev) {
@@ -271,8 +398,8 @@ rm_status run_eval(rm_map *m, const EvalReq &r, cudaStream_t s) {
       if (r.tri_id && !dev_id) plan.take<int>(P * r.n);
       if (r.bary && !dev_bary) plan.take<float>(2 * P * r.n);
     }
-    plan.take<float4>((size_t)m->V * nw);
-    plan.take<int2>((size_t)m->V * nw);
+    plan.take<int>((size_t)m->n_clusters * nw);
+    plan.take<int>(nw);
     plan.take<int>((size_t)tg.ntiles * nw);
     plan.take<TriRec>((size_t)tg.ntiles * tg.cap * nw);
     plan.take<double>((size_t)tg.ntiles * rmk::kNumVals * nw);
@@ -300,8 +427,8 @@ rm_status run_eval(rm_map *m, const EvalReq &r, cudaStream_t s) {
       if (r.tri_id) d_id = dev_id ? r.tri_id : cv.take<int>(P * r.n);
       if (r.bary) d_bary = dev_bary ? r.bary : cv.take<float>(2 * P * r.n);
     }
-    float4 *d_vc = cv.take<float4>((size_t)m->V * nw);
-    int2 *d_vs = cv.take<int2>((size_t)m->V * nw);
+    int *d_vis = cv.take<int>((size_t)m->n_clusters * nw);
+    int *d_vcount = cv.take<int>(nw);
     int *d_bcount = cv.take<int>((size_t)tg.ntiles * nw);
     TriRec *d_bins = cv.take<TriRec>((size_t)tg.ntiles * tg.cap * nw);
     double *d_partial = cv.take<double>((size_t)tg.ntiles * rmk::kNumVals * nw);
@@ -322,8 +449,9 @@ rm_status run_eval(rm_map *m, const EvalReq &r, cudaStream_t s) {
     a.faces = m->d_faces;
     a.planes = m->d_planes;
     a.Ms = d_M;
-    a.vc = d_vc;
-    a.vs = d_vs;
+    set_clusters(m, a);
+    a.vis = d_vis;
+    a.vis_count = d_vcount;
     a.counts = d_bcount;
     a.bins = d_bins;
     a.partial = d_partial;
@@ -435,6 +563,14 @@ rm_status rm_map_create(const float *vertices, int64_t n_vertices, const int32_t
     std::memcpy(&lab, &li, 4);
     hp[k] = make_float4((float)n[0], (float)n[1], (float)n[2], lab);
   }
+  Clusters cl;
+  build_clusters(hv, faces, n_faces, cl);
+  m->n_clusters = (int)cl.info.size();
+  auto up = [&](void **dst, const void *src, size_t bytes) -> cudaError_t {
+    cudaError_t e = cudaMalloc(dst, std::max<size_t>(bytes, 16));
+    if (e != cudaSuccess || bytes == 0) return e;
+    return cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+  };
   auto cleanup = [&](rm_status s) {
     rm_map_destroy(m);
     return s;
@@ -448,7 +584,12 @@ rm_status rm_map_create(const float *vertices, int64_t n_vertices, const int32_t
       (e = cudaMemcpy(m->d_v, hv.data(), sizeof(float4) * hv.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemcpy(m->d_faces, hf.data(), sizeof(int4) * hf.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemcpy(m->d_planes, hp.data(), sizeof(float4) * hp.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (e = cudaMemset(m->d_status, 0, sizeof(unsigned))) != cudaSuccess)
+      (e = cudaMemset(m->d_status, 0, sizeof(unsigned))) != cudaSuccess ||
+      (e = up((void **)&m->d_cl_info, cl.info.data(), sizeof(int4) * cl.info.size())) != cudaSuccess ||
+      (e = up((void **)&m->d_cl_sphere, cl.sphere.data(), sizeof(float4) * cl.sphere.size())) != cudaSuccess ||
+      (e = up((void **)&m->d_cl_verts, cl.verts.data(), sizeof(int) * cl.verts.size())) != cudaSuccess ||
+      (e = up((void **)&m->d_cl_tris, cl.tris.data(), sizeof(uchar4) * cl.tris.size())) != cudaSuccess ||
+      (e = up((void **)&m->d_cl_ids, cl.ids.data(), sizeof(int) * cl.ids.size())) != cudaSuccess)
     return cleanup(fail(e == cudaErrorMemoryAllocation ? RM_ENOMEM : RM_ECUDA,
                         std::string("map upload: ") + cudaGetErrorString(e)));
   *out = m;
@@ -462,6 +603,11 @@ void rm_map_destroy(rm_map *m) {
   cudaFree(m->d_v);
   cudaFree(m->d_faces);
   cudaFree(m->d_planes);
+  cudaFree(m->d_cl_info);
+  cudaFree(m->d_cl_sphere);
+  cudaFree(m->d_cl_verts);
+  cudaFree(m->d_cl_tris);
+  cudaFree(m->d_cl_ids);
   cudaFree(m->arena);
   cudaFree(m->d_status);
   if (m->h_status) cudaFreeHost(m->h_status);
@@ -581,7 +727,7 @@ rm_status rm_profile_read(rm_map *m, rm_kernel_time *out, int32_t cap, int32_t *
   if (!m || (cap > 0 && !out)) return fail(RM_EINVAL, "NULL argument");
   std::lock_guard<std::mutex> lk(m->mu);
   RM_TRY(drain_events(m));
-  static const char *names[4] = {"k_vertex_pinhole", "k_setup_pinhole", "k_raster", "k_reduce"};
+  static const char *names[4] = {"k_cull", "k_setup", "k_raster", "k_reduce"};
   int k = 0;
   for (int q = 0; q < 4 && k < cap; ++q) {
     if (m->prof_n[q] == 0) continue;
@@ -634,8 +780,8 @@ rm_status rm_align(rm_map *m, const rm_scan *scan, const double *init_pose,
     plan.take<double>(1);
     plan.take<double>(6);
     plan.take<double>(21);
-    plan.take<float4>(m->V);
-    plan.take<int2>(m->V);
+    plan.take<int>(m->n_clusters);
+    plan.take<int>(1);
     plan.take<int>(tg.ntiles);
     plan.take<TriRec>((size_t)tg.ntiles * tg.cap);
     plan.take<double>((size_t)tg.ntiles * rmk::kNumVals);
@@ -663,8 +809,9 @@ rm_status rm_align(rm_map *m, const rm_scan *scan, const double *init_pose,
     a.faces = m->d_faces;
     a.planes = m->d_planes;
     a.Ms = d_M;
-    a.vc = cv.take<float4>(m->V);
-    a.vs = cv.take<int2>(m->V);
+    set_clusters(m, a);
+    a.vis = cv.take<int>(m->n_clusters);
+    a.vis_count = cv.take<int>(1);
     a.counts = cv.take<int>(tg.ntiles);
     a.bins = cv.take<TriRec>((size_t)tg.ntiles * tg.cap);
     a.partial = cv.take<double>((size_t)tg.ntiles * rmk::kNumVals);

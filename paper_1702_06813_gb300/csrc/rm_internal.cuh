@@ -26,9 +26,6 @@ constexpr int kNumVals = 34;                      // counts 6 | e_ls | grad 6 | 
 constexpr unsigned kStatusOverflow = 1u;
 constexpr unsigned kStatusTimeout = 2u;
 constexpr int kThreads = 256;                     // raster CTA
-constexpr int kChunk = 256;                       // triangle records staged per TMA copy
-constexpr int kLargePixels = 48;                  // bbox-in-tile pixels above which a
-                                                  // triangle is rasterised by the whole CTA
 
 struct DevCam {
   int model, W, H, pad;

@@ -101,28 +101,56 @@ cudaError_t launch_pose_to_m(const double *poses, int n, double cx, double cy, d
   return cudaGetLastError();
 }
 
-// ------------------------------------------------------------------ vertices
+// ------------------------------------------------------------------ cluster culling
 
-__global__ void __launch_bounds__(256) k_vertex_pinhole(WaveArgs a) {
+// A cluster is dropped only when its bounding sphere lies entirely outside the view volume
+// that can hold a pixel sample: behind the near plane, beyond the far plane, or (pinhole)
+// outside the side planes through image columns -2 and W+2 and rows -2 and H+2. The slack
+// covers the FP32 error of transforming the sphere centre, so no triangle that the
+// rasteriser would draw is ever dropped.
+__device__ __forceinline__ bool cluster_visible(const DevCam &cam, const float *M, float4 sph) {
+  const float3 c = xform(M, sph.x, sph.y, sph.z);
+  const float r = sph.w;
+  const float slack = 1e-4f * (1.0f + fabsf(c.x) + fabsf(c.y) + fabsf(c.z) + r);
+  if (cam.model == 0) {
+    if (c.z + r < cam.near_m - slack) return false;
+    if (c.z - r > cam.far_m + slack) return false;
+    // side planes X - a Z = 0 with a = (x_edge - cx) / fx, likewise for Y
+    const float xl = -2.0f, xr = cam.W + 2.0f, yt = -2.0f, yb = cam.H + 2.0f;
+    const float al = (xl - cam.cx) / cam.fx, ar = (xr - cam.cx) / cam.fx;
+    const float at = (yt - cam.cy) / cam.fy, ab = (yb - cam.cy) / cam.fy;
+    const float sx = cam.fx > 0.0f ? 1.0f : -1.0f, sy = cam.fy > 0.0f ? 1.0f : -1.0f;
+    const float lim = r + slack;
+    if (sx * (c.x - al * c.z) < -lim * sqrtf(1.0f + al * al)) return false;
+    if (sx * (ar * c.z - c.x) < -lim * sqrtf(1.0f + ar * ar)) return false;
+    if (sy * (c.y - at * c.z) < -lim * sqrtf(1.0f + at * at)) return false;
+    if (sy * (ab * c.z - c.y) < -lim * sqrtf(1.0f + ab * ab)) return false;
+    return true;
+  }
+  const float dist = sqrtf(c.x * c.x + c.y * c.y + c.z * c.z);
+  if (dist + r < cam.near_m - slack) return false;
+  if (dist - r > cam.far_m + slack) return false;
+  return true;
+}
+
+__global__ void __launch_bounds__(256) k_cull(WaveArgs a) {
   if (a.skip && *a.skip) return;
   const int q = blockIdx.y;
   const float *Mg = a.Ms + 12 * (long long)(a.wave_base + q);
   float M[12];
 #pragma unroll
   for (int k = 0; k < 12; ++k) M[k] = Mg[k];
-  float4 *vc = a.vc + (long long)q * a.V;
-  int2 *vs = a.vs + (long long)q * a.V;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < a.V; k += gridDim.x * blockDim.x) {
-    float4 v = a.v[k];
-    float3 c = xform(M, v.x, v.y, v.z);
-    vc[k] = make_float4(c.x, c.y, c.z, 0.0f);
-    int2 s = make_int2(kSentinel, 1);  // behind the near plane
-    if (c.z >= a.cam.near_m) {
-      int xi, yi;
-      s = snap(a.cam, c.x, c.y, c.z, xi, yi) ? make_int2(xi, yi) : make_int2(kSentinel, 2);
-    }
-    vs[k] = s;
-  }
+  int *vis = a.vis + (long long)q * a.n_clusters;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool keep = c < a.n_clusters && cluster_visible(a.cam, M, a.cl_sphere[c]);
+  // warp-aggregated append
+  const unsigned m = __ballot_sync(0xffffffffu, keep);
+  if (m == 0) return;
+  const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(&a.vis_count[q], __popc(m));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (keep) vis[base + __popc(m & ((1u << lane) - 1u))] = c;
 }
 
 // ------------------------------------------------------------------ triangle setup + binning
@@ -162,132 +190,222 @@ __device__ __forceinline__ void emit_piece(int x0, int y0, int x1, int y1, int x
     }
 }
 
-__global__ void __launch_bounds__(256) k_setup_pinhole(WaveArgs a) {
+constexpr int kClusterMax = 64;  // vertices and triangles per cluster
+
+// One warp per visible cluster: its vertices are transformed and snapped once into shared
+// memory, then each lane sets up triangles (near-plane cut, culling, depth plane) and
+// appends them to the screen-tile bins.
+__global__ void __launch_bounds__(256) k_setup(WaveArgs a) {
+  __shared__ float4 s_vc[8][kClusterMax];
+  __shared__ int2 s_vs[8][kClusterMax];
+  __shared__ int s_gid[8][kClusterMax];
   if (a.skip && *a.skip) return;
   const int q = blockIdx.y;
-  const float4 *vc = a.vc + (long long)q * a.V;
-  const int2 *vs = a.vs + (long long)q * a.V;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const float *Mg = a.Ms + 12 * (long long)(a.wave_base + q);
+  float M[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) M[k] = Mg[k];
+  const int nvis = a.vis_count[q];
+  const int *vis = a.vis + (long long)q * a.n_clusters;
   int *counts = a.counts + (long long)q * a.tg.ntiles;
   TriRec *bins = a.bins + (long long)q * a.tg.ntiles * a.tg.cap;
   const int W = a.cam.W, H = a.cam.H;
   const float near_m = a.cam.near_m;
-  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < a.T;
-       k += (long long)gridDim.x * blockDim.x) {
-    const int4 f = a.faces[k];
-    const int2 s0 = vs[f.x], s1 = vs[f.y], s2 = vs[f.z];
-    if (s0.x != kSentinel && s1.x != kSentinel && s2.x != kSentinel) {
-      // all three in front of the near plane and inside the guard band
-      int xmin = min(s0.x, min(s1.x, s2.x)), xmax = max(s0.x, max(s1.x, s2.x));
-      int ymin = min(s0.y, min(s1.y, s2.y)), ymax = max(s0.y, max(s1.y, s2.y));
-      if (max((xmin + 127) >> 8, 0) > min((xmax - 128) >> 8, W - 1)) continue;
-      if (max((ymin + 127) >> 8, 0) > min((ymax - 128) >> 8, H - 1)) continue;
-      const float4 p0 = vc[f.x], p1 = vc[f.y], p2 = vc[f.z];
-      PlaneN pl = plane_n(make_float3(p0.x, p0.y, p0.z), make_float3(p1.x, p1.y, p1.z),
-                          make_float3(p2.x, p2.y, p2.z));
+  for (int ci = blockIdx.x * 8 + warp; ci < nvis; ci += gridDim.x * 8) {
+    const int4 info = a.cl_info[vis[ci]];  // vert offset, tri offset, nv, nt
+    for (int k = lane; k < info.z; k += 32) {
+      const int gv = a.cl_verts[info.x + k];
+      const float4 v = a.v[gv];
+      const float3 c = xform(M, v.x, v.y, v.z);
+      int2 sv = make_int2(kSentinel, 1);  // behind the near plane
+      if (c.z >= near_m) {
+        int xi, yi;
+        sv = snap(a.cam, c.x, c.y, c.z, xi, yi) ? make_int2(xi, yi) : make_int2(kSentinel, 2);
+      }
+      s_vc[warp][k] = make_float4(c.x, c.y, c.z, 0.0f);
+      s_vs[warp][k] = sv;
+      s_gid[warp][k] = gv;
+    }
+    __syncwarp();
+    for (int k = lane; k < info.w; k += 32) {
+      const uchar4 t = a.cl_tris[info.y + k];
+      const unsigned id = (unsigned)a.cl_ids[info.y + k];
+      const int2 s0 = s_vs[warp][t.x], s1 = s_vs[warp][t.y], s2 = s_vs[warp][t.z];
+      if (s0.x != kSentinel && s1.x != kSentinel && s2.x != kSentinel) {
+        // all three in front of the near plane and inside the guard band
+        const int xmin = min(s0.x, min(s1.x, s2.x)), xmax = max(s0.x, max(s1.x, s2.x));
+        const int ymin = min(s0.y, min(s1.y, s2.y)), ymax = max(s0.y, max(s1.y, s2.y));
+        if (max((xmin + 127) >> 8, 0) > min((xmax - 128) >> 8, W - 1)) continue;
+        if (max((ymin + 127) >> 8, 0) > min((ymax - 128) >> 8, H - 1)) continue;
+        const float4 p0 = s_vc[warp][t.x], p1 = s_vc[warp][t.y], p2 = s_vc[warp][t.z];
+        const PlaneN pl = plane_n(make_float3(p0.x, p0.y, p0.z), make_float3(p1.x, p1.y, p1.z),
+                                  make_float3(p2.x, p2.y, p2.z));
+        float A, B, C;
+        fold_pinhole(a.cam, pl, A, B, C);
+        emit_piece(s0.x, s0.y, s1.x, s1.y, s2.x, s2.y, A, B, C, pl.d, id, a, counts, bins);
+        continue;
+      }
+      // slow path: near-plane cut and/or guard band
+      const int loc[3] = {t.x, t.y, t.z};
+      int idx[3];
+      float3 v[3];
+      bool in[3];
+      int nin = 0;
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        const float4 p = s_vc[warp][loc[m]];
+        v[m] = make_float3(p.x, p.y, p.z);
+        idx[m] = s_gid[warp][loc[m]];
+        in[m] = v[m].z >= near_m;
+        nin += in[m];
+      }
+      if (nin == 0 || nin == 3) continue;  // all behind, or a vertex beyond the guard band
+      const PlaneN pl = plane_n(v[0], v[1], v[2]);
       float A, B, C;
       fold_pinhole(a.cam, pl, A, B, C);
-      emit_piece(s0.x, s0.y, s1.x, s1.y, s2.x, s2.y, A, B, C, pl.d, (unsigned)k, a, counts, bins);
-      continue;
-    }
-    // slow path: near-plane cut and/or guard band
-    const int idx[3] = {f.x, f.y, f.z};
-    float3 v[3];
+      float3 poly[4];
+      int n = 0;
 #pragma unroll
-    for (int m = 0; m < 3; ++m) {
-      float4 p = vc[idx[m]];
-      v[m] = make_float3(p.x, p.y, p.z);
+      for (int m = 0; m < 3; ++m) {
+        const int nx = (m + 1) % 3;
+        if (in[m]) poly[n++] = v[m];
+        if (in[m] != in[nx])
+          poly[n++] = idx[m] < idx[nx] ? near_cut(v[m], v[nx], near_m) : near_cut(v[nx], v[m], near_m);
+      }
+      int sx[4], sy[4];
+      bool ok = true;
+      for (int m = 0; m < n; ++m) ok = ok && snap(a.cam, poly[m].x, poly[m].y, poly[m].z, sx[m], sy[m]);
+      if (!ok) continue;
+      emit_piece(sx[0], sy[0], sx[1], sy[1], sx[2], sy[2], A, B, C, pl.d, id, a, counts, bins);
+      if (n == 4)
+        emit_piece(sx[0], sy[0], sx[2], sy[2], sx[3], sy[3], A, B, C, pl.d, id, a, counts, bins);
     }
-    bool in[3];
-    int nin = 0;
-#pragma unroll
-    for (int m = 0; m < 3; ++m) {
-      in[m] = v[m].z >= near_m;
-      nin += in[m];
-    }
-    if (nin == 0 || nin == 3) continue;  // all behind, or a vertex beyond the guard band
-    PlaneN pl = plane_n(v[0], v[1], v[2]);
-    float A, B, C;
-    fold_pinhole(a.cam, pl, A, B, C);
-    float3 poly[4];
-    int n = 0;
-#pragma unroll
-    for (int m = 0; m < 3; ++m) {
-      int nx = (m + 1) % 3;
-      if (in[m]) poly[n++] = v[m];
-      if (in[m] != in[nx]) poly[n++] = idx[m] < idx[nx] ? near_cut(v[m], v[nx], near_m)
-                                                        : near_cut(v[nx], v[m], near_m);
-    }
-    int sx[4], sy[4];
-    bool ok = true;
-    for (int m = 0; m < n; ++m) ok = ok && snap(a.cam, poly[m].x, poly[m].y, poly[m].z, sx[m], sy[m]);
-    if (!ok) continue;
-    emit_piece(sx[0], sy[0], sx[1], sy[1], sx[2], sy[2], A, B, C, pl.d, (unsigned)k, a, counts, bins);
-    if (n == 4)
-      emit_piece(sx[0], sy[0], sx[2], sy[2], sx[3], sy[3], A, B, C, pl.d, (unsigned)k, a, counts,
-                 bins);
+    __syncwarp();
   }
 }
 
 // ------------------------------------------------------------------ raster + epilogue
 
-struct EdgeSet {
-  long long dx[3], dy[3];
-  int xa[3], ya[3];
-  int bias[3];
-};
+constexpr int kRecMax = 512;  // bin records staged in shared memory per round
 
-__device__ __forceinline__ void edge_setup(const TriRec &r, EdgeSet &e) {
-  const int x[3] = {r.x0, r.x1, r.x2}, y[3] = {r.y0, r.y1, r.y2};
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    int b = k == 2 ? 0 : k + 1;
-    e.dx[k] = (long long)x[b] - x[k];
-    e.dy[k] = (long long)y[b] - y[k];
-    e.xa[k] = x[k];
-    e.ya[k] = y[k];
-    e.bias[k] = (e.dy[k] < 0 || (e.dy[k] == 0 && e.dx[k] > 0)) ? 0 : -1;  // top-left
+// Exact edge test with int32 operands and 64-bit products: E = dx (py - ya) - dy (px - xa).
+__device__ __forceinline__ bool edge_ok(int dx, int dy, int xa, int ya, int px, int py) {
+  const long long E = (long long)dx * (py - ya) - (long long)dy * (px - xa);
+  const bool top_left = dy < 0 || (dy == 0 && dx > 0);
+  return E > 0 || (E == 0 && top_left);
+}
+
+// Clips record k's sample bounding box to the tile, stores it (tile-relative origin and
+// width) in the record's spare word and returns its pixel count.
+__device__ __forceinline__ int derive_rect(TriRec *rec, int k, int cnt, int ox, int oy, int xe,
+                                           int ye) {
+  if (k >= cnt) return 0;
+  TriRec &r = rec[k];
+  const int xmin = min(r.x0, min(r.x1, r.x2)), xmax = max(r.x0, max(r.x1, r.x2));
+  const int ymin = min(r.y0, min(r.y1, r.y2)), ymax = max(r.y0, max(r.y1, r.y2));
+  const int i0 = max((xmin + 127) >> 8, ox), i1 = min((xmax - 128) >> 8, xe);
+  const int j0 = max((ymin + 127) >> 8, oy), j1 = min((ymax - 128) >> 8, ye);
+  if (i0 > i1 || j0 > j1) {
+    r.pad = 0;
+    return 0;
   }
+  const int bw = i1 - i0 + 1;
+  r.pad = (i0 - ox) | ((j0 - oy) << 8) | (bw << 16);
+  return bw * (j1 - j0 + 1);
 }
 
-__device__ __forceinline__ bool covers(const EdgeSet &e, int i, int j) {
-  const long long px = 256ll * i + 128, py = 256ll * j + 128;
-  bool in = true;
+// Rasterise every record of one (pose, tile) bin into the shared z-buffer. Records are staged
+// with one bulk copy per round; a block-wide scan of their clipped bounding-box pixel counts
+// lays all candidate fragments out in one index space, which is split evenly over the warps.
+// Each lane walks its fragments in record order (two-pointer over the scan), so no lane
+// idles on small triangles and no warp waits on large ones.
+template <int TW, int TH>
+__device__ __forceinline__ bool raster_tile(unsigned long long *zk, TriRec *stage, int *S,
+                                            int *wtot, unsigned long long *bar,
+                                            const TriRec *recs, int n, int ox, int oy, int xe,
+                                            int ye, float near_m, float far_m) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = kThreads / 32;
+  unsigned phase = 0;
+  for (int r0 = 0; r0 < n; r0 += kRecMax) {
+    const int cnt = min(kRecMax, n - r0);
+    if (tid == 0) {
+      fence_async_smem();
+      bulk_g2s(stage, recs + r0, (unsigned)(cnt * sizeof(TriRec)), bar);
+    }
+    bool ok = mbar_wait(bar, phase);
+    ok = __syncthreads_and(ok);
+    if (!ok) {
+      if (tid == 0) mbar_wait(bar, phase);
+      return false;
+    }
+    phase ^= 1u;
+    // pixel counts of records 2t and 2t+1, block-wide exclusive scan in record order
+    const int n0 = derive_rect(stage, 2 * tid, cnt, ox, oy, xe, ye);
+    const int n1 = derive_rect(stage, 2 * tid + 1, cnt, ox, oy, xe, ye);
+    int incl = n0 + n1;
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    long long E = e.dx[k] * (py - e.ya[k]) - e.dy[k] * (px - e.xa[k]);
-    in = in && (E + e.bias[k] >= 0);
+    for (int off = 1; off < 32; off <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += v;
+    }
+    if (lane == 31) wtot[warp] = incl;
+    __syncthreads();
+    int before = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) before += w < warp ? wtot[w] : 0;
+    int F = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) F += wtot[w];
+    const int ex = before + incl - (n0 + n1);
+    if (2 * tid < cnt) S[2 * tid] = ex;
+    if (2 * tid + 1 < cnt) S[2 * tid + 1] = ex + n0;
+    if (tid == 0) S[cnt] = F;
+    __syncthreads();
+    // this warp's share of the fragments
+    const int lo = (int)(((long long)F * warp) / NW), hi = (int)(((long long)F * (warp + 1)) / NW);
+    int f = lo + lane;
+    if (f < hi) {
+      int a = 0, b = cnt - 1;  // last record with S[r] <= f
+      while (a < b) {
+        const int m = (a + b + 1) >> 1;
+        if (S[m] <= f) a = m;
+        else b = m - 1;
+      }
+      int r = a;
+      for (; f < hi; f += 32) {
+        while (S[r + 1] <= f) ++r;
+        const TriRec &q = stage[r];
+        const int l = f - S[r];
+        const int bw = q.pad >> 16;
+        const int dj = __float2int_rz(__fmul_rn(__int2float_rn(l) + 0.5f, __frcp_rn(__int2float_rn(bw))));
+        const int i = ox + (q.pad & 0xff) + (l - dj * bw), j = oy + ((q.pad >> 8) & 0xff) + dj;
+        const int px = 256 * i + 128, py = 256 * j + 128;
+        if (edge_ok(q.x1 - q.x0, q.y1 - q.y0, q.x0, q.y0, px, py) &&
+            edge_ok(q.x2 - q.x1, q.y2 - q.y1, q.x1, q.y1, px, py) &&
+            edge_ok(q.x0 - q.x2, q.y0 - q.y2, q.x2, q.y2, px, py)) {
+          const float t = depth_pinhole(q.A, q.B, q.C, q.d, i, j);
+          if (t >= near_m && t <= far_m) atomicMin(&zk[(j - oy) * TW + (i - ox)], make_key(t, q.id));
+        }
+      }
+    }
+    __syncthreads();
   }
-  return in;
-}
-
-__device__ __forceinline__ void tri_rect(const TriRec &r, int ox, int oy, int xe, int ye,
-                                         int &i0, int &i1, int &j0, int &j1) {
-  int xmin = min(r.x0, min(r.x1, r.x2)), xmax = max(r.x0, max(r.x1, r.x2));
-  int ymin = min(r.y0, min(r.y1, r.y2)), ymax = max(r.y0, max(r.y1, r.y2));
-  i0 = max((xmin + 127) >> 8, ox);
-  i1 = min((xmax - 128) >> 8, xe);
-  j0 = max((ymin + 127) >> 8, oy);
-  j1 = min((ymax - 128) >> 8, ye);
-}
-
-template <int TW>
-__device__ __forceinline__ void deposit(unsigned long long *zk, const TriRec &r, int i, int j,
-                                        int ox, int oy, float near_m, float far_m) {
-  float t = depth_pinhole(r.A, r.B, r.C, r.d, i, j);
-  if (t >= near_m && t <= far_m) atomicMin(&zk[(j - oy) * TW + (i - ox)], make_key(t, r.id));
+  return true;
 }
 
 template <int TW, int TH, int MODE>
 __global__ void __launch_bounds__(kThreads) k_raster(WaveArgs a) {
   constexpr int NP = TW * TH;
+  constexpr int NW = kThreads / 32;
   __shared__ unsigned long long zk[NP];
-  __shared__ __align__(128) TriRec stage[2][kChunk];
-  __shared__ __align__(8) unsigned long long bar[2];
-  __shared__ int lq[kChunk];
-  __shared__ int lq_n;
-  __shared__ int s_abort;
-  __shared__ float red[kThreads / 32][28];
-  __shared__ int redc[kThreads / 32][6];
+  __shared__ __align__(128) TriRec stage[kRecMax];
+  __shared__ int S[kRecMax + 1];
+  __shared__ int wtot[NW];
+  __shared__ __align__(8) unsigned long long bar[1];
+  __shared__ float red[NW][28];
+  __shared__ int redc[NW][6];
 
   if (a.skip && *a.skip) return;
   const int tid = threadIdx.x;
@@ -295,74 +413,20 @@ __global__ void __launch_bounds__(kThreads) k_raster(WaveArgs a) {
   const int ox = (tile % a.tg.ntx) * TW, oy = (tile / a.tg.ntx) * TH;
   const int W = a.cam.W, H = a.cam.H;
   const int xe = min(ox + TW, W) - 1, ye = min(oy + TH, H) - 1;
-  const float near_m = a.cam.near_m, far_m = a.cam.far_m;
 
   for (int p = tid; p < NP; p += kThreads) zk[p] = kKeyEmpty;
   const long long bin = (long long)q * a.tg.ntiles + tile;
   const int n = min(a.counts[bin], a.tg.cap);
-  const TriRec *recs = a.bins + bin * a.tg.cap;
-  const int nchunks = (n + kChunk - 1) / kChunk;
   if (tid == 0) {
     mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
-    lq_n = 0;
-    s_abort = 0;
     fence_mbar_init();
   }
   __syncthreads();
-  if (tid == 0 && nchunks > 0) bulk_g2s(stage[0], recs, (unsigned)(min(kChunk, n) * sizeof(TriRec)), &bar[0]);
-
-  for (int c = 0; c < nchunks; ++c) {
-    const int buf = c & 1;
-    if (tid == 0 && c + 1 < nchunks) {
-      fence_async_smem();
-      bulk_g2s(stage[buf ^ 1], recs + (long long)(c + 1) * kChunk,
-               (unsigned)(min(kChunk, n - (c + 1) * kChunk) * sizeof(TriRec)), &bar[buf ^ 1]);
-    }
-    if (!mbar_wait(&bar[buf], (c >> 1) & 1)) s_abort = 1;
-    __syncthreads();
-    if (s_abort) {
-      if (tid == 0) {
-        atomicOr(a.status, kStatusTimeout);
-        if (c + 1 < nchunks) mbar_wait(&bar[buf ^ 1], ((c + 1) >> 1) & 1);
-      }
-      return;
-    }
-    const int cnt = min(kChunk, n - c * kChunk);
-    if (tid < cnt) {
-      const TriRec &r = stage[buf][tid];
-      int i0, i1, j0, j1;
-      tri_rect(r, ox, oy, xe, ye, i0, i1, j0, j1);
-      if (i0 <= i1 && j0 <= j1) {
-        if ((i1 - i0 + 1) * (j1 - j0 + 1) > kLargePixels) {
-          lq[atomicAdd(&lq_n, 1)] = tid;
-        } else {
-          EdgeSet e;
-          edge_setup(r, e);
-          for (int j = j0; j <= j1; ++j)
-            for (int i = i0; i <= i1; ++i)
-              if (covers(e, i, j)) deposit<TW>(zk, r, i, j, ox, oy, near_m, far_m);
-        }
-      }
-    }
-    __syncthreads();
-    const int nl = lq_n;
-    for (int k = 0; k < nl; ++k) {
-      const TriRec &r = stage[buf][lq[k]];
-      int i0, i1, j0, j1;
-      tri_rect(r, ox, oy, xe, ye, i0, i1, j0, j1);
-      const int bw = i1 - i0 + 1, npx = bw * (j1 - j0 + 1);
-      EdgeSet e;
-      edge_setup(r, e);
-      for (int p = tid; p < npx; p += kThreads) {
-        int i = i0 + p % bw, j = j0 + p / bw;
-        if (covers(e, i, j)) deposit<TW>(zk, r, i, j, ox, oy, near_m, far_m);
-      }
-    }
-    __syncthreads();
-    if (tid == 0) lq_n = 0;
+  if (!raster_tile<TW, TH>(zk, stage, S, wtot, bar, a.bins + bin * a.tg.cap, n, ox, oy, xe, ye,
+                           a.cam.near_m, a.cam.far_m)) {
+    if (tid == 0) atomicOr(a.status, kStatusTimeout);
+    return;
   }
-  __syncthreads();
 
   const long long P = (long long)W * H;
   if (MODE == kRender) {
@@ -386,8 +450,12 @@ __global__ void __launch_bounds__(kThreads) k_raster(WaveArgs a) {
       if (a.tri_id) a.tri_id[pix] = (int)id;
       if (a.bary) {
         const int4 f = a.faces[id];
-        const float4 *vc = a.vc + (long long)q * a.V;
-        const float4 v0 = vc[f.x], v1 = vc[f.y], v2 = vc[f.z];
+        const float *Mg = a.Ms + 12 * (long long)g;
+        float M[12];
+        for (int k = 0; k < 12; ++k) M[k] = Mg[k];
+        const float4 w0 = a.v[f.x], w1 = a.v[f.y], w2 = a.v[f.z];
+        const float3 v0 = xform(M, w0.x, w0.y, w0.z), v1 = xform(M, w1.x, w1.y, w1.z),
+                     v2 = xform(M, w2.x, w2.y, w2.z);
         const float rx = (i + 0.5f - a.cam.cx) / a.cam.fx, ry = (j + 0.5f - a.cam.cy) / a.cam.fy;
         const float hx = t * rx - v0.x, hy = t * ry - v0.y, hz = t - v0.z;
         const float e1x = v1.x - v0.x, e1y = v1.y - v0.y, e1z = v1.z - v0.z;
@@ -417,6 +485,7 @@ __global__ void __launch_bounds__(kThreads) k_raster(WaveArgs a) {
     R[3 * k + 2] = Mg[4 * k + 2];
   }
   const float eps = a.prm.eps;
+  const float ifx = 1.0f / a.cam.fx, ify = 1.0f / a.cam.fy;
   for (int p = tid; p < NP; p += kThreads) {
     const int i = ox + p % TW, j = oy + p / TW;
     if (i > xe || j > ye) continue;
@@ -454,11 +523,11 @@ __global__ void __launch_bounds__(kThreads) k_raster(WaveArgs a) {
     }
     acc[0] += 0.5f * w * r * r;
     if (MODE == kCostGrad && sgn != 0.0f) {
-      const float rx = (i + 0.5f - a.cam.cx) / a.cam.fx, ry = (j + 0.5f - a.cam.cy) / a.cam.fy;
+      const float rx = (i + 0.5f - a.cam.cx) * ifx, ry = (j + 0.5f - a.cam.cy) * ify;
       const float nx = R[0] * pl.x + R[1] * pl.y + R[2] * pl.z;
       const float ny = R[3] * pl.x + R[4] * pl.y + R[5] * pl.z;
       const float nz = R[6] * pl.x + R[7] * pl.y + R[8] * pl.z;
-      const float inv = 1.0f / (nx * rx + ny * ry + nz);
+      const float inv = __frcp_rn(nx * rx + ny * ry + nz);
       const float s = sgn * inv;
       float J[6];
       J[0] = -nx * s;
@@ -541,17 +610,19 @@ cudaError_t launch_wave(const WaveArgs &a, int mode, cudaStream_t s, cudaEvent_t
   cudaError_t e;
   e = cudaMemsetAsync(a.counts, 0, sizeof(int) * (size_t)a.tg.ntiles * a.n_poses, s);
   if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(a.vis_count, 0, sizeof(int) * (size_t)a.n_poses, s);
+  if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[0], s)) != cudaSuccess) return e;
-  if (a.V > 0) {
-    dim3 gv((a.V + 255) / 256, a.n_poses);
-    k_vertex_pinhole<<<gv, 256, 0, s>>>(a);
+  if (a.n_clusters > 0) {
+    dim3 gc((a.n_clusters + 255) / 256, a.n_poses);
+    k_cull<<<gc, 256, 0, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (ev && (e = cudaEventRecord(ev[1], s)) != cudaSuccess) return e;
-  if (a.T > 0) {
-    long long blocks = (a.T + 255) / 256;
-    dim3 gs((unsigned)(blocks < 65535 ? blocks : 65535), a.n_poses);
-    k_setup_pinhole<<<gs, 256, 0, s>>>(a);
+  if (a.n_clusters > 0) {
+    const int blocks = min(max(a.n_clusters / 64, 1), 96);
+    dim3 gs(blocks, a.n_poses);
+    k_setup<<<gs, 256, 0, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (ev && (e = cudaEventRecord(ev[2], s)) != cudaSuccess) return e;
@@ -569,7 +640,7 @@ cudaError_t launch_wave(const WaveArgs &a, int mode, cudaStream_t s, cudaEvent_t
 }
 
 int wave_kernel_launches(const WaveArgs &a, int mode) {
-  return (a.V > 0) + (a.T > 0) + 1 + (mode != kRender);
+  return 2 * (a.n_clusters > 0) + 1 + (mode != kRender);
 }
 
 // ------------------------------------------------------------------ Levenberg-Marquardt

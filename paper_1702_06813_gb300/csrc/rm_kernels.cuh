@@ -24,8 +24,15 @@ struct WaveArgs {
   const int4 *faces;  // i0, i1, i2, label
   const float4 *planes;  // unit world normal, label bits in w
   const float *Ms;    // 12 floats per global pose (world -> camera, FP32)
-  float4 *vc;         // wave: V camera-space vertices per pose
-  int2 *vs;           // wave: V snapped vertices per pose (pinhole)
+  // clusters of <= 64 triangles over <= 64 vertices, built at map creation
+  int n_clusters;
+  const int4 *cl_info;     // vertex offset, triangle offset, vertex count, triangle count
+  const float4 *cl_sphere; // bounding sphere (re-centred frame)
+  const int *cl_verts;     // global vertex index per cluster vertex
+  const uchar4 *cl_tris;   // local vertex indices per cluster triangle
+  const int *cl_ids;       // original face id per cluster triangle
+  int *vis;           // wave: visible cluster ids per pose (n_clusters each)
+  int *vis_count;     // wave: one counter per pose
   int *counts;        // wave: ntiles per pose
   TriRec *bins;       // wave: ntiles * cap per pose
   double *partial;    // wave: ntiles * kNumVals per pose
@@ -51,7 +58,7 @@ enum Mode { kRender = 0, kCost = 1, kCostGrad = 2 };
 
 cudaError_t launch_pose_to_m(const double *poses, int n, double cx, double cy, double cz,
                              float *Ms, cudaStream_t s);
-// ev (optional, 5 events): recorded before the vertex kernel, then after the vertex, setup,
+// ev (optional, 5 events): recorded before the cull kernel, then after the cull, setup,
 // raster and reduce kernels, on stream s.
 cudaError_t launch_wave(const WaveArgs &a, int mode, cudaStream_t s, cudaEvent_t *ev = nullptr);
 int wave_kernel_launches(const WaveArgs &a, int mode);
