@@ -164,9 +164,12 @@ def zbuffer(vc, faces, cam, brute=False, frags=False):
 
 
 def decode(keys):
-    """(depth float32 with NaN, tri id int32 with -1) from a key image."""
+    """(depth float32 with NaN, tri id int32 with -1) from a key image: the key's high word is
+    the bitwise complement of the FP32 inverse depth w, and depth = 1 / w rounded to FP32."""
     empty = keys == KEY_EMPTY
-    depth = (keys >> np.uint64(32)).astype(np.uint32).view(np.float32).copy()
+    w = (~(keys >> np.uint64(32)).astype(np.uint32)).view(np.float32)
+    with np.errstate(divide="ignore"):
+        depth = np.float32(1.0) / w
     depth[empty] = np.nan
     ids = (keys & np.uint64(0xFFFFFFFF)).astype(np.int64).astype(np.int32)
     ids[empty] = -1

@@ -79,7 +79,10 @@ void orc_transform(const float M[12], const float *v, int64_t V, float *vc) {
 /* the z-buffer (Sec. III.A render; depth buffer as in Sec. III)                          */
 /* ------------------------------------------------------------------------------------- */
 
-typedef struct { float nx, ny, nz, d, A, B, C; } plane32;
+/* Camera-space plane n . p = d of a triangle, and its inverse depth w = 1/t folded per pixel:
+ * pinhole w(px, py) = Ai px + Bi py + Ci (affine in the image, as a GPU z-buffer value is, Sec.
+ * IV), ray table w(r) = ni . r. */
+typedef struct { float nx, ny, nz, d, Ai, Bi, Ci, nix, niy, niz; } plane32;
 
 /* Camera-space plane of a triangle from its stored vertex order. */
 static void plane_of(const float *a, const float *b, const float *c, const orc_cam *cam,
@@ -91,38 +94,53 @@ static void plane_of(const float *a, const float *b, const float *c, const orc_c
   p->nz = fmaf(e1x, e2y, -(e1y * e2x));
   p->d = fmaf(p->nx, a[0], fmaf(p->ny, a[1], p->nz * a[2]));
   if (cam->model == 0) {
-    p->A = p->nx / cam->fx;
-    p->B = p->ny / cam->fy;
-    p->C = fmaf(-p->A, cam->cx, fmaf(-p->B, cam->cy, p->nz));
+    float A = p->nx / cam->fx;
+    float B = p->ny / cam->fy;
+    float C = fmaf(-A, cam->cx, fmaf(-B, cam->cy, p->nz));
+    p->Ai = A / p->d;
+    p->Bi = B / p->d;
+    p->Ci = C / p->d;
+    p->nix = p->niy = p->niz = 0.0f;
   } else {
-    p->A = p->B = p->C = 0.0f;
+    p->nix = p->nx / p->d;
+    p->niy = p->ny / p->d;
+    p->niz = p->nz / p->d;
+    p->Ai = p->Bi = p->Ci = 0.0f;
   }
 }
 
-static float depth_at(const plane32 *p, const orc_cam *cam, int i, int j) {
-  float den;
+static float inv_depth_at(const plane32 *p, const orc_cam *cam, int i, int j) {
   if (cam->model == 0) {
     float px = (float)i + 0.5f, py = (float)j + 0.5f;
-    den = fmaf(p->A, px, fmaf(p->B, py, p->C));
-  } else {
-    const float *r = cam->rays + 3 * ((int64_t)j * cam->width + i);
-    den = fmaf(p->nx, r[0], fmaf(p->ny, r[1], p->nz * r[2]));
+    return fmaf(p->Ai, px, fmaf(p->Bi, py, p->Ci));
   }
-  return p->d / den;
+  const float *r = cam->rays + 3 * ((int64_t)j * cam->width + i);
+  return fmaf(p->nix, r[0], fmaf(p->niy, r[1], p->niz * r[2]));
 }
 
+/* Keep a fragment iff its inverse depth lies in (0, 1/near] and >= 1/far (FP32 bounds); the
+ * key orders by decreasing inverse depth (nearest first), then by triangle id. */
 static void deposit(const plane32 *pl, const orc_cam *cam, int i, int j, uint32_t id,
                     uint64_t *keys, int32_t *frags, orc_stats *st) {
   int64_t pix = (int64_t)j * cam->width + i;
   if (frags) frags[pix] += 1;
   st->n_fragments += 1;
-  float t = depth_at(pl, cam, i, j);
-  if (t >= cam->near_m && t <= cam->far_m) {
+  float w = inv_depth_at(pl, cam, i, j);
+  float w_near = 1.0f / cam->near_m, w_far = 1.0f / cam->far_m;
+  if (w > 0.0f && w >= w_far && w <= w_near) {
     uint32_t bits;
-    memcpy(&bits, &t, 4);
-    uint64_t key = ((uint64_t)bits << 32) | (uint64_t)id;
+    memcpy(&bits, &w, 4);
+    uint64_t key = ((uint64_t)(~bits) << 32) | (uint64_t)id;
     if (key < keys[pix]) keys[pix] = key;
   }
+}
+
+/* Depth of a z-buffer key: t = 1 / w, rounded to FP32. */
+static float key_depth(uint64_t key) {
+  uint32_t bits = ~(uint32_t)(key >> 32);
+  float w;
+  memcpy(&w, &bits, 4);
+  return 1.0f / w;
 }
 
 /* Pinhole: project and snap to 1/256 pixel, round half to even. */
@@ -578,11 +596,7 @@ int orc_cost(const float *v, const float *vr, int64_t V, const double centre[3],
       uint64_t key = keys[p];
       int mc = key == KEY_EMPTY ? 3 : (int)labels[key & 0xFFFFFFFFu];
       int sc = scan_class_of(scan_depth, scan_class, p);
-      float t32 = 0.0f;
-      if (key != KEY_EMPTY) {
-        uint32_t bits = (uint32_t)(key >> 32);
-        memcpy(&t32, &bits, 4);
-      }
+      float t32 = key != KEY_EMPTY ? key_depth(key) : 0.0f;
       float dz32 = t32 - scan_depth[p];
       int oc = (mc == 3 || sc == 2) ? -1 : orc_table1(mc, sc, dz32, prm->eps);
       if (outcome) outcome[p] = (int8_t)oc;
@@ -680,9 +694,7 @@ double orc_cost_frozen(const float *v, const float *vr, int64_t V, const double 
       int mc = (int)labels[key & 0xFFFFFFFFu];
       int sc = scan_class_of(scan_depth, scan_class, p);
       if (sc == 2) continue;
-      float t32;
-      uint32_t bits = (uint32_t)(key >> 32);
-      memcpy(&t32, &bits, 4);
+      float t32 = key_depth(key);
       float dz32 = t32 - scan_depth[p];
       int oc = orc_table1(mc, sc, dz32, prm->eps);
       if (oc < 0) continue;

@@ -49,8 +49,8 @@ void orc_pose_matrix(const double Twc[16], const double centre[3], float M[12]);
 /* Camera-space FP32 vertices: vc = M * [v;1] in the contract's operation order. */
 void orc_transform(const float M[12], const float *v, int64_t V, float *vc);
 
-/* Z-buffer of camera-space geometry. keys: H*W uint64 (bits(depth)<<32 | tri id),
- * 0xFFFF..FF where nothing is hit. frags (optional): per-pixel count of covering triangles
+/* Z-buffer of camera-space geometry. keys: H*W uint64 (~bits(w) << 32 | tri id) with w the
+ * FP32 inverse depth (depth = 1/w), 0xFFFF..FF where nothing is hit. frags (optional): per-pixel count of covering triangles
  * before the depth test. brute != 0 tests every pixel against every triangle. */
 int orc_zbuffer(const float *vc, const int32_t *faces, int64_t T, const orc_cam *cam,
                 uint64_t *keys, int32_t *frags, int brute, orc_stats *st);

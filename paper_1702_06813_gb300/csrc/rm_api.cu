@@ -268,6 +268,8 @@ DevCam make_cam(const rm_intrinsics *in, const float *d_rays) {
   c.el_step = in->el_step;
   c.near_m = in->near_m;
   c.far_m = in->far_m;
+  c.w_near = 1.0f / in->near_m;  // FP32 division, round to nearest (host and oracle alike)
+  c.w_far = 1.0f / in->far_m;
   c.rays = d_rays;
   return c;
 }

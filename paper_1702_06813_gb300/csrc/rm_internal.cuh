@@ -7,9 +7,12 @@
 //   project:  xs = fma(fx, X / Z, cx); xi = rint(xs * 256)           (8 sub-pixel bits)
 //   near cut: s = (near - a.z) / (b.z - a.z), a = lower vertex index; P = a + s (b - a)
 //   plane:    n = (v1 - v0) x (v2 - v0), d = n . v0 (camera frame, stored vertex order)
-//   depth:    pinhole  t = d / fma(A, i + .5, fma(B, j + .5, C)), A = nx/fx, B = ny/fy,
-//                      C = fma(-A, cx, fma(-B, cy, nz));  ray table t = d / (n . r)
-//   key:      (bits(t) << 32) | triangle id, kept iff near <= t <= far, minimum wins.
+//   inverse depth (affine in the image, like a GPU z-buffer value, Sec. IV):
+//             pinhole  w = fma(Ai, i + .5, fma(Bi, j + .5, Ci)), Ai = A / d, Bi = B / d,
+//                      Ci = C / d with A = nx/fx, B = ny/fy, C = fma(-A, cx, fma(-B, cy, nz));
+//             ray table w = fma(nx/d, rx, fma(ny/d, ry, (nz/d) rz))
+//   key:      (~bits(w) << 32) | triangle id, kept iff 0 < w, 1/far <= w <= 1/near (FP32
+//             bounds), minimum key wins (nearest, then lowest id); depth t = 1 / w.
 // Coverage is decided on the snapped integer coordinates with int64 edge functions and
 // the top-left rule, so it is exact.
 #pragma once
@@ -32,6 +35,7 @@ struct DevCam {
   float fx, fy, cx, cy;
   float az0, az_step, el0, el_step;
   float near_m, far_m;
+  float w_near, w_far;  // 1/near_m and 1/far_m rounded to FP32
   const float *rays;  // ray-table model: device H*W*3
 };
 
@@ -45,9 +49,9 @@ struct TileGeom {
 // One snapped triangle (or near-clipped piece) in a screen-tile bin, 48 bytes.
 struct __align__(16) TriRec {
   int x0, y0, x1, y1, x2, y2;  // 1/256 px, winding normalised so the doubled area is > 0
-  float A, B, C, d;            // depth plane, see the contract above
+  float Ai, Bi, Ci;            // inverse-depth plane, see the contract above
   unsigned id;                 // parent triangle id
-  int pad;
+  int spare, pad;
 };
 static_assert(sizeof(TriRec) == 48, "record layout");
 
@@ -85,19 +89,25 @@ __device__ __forceinline__ PlaneN plane_n(float3 a, float3 b, float3 c) {
   return p;
 }
 
-// Pinhole depth plane folded into pixel coordinates.
-__device__ __forceinline__ void fold_pinhole(const DevCam &c, const PlaneN &p, float &A,
-                                             float &B, float &C) {
-  A = __fdiv_rn(p.nx, c.fx);
-  B = __fdiv_rn(p.ny, c.fy);
-  C = __fmaf_rn(-A, c.cx, __fmaf_rn(-B, c.cy, p.nz));
+// Pinhole inverse-depth plane folded into pixel coordinates.
+__device__ __forceinline__ void fold_pinhole(const DevCam &c, const PlaneN &p, float &Ai,
+                                             float &Bi, float &Ci) {
+  const float A = __fdiv_rn(p.nx, c.fx);
+  const float B = __fdiv_rn(p.ny, c.fy);
+  const float C = __fmaf_rn(-A, c.cx, __fmaf_rn(-B, c.cy, p.nz));
+  Ai = __fdiv_rn(A, p.d);
+  Bi = __fdiv_rn(B, p.d);
+  Ci = __fdiv_rn(C, p.d);
 }
 
-__device__ __forceinline__ float depth_pinhole(float A, float B, float C, float d, int i,
-                                               int j) {
-  float px = __fadd_rn(__int2float_rn(i), 0.5f);
-  float py = __fadd_rn(__int2float_rn(j), 0.5f);
-  return __fdiv_rn(d, __fmaf_rn(A, px, __fmaf_rn(B, py, C)));
+__device__ __forceinline__ float inv_depth_pinhole(float Ai, float Bi, float Ci, int i, int j) {
+  const float px = __fadd_rn(__int2float_rn(i), 0.5f);
+  const float py = __fadd_rn(__int2float_rn(j), 0.5f);
+  return __fmaf_rn(Ai, px, __fmaf_rn(Bi, py, Ci));
+}
+
+__device__ __forceinline__ bool keep_w(const DevCam &c, float w) {
+  return w > 0.0f && w >= c.w_far && w <= c.w_near;
 }
 
 __device__ __forceinline__ float3 near_cut(float3 a, float3 b, float near_m) {
@@ -106,8 +116,13 @@ __device__ __forceinline__ float3 near_cut(float3 a, float3 b, float near_m) {
                      near_m);
 }
 
-__device__ __forceinline__ unsigned long long make_key(float t, unsigned id) {
-  return ((unsigned long long)__float_as_uint(t) << 32) | (unsigned long long)id;
+__device__ __forceinline__ unsigned long long make_key(float w, unsigned id) {
+  return ((unsigned long long)(~__float_as_uint(w)) << 32) | (unsigned long long)id;
+}
+
+// Depth of a z-buffer key: t = 1 / w rounded to FP32.
+__device__ __forceinline__ float key_depth(unsigned long long key) {
+  return __frcp_rn(__uint_as_float(~(unsigned)(key >> 32)));
 }
 
 }  // namespace rmk

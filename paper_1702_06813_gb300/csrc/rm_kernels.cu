@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(256) k_cull(WaveArgs a) {
 // ------------------------------------------------------------------ triangle setup + binning
 
 __device__ __forceinline__ void emit_piece(int x0, int y0, int x1, int y1, int x2, int y2,
-                                           float A, float B, float C, float d, unsigned id,
+                                           float Ai, float Bi, float Ci, unsigned id,
                                            const WaveArgs &a, int *counts, TriRec *bins) {
   long long area = (long long)(x1 - x0) * (y2 - y0) - (long long)(y1 - y0) * (x2 - x0);
   if (area == 0) return;
@@ -173,8 +173,8 @@ __device__ __forceinline__ void emit_piece(int x0, int y0, int x1, int y1, int x
   const TileGeom &tg = a.tg;
   int tx0 = i0 / tg.tw, tx1 = i1 / tg.tw, ty0 = j0 / tg.th, ty1 = j1 / tg.th;
   int4 w0 = make_int4(x0, y0, x1, y1);
-  int4 w1 = make_int4(x2, y2, __float_as_int(A), __float_as_int(B));
-  int4 w2 = make_int4(__float_as_int(C), __float_as_int(d), (int)id, 0);
+  int4 w1 = make_int4(x2, y2, __float_as_int(Ai), __float_as_int(Bi));
+  int4 w2 = make_int4(__float_as_int(Ci), (int)id, 0, 0);
   for (int ty = ty0; ty <= ty1; ++ty)
     for (int tx = tx0; tx <= tx1; ++tx) {
       int tile = ty * tg.ntx + tx;
@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(256) k_setup(WaveArgs a) {
                                   make_float3(p2.x, p2.y, p2.z));
         float A, B, C;
         fold_pinhole(a.cam, pl, A, B, C);
-        emit_piece(s0.x, s0.y, s1.x, s1.y, s2.x, s2.y, A, B, C, pl.d, id, a, counts, bins);
+        emit_piece(s0.x, s0.y, s1.x, s1.y, s2.x, s2.y, A, B, C, id, a, counts, bins);
         continue;
       }
       // slow path: near-plane cut and/or guard band
@@ -277,9 +277,9 @@ __global__ void __launch_bounds__(256) k_setup(WaveArgs a) {
       bool ok = true;
       for (int m = 0; m < n; ++m) ok = ok && snap(a.cam, poly[m].x, poly[m].y, poly[m].z, sx[m], sy[m]);
       if (!ok) continue;
-      emit_piece(sx[0], sy[0], sx[1], sy[1], sx[2], sy[2], A, B, C, pl.d, id, a, counts, bins);
+      emit_piece(sx[0], sy[0], sx[1], sy[1], sx[2], sy[2], A, B, C, id, a, counts, bins);
       if (n == 4)
-        emit_piece(sx[0], sy[0], sx[2], sy[2], sx[3], sy[3], A, B, C, pl.d, id, a, counts, bins);
+        emit_piece(sx[0], sy[0], sx[2], sy[2], sx[3], sy[3], A, B, C, id, a, counts, bins);
     }
     __syncwarp();
   }
@@ -289,42 +289,72 @@ __global__ void __launch_bounds__(256) k_setup(WaveArgs a) {
 
 constexpr int kRecMax = 512;  // bin records staged in shared memory per round
 
-// Exact edge test with int32 operands and 64-bit products: E = dx (py - ya) - dy (px - xa).
+// Exact edge test with int32 operands and 64-bit products: E = dx (py - ya) - dy (px - xa),
+// covered iff E > 0 or E == 0 on a top or left edge.
 __device__ __forceinline__ bool edge_ok(int dx, int dy, int xa, int ya, int px, int py) {
   const long long E = (long long)dx * (py - ya) - (long long)dy * (px - xa);
   const bool top_left = dy < 0 || (dy == 0 && dx > 0);
   return E > 0 || (E == 0 && top_left);
 }
 
-// Clips record k's sample bounding box to the tile, stores it (tile-relative origin and
-// width) in the record's spare word and returns its pixel count.
-__device__ __forceinline__ int derive_rect(TriRec *rec, int k, int cnt, int ox, int oy, int xe,
-                                           int ye) {
+constexpr int kRecFallback = 1 << 24;  // record keeps its snapped vertices (int64 edge tests)
+
+// Per-record raster setup for one tile: clip the sample bounding box to the tile and turn
+// each edge function into an exact int32 affine function of the pixel offset (di, dj) inside
+// that rectangle, E = E0 + di*sx + dj*sy with the top-left bias folded into E0. Edges that
+// hold on the whole rectangle become E = 0; a record whose rectangle misses one edge's half
+// plane is dropped. Long edges whose range over the rectangle could leave int32 keep the
+// record's vertices for the int64 test. Returns the rectangle's pixel count (0 = nothing).
+__device__ __forceinline__ int derive_rect(TriRec *rec, int4 *hdr, int k, int cnt, int ox,
+                                           int oy, int xe, int ye) {
   if (k >= cnt) return 0;
   TriRec &r = rec[k];
   const int xmin = min(r.x0, min(r.x1, r.x2)), xmax = max(r.x0, max(r.x1, r.x2));
   const int ymin = min(r.y0, min(r.y1, r.y2)), ymax = max(r.y0, max(r.y1, r.y2));
   const int i0 = max((xmin + 127) >> 8, ox), i1 = min((xmax - 128) >> 8, xe);
   const int j0 = max((ymin + 127) >> 8, oy), j1 = min((ymax - 128) >> 8, ye);
-  if (i0 > i1 || j0 > j1) {
-    r.pad = 0;
-    return 0;
+  if (i0 > i1 || j0 > j1) return 0;
+  const int bw = i1 - i0 + 1, bh = j1 - j0 + 1;
+  const int xs[3] = {r.x0, r.x1, r.x2}, ys[3] = {r.y0, r.y1, r.y2};
+  const int px0 = 256 * i0 + 128, py0 = 256 * j0 + 128;
+  int e0[3], sx[3], sy[3];
+  bool fallback = false;
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    const int nb = e == 2 ? 0 : e + 1;
+    const int dx = xs[nb] - xs[e], dy = ys[nb] - ys[e];
+    const bool top_left = dy < 0 || (dy == 0 && dx > 0);
+    const long long E0 = (long long)dx * (py0 - ys[e]) - (long long)dy * (px0 - xs[e]) + (top_left ? 0 : -1);
+    const long long ax = -256ll * dy * (bw - 1), ay = 256ll * dx * (bh - 1);
+    const long long lo = E0 + min(ax, 0ll) + min(ay, 0ll), hi = E0 + max(ax, 0ll) + max(ay, 0ll);
+    if (hi < 0) return 0;              // no pixel of the rectangle is on the inner side
+    if (lo >= 0) {                     // the whole rectangle is on the inner side
+      e0[e] = 0; sx[e] = 0; sy[e] = 0;
+    } else if (abs(dx) + abs(dy) <= (1 << 18)) {
+      e0[e] = (int)E0; sx[e] = -256 * dy; sy[e] = 256 * dx;
+    } else {
+      fallback = true;
+      e0[e] = 0; sx[e] = 0; sy[e] = 0;
+    }
   }
-  const int bw = i1 - i0 + 1;
-  r.pad = (i0 - ox) | ((j0 - oy) << 8) | (bw << 16);
-  return bw * (j1 - j0 + 1);
+  hdr[k] = make_int4(e0[0], e0[1], e0[2], __float_as_int(__frcp_rn(__int2float_rn(bw))));
+  if (!fallback) {
+    r.x0 = sx[0]; r.y0 = sy[0]; r.x1 = sx[1]; r.y1 = sy[1]; r.x2 = sx[2]; r.y2 = sy[2];
+  }
+  r.pad = (i0 - ox) | ((j0 - oy) << 8) | (bw << 16) | (fallback ? kRecFallback : 0);
+  return bw * bh;
 }
 
 // Rasterise every record of one (pose, tile) bin into the shared z-buffer. Records are staged
-// with one bulk copy per round; a block-wide scan of their clipped bounding-box pixel counts
-// lays all candidate fragments out in one index space, which is split evenly over the warps.
-// Each lane walks its fragments in record order (two-pointer over the scan), so no lane
-// idles on small triangles and no warp waits on large ones.
+// with one bulk copy per round; a block-wide scan of their per-tile rectangle sizes lays all
+// candidate fragments out in one index space, which is split evenly over the warps. Each lane
+// walks its fragments in record order (two-pointer over the scan), so no lane idles on small
+// triangles and no warp waits on large ones.
 template <int TW, int TH>
-__device__ __forceinline__ bool raster_tile(unsigned long long *zk, TriRec *stage, int *S,
-                                            int *wtot, unsigned long long *bar,
+__device__ __forceinline__ bool raster_tile(unsigned long long *zk, TriRec *stage, int4 *hdr,
+                                            int *S, int *wtot, unsigned long long *bar,
                                             const TriRec *recs, int n, int ox, int oy, int xe,
-                                            int ye, float near_m, float far_m) {
+                                            int ye, const DevCam &cam) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int NW = kThreads / 32;
   unsigned phase = 0;
@@ -341,9 +371,9 @@ __device__ __forceinline__ bool raster_tile(unsigned long long *zk, TriRec *stag
       return false;
     }
     phase ^= 1u;
-    // pixel counts of records 2t and 2t+1, block-wide exclusive scan in record order
-    const int n0 = derive_rect(stage, 2 * tid, cnt, ox, oy, xe, ye);
-    const int n1 = derive_rect(stage, 2 * tid + 1, cnt, ox, oy, xe, ye);
+    // rectangle sizes of records 2t and 2t+1, block-wide exclusive scan in record order
+    const int n0 = derive_rect(stage, hdr, 2 * tid, cnt, ox, oy, xe, ye);
+    const int n1 = derive_rect(stage, hdr, 2 * tid + 1, cnt, ox, oy, xe, ye);
     int incl = n0 + n1;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
@@ -352,18 +382,17 @@ __device__ __forceinline__ bool raster_tile(unsigned long long *zk, TriRec *stag
     }
     if (lane == 31) wtot[warp] = incl;
     __syncthreads();
-    int before = 0;
+    int before = 0, F = 0;
 #pragma unroll
-    for (int w = 0; w < NW; ++w) before += w < warp ? wtot[w] : 0;
-    int F = 0;
-#pragma unroll
-    for (int w = 0; w < NW; ++w) F += wtot[w];
+    for (int w = 0; w < NW; ++w) {
+      before += w < warp ? wtot[w] : 0;
+      F += wtot[w];
+    }
     const int ex = before + incl - (n0 + n1);
     if (2 * tid < cnt) S[2 * tid] = ex;
     if (2 * tid + 1 < cnt) S[2 * tid + 1] = ex + n0;
     if (tid == 0) S[cnt] = F;
     __syncthreads();
-    // this warp's share of the fragments
     const int lo = (int)(((long long)F * warp) / NW), hi = (int)(((long long)F * (warp + 1)) / NW);
     int f = lo + lane;
     if (f < hi) {
@@ -373,20 +402,33 @@ __device__ __forceinline__ bool raster_tile(unsigned long long *zk, TriRec *stag
         if (S[m] <= f) a = m;
         else b = m - 1;
       }
-      int r = a;
+      int r = a, sr = S[a], snext = S[a + 1];
       for (; f < hi; f += 32) {
-        while (S[r + 1] <= f) ++r;
+        while (snext <= f) {
+          ++r;
+          sr = snext;
+          snext = S[r + 1];
+        }
         const TriRec &q = stage[r];
-        const int l = f - S[r];
-        const int bw = q.pad >> 16;
-        const int dj = __float2int_rz(__fmul_rn(__int2float_rn(l) + 0.5f, __frcp_rn(__int2float_rn(bw))));
-        const int i = ox + (q.pad & 0xff) + (l - dj * bw), j = oy + ((q.pad >> 8) & 0xff) + dj;
-        const int px = 256 * i + 128, py = 256 * j + 128;
-        if (edge_ok(q.x1 - q.x0, q.y1 - q.y0, q.x0, q.y0, px, py) &&
-            edge_ok(q.x2 - q.x1, q.y2 - q.y1, q.x1, q.y1, px, py) &&
-            edge_ok(q.x0 - q.x2, q.y0 - q.y2, q.x2, q.y2, px, py)) {
-          const float t = depth_pinhole(q.A, q.B, q.C, q.d, i, j);
-          if (t >= near_m && t <= far_m) atomicMin(&zk[(j - oy) * TW + (i - ox)], make_key(t, q.id));
+        const int4 h = hdr[r];
+        const int l = f - sr;
+        const int bw = (q.pad >> 16) & 0xff;
+        const int dj = __float2int_rz(__fmul_rn(__int2float_rn(l) + 0.5f, __int_as_float(h.w)));
+        const int di = l - dj * bw;
+        const int i = ox + (q.pad & 0xff) + di, j = oy + ((q.pad >> 8) & 0xff) + dj;
+        bool in;
+        if (!(q.pad & kRecFallback)) {
+          in = (h.x + di * q.x0 + dj * q.y0 >= 0) & (h.y + di * q.x1 + dj * q.y1 >= 0) &
+               (h.z + di * q.x2 + dj * q.y2 >= 0);
+        } else {
+          const int px = 256 * i + 128, py = 256 * j + 128;
+          in = edge_ok(q.x1 - q.x0, q.y1 - q.y0, q.x0, q.y0, px, py) &&
+               edge_ok(q.x2 - q.x1, q.y2 - q.y1, q.x1, q.y1, px, py) &&
+               edge_ok(q.x0 - q.x2, q.y0 - q.y2, q.x2, q.y2, px, py);
+        }
+        if (in) {
+          const float w = inv_depth_pinhole(q.Ai, q.Bi, q.Ci, i, j);
+          if (keep_w(cam, w)) atomicMin(&zk[(j - oy) * TW + (i - ox)], make_key(w, q.id));
         }
       }
     }
@@ -401,6 +443,7 @@ __global__ void __launch_bounds__(kThreads) k_raster(WaveArgs a) {
   constexpr int NW = kThreads / 32;
   __shared__ unsigned long long zk[NP];
   __shared__ __align__(128) TriRec stage[kRecMax];
+  __shared__ int4 hdr[kRecMax];
   __shared__ int S[kRecMax + 1];
   __shared__ int wtot[NW];
   __shared__ __align__(8) unsigned long long bar[1];
@@ -422,8 +465,8 @@ __global__ void __launch_bounds__(kThreads) k_raster(WaveArgs a) {
     fence_mbar_init();
   }
   __syncthreads();
-  if (!raster_tile<TW, TH>(zk, stage, S, wtot, bar, a.bins + bin * a.tg.cap, n, ox, oy, xe, ye,
-                           a.cam.near_m, a.cam.far_m)) {
+  if (!raster_tile<TW, TH>(zk, stage, hdr, S, wtot, bar, a.bins + bin * a.tg.cap, n, ox, oy, xe,
+                           ye, a.cam)) {
     if (tid == 0) atomicOr(a.status, kStatusTimeout);
     return;
   }
@@ -445,7 +488,7 @@ __global__ void __launch_bounds__(kThreads) k_raster(WaveArgs a) {
         continue;
       }
       const unsigned id = (unsigned)key;
-      const float t = __uint_as_float((unsigned)(key >> 32));
+      const float t = key_depth(key);
       a.depth[pix] = t;
       if (a.tri_id) a.tri_id[pix] = (int)id;
       if (a.bary) {
@@ -496,7 +539,7 @@ __global__ void __launch_bounds__(kThreads) k_raster(WaveArgs a) {
     const int sc = a.scan_cls[pix];
     if (sc > 1 || !(fabsf(sd) <= FLT_MAX)) continue;  // scan NaN column: ignore
     const unsigned id = (unsigned)key;
-    const float t = __uint_as_float((unsigned)(key >> 32));
+    const float t = key_depth(key);
     const float4 pl = a.planes[id];
     const int mc = __float_as_int(pl.w);
     if (mc > 1) continue;  // unknown-occupied row: ignore
