@@ -1,0 +1,69 @@
+"""Autotuner for the screen-tile size and the number of poses per kernel wave.
+
+For one (map, camera, batch size) it times rm_cost_grad over each candidate with CUDA events
+on the current stream and keeps the fastest, caching the choice in a JSON file keyed by image
+size, triangle count and batch size. The bin capacity needs no search: the library grows it
+when a bin overflows and keeps the grown value on the map.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+import torch
+
+from . import rendermap as rm
+
+TILES = ((32, 32), (32, 16), (16, 16))
+WAVES = (16, 32, 64, 128)
+DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "rendermap_autotune.json")
+
+
+def _key(m, intr, n):
+    return f"{intr.width}x{intr.height}-model{intr.model}-T{m.n_faces}-N{n}"
+
+
+def _time(m, scan, poses, params, reps):
+    s = torch.cuda.current_stream()
+    rm.cost_grad(m, scan, poses, params)  # warm, and grow the bins if needed
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(reps):
+        rm.cost_grad(m, scan, poses, params)
+    e1.record(s)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def autotune(m: rm.Map, scan: rm.Scan, poses, params=None, tiles=TILES, waves=WAVES, reps=3,
+             cache: str | None = DEFAULT_CACHE, force: bool = False) -> dict:
+    """Pick and apply the fastest (tile, wave_poses); returns {"tile", "wave_poses", "ms"}."""
+    poses = torch.as_tensor(poses, dtype=torch.float64, device="cuda").reshape(-1, 16)
+    n = poses.shape[0]
+    key = _key(m, scan.intr, n)
+    table = {}
+    if cache and os.path.exists(cache):
+        try:
+            with open(cache) as fh:
+                table = json.load(fh)
+        except (OSError, ValueError):
+            table = {}
+    if key in table and not force:
+        best = table[key]
+        m.set_tuning(tile=tuple(best["tile"]), wave_poses=best["wave_poses"])
+        return best
+    results = []
+    for tile in tiles:
+        for wave in [w for w in waves if w <= max(n, waves[0])]:
+            m.set_tuning(tile=tile, wave_poses=wave)
+            results.append({"tile": list(tile), "wave_poses": wave, "ms": _time(m, scan, poses, params, reps)})
+    best = min(results, key=lambda r: r["ms"])
+    m.set_tuning(tile=tuple(best["tile"]), wave_poses=best["wave_poses"])
+    if cache:
+        table[key] = best
+        os.makedirs(os.path.dirname(cache), exist_ok=True)
+        tmp = cache + f".{os.getpid()}"
+        with open(tmp, "w") as fh:
+            json.dump(table, fh, indent=1)
+        os.replace(tmp, cache)
+    return dict(best, candidates=results)

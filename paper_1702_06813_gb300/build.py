@@ -32,16 +32,20 @@ def _stale(target: str, deps: list[str]) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
-    """Compile every translation unit in parallel and link the shared library."""
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None,
+          out_dir: str | None = None) -> str:
+    """Compile every translation unit in parallel and link the shared library (into
+    out_dir/librendermap.so when given, e.g. for a build with other -D knobs)."""
+    build_dir = out_dir or BUILD
+    lib = os.path.join(build_dir, "librendermap.so")
+    os.makedirs(build_dir, exist_ok=True)
     nvcc = _nvcc()
     hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(ROOT, "include", "rendermap.h")]
     objs = []
     jobs = []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src.replace(".cu", ".o"))
+        o = os.path.join(build_dir, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _stale(o, [s] + hdrs):
             cmd = [nvcc, *ARCH, *FLAGS, *(extra or []), "-c", s, "-o", o]
@@ -54,15 +58,15 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
                     print(res.stdout + res.stderr)
                 if res.returncode != 0:
                     raise RuntimeError(f"nvcc failed for {cmd[-3]}")
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + f".{os.getpid()}.tmp"
+    if force or jobs or _stale(lib, objs):
+        tmp = lib + f".{os.getpid()}.tmp"
         res = subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"],
                              capture_output=True, text=True)
         if res.returncode != 0:
             print(res.stdout + res.stderr)
             raise RuntimeError("link of librendermap.so failed")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

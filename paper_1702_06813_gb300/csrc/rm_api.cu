@@ -276,10 +276,10 @@ DevCam make_cam(const rm_intrinsics *in, const float *d_rays) {
 
 int wave_size(const rm_map *m, int n, const TileGeom &tg) {
   if (m->tuning.wave_poses > 0) return std::min(n, m->tuning.wave_poses);
-  // keep per-wave scratch near 2 GiB
+  // up to 128 poses per wave, keeping the per-wave scratch near 4 GiB
   size_t per = (size_t)m->n_clusters * 4 + (size_t)tg.ntiles * ((size_t)tg.cap * sizeof(TriRec) + 8 * 40);
-  size_t w = std::max<size_t>(1, (size_t(2) << 30) / std::max<size_t>(per, 1));
-  return (int)std::min<size_t>(std::min<size_t>(w, 64), (size_t)n);
+  size_t w = std::max<size_t>(1, (size_t(4) << 30) / std::max<size_t>(per, 1));
+  return (int)std::min<size_t>(std::min<size_t>(w, 128), (size_t)n);
 }
 
 void set_clusters(const rm_map *m, WaveArgs &a) {

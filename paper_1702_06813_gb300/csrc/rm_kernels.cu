@@ -437,8 +437,12 @@ __device__ __forceinline__ bool raster_tile(unsigned long long *zk, TriRec *stag
   return true;
 }
 
+#ifndef RM_RASTER_MIN_BLOCKS
+#define RM_RASTER_MIN_BLOCKS 4  // resident CTAs per SM the register budget is sized for
+#endif
+
 template <int TW, int TH, int MODE>
-__global__ void __launch_bounds__(kThreads) k_raster(WaveArgs a) {
+__global__ void __launch_bounds__(kThreads, RM_RASTER_MIN_BLOCKS) k_raster(WaveArgs a) {
   constexpr int NP = TW * TH;
   constexpr int NW = kThreads / 32;
   __shared__ unsigned long long zk[NP];
@@ -619,17 +623,23 @@ __global__ void __launch_bounds__(kThreads) k_raster(WaveArgs a) {
   }
 }
 
-__global__ void k_reduce(WaveArgs a) {
+// Per pose: sum the per-tile partials. Warp w reduces values w, w+8, ...; lane l sums tiles
+// l, l+32, ... and a butterfly combines the lanes, so the order is fixed run to run.
+__global__ void __launch_bounds__(256) k_reduce(WaveArgs a) {
   if (a.skip && *a.skip) return;
   __shared__ double vals[kNumVals];
-  const int q = blockIdx.x, g = a.wave_base + q, k = threadIdx.x;
-  if (k < kNumVals) {
-    const double *p = a.partial + (long long)q * a.tg.ntiles * kNumVals + k;
+  const int q = blockIdx.x, g = a.wave_base + q;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const double *base = a.partial + (long long)q * a.tg.ntiles * kNumVals;
+  for (int k = warp; k < kNumVals; k += 8) {
     double s = 0.0;
-    for (int t = 0; t < a.tg.ntiles; ++t) s += p[(long long)t * kNumVals];
-    vals[k] = s;
+    for (int t = lane; t < a.tg.ntiles; t += 32) s += base[(long long)t * kNumVals + k];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) vals[k] = s;
   }
   __syncthreads();
+  const int k = threadIdx.x;
   if (k < 6 && a.res_counts) a.res_counts[6 * (long long)g + k] = (long long)vals[k];
   if (k == 6 && a.res_els) a.res_els[g] = vals[6];
   if (k >= 7 && k < 13 && a.res_grad) a.res_grad[6 * (long long)g + (k - 7)] = vals[k];
@@ -675,7 +685,7 @@ cudaError_t launch_wave(const WaveArgs &a, int mode, cudaStream_t s, cudaEvent_t
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[3], s)) != cudaSuccess) return e;
   if (mode != kRender) {
-    k_reduce<<<a.n_poses, 64, 0, s>>>(a);
+    k_reduce<<<a.n_poses, 256, 0, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (ev && (e = cudaEventRecord(ev[4], s)) != cudaSuccess) return e;
