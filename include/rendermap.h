@@ -206,6 +206,31 @@ rm_status rm_profile(rm_map *map, int32_t enable);
 rm_status rm_profile_read(rm_map *map, rm_kernel_time *out, int32_t cap, int32_t *n,
                           int64_t *launches);
 
+/* Cost and gradient of ONE pose without allocating (the paper has no counterpart; this is a
+ * deployment variant of rm_cost_grad). For callers that must not allocate device memory
+ * while they evaluate poses -- a real-time loop that may not call into the allocator after
+ * start-up (an allocation can synchronise the device and has unbounded latency), code under
+ * a memory manager that owns the whole device, or a fixed memory budget. All scratch (pose
+ * matrix, visible-cluster list, screen-tile bins, per-tile partial sums, status word) comes
+ * from one array of RM_NOALLOC_SCRATCH_BYTES in device global memory that belongs to the
+ * library: every GPU that loads the library holds it until the process exits.
+ *  - map: created earlier with rm_map_create (read only here); its tile size is used, and
+ *    the bin capacity is whatever fits in the array (at most 4096 records per tile).
+ *  - scan: depth and cls in DEVICE memory; pose: 16 doubles, host or device.
+ *  - out: DEVICE pointers (any may be NULL), one pose's values as for rm_cost_grad.
+ * The call waits for `stream` to read its status. The first call on each device looks up
+ * the array's device address (cudaGetSymbolAddress, with that device current); make that
+ * first call before any stream capture. Every call shares the one array and leaves its
+ * contents behind; the call clears what must start at zero. Calls whose GPU work overlaps
+ * (other streams, unordered threads) race on the array and give wrong results.
+ * Errors: RM_EINVAL for host scan/output pointers, or when the cluster list and tile arrays
+ * leave room for fewer than 256 records per tile; RM_EOVERFLOW when a tile's bin overflows
+ * (no growth is possible); RM_ECUDA, RM_ETIMEOUT as elsewhere. */
+#define RM_NOALLOC_SCRATCH_BYTES (48u << 20)
+rm_status rm_cost_grad_noalloc(const rm_map *map, const rm_scan *scan, const double *pose,
+                               const rm_cost_params *params, const rm_cost_out *out,
+                               void *stream);
+
 /* Reads and clears the map's device status word after work queued with async_status = 1;
  * returns RM_OK, RM_EOVERFLOW or RM_ETIMEOUT. */
 rm_status rm_status_sync(rm_map *map, void *stream);

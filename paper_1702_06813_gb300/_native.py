@@ -77,6 +77,8 @@ _SIGS = {
     "rm_pose_retract": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P, _P, _P]),
     "rm_align": (ctypes.c_int, [_P, ctypes.POINTER(rm_scan), _P, ctypes.POINTER(rm_cost_params),
                                 ctypes.POINTER(rm_align_params), _P, ctypes.POINTER(rm_align_report), _P]),
+    "rm_cost_grad_noalloc": (ctypes.c_int, [_P, ctypes.POINTER(rm_scan), _P,
+                                            ctypes.POINTER(rm_cost_params), ctypes.POINTER(rm_cost_out), _P]),
     "rm_status_sync": (ctypes.c_int, [_P, _P]),
     "rm_profile": (ctypes.c_int, [_P, ctypes.c_int32]),
     "rm_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(rm_kernel_time), ctypes.c_int32, _P, _P]),

@@ -509,6 +509,27 @@ rm_status run_eval(rm_map *m, const EvalReq &r, cudaStream_t s) {
 
 }  // namespace
 
+namespace rmapi {
+
+rm_status wave_inputs(const rm_map *m, const rm_intrinsics *in, WaveArgs *a, double centre[3]) {
+  if (!m) return fail(RM_EINVAL, "map is NULL");
+  RM_TRY(check_intr(in));
+  a->cam = make_cam(in, nullptr);
+  a->tg = make_tiles(m, in);
+  a->V = (int)m->V;
+  a->T = m->T;
+  a->v = m->d_v;
+  a->faces = m->d_faces;
+  a->planes = m->d_planes;
+  set_clusters(m, *a);
+  for (int k = 0; k < 3; ++k) centre[k] = m->centre[k];
+  return RM_OK;
+}
+
+void set_error(const std::string &msg) { g_err = msg; }
+
+}  // namespace rmapi
+
 extern "C" {
 
 const char *rm_last_error(void) { return g_err.c_str(); }

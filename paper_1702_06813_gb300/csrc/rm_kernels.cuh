@@ -2,8 +2,10 @@
 #pragma once
 
 #include <cstdint>
+#include <string>
 #include <cuda_runtime.h>
 
+#include "rendermap.h"
 #include "rm_internal.cuh"
 
 namespace rmk {
@@ -95,3 +97,13 @@ cudaError_t launch_lm_accept(LMState *st, const LMArgs &a, const long long *coun
                              int *skip, cudaStream_t s);
 
 }  // namespace rmk
+
+// Host-side helpers of rm_api.cu shared with the other entry-point files.
+namespace rmapi {
+// Fills the map- and camera-derived fields of a (camera, tiles, mesh and cluster arrays) and
+// the map centre; checks the intrinsics (RM_EINVAL with a message on failure).
+rm_status wave_inputs(const rm_map *map, const rm_intrinsics *intr, rmk::WaveArgs *a,
+                      double centre[3]);
+// Sets the calling thread's rm_last_error message.
+void set_error(const std::string &msg);
+}  // namespace rmapi
