@@ -52,6 +52,34 @@ def peaks():
         return PEAKS_FALLBACK, "fallback"
 
 
+def kernel_source_hash():
+    """First 16 hex digits of sha256 over the kernel sources (as recorded in profiles/)."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1702_06813_gb300", "csrc")
+    for f in ("rm_kernels.cu", "rm_internal.cuh"):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(hashlib.sha256(fh.read()).hexdigest().encode() + b"  " + f"paper_1702_06813_gb300/csrc/{f}\n".encode())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel, poses_per_launch):
+    """DRAM bytes per launch of `kernel` from the ncu summary in profiles/, scaled by poses per
+    launch; None when the summary is missing or was taken on different kernel sources."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_room1M_640x480.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    fields = dict(line.split(":", 1) for line in text.splitlines() if ":" in line and " " not in line.split(":", 1)[0])
+    try:
+        if fields["kernel_source_sha256_16"].strip() != kernel_source_hash():
+            return None
+        return int(fields["dram_bytes_per_launch"]) / int(fields["poses_per_launch"]) * poses_per_launch
+    except (KeyError, ValueError):
+        return None
+
+
 def algorithmic_bytes(V, T, P):
     """Bytes one pose evaluation must touch: vertices 12 V, faces + labels 13 T, scan 5 P."""
     return {"k_cull": 0, "k_setup": 12 * V + 13 * T, "k_raster": 5 * P, "k_reduce": 0,
@@ -327,7 +355,8 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(prof["launches"] // a.steps) * a.steps,
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": pk["hbm_gbs"],
-                     "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "traffic": None,
+                     "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
+                     "traffic": measured_traffic(dom, per_launch_poses),
                      "peak_kind": pk_kind, "avg_launch_ms": avg_s * 1e3,
                      "poses_per_launch": per_launch_poses},
     }
