@@ -237,7 +237,12 @@ rm_status check_intr(const rm_intrinsics *in) {
       return fail(RM_EINVAL, "pinhole fx, fy must be finite and non-zero, cx, cy finite");
     return RM_OK;
   }
-  if (in->model == RM_RAYTABLE) return fail(RM_EINVAL, "ray-table camera model is not built yet");
+  if (in->model == RM_RAYTABLE) {
+    if (!in->rays) return fail(RM_EINVAL, "ray-table camera needs its rays");
+    if (!(in->az_step > 0.0f && in->el_step > 0.0f && std::isfinite(in->az0) && std::isfinite(in->el0)))
+      return fail(RM_EINVAL, "ray-table layout needs az_step > 0, el_step > 0 and finite az0, el0");
+    return RM_OK;
+  }
   return fail(RM_EINVAL, "unknown camera model");
 }
 
@@ -249,6 +254,7 @@ TileGeom make_tiles(const rm_map *m, const rm_intrinsics *in) {
   tg.nty = (in->height + tg.th - 1) / tg.th;
   tg.ntiles = tg.ntx * tg.nty;
   tg.cap = m->cap;
+  tg.rec_bytes = in->model == RM_RAYTABLE ? (int)sizeof(rmk::RayRec) : (int)sizeof(TriRec);
   return tg;
 }
 
@@ -277,7 +283,7 @@ DevCam make_cam(const rm_intrinsics *in, const float *d_rays) {
 int wave_size(const rm_map *m, int n, const TileGeom &tg) {
   if (m->tuning.wave_poses > 0) return std::min(n, m->tuning.wave_poses);
   // up to 128 poses per wave, keeping the per-wave scratch near 4 GiB
-  size_t per = (size_t)m->n_clusters * 4 + (size_t)tg.ntiles * ((size_t)tg.cap * sizeof(TriRec) + 8 * 40);
+  size_t per = (size_t)m->n_clusters * 4 + (size_t)tg.ntiles * ((size_t)tg.cap * tg.rec_bytes + 8 * 40);
   size_t w = std::max<size_t>(1, (size_t(4) << 30) / std::max<size_t>(per, 1));
   return (int)std::min<size_t>(std::min<size_t>(w, 128), (size_t)n);
 }
@@ -375,6 +381,7 @@ rm_status run_eval(rm_map *m, const EvalReq &r, cudaStream_t s) {
   RM_CK(cudaSetDevice(m->device));
   const long long P = (long long)in->width * in->height;
   const bool host_poses = !on_device(r.poses);
+  const bool host_rays = in->model == RM_RAYTABLE && !on_device(in->rays);
   const bool host_scan = r.mode != rmk::kRender && !on_device(r.scan->depth);
   const bool host_cls = r.mode != rmk::kRender && !on_device(r.scan->cls);
   const bool dev_depth = r.mode == rmk::kRender && on_device(r.depth);
@@ -388,6 +395,7 @@ rm_status run_eval(rm_map *m, const EvalReq &r, cudaStream_t s) {
     Carver plan{nullptr};
     plan.take<double>(16 * (size_t)r.n);
     plan.take<float>(12 * (size_t)r.n);
+    if (host_rays) plan.take<float>(3 * P);
     if (host_scan) plan.take<float>(P);
     if (host_cls) plan.take<uint8_t>(P);
     plan.take<long long>(6 * (size_t)r.n);
@@ -403,13 +411,15 @@ rm_status run_eval(rm_map *m, const EvalReq &r, cudaStream_t s) {
     plan.take<int>((size_t)m->n_clusters * nw);
     plan.take<int>(nw);
     plan.take<int>((size_t)tg.ntiles * nw);
-    plan.take<TriRec>((size_t)tg.ntiles * tg.cap * nw);
+    plan.take<unsigned char>((size_t)tg.ntiles * tg.cap * nw * tg.rec_bytes);
     plan.take<double>((size_t)tg.ntiles * rmk::kNumVals * nw);
     RM_TRY(ensure_arena(m, plan.off, s));
     // ---- carve it
     Carver cv{m->arena};
     double *d_poses = cv.take<double>(16 * (size_t)r.n);
     float *d_M = cv.take<float>(12 * (size_t)r.n);
+    const float *d_rays = in->rays;
+    if (host_rays) d_rays = cv.take<float>(3 * P);
     const float *d_sd = nullptr;
     const uint8_t *d_sc = nullptr;
     if (r.mode != rmk::kRender) {
@@ -432,18 +442,19 @@ rm_status run_eval(rm_map *m, const EvalReq &r, cudaStream_t s) {
     int *d_vis = cv.take<int>((size_t)m->n_clusters * nw);
     int *d_vcount = cv.take<int>(nw);
     int *d_bcount = cv.take<int>((size_t)tg.ntiles * nw);
-    TriRec *d_bins = cv.take<TriRec>((size_t)tg.ntiles * tg.cap * nw);
+    unsigned char *d_bins = cv.take<unsigned char>((size_t)tg.ntiles * tg.cap * nw * tg.rec_bytes);
     double *d_partial = cv.take<double>((size_t)tg.ntiles * rmk::kNumVals * nw);
     // ---- inputs
     RM_CK(cudaMemcpyAsync(d_poses, r.poses, sizeof(double) * 16 * r.n,
                           host_poses ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+    if (host_rays) RM_CK(cudaMemcpyAsync((void *)d_rays, in->rays, sizeof(float) * 3 * P, cudaMemcpyHostToDevice, s));
     if (host_scan) RM_CK(cudaMemcpyAsync((void *)d_sd, r.scan->depth, sizeof(float) * P, cudaMemcpyHostToDevice, s));
     if (host_cls) RM_CK(cudaMemcpyAsync((void *)d_sc, r.scan->cls, P, cudaMemcpyHostToDevice, s));
     RM_CK(rmk::launch_pose_to_m(d_poses, r.n, m->centre[0], m->centre[1], m->centre[2], d_M, s));
     m->launches += 1;
     // ---- waves
     WaveArgs a{};
-    a.cam = make_cam(in, nullptr);
+    a.cam = make_cam(in, d_rays);
     a.tg = tg;
     a.V = (int)m->V;
     a.T = m->T;
@@ -514,7 +525,9 @@ namespace rmapi {
 rm_status wave_inputs(const rm_map *m, const rm_intrinsics *in, WaveArgs *a, double centre[3]) {
   if (!m) return fail(RM_EINVAL, "map is NULL");
   RM_TRY(check_intr(in));
-  a->cam = make_cam(in, nullptr);
+  if (in->model == RM_RAYTABLE && !on_device(in->rays))
+    return fail(RM_EINVAL, "this entry point needs the ray table in device memory");
+  a->cam = make_cam(in, in->rays);
   a->tg = make_tiles(m, in);
   a->V = (int)m->V;
   a->T = m->T;
@@ -789,10 +802,12 @@ rm_status rm_align(rm_map *m, const rm_scan *scan, const double *init_pose,
   RM_CK(cudaSetDevice(m->device));
   const long long P = (long long)in->width * in->height;
   const bool host_scan = !on_device(scan->depth), host_cls = !on_device(scan->cls);
+  const bool host_rays = in->model == RM_RAYTABLE && !on_device(in->rays);
   for (int attempt = 0;; ++attempt) {
     TileGeom tg = make_tiles(m, in);
     Carver plan{nullptr};
     plan.take<rmk::LMState>(1);
+    if (host_rays) plan.take<float>(3 * P);
     plan.take<double>(16);
     plan.take<float>(12);
     plan.take<int>(1);
@@ -806,11 +821,12 @@ rm_status rm_align(rm_map *m, const rm_scan *scan, const double *init_pose,
     plan.take<int>(m->n_clusters);
     plan.take<int>(1);
     plan.take<int>(tg.ntiles);
-    plan.take<TriRec>((size_t)tg.ntiles * tg.cap);
+    plan.take<unsigned char>((size_t)tg.ntiles * tg.cap * tg.rec_bytes);
     plan.take<double>((size_t)tg.ntiles * rmk::kNumVals);
     RM_TRY(ensure_arena(m, plan.off, s));
     Carver cv{m->arena};
     rmk::LMState *d_st = cv.take<rmk::LMState>(1);
+    const float *d_rays = host_rays ? cv.take<float>(3 * P) : in->rays;
     double *d_T0 = cv.take<double>(16);
     float *d_M = cv.take<float>(12);
     int *d_skip = cv.take<int>(1);
@@ -822,7 +838,7 @@ rm_status rm_align(rm_map *m, const rm_scan *scan, const double *init_pose,
     double *d_grad = cv.take<double>(6);
     double *d_jtj = cv.take<double>(21);
     WaveArgs a{};
-    a.cam = make_cam(in, nullptr);
+    a.cam = make_cam(in, d_rays);
     a.tg = tg;
     a.V = (int)m->V;
     a.T = m->T;
@@ -836,7 +852,7 @@ rm_status rm_align(rm_map *m, const rm_scan *scan, const double *init_pose,
     a.vis = cv.take<int>(m->n_clusters);
     a.vis_count = cv.take<int>(1);
     a.counts = cv.take<int>(tg.ntiles);
-    a.bins = cv.take<TriRec>((size_t)tg.ntiles * tg.cap);
+    a.bins = cv.take<unsigned char>((size_t)tg.ntiles * tg.cap * tg.rec_bytes);
     a.partial = cv.take<double>((size_t)tg.ntiles * rmk::kNumVals);
     a.status = m->d_status;
     a.skip = d_skip;
@@ -850,6 +866,7 @@ rm_status rm_align(rm_map *m, const rm_scan *scan, const double *init_pose,
     a.res_jtj = d_jtj;
     RM_CK(cudaMemcpyAsync(d_T0, init_pose, sizeof(double) * 16,
                           on_device(init_pose) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    if (host_rays) RM_CK(cudaMemcpyAsync((void *)d_rays, in->rays, sizeof(float) * 3 * P, cudaMemcpyHostToDevice, s));
     if (host_scan) RM_CK(cudaMemcpyAsync((void *)d_sd, scan->depth, sizeof(float) * P, cudaMemcpyHostToDevice, s));
     if (host_cls) RM_CK(cudaMemcpyAsync((void *)d_sc, scan->cls, P, cudaMemcpyHostToDevice, s));
     rmk::LMArgs la{lm->lambda0, lm->lambda_up, lm->lambda_down, lm->step_tol,

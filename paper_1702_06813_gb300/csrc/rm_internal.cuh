@@ -44,6 +44,7 @@ struct TileGeom {
   int ntx, nty;        // tiles per row / column
   int ntiles;
   int cap;             // records per bin
+  int rec_bytes;       // bytes per bin record: sizeof(TriRec) or sizeof(RayRec)
 };
 
 // One snapped triangle (or near-clipped piece) in a screen-tile bin, 48 bytes.
@@ -54,6 +55,20 @@ struct __align__(16) TriRec {
   int spare, pad;
 };
 static_assert(sizeof(TriRec) == 48, "record layout");
+
+// One triangle of the ray-table (panoramic) model in a screen-tile bin, 64 bytes. Coverage of
+// a pixel ray r: for each edge k, s = r . c_k with c_k the cross product of the edge's two
+// camera-frame vertices taken in increasing vertex-index order (so neighbours share the bits);
+// covered iff sigma_k s > 0 for every k, or s == 0 where sigma_k > 0.
+struct __align__(16) RayRec {
+  float c0x, c0y, c0z, c1x, c1y, c1z, c2x, c2y, c2z;  // edge normals c_k
+  float nix, niy, niz;         // inverse-depth normal n / d: w = ni . r
+  unsigned id;                 // triangle id
+  int sig;                     // bit k set: sigma_k = +1
+  int rect0;                   // columns i0 | i1 << 16 (no wrap); tile-relative after setup
+  int rect1;                   // rows    j0 | j1 << 16
+};
+static_assert(sizeof(RayRec) == 64, "record layout");
 
 // ---------------------------------------------------------------- contract helpers
 
@@ -108,6 +123,16 @@ __device__ __forceinline__ float inv_depth_pinhole(float Ai, float Bi, float Ci,
 
 __device__ __forceinline__ bool keep_w(const DevCam &c, float w) {
   return w > 0.0f && w >= c.w_far && w <= c.w_near;
+}
+
+// Ray-table contract helpers: cross and dot products in a fixed FMA order.
+__device__ __forceinline__ float3 cross_c(float3 p, float3 q) {
+  return make_float3(__fmaf_rn(p.y, q.z, -__fmul_rn(p.z, q.y)), __fmaf_rn(p.z, q.x, -__fmul_rn(p.x, q.z)),
+                     __fmaf_rn(p.x, q.y, -__fmul_rn(p.y, q.x)));
+}
+
+__device__ __forceinline__ float dot_c(float px, float py, float pz, float qx, float qy, float qz) {
+  return __fmaf_rn(px, qx, __fmaf_rn(py, qy, __fmul_rn(pz, qz)));
 }
 
 __device__ __forceinline__ float3 near_cut(float3 a, float3 b, float near_m) {

@@ -130,6 +130,13 @@ __device__ __forceinline__ bool cluster_visible(const DevCam &cam, const float *
   const float dist = sqrtf(c.x * c.x + c.y * c.y + c.z * c.z);
   if (dist + r < cam.near_m - slack) return false;
   if (dist - r > cam.far_m + slack) return false;
+  if (dist <= r + slack) return true;  // the sensor is inside the sphere
+  // elevation band of the rows (two rows of margin): the sphere subtends asin(r / dist)
+  const float alpha = asinf(fminf(1.0f, (r + slack) / dist)) + 1e-4f;
+  const float el_c = asinf(fmaxf(-1.0f, fminf(1.0f, -c.y / dist)));
+  const float top = cam.el0 + 2.0f * cam.el_step;
+  const float bot = cam.el0 - (cam.H + 1) * cam.el_step;
+  if (el_c - alpha > top || el_c + alpha < bot) return false;
   return true;
 }
 
@@ -157,7 +164,8 @@ __global__ void __launch_bounds__(256) k_cull(WaveArgs a) {
 
 __device__ __forceinline__ void emit_piece(int x0, int y0, int x1, int y1, int x2, int y2,
                                            float Ai, float Bi, float Ci, unsigned id,
-                                           const WaveArgs &a, int *counts, TriRec *bins) {
+                                           const WaveArgs &a, int *counts, unsigned char *bins_b) {
+  TriRec *bins = reinterpret_cast<TriRec *>(bins_b);
   long long area = (long long)(x1 - x0) * (y2 - y0) - (long long)(y1 - y0) * (x2 - x0);
   if (area == 0) return;
   if (area < 0) {
@@ -190,6 +198,122 @@ __device__ __forceinline__ void emit_piece(int x0, int y0, int x1, int y1, int x
     }
 }
 
+// Appends a ray-table record to the bins of every tile its pixel rectangle overlaps.
+__device__ __forceinline__ void emit_ray(const RayRec &rr, int i0, int i1, int j0, int j1,
+                                         const WaveArgs &a, int *counts, unsigned char *bins_b) {
+  RayRec *bins = reinterpret_cast<RayRec *>(bins_b);
+  const TileGeom &tg = a.tg;
+  const int4 *src = reinterpret_cast<const int4 *>(&rr);
+  int4 w3 = src[3];
+  w3.z = i0 | (i1 << 16);
+  w3.w = j0 | (j1 << 16);
+  for (int ty = j0 / tg.th; ty <= j1 / tg.th; ++ty)
+    for (int tx = i0 / tg.tw; tx <= i1 / tg.tw; ++tx) {
+      const int tile = ty * tg.ntx + tx;
+      const int slot = atomicAdd(&counts[tile], 1);
+      if (slot < tg.cap) {
+        int4 *dst = reinterpret_cast<int4 *>(bins + (long long)tile * tg.cap + slot);
+        dst[0] = src[0];
+        dst[1] = src[1];
+        dst[2] = src[2];
+        dst[3] = w3;
+      } else {
+        atomicOr(a.status, kStatusOverflow);
+      }
+    }
+}
+
+// Ray-table triangle: contract side normals and inverse-depth normal, then a conservative
+// pixel rectangle from the layout (azimuth from the vertices' smallest enclosing arc, full
+// when a pole is inside; elevation from the vertices widened by the great-circle bulge
+// bound z / cos(L/2), L the longest edge angle), two pixels of margin, split at the seam.
+__device__ __forceinline__ void setup_ray(const float3 v[3], const float4 u[3], const int gid[3],
+                                          unsigned id, const WaveArgs &a, int *counts,
+                                          unsigned char *bins) {
+  const DevCam &cam = a.cam;
+  const float3 c12 = cross_c(v[1], v[2]);
+  const float det = dot_c(v[0].x, v[0].y, v[0].z, c12.x, c12.y, c12.z);
+  if (det == 0.0f || det != det) return;
+  RayRec rr;
+  float3 side[3];
+  float sg[3];
+  int sig = 0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int m = k == 2 ? 0 : k + 1;
+    const bool lo_is_k = gid[k] < gid[m];
+    side[k] = lo_is_k ? cross_c(v[k], v[m]) : cross_c(v[m], v[k]);
+    sg[k] = (det > 0.0f ? 1.0f : -1.0f) * (lo_is_k ? 1.0f : -1.0f);
+    if (sg[k] > 0.0f) sig |= 1 << k;
+  }
+  rr.c0x = side[0].x; rr.c0y = side[0].y; rr.c0z = side[0].z;
+  rr.c1x = side[1].x; rr.c1y = side[1].y; rr.c1z = side[1].z;
+  rr.c2x = side[2].x; rr.c2y = side[2].y; rr.c2z = side[2].z;
+  const PlaneN pl = plane_n(v[0], v[1], v[2]);
+  rr.nix = __fdiv_rn(pl.nx, pl.d);
+  rr.niy = __fdiv_rn(pl.ny, pl.d);
+  rr.niz = __fdiv_rn(pl.nz, pl.d);
+  rr.id = id;
+  rr.sig = sig;
+  rr.rect0 = rr.rect1 = 0;
+  // ---- conservative pixel rectangle (any rounding; margins absorb it)
+  bool has_up = true, has_dn = true;  // up = (0,-1,0), down = (0,1,0)
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float nrm = sqrtf(side[k].x * side[k].x + side[k].y * side[k].y + side[k].z * side[k].z);
+    const float tol = 1e-4f * nrm;
+    if (-sg[k] * side[k].y < -tol) has_up = false;
+    if (sg[k] * side[k].y < -tol) has_dn = false;
+  }
+  float zmax = fmaxf(-u[0].y, fmaxf(-u[1].y, -u[2].y)), zmin = fminf(-u[0].y, fminf(-u[1].y, -u[2].y));
+  const float cmin = fminf(u[0].x * u[1].x + u[0].y * u[1].y + u[0].z * u[1].z,
+                           fminf(u[1].x * u[2].x + u[1].y * u[2].y + u[1].z * u[2].z,
+                                 u[2].x * u[0].x + u[2].y * u[0].y + u[2].z * u[0].z));
+  const float ch = sqrtf(fmaxf(0.0f, 0.5f * (1.0f + cmin)));
+  if (ch < 0.05f) {
+    zmax = 1.0f;
+    zmin = -1.0f;
+  } else {
+    if (zmax >= 0.0f) zmax = fminf(1.0f, zmax / ch);
+    if (zmin <= 0.0f) zmin = fmaxf(-1.0f, zmin / ch);
+  }
+  if (has_up) zmax = 1.0f;
+  if (has_dn) zmin = -1.0f;
+  const float el_hi = asinf(zmax), el_lo = asinf(zmin);
+  const int j0 = max(0, (int)ceilf((cam.el0 - el_hi) / cam.el_step - 2.0f));
+  const int j1 = min(cam.H - 1, (int)floorf((cam.el0 - el_lo) / cam.el_step + 2.0f));
+  if (j0 > j1) return;
+  if (has_up || has_dn) {
+    emit_ray(rr, 0, cam.W - 1, j0, j1, a, counts, bins);
+    return;
+  }
+  float s0 = u[0].w, s1 = u[1].w, s2 = u[2].w, t;
+  if (s0 > s1) { t = s0; s0 = s1; s1 = t; }
+  if (s1 > s2) { t = s1; s1 = s2; s2 = t; }
+  if (s0 > s1) { t = s0; s0 = s1; s1 = t; }
+  const float twopi = 6.28318530717958647692f;
+  const float g01 = s1 - s0, g12 = s2 - s1, g20 = s0 + twopi - s2;
+  float lo, hi;
+  if (g20 >= g01 && g20 >= g12) { lo = s0; hi = s2; }
+  else if (g01 >= g12) { lo = s1; hi = s0 + twopi; }
+  else { lo = s2; hi = s1 + twopi; }
+  const int ilo = (int)ceilf((lo - cam.az0) / cam.az_step - 0.5f - 2.0f);
+  const int ihi = (int)floorf((hi - cam.az0) / cam.az_step - 0.5f + 2.0f);
+  const int n = ihi - ilo + 1;
+  if (n >= cam.W) {
+    emit_ray(rr, 0, cam.W - 1, j0, j1, a, counts, bins);
+    return;
+  }
+  int st = ilo % cam.W;
+  if (st < 0) st += cam.W;
+  if (st + n <= cam.W) {
+    emit_ray(rr, st, st + n - 1, j0, j1, a, counts, bins);
+  } else {
+    emit_ray(rr, st, cam.W - 1, j0, j1, a, counts, bins);
+    emit_ray(rr, 0, st + n - 1 - cam.W, j0, j1, a, counts, bins);
+  }
+}
+
 constexpr int kClusterMax = 64;  // vertices and triangles per cluster
 
 // One warp per visible cluster: its vertices are transformed and snapped once into shared
@@ -199,6 +323,7 @@ __global__ void __launch_bounds__(256) k_setup(WaveArgs a) {
   __shared__ float4 s_vc[8][kClusterMax];
   __shared__ int2 s_vs[8][kClusterMax];
   __shared__ int s_gid[8][kClusterMax];
+  __shared__ float4 s_dir[8][kClusterMax];  // ray table: unit direction and azimuth
   if (a.skip && *a.skip) return;
   const int q = blockIdx.y;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -209,9 +334,10 @@ __global__ void __launch_bounds__(256) k_setup(WaveArgs a) {
   const int nvis = a.vis_count[q];
   const int *vis = a.vis + (long long)q * a.n_clusters;
   int *counts = a.counts + (long long)q * a.tg.ntiles;
-  TriRec *bins = a.bins + (long long)q * a.tg.ntiles * a.tg.cap;
+  unsigned char *bins = a.bins + (long long)q * a.tg.ntiles * a.tg.cap * a.tg.rec_bytes;
   const int W = a.cam.W, H = a.cam.H;
   const float near_m = a.cam.near_m;
+  const bool raytable = a.cam.model != 0;
   for (int ci = blockIdx.x * 8 + warp; ci < nvis; ci += gridDim.x * 8) {
     const int4 info = a.cl_info[vis[ci]];  // vert offset, tri offset, nv, nt
     for (int k = lane; k < info.z; k += 32) {
@@ -219,7 +345,11 @@ __global__ void __launch_bounds__(256) k_setup(WaveArgs a) {
       const float4 v = a.v[gv];
       const float3 c = xform(M, v.x, v.y, v.z);
       int2 sv = make_int2(kSentinel, 1);  // behind the near plane
-      if (c.z >= near_m) {
+      if (raytable) {
+        const float nr = sqrtf(c.x * c.x + c.y * c.y + c.z * c.z);
+        const float inv = nr > 0.0f ? 1.0f / nr : 0.0f;
+        s_dir[warp][k] = make_float4(c.x * inv, c.y * inv, c.z * inv, atan2f(c.x, c.z));
+      } else if (c.z >= near_m) {
         int xi, yi;
         sv = snap(a.cam, c.x, c.y, c.z, xi, yi) ? make_int2(xi, yi) : make_int2(kSentinel, 2);
       }
@@ -231,6 +361,21 @@ __global__ void __launch_bounds__(256) k_setup(WaveArgs a) {
     for (int k = lane; k < info.w; k += 32) {
       const uchar4 t = a.cl_tris[info.y + k];
       const unsigned id = (unsigned)a.cl_ids[info.y + k];
+      if (raytable) {
+        const int loc[3] = {t.x, t.y, t.z};
+        float3 v[3];
+        float4 u[3];
+        int gid[3];
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+          const float4 p = s_vc[warp][loc[m]];
+          v[m] = make_float3(p.x, p.y, p.z);
+          u[m] = s_dir[warp][loc[m]];
+          gid[m] = s_gid[warp][loc[m]];
+        }
+        setup_ray(v, u, gid, id, a, counts, bins);
+        continue;
+      }
       const int2 s0 = s_vs[warp][t.x], s1 = s_vs[warp][t.y], s2 = s_vs[warp][t.z];
       if (s0.x != kSentinel && s1.x != kSentinel && s2.x != kSentinel) {
         // all three in front of the near plane and inside the guard band
@@ -287,7 +432,8 @@ __global__ void __launch_bounds__(256) k_setup(WaveArgs a) {
 
 // ------------------------------------------------------------------ raster + epilogue
 
-constexpr int kRecMax = 512;  // bin records staged in shared memory per round
+constexpr int kRecMaxPinhole = 512;  // bin records staged in shared memory per round (48 B)
+constexpr int kRecMaxRay = 384;      // (64 B)
 
 // Exact edge test with int32 operands and 64-bit products: E = dx (py - ya) - dy (px - xa),
 // covered iff E > 0 or E == 0 on a top or left edge.
@@ -355,6 +501,7 @@ __device__ __forceinline__ bool raster_tile(unsigned long long *zk, TriRec *stag
                                             int *S, int *wtot, unsigned long long *bar,
                                             const TriRec *recs, int n, int ox, int oy, int xe,
                                             int ye, const DevCam &cam) {
+  constexpr int kRecMax = kRecMaxPinhole;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int NW = kThreads / 32;
   unsigned phase = 0;
@@ -437,18 +584,120 @@ __device__ __forceinline__ bool raster_tile(unsigned long long *zk, TriRec *stag
   return true;
 }
 
+
+// Ray-table counterpart of derive_rect: clip the record's pixel rectangle to the tile and keep
+// its tile-relative origin and width in rect0.
+__device__ __forceinline__ int derive_ray_rect(RayRec *rec, int k, int cnt, int ox, int oy,
+                                               int xe, int ye) {
+  if (k >= cnt) return 0;
+  RayRec &r = rec[k];
+  const int i0 = max(r.rect0 & 0xffff, ox), i1 = min(r.rect0 >> 16, xe);
+  const int j0 = max(r.rect1 & 0xffff, oy), j1 = min(r.rect1 >> 16, ye);
+  if (i0 > i1 || j0 > j1) return 0;
+  const int bw = i1 - i0 + 1;
+  r.rect0 = (i0 - ox) | ((j0 - oy) << 8) | (bw << 16);
+  return bw * (j1 - j0 + 1);
+}
+
+// Ray-table tile raster: the tile's rays are staged in shared memory; each fragment is a cone
+// test of its ray against the three edge normals and an inverse-depth dot product.
+template <int TW, int TH>
+__device__ __forceinline__ bool raster_tile_ray(unsigned long long *zk, RayRec *stage,
+                                                const float *rx, const float *ry, const float *rz,
+                                                int *S, int *wtot, unsigned long long *bar,
+                                                const RayRec *recs, int n, int ox, int oy,
+                                                int xe, int ye, const DevCam &cam) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = kThreads / 32;
+  constexpr int kRecMax = kRecMaxRay;
+  unsigned phase = 0;
+  for (int r0 = 0; r0 < n; r0 += kRecMax) {
+    const int cnt = min(kRecMax, n - r0);
+    if (tid == 0) {
+      fence_async_smem();
+      bulk_g2s(stage, recs + r0, (unsigned)(cnt * sizeof(RayRec)), bar);
+    }
+    bool ok = mbar_wait(bar, phase);
+    ok = __syncthreads_and(ok);
+    if (!ok) {
+      if (tid == 0) mbar_wait(bar, phase);
+      return false;
+    }
+    phase ^= 1u;
+    // records 2t and 2t+1 per thread keep the scan in record order
+    const int n0 = derive_ray_rect(stage, 2 * tid, cnt, ox, oy, xe, ye);
+    const int n1 = derive_ray_rect(stage, 2 * tid + 1, cnt, ox, oy, xe, ye);
+    int incl = n0 + n1;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += v;
+    }
+    if (lane == 31) wtot[warp] = incl;
+    __syncthreads();
+    int before = 0, F = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+      before += w < warp ? wtot[w] : 0;
+      F += wtot[w];
+    }
+    const int ex = before + incl - (n0 + n1);
+    if (2 * tid < cnt) S[2 * tid] = ex;
+    if (2 * tid + 1 < cnt) S[2 * tid + 1] = ex + n0;
+    if (tid == 0) S[cnt] = F;
+    __syncthreads();
+    const int lo = (int)(((long long)F * warp) / NW), hi = (int)(((long long)F * (warp + 1)) / NW);
+    int f = lo + lane;
+    if (f < hi) {
+      int a = 0, b = cnt - 1;
+      while (a < b) {
+        const int m = (a + b + 1) >> 1;
+        if (S[m] <= f) a = m;
+        else b = m - 1;
+      }
+      int r = a, sr = S[a], snext = S[a + 1];
+      for (; f < hi; f += 32) {
+        while (snext <= f) {
+          ++r;
+          sr = snext;
+          snext = S[r + 1];
+        }
+        const RayRec &q = stage[r];
+        const int l = f - sr;
+        const int bw = q.rect0 >> 16;
+        const int dj = __float2int_rz(__fmul_rn(__int2float_rn(l) + 0.5f, __frcp_rn(__int2float_rn(bw))));
+        const int li = (q.rect0 & 0xff) + (l - dj * bw), lj = ((q.rect0 >> 8) & 0xff) + dj;
+        const int p = lj * TW + li;
+        const float x = rx[p], y = ry[p], z = rz[p];
+        const float s0 = dot_c(x, y, z, q.c0x, q.c0y, q.c0z);
+        const float s1 = dot_c(x, y, z, q.c1x, q.c1y, q.c1z);
+        const float s2 = dot_c(x, y, z, q.c2x, q.c2y, q.c2z);
+        const bool in = ((q.sig & 1) ? s0 >= 0.0f : s0 < 0.0f) && ((q.sig & 2) ? s1 >= 0.0f : s1 < 0.0f) &&
+                        ((q.sig & 4) ? s2 >= 0.0f : s2 < 0.0f);
+        if (in) {
+          const float w = dot_c(q.nix, q.niy, q.niz, x, y, z);
+          if (keep_w(cam, w)) atomicMin(&zk[p], make_key(w, q.id));
+        }
+      }
+    }
+    __syncthreads();
+  }
+  return true;
+}
+
 #ifndef RM_RASTER_MIN_BLOCKS
 #define RM_RASTER_MIN_BLOCKS 4  // resident CTAs per SM the register budget is sized for
 #endif
 
-template <int TW, int TH, int MODE>
+template <int TW, int TH, int MODE, int MODEL>
 __global__ void __launch_bounds__(kThreads, RM_RASTER_MIN_BLOCKS) k_raster(WaveArgs a) {
   constexpr int NP = TW * TH;
   constexpr int NW = kThreads / 32;
+  // pinhole: 512 records + their int4 edge headers; ray table: 384 records + the tile's rays
+  constexpr int kBuf = MODEL == 0 ? kRecMaxPinhole * (48 + 16) : kRecMaxRay * 64 + 12 * NP;
   __shared__ unsigned long long zk[NP];
-  __shared__ __align__(128) TriRec stage[kRecMax];
-  __shared__ int4 hdr[kRecMax];
-  __shared__ int S[kRecMax + 1];
+  __shared__ __align__(128) unsigned char sbuf[kBuf];
+  __shared__ int S[(MODEL == 0 ? kRecMaxPinhole : kRecMaxRay) + 1];
   __shared__ int wtot[NW];
   __shared__ __align__(8) unsigned long long bar[1];
   __shared__ float red[NW][28];
@@ -464,13 +713,41 @@ __global__ void __launch_bounds__(kThreads, RM_RASTER_MIN_BLOCKS) k_raster(WaveA
   for (int p = tid; p < NP; p += kThreads) zk[p] = kKeyEmpty;
   const long long bin = (long long)q * a.tg.ntiles + tile;
   const int n = min(a.counts[bin], a.tg.cap);
+  float *rx = nullptr, *ry = nullptr, *rz = nullptr;
+  if (MODEL != 0) {
+    rx = reinterpret_cast<float *>(sbuf + kRecMaxRay * 64);
+    ry = rx + NP;
+    rz = ry + NP;
+    for (int p = tid; p < NP; p += kThreads) {
+      const int i = ox + p % TW, j = oy + p / TW;
+      float x = 0.0f, y = 0.0f, z = 0.0f;
+      if (i <= xe && j <= ye) {
+        const float *rr = a.cam.rays + 3 * ((long long)j * W + i);
+        x = rr[0];
+        y = rr[1];
+        z = rr[2];
+      }
+      rx[p] = x;
+      ry[p] = y;
+      rz[p] = z;
+    }
+  }
   if (tid == 0) {
     mbar_init(&bar[0], 1);
     fence_mbar_init();
   }
   __syncthreads();
-  if (!raster_tile<TW, TH>(zk, stage, hdr, S, wtot, bar, a.bins + bin * a.tg.cap, n, ox, oy, xe,
-                           ye, a.cam)) {
+  bool ok;
+  if (MODEL == 0)
+    ok = raster_tile<TW, TH>(zk, reinterpret_cast<TriRec *>(sbuf),
+                             reinterpret_cast<int4 *>(sbuf + kRecMaxPinhole * 48), S, wtot, bar,
+                             reinterpret_cast<const TriRec *>(a.bins) + bin * a.tg.cap, n, ox, oy,
+                             xe, ye, a.cam);
+  else
+    ok = raster_tile_ray<TW, TH>(zk, reinterpret_cast<RayRec *>(sbuf), rx, ry, rz, S, wtot, bar,
+                                 reinterpret_cast<const RayRec *>(a.bins) + bin * a.tg.cap, n, ox,
+                                 oy, xe, ye, a.cam);
+  if (!ok) {
     if (tid == 0) atomicOr(a.status, kStatusTimeout);
     return;
   }
@@ -503,8 +780,18 @@ __global__ void __launch_bounds__(kThreads, RM_RASTER_MIN_BLOCKS) k_raster(WaveA
         const float4 w0 = a.v[f.x], w1 = a.v[f.y], w2 = a.v[f.z];
         const float3 v0 = xform(M, w0.x, w0.y, w0.z), v1 = xform(M, w1.x, w1.y, w1.z),
                      v2 = xform(M, w2.x, w2.y, w2.z);
-        const float rx = (i + 0.5f - a.cam.cx) / a.cam.fx, ry = (j + 0.5f - a.cam.cy) / a.cam.fy;
-        const float hx = t * rx - v0.x, hy = t * ry - v0.y, hz = t - v0.z;
+        float rx, ry, rz;
+        if (MODEL == 0) {
+          rx = (i + 0.5f - a.cam.cx) / a.cam.fx;
+          ry = (j + 0.5f - a.cam.cy) / a.cam.fy;
+          rz = 1.0f;
+        } else {
+          const float *rr = a.cam.rays + 3 * ((long long)j * W + i);
+          rx = rr[0];
+          ry = rr[1];
+          rz = rr[2];
+        }
+        const float hx = t * rx - v0.x, hy = t * ry - v0.y, hz = t * rz - v0.z;
         const float e1x = v1.x - v0.x, e1y = v1.y - v0.y, e1z = v1.z - v0.z;
         const float e2x = v2.x - v0.x, e2y = v2.y - v0.y, e2z = v2.z - v0.z;
         const float nx = e1y * e2z - e1z * e2y, ny = e1z * e2x - e1x * e2z, nz = e1x * e2y - e1y * e2x;
@@ -570,18 +857,28 @@ __global__ void __launch_bounds__(kThreads, RM_RASTER_MIN_BLOCKS) k_raster(WaveA
     }
     acc[0] += 0.5f * w * r * r;
     if (MODE == kCostGrad && sgn != 0.0f) {
-      const float rx = (i + 0.5f - a.cam.cx) * ifx, ry = (j + 0.5f - a.cam.cy) * ify;
+      float rx, ry, rz;
+      if (MODEL == 0) {
+        rx = (i + 0.5f - a.cam.cx) * ifx;
+        ry = (j + 0.5f - a.cam.cy) * ify;
+        rz = 1.0f;
+      } else {
+        const float *rr = a.cam.rays + 3 * pix;
+        rx = rr[0];
+        ry = rr[1];
+        rz = rr[2];
+      }
       const float nx = R[0] * pl.x + R[1] * pl.y + R[2] * pl.z;
       const float ny = R[3] * pl.x + R[4] * pl.y + R[5] * pl.z;
       const float nz = R[6] * pl.x + R[7] * pl.y + R[8] * pl.z;
-      const float inv = __frcp_rn(nx * rx + ny * ry + nz);
+      const float inv = __frcp_rn(nx * rx + ny * ry + nz * rz);
       const float s = sgn * inv;
       float J[6];
       J[0] = -nx * s;
       J[1] = -ny * s;
       J[2] = -nz * s;
-      J[3] = -t * (ry * nz - ny) * s;
-      J[4] = -t * (nx - rx * nz) * s;
+      J[3] = -t * (ry * nz - rz * ny) * s;
+      J[4] = -t * (rz * nx - rx * nz) * s;
       J[5] = -t * (rx * ny - ry * nx) * s;
       const float wr = w * r;
 #pragma unroll
@@ -650,13 +947,18 @@ __global__ void __launch_bounds__(256) k_reduce(WaveArgs a) {
 
 // ------------------------------------------------------------------ launch
 
+template <int TW, int TH, int MODEL>
+static cudaError_t launch_raster_m(const WaveArgs &a, int mode, cudaStream_t s) {
+  dim3 grid(a.tg.ntiles, a.n_poses);
+  if (mode == kRender) k_raster<TW, TH, kRender, MODEL><<<grid, kThreads, 0, s>>>(a);
+  else if (mode == kCost) k_raster<TW, TH, kCost, MODEL><<<grid, kThreads, 0, s>>>(a);
+  else k_raster<TW, TH, kCostGrad, MODEL><<<grid, kThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
 template <int TW, int TH>
 static cudaError_t launch_raster(const WaveArgs &a, int mode, cudaStream_t s) {
-  dim3 grid(a.tg.ntiles, a.n_poses);
-  if (mode == kRender) k_raster<TW, TH, kRender><<<grid, kThreads, 0, s>>>(a);
-  else if (mode == kCost) k_raster<TW, TH, kCost><<<grid, kThreads, 0, s>>>(a);
-  else k_raster<TW, TH, kCostGrad><<<grid, kThreads, 0, s>>>(a);
-  return cudaGetLastError();
+  return a.cam.model == 0 ? launch_raster_m<TW, TH, 0>(a, mode, s) : launch_raster_m<TW, TH, 1>(a, mode, s);
 }
 
 cudaError_t launch_wave(const WaveArgs &a, int mode, cudaStream_t s, cudaEvent_t *ev) {

@@ -36,7 +36,7 @@ struct WaveArgs {
   int *vis;           // wave: visible cluster ids per pose (n_clusters each)
   int *vis_count;     // wave: one counter per pose
   int *counts;        // wave: ntiles per pose
-  TriRec *bins;       // wave: ntiles * cap per pose
+  unsigned char *bins;  // wave: ntiles * cap records of tg.rec_bytes per pose
   double *partial;    // wave: ntiles * kNumVals per pose
   unsigned *status;   // device status word
   const int *skip;    // optional: non-zero means "skip this evaluation" (LM control)

@@ -100,13 +100,13 @@ extern "C" rm_status rm_cost_grad_noalloc(const rm_map *map, const rm_scan *scan
   if (off >= kScratchBytes)
     return na_fail(RM_EINVAL, "map or image too large for the static scratch (cluster list and tiles)");
   const size_t left = kScratchBytes - off;
-  long long cap = (long long)(left / ((size_t)a.tg.ntiles * sizeof(rmk::TriRec)));
+  long long cap = (long long)(left / ((size_t)a.tg.ntiles * a.tg.rec_bytes));
   if (cap > 4096) cap = 4096;
   if (cap < 256)
     return na_fail(RM_EINVAL, "image too large for the static scratch: fewer than 256 triangle "
                               "records per screen tile would fit");
   a.tg.cap = (int)cap;
-  rmk::TriRec *d_bins = reinterpret_cast<rmk::TriRec *>(take(sizeof(rmk::TriRec) * (size_t)cap * a.tg.ntiles));
+  unsigned char *d_bins = take((size_t)a.tg.rec_bytes * (size_t)cap * a.tg.ntiles);
 
   // everything that must start at zero is cleared by this call (counters are cleared by
   // the kernel launcher); the rest is written before it is read

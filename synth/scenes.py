@@ -382,12 +382,12 @@ def terrain_height(terrain, x, y):
 
 
 def _cast_terrain(terrain, origin, dirs):
-    """Ray-march the heightfield (the world the terrain mesh samples), then bisect."""
+    """Ray-march the heightfield (the world the terrain mesh samples), then bisect the first
+    crossing of every ray (vectorised)."""
     shape = dirs.shape[:-1]
     d = dirs.reshape(-1, 3)
     tmax = terrain["max_range"]
     step = terrain["march_step"]
-    t_prev = np.zeros(d.shape[0])
     best = np.full(d.shape[0], np.inf)
     alive = np.ones(d.shape[0], bool)
     t = step
@@ -396,18 +396,18 @@ def _cast_terrain(terrain, origin, dirs):
         p = origin[None, :] + t * d[idx]
         inside = (np.abs(p[:, 0]) <= terrain["half"]) & (np.abs(p[:, 1]) <= terrain["half"])
         below = inside & (p[:, 2] <= terrain_height(terrain, p[:, 0], p[:, 1]))
-        for k in np.nonzero(below)[0]:
-            i = idx[k]
-            a, b = t - step, t
+        hit = idx[below]
+        if hit.size:
+            a = np.full(hit.size, t - step)
+            b = np.full(hit.size, t)
             for _ in range(30):
                 m = 0.5 * (a + b)
-                q = origin + m * d[i]
-                if q[2] <= terrain_height(terrain, q[0], q[1]):
-                    b = m
-                else:
-                    a = m
-            best[i] = 0.5 * (a + b)
-        alive[idx[below]] = False
+                q = origin[None, :] + m[:, None] * d[hit]
+                under = q[:, 2] <= terrain_height(terrain, q[:, 0], q[:, 1])
+                b = np.where(under, m, b)
+                a = np.where(under, a, m)
+            best[hit] = 0.5 * (a + b)
+            alive[hit] = False
         t += step
     return best.reshape(shape)
 
@@ -484,6 +484,19 @@ def terrain_mesh(seed, half=100.0, n_buildings=40, target_fo=1_400_000, target_f
                 faces=np.ascontiguousarray(F.astype(np.int32)), labels=np.ascontiguousarray(L),
                 boxes=np.array([[lo, hi] for lo, hi in boxes]).reshape(-1, 2, 3), room=None,
                 terrain=terrain)
+
+
+def workload_lidar(seed=4000, target_fo=1_400_000, target_fu=600_000, n_panels=400, noise=0.02):
+    """Panoramic Lidar on a 200x200 m outdoor mesh: 1024 azimuths x 64 rings (+15..-25 deg),
+    range 1-80 m, sigma 2 cm; the start pose is 30 cm / 3 deg off the true pose."""
+    mesh = terrain_mesh(seed, target_fo=target_fo, target_fu=target_fu, n_panels=n_panels)
+    cam = cam_lidar_1024x64()
+    r = np.random.Generator(np.random.PCG64(seed + 1))
+    gt = terrain_pose(r, mesh)
+    depth, cls = synth_scan(mesh, cam, gt, r, sigma_abs=noise)
+    start = perturb_fixed(gt, r, 0.30, 3.0)
+    return dict(name="terrain-2M-lidar-1024x64", mesh=mesh, cam=cam, gt=gt, scan=(depth, cls),
+                start=start)
 
 
 def terrain_pose(rng, mesh: Mesh, height=1.8) -> np.ndarray:

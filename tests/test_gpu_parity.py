@@ -304,3 +304,81 @@ def test_align_matches_oracle_config1(c1):
     assert rep["e_ls_final"] < rep["e_ls_initial"]
     dgt, agt = _pose_gap(pg, gt)
     assert dgt < 0.01 and agt < 0.5
+
+
+# ---------------------------------------------------------------------------------------
+# ray-table (panoramic) camera
+# ---------------------------------------------------------------------------------------
+
+def _soup_around(seed, n=120):
+    r = cases.rng(seed)
+    c = r.normal(size=(n, 3))
+    c /= np.linalg.norm(c, axis=1, keepdims=True)
+    c *= r.uniform(2, 15, (n, 1))
+    v = c[:, None, :] + r.normal(scale=1.0, size=(n, 3, 3)) * r.uniform(0.1, 3.0, (n, 1, 1))
+    # a large ground triangle under the sensor (contains the down pole) and one over it
+    v = np.concatenate([v, np.array([[[-40, 3, -40], [40, 3, -40], [0, 3, 60]],
+                                     [[-30, -4, 30], [30, -4, 30], [0, -4, -50]]], float)])
+    vc = v.reshape(-1, 3).astype(np.float32)
+    return vc, np.arange(vc.shape[0], dtype=np.int32).reshape(-1, 3)
+
+
+@pytest.mark.parametrize("seed", [21, 22, 23])
+def test_raytable_render_bit_exact_soup(seed):
+    cam = cases.small_spherical(w=96, h=16)
+    vc, f = _soup_around(seed)
+    om = oracle.OracleMap(vc, f, np.zeros(len(f), np.uint8))
+    o = om.render(np.eye(4), cam)
+    gm = rm.Map(vc, f, np.zeros(len(f), np.uint8))
+    g = rm.render_depth(gm, np.eye(4)[None], rm.Intrinsics.from_camera(cam))
+    _same_render({"tri_id": g["tri_id"][0], "depth": g["depth"][0]}, o)
+    assert (~np.isnan(o["depth"])).mean() > 0.3
+
+
+def test_raytable_closed_box_gpu():
+    v, f = cases.closed_box((-6, -5, -2), (7, 4, 5), 0.9)
+    cam = cases.small_spherical(w=128, h=24)
+    om = oracle.OracleMap(v, f, np.zeros(len(f), np.uint8))
+    pose = synth.pose_from(np.array([0.5, 0.3, 0.1]), 0.7, 0.05, 0.02)
+    o = om.render(pose, cam)
+    gm = rm.Map(v, f, np.zeros(len(f), np.uint8))
+    g = rm.render_depth(gm, pose[None], rm.Intrinsics.from_camera(cam))
+    _same_render({"tri_id": g["tri_id"][0], "depth": g["depth"][0]}, o)
+    assert not torch.isnan(g["depth"]).any()
+
+
+@pytest.fixture(scope="module")
+def lidar():
+    w = synth.workload_lidar(seed=4100, target_fo=140_000, target_fu=60_000, n_panels=120)
+    om = oracle.OracleMap(w["mesh"].vertices, w["mesh"].faces, w["mesh"].labels)
+    gm = rm.Map(w["mesh"].vertices, w["mesh"].faces, w["mesh"].labels)
+    intr = rm.Intrinsics.from_camera(w["cam"])
+    return dict(w, om=om, gm=gm, intr=intr, gscan=rm.Scan.make(intr, *w["scan"]))
+
+
+def test_raytable_lidar_render_and_cost(lidar):
+    r = cases.rng(31)
+    poses = [lidar["gt"], lidar["start"], synth.perturb_fixed(lidar["gt"], r, 1.0, 10.0)]
+    g = rm.render_depth(lidar["gm"], np.stack(poses), lidar["intr"], want_bary=True)
+    gc = rm.cost_grad(lidar["gm"], lidar["gscan"], np.stack(poses))
+    sd, sc = lidar["scan"]
+    for k, P in enumerate(poses):
+        o = lidar["om"].render(P, lidar["cam"])
+        _same_render({"tri_id": g["tri_id"][k], "depth": g["depth"][k]}, o)
+        b64 = lidar["om"].barycentrics(P, lidar["cam"], o["keys"])
+        hit = ~np.isnan(o["depth"])
+        assert np.nanmax(np.abs(_np(g["bary"][k])[hit] - b64[hit])) < 5e-3
+        _check_cost(gc, lidar["om"].cost(P, lidar["cam"], sd, sc), k)
+
+
+def test_raytable_align_matches_oracle(lidar):
+    """From 30 cm / 3 deg the truncated surrogate gains inliers slowly: LM needs ~120
+    iterations to meet step_tol here; both sides must converge to the same pose."""
+    sd, sc = lidar["scan"]
+    pg, rep = rm.align(lidar["gm"], lidar["gscan"], lidar["start"], max_iters=200, step_tol=1e-7)
+    po, orep = lidar["om"].align(lidar["start"], lidar["cam"], sd, sc, max_iters=200, step_tol=1e-7)
+    assert rep["converged"] == 1 and orep["converged"] == 1, (rep, orep)
+    dt, da = _pose_gap(pg, po)
+    assert dt < 1e-3 and da < 1e-2, (dt, da, rep, orep)
+    dgt, agt = _pose_gap(pg, lidar["gt"])
+    assert dgt < 0.05 and agt < 0.5, (dgt, agt)
