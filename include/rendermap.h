@@ -206,6 +206,32 @@ rm_status rm_profile(rm_map *map, int32_t enable);
 rm_status rm_profile_read(rm_map *map, rm_kernel_time *out, int32_t cap, int32_t *n,
                           int64_t *launches);
 
+/* One problem of a heterogeneous batch: its own scan (camera model, size and arrays, host or
+ * device) and a pose (16 doubles, host or device): the pose evaluated by rm_cost_grad_batch,
+ * the start pose of rm_align_batch. */
+typedef struct {
+  rm_scan scan;
+  const double *pose;
+} rm_problem;
+
+/* rm_cost_grad for n problems that may differ in camera model, resolution and scan, in ONE
+ * persistent kernel: CTAs take (problem, phase, index) items from a device queue in order and
+ * wait, with bounded spins, only on items earlier in the queue (cluster culling -> triangle
+ * setup -> tile raster -> reduction per problem). Outputs as for rm_cost_grad, per problem
+ * (index k = problem). Screen tiles are 32x32. (Sec. III.C / Sec. V: many evaluations per
+ * scan match; batching them is this library's extension.) */
+rm_status rm_cost_grad_batch(rm_map *map, const rm_problem *problems, int32_t n,
+                             const rm_cost_params *params, const rm_cost_out *out, void *stream);
+
+/* rm_align for n problems at once: every LM iteration of every problem runs inside one
+ * persistent-kernel launch (each problem's next evaluation waits for its own LM step), so a
+ * whole tracking frame of mixed sensors is one launch. poses_out: n*16 doubles (host or
+ * device); reports: n entries (optional, host). Returns RM_ENOTCONV if any problem stopped at
+ * max_iters (its pose is still written). */
+rm_status rm_align_batch(rm_map *map, const rm_problem *problems, int32_t n,
+                         const rm_cost_params *params, const rm_align_params *lm,
+                         double *poses_out, rm_align_report *reports, void *stream);
+
 /* Cost and gradient of ONE pose without allocating (the paper has no counterpart; this is a
  * deployment variant of rm_cost_grad). For callers that must not allocate device memory
  * while they evaluate poses -- a real-time loop that may not call into the allocator after

@@ -5,6 +5,7 @@ pose is scored by rendering the map's z-buffer from it and comparing it per pixe
 observed range image by Table I (Sec. III.B, Eq. 1). All of it runs in hand-written sm_103a
 CUDA kernels behind the C ABI of include/rendermap.h; this package is the thin binding.
 """
-from .rendermap import (Intrinsics, Map, RenderMapCost, Scan, align, cost, cost_grad,  # noqa: F401
-                        cost_params, pose_retract, render_depth, OUTCOMES, RM_PINHOLE, RM_RAYTABLE)
+from .rendermap import (Intrinsics, Map, RenderMapCost, Scan, align, align_batch, cost,  # noqa: F401
+                        cost_grad, cost_grad_batch, cost_params, pose_retract, render_depth,
+                        OUTCOMES, RM_PINHOLE, RM_RAYTABLE)
 from ._native import RenderMapError, exported_symbols  # noqa: F401

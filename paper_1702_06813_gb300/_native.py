@@ -29,6 +29,10 @@ class rm_scan(ctypes.Structure):
     _fields_ = [("intr", rm_intrinsics), ("depth", ctypes.c_void_p), ("cls", ctypes.c_void_p)]
 
 
+class rm_problem(ctypes.Structure):
+    _fields_ = [("scan", rm_scan), ("pose", ctypes.c_void_p)]
+
+
 class rm_cost_params(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_float), ("w_fofo", ctypes.c_float), ("w_fofu", ctypes.c_float),
                 ("w_fufo", ctypes.c_float)]
@@ -75,6 +79,11 @@ _SIGS = {
     "rm_cost_grad": (ctypes.c_int, [_P, ctypes.POINTER(rm_scan), _P, ctypes.c_int32,
                                     ctypes.POINTER(rm_cost_params), ctypes.POINTER(rm_cost_out), _P]),
     "rm_pose_retract": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P, _P, _P]),
+    "rm_cost_grad_batch": (ctypes.c_int, [_P, ctypes.POINTER(rm_problem), ctypes.c_int32,
+                                          ctypes.POINTER(rm_cost_params), ctypes.POINTER(rm_cost_out), _P]),
+    "rm_align_batch": (ctypes.c_int, [_P, ctypes.POINTER(rm_problem), ctypes.c_int32,
+                                      ctypes.POINTER(rm_cost_params), ctypes.POINTER(rm_align_params), _P,
+                                      ctypes.POINTER(rm_align_report), _P]),
     "rm_align": (ctypes.c_int, [_P, ctypes.POINTER(rm_scan), _P, ctypes.POINTER(rm_cost_params),
                                 ctypes.POINTER(rm_align_params), _P, ctypes.POINTER(rm_align_report), _P]),
     "rm_cost_grad_noalloc": (ctypes.c_int, [_P, ctypes.POINTER(rm_scan), _P,

@@ -520,6 +520,246 @@ rm_status run_eval(rm_map *m, const EvalReq &r, cudaStream_t s) {
 
 }  // namespace
 
+namespace {
+
+// Shared driver of rm_cost_grad_batch (lm == nullptr) and rm_align_batch.
+rm_status run_batch(rm_map *m, const rm_problem *probs, int n, const rm_cost_params *prm,
+                    const rm_align_params *lm, const rm_cost_out *out, double *poses_out,
+                    rm_align_report *reps, cudaStream_t s) {
+  if (n < 0) return fail(RM_EINVAL, "n < 0");
+  if (n == 0) return RM_OK;
+  if (!probs || !prm) return fail(RM_EINVAL, "NULL argument");
+  if (!(prm->eps >= 0.0f)) return fail(RM_EINVAL, "eps must be >= 0");
+  if (lm && (lm->max_iters < 0 || lm->max_iters > 100000)) return fail(RM_EINVAL, "max_iters out of range");
+  if (lm && !poses_out) return fail(RM_EINVAL, "poses_out is NULL");
+  for (int p = 0; p < n; ++p) {
+    RM_TRY(check_intr(&probs[p].scan.intr));
+    if (!probs[p].scan.depth || !probs[p].scan.cls || !probs[p].pose)
+      return fail(RM_EINVAL, "problem " + std::to_string(p) + ": NULL scan array or pose");
+  }
+  RM_CK(cudaSetDevice(m->device));
+  const int K = lm ? lm->max_iters : 0;
+  const int nc = m->n_clusters;
+  const int ncull = (nc + 255) / 256;
+  const int nwork = std::min(64, std::max(1, nc / 512));
+  for (int attempt = 0;; ++attempt) {
+    std::vector<TileGeom> tg(n);
+    std::vector<long long> P(n);
+    size_t tiles_total = 0, bins_bytes = 0, px_total = 0, rays_total = 0;
+    for (int p = 0; p < n; ++p) {
+      const rm_intrinsics *in = &probs[p].scan.intr;
+      tg[p].tw = tg[p].th = 32;
+      tg[p].ntx = (in->width + 31) / 32;
+      tg[p].nty = (in->height + 31) / 32;
+      tg[p].ntiles = tg[p].ntx * tg[p].nty;
+      tg[p].cap = m->cap;
+      tg[p].rec_bytes = in->model == RM_RAYTABLE ? (int)sizeof(rmk::RayRec) : (int)sizeof(TriRec);
+      P[p] = (long long)in->width * in->height;
+      tiles_total += tg[p].ntiles;
+      bins_bytes += align_up((size_t)tg[p].ntiles * tg[p].cap * tg[p].rec_bytes, 256);
+      px_total += align_up((size_t)P[p], 64);
+      if (in->model == RM_RAYTABLE) rays_total += 3 * (size_t)P[p];
+    }
+    // queue: per evaluation, groups of 8 problems, phase by phase within a group
+    std::vector<int4> items;
+    for (int it = 0; it <= K; ++it)
+      for (int g0 = 0; g0 < n; g0 += 8) {
+        const int g1 = std::min(n, g0 + 8);
+        for (int p = g0; p < g1; ++p)
+          for (int k = 0; k < ncull; ++k) items.push_back(make_int4(p, 0, k, it));
+        for (int p = g0; p < g1; ++p)
+          for (int k = 0; k < nwork; ++k) items.push_back(make_int4(p, 1, k, it));
+        for (int p = g0; p < g1; ++p)
+          for (int k = 0; k < tg[p].ntiles; ++k) items.push_back(make_int4(p, 2, k, it));
+        for (int p = g0; p < g1; ++p) items.push_back(make_int4(p, 3, 0, it));
+      }
+    std::vector<int> need(3 * (size_t)n);
+    for (int p = 0; p < n; ++p) {
+      need[3 * p] = ncull;
+      need[3 * p + 1] = nwork;
+      need[3 * p + 2] = tg[p].ntiles;
+    }
+    // ---- plan and carve the arena
+    auto layout = [&](Carver &cv, bool carve, WaveArgs **d_args, int4 **d_items, int **d_next,
+                      int **d_done, int **d_need, float **d_M, int **d_skip, double **d_poses,
+                      rmk::LMState **d_lm, int **d_vcount, int **d_vis, int **d_counts,
+                      double **d_partial, unsigned char **d_bins, float **d_sd, uint8_t **d_sc,
+                      float **d_rays, long long **r_counts, long long **r_et, double **r_els,
+                      double **r_grad, double **r_jtj) {
+      (void)carve;
+      *d_args = cv.take<WaveArgs>(n);
+      *d_items = cv.take<int4>(items.size());
+      *d_next = cv.take<int>(1);
+      *d_done = cv.take<int>(4 * (size_t)n);
+      *d_need = cv.take<int>(3 * (size_t)n);
+      *d_M = cv.take<float>(12 * (size_t)n);
+      *d_skip = cv.take<int>(n);
+      *d_poses = cv.take<double>(16 * (size_t)n);
+      *d_lm = cv.take<rmk::LMState>(n);
+      *d_vcount = cv.take<int>(n);
+      *d_vis = cv.take<int>((size_t)n * std::max(nc, 1));
+      *d_counts = cv.take<int>(tiles_total);
+      *d_partial = cv.take<double>(tiles_total * rmk::kNumVals);
+      *d_bins = cv.take<unsigned char>(bins_bytes);
+      *d_sd = cv.take<float>(px_total);
+      *d_sc = cv.take<uint8_t>(px_total);
+      *d_rays = cv.take<float>(std::max<size_t>(rays_total, 1));
+      *r_counts = cv.take<long long>(6 * (size_t)n);
+      *r_et = cv.take<long long>(n);
+      *r_els = cv.take<double>(n);
+      *r_grad = cv.take<double>(6 * (size_t)n);
+      *r_jtj = cv.take<double>(21 * (size_t)n);
+    };
+    WaveArgs *d_args; int4 *d_items; int *d_next, *d_done, *d_need, *d_skip, *d_vcount, *d_vis, *d_counts;
+    float *d_M, *d_sd, *d_rays; double *d_poses, *d_partial, *r_els, *r_grad, *r_jtj; rmk::LMState *d_lm;
+    unsigned char *d_bins; uint8_t *d_sc; long long *r_counts, *r_et;
+    Carver plan{nullptr};
+    layout(plan, false, &d_args, &d_items, &d_next, &d_done, &d_need, &d_M, &d_skip, &d_poses, &d_lm,
+           &d_vcount, &d_vis, &d_counts, &d_partial, &d_bins, &d_sd, &d_sc, &d_rays, &r_counts, &r_et,
+           &r_els, &r_grad, &r_jtj);
+    RM_TRY(ensure_arena(m, plan.off, s));
+    Carver cv{m->arena};
+    layout(cv, true, &d_args, &d_items, &d_next, &d_done, &d_need, &d_M, &d_skip, &d_poses, &d_lm,
+           &d_vcount, &d_vis, &d_counts, &d_partial, &d_bins, &d_sd, &d_sc, &d_rays, &r_counts, &r_et,
+           &r_els, &r_grad, &r_jtj);
+    // ---- per-problem arguments and inputs
+    std::vector<WaveArgs> args(n);
+    size_t t_off = 0, b_off = 0, px_off = 0, r_off = 0;
+    for (int p = 0; p < n; ++p) {
+      const rm_scan &sc = probs[p].scan;
+      const rm_intrinsics *in = &sc.intr;
+      float *rays = nullptr;
+      if (in->model == RM_RAYTABLE) {
+        rays = d_rays + r_off;
+        r_off += 3 * (size_t)P[p];
+        RM_CK(cudaMemcpyAsync(rays, in->rays, sizeof(float) * 3 * P[p],
+                              on_device(in->rays) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+      }
+      RM_CK(cudaMemcpyAsync(d_sd + px_off, sc.depth, sizeof(float) * P[p],
+                            on_device(sc.depth) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+      RM_CK(cudaMemcpyAsync(d_sc + px_off, sc.cls, (size_t)P[p],
+                            on_device(sc.cls) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+      RM_CK(cudaMemcpyAsync(d_poses + 16 * (size_t)p, probs[p].pose, sizeof(double) * 16,
+                            on_device(probs[p].pose) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+      WaveArgs &a = args[p];
+      a = WaveArgs{};
+      a.cam = make_cam(in, rays);
+      a.tg = tg[p];
+      a.V = (int)m->V;
+      a.T = m->T;
+      a.n_poses = 1;
+      a.wave_base = 0;
+      a.v = m->d_v;
+      a.faces = m->d_faces;
+      a.planes = m->d_planes;
+      set_clusters(m, a);
+      a.Ms = d_M + 12 * (size_t)p;
+      a.vis = d_vis + (size_t)p * std::max(nc, 1);
+      a.vis_count = d_vcount + p;
+      a.counts = d_counts + t_off;
+      a.bins = d_bins + b_off;
+      a.partial = d_partial + t_off * rmk::kNumVals;
+      a.status = m->d_status;
+      a.skip = d_skip + p;
+      a.scan_depth = d_sd + px_off;
+      a.scan_cls = d_sc + px_off;
+      a.prm = {prm->eps, prm->w_fofo, prm->w_fofu, prm->w_fufo};
+      a.res_counts = r_counts + 6 * (size_t)p;
+      a.res_etable = r_et + p;
+      a.res_els = r_els + p;
+      a.res_grad = r_grad + 6 * (size_t)p;
+      a.res_jtj = r_jtj + 21 * (size_t)p;
+      t_off += tg[p].ntiles;
+      b_off += align_up((size_t)tg[p].ntiles * tg[p].cap * tg[p].rec_bytes, 256);
+      px_off += align_up((size_t)P[p], 64);
+    }
+    RM_CK(cudaMemcpyAsync(d_args, args.data(), sizeof(WaveArgs) * n, cudaMemcpyHostToDevice, s));
+    RM_CK(cudaMemcpyAsync(d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, s));
+    RM_CK(cudaMemcpyAsync(d_need, need.data(), sizeof(int) * need.size(), cudaMemcpyHostToDevice, s));
+    RM_CK(cudaMemsetAsync(d_next, 0, sizeof(int), s));
+    RM_CK(cudaMemsetAsync(d_done, 0, sizeof(int) * 4 * n, s));
+    RM_CK(cudaMemsetAsync(d_skip, 0, sizeof(int) * n, s));
+    RM_CK(cudaMemsetAsync(d_vcount, 0, sizeof(int) * n, s));
+    RM_CK(cudaMemsetAsync(d_counts, 0, sizeof(int) * tiles_total, s));
+    rmk::LMArgs la{};
+    la.cx = m->centre[0];
+    la.cy = m->centre[1];
+    la.cz = m->centre[2];
+    if (lm) {
+      la.lambda0 = lm->lambda0;
+      la.lambda_up = lm->lambda_up;
+      la.lambda_down = lm->lambda_down;
+      la.step_tol = lm->step_tol;
+      RM_CK(rmk::launch_lm_init_batch(d_lm, d_poses, n, la, d_M, d_skip, s));
+    } else {
+      RM_CK(rmk::launch_pose_to_m(d_poses, n, m->centre[0], m->centre[1], m->centre[2], d_M, s));
+    }
+    rmk::BatchArgs b{};
+    b.probs = d_args;
+    b.items = d_items;
+    b.n_items = (int)items.size();
+    b.next = d_next;
+    b.done = d_done;
+    b.need = d_need;
+    b.lm = lm ? d_lm : nullptr;
+    b.Ms = d_M;
+    b.skip = d_skip;
+    b.lmargs = la;
+    b.lm_iters = K;
+    b.status = m->d_status;
+    b.spin_limit = 1ll << 32;
+    const int grid = rmk::persist_grid(m->device);
+    if (grid <= 0) return fail(RM_ECUDA, "could not size the persistent grid");
+    RM_CK(rmk::launch_persist(b, grid, s));
+    m->launches += 2;
+    bool host_out = false;
+    std::vector<rmk::LMState> hs;
+    if (lm) {
+      hs.resize(n);
+      RM_CK(cudaMemcpyAsync(hs.data(), d_lm, sizeof(rmk::LMState) * n, cudaMemcpyDeviceToHost, s));
+    } else if (out) {
+      RM_TRY(copy_out(out->counts, r_counts, sizeof(long long) * 6 * n, s, &host_out));
+      RM_TRY(copy_out(out->e_table, r_et, sizeof(long long) * n, s, &host_out));
+      RM_TRY(copy_out(out->e_ls, r_els, sizeof(double) * n, s, &host_out));
+      RM_TRY(copy_out(out->grad, r_grad, sizeof(double) * 6 * n, s, &host_out));
+      RM_TRY(copy_out(out->jtj, r_jtj, sizeof(double) * 21 * n, s, &host_out));
+    }
+    unsigned st = 0;
+    RM_TRY(read_status(m, s, &st));  // synchronises the stream
+    if (st & rmk::kStatusTimeout) return fail(RM_ETIMEOUT, "a device-side wait ran out of time");
+    if (st & rmk::kStatusOverflow) {
+      if (m->cap >= (1 << 22) || attempt > 12)
+        return fail(RM_EOVERFLOW, "screen-tile bin overflow at the largest capacity");
+      m->cap *= 2;
+      continue;
+    }
+    if (!lm) return RM_OK;
+    bool all_conv = true;
+    std::vector<double> pout(16 * (size_t)n);
+    for (int p = 0; p < n; ++p) {
+      std::memcpy(&pout[16 * (size_t)p], hs[p].T, sizeof(double) * 16);
+      all_conv = all_conv && hs[p].converged;
+      if (reps) {
+        reps[p].iters = hs[p].iters;
+        reps[p].accepted = hs[p].accepted;
+        reps[p].converged = hs[p].converged;
+        reps[p].reserved = 0;
+        reps[p].e_ls_initial = hs[p].e_ls0;
+        reps[p].e_ls_final = hs[p].e;
+        reps[p].e_table_initial = hs[p].e_table0;
+        reps[p].e_table_final = hs[p].e_table;
+      }
+    }
+    if (on_device(poses_out))
+      RM_CK(cudaMemcpy(poses_out, pout.data(), sizeof(double) * 16 * n, cudaMemcpyHostToDevice));
+    else
+      std::memcpy(poses_out, pout.data(), sizeof(double) * 16 * n);
+    return all_conv ? RM_OK : fail(RM_ENOTCONV, "a problem reached max_iters before step_tol");
+  }
+}
+
+}  // namespace
+
 namespace rmapi {
 
 rm_status wave_inputs(const rm_map *m, const rm_intrinsics *in, WaveArgs *a, double centre[3]) {
@@ -776,6 +1016,22 @@ rm_status rm_profile_read(rm_map *m, rm_kernel_time *out, int32_t cap, int32_t *
   if (n) *n = k;
   if (launches) *launches = m->launches;
   return RM_OK;
+}
+
+rm_status rm_cost_grad_batch(rm_map *m, const rm_problem *probs, int32_t n,
+                             const rm_cost_params *prm, const rm_cost_out *out, void *stream) {
+  if (!m) return fail(RM_EINVAL, "map is NULL");
+  std::lock_guard<std::mutex> lk(m->mu);
+  return run_batch(m, probs, n, prm, nullptr, out, nullptr, nullptr, (cudaStream_t)stream);
+}
+
+rm_status rm_align_batch(rm_map *m, const rm_problem *probs, int32_t n, const rm_cost_params *prm,
+                         const rm_align_params *lm, double *poses_out, rm_align_report *reps,
+                         void *stream) {
+  if (!m) return fail(RM_EINVAL, "map is NULL");
+  if (!lm) return fail(RM_EINVAL, "lm is NULL");
+  std::lock_guard<std::mutex> lk(m->mu);
+  return run_batch(m, probs, n, prm, lm, nullptr, poses_out, reps, (cudaStream_t)stream);
 }
 
 rm_status rm_status_sync(rm_map *m, void *stream) {

@@ -140,15 +140,22 @@ __device__ __forceinline__ bool cluster_visible(const DevCam &cam, const float *
   return true;
 }
 
-__global__ void __launch_bounds__(256) k_cull(WaveArgs a) {
-  if (a.skip && *a.skip) return;
-  const int q = blockIdx.y;
+// Reads of data that another CTA of the same (persistent) kernel may have written bypass L1.
+__device__ __forceinline__ int ld_cg(const int *p) { return __ldcg(p); }
+__device__ __forceinline__ bool skipped(const WaveArgs &a) { return a.skip && __ldcg(a.skip) != 0; }
+
+__device__ __forceinline__ void load_m(const WaveArgs &a, int q, float *M) {
   const float *Mg = a.Ms + 12 * (long long)(a.wave_base + q);
-  float M[12];
 #pragma unroll
-  for (int k = 0; k < 12; ++k) M[k] = Mg[k];
+  for (int k = 0; k < 12; ++k) M[k] = __ldcg(Mg + k);
+}
+
+// Clusters chunk*256 + threadIdx.x of pose q: test, and append the visible ones.
+__device__ __forceinline__ void cull_block(const WaveArgs &a, int q, int chunk) {
+  float M[12];
+  load_m(a, q, M);
   int *vis = a.vis + (long long)q * a.n_clusters;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = chunk * blockDim.x + threadIdx.x;
   const bool keep = c < a.n_clusters && cluster_visible(a.cam, M, a.cl_sphere[c]);
   // warp-aggregated append
   const unsigned m = __ballot_sync(0xffffffffu, keep);
@@ -158,6 +165,11 @@ __global__ void __launch_bounds__(256) k_cull(WaveArgs a) {
   if (lane == leader) base = atomicAdd(&a.vis_count[q], __popc(m));
   base = __shfl_sync(0xffffffffu, base, leader);
   if (keep) vis[base + __popc(m & ((1u << lane) - 1u))] = c;
+}
+
+__global__ void __launch_bounds__(256) k_cull(WaveArgs a) {
+  if (skipped(a)) return;
+  cull_block(a, blockIdx.y, blockIdx.x);
 }
 
 // ------------------------------------------------------------------ triangle setup + binning
@@ -319,27 +331,31 @@ constexpr int kClusterMax = 64;  // vertices and triangles per cluster
 // One warp per visible cluster: its vertices are transformed and snapped once into shared
 // memory, then each lane sets up triangles (near-plane cut, culling, depth plane) and
 // appends them to the screen-tile bins.
-__global__ void __launch_bounds__(256) k_setup(WaveArgs a) {
-  __shared__ float4 s_vc[8][kClusterMax];
-  __shared__ int2 s_vs[8][kClusterMax];
-  __shared__ int s_gid[8][kClusterMax];
-  __shared__ float4 s_dir[8][kClusterMax];  // ray table: unit direction and azimuth
-  if (a.skip && *a.skip) return;
-  const int q = blockIdx.y;
+struct SetupSmem {
+  float4 s_vc[8][kClusterMax];
+  int2 s_vs[8][kClusterMax];
+  int s_gid[8][kClusterMax];
+  float4 s_dir[8][kClusterMax];  // ray table: unit direction and azimuth
+};
+
+__device__ __forceinline__ void setup_block(const WaveArgs &a, int q, int worker, int nworkers,
+                                            SetupSmem &sm) {
+  float4(*s_vc)[kClusterMax] = sm.s_vc;
+  int2(*s_vs)[kClusterMax] = sm.s_vs;
+  int(*s_gid)[kClusterMax] = sm.s_gid;
+  float4(*s_dir)[kClusterMax] = sm.s_dir;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const float *Mg = a.Ms + 12 * (long long)(a.wave_base + q);
   float M[12];
-#pragma unroll
-  for (int k = 0; k < 12; ++k) M[k] = Mg[k];
-  const int nvis = a.vis_count[q];
+  load_m(a, q, M);
+  const int nvis = ld_cg(&a.vis_count[q]);
   const int *vis = a.vis + (long long)q * a.n_clusters;
   int *counts = a.counts + (long long)q * a.tg.ntiles;
   unsigned char *bins = a.bins + (long long)q * a.tg.ntiles * a.tg.cap * a.tg.rec_bytes;
   const int W = a.cam.W, H = a.cam.H;
   const float near_m = a.cam.near_m;
   const bool raytable = a.cam.model != 0;
-  for (int ci = blockIdx.x * 8 + warp; ci < nvis; ci += gridDim.x * 8) {
-    const int4 info = a.cl_info[vis[ci]];  // vert offset, tri offset, nv, nt
+  for (int ci = worker * 8 + warp; ci < nvis; ci += nworkers * 8) {
+    const int4 info = a.cl_info[ld_cg(&vis[ci])];  // vert offset, tri offset, nv, nt
     for (int k = lane; k < info.z; k += 32) {
       const int gv = a.cl_verts[info.x + k];
       const float4 v = a.v[gv];
@@ -428,6 +444,12 @@ __global__ void __launch_bounds__(256) k_setup(WaveArgs a) {
     }
     __syncwarp();
   }
+}
+
+__global__ void __launch_bounds__(256) k_setup(WaveArgs a) {
+  __shared__ SetupSmem sm;
+  if (skipped(a)) return;
+  setup_block(a, blockIdx.y, blockIdx.x, gridDim.x, sm);
 }
 
 // ------------------------------------------------------------------ raster + epilogue
@@ -689,30 +711,41 @@ __device__ __forceinline__ bool raster_tile_ray(unsigned long long *zk, RayRec *
 #define RM_RASTER_MIN_BLOCKS 4  // resident CTAs per SM the register budget is sized for
 #endif
 
-template <int TW, int TH, int MODE, int MODEL>
-__global__ void __launch_bounds__(kThreads, RM_RASTER_MIN_BLOCKS) k_raster(WaveArgs a) {
-  constexpr int NP = TW * TH;
-  constexpr int NW = kThreads / 32;
+template <int NP, int MODEL>
+struct RasterSmem {
+  static constexpr int NW = kThreads / 32;
   // pinhole: 512 records + their int4 edge headers; ray table: 384 records + the tile's rays
-  constexpr int kBuf = MODEL == 0 ? kRecMaxPinhole * (48 + 16) : kRecMaxRay * 64 + 12 * NP;
-  __shared__ unsigned long long zk[NP];
-  __shared__ __align__(128) unsigned char sbuf[kBuf];
-  __shared__ int S[(MODEL == 0 ? kRecMaxPinhole : kRecMaxRay) + 1];
-  __shared__ int wtot[NW];
-  __shared__ __align__(8) unsigned long long bar[1];
-  __shared__ float red[NW][28];
-  __shared__ int redc[NW][6];
+  static constexpr int kBuf = MODEL == 0 ? kRecMaxPinhole * (48 + 16) : kRecMaxRay * 64 + 12 * NP;
+  unsigned long long zk[NP];
+  alignas(128) unsigned char sbuf[kBuf];
+  int S[(MODEL == 0 ? kRecMaxPinhole : kRecMaxRay) + 1];
+  int wtot[NW];
+  unsigned long long bar[1];
+  float red[NW][28];
+  int redc[NW][6];
+};
 
-  if (a.skip && *a.skip) return;
+// One (pose q, tile) of the z-buffer and its fused epilogue. Returns false on a timed-out wait.
+template <int TW, int TH, int MODE, int MODEL>
+__device__ __forceinline__ void raster_block(const WaveArgs &a, int tile, int q,
+                                             RasterSmem<TW * TH, MODEL> &sm) {
+  constexpr int NP = TW * TH;
+  unsigned long long *zk = sm.zk;
+  unsigned char *sbuf = sm.sbuf;
+  int *S = sm.S;
+  int *wtot = sm.wtot;
+  unsigned long long *bar = sm.bar;
+  float(*red)[28] = sm.red;
+  int(*redc)[6] = sm.redc;
   const int tid = threadIdx.x;
-  const int tile = blockIdx.x, q = blockIdx.y, g = a.wave_base + q;
+  const int g = a.wave_base + q;
   const int ox = (tile % a.tg.ntx) * TW, oy = (tile / a.tg.ntx) * TH;
   const int W = a.cam.W, H = a.cam.H;
   const int xe = min(ox + TW, W) - 1, ye = min(oy + TH, H) - 1;
 
   for (int p = tid; p < NP; p += kThreads) zk[p] = kKeyEmpty;
   const long long bin = (long long)q * a.tg.ntiles + tile;
-  const int n = min(a.counts[bin], a.tg.cap);
+  const int n = min(ld_cg(&a.counts[bin]), a.tg.cap);
   float *rx = nullptr, *ry = nullptr, *rz = nullptr;
   if (MODEL != 0) {
     rx = reinterpret_cast<float *>(sbuf + kRecMaxRay * 64);
@@ -751,6 +784,7 @@ __global__ void __launch_bounds__(kThreads, RM_RASTER_MIN_BLOCKS) k_raster(WaveA
     if (tid == 0) atomicOr(a.status, kStatusTimeout);
     return;
   }
+  __syncthreads();
 
   const long long P = (long long)W * H;
   if (MODE == kRender) {
@@ -774,9 +808,8 @@ __global__ void __launch_bounds__(kThreads, RM_RASTER_MIN_BLOCKS) k_raster(WaveA
       if (a.tri_id) a.tri_id[pix] = (int)id;
       if (a.bary) {
         const int4 f = a.faces[id];
-        const float *Mg = a.Ms + 12 * (long long)g;
         float M[12];
-        for (int k = 0; k < 12; ++k) M[k] = Mg[k];
+        load_m(a, q, M);
         const float4 w0 = a.v[f.x], w1 = a.v[f.y], w2 = a.v[f.z];
         const float3 v0 = xform(M, w0.x, w0.y, w0.z), v1 = xform(M, w1.x, w1.y, w1.z),
                      v2 = xform(M, w2.x, w2.y, w2.z);
@@ -810,13 +843,16 @@ __global__ void __launch_bounds__(kThreads, RM_RASTER_MIN_BLOCKS) k_raster(WaveA
   float acc[28];
 #pragma unroll
   for (int k = 0; k < 28; ++k) acc[k] = 0.0f;
-  const float *Mg = a.Ms + 12 * (long long)g;
   float R[9];
+  {
+    float M[12];
+    load_m(a, q, M);
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    R[3 * k] = Mg[4 * k];
-    R[3 * k + 1] = Mg[4 * k + 1];
-    R[3 * k + 2] = Mg[4 * k + 2];
+    for (int k = 0; k < 3; ++k) {
+      R[3 * k] = M[4 * k];
+      R[3 * k + 1] = M[4 * k + 1];
+      R[3 * k + 2] = M[4 * k + 2];
+    }
   }
   const float eps = a.prm.eps;
   const float ifx = 1.0f / a.cam.fx, ify = 1.0f / a.cam.fy;
@@ -920,17 +956,22 @@ __global__ void __launch_bounds__(kThreads, RM_RASTER_MIN_BLOCKS) k_raster(WaveA
   }
 }
 
+template <int TW, int TH, int MODE, int MODEL>
+__global__ void __launch_bounds__(kThreads, RM_RASTER_MIN_BLOCKS) k_raster(WaveArgs a) {
+  __shared__ RasterSmem<TW * TH, MODEL> sm;
+  if (skipped(a)) return;
+  raster_block<TW, TH, MODE, MODEL>(a, blockIdx.x, blockIdx.y, sm);
+}
+
 // Per pose: sum the per-tile partials. Warp w reduces values w, w+8, ...; lane l sums tiles
 // l, l+32, ... and a butterfly combines the lanes, so the order is fixed run to run.
-__global__ void __launch_bounds__(256) k_reduce(WaveArgs a) {
-  if (a.skip && *a.skip) return;
-  __shared__ double vals[kNumVals];
-  const int q = blockIdx.x, g = a.wave_base + q;
+__device__ __forceinline__ void reduce_block(const WaveArgs &a, int q, double *vals) {
+  const int g = a.wave_base + q;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const double *base = a.partial + (long long)q * a.tg.ntiles * kNumVals;
   for (int k = warp; k < kNumVals; k += 8) {
     double s = 0.0;
-    for (int t = lane; t < a.tg.ntiles; t += 32) s += base[(long long)t * kNumVals + k];
+    for (int t = lane; t < a.tg.ntiles; t += 32) s += __ldcg(base + (long long)t * kNumVals + k);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
     if (lane == 0) vals[k] = s;
@@ -943,6 +984,12 @@ __global__ void __launch_bounds__(256) k_reduce(WaveArgs a) {
   if (k >= 13 && k < kNumVals && a.res_jtj) a.res_jtj[21 * (long long)g + (k - 13)] = vals[k];
   if (k == 0 && a.res_etable)
     a.res_etable[g] = (long long)(vals[1] + vals[3] + vals[5]) - (long long)(vals[0] + vals[2] + vals[4]);
+}
+
+__global__ void __launch_bounds__(256) k_reduce(WaveArgs a) {
+  __shared__ double vals[kNumVals];
+  if (skipped(a)) return;
+  reduce_block(a, blockIdx.x, vals);
 }
 
 // ------------------------------------------------------------------ launch
@@ -1167,65 +1214,208 @@ __device__ bool lm_solve_dev(const double *jtj, const double *g, double lambda, 
   return true;
 }
 
-__global__ void k_lm_init(LMState *st, const double *T0, LMArgs a, float *M, int *skip) {
-  for (int k = 0; k < 16; ++k) st->T[k] = st->Tc[k] = T0[k];
-  st->lambda = a.lambda0;
-  st->iters = st->accepted = st->converged = st->done = 0;
-  st->have_candidate = 1;
-  pose_to_m(T0, a.cx, a.cy, a.cz, M);
-  *skip = 0;
+__device__ void lm_take_initial_dev(LMState &st, const long long *counts, const double *els,
+                                    const double *grad, const double *jtj) {
+  st.e = els[0];
+  st.e_ls0 = els[0];
+  for (int k = 0; k < 6; ++k) st.g[k] = grad[k];
+  for (int k = 0; k < 21; ++k) st.H[k] = jtj[k];
+  st.e_table = (counts[1] + counts[3] + counts[5]) - (counts[0] + counts[2] + counts[4]);
+  st.e_table0 = st.e_table;
 }
 
-__global__ void k_lm_take_initial(LMState *st, const long long *counts, const double *els,
-                                  const double *grad, const double *jtj) {
-  st->e = els[0];
-  st->e_ls0 = els[0];
-  for (int k = 0; k < 6; ++k) st->g[k] = grad[k];
-  for (int k = 0; k < 21; ++k) st->H[k] = jtj[k];
-  st->e_table = (counts[1] + counts[3] + counts[5]) - (counts[0] + counts[2] + counts[4]);
-  st->e_table0 = st->e_table;
-}
-
-__global__ void k_lm_propose(LMState *st, LMArgs a, float *M, int *skip) {
-  if (st->done) {
+// Solve for the next step; writes the candidate's matrix and clears *skip, or sets *skip when
+// there is nothing to evaluate (converged, or a damped system that is not positive definite).
+__device__ void lm_propose_dev(LMState &st, const LMArgs &a, float *M, int *skip) {
+  if (st.done) {
     *skip = 1;
     return;
   }
   double dx[6];
-  if (!lm_solve_dev(st->H, st->g, st->lambda, dx)) {
-    st->lambda *= a.lambda_up;
-    st->iters += 1;
+  if (!lm_solve_dev(st.H, st.g, st.lambda, dx)) {
+    st.lambda *= a.lambda_up;
+    st.iters += 1;
     *skip = 1;
     return;
   }
   double nrm = 0.0;
   for (int k = 0; k < 6; ++k) nrm += dx[k] * dx[k];
   if (sqrt(nrm) < a.step_tol) {
-    st->done = 1;
-    st->converged = 1;
+    st.done = 1;
+    st.converged = 1;
     *skip = 1;
     return;
   }
-  se3_right_dev(st->T, dx, st->Tc);
-  pose_to_m(st->Tc, a.cx, a.cy, a.cz, M);
+  se3_right_dev(st.T, dx, st.Tc);
+  pose_to_m(st.Tc, a.cx, a.cy, a.cz, M);
   *skip = 0;
+}
+
+// Accept the evaluated candidate if it lowered the surrogate (nothing when it was skipped).
+__device__ void lm_accept_dev(LMState &st, const LMArgs &a, const long long *counts,
+                              const double *els, const double *grad, const double *jtj,
+                              bool was_skipped) {
+  if (was_skipped) return;
+  st.iters += 1;
+  if (els[0] < st.e) {
+    for (int k = 0; k < 16; ++k) st.T[k] = st.Tc[k];
+    st.e = els[0];
+    for (int k = 0; k < 6; ++k) st.g[k] = grad[k];
+    for (int k = 0; k < 21; ++k) st.H[k] = jtj[k];
+    st.e_table = (counts[1] + counts[3] + counts[5]) - (counts[0] + counts[2] + counts[4]);
+    st.lambda /= a.lambda_down;
+    st.accepted += 1;
+  } else {
+    st.lambda *= a.lambda_up;
+  }
+}
+
+__device__ void lm_init_dev(LMState &st, const double *T0, const LMArgs &a, float *M, int *skip) {
+  for (int k = 0; k < 16; ++k) st.T[k] = st.Tc[k] = T0[k];
+  st.lambda = a.lambda0;
+  st.iters = st.accepted = st.converged = st.done = 0;
+  st.have_candidate = 1;
+  pose_to_m(T0, a.cx, a.cy, a.cz, M);
+  *skip = 0;
+}
+
+__global__ void k_lm_init(LMState *st, const double *T0, LMArgs a, float *M, int *skip) {
+  lm_init_dev(*st, T0, a, M, skip);
+}
+
+__global__ void k_lm_take_initial(LMState *st, const long long *counts, const double *els,
+                                  const double *grad, const double *jtj) {
+  lm_take_initial_dev(*st, counts, els, grad, jtj);
+}
+
+__global__ void k_lm_propose(LMState *st, LMArgs a, float *M, int *skip) {
+  lm_propose_dev(*st, a, M, skip);
 }
 
 __global__ void k_lm_accept(LMState *st, LMArgs a, const long long *counts, const double *els,
                             const double *grad, const double *jtj, int *skip) {
-  if (*skip) return;
-  st->iters += 1;
-  if (els[0] < st->e) {
-    for (int k = 0; k < 16; ++k) st->T[k] = st->Tc[k];
-    st->e = els[0];
-    for (int k = 0; k < 6; ++k) st->g[k] = grad[k];
-    for (int k = 0; k < 21; ++k) st->H[k] = jtj[k];
-    st->e_table = (counts[1] + counts[3] + counts[5]) - (counts[0] + counts[2] + counts[4]);
-    st->lambda /= a.lambda_down;
-    st->accepted += 1;
-  } else {
-    st->lambda *= a.lambda_up;
+  lm_accept_dev(*st, a, counts, els, grad, jtj, *skip != 0);
+}
+
+// ------------------------------------------------------------------ persistent batch kernel
+
+__global__ void k_lm_init_batch(LMState *st, const double *T0, int n, LMArgs a, float *Ms,
+                                int *skip) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) lm_init_dev(st[k], T0 + 16 * (long long)k, a, Ms + 12 * (long long)k, skip + k);
+}
+
+// Copies an LM state with L2 loads (another SM may have written it during this kernel).
+__device__ void lm_load_cg(const LMState *src, LMState &dst) {
+  const long long *s = reinterpret_cast<const long long *>(src);
+  long long *d = reinterpret_cast<long long *>(&dst);
+  for (int k = 0; k < (int)(sizeof(LMState) / 8); ++k) d[k] = __ldcg(s + k);
+}
+
+// One launch runs every phase of every problem of a batch (and, with LM, every iteration):
+// CTAs take items (problem, phase, index, iteration) in queue order from a global counter.
+// An item waits (bounded) until the items it depends on have completed: the setup of a
+// problem's evaluation waits for all of its cull items, the raster for all setup items, the
+// reduction (and LM step) for all tiles, and the next evaluation's cull for that LM step.
+// Dependencies always point to earlier queue positions, which running CTAs have already
+// taken, so the waits end without any co-residency assumption.
+__global__ void __launch_bounds__(kThreads, RM_RASTER_MIN_BLOCKS) k_persist(BatchArgs b) {
+  union PersistSmem {
+    RasterSmem<1024, 0> r0;
+    RasterSmem<1024, 1> r1;
+    SetupSmem su;
+    double vals[kNumVals];
+  };
+  __shared__ PersistSmem u;
+  __shared__ int4 s_item;
+  __shared__ int s_abort;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const int k = atomicAdd(b.next, 1);
+      int4 item = k < b.n_items ? b.items[k] : make_int4(-1, 0, 0, 0);
+      int abort = 0;
+      if (item.x >= 0) {
+        const int p = item.x, ph = item.y, it = item.w;
+        const int *ctr;
+        int target;
+        if (ph == 0) {
+          ctr = b.done + 4 * p + 3;
+          target = it;
+        } else {
+          ctr = b.done + 4 * p + ph - 1;
+          target = (it + 1) * b.need[3 * p + ph - 1];
+        }
+        const long long t0 = clock64();
+        while (*(volatile const int *)ctr < target) {
+          if (clock64() - t0 > b.spin_limit) {
+            atomicOr(b.status, kStatusTimeout);
+            abort = 1;
+            break;
+          }
+          __nanosleep(64);
+        }
+        __threadfence();
+      }
+      s_item = item;
+      s_abort = abort;
+    }
+    __syncthreads();
+    const int4 item = s_item;
+    if (item.x < 0 || s_abort) break;
+    const WaveArgs &a = b.probs[item.x];
+    const bool skip = skipped(a);
+    if (!skip) {
+      switch (item.y) {
+        case 0: cull_block(a, 0, item.z); break;
+        case 1: setup_block(a, 0, item.z, b.need[3 * item.x + 1], u.su); break;
+        case 2:
+          if (a.cam.model == 0) raster_block<32, 32, kCostGrad, 0>(a, item.z, 0, u.r0);
+          else raster_block<32, 32, kCostGrad, 1>(a, item.z, 0, u.r1);
+          break;
+        default: reduce_block(a, 0, u.vals); break;
+      }
+    }
+    if (item.y == 3 && b.lm) {
+      __syncthreads();
+      const int p = item.x, it = item.w;
+      if (threadIdx.x == 0) {
+        LMState st;
+        lm_load_cg(b.lm + p, st);
+        if (it == 0) lm_take_initial_dev(st, a.res_counts, a.res_els, a.res_grad, a.res_jtj);
+        else lm_accept_dev(st, b.lmargs, a.res_counts, a.res_els, a.res_grad, a.res_jtj, skip);
+        if (it < b.lm_iters) lm_propose_dev(st, b.lmargs, b.Ms + 12 * (long long)p, b.skip + p);
+        b.lm[p] = st;
+      }
+      if (it < b.lm_iters) {  // the next evaluation starts from empty lists and bins
+        for (int t = threadIdx.x; t < a.tg.ntiles; t += blockDim.x) a.counts[t] = 0;
+        if (threadIdx.x == 0) a.vis_count[0] = 0;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(b.done + 4 * item.x + item.y, 1);
+    }
   }
+}
+
+cudaError_t launch_lm_init_batch(LMState *st, const double *T0, int n, const LMArgs &a,
+                                 float *Ms, int *skip, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_lm_init_batch<<<(n + 63) / 64, 64, 0, s>>>(st, T0, n, a, Ms, skip);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_persist(const BatchArgs &b, int grid, cudaStream_t s) {
+  k_persist<<<grid, kThreads, 0, s>>>(b);
+  return cudaGetLastError();
+}
+
+int persist_grid(int device) {
+  int sms = 0, per = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_persist, kThreads, 0) != cudaSuccess) return 0;
+  return sms * (per > 0 ? per : 1);
 }
 
 cudaError_t launch_lm_init(LMState *st, const double *T0, const LMArgs &a, float *M, int *skip,

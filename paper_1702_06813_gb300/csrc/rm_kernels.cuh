@@ -86,6 +86,29 @@ struct LMArgs {
   double cx, cy, cz;   // map centre
 };
 
+// Batch of problems (each its own camera, scan and scratch) run by one persistent kernel.
+struct BatchArgs {
+  const WaveArgs *probs;   // one per problem (n_poses 1, wave_base 0)
+  const int4 *items;       // queue: problem, phase (0 cull, 1 setup, 2 raster, 3 reduce+LM),
+                           // index within the phase, evaluation number
+  int n_items;
+  int *next;               // queue head, zero before launch
+  int *done;               // 4 counters per problem (items completed per phase), zero before
+  const int *need;         // per problem: cull items, setup workers, tiles (per evaluation)
+  LMState *lm;             // per problem, or null for a plain evaluation
+  float *Ms;               // 12 floats per problem (the problems' a.Ms point here)
+  int *skip;               // one flag per problem (the problems' a.skip point here)
+  LMArgs lmargs;
+  int lm_iters;            // LM iterations (evaluations 0..lm_iters)
+  unsigned *status;
+  long long spin_limit;    // cycles an item may wait for its dependencies
+};
+
+cudaError_t launch_lm_init_batch(LMState *st, const double *T0, int n, const LMArgs &a,
+                                 float *Ms, int *skip, cudaStream_t s);
+cudaError_t launch_persist(const BatchArgs &b, int grid, cudaStream_t s);
+int persist_grid(int device);
+
 cudaError_t launch_lm_init(LMState *st, const double *T0, const LMArgs &a, float *M,
                            int *skip, cudaStream_t s);
 cudaError_t launch_lm_take_initial(LMState *st, const long long *counts, const double *els,

@@ -255,3 +255,51 @@ class RenderMapCost(torch.autograd.Function):
         g, jr = ctx.saved_tensors
         gx = jr.transpose(0, 1) @ g
         return (grad_out.to(gx.device) * gx).to(ctx.xi_device), None, None, None, None
+
+
+def _problems(problems):
+    """ctypes array of rm_problem from [(Scan, pose), ...]; keeps the pose tensors alive."""
+    arr = (N.rm_problem * len(problems))()
+    keep = []
+    for k, (scan, pose) in enumerate(problems):
+        p = _dev_tensor(pose, torch.float64).reshape(16)
+        keep.append(p)
+        arr[k].scan = scan.c()
+        arr[k].pose = p.data_ptr()
+    return arr, keep
+
+
+def cost_grad_batch(m: Map, problems, params=None):
+    """cost_grad for [(Scan, pose), ...] that may differ in camera and size: one persistent
+    kernel launch. Returns the same dict as cost_grad, indexed by problem."""
+    n = len(problems)
+    arr, keep = _problems(problems)
+    counts = torch.empty((n, 6), dtype=torch.int64, device="cuda")
+    etab = torch.empty(n, dtype=torch.int64, device="cuda")
+    els = torch.empty(n, dtype=torch.float64, device="cuda")
+    g = torch.empty((n, 6), dtype=torch.float64, device="cuda")
+    h = torch.empty((n, 21), dtype=torch.float64, device="cuda")
+    out = N.rm_cost_out(counts.data_ptr(), etab.data_ptr(), els.data_ptr(), g.data_ptr(), h.data_ptr())
+    prm = params if params is not None else cost_params()
+    check(lib().rm_cost_grad_batch(m.handle, arr, n, ctypes.byref(prm), ctypes.byref(out), _stream()))
+    del keep
+    return {"counts": counts, "e_table": etab, "e_ls": els, "grad": g, "jtj": h}
+
+
+def align_batch(m: Map, problems, params=None, max_iters=5, lambda0=1e-3, lambda_up=10.0,
+                lambda_down=10.0, step_tol=1e-8):
+    """LM for [(Scan, start pose), ...] with every iteration of every problem in one persistent
+    kernel launch. Returns (poses (n,4,4) numpy, list of reports, status name)."""
+    n = len(problems)
+    arr, keep = _problems(problems)
+    out = np.empty((n, 16))
+    reps = (N.rm_align_report * n)()
+    lm = N.rm_align_params(max_iters, 0, lambda0, lambda_up, lambda_down, step_tol)
+    prm = params if params is not None else cost_params()
+    st = lib().rm_align_batch(m.handle, arr, n, ctypes.byref(prm), ctypes.byref(lm),
+                              out.ctypes.data_as(ctypes.c_void_p), reps, _stream())
+    if st not in (N.RM_OK, N.RM_ENOTCONV):
+        check(st)
+    del keep
+    reports = [{f: getattr(r, f) for f, _ in N.rm_align_report._fields_ if f != "reserved"} for r in reps]
+    return out.reshape(n, 4, 4), reports, N.STATUS_NAMES[st]
