@@ -97,6 +97,10 @@ struct rm_map {
   double prof_ms[4] = {0, 0, 0, 0};
   long long prof_n[4] = {0, 0, 0, 0};
   long long launches = 0;  // kernels launched since the last rm_profile(map, 1)
+  // persistent batch: its launches captured once per batch shape and replayed as a graph
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t batch_exec = nullptr;
+  std::string batch_sig;
 };
 
 namespace {
@@ -216,6 +220,11 @@ void build_clusters(const std::vector<float4> &hv, const int32_t *faces, int64_t
 rm_status ensure_arena(rm_map *m, size_t bytes, cudaStream_t s) {
   if (bytes <= m->arena_bytes) return RM_OK;
   RM_CK(cudaStreamSynchronize(s));
+  if (m->batch_exec) {  // the captured batch graph points into the old arena
+    cudaGraphExecDestroy(m->batch_exec);
+    m->batch_exec = nullptr;
+    m->batch_sig.clear();
+  }
   if (m->arena) RM_CK(cudaFree(m->arena));
   m->arena = nullptr;
   m->arena_bytes = 0;
@@ -540,12 +549,34 @@ rm_status run_batch(rm_map *m, const rm_problem *probs, int n, const rm_cost_par
   RM_CK(cudaSetDevice(m->device));
   const int K = lm ? lm->max_iters : 0;
   const int nc = m->n_clusters;
-  const int ncull = (nc + 255) / 256;
+  const int ncull = ((nc + 255) / 256 + rmk::kPersistCull - 1) / rmk::kPersistCull;
   const int nwork = std::min(64, std::max(1, nc / 512));
   for (int attempt = 0;; ++attempt) {
     std::vector<TileGeom> tg(n);
     std::vector<long long> P(n);
     size_t tiles_total = 0, bins_bytes = 0, px_total = 0, rays_total = 0;
+    // problems that share a scan (same arrays) share one staged copy; likewise ray tables
+    std::vector<int> scan_of(n), rays_of(n, -1);
+    for (int p = 0; p < n; ++p) {
+      scan_of[p] = p;
+      for (int q = 0; q < p; ++q)
+        if (probs[q].scan.depth == probs[p].scan.depth && probs[q].scan.cls == probs[p].scan.cls &&
+            probs[q].scan.intr.width == probs[p].scan.intr.width &&
+            probs[q].scan.intr.height == probs[p].scan.intr.height) {
+          scan_of[p] = scan_of[q];
+          break;
+        }
+      if (probs[p].scan.intr.model == RM_RAYTABLE) {
+        rays_of[p] = p;
+        for (int q = 0; q < p; ++q)
+          if (rays_of[q] >= 0 && probs[q].scan.intr.rays == probs[p].scan.intr.rays &&
+              probs[q].scan.intr.width == probs[p].scan.intr.width &&
+              probs[q].scan.intr.height == probs[p].scan.intr.height) {
+            rays_of[p] = rays_of[q];
+            break;
+          }
+      }
+    }
     for (int p = 0; p < n; ++p) {
       const rm_intrinsics *in = &probs[p].scan.intr;
       tg[p].tw = tg[p].th = 32;
@@ -557,27 +588,40 @@ rm_status run_batch(rm_map *m, const rm_problem *probs, int n, const rm_cost_par
       P[p] = (long long)in->width * in->height;
       tiles_total += tg[p].ntiles;
       bins_bytes += align_up((size_t)tg[p].ntiles * tg[p].cap * tg[p].rec_bytes, 256);
-      px_total += align_up((size_t)P[p], 64);
-      if (in->model == RM_RAYTABLE) rays_total += 3 * (size_t)P[p];
+      if (scan_of[p] == p) px_total += align_up((size_t)P[p], 64);
+      if (rays_of[p] == p) rays_total += 3 * (size_t)P[p];
     }
-    // queue: per evaluation, groups of 8 problems, phase by phase within a group
+    // queue: per evaluation, groups of problems; the cull and setup items of group g+1 go
+    // ahead of the raster and reduce items of group g, so by the time a CTA takes a tile its
+    // problem's bins are (almost always) complete and dependency waits stay short
     std::vector<int4> items;
-    for (int it = 0; it <= K; ++it)
-      for (int g0 = 0; g0 < n; g0 += 8) {
-        const int g1 = std::min(n, g0 + 8);
-        for (int p = g0; p < g1; ++p)
-          for (int k = 0; k < ncull; ++k) items.push_back(make_int4(p, 0, k, it));
-        for (int p = g0; p < g1; ++p)
-          for (int k = 0; k < nwork; ++k) items.push_back(make_int4(p, 1, k, it));
-        for (int p = g0; p < g1; ++p)
-          for (int k = 0; k < tg[p].ntiles; ++k) items.push_back(make_int4(p, 2, k, it));
-        for (int p = g0; p < g1; ++p) items.push_back(make_int4(p, 3, 0, it));
+    const int G = 8;
+    auto front = [&](int g0, int it) {
+      const int g1 = std::min(n, g0 + G);
+      for (int p = g0; p < g1; ++p)
+        for (int k = 0; k < ncull; ++k) items.push_back(make_int4(p, 0, k, it));
+      for (int p = g0; p < g1; ++p)
+        for (int k = 0; k < nwork; ++k) items.push_back(make_int4(p, 1, k, it));
+    };
+    auto back = [&](int g0, int it) {
+      const int g1 = std::min(n, g0 + G);
+      for (int p = g0; p < g1; ++p)
+        for (int k = 0; k < (tg[p].ntiles + rmk::kPersistTiles - 1) / rmk::kPersistTiles; ++k)
+          items.push_back(make_int4(p, 2, k, it));
+      for (int p = g0; p < g1; ++p) items.push_back(make_int4(p, 3, 0, it));
+    };
+    for (int it = 0; it <= K; ++it) {
+      front(0, it);
+      for (int g0 = 0; g0 < n; g0 += G) {
+        if (g0 + G < n) front(g0 + G, it);
+        back(g0, it);
       }
+    }
     std::vector<int> need(3 * (size_t)n);
     for (int p = 0; p < n; ++p) {
       need[3 * p] = ncull;
       need[3 * p + 1] = nwork;
-      need[3 * p + 2] = tg[p].ntiles;
+      need[3 * p + 2] = (tg[p].ntiles + rmk::kPersistTiles - 1) / rmk::kPersistTiles;
     }
     // ---- plan and carve the arena
     auto layout = [&](Carver &cv, bool carve, WaveArgs **d_args, int4 **d_items, int **d_next,
@@ -624,21 +668,33 @@ rm_status run_batch(rm_map *m, const rm_problem *probs, int n, const rm_cost_par
            &r_els, &r_grad, &r_jtj);
     // ---- per-problem arguments and inputs
     std::vector<WaveArgs> args(n);
+    std::vector<size_t> px_at(n), rays_at(n);
     size_t t_off = 0, b_off = 0, px_off = 0, r_off = 0;
     for (int p = 0; p < n; ++p) {
       const rm_scan &sc = probs[p].scan;
       const rm_intrinsics *in = &sc.intr;
       float *rays = nullptr;
       if (in->model == RM_RAYTABLE) {
-        rays = d_rays + r_off;
-        r_off += 3 * (size_t)P[p];
-        RM_CK(cudaMemcpyAsync(rays, in->rays, sizeof(float) * 3 * P[p],
-                              on_device(in->rays) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+        if (rays_of[p] == p) {
+          rays_at[p] = r_off;
+          r_off += 3 * (size_t)P[p];
+          RM_CK(cudaMemcpyAsync(d_rays + rays_at[p], in->rays, sizeof(float) * 3 * P[p],
+                                on_device(in->rays) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+        } else {
+          rays_at[p] = rays_at[rays_of[p]];
+        }
+        rays = d_rays + rays_at[p];
       }
-      RM_CK(cudaMemcpyAsync(d_sd + px_off, sc.depth, sizeof(float) * P[p],
-                            on_device(sc.depth) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
-      RM_CK(cudaMemcpyAsync(d_sc + px_off, sc.cls, (size_t)P[p],
-                            on_device(sc.cls) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+      if (scan_of[p] == p) {
+        px_at[p] = px_off;
+        px_off += align_up((size_t)P[p], 64);
+        RM_CK(cudaMemcpyAsync(d_sd + px_at[p], sc.depth, sizeof(float) * P[p],
+                              on_device(sc.depth) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+        RM_CK(cudaMemcpyAsync(d_sc + px_at[p], sc.cls, (size_t)P[p],
+                              on_device(sc.cls) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+      } else {
+        px_at[p] = px_at[scan_of[p]];
+      }
       RM_CK(cudaMemcpyAsync(d_poses + 16 * (size_t)p, probs[p].pose, sizeof(double) * 16,
                             on_device(probs[p].pose) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
       WaveArgs &a = args[p];
@@ -661,8 +717,8 @@ rm_status run_batch(rm_map *m, const rm_problem *probs, int n, const rm_cost_par
       a.partial = d_partial + t_off * rmk::kNumVals;
       a.status = m->d_status;
       a.skip = d_skip + p;
-      a.scan_depth = d_sd + px_off;
-      a.scan_cls = d_sc + px_off;
+      a.scan_depth = d_sd + px_at[p];
+      a.scan_cls = d_sc + px_at[p];
       a.prm = {prm->eps, prm->w_fofo, prm->w_fofu, prm->w_fufo};
       a.res_counts = r_counts + 6 * (size_t)p;
       a.res_etable = r_et + p;
@@ -671,16 +727,10 @@ rm_status run_batch(rm_map *m, const rm_problem *probs, int n, const rm_cost_par
       a.res_jtj = r_jtj + 21 * (size_t)p;
       t_off += tg[p].ntiles;
       b_off += align_up((size_t)tg[p].ntiles * tg[p].cap * tg[p].rec_bytes, 256);
-      px_off += align_up((size_t)P[p], 64);
     }
     RM_CK(cudaMemcpyAsync(d_args, args.data(), sizeof(WaveArgs) * n, cudaMemcpyHostToDevice, s));
     RM_CK(cudaMemcpyAsync(d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, s));
     RM_CK(cudaMemcpyAsync(d_need, need.data(), sizeof(int) * need.size(), cudaMemcpyHostToDevice, s));
-    RM_CK(cudaMemsetAsync(d_next, 0, sizeof(int), s));
-    RM_CK(cudaMemsetAsync(d_done, 0, sizeof(int) * 4 * n, s));
-    RM_CK(cudaMemsetAsync(d_skip, 0, sizeof(int) * n, s));
-    RM_CK(cudaMemsetAsync(d_vcount, 0, sizeof(int) * n, s));
-    RM_CK(cudaMemsetAsync(d_counts, 0, sizeof(int) * tiles_total, s));
     rmk::LMArgs la{};
     la.cx = m->centre[0];
     la.cy = m->centre[1];
@@ -690,9 +740,6 @@ rm_status run_batch(rm_map *m, const rm_problem *probs, int n, const rm_cost_par
       la.lambda_up = lm->lambda_up;
       la.lambda_down = lm->lambda_down;
       la.step_tol = lm->step_tol;
-      RM_CK(rmk::launch_lm_init_batch(d_lm, d_poses, n, la, d_M, d_skip, s));
-    } else {
-      RM_CK(rmk::launch_pose_to_m(d_poses, n, m->centre[0], m->centre[1], m->centre[2], d_M, s));
     }
     rmk::BatchArgs b{};
     b.probs = d_args;
@@ -710,7 +757,49 @@ rm_status run_batch(rm_map *m, const rm_problem *probs, int n, const rm_cost_par
     b.spin_limit = 1ll << 32;
     const int grid = rmk::persist_grid(m->device);
     if (grid <= 0) return fail(RM_ECUDA, "could not size the persistent grid");
-    RM_CK(rmk::launch_persist(b, grid, s));
+    // counters to zero, LM state / pose matrices, the persistent kernel: one captured graph
+    // per batch shape (the arena layout is a function of the shape), replayed every call
+    char sig[512];
+    std::snprintf(sig, sizeof(sig), "%p|%d|%d|%zu|%d|%d|%a|%a|%a|%a|%zu|%zu|%zu|%d", (void *)m->arena, n,
+                  K, items.size(), grid, lm ? 1 : 0, la.lambda0, la.lambda_up, la.lambda_down,
+                  la.step_tol, tiles_total, px_total, rays_total, m->cap);
+    std::string key(sig);
+    for (int p = 0; p < n; ++p) key += "|" + std::to_string(probs[p].scan.intr.model) + "x" +
+                                        std::to_string(probs[p].scan.intr.width) + "x" +
+                                        std::to_string(probs[p].scan.intr.height);
+    if (!m->batch_exec || key != m->batch_sig) {
+      if (m->batch_exec) {
+        RM_CK(cudaGraphExecDestroy(m->batch_exec));
+        m->batch_exec = nullptr;
+        m->batch_sig.clear();
+      }
+      if (!m->cap_stream) RM_CK(cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking));
+      cudaStream_t c = m->cap_stream;
+      RM_CK(cudaStreamBeginCapture(c, cudaStreamCaptureModeThreadLocal));
+      cudaError_t e = cudaSuccess;
+      auto rec = [&](cudaError_t x) {
+        if (e == cudaSuccess) e = x;
+      };
+      rec(cudaMemsetAsync(d_next, 0, sizeof(int), c));
+      rec(cudaMemsetAsync(d_done, 0, sizeof(int) * 4 * n, c));
+      rec(cudaMemsetAsync(d_skip, 0, sizeof(int) * n, c));
+      rec(cudaMemsetAsync(d_vcount, 0, sizeof(int) * n, c));
+      rec(cudaMemsetAsync(d_counts, 0, sizeof(int) * tiles_total, c));
+      if (lm) rec(rmk::launch_lm_init_batch(d_lm, d_poses, n, la, d_M, d_skip, c));
+      else rec(rmk::launch_pose_to_m(d_poses, n, m->centre[0], m->centre[1], m->centre[2], d_M, c));
+      rec(rmk::launch_persist(b, grid, c));
+      cudaGraph_t graph = nullptr;
+      const cudaError_t ec = cudaStreamEndCapture(c, &graph);
+      if (e == cudaSuccess) e = ec;
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&m->batch_exec, graph, 0);
+      if (graph) cudaGraphDestroy(graph);
+      if (e != cudaSuccess) {
+        m->batch_exec = nullptr;
+        return fail(RM_ECUDA, std::string("batch graph capture: ") + cudaGetErrorString(e));
+      }
+      m->batch_sig = key;
+    }
+    RM_CK(cudaGraphLaunch(m->batch_exec, s));
     m->launches += 2;
     bool host_out = false;
     std::vector<rmk::LMState> hs;
@@ -890,6 +979,8 @@ void rm_map_destroy(rm_map *m) {
   for (auto &ev : m->ev_pending)
     for (auto e : ev) cudaEventDestroy(e);
   for (auto e : m->ev_free) cudaEventDestroy(e);
+  if (m->batch_exec) cudaGraphExecDestroy(m->batch_exec);
+  if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
   delete m;
 }
 

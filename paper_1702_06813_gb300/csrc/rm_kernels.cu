@@ -144,16 +144,19 @@ __device__ __forceinline__ bool cluster_visible(const DevCam &cam, const float *
 __device__ __forceinline__ int ld_cg(const int *p) { return __ldcg(p); }
 __device__ __forceinline__ bool skipped(const WaveArgs &a) { return a.skip && __ldcg(a.skip) != 0; }
 
-__device__ __forceinline__ void load_m(const WaveArgs &a, int q, float *M) {
-  const float *Mg = a.Ms + 12 * (long long)(a.wave_base + q);
-#pragma unroll
-  for (int k = 0; k < 12; ++k) M[k] = __ldcg(Mg + k);
+// The pose matrix of pose q, read once per CTA (from L2: another CTA may have written it)
+// into shared memory; every thread then copies it from there.
+__device__ __forceinline__ void load_m_block(const WaveArgs &a, int q, float *sM) {
+  if (threadIdx.x < 12) sM[threadIdx.x] = __ldcg(a.Ms + 12 * (long long)(a.wave_base + q) + threadIdx.x);
+  __syncthreads();
 }
 
 // Clusters chunk*256 + threadIdx.x of pose q: test, and append the visible ones.
-__device__ __forceinline__ void cull_block(const WaveArgs &a, int q, int chunk) {
+__device__ __forceinline__ void cull_block(const WaveArgs &a, int q, int chunk, float *sM) {
+  load_m_block(a, q, sM);
   float M[12];
-  load_m(a, q, M);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) M[k] = sM[k];
   int *vis = a.vis + (long long)q * a.n_clusters;
   const int c = chunk * blockDim.x + threadIdx.x;
   const bool keep = c < a.n_clusters && cluster_visible(a.cam, M, a.cl_sphere[c]);
@@ -168,8 +171,9 @@ __device__ __forceinline__ void cull_block(const WaveArgs &a, int q, int chunk) 
 }
 
 __global__ void __launch_bounds__(256) k_cull(WaveArgs a) {
+  __shared__ float sM[12];
   if (skipped(a)) return;
-  cull_block(a, blockIdx.y, blockIdx.x);
+  cull_block(a, blockIdx.y, blockIdx.x, sM);
 }
 
 // ------------------------------------------------------------------ triangle setup + binning
@@ -332,6 +336,8 @@ constexpr int kClusterMax = 64;  // vertices and triangles per cluster
 // memory, then each lane sets up triangles (near-plane cut, culling, depth plane) and
 // appends them to the screen-tile bins.
 struct SetupSmem {
+  float M[12];
+  int nvis;
   float4 s_vc[8][kClusterMax];
   int2 s_vs[8][kClusterMax];
   int s_gid[8][kClusterMax];
@@ -345,9 +351,12 @@ __device__ __forceinline__ void setup_block(const WaveArgs &a, int q, int worker
   int(*s_gid)[kClusterMax] = sm.s_gid;
   float4(*s_dir)[kClusterMax] = sm.s_dir;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) sm.nvis = ld_cg(&a.vis_count[q]);
+  load_m_block(a, q, sm.M);
   float M[12];
-  load_m(a, q, M);
-  const int nvis = ld_cg(&a.vis_count[q]);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) M[k] = sm.M[k];
+  const int nvis = sm.nvis;
   const int *vis = a.vis + (long long)q * a.n_clusters;
   int *counts = a.counts + (long long)q * a.tg.ntiles;
   unsigned char *bins = a.bins + (long long)q * a.tg.ntiles * a.tg.cap * a.tg.rec_bytes;
@@ -526,6 +535,7 @@ __device__ __forceinline__ bool raster_tile(unsigned long long *zk, TriRec *stag
   constexpr int kRecMax = kRecMaxPinhole;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int NW = kThreads / 32;
+  const float w_near = cam.w_near, w_far = cam.w_far;
   unsigned phase = 0;
   for (int r0 = 0; r0 < n; r0 += kRecMax) {
     const int cnt = min(kRecMax, n - r0);
@@ -597,7 +607,7 @@ __device__ __forceinline__ bool raster_tile(unsigned long long *zk, TriRec *stag
         }
         if (in) {
           const float w = inv_depth_pinhole(q.Ai, q.Bi, q.Ci, i, j);
-          if (keep_w(cam, w)) atomicMin(&zk[(j - oy) * TW + (i - ox)], make_key(w, q.id));
+          if (w > 0.0f && w >= w_far && w <= w_near) atomicMin(&zk[(j - oy) * TW + (i - ox)], make_key(w, q.id));
         }
       }
     }
@@ -632,6 +642,7 @@ __device__ __forceinline__ bool raster_tile_ray(unsigned long long *zk, RayRec *
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int NW = kThreads / 32;
   constexpr int kRecMax = kRecMaxRay;
+  const float w_near = cam.w_near, w_far = cam.w_far;
   unsigned phase = 0;
   for (int r0 = 0; r0 < n; r0 += kRecMax) {
     const int cnt = min(kRecMax, n - r0);
@@ -698,7 +709,7 @@ __device__ __forceinline__ bool raster_tile_ray(unsigned long long *zk, RayRec *
                         ((q.sig & 4) ? s2 >= 0.0f : s2 < 0.0f);
         if (in) {
           const float w = dot_c(q.nix, q.niy, q.niz, x, y, z);
-          if (keep_w(cam, w)) atomicMin(&zk[p], make_key(w, q.id));
+          if (w > 0.0f && w >= w_far && w <= w_near) atomicMin(&zk[p], make_key(w, q.id));
         }
       }
     }
@@ -706,6 +717,10 @@ __device__ __forceinline__ bool raster_tile_ray(unsigned long long *zk, RayRec *
   }
   return true;
 }
+
+#ifndef RM_PERSIST_MIN_BLOCKS
+#define RM_PERSIST_MIN_BLOCKS 4
+#endif
 
 #ifndef RM_RASTER_MIN_BLOCKS
 #define RM_RASTER_MIN_BLOCKS 4  // resident CTAs per SM the register budget is sized for
@@ -717,6 +732,8 @@ struct RasterSmem {
   // pinhole: 512 records + their int4 edge headers; ray table: 384 records + the tile's rays
   static constexpr int kBuf = MODEL == 0 ? kRecMaxPinhole * (48 + 16) : kRecMaxRay * 64 + 12 * NP;
   unsigned long long zk[NP];
+  float M[12];
+  int n;
   alignas(128) unsigned char sbuf[kBuf];
   int S[(MODEL == 0 ? kRecMaxPinhole : kRecMaxRay) + 1];
   int wtot[NW];
@@ -745,7 +762,8 @@ __device__ __forceinline__ void raster_block(const WaveArgs &a, int tile, int q,
 
   for (int p = tid; p < NP; p += kThreads) zk[p] = kKeyEmpty;
   const long long bin = (long long)q * a.tg.ntiles + tile;
-  const int n = min(ld_cg(&a.counts[bin]), a.tg.cap);
+  if (tid < 12) sm.M[tid] = __ldcg(a.Ms + 12 * (long long)g + tid);
+  if (tid == 0) sm.n = min(ld_cg(&a.counts[bin]), a.tg.cap);
   float *rx = nullptr, *ry = nullptr, *rz = nullptr;
   if (MODEL != 0) {
     rx = reinterpret_cast<float *>(sbuf + kRecMaxRay * 64);
@@ -770,6 +788,7 @@ __device__ __forceinline__ void raster_block(const WaveArgs &a, int tile, int q,
     fence_mbar_init();
   }
   __syncthreads();
+  const int n = sm.n;
   bool ok;
   if (MODEL == 0)
     ok = raster_tile<TW, TH>(zk, reinterpret_cast<TriRec *>(sbuf),
@@ -809,7 +828,7 @@ __device__ __forceinline__ void raster_block(const WaveArgs &a, int tile, int q,
       if (a.bary) {
         const int4 f = a.faces[id];
         float M[12];
-        load_m(a, q, M);
+        for (int k = 0; k < 12; ++k) M[k] = sm.M[k];
         const float4 w0 = a.v[f.x], w1 = a.v[f.y], w2 = a.v[f.z];
         const float3 v0 = xform(M, w0.x, w0.y, w0.z), v1 = xform(M, w1.x, w1.y, w1.z),
                      v2 = xform(M, w2.x, w2.y, w2.z);
@@ -844,15 +863,11 @@ __device__ __forceinline__ void raster_block(const WaveArgs &a, int tile, int q,
 #pragma unroll
   for (int k = 0; k < 28; ++k) acc[k] = 0.0f;
   float R[9];
-  {
-    float M[12];
-    load_m(a, q, M);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      R[3 * k] = M[4 * k];
-      R[3 * k + 1] = M[4 * k + 1];
-      R[3 * k + 2] = M[4 * k + 2];
-    }
+  for (int k = 0; k < 3; ++k) {
+    R[3 * k] = sm.M[4 * k];
+    R[3 * k + 1] = sm.M[4 * k + 1];
+    R[3 * k + 2] = sm.M[4 * k + 2];
   }
   const float eps = a.prm.eps;
   const float ifx = 1.0f / a.cam.fx, ify = 1.0f / a.cam.fy;
@@ -1047,7 +1062,7 @@ int wave_kernel_launches(const WaveArgs &a, int mode) {
 
 // ------------------------------------------------------------------ Levenberg-Marquardt
 
-__device__ void se3_right_dev(const double *T, const double *xi, double *out) {
+__device__ __noinline__ void se3_right_dev(const double *T, const double *xi, double *out) {
   const double *rho = xi, *phi = xi + 3;
   const double th2 = phi[0] * phi[0] + phi[1] * phi[1] + phi[2] * phi[2], th = sqrt(th2);
   double A, B, C;
@@ -1178,7 +1193,7 @@ cudaError_t launch_retract(const double *T, const double *xi, int n, double *out
 }
 
 // (H + lambda diag H) x = -g by Cholesky in FP64; false if not positive definite.
-__device__ bool lm_solve_dev(const double *jtj, const double *g, double lambda, double *x) {
+__device__ __noinline__ bool lm_solve_dev(const double *jtj, const double *g, double lambda, double *x) {
   double A[36], L[36];
   int q = 0;
   for (int u = 0; u < 6; ++u)
@@ -1214,7 +1229,7 @@ __device__ bool lm_solve_dev(const double *jtj, const double *g, double lambda, 
   return true;
 }
 
-__device__ void lm_take_initial_dev(LMState &st, const long long *counts, const double *els,
+__device__ __noinline__ void lm_take_initial_dev(LMState &st, const long long *counts, const double *els,
                                     const double *grad, const double *jtj) {
   st.e = els[0];
   st.e_ls0 = els[0];
@@ -1226,7 +1241,7 @@ __device__ void lm_take_initial_dev(LMState &st, const long long *counts, const 
 
 // Solve for the next step; writes the candidate's matrix and clears *skip, or sets *skip when
 // there is nothing to evaluate (converged, or a damped system that is not positive definite).
-__device__ void lm_propose_dev(LMState &st, const LMArgs &a, float *M, int *skip) {
+__device__ __noinline__ void lm_propose_dev(LMState &st, const LMArgs &a, float *M, int *skip) {
   if (st.done) {
     *skip = 1;
     return;
@@ -1252,7 +1267,7 @@ __device__ void lm_propose_dev(LMState &st, const LMArgs &a, float *M, int *skip
 }
 
 // Accept the evaluated candidate if it lowered the surrogate (nothing when it was skipped).
-__device__ void lm_accept_dev(LMState &st, const LMArgs &a, const long long *counts,
+__device__ __noinline__ void lm_accept_dev(LMState &st, const LMArgs &a, const long long *counts,
                               const double *els, const double *grad, const double *jtj,
                               bool was_skipped) {
   if (was_skipped) return;
@@ -1306,7 +1321,7 @@ __global__ void k_lm_init_batch(LMState *st, const double *T0, int n, LMArgs a, 
 }
 
 // Copies an LM state with L2 loads (another SM may have written it during this kernel).
-__device__ void lm_load_cg(const LMState *src, LMState &dst) {
+__device__ __noinline__ void lm_load_cg(const LMState *src, LMState &dst) {
   const long long *s = reinterpret_cast<const long long *>(src);
   long long *d = reinterpret_cast<long long *>(&dst);
   for (int k = 0; k < (int)(sizeof(LMState) / 8); ++k) d[k] = __ldcg(s + k);
@@ -1319,7 +1334,7 @@ __device__ void lm_load_cg(const LMState *src, LMState &dst) {
 // reduction (and LM step) for all tiles, and the next evaluation's cull for that LM step.
 // Dependencies always point to earlier queue positions, which running CTAs have already
 // taken, so the waits end without any co-residency assumption.
-__global__ void __launch_bounds__(kThreads, RM_RASTER_MIN_BLOCKS) k_persist(BatchArgs b) {
+__global__ void __launch_bounds__(kThreads, RM_PERSIST_MIN_BLOCKS) k_persist(BatchArgs b) {
   union PersistSmem {
     RasterSmem<1024, 0> r0;
     RasterSmem<1024, 1> r1;
@@ -1327,6 +1342,8 @@ __global__ void __launch_bounds__(kThreads, RM_RASTER_MIN_BLOCKS) k_persist(Batc
     double vals[kNumVals];
   };
   __shared__ PersistSmem u;
+  __shared__ float s_M[12];
+  __shared__ WaveArgs s_args;  // the current item's problem, copied once per item
   __shared__ int4 s_item;
   __shared__ int s_abort;
   for (;;) {
@@ -1362,16 +1379,34 @@ __global__ void __launch_bounds__(kThreads, RM_RASTER_MIN_BLOCKS) k_persist(Batc
     __syncthreads();
     const int4 item = s_item;
     if (item.x < 0 || s_abort) break;
-    const WaveArgs &a = b.probs[item.x];
+    {
+      const int *src = reinterpret_cast<const int *>(b.probs + item.x);
+      int *dst = reinterpret_cast<int *>(&s_args);
+      for (int k = threadIdx.x; k < (int)(sizeof(WaveArgs) / 4); k += blockDim.x) dst[k] = src[k];
+    }
+    __syncthreads();
+    const WaveArgs &a = s_args;
     const bool skip = skipped(a);
     if (!skip) {
       switch (item.y) {
-        case 0: cull_block(a, 0, item.z); break;
-        case 1: setup_block(a, 0, item.z, b.need[3 * item.x + 1], u.su); break;
-        case 2:
-          if (a.cam.model == 0) raster_block<32, 32, kCostGrad, 0>(a, item.z, 0, u.r0);
-          else raster_block<32, 32, kCostGrad, 1>(a, item.z, 0, u.r1);
+        case 0: {  // kPersistCull chunks of 256 clusters
+          const int c1 = min((item.z + 1) * kPersistCull, (a.n_clusters + 255) / 256);
+          for (int c = item.z * kPersistCull; c < c1; ++c) {
+            cull_block(a, 0, c, s_M);
+            __syncthreads();
+          }
           break;
+        }
+        case 1: setup_block(a, 0, item.z, b.need[3 * item.x + 1], u.su); break;
+        case 2: {  // kPersistTiles tiles
+          const int t1 = min((item.z + 1) * kPersistTiles, a.tg.ntiles);
+          for (int t = item.z * kPersistTiles; t < t1; ++t) {
+            if (a.cam.model == 0) raster_block<32, 32, kCostGrad, 0>(a, t, 0, u.r0);
+            else raster_block<32, 32, kCostGrad, 1>(a, t, 0, u.r1);
+            __syncthreads();
+          }
+          break;
+        }
         default: reduce_block(a, 0, u.vals); break;
       }
     }

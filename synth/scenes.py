@@ -552,3 +552,39 @@ def workload_headline(seed=3000, n_poses=256):
     poses = perturb_gauss(gt, r, 0.10, 5.0, n_poses)
     return dict(name="room-1M-640x480-256poses", mesh=mesh, cam=cam, gt=gt, scan=(depth, cls),
                 poses=poses)
+
+
+def workload_tracking(seed=5000, n_agents=64, n_frames=200, target_fo=1_400_000,
+                      target_fu=600_000, n_panels=400, speed=0.5, rate_hz=2.0):
+    """Uneven tracking batch: n_agents walk seeded smooth trajectories (0.5 m/s, 2 Hz sensor
+    rate, so 0.25 m per frame) over the outdoor mesh; agent a carries sensor a mod 3 in
+    {160x120 pinhole, 640x480 pinhole, 1024x64 Lidar}. Returns the true camera poses per frame
+    and agent; the observed scans are made per frame by the caller."""
+    mesh = terrain_mesh(seed, target_fo=target_fo, target_fu=target_fu, n_panels=n_panels)
+    r = np.random.Generator(np.random.PCG64(seed + 1))
+    cams = [dataclasses.replace(cam_160x120(), range_max=40.0, near=0.3),
+            dataclasses.replace(cam_kinect_640x480(), range_max=40.0, range_min=0.3, near=0.3),
+            cam_lidar_1024x64()]
+    step = speed / rate_hz
+    poses = np.empty((n_frames, n_agents, 4, 4))
+    kinds = np.arange(n_agents) % 3
+    half = mesh.terrain["half"]
+    for a in range(n_agents):
+        for _ in range(1000):
+            p0 = r.uniform(-half * 0.4, half * 0.4, size=2)
+            if not _inside_any(np.array([p0[0], p0[1], 0.0]) * np.array([1, 1, 0]) +
+                               np.array([0, 0, float(terrain_height(mesh.terrain, p0[0], p0[1]))]),
+                               mesh.boxes, 3.0):
+                break
+        psi0, amp, ph = r.uniform(-math.pi, math.pi), r.uniform(0.1, 0.4), r.uniform(0, 2 * math.pi)
+        h = 1.8 if kinds[a] == 2 else 1.5
+        pitch = 0.0 if kinds[a] == 2 else math.radians(15.0)
+        xy = p0.copy()
+        for f in range(n_frames):
+            psi = psi0 + amp * math.sin(2 * math.pi * f / 60.0 + ph)
+            if f > 0:
+                xy = xy + step * np.array([math.cos(psi), math.sin(psi)])
+            z = float(terrain_height(mesh.terrain, xy[0], xy[1])) + h
+            poses[f, a] = pose_from(np.array([xy[0], xy[1], z]), psi, pitch, 0.0)
+    return dict(name=f"terrain-2M-tracking-{n_agents}x{n_frames}", mesh=mesh, cams=cams,
+                kinds=kinds, poses=poses)
