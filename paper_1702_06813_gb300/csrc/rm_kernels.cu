@@ -474,7 +474,7 @@ __device__ __forceinline__ bool edge_ok(int dx, int dy, int xa, int ya, int px, 
   return E > 0 || (E == 0 && top_left);
 }
 
-constexpr int kRecFallback = 1 << 24;  // record keeps its snapped vertices (int64 edge tests)
+constexpr int kRecFallback = 1 << 28;  // record keeps its snapped vertices (int64 edge tests)
 
 // Per-record raster setup for one tile: clip the sample bounding box to the tile and turn
 // each edge function into an exact int32 affine function of the pixel offset (di, dj) inside
@@ -514,13 +514,28 @@ __device__ __forceinline__ int derive_rect(TriRec *rec, int4 *hdr, int k, int cn
       e0[e] = 0; sx[e] = 0; sy[e] = 0;
     }
   }
-  hdr[k] = make_int4(e0[0], e0[1], e0[2], __float_as_int(__frcp_rn(__int2float_rn(bw))));
+  const int qw = (bw + 1) >> 1, qh = (bh + 1) >> 1;  // 2x2 pixel quads over the rectangle
+  hdr[k] = make_int4(e0[0], e0[1], e0[2], __float_as_int(__frcp_rn(__int2float_rn(qw))));
   if (!fallback) {
     r.x0 = sx[0]; r.y0 = sy[0]; r.x1 = sx[1]; r.y1 = sy[1]; r.x2 = sx[2]; r.y2 = sy[2];
   }
-  r.pad = (i0 - ox) | ((j0 - oy) << 8) | (bw << 16) | (fallback ? kRecFallback : 0);
-  return bw * bh;
+  r.pad = (i0 - ox) | ((j0 - oy) << 8) | (bw << 16) | (bh << 22) | (fallback ? kRecFallback : 0);
+  return qw * qh;
 }
+
+// Coverage of pixel (i, j) from a record's vertices with exact int64 edge functions.
+__device__ __forceinline__ bool covers_exact(const TriRec &q, int i, int j) {
+  const int px = 256 * i + 128, py = 256 * j + 128;
+  return edge_ok(q.x1 - q.x0, q.y1 - q.y0, q.x0, q.y0, px, py) &&
+         edge_ok(q.x2 - q.x1, q.y2 - q.y1, q.x1, q.y1, px, py) &&
+         edge_ok(q.x0 - q.x2, q.y0 - q.y2, q.x2, q.y2, px, py);
+}
+
+// Inner-side test of one pixel from the three int32 edge values (wrapping adds: a value is
+// only used when its pixel lies inside the record's rectangle, where it cannot wrap).
+__device__ __forceinline__ bool inner3(int a, int b, int c) { return (a | b | c) >= 0; }
+
+__device__ __forceinline__ int wadd(int a, int b) { return (int)((unsigned)a + (unsigned)b); }
 
 // Rasterise every record of one (pose, tile) bin into the shared z-buffer. Records are staged
 // with one bulk copy per round; a block-wide scan of their per-tile rectangle sizes lays all
@@ -591,23 +606,44 @@ __device__ __forceinline__ bool raster_tile(unsigned long long *zk, TriRec *stag
         const TriRec &q = stage[r];
         const int4 h = hdr[r];
         const int l = f - sr;
-        const int bw = (q.pad >> 16) & 0xff;
-        const int dj = __float2int_rz(__fmul_rn(__int2float_rn(l) + 0.5f, __int_as_float(h.w)));
-        const int di = l - dj * bw;
+        const int bw = (q.pad >> 16) & 0x3f, bh = (q.pad >> 22) & 0x3f;
+        const int qw = (bw + 1) >> 1;
+        const int qj = __float2int_rz(__fmul_rn(__int2float_rn(l) + 0.5f, __int_as_float(h.w)));
+        const int di = 2 * (l - qj * qw), dj = 2 * qj;
         const int i = ox + (q.pad & 0xff) + di, j = oy + ((q.pad >> 8) & 0xff) + dj;
-        bool in;
+        const bool has_r = di + 1 < bw, has_d = dj + 1 < bh;
+        bool in00, in10, in01, in11;
         if (!(q.pad & kRecFallback)) {
-          in = (h.x + di * q.x0 + dj * q.y0 >= 0) & (h.y + di * q.x1 + dj * q.y1 >= 0) &
-               (h.z + di * q.x2 + dj * q.y2 >= 0);
+          const int a = h.x + di * q.x0 + dj * q.y0;
+          const int b = h.y + di * q.x1 + dj * q.y1;
+          const int c = h.z + di * q.x2 + dj * q.y2;
+          in00 = inner3(a, b, c);
+          in10 = has_r && inner3(wadd(a, q.x0), wadd(b, q.x1), wadd(c, q.x2));
+          in01 = has_d && inner3(wadd(a, q.y0), wadd(b, q.y1), wadd(c, q.y2));
+          in11 = has_r && has_d &&
+                 inner3(wadd(wadd(a, q.x0), q.y0), wadd(wadd(b, q.x1), q.y1), wadd(wadd(c, q.x2), q.y2));
         } else {
-          const int px = 256 * i + 128, py = 256 * j + 128;
-          in = edge_ok(q.x1 - q.x0, q.y1 - q.y0, q.x0, q.y0, px, py) &&
-               edge_ok(q.x2 - q.x1, q.y2 - q.y1, q.x1, q.y1, px, py) &&
-               edge_ok(q.x0 - q.x2, q.y0 - q.y2, q.x2, q.y2, px, py);
+          in00 = covers_exact(q, i, j);
+          in10 = has_r && covers_exact(q, i + 1, j);
+          in01 = has_d && covers_exact(q, i, j + 1);
+          in11 = has_r && has_d && covers_exact(q, i + 1, j + 1);
         }
-        if (in) {
+        const int zi = (j - oy) * TW + (i - ox);
+        if (in00) {
           const float w = inv_depth_pinhole(q.Ai, q.Bi, q.Ci, i, j);
-          if (w > 0.0f && w >= w_far && w <= w_near) atomicMin(&zk[(j - oy) * TW + (i - ox)], make_key(w, q.id));
+          if (w > 0.0f && w >= w_far && w <= w_near) atomicMin(&zk[zi], make_key(w, q.id));
+        }
+        if (in10) {
+          const float w = inv_depth_pinhole(q.Ai, q.Bi, q.Ci, i + 1, j);
+          if (w > 0.0f && w >= w_far && w <= w_near) atomicMin(&zk[zi + 1], make_key(w, q.id));
+        }
+        if (in01) {
+          const float w = inv_depth_pinhole(q.Ai, q.Bi, q.Ci, i, j + 1);
+          if (w > 0.0f && w >= w_far && w <= w_near) atomicMin(&zk[zi + TW], make_key(w, q.id));
+        }
+        if (in11) {
+          const float w = inv_depth_pinhole(q.Ai, q.Bi, q.Ci, i + 1, j + 1);
+          if (w > 0.0f && w >= w_far && w <= w_near) atomicMin(&zk[zi + TW + 1], make_key(w, q.id));
         }
       }
     }
