@@ -977,27 +977,30 @@ __device__ __forceinline__ void raster_block(const WaveArgs &a, int tile, int q,
         for (int v = u; v < 6; ++v) acc[qk++] += w * J[u] * J[v];
     }
   }
-  // fixed-order reduction: warp butterflies (FP32), then FP64 over warps
+  // fixed-order reduction: a reduce-scatter butterfly over the warp (lane L ends with the
+  // warp's sum of value L), integer counts by warp reduction, then FP64 over warps
+  float v[32];
 #pragma unroll
-  for (int k = 0; k < 28; ++k) {
-    float v = acc[k];
+  for (int k = 0; k < 28; ++k) v[k] = acc[k];
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    acc[k] = v;
+  for (int k = 28; k < 32; ++k) v[k] = 0.0f;
+  const int warp = tid >> 5, lane = tid & 31;
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) {
+    const bool hi = (lane & off) != 0;
+#pragma unroll
+    for (int m = 0; m < off; ++m) {
+      const float keep = hi ? v[m + off] : v[m];
+      const float send = hi ? v[m] : v[m + off];
+      v[m] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+    }
   }
+  // after the butterfly, lane L holds the warp's sum of value L
+  if (lane < 28) red[warp][lane] = v[0];
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
-    int v = cnt6[k];
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    cnt6[k] = v;
-  }
-  const int warp = tid >> 5, lane = tid & 31;
-  if (lane == 0) {
-#pragma unroll
-    for (int k = 0; k < 28; ++k) red[warp][k] = acc[k];
-#pragma unroll
-    for (int k = 0; k < 6; ++k) redc[warp][k] = cnt6[k];
+    const unsigned c = __reduce_add_sync(0xffffffffu, (unsigned)cnt6[k]);
+    if (lane == 0) redc[warp][k] = (int)c;
   }
   __syncthreads();
   if (tid < kNumVals) {
