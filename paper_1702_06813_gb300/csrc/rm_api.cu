@@ -88,7 +88,7 @@ struct rm_map {
   unsigned *d_status = nullptr;
   unsigned *h_status = nullptr;
   rm_tuning tuning{};
-  int cap = 2048;
+  int cap = 512;  // records per tile bin; doubled whenever a bin overflows
   std::mutex mu;
   // profiling: events recorded around each kernel of each wave while enabled
   bool prof = false;

@@ -1359,6 +1359,35 @@ __global__ void k_lm_init_batch(LMState *st, const double *T0, int n, LMArgs a, 
   if (k < n) lm_init_dev(st[k], T0 + 16 * (long long)k, a, Ms + 12 * (long long)k, skip + k);
 }
 
+// Phase bodies of the persistent kernel, each compiled out of line so that its register
+// allocation is its own (as in the per-phase kernels) rather than the union of all phases.
+__device__ __noinline__ void persist_cull(const WaveArgs &a, int item, float *sM) {
+  const int c1 = min((item + 1) * kPersistCull, (a.n_clusters + 255) / 256);
+  for (int c = item * kPersistCull; c < c1; ++c) {
+    cull_block(a, 0, c, sM);
+    __syncthreads();
+  }
+}
+
+__device__ __noinline__ void persist_setup(const WaveArgs &a, int worker, int nworkers,
+                                           SetupSmem &sm) {
+  setup_block(a, 0, worker, nworkers, sm);
+}
+
+template <int MODEL>
+__device__ __noinline__ void persist_raster(const WaveArgs &a, int item,
+                                            RasterSmem<1024, MODEL> &sm) {
+  const int t1 = min((item + 1) * kPersistTiles, a.tg.ntiles);
+  for (int t = item * kPersistTiles; t < t1; ++t) {
+    raster_block<32, 32, kCostGrad, MODEL>(a, t, 0, sm);
+    __syncthreads();
+  }
+}
+
+__device__ __noinline__ void persist_reduce(const WaveArgs &a, double *vals) {
+  reduce_block(a, 0, vals);
+}
+
 // Copies an LM state with L2 loads (another SM may have written it during this kernel).
 __device__ __noinline__ void lm_load_cg(const LMState *src, LMState &dst) {
   const long long *s = reinterpret_cast<const long long *>(src);
@@ -1428,25 +1457,13 @@ __global__ void __launch_bounds__(kThreads, RM_PERSIST_MIN_BLOCKS) k_persist(Bat
     const bool skip = skipped(a);
     if (!skip) {
       switch (item.y) {
-        case 0: {  // kPersistCull chunks of 256 clusters
-          const int c1 = min((item.z + 1) * kPersistCull, (a.n_clusters + 255) / 256);
-          for (int c = item.z * kPersistCull; c < c1; ++c) {
-            cull_block(a, 0, c, s_M);
-            __syncthreads();
-          }
+        case 0: persist_cull(a, item.z, s_M); break;
+        case 1: persist_setup(a, item.z, b.need[3 * item.x + 1], u.su); break;
+        case 2:
+          if (a.cam.model == 0) persist_raster<0>(a, item.z, u.r0);
+          else persist_raster<1>(a, item.z, u.r1);
           break;
-        }
-        case 1: setup_block(a, 0, item.z, b.need[3 * item.x + 1], u.su); break;
-        case 2: {  // kPersistTiles tiles
-          const int t1 = min((item.z + 1) * kPersistTiles, a.tg.ntiles);
-          for (int t = item.z * kPersistTiles; t < t1; ++t) {
-            if (a.cam.model == 0) raster_block<32, 32, kCostGrad, 0>(a, t, 0, u.r0);
-            else raster_block<32, 32, kCostGrad, 1>(a, t, 0, u.r1);
-            __syncthreads();
-          }
-          break;
-        }
-        default: reduce_block(a, 0, u.vals); break;
+        default: persist_reduce(a, u.vals); break;
       }
     }
     if (item.y == 3 && b.lm) {
