@@ -280,8 +280,9 @@ def run_tracking(a):
                    "triangles": mesh.n_tris, "sensors": ["160x120", "640x480", "1024x64 lidar"],
                    "pose_evals": evals, "pose_evals_per_s": evals / (total_ms * 1e-3),
                    "plain_per_pose_frames_per_s": plain_value, "batched_over_plain": value / plain_value,
-                   "mean_pos_err_m_last_frame": float(errs[-1].mean()),
-                   "median_pos_err_m_all": float(np.median(errs))},
+                   "median_pos_err_m_all_frames": float(np.median(errs)),
+                   "agents_within_0.1m_last_frame": float(np.mean(errs[-1] < 0.1)),
+                   "agents_within_0.1m_all_frames": float(np.mean(np.all(errs < 0.1, axis=0)))},
         "gpu_launches": a.frames}))
 
 

@@ -85,7 +85,7 @@ typedef struct {
   float near_m;             /* render clip: only depths >= near_m are kept (> 0) */
   float far_m;              /* and <= far_m (INFINITY allowed) */
   const float *rays;        /* RM_RAYTABLE only: H*W*3 float32 unit rays, camera frame, host
-                               or device; each ray within 0.5 px of the layout above */
+                               or device; each ray within 0.25 px of the layout above */
 } rm_intrinsics;
 
 /* Observed scan Z_s (Eq. 1): depth and class per pixel, same layout and size as `intr`. */

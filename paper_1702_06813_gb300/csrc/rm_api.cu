@@ -88,7 +88,8 @@ struct rm_map {
   unsigned *d_status = nullptr;
   unsigned *h_status = nullptr;
   rm_tuning tuning{};
-  int cap = 512;  // records per tile bin; doubled whenever a bin overflows
+  int cap = 512;      // records per pinhole tile bin; doubled whenever one overflows
+  int cap_ray = 512;  // likewise for ray-table bins
   std::mutex mu;
   // profiling: events recorded around each kernel of each wave while enabled
   bool prof = false;
@@ -262,7 +263,7 @@ TileGeom make_tiles(const rm_map *m, const rm_intrinsics *in) {
   tg.ntx = (in->width + tg.tw - 1) / tg.tw;
   tg.nty = (in->height + tg.th - 1) / tg.th;
   tg.ntiles = tg.ntx * tg.nty;
-  tg.cap = m->cap;
+  tg.cap = in->model == RM_RAYTABLE ? m->cap_ray : m->cap;
   tg.rec_bytes = in->model == RM_RAYTABLE ? (int)sizeof(rmk::RayRec) : (int)sizeof(TriRec);
   return tg;
 }
@@ -341,6 +342,16 @@ rm_status wave(rm_map *m, const WaveArgs &a, int mode, cudaStream_t s) {
   RM_CK(rmk::launch_wave(a, mode, s, m->prof ? ev : nullptr));
   m->launches += rmk::wave_kernel_launches(a, mode);
   if (m->prof) m->ev_pending.push_back({ev[0], ev[1], ev[2], ev[3], ev[4]});
+  return RM_OK;
+}
+
+// Doubles the capacity of the bins that overflowed (pinhole and ray-table tracked apart).
+rm_status grow_bins(rm_map *m, unsigned st, int attempt) {
+  const bool pin = st & rmk::kStatusOverflow, ray = st & rmk::kStatusOverflowRay;
+  if (attempt > 16 || (pin && m->cap >= (1 << 22)) || (ray && m->cap_ray >= (1 << 22)))
+    return fail(RM_EOVERFLOW, "screen-tile bin overflow at the largest capacity");
+  if (pin) m->cap *= 2;
+  if (ray) m->cap_ray *= 2;
   return RM_OK;
 }
 
@@ -517,10 +528,8 @@ rm_status run_eval(rm_map *m, const EvalReq &r, cudaStream_t s) {
     unsigned st = 0;
     RM_TRY(read_status(m, s, &st));
     if (st & rmk::kStatusTimeout) return fail(RM_ETIMEOUT, "a device-side wait ran out of time");
-    if (st & rmk::kStatusOverflow) {
-      if (m->cap >= (1 << 22) || attempt > 12)
-        return fail(RM_EOVERFLOW, "screen-tile bin overflow at the largest capacity");
-      m->cap *= 2;
+    if (st & (rmk::kStatusOverflow | rmk::kStatusOverflowRay)) {
+      RM_TRY(grow_bins(m, st, attempt));
       continue;
     }
     return RM_OK;
@@ -583,7 +592,7 @@ rm_status run_batch(rm_map *m, const rm_problem *probs, int n, const rm_cost_par
       tg[p].ntx = (in->width + 31) / 32;
       tg[p].nty = (in->height + 31) / 32;
       tg[p].ntiles = tg[p].ntx * tg[p].nty;
-      tg[p].cap = m->cap;
+      tg[p].cap = in->model == RM_RAYTABLE ? m->cap_ray : m->cap;
       tg[p].rec_bytes = in->model == RM_RAYTABLE ? (int)sizeof(rmk::RayRec) : (int)sizeof(TriRec);
       P[p] = (long long)in->width * in->height;
       tiles_total += tg[p].ntiles;
@@ -762,7 +771,7 @@ rm_status run_batch(rm_map *m, const rm_problem *probs, int n, const rm_cost_par
     char sig[512];
     std::snprintf(sig, sizeof(sig), "%p|%d|%d|%zu|%d|%d|%a|%a|%a|%a|%zu|%zu|%zu|%d", (void *)m->arena, n,
                   K, items.size(), grid, lm ? 1 : 0, la.lambda0, la.lambda_up, la.lambda_down,
-                  la.step_tol, tiles_total, px_total, rays_total, m->cap);
+                  la.step_tol, tiles_total, px_total, rays_total, m->cap * 4096 + m->cap_ray);
     std::string key(sig);
     for (int p = 0; p < n; ++p) key += "|" + std::to_string(probs[p].scan.intr.model) + "x" +
                                         std::to_string(probs[p].scan.intr.width) + "x" +
@@ -816,10 +825,8 @@ rm_status run_batch(rm_map *m, const rm_problem *probs, int n, const rm_cost_par
     unsigned st = 0;
     RM_TRY(read_status(m, s, &st));  // synchronises the stream
     if (st & rmk::kStatusTimeout) return fail(RM_ETIMEOUT, "a device-side wait ran out of time");
-    if (st & rmk::kStatusOverflow) {
-      if (m->cap >= (1 << 22) || attempt > 12)
-        return fail(RM_EOVERFLOW, "screen-tile bin overflow at the largest capacity");
-      m->cap *= 2;
+    if (st & (rmk::kStatusOverflow | rmk::kStatusOverflowRay)) {
+      RM_TRY(grow_bins(m, st, attempt));
       continue;
     }
     if (!lm) return RM_OK;
@@ -1002,7 +1009,7 @@ rm_status rm_map_set_tuning(rm_map *m, const rm_tuning *t) {
   if (!ok_tile) return fail(RM_EINVAL, "tile must be 16x16, 32x16 or 32x32");
   if (u.bin_capacity < 0 || u.wave_poses < 0) return fail(RM_EINVAL, "negative tuning value");
   m->tuning = u;
-  if (u.bin_capacity > 0) m->cap = u.bin_capacity;
+  if (u.bin_capacity > 0) m->cap = m->cap_ray = u.bin_capacity;
   return RM_OK;
 }
 
@@ -1131,7 +1138,7 @@ rm_status rm_status_sync(rm_map *m, void *stream) {
   unsigned st = 0;
   RM_TRY(read_status(m, (cudaStream_t)stream, &st));
   if (st & rmk::kStatusTimeout) return fail(RM_ETIMEOUT, "a device-side wait ran out of time");
-  if (st & rmk::kStatusOverflow) return fail(RM_EOVERFLOW, "screen-tile bin overflow");
+  if (st & (rmk::kStatusOverflow | rmk::kStatusOverflowRay)) return fail(RM_EOVERFLOW, "screen-tile bin overflow");
   return RM_OK;
 }
 
@@ -1231,10 +1238,8 @@ rm_status rm_align(rm_map *m, const rm_scan *scan, const double *init_pose,
     unsigned st = 0;
     RM_TRY(read_status(m, s, &st));  // synchronises the stream
     if (st & rmk::kStatusTimeout) return fail(RM_ETIMEOUT, "a device-side wait ran out of time");
-    if (st & rmk::kStatusOverflow) {
-      if (m->cap >= (1 << 22) || attempt > 12)
-        return fail(RM_EOVERFLOW, "screen-tile bin overflow at the largest capacity");
-      m->cap *= 2;
+    if (st & (rmk::kStatusOverflow | rmk::kStatusOverflowRay)) {
+      RM_TRY(grow_bins(m, st, attempt));
       continue;
     }
     if (on_device(pose_out)) RM_CK(cudaMemcpy(pose_out, hs.T, sizeof(double) * 16, cudaMemcpyHostToDevice));

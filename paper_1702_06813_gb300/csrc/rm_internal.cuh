@@ -26,8 +26,10 @@ constexpr float kGuardPx = 2097152.0f;           // 2^21 px: snapped |x| < 2^29
 constexpr unsigned long long kKeyEmpty = ~0ull;
 constexpr int kSentinel = (int)0x80000000;       // vs.x of a vertex that cannot be snapped
 constexpr int kNumVals = 34;                      // counts 6 | e_ls | grad 6 | jtj 21
-constexpr unsigned kStatusOverflow = 1u;
+constexpr unsigned kStatusOverflow = 1u;     // a pinhole bin overflowed
 constexpr unsigned kStatusTimeout = 2u;
+constexpr unsigned kStatusOverflowRay = 4u;  // a ray-table bin overflowed
+constexpr float kRayMarginPx = 0.25f;        // ray-table rectangles: margin in pixels
 constexpr int kThreads = 256;                     // raster CTA
 
 struct DevCam {

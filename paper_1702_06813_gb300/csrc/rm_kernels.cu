@@ -234,7 +234,7 @@ __device__ __forceinline__ void emit_ray(const RayRec &rr, int i0, int i1, int j
         dst[2] = src[2];
         dst[3] = w3;
       } else {
-        atomicOr(a.status, kStatusOverflow);
+        atomicOr(a.status, kStatusOverflowRay);
       }
     }
 }
@@ -242,7 +242,9 @@ __device__ __forceinline__ void emit_ray(const RayRec &rr, int i0, int i1, int j
 // Ray-table triangle: contract side normals and inverse-depth normal, then a conservative
 // pixel rectangle from the layout (azimuth from the vertices' smallest enclosing arc, full
 // when a pole is inside; elevation from the vertices widened by the great-circle bulge
-// bound z / cos(L/2), L the longest edge angle), two pixels of margin, split at the seam.
+// bound z / cos(L/2), L the longest edge angle), a quarter-pixel margin (the FP32 angles
+// are good to ~1e-6 rad and the table's rays lie within that margin of the layout), split
+// at the seam. A triangle between pixel rays gets an empty rectangle and no record.
 __device__ __forceinline__ void setup_ray(const float3 v[3], const float4 u[3], const int gid[3],
                                           unsigned id, const WaveArgs &a, int *counts,
                                           unsigned char *bins) {
@@ -296,8 +298,8 @@ __device__ __forceinline__ void setup_ray(const float3 v[3], const float4 u[3], 
   if (has_up) zmax = 1.0f;
   if (has_dn) zmin = -1.0f;
   const float el_hi = asinf(zmax), el_lo = asinf(zmin);
-  const int j0 = max(0, (int)ceilf((cam.el0 - el_hi) / cam.el_step - 2.0f));
-  const int j1 = min(cam.H - 1, (int)floorf((cam.el0 - el_lo) / cam.el_step + 2.0f));
+  const int j0 = max(0, (int)ceilf((cam.el0 - el_hi) / cam.el_step - kRayMarginPx));
+  const int j1 = min(cam.H - 1, (int)floorf((cam.el0 - el_lo) / cam.el_step + kRayMarginPx));
   if (j0 > j1) return;
   if (has_up || has_dn) {
     emit_ray(rr, 0, cam.W - 1, j0, j1, a, counts, bins);
@@ -313,8 +315,8 @@ __device__ __forceinline__ void setup_ray(const float3 v[3], const float4 u[3], 
   if (g20 >= g01 && g20 >= g12) { lo = s0; hi = s2; }
   else if (g01 >= g12) { lo = s1; hi = s0 + twopi; }
   else { lo = s2; hi = s1 + twopi; }
-  const int ilo = (int)ceilf((lo - cam.az0) / cam.az_step - 0.5f - 2.0f);
-  const int ihi = (int)floorf((hi - cam.az0) / cam.az_step - 0.5f + 2.0f);
+  const int ilo = (int)ceilf((lo - cam.az0) / cam.az_step - 0.5f - kRayMarginPx);
+  const int ihi = (int)floorf((hi - cam.az0) / cam.az_step - 0.5f + kRayMarginPx);
   const int n = ihi - ilo + 1;
   if (n >= cam.W) {
     emit_ray(rr, 0, cam.W - 1, j0, j1, a, counts, bins);

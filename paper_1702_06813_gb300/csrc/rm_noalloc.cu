@@ -142,7 +142,7 @@ extern "C" rm_status rm_cost_grad_noalloc(const rm_map *map, const rm_scan *scan
       (e = cudaStreamSynchronize(s)) != cudaSuccess)
     return na_fail(RM_ECUDA, std::string("status read: ") + cudaGetErrorString(e));
   if (h_status & rmk::kStatusTimeout) return na_fail(RM_ETIMEOUT, "a device-side wait ran out of time");
-  if (h_status & rmk::kStatusOverflow)
+  if (h_status & (rmk::kStatusOverflow | rmk::kStatusOverflowRay))
     return na_fail(RM_EOVERFLOW, "a screen-tile bin overflowed the static scratch (capacity " +
                                      std::to_string(cap) + " records per tile)");
   return RM_OK;
