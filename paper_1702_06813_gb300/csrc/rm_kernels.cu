@@ -465,8 +465,8 @@ __global__ void __launch_bounds__(256) k_setup(WaveArgs a) {
 
 // ------------------------------------------------------------------ raster + epilogue
 
-constexpr int kRecMaxPinhole = 512;  // bin records staged in shared memory per round (48 B)
-constexpr int kRecMaxRay = 384;      // (64 B)
+constexpr int kRecMaxPinhole = 256;  // bin records staged in shared memory per round (48 B)
+constexpr int kRecMaxRay = 192;      // (64 B)
 
 // Exact edge test with int32 operands and 64-bit products: E = dx (py - ya) - dy (px - xa),
 // covered iff E > 0 or E == 0 on a top or left edge.
@@ -761,7 +761,7 @@ __device__ __forceinline__ bool raster_tile_ray(unsigned long long *zk, RayRec *
 #endif
 
 #ifndef RM_RASTER_MIN_BLOCKS
-#define RM_RASTER_MIN_BLOCKS 5  // resident CTAs per SM the register budget is sized for
+#define RM_RASTER_MIN_BLOCKS 6  // resident CTAs per SM the register budget is sized for
 #endif
 
 template <int NP, int MODEL>
