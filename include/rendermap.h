@@ -111,7 +111,7 @@ typedef struct {
 
 /* Execution knobs; a zeroed struct (or NULL) means "library defaults / autotuned". */
 typedef struct {
-  int32_t tile_w, tile_h;   /* screen tile, pixels: 16x16, 32x16 or 32x32 */
+  int32_t tile_w, tile_h;   /* screen tile, pixels: 16x16, 32x16, 32x32 or 64x32 */
   int32_t bin_capacity;     /* triangle records per tile bin (grown on overflow) */
   int32_t wave_poses;       /* poses processed together per kernel wave */
   int32_t async_status;     /* 1: do not read the device status back (graph capture);

@@ -14,7 +14,7 @@ import torch
 
 from . import rendermap as rm
 
-TILES = ((32, 32), (32, 16), (16, 16))
+TILES = ((64, 32), (32, 32), (32, 16), (16, 16))
 WAVES = (16, 32, 64, 128)
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "rendermap_autotune.json")
 

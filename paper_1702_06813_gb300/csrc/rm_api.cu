@@ -1004,9 +1004,10 @@ rm_status rm_map_set_tuning(rm_map *m, const rm_tuning *t) {
   std::lock_guard<std::mutex> lk(m->mu);
   rm_tuning z{};
   const rm_tuning &u = t ? *t : z;
-  bool ok_tile = (u.tile_w == 0 && u.tile_h == 0) || (u.tile_w == 32 && u.tile_h == 32) ||
-                 (u.tile_w == 32 && u.tile_h == 16) || (u.tile_w == 16 && u.tile_h == 16);
-  if (!ok_tile) return fail(RM_EINVAL, "tile must be 16x16, 32x16 or 32x32");
+  bool ok_tile = (u.tile_w == 0 && u.tile_h == 0) || (u.tile_w == 64 && u.tile_h == 32) ||
+                 (u.tile_w == 32 && u.tile_h == 32) || (u.tile_w == 32 && u.tile_h == 16) ||
+                 (u.tile_w == 16 && u.tile_h == 16);
+  if (!ok_tile) return fail(RM_EINVAL, "tile must be 16x16, 32x16, 32x32 or 64x32");
   if (u.bin_capacity < 0 || u.wave_poses < 0) return fail(RM_EINVAL, "negative tuning value");
   m->tuning = u;
   if (u.bin_capacity > 0) m->cap = m->cap_ray = u.bin_capacity;

@@ -2,14 +2,17 @@
 //
 // Per pose (one wave of poses at a time, blockIdx.y = pose within the wave):
 //   k_pose_to_m   camera-to-world FP64 pose -> world-to-camera FP32 3x4 (Eq. 1's T(X) -> Y)
-//   k_vertex      camera-space vertices and their 1/256-px snapped projections
-//   k_setup       per triangle: near-plane cut, cull, depth plane, append to screen-tile bins
+//   k_cull        per cluster of <= 64 triangles: bounding sphere against the view volume
+//   k_setup       per visible cluster: camera-space vertices and their 1/256-px snapped
+//                 projections, then per triangle: near-plane cut, cull, depth plane, append
+//                 to the screen-tile bins
 //   k_raster      one CTA per (pose, tile): bins staged into shared memory with bulk (TMA)
 //                 copies, integer edge functions with the top-left rule, 64-bit
 //                 depth|id z-test by shared-memory atomicMin (the z-buffer R(Y) of Sec. III);
 //                 then the fused epilogue: Table I per pixel (Sec. III.B), the truncated
 //                 least-squares residual, its pose Jacobian, and a fixed-order reduction
 //   k_reduce      per pose: fixed-order sum of the per-tile partials
+// k_persist runs the same phases for a batch of problems (and LM iterations) in one launch.
 #include <cfloat>
 #include <cmath>
 
@@ -214,6 +217,61 @@ __device__ __forceinline__ void emit_piece(int x0, int y0, int x1, int y1, int x
     }
 }
 
+// Warp-collective form of emit_piece (all 32 lanes call it; `valid` marks the lanes that
+// hold a piece). The lanes append to the tiles their pieces overlap one tile per step; the
+// lanes that target the same tile in a step take consecutive slots through one atomic add
+// by their lowest lane, so a cluster's triangles, which mostly share a tile or two, cost
+// a few atomics per step instead of one per triangle.
+__device__ __forceinline__ void emit_piece_warp(bool valid, int x0, int y0, int x1, int y1,
+                                                int x2, int y2, float Ai, float Bi, float Ci,
+                                                unsigned id, const WaveArgs &a, int *counts,
+                                                unsigned char *bins_b) {
+  TriRec *bins = reinterpret_cast<TriRec *>(bins_b);
+  const TileGeom &tg = a.tg;
+  const int lane = threadIdx.x & 31;
+  long long area = (long long)(x1 - x0) * (y2 - y0) - (long long)(y1 - y0) * (x2 - x0);
+  if (area < 0) {
+    int t = x1; x1 = x2; x2 = t;
+    t = y1; y1 = y2; y2 = t;
+  }
+  const int W = a.cam.W, H = a.cam.H;
+  const int xmin = min(x0, min(x1, x2)), xmax = max(x0, max(x1, x2));
+  const int ymin = min(y0, min(y1, y2)), ymax = max(y0, max(y1, y2));
+  const int i0 = max((xmin + 127) >> 8, 0), i1 = min((xmax - 128) >> 8, W - 1);
+  const int j0 = max((ymin + 127) >> 8, 0), j1 = min((ymax - 128) >> 8, H - 1);
+  valid = valid && area != 0 && i0 <= i1 && j0 <= j1;
+  int tx0 = 0, nx = 0, ty0 = 0, nt = 0;
+  if (valid) {
+    tx0 = i0 / tg.tw;
+    ty0 = j0 / tg.th;
+    nx = i1 / tg.tw - tx0 + 1;
+    nt = nx * (j1 / tg.th - ty0 + 1);
+  }
+  const int4 w0 = make_int4(x0, y0, x1, y1);
+  const int4 w1 = make_int4(x2, y2, __float_as_int(Ai), __float_as_int(Bi));
+  const int4 w2 = make_int4(__float_as_int(Ci), (int)id, 0, 0);
+  for (int k = 0; __any_sync(0xffffffffu, k < nt); ++k) {
+    const bool has = k < nt;
+    const int tile = has ? (ty0 + k / nx) * tg.ntx + tx0 + k % nx : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, tile);
+    const int leader = __ffs(peers) - 1;
+    int base = 0;
+    if (has && lane == leader) base = atomicAdd(&counts[tile], __popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (has) {
+      const int slot = base + __popc(peers & ((1u << lane) - 1u));
+      if (slot < tg.cap) {
+        int4 *dst = reinterpret_cast<int4 *>(bins + (long long)tile * tg.cap + slot);
+        dst[0] = w0;
+        dst[1] = w1;
+        dst[2] = w2;
+      } else {
+        atomicOr(a.status, kStatusOverflow);
+      }
+    }
+  }
+}
+
 // Appends a ray-table record to the bins of every tile its pixel rectangle overlaps.
 __device__ __forceinline__ void emit_ray(const RayRec &rr, int i0, int i1, int j0, int j1,
                                          const WaveArgs &a, int *counts, unsigned char *bins_b) {
@@ -385,10 +443,10 @@ __device__ __forceinline__ void setup_block(const WaveArgs &a, int q, int worker
       s_gid[warp][k] = gv;
     }
     __syncwarp();
-    for (int k = lane; k < info.w; k += 32) {
-      const uchar4 t = a.cl_tris[info.y + k];
-      const unsigned id = (unsigned)a.cl_ids[info.y + k];
-      if (raytable) {
+    if (raytable) {
+      for (int k = lane; k < info.w; k += 32) {
+        const uchar4 t = a.cl_tris[info.y + k];
+        const unsigned id = (unsigned)a.cl_ids[info.y + k];
         const int loc[3] = {t.x, t.y, t.z};
         float3 v[3];
         float4 u[3];
@@ -401,57 +459,75 @@ __device__ __forceinline__ void setup_block(const WaveArgs &a, int q, int worker
           gid[m] = s_gid[warp][loc[m]];
         }
         setup_ray(v, u, gid, id, a, counts, bins);
-        continue;
       }
-      const int2 s0 = s_vs[warp][t.x], s1 = s_vs[warp][t.y], s2 = s_vs[warp][t.z];
-      if (s0.x != kSentinel && s1.x != kSentinel && s2.x != kSentinel) {
-        // all three in front of the near plane and inside the guard band
-        const int xmin = min(s0.x, min(s1.x, s2.x)), xmax = max(s0.x, max(s1.x, s2.x));
-        const int ymin = min(s0.y, min(s1.y, s2.y)), ymax = max(s0.y, max(s1.y, s2.y));
-        if (max((xmin + 127) >> 8, 0) > min((xmax - 128) >> 8, W - 1)) continue;
-        if (max((ymin + 127) >> 8, 0) > min((ymax - 128) >> 8, H - 1)) continue;
-        const float4 p0 = s_vc[warp][t.x], p1 = s_vc[warp][t.y], p2 = s_vc[warp][t.z];
-        const PlaneN pl = plane_n(make_float3(p0.x, p0.y, p0.z), make_float3(p1.x, p1.y, p1.z),
-                                  make_float3(p2.x, p2.y, p2.z));
-        float A, B, C;
-        fold_pinhole(a.cam, pl, A, B, C);
-        emit_piece(s0.x, s0.y, s1.x, s1.y, s2.x, s2.y, A, B, C, id, a, counts, bins);
-        continue;
-      }
-      // slow path: near-plane cut and/or guard band
-      const int loc[3] = {t.x, t.y, t.z};
-      int idx[3];
-      float3 v[3];
-      bool in[3];
-      int nin = 0;
+      __syncwarp();
+      continue;
+    }
+    // pinhole: every lane of the warp steps through the cluster's triangles together, so the
+    // (at most two) pieces of a lane's triangle are appended by the warp-collective emitter
+    for (int k0 = 0; k0 < info.w; k0 += 32) {
+      const int k = k0 + lane;
+      bool va = false, vb = false;
+      int sx[4] = {0, 0, 0, 0}, sy[4] = {0, 0, 0, 0};
+      float A = 0.0f, B = 0.0f, C = 0.0f;
+      unsigned id = 0;
+      if (k < info.w) {
+        const uchar4 t = a.cl_tris[info.y + k];
+        id = (unsigned)a.cl_ids[info.y + k];
+        const int2 s0 = s_vs[warp][t.x], s1 = s_vs[warp][t.y], s2 = s_vs[warp][t.z];
+        if (s0.x != kSentinel && s1.x != kSentinel && s2.x != kSentinel) {
+          // all three in front of the near plane and inside the guard band
+          const int xmin = min(s0.x, min(s1.x, s2.x)), xmax = max(s0.x, max(s1.x, s2.x));
+          const int ymin = min(s0.y, min(s1.y, s2.y)), ymax = max(s0.y, max(s1.y, s2.y));
+          if (max((xmin + 127) >> 8, 0) <= min((xmax - 128) >> 8, W - 1) &&
+              max((ymin + 127) >> 8, 0) <= min((ymax - 128) >> 8, H - 1)) {
+            const float4 p0 = s_vc[warp][t.x], p1 = s_vc[warp][t.y], p2 = s_vc[warp][t.z];
+            const PlaneN pl = plane_n(make_float3(p0.x, p0.y, p0.z), make_float3(p1.x, p1.y, p1.z),
+                                      make_float3(p2.x, p2.y, p2.z));
+            fold_pinhole(a.cam, pl, A, B, C);
+            sx[0] = s0.x; sy[0] = s0.y; sx[1] = s1.x; sy[1] = s1.y; sx[2] = s2.x; sy[2] = s2.y;
+            va = true;
+          }
+        } else {
+          // slow path: near-plane cut and/or guard band
+          const int loc[3] = {t.x, t.y, t.z};
+          int idx[3];
+          float3 v[3];
+          bool in[3];
+          int nin = 0;
 #pragma unroll
-      for (int m = 0; m < 3; ++m) {
-        const float4 p = s_vc[warp][loc[m]];
-        v[m] = make_float3(p.x, p.y, p.z);
-        idx[m] = s_gid[warp][loc[m]];
-        in[m] = v[m].z >= near_m;
-        nin += in[m];
-      }
-      if (nin == 0 || nin == 3) continue;  // all behind, or a vertex beyond the guard band
-      const PlaneN pl = plane_n(v[0], v[1], v[2]);
-      float A, B, C;
-      fold_pinhole(a.cam, pl, A, B, C);
-      float3 poly[4];
-      int n = 0;
+          for (int m = 0; m < 3; ++m) {
+            const float4 p = s_vc[warp][loc[m]];
+            v[m] = make_float3(p.x, p.y, p.z);
+            idx[m] = s_gid[warp][loc[m]];
+            in[m] = v[m].z >= near_m;
+            nin += in[m];
+          }
+          // all behind, or all in front with a vertex beyond the guard band: nothing drawn
+          if (nin != 0 && nin != 3) {
+            const PlaneN pl = plane_n(v[0], v[1], v[2]);
+            fold_pinhole(a.cam, pl, A, B, C);
+            float3 poly[4];
+            int n = 0;
 #pragma unroll
-      for (int m = 0; m < 3; ++m) {
-        const int nx = (m + 1) % 3;
-        if (in[m]) poly[n++] = v[m];
-        if (in[m] != in[nx])
-          poly[n++] = idx[m] < idx[nx] ? near_cut(v[m], v[nx], near_m) : near_cut(v[nx], v[m], near_m);
+            for (int m = 0; m < 3; ++m) {
+              const int nx = (m + 1) % 3;
+              if (in[m]) poly[n++] = v[m];
+              if (in[m] != in[nx])
+                poly[n++] = idx[m] < idx[nx] ? near_cut(v[m], v[nx], near_m) : near_cut(v[nx], v[m], near_m);
+            }
+            bool ok = true;
+#pragma unroll
+            for (int m = 0; m < 4; ++m)
+              if (m < n) ok = ok && snap(a.cam, poly[m].x, poly[m].y, poly[m].z, sx[m], sy[m]);
+            va = ok;
+            vb = ok && n == 4;
+          }
+        }
       }
-      int sx[4], sy[4];
-      bool ok = true;
-      for (int m = 0; m < n; ++m) ok = ok && snap(a.cam, poly[m].x, poly[m].y, poly[m].z, sx[m], sy[m]);
-      if (!ok) continue;
-      emit_piece(sx[0], sy[0], sx[1], sy[1], sx[2], sy[2], A, B, C, id, a, counts, bins);
-      if (n == 4)
-        emit_piece(sx[0], sy[0], sx[2], sy[2], sx[3], sy[3], A, B, C, id, a, counts, bins);
+      emit_piece_warp(va, sx[0], sy[0], sx[1], sy[1], sx[2], sy[2], A, B, C, id, a, counts, bins);
+      if (__any_sync(0xffffffffu, vb))
+        emit_piece_warp(vb, sx[0], sy[0], sx[2], sy[2], sx[3], sy[3], A, B, C, id, a, counts, bins);
     }
     __syncwarp();
   }
@@ -465,7 +541,7 @@ __global__ void __launch_bounds__(256) k_setup(WaveArgs a) {
 
 // ------------------------------------------------------------------ raster + epilogue
 
-constexpr int kRecMaxPinhole = 256;  // bin records staged in shared memory per round (48 B)
+constexpr int kRecMaxPinhole = 192;  // bin records staged in shared memory per round (48 B)
 constexpr int kRecMaxRay = 192;      // (64 B)
 
 // Exact edge test with int32 operands and 64-bit products: E = dx (py - ya) - dy (px - xa),
@@ -482,10 +558,15 @@ constexpr int kRecFallback = 1 << 28;  // record keeps its snapped vertices (int
 // each edge function into an exact int32 affine function of the pixel offset (di, dj) inside
 // that rectangle, E = E0 + di*sx + dj*sy with the top-left bias folded into E0. Edges that
 // hold on the whole rectangle become E = 0; a record whose rectangle misses one edge's half
-// plane is dropped. Long edges whose range over the rectangle could leave int32 keep the
-// record's vertices for the int64 test. Returns the rectangle's pixel count (0 = nothing).
+// plane is dropped. Over the rectangle every value of E lies strictly between -(|ax| + |ay|)
+// and |ax| + |ay| (ax, ay its extent along x and y), which is below 2^31 when
+// 256 (|dx| + |dy|) (max(TW, TH) - 1) < 2^31: edges longer than that keep the record's
+// vertices for the int64 test. Returns the rectangle's 2x2-quad count (0 = nothing).
+template <int TW, int TH>
 __device__ __forceinline__ int derive_rect(TriRec *rec, int4 *hdr, int k, int cnt, int ox,
                                            int oy, int xe, int ye) {
+  constexpr int kEdgeMax = (TW > 32 || TH > 32) ? (1 << 17) : (1 << 18);
+  static_assert(256ll * kEdgeMax * ((TW > TH ? TW : TH) - 1) < (1ll << 31), "int32 edge range");
   if (k >= cnt) return 0;
   TriRec &r = rec[k];
   const int xmin = min(r.x0, min(r.x1, r.x2)), xmax = max(r.x0, max(r.x1, r.x2));
@@ -509,7 +590,7 @@ __device__ __forceinline__ int derive_rect(TriRec *rec, int4 *hdr, int k, int cn
     if (hi < 0) return 0;              // no pixel of the rectangle is on the inner side
     if (lo >= 0) {                     // the whole rectangle is on the inner side
       e0[e] = 0; sx[e] = 0; sy[e] = 0;
-    } else if (abs(dx) + abs(dy) <= (1 << 18)) {
+    } else if (abs(dx) + abs(dy) <= kEdgeMax) {
       e0[e] = (int)E0; sx[e] = -256 * dy; sy[e] = 256 * dx;
     } else {
       fallback = true;
@@ -521,7 +602,7 @@ __device__ __forceinline__ int derive_rect(TriRec *rec, int4 *hdr, int k, int cn
   if (!fallback) {
     r.x0 = sx[0]; r.y0 = sy[0]; r.x1 = sx[1]; r.y1 = sy[1]; r.x2 = sx[2]; r.y2 = sy[2];
   }
-  r.pad = (i0 - ox) | ((j0 - oy) << 8) | (bw << 16) | (bh << 22) | (fallback ? kRecFallback : 0);
+  r.pad = (i0 - ox) | ((j0 - oy) << 8) | ((bw - 1) << 16) | ((bh - 1) << 22) | (fallback ? kRecFallback : 0);
   return qw * qh;
 }
 
@@ -550,9 +631,12 @@ __device__ __forceinline__ bool raster_tile(unsigned long long *zk, TriRec *stag
                                             const TriRec *recs, int n, int ox, int oy, int xe,
                                             int ye, const DevCam &cam) {
   constexpr int kRecMax = kRecMaxPinhole;
+  static_assert(kRecMax <= kThreads, "one record per thread");
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int NW = kThreads / 32;
-  const float w_near = cam.w_near, w_far = cam.w_far;
+  // kept iff 0 < w, w_far <= w <= w_near: w_far >= 0, so the first two tests are one
+  // comparison with the larger of w_far and the smallest positive (subnormal) float
+  const float w_lo = fmaxf(cam.w_far, __int_as_float(1)), w_hi = cam.w_near;
   unsigned phase = 0;
   for (int r0 = 0; r0 < n; r0 += kRecMax) {
     const int cnt = min(kRecMax, n - r0);
@@ -567,10 +651,9 @@ __device__ __forceinline__ bool raster_tile(unsigned long long *zk, TriRec *stag
       return false;
     }
     phase ^= 1u;
-    // rectangle sizes of records 2t and 2t+1, block-wide exclusive scan in record order
-    const int n0 = derive_rect(stage, hdr, 2 * tid, cnt, ox, oy, xe, ye);
-    const int n1 = derive_rect(stage, hdr, 2 * tid + 1, cnt, ox, oy, xe, ye);
-    int incl = n0 + n1;
+    // quad count of record t, block-wide exclusive scan in record order
+    const int n0 = derive_rect<TW, TH>(stage, hdr, tid, cnt, ox, oy, xe, ye);
+    int incl = n0;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
       const int v = __shfl_up_sync(0xffffffffu, incl, off);
@@ -584,9 +667,7 @@ __device__ __forceinline__ bool raster_tile(unsigned long long *zk, TriRec *stag
       before += w < warp ? wtot[w] : 0;
       F += wtot[w];
     }
-    const int ex = before + incl - (n0 + n1);
-    if (2 * tid < cnt) S[2 * tid] = ex;
-    if (2 * tid + 1 < cnt) S[2 * tid + 1] = ex + n0;
+    if (tid < cnt) S[tid] = before + incl - n0;
     if (tid == 0) S[cnt] = F;
     __syncthreads();
     const int lo = (int)(((long long)F * warp) / NW), hi = (int)(((long long)F * (warp + 1)) / NW);
@@ -608,14 +689,16 @@ __device__ __forceinline__ bool raster_tile(unsigned long long *zk, TriRec *stag
         const TriRec &q = stage[r];
         const int4 h = hdr[r];
         const int l = f - sr;
-        const int bw = (q.pad >> 16) & 0x3f, bh = (q.pad >> 22) & 0x3f;
+        const int pad = q.pad;
+        const int bw = ((pad >> 16) & 0x3f) + 1, bh = ((pad >> 22) & 0x3f) + 1;
         const int qw = (bw + 1) >> 1;
         const int qj = __float2int_rz(__fmul_rn(__int2float_rn(l) + 0.5f, __int_as_float(h.w)));
         const int di = 2 * (l - qj * qw), dj = 2 * qj;
-        const int i = ox + (q.pad & 0xff) + di, j = oy + ((q.pad >> 8) & 0xff) + dj;
+        const int li = (pad & 0xff) + di, lj = ((pad >> 8) & 0xff) + dj;
+        const int i = ox + li, j = oy + lj;
         const bool has_r = di + 1 < bw, has_d = dj + 1 < bh;
         bool in00, in10, in01, in11;
-        if (!(q.pad & kRecFallback)) {
+        if (!(pad & kRecFallback)) {
           const int a = h.x + di * q.x0 + dj * q.y0;
           const int b = h.y + di * q.x1 + dj * q.y1;
           const int c = h.z + di * q.x2 + dj * q.y2;
@@ -630,23 +713,19 @@ __device__ __forceinline__ bool raster_tile(unsigned long long *zk, TriRec *stag
           in01 = has_d && covers_exact(q, i, j + 1);
           in11 = has_r && has_d && covers_exact(q, i + 1, j + 1);
         }
-        const int zi = (j - oy) * TW + (i - ox);
-        if (in00) {
-          const float w = inv_depth_pinhole(q.Ai, q.Bi, q.Ci, i, j);
-          if (w > 0.0f && w >= w_far && w <= w_near) atomicMin(&zk[zi], make_key(w, q.id));
-        }
-        if (in10) {
-          const float w = inv_depth_pinhole(q.Ai, q.Bi, q.Ci, i + 1, j);
-          if (w > 0.0f && w >= w_far && w <= w_near) atomicMin(&zk[zi + 1], make_key(w, q.id));
-        }
-        if (in01) {
-          const float w = inv_depth_pinhole(q.Ai, q.Bi, q.Ci, i, j + 1);
-          if (w > 0.0f && w >= w_far && w <= w_near) atomicMin(&zk[zi + TW], make_key(w, q.id));
-        }
-        if (in11) {
-          const float w = inv_depth_pinhole(q.Ai, q.Bi, q.Ci, i + 1, j + 1);
-          if (w > 0.0f && w >= w_far && w <= w_near) atomicMin(&zk[zi + TW + 1], make_key(w, q.id));
-        }
+        // inverse depth at the four samples, each exactly inv_depth_pinhole's expression
+        // (i + 1.5 = (i + .5) + 1 and j + 1.5 are exact in FP32)
+        const float fi = __fadd_rn(__int2float_rn(i), 0.5f), fj = __fadd_rn(__int2float_rn(j), 0.5f);
+        const float fi1 = __fadd_rn(fi, 1.0f), fj1 = __fadd_rn(fj, 1.0f);
+        const float row0 = __fmaf_rn(q.Bi, fj, q.Ci), row1 = __fmaf_rn(q.Bi, fj1, q.Ci);
+        const float w00 = __fmaf_rn(q.Ai, fi, row0), w10 = __fmaf_rn(q.Ai, fi1, row0);
+        const float w01 = __fmaf_rn(q.Ai, fi, row1), w11 = __fmaf_rn(q.Ai, fi1, row1);
+        const unsigned id = q.id;
+        const int zi = lj * TW + li;
+        if (in00 && w00 >= w_lo && w00 <= w_hi) atomicMin(&zk[zi], make_key(w00, id));
+        if (in10 && w10 >= w_lo && w10 <= w_hi) atomicMin(&zk[zi + 1], make_key(w10, id));
+        if (in01 && w01 >= w_lo && w01 <= w_hi) atomicMin(&zk[zi + TW], make_key(w01, id));
+        if (in11 && w11 >= w_lo && w11 <= w_hi) atomicMin(&zk[zi + TW + 1], make_key(w11, id));
       }
     }
     __syncthreads();
@@ -680,6 +759,7 @@ __device__ __forceinline__ bool raster_tile_ray(unsigned long long *zk, RayRec *
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int NW = kThreads / 32;
   constexpr int kRecMax = kRecMaxRay;
+  static_assert(kRecMax <= kThreads, "one record per thread");
   const float w_near = cam.w_near, w_far = cam.w_far;
   unsigned phase = 0;
   for (int r0 = 0; r0 < n; r0 += kRecMax) {
@@ -695,10 +775,9 @@ __device__ __forceinline__ bool raster_tile_ray(unsigned long long *zk, RayRec *
       return false;
     }
     phase ^= 1u;
-    // records 2t and 2t+1 per thread keep the scan in record order
-    const int n0 = derive_ray_rect(stage, 2 * tid, cnt, ox, oy, xe, ye);
-    const int n1 = derive_ray_rect(stage, 2 * tid + 1, cnt, ox, oy, xe, ye);
-    int incl = n0 + n1;
+    // pixel count of record t, block-wide exclusive scan in record order
+    const int n0 = derive_ray_rect(stage, tid, cnt, ox, oy, xe, ye);
+    int incl = n0;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
       const int v = __shfl_up_sync(0xffffffffu, incl, off);
@@ -712,9 +791,7 @@ __device__ __forceinline__ bool raster_tile_ray(unsigned long long *zk, RayRec *
       before += w < warp ? wtot[w] : 0;
       F += wtot[w];
     }
-    const int ex = before + incl - (n0 + n1);
-    if (2 * tid < cnt) S[2 * tid] = ex;
-    if (2 * tid + 1 < cnt) S[2 * tid + 1] = ex + n0;
+    if (tid < cnt) S[tid] = before + incl - n0;
     if (tid == 0) S[cnt] = F;
     __syncthreads();
     const int lo = (int)(((long long)F * warp) / NW), hi = (int)(((long long)F * (warp + 1)) / NW);
@@ -767,7 +844,7 @@ __device__ __forceinline__ bool raster_tile_ray(unsigned long long *zk, RayRec *
 template <int NP, int MODEL>
 struct RasterSmem {
   static constexpr int NW = kThreads / 32;
-  // pinhole: 512 records + their int4 edge headers; ray table: 384 records + the tile's rays
+  // pinhole: staged records + their int4 edge headers; ray table: records + the tile's rays
   static constexpr int kBuf = MODEL == 0 ? kRecMaxPinhole * (48 + 16) : kRecMaxRay * 64 + 12 * NP;
   unsigned long long zk[NP];
   float M[12];
@@ -896,7 +973,9 @@ __device__ __forceinline__ void raster_block(const WaveArgs &a, int tile, int q,
   }
 
   // ---- fused Table I + least-squares residual (+ adjoint) epilogue
-  int cnt6[6] = {0, 0, 0, 0, 0, 0};
+  // per-thread outcome counts, 5 bits each (a thread sees at most NP / kThreads pixels)
+  static_assert(NP / kThreads < 32, "count fields");
+  unsigned cnt6 = 0;
   float acc[28];
 #pragma unroll
   for (int k = 0; k < 28; ++k) acc[k] = 0.0f;
@@ -909,6 +988,7 @@ __device__ __forceinline__ void raster_block(const WaveArgs &a, int tile, int q,
   }
   const float eps = a.prm.eps;
   const float ifx = 1.0f / a.cam.fx, ify = 1.0f / a.cam.fy;
+#pragma unroll 1
   for (int p = tid; p < NP; p += kThreads) {
     const int i = ox + p % TW, j = oy + p / TW;
     if (i > xe || j > ye) continue;
@@ -928,7 +1008,7 @@ __device__ __forceinline__ void raster_block(const WaveArgs &a, int tile, int q,
     if (mc == 0) oc = sc == 0 ? (fabsf(dz) <= eps ? 0 : 1) : (dz > 0.0f ? 2 : 3);
     else if (sc == 0) oc = dz <= 0.0f ? 4 : 5;
     else continue;  // FU / FU: ignore
-    cnt6[oc] += 1;
+    cnt6 += 1u << (5 * oc);
     float r, w, sgn = 0.0f;
     switch (oc) {
       case 0: w = a.prm.w_fofo; r = dz; sgn = 1.0f; break;
@@ -980,7 +1060,8 @@ __device__ __forceinline__ void raster_block(const WaveArgs &a, int tile, int q,
     }
   }
   // fixed-order reduction: a reduce-scatter butterfly over the warp (lane L ends with the
-  // warp's sum of value L), integer counts by warp reduction, then FP64 over warps
+  // warp's sum of value L), integer counts by warp reduction, then over the warps in order
+  // (FP32, then one conversion to the FP64 tile partial)
   float v[32];
 #pragma unroll
   for (int k = 0; k < 28; ++k) v[k] = acc[k];
@@ -1001,14 +1082,20 @@ __device__ __forceinline__ void raster_block(const WaveArgs &a, int tile, int q,
   if (lane < 28) red[warp][lane] = v[0];
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
-    const unsigned c = __reduce_add_sync(0xffffffffu, (unsigned)cnt6[k]);
+    const unsigned c = __reduce_add_sync(0xffffffffu, (cnt6 >> (5 * k)) & 31u);
     if (lane == 0) redc[warp][k] = (int)c;
   }
   __syncthreads();
-  if (tid < kNumVals) {
-    double s = 0.0;
-    for (int w = 0; w < kThreads / 32; ++w) s += tid < 6 ? (double)redc[w][tid] : (double)red[w][tid - 6];
-    a.partial[bin * kNumVals + tid] = s;
+  if (tid < 6) {
+    int c = 0;
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) c += redc[w][tid];
+    a.partial[bin * kNumVals + tid] = (double)c;
+  } else if (tid < kNumVals) {
+    float f = 0.0f;
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) f = __fadd_rn(f, red[w][tid - 6]);
+    a.partial[bin * kNumVals + tid] = (double)f;
   }
 }
 
@@ -1084,7 +1171,8 @@ cudaError_t launch_wave(const WaveArgs &a, int mode, cudaStream_t s, cudaEvent_t
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (ev && (e = cudaEventRecord(ev[2], s)) != cudaSuccess) return e;
-  if (a.tg.tw == 32 && a.tg.th == 32) e = launch_raster<32, 32>(a, mode, s);
+  if (a.tg.tw == 64 && a.tg.th == 32) e = launch_raster<64, 32>(a, mode, s);
+  else if (a.tg.tw == 32 && a.tg.th == 32) e = launch_raster<32, 32>(a, mode, s);
   else if (a.tg.tw == 32 && a.tg.th == 16) e = launch_raster<32, 16>(a, mode, s);
   else e = launch_raster<16, 16>(a, mode, s);
   if (e != cudaSuccess) return e;

@@ -70,7 +70,7 @@ def c1():
 # visibility
 # ---------------------------------------------------------------------------------------
 
-@pytest.mark.parametrize("tile", [(32, 32), (32, 16), (16, 16)])
+@pytest.mark.parametrize("tile", [(64, 32), (32, 32), (32, 16), (16, 16)])
 def test_render_bit_exact_config1(c1, tile):
     c1["gm"].set_tuning(tile=tile)
     r = cases.rng(5)
