@@ -387,9 +387,8 @@ def main():
     plain_value = n * plain_steps / (ms_plain * 1e-3)
 
     # the persistent batch kernel (one launch, replayed as a CUDA graph) on the same batch
-    probs = [(scan, poses[i]) for i in range(n)]
-    rm.cost_grad_batch(gm, probs)
-    ms_pers, _ = timed(lambda: rm.cost_grad_batch(gm, probs), a.steps)
+    rm.cost_grad_batch(gm, scans=scan, poses=poses)
+    ms_pers, _ = timed(lambda: rm.cost_grad_batch(gm, scans=scan, poses=poses), a.steps)
     pers_value = n * a.steps / (ms_pers * 1e-3)
 
     # end to end through the C ABI with pinned host buffers

@@ -111,7 +111,9 @@ typedef struct {
 
 /* Execution knobs; a zeroed struct (or NULL) means "library defaults / autotuned". */
 typedef struct {
-  int32_t tile_w, tile_h;   /* screen tile, pixels: 16x16, 32x16, 32x32 or 64x32 */
+  int32_t tile_w, tile_h;   /* screen tile, pixels: 16x16, 32x16, 32x32 or 64x32; 0 = per
+                               camera model as in the batched entry points (64x32 pinhole,
+                               32x32 ray table) */
   int32_t bin_capacity;     /* triangle records per tile bin (grown on overflow) */
   int32_t wave_poses;       /* poses processed together per kernel wave */
   int32_t async_status;     /* 1: do not read the device status back (graph capture);
@@ -218,7 +220,9 @@ typedef struct {
  * persistent kernel: CTAs take (problem, phase, index) items from a device queue in order and
  * wait, with bounded spins, only on items earlier in the queue (cluster culling -> triangle
  * setup -> tile raster -> reduction per problem). Outputs as for rm_cost_grad, per problem
- * (index k = problem). Screen tiles are 32x32. (Sec. III.C / Sec. V: many evaluations per
+ * (index k = problem). Screen tiles are 64x32 for pinhole problems and 32x32 for ray-table
+ * problems, the per-call entry points' defaults, so a problem's results equal those of
+ * rm_cost_grad with default tiles bit for bit. (Sec. III.C / Sec. V: many evaluations per
  * scan match; batching them is this library's extension.) */
 rm_status rm_cost_grad_batch(rm_map *map, const rm_problem *problems, int32_t n,
                              const rm_cost_params *params, const rm_cost_out *out, void *stream);

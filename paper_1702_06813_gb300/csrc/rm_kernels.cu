@@ -1465,11 +1465,11 @@ __device__ __noinline__ void persist_setup(const WaveArgs &a, int worker, int nw
 }
 
 template <int MODEL>
-__device__ __noinline__ void persist_raster(const WaveArgs &a, int item,
-                                            RasterSmem<1024, MODEL> &sm) {
-  const int t1 = min((item + 1) * kPersistTiles, a.tg.ntiles);
-  for (int t = item * kPersistTiles; t < t1; ++t) {
-    raster_block<32, 32, kCostGrad, MODEL>(a, t, 0, sm);
+__device__ __noinline__ void persist_raster(
+    const WaveArgs &a, int item, RasterSmem<kPersistTileW[MODEL] * kPersistTileH[MODEL], MODEL> &sm) {
+  const int t1 = min((item + 1) * kPersistTiles[MODEL], a.tg.ntiles);
+  for (int t = item * kPersistTiles[MODEL]; t < t1; ++t) {
+    raster_block<kPersistTileW[MODEL], kPersistTileH[MODEL], kCostGrad, MODEL>(a, t, 0, sm);
     __syncthreads();
   }
 }
@@ -1491,11 +1491,14 @@ __device__ __noinline__ void lm_load_cg(const LMState *src, LMState &dst) {
 // problem's evaluation waits for all of its cull items, the raster for all setup items, the
 // reduction (and LM step) for all tiles, and the next evaluation's cull for that LM step.
 // Dependencies always point to earlier queue positions, which running CTAs have already
-// taken, so the waits end without any co-residency assumption.
+// taken, so the waits end without any co-residency assumption. Thread 0 takes the following
+// item while the current one runs (the atomic's latency overlaps the work). A CTA still runs
+// its items in queue order, so the earliest unfinished item is always being run and every
+// wait still ends.
 __global__ void __launch_bounds__(kThreads, RM_PERSIST_MIN_BLOCKS) k_persist(BatchArgs b) {
   union PersistSmem {
-    RasterSmem<1024, 0> r0;
-    RasterSmem<1024, 1> r1;
+    RasterSmem<kPersistTileW[0] * kPersistTileH[0], 0> r0;
+    RasterSmem<kPersistTileW[1] * kPersistTileH[1], 1> r1;
     SetupSmem su;
     double vals[kNumVals];
   };
@@ -1504,9 +1507,12 @@ __global__ void __launch_bounds__(kThreads, RM_PERSIST_MIN_BLOCKS) k_persist(Bat
   __shared__ WaveArgs s_args;  // the current item's problem, copied once per item
   __shared__ int4 s_item;
   __shared__ int s_abort;
+  int pre = -1;    // thread 0: the queue position taken ahead
+  int loaded = -1;  // the problem whose arguments s_args holds
   for (;;) {
     if (threadIdx.x == 0) {
-      const int k = atomicAdd(b.next, 1);
+      const int k = pre >= 0 ? pre : atomicAdd(b.next, 1);
+      pre = k < b.n_items ? atomicAdd(b.next, 1) : -1;
       int4 item = k < b.n_items ? b.items[k] : make_int4(-1, 0, 0, 0);
       int abort = 0;
       if (item.x >= 0) {
@@ -1537,12 +1543,13 @@ __global__ void __launch_bounds__(kThreads, RM_PERSIST_MIN_BLOCKS) k_persist(Bat
     __syncthreads();
     const int4 item = s_item;
     if (item.x < 0 || s_abort) break;
-    {
+    if (item.x != loaded) {  // consecutive items of one problem keep its arguments
       const int *src = reinterpret_cast<const int *>(b.probs + item.x);
       int *dst = reinterpret_cast<int *>(&s_args);
       for (int k = threadIdx.x; k < (int)(sizeof(WaveArgs) / 4); k += blockDim.x) dst[k] = src[k];
+      loaded = item.x;
+      __syncthreads();
     }
-    __syncthreads();
     const WaveArgs &a = s_args;
     const bool skip = skipped(a);
     if (!skip) {

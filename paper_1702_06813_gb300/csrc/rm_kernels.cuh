@@ -88,7 +88,11 @@ struct LMArgs {
 
 // Batch of problems (each its own camera, scan and scratch) run by one persistent kernel.
 constexpr int kPersistCull = 4;   // 256-cluster chunks per cull item
-constexpr int kPersistTiles = 2;  // 32x32 tiles per raster item
+// Persistent kernel screen tiles: pinhole problems use 64x32 tiles, one per raster item;
+// ray-table problems use 32x32 tiles, two per raster item.
+constexpr int kPersistTileW[2] = {64, 32};
+constexpr int kPersistTileH[2] = {32, 32};
+constexpr int kPersistTiles[2] = {1, 2};
 struct BatchArgs {
   const WaveArgs *probs;   // one per problem (n_poses 1, wave_base 0)
   const int4 *items;       // queue: problem, phase (0 cull, 1 setup, 2 raster, 3 reduce+LM),

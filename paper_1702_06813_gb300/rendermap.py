@@ -257,23 +257,50 @@ class RenderMapCost(torch.autograd.Function):
         return (grad_out.to(gx.device) * gx).to(ctx.xi_device), None, None, None, None
 
 
-def _problems(problems):
-    """ctypes array of rm_problem from [(Scan, pose), ...]; keeps the pose tensors alive."""
-    arr = (N.rm_problem * len(problems))()
-    keep = []
-    for k, (scan, pose) in enumerate(problems):
-        p = _dev_tensor(pose, torch.float64).reshape(16)
-        keep.append(p)
-        arr[k].scan = scan.c()
-        arr[k].pose = p.data_ptr()
-    return arr, keep
+def _problems(problems=None, scans=None, poses=None):
+    """ctypes array of rm_problem from [(Scan, pose), ...], or from `scans` (one Scan, or one
+    per problem) and `poses` (n x 4 x 4 or n x 16). The poses are laid out back to back in one
+    device array (one copy in the library); the array is built from per-scan byte templates
+    rather than field by field. Returns the array and the tensors it points into."""
+    if problems is not None:
+        scans = [sc for sc, _ in problems]
+        poses = [ps for _, ps in problems]
+    if isinstance(poses, torch.Tensor):
+        P = poses.to(device="cuda", dtype=torch.float64).reshape(-1, 16).contiguous()
+    elif all(isinstance(ps, torch.Tensor) for ps in poses):
+        P = torch.stack([ps.reshape(16) for ps in poses]).to(device="cuda", dtype=torch.float64).contiguous()
+    else:
+        P = torch.as_tensor(np.stack([np.asarray(ps, dtype=np.float64).reshape(16) for ps in poses]),
+                            device="cuda")
+    n = P.shape[0]
+    if isinstance(scans, Scan):
+        scans = [scans] * n
+    if len(scans) != n:
+        raise ValueError("one scan per pose")
+    rows, index = [], {}
+    idx = np.empty(n, dtype=np.int64)
+    for k, sc in enumerate(scans):
+        j = index.get(id(sc))
+        if j is None:
+            j = index[id(sc)] = len(rows)
+            t = N.rm_problem()
+            t.scan = sc.c()
+            rows.append(np.frombuffer(bytes(t), dtype=np.uint8))
+        idx[k] = j
+    size, off = ctypes.sizeof(N.rm_problem), N.rm_problem.pose.offset
+    buf = np.stack(rows)[idx]
+    ptrs = P.data_ptr() + 128 * np.arange(n, dtype=np.uint64)
+    buf[:, off:off + 8] = ptrs.astype("<u8").view(np.uint8).reshape(n, 8)
+    arr = (N.rm_problem * n).from_buffer_copy(np.ascontiguousarray(buf).reshape(n * size))
+    return arr, [P, scans]
 
 
-def cost_grad_batch(m: Map, problems, params=None):
-    """cost_grad for [(Scan, pose), ...] that may differ in camera and size: one persistent
-    kernel launch. Returns the same dict as cost_grad, indexed by problem."""
-    n = len(problems)
-    arr, keep = _problems(problems)
+def cost_grad_batch(m: Map, problems=None, params=None, *, scans=None, poses=None):
+    """cost_grad for [(Scan, pose), ...] that may differ in camera and size (or for `scans` and
+    `poses` as in _problems): one persistent kernel launch. Returns the same dict as
+    cost_grad, indexed by problem."""
+    arr, keep = _problems(problems, scans, poses)
+    n = len(arr)
     counts = torch.empty((n, 6), dtype=torch.int64, device="cuda")
     etab = torch.empty(n, dtype=torch.int64, device="cuda")
     els = torch.empty(n, dtype=torch.float64, device="cuda")
@@ -286,12 +313,13 @@ def cost_grad_batch(m: Map, problems, params=None):
     return {"counts": counts, "e_table": etab, "e_ls": els, "grad": g, "jtj": h}
 
 
-def align_batch(m: Map, problems, params=None, max_iters=5, lambda0=1e-3, lambda_up=10.0,
-                lambda_down=10.0, step_tol=1e-8):
-    """LM for [(Scan, start pose), ...] with every iteration of every problem in one persistent
-    kernel launch. Returns (poses (n,4,4) numpy, list of reports, status name)."""
-    n = len(problems)
-    arr, keep = _problems(problems)
+def align_batch(m: Map, problems=None, params=None, max_iters=5, lambda0=1e-3, lambda_up=10.0,
+                lambda_down=10.0, step_tol=1e-8, *, scans=None, poses=None):
+    """LM for [(Scan, start pose), ...] (or `scans` and `poses` as in _problems) with every
+    iteration of every problem in one persistent kernel launch. Returns (poses (n,4,4) numpy,
+    list of reports, status name)."""
+    arr, keep = _problems(problems, scans, poses)
+    n = len(arr)
     out = np.empty((n, 16))
     reps = (N.rm_align_report * n)()
     lm = N.rm_align_params(max_iters, 0, lambda0, lambda_up, lambda_down, step_tol)

@@ -61,7 +61,7 @@ def mixed():
 
 def test_batch_cost_grad_equals_single_calls(mixed):
     gm = mixed["gm"]
-    gm.set_tuning(tile=(32, 32))
+    gm.set_tuning()  # default tiles: the batched kernel's per camera model
     b = rm.cost_grad_batch(gm, [(pr["gscan"], pr["start"]) for pr in mixed["probs"]])
     for k, pr in enumerate(mixed["probs"]):
         s = rm.cost_grad(gm, pr["gscan"], pr["start"][None])
@@ -79,7 +79,7 @@ def test_batch_cost_grad_equals_single_calls(mixed):
 
 def test_batch_align_equals_single_calls(mixed):
     gm = mixed["gm"]
-    gm.set_tuning(tile=(32, 32))
+    gm.set_tuning()
     probs = mixed["probs"]
     poses, reps, status = rm.align_batch(gm, [(pr["gscan"], pr["start"]) for pr in probs], max_iters=5)
     for k, pr in enumerate(probs):
@@ -98,6 +98,36 @@ def test_batch_many_problems_room():
     r = cases.rng(44)
     poses = [synth.perturb_fixed(c["gt"], r, 0.1, 3.0) for _ in range(40)]
     b = rm.cost_grad_batch(gm, [(scan, P) for P in poses])
-    s = rm.cost_grad(gm, scan, np.stack(poses))
+    s = rm.cost_grad(gm, scan, np.stack(poses))  # default tiles, as the batch
     for key in ("counts", "e_table", "e_ls", "grad", "jtj"):
         assert torch.equal(b[key], s[key]), key
+
+
+def test_batch_repeated_calls_and_bin_growth():
+    """Calls of one batch shape reuse the device queue: back-to-back calls with new poses, a
+    per-pose call in between (which reuses the arena), and a call whose bins overflow and
+    grow (which reallocates it) must all still equal the per-pose results."""
+    c = cases.config1(seed=1000)
+    gm = rm.Map(c["mesh"].vertices, c["mesh"].faces, c["mesh"].labels)
+    scan = rm.Scan.make(rm.Intrinsics.from_camera(c["cam"]), *c["scan"])
+    r = cases.rng(45)
+    A = np.stack([synth.perturb_fixed(c["gt"], r, 0.1, 3.0) for _ in range(24)])
+    B = np.stack([synth.perturb_fixed(c["gt"], r, 0.1, 3.0) for _ in range(24)])
+    keys = ("counts", "e_table", "e_ls", "grad", "jtj")
+    bA = rm.cost_grad_batch(gm, scans=scan, poses=torch.as_tensor(A))
+    bB = rm.cost_grad_batch(gm, scans=scan, poses=torch.as_tensor(B))  # same shape, new poses
+    bB2 = rm.cost_grad_batch(gm, [(scan, P) for P in B])               # list form, same shape
+    sA = rm.cost_grad(gm, scan, A)
+    sB = rm.cost_grad(gm, scan, B)
+    bA2 = rm.cost_grad_batch(gm, scans=scan, poses=torch.as_tensor(A))  # after a per-pose call
+    for key in keys:
+        assert torch.equal(bA[key], sA[key]), key
+        assert torch.equal(bB[key], sB[key]), key
+        assert torch.equal(bB2[key], sB[key]), key
+        assert torch.equal(bA2[key], sA[key]), key
+    gm.set_tuning(bin_capacity=4)  # every bin overflows: grown over several attempts
+    bA3 = rm.cost_grad_batch(gm, scans=scan, poses=torch.as_tensor(A))
+    assert gm.get_tuning()["bin_capacity"] > 4
+    for key in keys:
+        assert torch.equal(bA3[key], sA[key]), key
+    gm.close()
