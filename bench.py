@@ -40,6 +40,7 @@ def args_():
     ap.add_argument("--seed", type=int, default=3000)
     ap.add_argument("--cpu-sample", type=int, default=64, help="poses per step of the reference arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tile", default=None, help="WxH screen tile (e.g. 64x32): skip the autotuner")
     ap.add_argument("--workload", choices=["headline", "tracking"], default="headline")
     ap.add_argument("--frames", type=int, default=200, help="tracking: frames of the trajectory")
     ap.add_argument("--agents", type=int, default=64, help="tracking: agents (scans per frame)")
@@ -330,7 +331,12 @@ def main():
         return rm.cost_grad(gm, scan, poses)
 
     from paper_1702_06813_gb300 import autotune
-    tuned = autotune.autotune(gm, scan, poses, cache=None, reps=3)  # untimed: part of warm-up
+    if a.tile:
+        tw, th = (int(x) for x in a.tile.split("x"))
+        gm.set_tuning(tile=(tw, th), wave_poses=min(n, 128))
+        tuned = {"ms": None}
+    else:
+        tuned = autotune.autotune(gm, scan, poses, cache=None, reps=3)  # untimed: part of warm-up
     for _ in range(max(3, a.warmup)):
         out = step()
     torch.cuda.synchronize()
