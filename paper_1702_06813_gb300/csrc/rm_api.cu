@@ -82,7 +82,7 @@ struct rm_map {
   int n_clusters = 0;
   int4 *d_cl_info = nullptr;
   float4 *d_cl_sphere = nullptr;
-  int *d_cl_verts = nullptr;
+  float4 *d_cl_pos = nullptr;
   uchar4 *d_cl_tris = nullptr;
   int *d_cl_ids = nullptr;
   char *arena = nullptr;
@@ -128,7 +128,7 @@ uint64_t spread21(uint64_t x) {
 struct Clusters {
   std::vector<int4> info;
   std::vector<float4> sphere;
-  std::vector<int> verts;
+  std::vector<float4> pos;  // vertex position with its global index's bits in w
   std::vector<uchar4> tris;
   std::vector<int> ids;
 };
@@ -187,7 +187,11 @@ void build_clusters(const std::vector<float4> &hv, const int32_t *faces, int64_t
     while ((double)r32 < r) r32 = std::nextafter(r32, INFINITY);
     cl.info.push_back(make_int4(voff, toff, nv, nt));
     cl.sphere.push_back(make_float4(c32[0], c32[1], c32[2], r32));
-    for (int k = 0; k < nv; ++k) cl.verts.push_back(loc[k]);
+    for (int k = 0; k < nv; ++k) {
+      float4 p = hv[loc[k]];
+      std::memcpy(&p.w, &loc[k], sizeof(float));
+      cl.pos.push_back(p);
+    }
     voff += nv;
     toff += nt;
     nv = nt = 0;
@@ -313,7 +317,7 @@ void set_clusters(const rm_map *m, WaveArgs &a) {
   a.n_clusters = m->n_clusters;
   a.cl_info = m->d_cl_info;
   a.cl_sphere = m->d_cl_sphere;
-  a.cl_verts = m->d_cl_verts;
+  a.cl_pos = m->d_cl_pos;
   a.cl_tris = m->d_cl_tris;
   a.cl_ids = m->d_cl_ids;
 }
@@ -439,7 +443,7 @@ rm_status run_eval(rm_map *m, const EvalReq &r, cudaStream_t s) {
       if (r.tri_id && !dev_id) plan.take<int>(P * r.n);
       if (r.bary && !dev_bary) plan.take<float>(2 * P * r.n);
     }
-    plan.take<int>((size_t)m->n_clusters * nw);
+    plan.take<int4>((size_t)m->n_clusters * nw);
     plan.take<int>(nw);
     plan.take<int>((size_t)tg.ntiles * nw);
     plan.take<unsigned char>((size_t)tg.ntiles * tg.cap * nw * tg.rec_bytes);
@@ -471,7 +475,7 @@ rm_status run_eval(rm_map *m, const EvalReq &r, cudaStream_t s) {
       if (r.tri_id) d_id = dev_id ? r.tri_id : cv.take<int>(P * r.n);
       if (r.bary) d_bary = dev_bary ? r.bary : cv.take<float>(2 * P * r.n);
     }
-    int *d_vis = cv.take<int>((size_t)m->n_clusters * nw);
+    int4 *d_vis = cv.take<int4>((size_t)m->n_clusters * nw);
     int *d_vcount = cv.take<int>(nw);
     int *d_bcount = cv.take<int>((size_t)tg.ntiles * nw);
     unsigned char *d_bins = cv.take<unsigned char>((size_t)tg.ntiles * tg.cap * nw * tg.rec_bytes);
@@ -655,7 +659,7 @@ rm_status run_batch(rm_map *m, const rm_problem *probs, int n, const rm_cost_par
     // ---- plan and carve the arena
     auto layout = [&](Carver &cv, bool carve, WaveArgs **d_args, int4 **d_items, int **d_next,
                       int **d_done, int **d_need, float **d_M, int **d_skip, double **d_poses,
-                      rmk::LMState **d_lm, int **d_vcount, int **d_vis, int **d_counts,
+                      rmk::LMState **d_lm, int **d_vcount, int4 **d_vis, int **d_counts,
                       double **d_partial, unsigned char **d_bins, float **d_sd, uint8_t **d_sc,
                       float **d_rays, long long **r_counts, long long **r_et, double **r_els,
                       double **r_grad, double **r_jtj) {
@@ -670,7 +674,7 @@ rm_status run_batch(rm_map *m, const rm_problem *probs, int n, const rm_cost_par
       *d_poses = cv.take<double>(16 * (size_t)n);
       *d_lm = cv.take<rmk::LMState>(n);
       *d_vcount = cv.take<int>(n);
-      *d_vis = cv.take<int>((size_t)n * std::max(nc, 1));
+      *d_vis = cv.take<int4>((size_t)n * std::max(nc, 1));
       *d_counts = cv.take<int>(tiles_total);
       *d_partial = cv.take<double>(tiles_total * rmk::kNumVals);
       *d_bins = cv.take<unsigned char>(bins_bytes);
@@ -683,7 +687,7 @@ rm_status run_batch(rm_map *m, const rm_problem *probs, int n, const rm_cost_par
       *r_grad = cv.take<double>(6 * (size_t)n);
       *r_jtj = cv.take<double>(21 * (size_t)n);
     };
-    WaveArgs *d_args; int4 *d_items; int *d_next, *d_done, *d_need, *d_skip, *d_vcount, *d_vis, *d_counts;
+    WaveArgs *d_args; int4 *d_items, *d_vis; int *d_next, *d_done, *d_need, *d_skip, *d_vcount, *d_counts;
     float *d_M, *d_sd, *d_rays; double *d_poses, *d_partial, *r_els, *r_grad, *r_jtj; rmk::LMState *d_lm;
     unsigned char *d_bins; uint8_t *d_sc; long long *r_counts, *r_et;
     Carver plan{nullptr};
@@ -1003,7 +1007,7 @@ rm_status rm_map_create(const float *vertices, int64_t n_vertices, const int32_t
       (e = cudaMemset(m->d_status, 0, sizeof(unsigned))) != cudaSuccess ||
       (e = up((void **)&m->d_cl_info, cl.info.data(), sizeof(int4) * cl.info.size())) != cudaSuccess ||
       (e = up((void **)&m->d_cl_sphere, cl.sphere.data(), sizeof(float4) * cl.sphere.size())) != cudaSuccess ||
-      (e = up((void **)&m->d_cl_verts, cl.verts.data(), sizeof(int) * cl.verts.size())) != cudaSuccess ||
+      (e = up((void **)&m->d_cl_pos, cl.pos.data(), sizeof(float4) * cl.pos.size())) != cudaSuccess ||
       (e = up((void **)&m->d_cl_tris, cl.tris.data(), sizeof(uchar4) * cl.tris.size())) != cudaSuccess ||
       (e = up((void **)&m->d_cl_ids, cl.ids.data(), sizeof(int) * cl.ids.size())) != cudaSuccess)
     return cleanup(fail(e == cudaErrorMemoryAllocation ? RM_ENOMEM : RM_ECUDA,
@@ -1021,7 +1025,7 @@ void rm_map_destroy(rm_map *m) {
   cudaFree(m->d_planes);
   cudaFree(m->d_cl_info);
   cudaFree(m->d_cl_sphere);
-  cudaFree(m->d_cl_verts);
+  cudaFree(m->d_cl_pos);
   cudaFree(m->d_cl_tris);
   cudaFree(m->d_cl_ids);
   cudaFree(m->arena);
@@ -1213,7 +1217,7 @@ rm_status rm_align(rm_map *m, const rm_scan *scan, const double *init_pose,
     plan.take<double>(1);
     plan.take<double>(6);
     plan.take<double>(21);
-    plan.take<int>(m->n_clusters);
+    plan.take<int4>(m->n_clusters);
     plan.take<int>(1);
     plan.take<int>(tg.ntiles);
     plan.take<unsigned char>((size_t)tg.ntiles * tg.cap * tg.rec_bytes);
@@ -1245,7 +1249,7 @@ rm_status rm_align(rm_map *m, const rm_scan *scan, const double *init_pose,
     a.planes = m->d_planes;
     a.Ms = d_M;
     set_clusters(m, a);
-    a.vis = cv.take<int>(m->n_clusters);
+    a.vis = cv.take<int4>(m->n_clusters);
     a.vis_count = cv.take<int>(1);
     a.counts = cv.take<int>(tg.ntiles);
     a.bins = cv.take<unsigned char>((size_t)tg.ntiles * tg.cap * tg.rec_bytes);

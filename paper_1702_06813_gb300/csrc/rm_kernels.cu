@@ -160,7 +160,7 @@ __device__ __forceinline__ void cull_block(const WaveArgs &a, int q, int chunk, 
   float M[12];
 #pragma unroll
   for (int k = 0; k < 12; ++k) M[k] = sM[k];
-  int *vis = a.vis + (long long)q * a.n_clusters;
+  int4 *vis = a.vis + (long long)q * a.n_clusters;
   const int c = chunk * blockDim.x + threadIdx.x;
   const bool keep = c < a.n_clusters && cluster_visible(a.cam, M, a.cl_sphere[c]);
   // warp-aggregated append
@@ -170,7 +170,7 @@ __device__ __forceinline__ void cull_block(const WaveArgs &a, int q, int chunk, 
   int base = 0;
   if (lane == leader) base = atomicAdd(&a.vis_count[q], __popc(m));
   base = __shfl_sync(0xffffffffu, base, leader);
-  if (keep) vis[base + __popc(m & ((1u << lane) - 1u))] = c;
+  if (keep) vis[base + __popc(m & ((1u << lane) - 1u))] = a.cl_info[c];  // setup needs no lookup
 }
 
 __global__ void __launch_bounds__(256) k_cull(WaveArgs a) {
@@ -417,17 +417,17 @@ __device__ __forceinline__ void setup_block(const WaveArgs &a, int q, int worker
 #pragma unroll
   for (int k = 0; k < 12; ++k) M[k] = sm.M[k];
   const int nvis = sm.nvis;
-  const int *vis = a.vis + (long long)q * a.n_clusters;
+  const int4 *vis = a.vis + (long long)q * a.n_clusters;
   int *counts = a.counts + (long long)q * a.tg.ntiles;
   unsigned char *bins = a.bins + (long long)q * a.tg.ntiles * a.tg.cap * a.tg.rec_bytes;
   const int W = a.cam.W, H = a.cam.H;
   const float near_m = a.cam.near_m;
   const bool raytable = a.cam.model != 0;
   for (int ci = worker * 8 + warp; ci < nvis; ci += nworkers * 8) {
-    const int4 info = a.cl_info[ld_cg(&vis[ci])];  // vert offset, tri offset, nv, nt
+    const int4 info = __ldcg(&vis[ci]);  // vert offset, tri offset, nv, nt
     for (int k = lane; k < info.z; k += 32) {
-      const int gv = a.cl_verts[info.x + k];
-      const float4 v = a.v[gv];
+      const float4 v = a.cl_pos[info.x + k];
+      const int gv = __float_as_int(v.w);
       const float3 c = xform(M, v.x, v.y, v.z);
       int2 sv = make_int2(kSentinel, 1);  // behind the near plane
       if (raytable) {
@@ -533,7 +533,9 @@ __device__ __forceinline__ void setup_block(const WaveArgs &a, int q, int worker
   }
 }
 
-__global__ void __launch_bounds__(256) k_setup(WaveArgs a) {
+// six resident CTAs per SM (40 registers): setup is bound by the latency of its dependent
+// loads, so more resident warps pay more than registers
+__global__ void __launch_bounds__(256, 6) k_setup(WaveArgs a) {
   __shared__ SetupSmem sm;
   if (skipped(a)) return;
   setup_block(a, blockIdx.y, blockIdx.x, gridDim.x, sm);

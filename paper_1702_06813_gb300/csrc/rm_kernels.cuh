@@ -30,10 +30,10 @@ struct WaveArgs {
   int n_clusters;
   const int4 *cl_info;     // vertex offset, triangle offset, vertex count, triangle count
   const float4 *cl_sphere; // bounding sphere (re-centred frame)
-  const int *cl_verts;     // global vertex index per cluster vertex
+  const float4 *cl_pos;    // per cluster vertex: position (re-centred), global index bits in w
   const uchar4 *cl_tris;   // local vertex indices per cluster triangle
   const int *cl_ids;       // original face id per cluster triangle
-  int *vis;           // wave: visible cluster ids per pose (n_clusters each)
+  int4 *vis;          // wave: the visible clusters' info records per pose (n_clusters each)
   int *vis_count;     // wave: one counter per pose
   int *counts;        // wave: ntiles per pose
   unsigned char *bins;  // wave: ntiles * cap records of tg.rec_bytes per pose

@@ -94,7 +94,7 @@ extern "C" rm_status rm_cost_grad_noalloc(const rm_map *map, const rm_scan *scan
   double *d_pose = reinterpret_cast<double *>(take(16 * sizeof(double)));
   float *d_M = reinterpret_cast<float *>(take(12 * sizeof(float)));
   int *d_vcount = reinterpret_cast<int *>(take(sizeof(int)));
-  int *d_vis = reinterpret_cast<int *>(take(sizeof(int) * (size_t)(a.n_clusters > 0 ? a.n_clusters : 1)));
+  int4 *d_vis = reinterpret_cast<int4 *>(take(sizeof(int4) * (size_t)(a.n_clusters > 0 ? a.n_clusters : 1)));
   int *d_bcount = reinterpret_cast<int *>(take(sizeof(int) * (size_t)a.tg.ntiles));
   double *d_partial = reinterpret_cast<double *>(take(sizeof(double) * rmk::kNumVals * (size_t)a.tg.ntiles));
   if (off >= kScratchBytes)
