@@ -181,44 +181,11 @@ __global__ void __launch_bounds__(256) k_cull(WaveArgs a) {
 
 // ------------------------------------------------------------------ triangle setup + binning
 
-__device__ __forceinline__ void emit_piece(int x0, int y0, int x1, int y1, int x2, int y2,
-                                           float Ai, float Bi, float Ci, unsigned id,
-                                           const WaveArgs &a, int *counts, unsigned char *bins_b) {
-  TriRec *bins = reinterpret_cast<TriRec *>(bins_b);
-  long long area = (long long)(x1 - x0) * (y2 - y0) - (long long)(y1 - y0) * (x2 - x0);
-  if (area == 0) return;
-  if (area < 0) {
-    int t = x1; x1 = x2; x2 = t;
-    t = y1; y1 = y2; y2 = t;
-  }
-  const int W = a.cam.W, H = a.cam.H;
-  int xmin = min(x0, min(x1, x2)), xmax = max(x0, max(x1, x2));
-  int ymin = min(y0, min(y1, y2)), ymax = max(y0, max(y1, y2));
-  int i0 = max((xmin + 127) >> 8, 0), i1 = min((xmax - 128) >> 8, W - 1);
-  int j0 = max((ymin + 127) >> 8, 0), j1 = min((ymax - 128) >> 8, H - 1);
-  if (i0 > i1 || j0 > j1) return;
-  const TileGeom &tg = a.tg;
-  int tx0 = i0 / tg.tw, tx1 = i1 / tg.tw, ty0 = j0 / tg.th, ty1 = j1 / tg.th;
-  int4 w0 = make_int4(x0, y0, x1, y1);
-  int4 w1 = make_int4(x2, y2, __float_as_int(Ai), __float_as_int(Bi));
-  int4 w2 = make_int4(__float_as_int(Ci), (int)id, 0, 0);
-  for (int ty = ty0; ty <= ty1; ++ty)
-    for (int tx = tx0; tx <= tx1; ++tx) {
-      int tile = ty * tg.ntx + tx;
-      int slot = atomicAdd(&counts[tile], 1);
-      if (slot < tg.cap) {
-        int4 *dst = reinterpret_cast<int4 *>(bins + (long long)tile * tg.cap + slot);
-        dst[0] = w0;
-        dst[1] = w1;
-        dst[2] = w2;
-      } else {
-        atomicOr(a.status, kStatusOverflow);
-      }
-    }
-}
-
-// Warp-collective form of emit_piece (all 32 lanes call it; `valid` marks the lanes that
-// hold a piece). The lanes append to the tiles their pieces overlap one tile per step; the
+// Appends a snapped triangle piece (vertices in 1/256 px, inverse-depth plane, parent id) to
+// the bins of every tile its sample bounding box overlaps, after normalising the winding so
+// the doubled area is positive; zero-area pieces and pieces that cover no sample are dropped.
+// Warp-collective: all 32 lanes call it, `valid` marks the lanes that hold a piece. The
+// lanes append to the tiles their pieces overlap one tile per step; the
 // lanes that target the same tile in a step take consecutive slots through one atomic add
 // by their lowest lane, so a cluster's triangles, which mostly share a tile or two, cost
 // a few atomics per step instead of one per triangle.
@@ -1042,7 +1009,7 @@ __device__ __forceinline__ void raster_block(const WaveArgs &a, int tile, int q,
       const float nx = R[0] * pl.x + R[1] * pl.y + R[2] * pl.z;
       const float ny = R[3] * pl.x + R[4] * pl.y + R[5] * pl.z;
       const float nz = R[6] * pl.x + R[7] * pl.y + R[8] * pl.z;
-      const float inv = __frcp_rn(nx * rx + ny * ry + nz * rz);
+      const float inv = __fdividef(1.0f, nx * rx + ny * ry + nz * rz);  // Jacobian only
       const float s = sgn * inv;
       float J[6];
       J[0] = -nx * s;
