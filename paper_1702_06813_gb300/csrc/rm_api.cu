@@ -351,10 +351,10 @@ rm_status drain_events(rm_map *m) {
 }
 
 // One wave, with events around its kernels when profiling.
-rm_status wave(rm_map *m, const WaveArgs &a, int mode, cudaStream_t s) {
+rm_status wave(rm_map *m, const WaveArgs &a, int mode, cudaStream_t s, bool zero_counters = true) {
   cudaEvent_t ev[5];
   if (m->prof) RM_TRY(take_events(m, ev));
-  RM_CK(rmk::launch_wave(a, mode, s, m->prof ? ev : nullptr));
+  RM_CK(rmk::launch_wave(a, mode, s, m->prof ? ev : nullptr, zero_counters));
   m->launches += rmk::wave_kernel_launches(a, mode);
   if (m->prof) m->ev_pending.push_back({ev[0], ev[1], ev[2], ev[3], ev[4]});
   return RM_OK;
@@ -422,13 +422,21 @@ rm_status run_eval(rm_map *m, const EvalReq &r, cudaStream_t s) {
   const bool dev_depth = r.mode == rmk::kRender && on_device(r.depth);
   const bool dev_id = r.tri_id && on_device(r.tri_id);
   const bool dev_bary = r.bary && on_device(r.bary);
+  // cost outputs in device memory are written by the kernels in place; host ones are staged
+  const bool cost_mode = r.mode != rmk::kRender && r.out;
+  const bool grad_mode = cost_mode && r.mode == rmk::kCostGrad;
+  const bool dev_counts = cost_mode && r.out->counts && on_device(r.out->counts);
+  const bool dev_etable = cost_mode && r.out->e_table && on_device(r.out->e_table);
+  const bool dev_els = cost_mode && r.out->e_ls && on_device(r.out->e_ls);
+  const bool dev_grad = grad_mode && r.out->grad && on_device(r.out->grad);
+  const bool dev_jtj = grad_mode && r.out->jtj && on_device(r.out->jtj);
 
   for (int attempt = 0;; ++attempt) {
     TileGeom tg = make_tiles(m, in);
     const int nw = wave_size(m, r.n, tg);
     // ---- plan the arena
     Carver plan{nullptr};
-    plan.take<double>(16 * (size_t)r.n);
+    if (host_poses) plan.take<double>(16 * (size_t)r.n);
     plan.take<float>(12 * (size_t)r.n);
     if (host_rays) plan.take<float>(3 * P);
     if (host_scan) plan.take<float>(P);
@@ -444,15 +452,14 @@ rm_status run_eval(rm_map *m, const EvalReq &r, cudaStream_t s) {
       if (r.bary && !dev_bary) plan.take<float>(2 * P * r.n);
     }
     plan.take<int4>((size_t)m->n_clusters * nw);
-    plan.take<int>(nw);
-    plan.take<int>((size_t)tg.ntiles * nw);
+    plan.take<int>((size_t)(tg.ntiles + 1) * r.n);
     plan.take<unsigned char>((size_t)tg.ntiles * tg.cap * nw * tg.rec_bytes);
     plan.take<double>((size_t)tg.ntiles * rmk::kNumVals * nw);
     RM_TRY(ensure_arena(m, plan.off, s));
     m->batch_inputs_valid = false;
     // ---- carve it
     Carver cv{m->arena};
-    double *d_poses = cv.take<double>(16 * (size_t)r.n);
+    const double *d_poses = host_poses ? cv.take<double>(16 * (size_t)r.n) : r.poses;
     float *d_M = cv.take<float>(12 * (size_t)r.n);
     const float *d_rays = in->rays;
     if (host_rays) d_rays = cv.take<float>(3 * P);
@@ -476,17 +483,19 @@ rm_status run_eval(rm_map *m, const EvalReq &r, cudaStream_t s) {
       if (r.bary) d_bary = dev_bary ? r.bary : cv.take<float>(2 * P * r.n);
     }
     int4 *d_vis = cv.take<int4>((size_t)m->n_clusters * nw);
-    int *d_vcount = cv.take<int>(nw);
-    int *d_bcount = cv.take<int>((size_t)tg.ntiles * nw);
+    // every pose's bin counts and visible-cluster count, zeroed together once per call
+    int *d_bcount = cv.take<int>((size_t)(tg.ntiles + 1) * r.n);
+    int *d_vcount = d_bcount + (size_t)tg.ntiles * r.n;
     unsigned char *d_bins = cv.take<unsigned char>((size_t)tg.ntiles * tg.cap * nw * tg.rec_bytes);
     double *d_partial = cv.take<double>((size_t)tg.ntiles * rmk::kNumVals * nw);
     // ---- inputs
-    RM_CK(cudaMemcpyAsync(d_poses, r.poses, sizeof(double) * 16 * r.n,
-                          host_poses ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+    if (host_poses)
+      RM_CK(cudaMemcpyAsync((void *)d_poses, r.poses, sizeof(double) * 16 * r.n, cudaMemcpyHostToDevice, s));
     if (host_rays) RM_CK(cudaMemcpyAsync((void *)d_rays, in->rays, sizeof(float) * 3 * P, cudaMemcpyHostToDevice, s));
     if (host_scan) RM_CK(cudaMemcpyAsync((void *)d_sd, r.scan->depth, sizeof(float) * P, cudaMemcpyHostToDevice, s));
     if (host_cls) RM_CK(cudaMemcpyAsync((void *)d_sc, r.scan->cls, P, cudaMemcpyHostToDevice, s));
     RM_CK(rmk::launch_pose_to_m(d_poses, r.n, m->centre[0], m->centre[1], m->centre[2], d_M, s));
+    RM_CK(cudaMemsetAsync(d_bcount, 0, sizeof(int) * (size_t)(tg.ntiles + 1) * r.n, s));
     m->launches += 1;
     // ---- waves
     WaveArgs a{};
@@ -509,18 +518,20 @@ rm_status run_eval(rm_map *m, const EvalReq &r, cudaStream_t s) {
     a.scan_depth = d_sd;
     a.scan_cls = d_sc;
     if (r.prm) a.prm = {r.prm->eps, r.prm->w_fofo, r.prm->w_fofu, r.prm->w_fufo};
-    a.res_counts = d_counts;
-    a.res_etable = d_etable;
-    a.res_els = d_els;
-    a.res_grad = d_grad;
-    a.res_jtj = d_jtj;
+    a.res_counts = dev_counts ? reinterpret_cast<long long *>(r.out->counts) : d_counts;
+    a.res_etable = dev_etable ? reinterpret_cast<long long *>(r.out->e_table) : d_etable;
+    a.res_els = dev_els ? r.out->e_ls : d_els;
+    a.res_grad = dev_grad ? r.out->grad : d_grad;
+    a.res_jtj = dev_jtj ? r.out->jtj : d_jtj;
     a.depth = d_depth;
     a.tri_id = d_id;
     a.bary = d_bary;
     for (int w0 = 0; w0 < r.n; w0 += nw) {
       a.wave_base = w0;
       a.n_poses = std::min(nw, r.n - w0);
-      RM_TRY(wave(m, a, r.mode, s));
+      a.counts = d_bcount + (size_t)w0 * tg.ntiles;
+      a.vis_count = d_vcount + w0;
+      RM_TRY(wave(m, a, r.mode, s, false));
     }
     // ---- outputs
     bool host_out = false;
@@ -529,12 +540,12 @@ rm_status run_eval(rm_map *m, const EvalReq &r, cudaStream_t s) {
       if (r.tri_id && !dev_id) RM_TRY(copy_out(r.tri_id, d_id, sizeof(int) * P * r.n, s, &host_out));
       if (r.bary && !dev_bary) RM_TRY(copy_out(r.bary, d_bary, sizeof(float) * 2 * P * r.n, s, &host_out));
     } else if (r.out) {
-      RM_TRY(copy_out(r.out->counts, d_counts, sizeof(long long) * 6 * r.n, s, &host_out));
-      RM_TRY(copy_out(r.out->e_table, d_etable, sizeof(long long) * r.n, s, &host_out));
-      RM_TRY(copy_out(r.out->e_ls, d_els, sizeof(double) * r.n, s, &host_out));
+      if (!dev_counts) RM_TRY(copy_out(r.out->counts, d_counts, sizeof(long long) * 6 * r.n, s, &host_out));
+      if (!dev_etable) RM_TRY(copy_out(r.out->e_table, d_etable, sizeof(long long) * r.n, s, &host_out));
+      if (!dev_els) RM_TRY(copy_out(r.out->e_ls, d_els, sizeof(double) * r.n, s, &host_out));
       if (r.mode == rmk::kCostGrad) {
-        RM_TRY(copy_out(r.out->grad, d_grad, sizeof(double) * 6 * r.n, s, &host_out));
-        RM_TRY(copy_out(r.out->jtj, d_jtj, sizeof(double) * 21 * r.n, s, &host_out));
+        if (!dev_grad) RM_TRY(copy_out(r.out->grad, d_grad, sizeof(double) * 6 * r.n, s, &host_out));
+        if (!dev_jtj) RM_TRY(copy_out(r.out->jtj, d_jtj, sizeof(double) * 21 * r.n, s, &host_out));
       }
     }
     if (m->tuning.async_status) {

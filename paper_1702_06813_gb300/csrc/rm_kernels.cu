@@ -1120,12 +1120,15 @@ static cudaError_t launch_raster(const WaveArgs &a, int mode, cudaStream_t s) {
   return a.cam.model == 0 ? launch_raster_m<TW, TH, 0>(a, mode, s) : launch_raster_m<TW, TH, 1>(a, mode, s);
 }
 
-cudaError_t launch_wave(const WaveArgs &a, int mode, cudaStream_t s, cudaEvent_t *ev) {
+cudaError_t launch_wave(const WaveArgs &a, int mode, cudaStream_t s, cudaEvent_t *ev,
+                        bool zero_counters) {
   cudaError_t e;
-  e = cudaMemsetAsync(a.counts, 0, sizeof(int) * (size_t)a.tg.ntiles * a.n_poses, s);
-  if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(a.vis_count, 0, sizeof(int) * (size_t)a.n_poses, s);
-  if (e != cudaSuccess) return e;
+  if (zero_counters) {
+    e = cudaMemsetAsync(a.counts, 0, sizeof(int) * (size_t)a.tg.ntiles * a.n_poses, s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(a.vis_count, 0, sizeof(int) * (size_t)a.n_poses, s);
+    if (e != cudaSuccess) return e;
+  }
   if (ev && (e = cudaEventRecord(ev[0], s)) != cudaSuccess) return e;
   if (a.n_clusters > 0) {
     dim3 gc((a.n_clusters + 255) / 256, a.n_poses);

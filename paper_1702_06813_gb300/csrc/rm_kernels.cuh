@@ -62,7 +62,10 @@ cudaError_t launch_pose_to_m(const double *poses, int n, double cx, double cy, d
                              float *Ms, cudaStream_t s);
 // ev (optional, 5 events): recorded before the cull kernel, then after the cull, setup,
 // raster and reduce kernels, on stream s.
-cudaError_t launch_wave(const WaveArgs &a, int mode, cudaStream_t s, cudaEvent_t *ev = nullptr);
+// zero_counters: clear the wave's bin counts and visible-cluster count first (callers that
+// clear them for several waves at once pass false)
+cudaError_t launch_wave(const WaveArgs &a, int mode, cudaStream_t s, cudaEvent_t *ev = nullptr,
+                        bool zero_counters = true);
 int wave_kernel_launches(const WaveArgs &a, int mode);
 cudaError_t launch_retract(const double *T, const double *xi, int n, double *out, double *jr,
                            cudaStream_t s);

@@ -81,11 +81,20 @@ class Scan:
         return Scan(intr, _dev_tensor(depth, torch.float32, device), _dev_tensor(cls, torch.uint8, device))
 
     def c(self) -> N.rm_scan:
-        return N.rm_scan(self.intr.c(), self.depth.data_ptr(), self.cls.data_ptr())
+        """The C view of this scan (rebuilt when the arrays or the intrinsics change)."""
+        key = (self.depth.data_ptr(), self.cls.data_ptr(), id(self.intr), self.intr.width, self.intr.height)
+        cached = self.__dict__.get("_c")
+        if cached is None or cached[0] != key:
+            cached = (key, N.rm_scan(self.intr.c(), self.depth.data_ptr(), self.cls.data_ptr()))
+            self.__dict__["_c"] = cached
+        return cached[1]
 
 
 def cost_params(eps=0.1, w_fofo=1.0, w_fofu=1.0, w_fufo=1.0) -> N.rm_cost_params:
     return N.rm_cost_params(eps, w_fofo, w_fofu, w_fufo)
+
+
+_DEFAULT_PARAMS = cost_params()
 
 
 class Map:
@@ -155,7 +164,11 @@ class Map:
 
 
 def _poses(poses, device="cuda"):
-    p = _dev_tensor(poses, torch.float64, device).reshape(-1, 16)
+    if (isinstance(poses, torch.Tensor) and poses.is_cuda and poses.dtype == torch.float64
+            and poses.is_contiguous()):
+        p = poses.view(-1, 16)
+    else:
+        p = _dev_tensor(poses, torch.float64, device).reshape(-1, 16)
     return p, p.shape[0]
 
 
@@ -182,7 +195,7 @@ def _cost(fn, m, scan, poses, params, grad):
     out = N.rm_cost_out(counts.data_ptr(), etab.data_ptr(), els.data_ptr(),
                         None if g is None else g.data_ptr(), None if h is None else h.data_ptr())
     cs = scan.c()
-    prm = params if params is not None else cost_params()
+    prm = params if params is not None else _DEFAULT_PARAMS
     check(fn(m.handle, ctypes.byref(cs), _ptr(p), n, ctypes.byref(prm), ctypes.byref(out), _stream()))
     res = {"counts": counts, "e_table": etab, "e_ls": els}
     if grad:
