@@ -807,7 +807,7 @@ __device__ __forceinline__ bool raster_tile_ray(unsigned long long *zk, RayRec *
 #endif
 
 #ifndef RM_RASTER_MIN_BLOCKS
-#define RM_RASTER_MIN_BLOCKS 6  // resident CTAs per SM the register budget is sized for
+#define RM_RASTER_MIN_BLOCKS 5  // resident CTAs per SM the register budget is sized for (48 registers)
 #endif
 
 template <int NP, int MODEL>
