@@ -108,7 +108,6 @@ struct rm_map {
   // uploaded into the arena; valid until another call carves the arena
   bool batch_inputs_valid = false;
   std::vector<int> batch_shape;
-  std::vector<int4> batch_items;
   std::vector<WaveArgs> batch_args;
 };
 
@@ -591,8 +590,10 @@ rm_status run_batch(rm_map *m, const rm_problem *probs, int n, const rm_cost_par
   RM_CK(cudaSetDevice(m->device));
   const int K = lm ? lm->max_iters : 0;
   const int nc = m->n_clusters;
-  const int ncull = ((nc + 255) / 256 + rmk::kPersistCull - 1) / rmk::kPersistCull;
-  const int nwork = std::min(64, std::max(1, nc / 512));
+  // at least one item per phase, so that every phase completes and publishes the next
+  const int ncull = std::max(1, ((nc + 255) / 256 + rmk::kPersistCull - 1) / rmk::kPersistCull);
+  // setup items per evaluation are set on the device from the visible clusters; at most
+  const int max_setup = std::max(1, (nc + rmk::kSetupClusters - 1) / rmk::kSetupClusters);
   for (int attempt = 0;; ++attempt) {
     std::vector<TileGeom> tg(n);
     std::vector<long long> P(n);
@@ -625,46 +626,22 @@ rm_status run_batch(rm_map *m, const rm_problem *probs, int n, const rm_cost_par
       if (scan_of[p] == p) px_total += align_up((size_t)P[p], 64);
       if (rays_of[p] == p) rays_total += 3 * (size_t)P[p];
     }
-    // queue: per evaluation, groups of problems; the cull and setup items of group g+1 go
-    // ahead of the raster and reduce items of group g, so by the time a CTA takes a tile its
-    // problem's bins are (almost always) complete and dependency waits stay short. The queue
-    // and the dependency counts are a function of `shape` alone: a call with the shape of the
-    // previous batch call reuses the host copy, and the device copy too while the arena still
-    // holds it.
-    std::vector<int> shape = {n, K, ncull, nwork};
-    for (int p = 0; p < n; ++p) shape.push_back(raster_items(tg[p], probs[p].scan.intr.model));
-    const bool same_shape = shape == m->batch_shape && !m->batch_items.empty();
-    std::vector<int4> built;
-    std::vector<int4> &items = same_shape ? m->batch_items : built;
-    const int G = 8;
-    auto front = [&](int g0, int it) {
-      const int g1 = std::min(n, g0 + G);
-      for (int p = g0; p < g1; ++p)
-        for (int k = 0; k < ncull; ++k) items.push_back(make_int4(p, 0, k, it));
-      for (int p = g0; p < g1; ++p)
-        for (int k = 0; k < nwork; ++k) items.push_back(make_int4(p, 1, k, it));
-    };
-    auto back = [&](int g0, int it) {
-      const int g1 = std::min(n, g0 + G);
-      for (int p = g0; p < g1; ++p)
-        for (int k = 0; k < raster_items(tg[p], probs[p].scan.intr.model); ++k)
-          items.push_back(make_int4(p, 2, k, it));
-      for (int p = g0; p < g1; ++p) items.push_back(make_int4(p, 3, 0, it));
-    };
-    if (!same_shape) {
-      for (int it = 0; it <= K; ++it) {
-        front(0, it);
-        for (int g0 = 0; g0 < n; g0 += G) {
-          if (g0 + G < n) front(g0 + G, it);
-          back(g0, it);
-        }
-      }
+    // the ready queue: one slot per item of every evaluation of every problem; the kernel
+    // publishes a problem's items phase by phase. The dependency counts are a function of
+    // `shape` alone and are re-sent only when it changes or the arena was reused.
+    std::vector<int> shape = {n, K, ncull};
+    size_t cap_hi = 0, cap_lo = 0;  // raster + reduce slots, cull + setup slots
+    for (int p = 0; p < n; ++p) {
+      const int nr = raster_items(tg[p], probs[p].scan.intr.model);
+      shape.push_back(nr);
+      cap_hi += (size_t)(K + 1) * (nr + 1);
+      cap_lo += (size_t)(K + 1) * (ncull + max_setup);
     }
-    const size_t n_items = items.size();
+    const bool same_shape = shape == m->batch_shape;
     std::vector<int> need(3 * (size_t)n);
     for (int p = 0; p < n; ++p) {
       need[3 * p] = ncull;
-      need[3 * p + 1] = nwork;
+      need[3 * p + 1] = 0;  // set by the kernel
       need[3 * p + 2] = raster_items(tg[p], probs[p].scan.intr.model);
     }
     // ---- plan and carve the arena
@@ -676,8 +653,8 @@ rm_status run_batch(rm_map *m, const rm_problem *probs, int n, const rm_cost_par
                       double **r_grad, double **r_jtj) {
       (void)carve;
       *d_args = cv.take<WaveArgs>(n);
-      *d_items = cv.take<int4>(n_items);
-      *d_next = cv.take<int>(1);
+      *d_items = cv.take<int4>(cap_hi + cap_lo);
+      *d_next = cv.take<int>(8);  // queue heads and tails, finished problems
       *d_done = cv.take<int>(4 * (size_t)n);
       *d_need = cv.take<int>(3 * (size_t)n);
       *d_M = cv.take<float>(12 * (size_t)n);
@@ -786,14 +763,9 @@ rm_status run_batch(rm_map *m, const rm_problem *probs, int n, const rm_cost_par
     const bool same_args = dev_shape && m->batch_args.size() == args.size() &&
                            std::memcmp(m->batch_args.data(), args.data(), sizeof(WaveArgs) * n) == 0;
     m->batch_inputs_valid = false;
-    if (!dev_shape) {
-      RM_CK(cudaMemcpyAsync(d_items, items.data(), sizeof(int4) * n_items, cudaMemcpyHostToDevice, s));
+    if (!dev_shape)
       RM_CK(cudaMemcpyAsync(d_need, need.data(), sizeof(int) * need.size(), cudaMemcpyHostToDevice, s));
-    }
-    if (!same_shape) {
-      m->batch_items.swap(built);
-      m->batch_shape = shape;
-    }
+    m->batch_shape = shape;
     if (!same_args) {
       RM_CK(cudaMemcpyAsync(d_args, args.data(), sizeof(WaveArgs) * n, cudaMemcpyHostToDevice, s));
       m->batch_args = args;
@@ -811,9 +783,12 @@ rm_status run_batch(rm_map *m, const rm_problem *probs, int n, const rm_cost_par
     }
     rmk::BatchArgs b{};
     b.probs = d_args;
+    if (cap_hi + cap_lo > (size_t)INT32_MAX) return fail(RM_EINVAL, "batch too large for the work queue");
+    b.n_problems = n;
     b.items = d_items;
-    b.n_items = (int)n_items;
-    b.next = d_next;
+    b.cap[0] = (int)cap_hi;
+    b.cap[1] = (int)cap_lo;
+    b.qctl = d_next;
     b.done = d_done;
     b.need = d_need;
     b.lm = lm ? d_lm : nullptr;
@@ -829,7 +804,7 @@ rm_status run_batch(rm_map *m, const rm_problem *probs, int n, const rm_cost_par
     // per batch shape (the arena layout is a function of the shape), replayed every call
     char sig[512];
     std::snprintf(sig, sizeof(sig), "%p|%d|%d|%zu|%d|%d|%a|%a|%a|%a|%zu|%zu|%zu|%d", (void *)m->arena, n,
-                  K, n_items, grid, lm ? 1 : 0, la.lambda0, la.lambda_up, la.lambda_down,
+                  K, cap_hi + cap_lo, grid, lm ? 1 : 0, la.lambda0, la.lambda_up, la.lambda_down,
                   la.step_tol, tiles_total, px_total, rays_total, m->cap * 4096 + m->cap_ray);
     std::string key(sig);
     for (int p = 0; p < n; ++p) key += "|" + std::to_string(probs[p].scan.intr.model) + "x" +
@@ -848,7 +823,8 @@ rm_status run_batch(rm_map *m, const rm_problem *probs, int n, const rm_cost_par
       auto rec = [&](cudaError_t x) {
         if (e == cudaSuccess) e = x;
       };
-      rec(cudaMemsetAsync(d_next, 0, sizeof(int), c));
+      rec(cudaMemsetAsync(d_next, 0, 8 * sizeof(int), c));
+      rec(rmk::launch_queue_init(d_items, (int)(cap_hi + cap_lo), (int)cap_hi, n, ncull, d_next, c));
       rec(cudaMemsetAsync(d_done, 0, sizeof(int) * 4 * n, c));
       rec(cudaMemsetAsync(d_skip, 0, sizeof(int) * n, c));
       rec(cudaMemsetAsync(d_vcount, 0, sizeof(int) * n, c));
@@ -883,6 +859,7 @@ rm_status run_batch(rm_map *m, const rm_problem *probs, int n, const rm_cost_par
     }
     unsigned st = 0;
     RM_TRY(read_status(m, s, &st));  // synchronises the stream
+    if (st & rmk::kStatusQueue) return fail(RM_ECUDA, "the persistent queue ran out of slots");
     if (st & rmk::kStatusTimeout) return fail(RM_ETIMEOUT, "a device-side wait ran out of time");
     if (st & (rmk::kStatusOverflow | rmk::kStatusOverflowRay)) {
       RM_TRY(grow_bins(m, st, attempt));

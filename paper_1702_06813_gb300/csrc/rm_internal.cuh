@@ -29,6 +29,7 @@ constexpr int kNumVals = 34;                      // counts 6 | e_ls | grad 6 | 
 constexpr unsigned kStatusOverflow = 1u;     // a pinhole bin overflowed
 constexpr unsigned kStatusTimeout = 2u;
 constexpr unsigned kStatusOverflowRay = 4u;  // a ray-table bin overflowed
+constexpr unsigned kStatusQueue = 8u;        // the persistent queue ran out of slots (a bug)
 constexpr float kRayMarginPx = 0.25f;        // ray-table rectangles: margin in pixels
 constexpr int kThreads = 256;                     // raster CTA
 

@@ -239,19 +239,36 @@ __device__ __forceinline__ void emit_piece_warp(bool valid, int x0, int y0, int 
   }
 }
 
-// Appends a ray-table record to the bins of every tile its pixel rectangle overlaps.
-__device__ __forceinline__ void emit_ray(const RayRec &rr, int i0, int i1, int j0, int j1,
-                                         const WaveArgs &a, int *counts, unsigned char *bins_b) {
+// Warp-collective append of a ray-table record to the bins of every tile its pixel rectangle
+// r = (i0, i1, j0, j1) overlaps; `valid` marks the lanes that hold one. As for pinhole pieces,
+// lanes that target the same tile in a step take consecutive slots with one atomic add.
+__device__ __forceinline__ void emit_ray_warp(bool valid, const RayRec &rr, int4 r,
+                                              const WaveArgs &a, int *counts,
+                                              unsigned char *bins_b) {
   RayRec *bins = reinterpret_cast<RayRec *>(bins_b);
   const TileGeom &tg = a.tg;
+  const int lane = threadIdx.x & 31;
+  int tx0 = 0, nx = 0, ty0 = 0, nt = 0;
+  if (valid) {
+    tx0 = r.x / tg.tw;
+    ty0 = r.z / tg.th;
+    nx = r.y / tg.tw - tx0 + 1;
+    nt = nx * (r.w / tg.th - ty0 + 1);
+  }
   const int4 *src = reinterpret_cast<const int4 *>(&rr);
   int4 w3 = src[3];
-  w3.z = i0 | (i1 << 16);
-  w3.w = j0 | (j1 << 16);
-  for (int ty = j0 / tg.th; ty <= j1 / tg.th; ++ty)
-    for (int tx = i0 / tg.tw; tx <= i1 / tg.tw; ++tx) {
-      const int tile = ty * tg.ntx + tx;
-      const int slot = atomicAdd(&counts[tile], 1);
+  w3.z = r.x | (r.y << 16);
+  w3.w = r.z | (r.w << 16);
+  for (int k = 0; __any_sync(0xffffffffu, k < nt); ++k) {
+    const bool has = k < nt;
+    const int tile = has ? (ty0 + k / nx) * tg.ntx + tx0 + k % nx : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, tile);
+    const int leader = __ffs(peers) - 1;
+    int base = 0;
+    if (has && lane == leader) base = atomicAdd(&counts[tile], __popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (has) {
+      const int slot = base + __popc(peers & ((1u << lane) - 1u));
       if (slot < tg.cap) {
         int4 *dst = reinterpret_cast<int4 *>(bins + (long long)tile * tg.cap + slot);
         dst[0] = src[0];
@@ -262,6 +279,7 @@ __device__ __forceinline__ void emit_ray(const RayRec &rr, int i0, int i1, int j
         atomicOr(a.status, kStatusOverflowRay);
       }
     }
+  }
 }
 
 // Ray-table triangle: contract side normals and inverse-depth normal, then a conservative
@@ -269,15 +287,15 @@ __device__ __forceinline__ void emit_ray(const RayRec &rr, int i0, int i1, int j
 // when a pole is inside; elevation from the vertices widened by the great-circle bulge
 // bound z / cos(L/2), L the longest edge angle), a quarter-pixel margin (the FP32 angles
 // are good to ~1e-6 rad and the table's rays lie within that margin of the layout), split
-// at the seam. A triangle between pixel rays gets an empty rectangle and no record.
-__device__ __forceinline__ void setup_ray(const float3 v[3], const float4 u[3], const int gid[3],
-                                          unsigned id, const WaveArgs &a, int *counts,
-                                          unsigned char *bins) {
-  const DevCam &cam = a.cam;
+// at the seam into at most two rectangles (i0, i1, j0, j1), which are returned with their
+// count. A triangle between pixel rays gets no rectangle; most far triangles of a panorama
+// are such, so the record's plane is computed only once a rectangle exists.
+__device__ __forceinline__ int setup_ray(const float3 v[3], const float4 u[3], const int gid[3],
+                                         unsigned id, const DevCam &cam, RayRec &rr,
+                                         int4 rect[2]) {
   const float3 c12 = cross_c(v[1], v[2]);
   const float det = dot_c(v[0].x, v[0].y, v[0].z, c12.x, c12.y, c12.z);
-  if (det == 0.0f || det != det) return;
-  RayRec rr;
+  if (det == 0.0f || det != det) return 0;
   float3 side[3];
   float sg[3];
   int sig = 0;
@@ -289,16 +307,6 @@ __device__ __forceinline__ void setup_ray(const float3 v[3], const float4 u[3], 
     sg[k] = (det > 0.0f ? 1.0f : -1.0f) * (lo_is_k ? 1.0f : -1.0f);
     if (sg[k] > 0.0f) sig |= 1 << k;
   }
-  rr.c0x = side[0].x; rr.c0y = side[0].y; rr.c0z = side[0].z;
-  rr.c1x = side[1].x; rr.c1y = side[1].y; rr.c1z = side[1].z;
-  rr.c2x = side[2].x; rr.c2y = side[2].y; rr.c2z = side[2].z;
-  const PlaneN pl = plane_n(v[0], v[1], v[2]);
-  rr.nix = __fdiv_rn(pl.nx, pl.d);
-  rr.niy = __fdiv_rn(pl.ny, pl.d);
-  rr.niz = __fdiv_rn(pl.nz, pl.d);
-  rr.id = id;
-  rr.sig = sig;
-  rr.rect0 = rr.rect1 = 0;
   // ---- conservative pixel rectangle (any rounding; margins absorb it)
   bool has_up = true, has_dn = true;  // up = (0,-1,0), down = (0,1,0)
 #pragma unroll
@@ -325,36 +333,53 @@ __device__ __forceinline__ void setup_ray(const float3 v[3], const float4 u[3], 
   const float el_hi = asinf(zmax), el_lo = asinf(zmin);
   const int j0 = max(0, (int)ceilf((cam.el0 - el_hi) / cam.el_step - kRayMarginPx));
   const int j1 = min(cam.H - 1, (int)floorf((cam.el0 - el_lo) / cam.el_step + kRayMarginPx));
-  if (j0 > j1) return;
+  if (j0 > j1) return 0;
+  int nrect;
   if (has_up || has_dn) {
-    emit_ray(rr, 0, cam.W - 1, j0, j1, a, counts, bins);
-    return;
-  }
-  float s0 = u[0].w, s1 = u[1].w, s2 = u[2].w, t;
-  if (s0 > s1) { t = s0; s0 = s1; s1 = t; }
-  if (s1 > s2) { t = s1; s1 = s2; s2 = t; }
-  if (s0 > s1) { t = s0; s0 = s1; s1 = t; }
-  const float twopi = 6.28318530717958647692f;
-  const float g01 = s1 - s0, g12 = s2 - s1, g20 = s0 + twopi - s2;
-  float lo, hi;
-  if (g20 >= g01 && g20 >= g12) { lo = s0; hi = s2; }
-  else if (g01 >= g12) { lo = s1; hi = s0 + twopi; }
-  else { lo = s2; hi = s1 + twopi; }
-  const int ilo = (int)ceilf((lo - cam.az0) / cam.az_step - 0.5f - kRayMarginPx);
-  const int ihi = (int)floorf((hi - cam.az0) / cam.az_step - 0.5f + kRayMarginPx);
-  const int n = ihi - ilo + 1;
-  if (n >= cam.W) {
-    emit_ray(rr, 0, cam.W - 1, j0, j1, a, counts, bins);
-    return;
-  }
-  int st = ilo % cam.W;
-  if (st < 0) st += cam.W;
-  if (st + n <= cam.W) {
-    emit_ray(rr, st, st + n - 1, j0, j1, a, counts, bins);
+    rect[0] = make_int4(0, cam.W - 1, j0, j1);
+    nrect = 1;
   } else {
-    emit_ray(rr, st, cam.W - 1, j0, j1, a, counts, bins);
-    emit_ray(rr, 0, st + n - 1 - cam.W, j0, j1, a, counts, bins);
+    float s0 = u[0].w, s1 = u[1].w, s2 = u[2].w, t;
+    if (s0 > s1) { t = s0; s0 = s1; s1 = t; }
+    if (s1 > s2) { t = s1; s1 = s2; s2 = t; }
+    if (s0 > s1) { t = s0; s0 = s1; s1 = t; }
+    const float twopi = 6.28318530717958647692f;
+    const float g01 = s1 - s0, g12 = s2 - s1, g20 = s0 + twopi - s2;
+    float lo, hi;
+    if (g20 >= g01 && g20 >= g12) { lo = s0; hi = s2; }
+    else if (g01 >= g12) { lo = s1; hi = s0 + twopi; }
+    else { lo = s2; hi = s1 + twopi; }
+    const int ilo = (int)ceilf((lo - cam.az0) / cam.az_step - 0.5f - kRayMarginPx);
+    const int ihi = (int)floorf((hi - cam.az0) / cam.az_step - 0.5f + kRayMarginPx);
+    const int n = ihi - ilo + 1;
+    if (n <= 0) return 0;
+    if (n >= cam.W) {
+      rect[0] = make_int4(0, cam.W - 1, j0, j1);
+      nrect = 1;
+    } else {
+      int st = ilo % cam.W;
+      if (st < 0) st += cam.W;
+      if (st + n <= cam.W) {
+        rect[0] = make_int4(st, st + n - 1, j0, j1);
+        nrect = 1;
+      } else {
+        rect[0] = make_int4(st, cam.W - 1, j0, j1);
+        rect[1] = make_int4(0, st + n - 1 - cam.W, j0, j1);
+        nrect = 2;
+      }
+    }
   }
+  rr.c0x = side[0].x; rr.c0y = side[0].y; rr.c0z = side[0].z;
+  rr.c1x = side[1].x; rr.c1y = side[1].y; rr.c1z = side[1].z;
+  rr.c2x = side[2].x; rr.c2y = side[2].y; rr.c2z = side[2].z;
+  const PlaneN pl = plane_n(v[0], v[1], v[2]);
+  rr.nix = __fdiv_rn(pl.nx, pl.d);
+  rr.niy = __fdiv_rn(pl.ny, pl.d);
+  rr.niz = __fdiv_rn(pl.nz, pl.d);
+  rr.id = id;
+  rr.sig = sig;
+  rr.rect0 = rr.rect1 = 0;
+  return nrect;
 }
 
 constexpr int kClusterMax = 64;  // vertices and triangles per cluster
@@ -371,6 +396,7 @@ struct SetupSmem {
   float4 s_dir[8][kClusterMax];  // ray table: unit direction and azimuth
 };
 
+template <int MODEL>
 __device__ __forceinline__ void setup_block(const WaveArgs &a, int q, int worker, int nworkers,
                                             SetupSmem &sm) {
   float4(*s_vc)[kClusterMax] = sm.s_vc;
@@ -389,7 +415,7 @@ __device__ __forceinline__ void setup_block(const WaveArgs &a, int q, int worker
   unsigned char *bins = a.bins + (long long)q * a.tg.ntiles * a.tg.cap * a.tg.rec_bytes;
   const int W = a.cam.W, H = a.cam.H;
   const float near_m = a.cam.near_m;
-  const bool raytable = a.cam.model != 0;
+  constexpr bool raytable = MODEL != 0;  // one instantiation per camera model
   for (int ci = worker * 8 + warp; ci < nvis; ci += nworkers * 8) {
     const int4 info = __ldcg(&vis[ci]);  // vert offset, tri offset, nv, nt
     for (int k = lane; k < info.z; k += 32) {
@@ -411,21 +437,30 @@ __device__ __forceinline__ void setup_block(const WaveArgs &a, int q, int worker
     }
     __syncwarp();
     if (raytable) {
-      for (int k = lane; k < info.w; k += 32) {
-        const uchar4 t = a.cl_tris[info.y + k];
-        const unsigned id = (unsigned)a.cl_ids[info.y + k];
-        const int loc[3] = {t.x, t.y, t.z};
-        float3 v[3];
-        float4 u[3];
-        int gid[3];
+      // every lane steps through the cluster's triangles together (warp-collective appends)
+      for (int k0 = 0; k0 < info.w; k0 += 32) {
+        const int k = k0 + lane;
+        RayRec rr;
+        int4 rect[2];
+        int nrect = 0;
+        if (k < info.w) {
+          const uchar4 t = a.cl_tris[info.y + k];
+          const unsigned id = (unsigned)a.cl_ids[info.y + k];
+          const int loc[3] = {t.x, t.y, t.z};
+          float3 v[3];
+          float4 u[3];
+          int gid[3];
 #pragma unroll
-        for (int m = 0; m < 3; ++m) {
-          const float4 p = s_vc[warp][loc[m]];
-          v[m] = make_float3(p.x, p.y, p.z);
-          u[m] = s_dir[warp][loc[m]];
-          gid[m] = s_gid[warp][loc[m]];
+          for (int m = 0; m < 3; ++m) {
+            const float4 p = s_vc[warp][loc[m]];
+            v[m] = make_float3(p.x, p.y, p.z);
+            u[m] = s_dir[warp][loc[m]];
+            gid[m] = s_gid[warp][loc[m]];
+          }
+          nrect = setup_ray(v, u, gid, id, a.cam, rr, rect);
         }
-        setup_ray(v, u, gid, id, a, counts, bins);
+        emit_ray_warp(nrect > 0, rr, rect[0], a, counts, bins);
+        if (__any_sync(0xffffffffu, nrect > 1)) emit_ray_warp(nrect > 1, rr, rect[1], a, counts, bins);
       }
       __syncwarp();
       continue;
@@ -500,12 +535,14 @@ __device__ __forceinline__ void setup_block(const WaveArgs &a, int q, int worker
   }
 }
 
-// six resident CTAs per SM (40 registers): setup is bound by the latency of its dependent
-// loads, so more resident warps pay more than registers
-__global__ void __launch_bounds__(256, 6) k_setup(WaveArgs a) {
+// pinhole: six resident CTAs per SM (40 registers): setup is bound by the latency of its
+// dependent loads, so more resident warps pay more than registers; the ray-table setup keeps
+// a record and two rectangles per lane across its appends and gets 64 registers
+template <int MODEL>
+__global__ void __launch_bounds__(256, MODEL == 0 ? 6 : 4) k_setup(WaveArgs a) {
   __shared__ SetupSmem sm;
   if (skipped(a)) return;
-  setup_block(a, blockIdx.y, blockIdx.x, gridDim.x, sm);
+  setup_block<MODEL>(a, blockIdx.y, blockIdx.x, gridDim.x, sm);
 }
 
 // ------------------------------------------------------------------ raster + epilogue
@@ -1139,7 +1176,8 @@ cudaError_t launch_wave(const WaveArgs &a, int mode, cudaStream_t s, cudaEvent_t
   if (a.n_clusters > 0) {
     const int blocks = min(max(a.n_clusters / 64, 1), 96);
     dim3 gs(blocks, a.n_poses);
-    k_setup<<<gs, 256, 0, s>>>(a);
+    if (a.cam.model == 0) k_setup<0><<<gs, 256, 0, s>>>(a);
+    else k_setup<1><<<gs, 256, 0, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (ev && (e = cudaEventRecord(ev[2], s)) != cudaSuccess) return e;
@@ -1431,9 +1469,10 @@ __device__ __noinline__ void persist_cull(const WaveArgs &a, int item, float *sM
   }
 }
 
+template <int MODEL>
 __device__ __noinline__ void persist_setup(const WaveArgs &a, int worker, int nworkers,
                                            SetupSmem &sm) {
-  setup_block(a, 0, worker, nworkers, sm);
+  setup_block<MODEL>(a, 0, worker, nworkers, sm);
 }
 
 template <int MODEL>
@@ -1457,16 +1496,24 @@ __device__ __noinline__ void lm_load_cg(const LMState *src, LMState &dst) {
   for (int k = 0; k < (int)(sizeof(LMState) / 8); ++k) d[k] = __ldcg(s + k);
 }
 
-// One launch runs every phase of every problem of a batch (and, with LM, every iteration):
-// CTAs take items (problem, phase, index, iteration) in queue order from a global counter.
-// An item waits (bounded) until the items it depends on have completed: the setup of a
-// problem's evaluation waits for all of its cull items, the raster for all setup items, the
-// reduction (and LM step) for all tiles, and the next evaluation's cull for that LM step.
-// Dependencies always point to earlier queue positions, which running CTAs have already
-// taken, so the waits end without any co-residency assumption. Thread 0 takes the following
-// item while the current one runs (the atomic's latency overlaps the work). A CTA still runs
-// its items in queue order, so the earliest unfinished item is always being run and every
-// wait still ends.
+// Claims the next slot of a queue that looks non-empty (one atomic add), or returns -1. Two
+// CTAs racing for its last item can both claim; the later one then waits for the queue's next
+// publication, or for the end of the batch.
+__device__ __forceinline__ int claim_slot(int *head, const int *tail) {
+  if (*(volatile const int *)head >= *(volatile const int *)tail) return -1;
+  return atomicAdd(head, 1);
+}
+
+// One launch runs every phase of every problem of a batch (and, with LM, every iteration).
+// Items enter a ready queue only once they can run: the launch starts with the evaluation-0
+// cull items of every problem, and the CTA that completes the last item of a problem's phase
+// appends the next phase (cull -> setup -> raster -> reduce and LM step -> the next
+// evaluation's cull). The number of setup items follows the visible-cluster count of that
+// evaluation. Raster and reduce items go to a queue that is served first, so problems that
+// have reached their raster finish their evaluation before new ones start theirs. A CTA takes
+// only slots that have been reserved by a publisher (whose write is then at most a few
+// instructions away) and exits once every problem has finished; with nothing to take it
+// sleeps and retries (bounded).
 __global__ void __launch_bounds__(kThreads, RM_PERSIST_MIN_BLOCKS) k_persist(BatchArgs b) {
   union PersistSmem {
     RasterSmem<kPersistTileW[0] * kPersistTileH[0], 0> r0;
@@ -1476,38 +1523,54 @@ __global__ void __launch_bounds__(kThreads, RM_PERSIST_MIN_BLOCKS) k_persist(Bat
   };
   __shared__ PersistSmem u;
   __shared__ float s_M[12];
-  __shared__ WaveArgs s_args;  // the current item's problem, copied once per item
+  __shared__ WaveArgs s_args;  // the current item's problem, copied once per problem
   __shared__ int4 s_item;
+  __shared__ int4 s_enq;       // successors to publish: phase, count, first slot, evaluation
   __shared__ int s_abort;
-  int pre = -1;    // thread 0: the queue position taken ahead
   int loaded = -1;  // the problem whose arguments s_args holds
   for (;;) {
     if (threadIdx.x == 0) {
-      const int k = pre >= 0 ? pre : atomicAdd(b.next, 1);
-      pre = k < b.n_items ? atomicAdd(b.next, 1) : -1;
-      int4 item = k < b.n_items ? b.items[k] : make_int4(-1, 0, 0, 0);
+      int4 item = make_int4(-1, 0, 0, 0);
       int abort = 0;
-      if (item.x >= 0) {
-        const int p = item.x, ph = item.y, it = item.w;
-        const int *ctr;
-        int target;
-        if (ph == 0) {
-          ctr = b.done + 4 * p + 3;
-          target = it;
-        } else {
-          ctr = b.done + 4 * p + ph - 1;
-          target = (it + 1) * b.need[3 * p + ph - 1];
+      const long long t0 = clock64();
+      unsigned ns = 32;
+      for (;;) {
+        // a claim past a queue's capacity (racing claims at its very end) holds no slot
+        int slot = claim_slot(b.qctl + 0, b.qctl + 1);
+        if (slot >= b.cap[0]) slot = -1;
+        if (slot < 0) {
+          slot = claim_slot(b.qctl + 2, b.qctl + 3);
+          slot = slot >= b.cap[1] ? -1 : (slot >= 0 ? slot + b.cap[0] : -1);
         }
-        const long long t0 = clock64();
-        while (*(volatile const int *)ctr < target) {
-          if (clock64() - t0 > b.spin_limit) {
+        if (slot >= 0) {
+          int x;
+          bool finished = false;
+          while ((x = *(volatile const int *)&b.items[slot].x) < 0) {
+            if (*(volatile const int *)(b.qctl + 4) >= b.n_problems) {  // nothing more will come
+              finished = true;
+              break;
+            }
+            if (clock64() - t0 > b.spin_limit) break;
+            __nanosleep(64);
+          }
+          if (finished) break;
+          if (x < 0) {
             atomicOr(b.status, kStatusTimeout);
             abort = 1;
             break;
           }
-          __nanosleep(64);
+          __threadfence();
+          item = make_int4(x, __ldcg(&b.items[slot].y), __ldcg(&b.items[slot].z), __ldcg(&b.items[slot].w));
+          break;
         }
-        __threadfence();
+        if (*(volatile const int *)(b.qctl + 4) >= b.n_problems) break;  // all finished
+        if (clock64() - t0 > b.spin_limit) {
+          atomicOr(b.status, kStatusTimeout);
+          abort = 1;
+          break;
+        }
+        __nanosleep(ns);
+        if (ns < 1024) ns *= 2;
       }
       s_item = item;
       s_abort = abort;
@@ -1527,7 +1590,10 @@ __global__ void __launch_bounds__(kThreads, RM_PERSIST_MIN_BLOCKS) k_persist(Bat
     if (!skip) {
       switch (item.y) {
         case 0: persist_cull(a, item.z, s_M); break;
-        case 1: persist_setup(a, item.z, b.need[3 * item.x + 1], u.su); break;
+        case 1:
+          if (a.cam.model == 0) persist_setup<0>(a, item.z, __ldcg(b.need + 3 * item.x + 1), u.su);
+          else persist_setup<1>(a, item.z, __ldcg(b.need + 3 * item.x + 1), u.su);
+          break;
         case 2:
           if (a.cam.model == 0) persist_raster<0>(a, item.z, u.r0);
           else persist_raster<1>(a, item.z, u.r1);
@@ -1552,11 +1618,75 @@ __global__ void __launch_bounds__(kThreads, RM_PERSIST_MIN_BLOCKS) k_persist(Bat
       }
     }
     __syncthreads();
+    // completion; the last item of the problem's phase publishes the successors
     if (threadIdx.x == 0) {
       __threadfence();
-      atomicAdd(b.done + 4 * item.x + item.y, 1);
+      const int p = item.x, ph = item.y, it = item.w;
+      int4 eq = make_int4(0, 0, -1, it);  // phase, count, queue, evaluation
+      if (ph < 3) {
+        const int c = atomicAdd(b.done + 4 * p + ph, 1) + 1;
+        if (c == __ldcg(b.need + 3 * p + ph)) {
+          if (ph == 0) {
+            // all cull items are in: size the setup phase by the visible clusters
+            const int nv = __ldcg(a.vis_count);
+            const int nsetup = max(1, (nv + kSetupClusters - 1) / kSetupClusters);
+            b.need[3 * p + 1] = nsetup;
+            eq = make_int4(1, nsetup, 1, it);
+          } else if (ph == 1) {
+            eq = make_int4(2, b.need[3 * p + 2], 0, it);
+          } else {
+            eq = make_int4(3, 1, 0, it);
+          }
+        }
+      } else if (b.lm && it < b.lm_iters) {
+        b.done[4 * p + 0] = 0;
+        b.done[4 * p + 1] = 0;
+        b.done[4 * p + 2] = 0;
+        eq = make_int4(0, b.need[3 * p], 1, it + 1);
+      } else {
+        atomicAdd(b.qctl + 4, 1);  // the problem is finished
+      }
+      if (eq.y > 0) {
+        const int q = eq.z;
+        const int first = atomicAdd(b.qctl + 2 * q + 1, eq.y);
+        if (first + eq.y > b.cap[q]) atomicOr(b.status, kStatusQueue);  // cannot happen
+        eq.z = (q == 0 ? 0 : b.cap[0]) + first;
+        eq.y = max(0, min(eq.y, b.cap[q] - first));
+      }
+      s_enq = eq;
+    }
+    __syncthreads();
+    const int4 eq = s_enq;
+    if (eq.y > 0) {
+      for (int k = threadIdx.x; k < eq.y; k += blockDim.x) {
+        int4 *slot = b.items + eq.z + k;
+        slot->y = eq.x;
+        slot->z = k;
+        slot->w = eq.w;
+      }
+      __threadfence();
+      __syncthreads();
+      for (int k = threadIdx.x; k < eq.y; k += blockDim.x) atomicExch(&b.items[eq.z + k].x, item.x);
     }
   }
+}
+
+__global__ void k_queue_init(int4 *items, int n_slots, int first_low, int n_problems,
+                             int cull_items, int *qctl) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n0 = n_problems * cull_items;
+  if (k < n_slots) {
+    const int c = k - first_low;
+    items[k] = c >= 0 && c < n0 ? make_int4(c / cull_items, 0, c % cull_items, 0) : make_int4(-1, 0, 0, 0);
+  }
+  if (k == 0) qctl[3] = n0;
+}
+
+cudaError_t launch_queue_init(int4 *items, int n_slots, int first_low, int n_problems,
+                              int cull_items, int *qctl, cudaStream_t s) {
+  k_queue_init<<<(n_slots + 255) / 256, 256, 0, s>>>(items, n_slots, first_low, n_problems,
+                                                     cull_items, qctl);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_lm_init_batch(LMState *st, const double *T0, int n, const LMArgs &a,

@@ -98,20 +98,33 @@ constexpr int kPersistTileH[2] = {32, 32};
 constexpr int kPersistTiles[2] = {1, 2};
 struct BatchArgs {
   const WaveArgs *probs;   // one per problem (n_poses 1, wave_base 0)
-  const int4 *items;       // queue: problem, phase (0 cull, 1 setup, 2 raster, 3 reduce+LM),
-                           // index within the phase, evaluation number
-  int n_items;
-  int *next;               // queue head, zero before launch
-  int *done;               // 4 counters per problem (items completed per phase), zero before
-  const int *need;         // per problem: cull items, setup workers, tiles (per evaluation)
+  int n_problems;
+  // Two ready queues in one slot array: slots [0, cap[0]) take raster and reduce items, slots
+  // [cap[0], cap[0] + cap[1]) cull and setup items. An item is (problem, phase (0 cull,
+  // 1 setup, 2 raster, 3 reduce+LM), index within the phase, evaluation number); a slot's
+  // problem field is -1 until the slot is published.
+  int4 *items;
+  int cap[2];
+  int *qctl;               // head (claimed) and tail (reserved) of each queue, then the number
+                           // of finished problems; zero before launch except the first tail
+  int *done;               // 4 counters per problem: items completed per phase this evaluation
+  int *need;               // per problem: cull items, setup items (set by the kernel each
+                           // evaluation from the visible-cluster count), raster items
   LMState *lm;             // per problem, or null for a plain evaluation
   float *Ms;               // 12 floats per problem (the problems' a.Ms point here)
   int *skip;               // one flag per problem (the problems' a.skip point here)
   LMArgs lmargs;
   int lm_iters;            // LM iterations (evaluations 0..lm_iters)
   unsigned *status;
-  long long spin_limit;    // cycles an item may wait for its dependencies
+  long long spin_limit;    // cycles a CTA may go without finding work before it gives up
 };
+
+constexpr int kSetupClusters = 64;  // visible clusters per setup item (eight per warp)
+
+// Every slot unpublished except the evaluation-0 cull items of every problem at the head of
+// the cull/setup queue; sets that queue's tail.
+cudaError_t launch_queue_init(int4 *items, int n_slots, int first_low, int n_problems,
+                              int cull_items, int *qctl, cudaStream_t s);
 
 cudaError_t launch_lm_init_batch(LMState *st, const double *T0, int n, const LMArgs &a,
                                  float *Ms, int *skip, cudaStream_t s);

@@ -131,3 +131,22 @@ def test_batch_repeated_calls_and_bin_growth():
     for key in keys:
         assert torch.equal(bA3[key], sA[key]), key
     gm.close()
+
+
+def test_batch_empty_map_and_nothing_visible():
+    """A map with no triangles, and one whose only triangles are behind the camera: the
+    persistent kernel still runs every phase (and every LM iteration) and reports zero cost."""
+    cam = cases.small_pinhole()
+    intr = rm.Intrinsics.from_camera(cam)
+    depth = np.full((cam.height, cam.width), 2.0, np.float32)
+    cls = np.zeros((cam.height, cam.width), np.uint8)
+    scan = rm.Scan.make(intr, depth, cls)
+    v, f = cases.plane_grid(3, 3, (-1, -1, -2.0), (2, 0, 0), (0, 2, 0))
+    for mesh in ((np.zeros((0, 3), np.float32), np.zeros((0, 3), np.int32)), (v, f)):
+        gm = rm.Map(mesh[0], mesh[1], np.zeros(len(mesh[1]), np.uint8))
+        b = rm.cost_grad_batch(gm, [(scan, np.eye(4))] * 3)
+        assert int(b["counts"].sum()) == 0 and float(b["e_ls"].abs().sum()) == 0.0
+        poses, reps, status = rm.align_batch(gm, [(scan, np.eye(4))] * 2, max_iters=3)
+        assert status in ("RM_OK", "RM_ENOTCONV")
+        assert np.allclose(poses, np.eye(4)[None])
+        gm.close()
