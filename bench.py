@@ -68,9 +68,10 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def measured_traffic(kernel, poses_per_launch):
+def measured_traffic(kernel, poses_per_launch, n_tris):
     """DRAM bytes per launch of `kernel` from the ncu summary in profiles/, scaled by poses per
-    launch; None when the summary is missing or was taken on different kernel sources."""
+    launch; None when the summary is missing or was taken on different kernel sources or a
+    different map."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_room1M_640x480.md")
     try:
         text = open(path).read()
@@ -79,6 +80,8 @@ def measured_traffic(kernel, poses_per_launch):
     fields = dict(line.split(":", 1) for line in text.splitlines() if ":" in line and " " not in line.split(":", 1)[0])
     try:
         if fields["kernel_source_sha256_16"].strip() != kernel_source_hash():
+            return None
+        if int(fields["map_triangles"]) != int(n_tris):
             return None
         return int(fields["dram_bytes_per_launch"]) / int(fields["poses_per_launch"]) * poses_per_launch
     except (KeyError, ValueError):
@@ -467,7 +470,7 @@ def main():
         "gpu_launches": int(prof["launches"] // a.steps) * a.steps,
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": pk["hbm_gbs"],
                      "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
-                     "traffic": measured_traffic(dom, per_launch_poses),
+                     "traffic": measured_traffic(dom, per_launch_poses, mesh.n_tris),
                      "peak_kind": pk_kind, "avg_launch_ms": avg_s * 1e3,
                      "poses_per_launch": per_launch_poses},
     }
