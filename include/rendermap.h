@@ -217,9 +217,11 @@ typedef struct {
 } rm_problem;
 
 /* rm_cost_grad for n problems that may differ in camera model, resolution and scan, in ONE
- * persistent kernel: CTAs take (problem, phase, index) items from a device queue in order and
- * wait, with bounded spins, only on items earlier in the queue (cluster culling -> triangle
- * setup -> tile raster -> reduction per problem). Outputs as for rm_cost_grad, per problem
+ * persistent kernel: CTAs take (problem, phase, index) items from device ready queues; an item
+ * enters a queue only when its problem's previous phase has completed (cluster culling ->
+ * triangle setup -> tile raster -> reduction per problem), the number of setup items follows
+ * the visible clusters, and raster/reduction items are served first. Every wait is bounded
+ * (RM_ETIMEOUT). Outputs as for rm_cost_grad, per problem
  * (index k = problem). Screen tiles are 64x32 for pinhole problems and 32x32 for ray-table
  * problems, the per-call entry points' defaults, so a problem's results equal those of
  * rm_cost_grad with default tiles bit for bit. (Sec. III.C / Sec. V: many evaluations per
