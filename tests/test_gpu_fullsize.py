@@ -1,4 +1,5 @@
-"""Parity at the benchmark's full size and in its launch configuration.
+"""Parity at full size: the benchmark's workload in its launch configuration, and the
+2M-triangle panoramic (ray-table) workload.
 
 The 1M-triangle 640x480 room with 256 candidate poses, evaluated as the benchmark does (64x32
 tiles, two waves of 128 poses), is checked against the oracle on sampled poses: the first and
@@ -82,3 +83,28 @@ def test_fullsize_persistent_equals_waves(head):
     b = rm.cost_grad_batch(head["gm"], scans=head["scan"], poses=head["poses"])
     for key in ("counts", "e_table", "e_ls", "grad", "jtj"):
         assert torch.equal(g[key], b[key]), key
+
+
+def test_fullsize_lidar_render_and_cost():
+    """The 2M-triangle terrain seen by the 1024x64 panoramic sensor (ray-table model) at its
+    full size: the z-buffer at the true pose bit for bit, cost and gradient at the start pose
+    (30 cm / 3 deg off) within the parity tolerances."""
+    w = synth.workload_lidar()
+    mesh, cam = w["mesh"], w["cam"]
+    gm = rm.Map(mesh.vertices, mesh.faces, mesh.labels)
+    om = oracle.OracleMap(mesh.vertices, mesh.faces, mesh.labels)
+    intr = rm.Intrinsics.from_camera(cam)
+    scan = rm.Scan.make(intr, *w["scan"])
+    r = rm.render_depth(gm, w["gt"][None], intr)
+    o = om.render(w["gt"], cam)
+    ids, depth = _np(r["tri_id"][0]), _np(r["depth"][0])
+    assert np.array_equal(ids, o["tri_id"]), f"{np.sum(ids != o['tri_id'])} pixels differ"
+    hit = ~np.isnan(o["depth"])
+    assert np.array_equal(depth[hit].view(np.uint32), o["depth"][hit].view(np.uint32))
+    g = rm.cost_grad(gm, scan, w["start"][None])
+    oc = om.cost(w["start"], cam, *w["scan"])
+    assert np.array_equal(_np(g["counts"])[0], oc["counts"])
+    assert abs(float(_np(g["e_ls"])[0]) - oc["e_ls"]) <= EPS_REL_COST * abs(oc["e_ls"])
+    assert np.linalg.norm(_np(g["grad"])[0] - oc["grad"]) <= EPS_REL_GRAD * np.linalg.norm(oc["grad"])
+    assert np.linalg.norm(_np(g["jtj"])[0] - oc["jtj"]) <= EPS_REL_GRAD * np.linalg.norm(oc["jtj"])
+    gm.close()
