@@ -102,6 +102,10 @@ struct rm_map {
   long long launches = 0;  // kernels launched since the last rm_profile(map, 1)
   // persistent batch: its launches captured once per batch shape and replayed as a graph
   cudaStream_t cap_stream = nullptr;
+  // per-call waves alternate between the caller's stream and this one, so that one wave's
+  // culling and setup overlap the previous wave's raster
+  cudaStream_t aux_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaGraphExec_t batch_exec = nullptr;
   std::string batch_sig;
   // host copies of the batch queue, dependency counts and per-problem arguments last
@@ -307,7 +311,7 @@ DevCam make_cam(const rm_intrinsics *in, const float *d_rays) {
 int wave_size(const rm_map *m, int n, const TileGeom &tg) {
   if (m->tuning.wave_poses > 0) return std::min(n, m->tuning.wave_poses);
   // up to 128 poses per wave, keeping the per-wave scratch near 4 GiB
-  size_t per = (size_t)m->n_clusters * 4 + (size_t)tg.ntiles * ((size_t)tg.cap * tg.rec_bytes + 8 * 40);
+  size_t per = (size_t)m->n_clusters * sizeof(int4) + (size_t)tg.ntiles * ((size_t)tg.cap * tg.rec_bytes + 8 * 40);
   size_t w = std::max<size_t>(1, (size_t(4) << 30) / std::max<size_t>(per, 1));
   return (int)std::min<size_t>(std::min<size_t>(w, 128), (size_t)n);
 }
@@ -450,10 +454,14 @@ rm_status run_eval(rm_map *m, const EvalReq &r, cudaStream_t s) {
       if (r.tri_id && !dev_id) plan.take<int>(P * r.n);
       if (r.bary && !dev_bary) plan.take<float>(2 * P * r.n);
     }
-    plan.take<int4>((size_t)m->n_clusters * nw);
+    // two sets of per-wave buffers when there are several waves: consecutive waves run on
+    // two streams and overlap (not while profiling, whose per-kernel intervals would then
+    // include the other stream's kernels)
+    const int nbuf = r.n > nw && !m->prof ? 2 : 1;
+    plan.take<int4>((size_t)m->n_clusters * nw * nbuf);
     plan.take<int>((size_t)(tg.ntiles + 1) * r.n);
-    plan.take<unsigned char>((size_t)tg.ntiles * tg.cap * nw * tg.rec_bytes);
-    plan.take<double>((size_t)tg.ntiles * rmk::kNumVals * nw);
+    plan.take<unsigned char>((size_t)tg.ntiles * tg.cap * nw * tg.rec_bytes * nbuf);
+    plan.take<double>((size_t)tg.ntiles * rmk::kNumVals * nw * nbuf);
     RM_TRY(ensure_arena(m, plan.off, s));
     m->batch_inputs_valid = false;
     // ---- carve it
@@ -481,12 +489,12 @@ rm_status run_eval(rm_map *m, const EvalReq &r, cudaStream_t s) {
       if (r.tri_id) d_id = dev_id ? r.tri_id : cv.take<int>(P * r.n);
       if (r.bary) d_bary = dev_bary ? r.bary : cv.take<float>(2 * P * r.n);
     }
-    int4 *d_vis = cv.take<int4>((size_t)m->n_clusters * nw);
+    int4 *d_vis = cv.take<int4>((size_t)m->n_clusters * nw * nbuf);
     // every pose's bin counts and visible-cluster count, zeroed together once per call
     int *d_bcount = cv.take<int>((size_t)(tg.ntiles + 1) * r.n);
     int *d_vcount = d_bcount + (size_t)tg.ntiles * r.n;
-    unsigned char *d_bins = cv.take<unsigned char>((size_t)tg.ntiles * tg.cap * nw * tg.rec_bytes);
-    double *d_partial = cv.take<double>((size_t)tg.ntiles * rmk::kNumVals * nw);
+    unsigned char *d_bins = cv.take<unsigned char>((size_t)tg.ntiles * tg.cap * nw * tg.rec_bytes * nbuf);
+    double *d_partial = cv.take<double>((size_t)tg.ntiles * rmk::kNumVals * nw * nbuf);
     // ---- inputs
     if (host_poses)
       RM_CK(cudaMemcpyAsync((void *)d_poses, r.poses, sizeof(double) * 16 * r.n, cudaMemcpyHostToDevice, s));
@@ -525,12 +533,27 @@ rm_status run_eval(rm_map *m, const EvalReq &r, cudaStream_t s) {
     a.depth = d_depth;
     a.tri_id = d_id;
     a.bary = d_bary;
-    for (int w0 = 0; w0 < r.n; w0 += nw) {
+    if (nbuf == 2) {
+      if (!m->aux_stream) RM_CK(cudaStreamCreateWithFlags(&m->aux_stream, cudaStreamNonBlocking));
+      if (!m->ev_fork) RM_CK(cudaEventCreateWithFlags(&m->ev_fork, cudaEventDisableTiming));
+      if (!m->ev_join) RM_CK(cudaEventCreateWithFlags(&m->ev_join, cudaEventDisableTiming));
+      RM_CK(cudaEventRecord(m->ev_fork, s));
+      RM_CK(cudaStreamWaitEvent(m->aux_stream, m->ev_fork, 0));
+    }
+    for (int w0 = 0, k = 0; w0 < r.n; w0 += nw, ++k) {
+      const int b = k % nbuf;  // buffer set and stream of this wave
       a.wave_base = w0;
       a.n_poses = std::min(nw, r.n - w0);
       a.counts = d_bcount + (size_t)w0 * tg.ntiles;
       a.vis_count = d_vcount + w0;
-      RM_TRY(wave(m, a, r.mode, s, false));
+      a.vis = d_vis + (size_t)m->n_clusters * nw * b;
+      a.bins = d_bins + (size_t)tg.ntiles * tg.cap * nw * tg.rec_bytes * b;
+      a.partial = d_partial + (size_t)tg.ntiles * rmk::kNumVals * nw * b;
+      RM_TRY(wave(m, a, r.mode, b == 0 ? s : m->aux_stream, false));
+    }
+    if (nbuf == 2) {
+      RM_CK(cudaEventRecord(m->ev_join, m->aux_stream));
+      RM_CK(cudaStreamWaitEvent(s, m->ev_join, 0));
     }
     // ---- outputs
     bool host_out = false;
@@ -1017,6 +1040,9 @@ void rm_map_destroy(rm_map *m) {
   cudaFree(m->d_cl_tris);
   cudaFree(m->d_cl_ids);
   cudaFree(m->arena);
+  if (m->aux_stream) cudaStreamDestroy(m->aux_stream);
+  if (m->ev_fork) cudaEventDestroy(m->ev_fork);
+  if (m->ev_join) cudaEventDestroy(m->ev_join);
   cudaFree(m->d_status);
   if (m->h_status) cudaFreeHost(m->h_status);
   for (auto &ev : m->ev_pending)
