@@ -16,7 +16,11 @@ Parity status of each function (what pins it, see ``tests/test_oracle_pins.py``)
   * cost: zero least-squares cost and all-reward Table I at the true pose of a noise-free
     scan rendered by the oracle itself;
   * gradient: central finite differences of the FP64 frozen-visibility cost;
-  * LM: convergence from a perturbed start to the true pose on noise-free scans.
+  * LM: convergence from a perturbed start to the true pose on noise-free scans;
+  * point-to-plane ICP terms: closed forms for a fronto-parallel wall (association count,
+    C, residuals, J^T e, J^T J), the association rules (tolerance, labels, scan classes),
+    finite differences of the frozen point-to-plane cost (J^T e; J^T J where the residuals
+    vanish); ICP alignment: convergence to the true pose on noise-free scans.
 """
 from __future__ import annotations
 
@@ -92,6 +96,7 @@ def lib():
     if _lib is None:
         _lib = ctypes.CDLL(build())
         _lib.orc_cost_frozen.restype = ctypes.c_double
+        _lib.orc_icp_frozen.restype = ctypes.c_double
     return _lib
 
 
@@ -292,3 +297,46 @@ class OracleMap:
                                        ctypes.byref(prm), _p(counts), _p(e), _p(g), _p(h))
         del keep
         return {"counts": counts, "e_ls": e, "grad": g, "jtj": h, "threads": threads}
+
+    def icp_terms(self, pose, cam, scan_depth, scan_class, tol):
+        """Point-to-plane ICP terms with projective association (Sec. IV)."""
+        c, keep = make_cam(cam)
+        na = ctypes.c_int64()
+        l1 = ctypes.c_double()
+        e2 = ctypes.c_double()
+        g = np.zeros(6)
+        h = np.zeros(21)
+        lib().orc_icp_terms(_p(self.v), _p(self.vr), self.V, _p(self.centre), _p(self.faces),
+                            _p(self.labels), self.T, _p(_f64(pose).reshape(16)), ctypes.byref(c),
+                            _p(_f32(scan_depth)), _p(np.ascontiguousarray(scan_class, np.uint8)),
+                            ctypes.c_float(tol), ctypes.byref(na), ctypes.byref(l1),
+                            ctypes.byref(e2), _p(g), _p(h))
+        del keep
+        return {"n_assoc": na.value, "cost_l1": l1.value, "e2": e2.value, "jte": g, "jtj": h}
+
+    def icp_frozen(self, pose, cam, scan_depth, scan_class, tol, xi):
+        c, keep = make_cam(cam)
+        r = lib().orc_icp_frozen(_p(self.v), _p(self.vr), self.V, _p(self.centre), _p(self.faces),
+                                 _p(self.labels), self.T, _p(_f64(pose).reshape(16)),
+                                 ctypes.byref(c), _p(_f32(scan_depth)),
+                                 _p(np.ascontiguousarray(scan_class, np.uint8)),
+                                 ctypes.c_float(tol), _p(_f64(xi)))
+        del keep
+        return r
+
+    def icp_align(self, pose0, cam, scan_depth, scan_class, tol, max_iters=30, step_tol=1e-8):
+        c, keep = make_cam(cam)
+        out = np.empty(16)
+        it = ctypes.c_int()
+        conv = ctypes.c_int()
+        na = ctypes.c_int64()
+        l1 = ctypes.c_double()
+        lib().orc_icp_align(_p(self.v), _p(self.vr), self.V, _p(self.centre), _p(self.faces),
+                            _p(self.labels), self.T, _p(_f64(pose0).reshape(16)), ctypes.byref(c),
+                            _p(_f32(scan_depth)), _p(np.ascontiguousarray(scan_class, np.uint8)),
+                            ctypes.c_float(tol), int(max_iters), ctypes.c_double(step_tol), _p(out),
+                            ctypes.byref(it), ctypes.byref(conv), ctypes.byref(na),
+                            ctypes.byref(l1))
+        del keep
+        return out.reshape(4, 4), {"iters": it.value, "converged": conv.value,
+                                   "n_assoc": na.value, "cost_l1": l1.value}

@@ -819,3 +819,143 @@ int orc_cost_batch(const float *v, const float *vr, int64_t V, const double cent
              0, counts + 6 * k, e_ls + k, grad + 6 * k, jtj + 21 * k, NULL, NULL);
   return threads;
 }
+
+/* ------------------------------------------------------------------------------------- */
+/* Render-accelerated point-to-plane ICP (Sec. IV)                                         */
+/* ------------------------------------------------------------------------------------- */
+
+/* One ICP association at pixel p of the render at Twc: the map surface seen at the pixel
+ * must be occupied (FO), the scan pixel a return (FO), and |Z_M - Z_1| below the tolerance
+ * (Sec. IV), decided on the FP32 z-buffer depth and the FP32 difference. On success returns
+ * 1 with the unit camera-frame normal of the map surface nu, the ray r, the map depth t and
+ * the scan depth d (both as FP64 from the FP32 values) and the FP32 difference. */
+static int icp_pair(const float *v, const int32_t *faces, const uint8_t *labels,
+                    const double Twc[16], const orc_cam *cam, const float *scan_depth,
+                    const uint8_t *scan_class, float tol, const uint64_t *keys, int i, int j,
+                    double nu[3], double r[3], double *t, double *d, float *dz_out) {
+  int64_t p = (int64_t)j * cam->width + i;
+  uint64_t key = keys[p];
+  if (key == KEY_EMPTY) return 0;
+  int64_t id = (int64_t)(key & 0xFFFFFFFFu);
+  if (labels[id] != 0) return 0;
+  if (scan_class_of(scan_depth, scan_class, p) != 0) return 0;
+  float t32 = key_depth(key);
+  float dz32 = t32 - scan_depth[p];
+  if (!(fabsf(dz32) < tol)) return 0;
+  double n[3], dc;
+  plane64(v, faces, id, Twc, n, &dc);
+  double nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+  if (!(nn > 0)) return 0;
+  for (int a = 0; a < 3; ++a) nu[a] = n[a] / nn;
+  ray64(cam, i, j, r);
+  *t = (double)t32;
+  *d = (double)scan_depth[p];
+  *dz_out = dz32;
+  return 1;
+}
+
+int orc_icp_terms(const float *v, const float *vr, int64_t V, const double centre[3],
+                  const int32_t *faces, const uint8_t *labels, int64_t T, const double Twc[16],
+                  const orc_cam *cam, const float *scan_depth, const uint8_t *scan_class,
+                  float tol, int64_t *n_assoc, double *cost_l1, double *e2, double jte[6],
+                  double jtj[21]) {
+  int64_t P = (int64_t)cam->width * cam->height;
+  uint64_t *keys = (uint64_t *)malloc(sizeof(uint64_t) * (P > 0 ? P : 1));
+  if (!keys) return -1;
+  orc_render(vr, V, centre, faces, T, Twc, cam, keys, NULL, 0, NULL);
+  int64_t na = 0;
+  double C = 0.0, E2 = 0.0, g[6] = {0}, H[36] = {0};
+  for (int j = 0; j < cam->height; ++j)
+    for (int i = 0; i < cam->width; ++i) {
+      double nu[3], r[3], t, d;
+      float dz32;
+      if (!icp_pair(v, faces, labels, Twc, cam, scan_depth, scan_class, tol, keys, i, j, nu, r, &t,
+                    &d, &dz32))
+        continue;
+      /* scan point p = d r and map point q = t r on the same ray; residual (p - q) . nu */
+      double pnt[3] = {d * r[0], d * r[1], d * r[2]};
+      double e = (d - t) * (r[0] * nu[0] + r[1] * nu[1] + r[2] * nu[2]);
+      /* d e / d (rho, phi) for Twc <- Twc exp(xi^): the scan point moves by rho + phi x p */
+      double J[6] = {nu[0], nu[1], nu[2], pnt[1] * nu[2] - pnt[2] * nu[1],
+                     pnt[2] * nu[0] - pnt[0] * nu[2], pnt[0] * nu[1] - pnt[1] * nu[0]};
+      na += 1;
+      C += fabs((double)dz32);
+      E2 += e * e;
+      for (int a = 0; a < 6; ++a) {
+        g[a] += J[a] * e;
+        for (int b = 0; b < 6; ++b) H[6 * a + b] += J[a] * J[b];
+      }
+    }
+  free(keys);
+  *n_assoc = na;
+  *cost_l1 = C;
+  *e2 = E2;
+  int q = 0;
+  for (int a = 0; a < 6; ++a) {
+    jte[a] = g[a];
+    for (int b = a; b < 6; ++b) jtj[q++] = H[6 * a + b];
+  }
+  return 0;
+}
+
+double orc_icp_frozen(const float *v, const float *vr, int64_t V, const double centre[3],
+                      const int32_t *faces, const uint8_t *labels, int64_t T,
+                      const double Twc[16], const orc_cam *cam, const float *scan_depth,
+                      const uint8_t *scan_class, float tol, const double xi[6]) {
+  int64_t P = (int64_t)cam->width * cam->height;
+  uint64_t *keys = (uint64_t *)malloc(sizeof(uint64_t) * (P > 0 ? P : 1));
+  if (!keys) return NAN;
+  orc_render(vr, V, centre, faces, T, Twc, cam, keys, NULL, 0, NULL);
+  static const double I[16] = {1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1};
+  double X[16];
+  orc_se3_right(I, xi, X); /* exp(xi^): moves the scan points in the current camera frame */
+  double E = 0.0;
+  for (int j = 0; j < cam->height; ++j)
+    for (int i = 0; i < cam->width; ++i) {
+      double nu[3], r[3], t, d;
+      float dz32;
+      if (!icp_pair(v, faces, labels, Twc, cam, scan_depth, scan_class, tol, keys, i, j, nu, r, &t,
+                    &d, &dz32))
+        continue;
+      double p[3] = {d * r[0], d * r[1], d * r[2]}, q[3] = {t * r[0], t * r[1], t * r[2]};
+      double pm[3];
+      for (int a = 0; a < 3; ++a) pm[a] = X[4 * a] * p[0] + X[4 * a + 1] * p[1] + X[4 * a + 2] * p[2] + X[4 * a + 3];
+      double e = (pm[0] - q[0]) * nu[0] + (pm[1] - q[1]) * nu[1] + (pm[2] - q[2]) * nu[2];
+      E += 0.5 * e * e;
+    }
+  free(keys);
+  return E;
+}
+
+int orc_icp_align(const float *v, const float *vr, int64_t V, const double centre[3],
+                  const int32_t *faces, const uint8_t *labels, int64_t T, const double Twc0[16],
+                  const orc_cam *cam, const float *scan_depth, const uint8_t *scan_class,
+                  float tol, int max_iters, double step_tol, double Twc_out[16], int *iters,
+                  int *converged, int64_t *n_assoc, double *cost_l1) {
+  double Tc[16], Tn[16];
+  memcpy(Tc, Twc0, sizeof(Tc));
+  *converged = 0;
+  int it;
+  int64_t na = 0;
+  double C = 0.0;
+  for (it = 0; it < max_iters; ++it) {
+    double e2, g[6], H[21], dx[6];
+    orc_icp_terms(v, vr, V, centre, faces, labels, T, Tc, cam, scan_depth, scan_class, tol, &na,
+                  &C, &e2, g, H);
+    if (!lm_solve(H, g, 0.0, dx)) break; /* Gauss-Newton: J^T J dx = -J^T e */
+    double nrm = 0;
+    for (int a = 0; a < 6; ++a) nrm += dx[a] * dx[a];
+    orc_se3_right(Tc, dx, Tn);
+    memcpy(Tc, Tn, sizeof(Tc));
+    if (sqrt(nrm) < step_tol) {
+      *converged = 1;
+      ++it;
+      break;
+    }
+  }
+  *iters = it;
+  if (n_assoc) *n_assoc = na;
+  if (cost_l1) *cost_l1 = C;
+  memcpy(Twc_out, Tc, sizeof(Tc));
+  return 0;
+}

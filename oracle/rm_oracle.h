@@ -119,6 +119,35 @@ int orc_cost_batch(const float *v, const float *vr, int64_t V, const double cent
                    const uint8_t *scan_class, const orc_params *prm, int64_t *counts,
                    double *e_ls, double *grad, double *jtj);
 
+/* Render-accelerated point-to-plane ICP (Sec. IV). One iteration's terms at pose Twc: a pixel
+ * is associated when the map surface it sees is FO, the scan pixel is an FO return and
+ * |Z_M - Z_1| < tol (FP32 z-buffer depth, FP32 difference; Sec. IV's z-difference test). With
+ * the scan point p = d r, the map point q = t r on the same ray and the map surface's unit
+ * camera-frame normal n, the residual is e = (p - q) . n and its Jacobian w.r.t. the right-
+ * perturbation twist (rho, phi) of Twc is J = (n, p x n). n_assoc counts the associations,
+ * cost_l1 = sum |Z_M - Z_1| over them (the paper's C), e2 = sum e^2, jte = sum J e,
+ * jtj = upper triangle of sum J J^T. */
+int orc_icp_terms(const float *v, const float *vr, int64_t V, const double centre[3],
+                  const int32_t *faces, const uint8_t *labels, int64_t T, const double Twc[16],
+                  const orc_cam *cam, const float *scan_depth, const uint8_t *scan_class,
+                  float tol, int64_t *n_assoc, double *cost_l1, double *e2, double jte[6],
+                  double jtj[21]);
+
+/* 1/2 sum e^2 with the associations, map points and normals of pose Twc frozen and the scan
+ * points moved by exp(xi^) in its camera frame (for finite-difference checks of jte). */
+double orc_icp_frozen(const float *v, const float *vr, int64_t V, const double centre[3],
+                      const int32_t *faces, const uint8_t *labels, int64_t T,
+                      const double Twc[16], const orc_cam *cam, const float *scan_depth,
+                      const uint8_t *scan_class, float tol, const double xi[6]);
+
+/* ICP iterations: re-render and re-associate, solve J^T J dx = -J^T e (Cholesky), Twc <-
+ * Twc exp(dx^), until |dx| < step_tol (converged = 1) or max_iters iterations. */
+int orc_icp_align(const float *v, const float *vr, int64_t V, const double centre[3],
+                  const int32_t *faces, const uint8_t *labels, int64_t T, const double Twc0[16],
+                  const orc_cam *cam, const float *scan_depth, const uint8_t *scan_class,
+                  float tol, int max_iters, double step_tol, double Twc_out[16], int *iters,
+                  int *converged, int64_t *n_assoc, double *cost_l1);
+
 #ifdef __cplusplus
 }
 #endif
