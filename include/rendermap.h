@@ -53,7 +53,7 @@ typedef enum {
   RM_ECUDA = 3,      /* a CUDA runtime call failed (message in rm_last_error) */
   RM_EOVERFLOW = 4,  /* a screen-tile bin overflowed and could not be grown */
   RM_ETIMEOUT = 5,   /* a bounded device-side wait gave up */
-  RM_ENOTCONV = 6    /* rm_align stopped at max_iters without meeting step_tol */
+  RM_ENOTCONV = 6    /* rm_align / rm_icp_align stopped without meeting step_tol */
 } rm_status;
 
 /* Face labels (Sec. III.A): the interface a map face lies on. */
@@ -193,6 +193,56 @@ rm_status rm_pose_retract(const double *poses, const double *twists, int32_t n_p
 rm_status rm_align(rm_map *map, const rm_scan *scan, const double *init_pose,
                    const rm_cost_params *params, const rm_align_params *lm, double *pose_out,
                    rm_align_report *rep, void *stream);
+
+/* ---- Render-accelerated point-to-plane ICP (Sec. IV) ----------------------------------
+ * Projective association: the map is rendered at the pose and each pixel's winning surface is
+ * paired with the scan return of the same pixel when the surface is FO, the scan pixel is an
+ * FO return, and |Z_M - Z_1| < tol (decided in FP32 on the z-buffer depth and the scan depth,
+ * the z-difference test of Sec. IV). For a pair, with r the pixel's ray, t the map depth, d
+ * the scan depth, p = d r the scan point and n the map surface's unit normal in the camera
+ * frame, the residual is the point-to-plane distance e = (d - t) (n . r) and its Jacobian
+ * with respect to the right-perturbation twist (rho, phi) of the pose (T <- T exp(xi^)) is
+ * J = (n, p x n). Per pose the terms are summed over the pairs in a fixed order. */
+
+/* Per-pose outputs of rm_icp_terms; any pointer may be NULL; host or device. */
+typedef struct {
+  int64_t *n_assoc;         /* N   associated pixels */
+  double *cost_l1;          /* N   C = sum |Z_M - Z_1| over the associated pixels (Sec. IV) */
+  double *e2;               /* N   sum e^2 */
+  double *jte;              /* N*6 sum J e */
+  double *jtj;              /* N*21 packed sum J J^T (row-major upper triangle) */
+} rm_icp_out;
+
+/* ICP terms for N poses (poses: N*16 doubles camera-to-world, host or device) against one
+ * scan. tol (metres) must be >= 0 (0 associates nothing). Arguments are checked as in
+ * rm_cost_grad (RM_EINVAL); the map is not modified. */
+rm_status rm_icp_terms(rm_map *map, const rm_scan *scan, const double *poses, int32_t n_poses,
+                       float tol, const rm_icp_out *out, void *stream);
+
+typedef struct {
+  float tol;                /* association tolerance |Z_M - Z_1|, metres */
+  int32_t max_iters;        /* Gauss-Newton iterations, each one render + association + solve */
+  double step_tol;          /* stop when |delta xi| < step_tol (converged) */
+} rm_icp_params;
+
+typedef struct {
+  int32_t iters;            /* pose updates applied */
+  int32_t converged;        /* 1 when a step below step_tol ended the iterations */
+  int64_t n_assoc;          /* associated pixels at the last evaluation */
+  double cost_l1_initial;   /* C at the initial pose */
+  double cost_l1_final;     /* C at the last evaluation */
+} rm_icp_report;
+
+/* Point-to-plane ICP of one scan from init_pose (16 doubles, host or device), all on the
+ * device: each iteration re-renders and re-associates at the current pose, solves
+ * J^T J delta = -J^T e by Cholesky in FP64 and moves the pose to T exp(delta^). Stops when
+ * |delta| < step_tol, when J^T J is not positive definite (too few or degenerate pairs; the
+ * pose is left where it was), or after max_iters iterations (0..100000). pose_out (16
+ * doubles, host or device) and rep (optional, host) are written in every case; returns
+ * RM_ENOTCONV when no step fell below step_tol. */
+rm_status rm_icp_align(rm_map *map, const rm_scan *scan, const double *init_pose,
+                       const rm_icp_params *params, double *pose_out, rm_icp_report *rep,
+                       void *stream);
 
 /* Per-kernel timing, recorded with CUDA events on the launch stream around every kernel
  * the map launches while enabled. rm_profile(map, 1) clears the record and starts, 0 stops.

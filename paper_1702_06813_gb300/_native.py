@@ -62,6 +62,20 @@ class rm_align_report(ctypes.Structure):
                 ("e_table_initial", ctypes.c_int64), ("e_table_final", ctypes.c_int64)]
 
 
+class rm_icp_out(ctypes.Structure):
+    _fields_ = [("n_assoc", ctypes.c_void_p), ("cost_l1", ctypes.c_void_p), ("e2", ctypes.c_void_p),
+                ("jte", ctypes.c_void_p), ("jtj", ctypes.c_void_p)]
+
+
+class rm_icp_params(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_float), ("max_iters", ctypes.c_int32), ("step_tol", ctypes.c_double)]
+
+
+class rm_icp_report(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("converged", ctypes.c_int32), ("n_assoc", ctypes.c_int64),
+                ("cost_l1_initial", ctypes.c_double), ("cost_l1_final", ctypes.c_double)]
+
+
 class rm_kernel_time(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
@@ -86,6 +100,10 @@ _SIGS = {
                                       ctypes.POINTER(rm_align_report), _P]),
     "rm_align": (ctypes.c_int, [_P, ctypes.POINTER(rm_scan), _P, ctypes.POINTER(rm_cost_params),
                                 ctypes.POINTER(rm_align_params), _P, ctypes.POINTER(rm_align_report), _P]),
+    "rm_icp_terms": (ctypes.c_int, [_P, ctypes.POINTER(rm_scan), _P, ctypes.c_int32, ctypes.c_float,
+                                    ctypes.POINTER(rm_icp_out), _P]),
+    "rm_icp_align": (ctypes.c_int, [_P, ctypes.POINTER(rm_scan), _P, ctypes.POINTER(rm_icp_params), _P,
+                                    ctypes.POINTER(rm_icp_report), _P]),
     "rm_cost_grad_noalloc": (ctypes.c_int, [_P, ctypes.POINTER(rm_scan), _P,
                                             ctypes.POINTER(rm_cost_params), ctypes.POINTER(rm_cost_out), _P]),
     "rm_status_sync": (ctypes.c_int, [_P, _P]),

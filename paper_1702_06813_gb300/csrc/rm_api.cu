@@ -399,6 +399,7 @@ struct EvalReq {
   const rm_cost_params *prm;
   int mode;
   const rm_cost_out *out;
+  const rm_icp_out *icp;  // kIcp: outputs (the tolerance is prm->eps)
   float *depth;
   int32_t *tri_id;
   float *bary;
@@ -433,6 +434,12 @@ rm_status run_eval(rm_map *m, const EvalReq &r, cudaStream_t s) {
   const bool dev_els = cost_mode && r.out->e_ls && on_device(r.out->e_ls);
   const bool dev_grad = grad_mode && r.out->grad && on_device(r.out->grad);
   const bool dev_jtj = grad_mode && r.out->jtj && on_device(r.out->jtj);
+  const bool icp_mode = r.mode == rmk::kIcp && r.icp;
+  const bool dev_n = icp_mode && r.icp->n_assoc && on_device(r.icp->n_assoc);
+  const bool dev_l1 = icp_mode && r.icp->cost_l1 && on_device(r.icp->cost_l1);
+  const bool dev_e2 = icp_mode && r.icp->e2 && on_device(r.icp->e2);
+  const bool dev_jte = icp_mode && r.icp->jte && on_device(r.icp->jte);
+  const bool dev_ijtj = icp_mode && r.icp->jtj && on_device(r.icp->jtj);
 
   for (int attempt = 0;; ++attempt) {
     TileGeom tg = make_tiles(m, in);
@@ -449,6 +456,7 @@ rm_status run_eval(rm_map *m, const EvalReq &r, cudaStream_t s) {
     plan.take<double>(r.n);
     plan.take<double>(6 * (size_t)r.n);
     plan.take<double>(21 * (size_t)r.n);
+    plan.take<double>(r.n);
     if (r.mode == rmk::kRender) {
       if (!dev_depth) plan.take<float>(P * r.n);
       if (r.tri_id && !dev_id) plan.take<int>(P * r.n);
@@ -481,6 +489,7 @@ rm_status run_eval(rm_map *m, const EvalReq &r, cudaStream_t s) {
     double *d_els = cv.take<double>(r.n);
     double *d_grad = cv.take<double>(6 * (size_t)r.n);
     double *d_jtj = cv.take<double>(21 * (size_t)r.n);
+    double *d_l1 = cv.take<double>(r.n);
     float *d_depth = nullptr;
     int *d_id = nullptr;
     float *d_bary = nullptr;
@@ -530,6 +539,15 @@ rm_status run_eval(rm_map *m, const EvalReq &r, cudaStream_t s) {
     a.res_els = dev_els ? r.out->e_ls : d_els;
     a.res_grad = dev_grad ? r.out->grad : d_grad;
     a.res_jtj = dev_jtj ? r.out->jtj : d_jtj;
+    if (r.mode == rmk::kIcp) {
+      a.res_counts = nullptr;
+      a.res_etable = nullptr;
+      a.res_n = dev_n ? reinterpret_cast<long long *>(r.icp->n_assoc) : d_counts;
+      a.res_l1 = dev_l1 ? r.icp->cost_l1 : d_l1;
+      a.res_els = dev_e2 ? r.icp->e2 : d_els;
+      a.res_grad = dev_jte ? r.icp->jte : d_grad;
+      a.res_jtj = dev_ijtj ? r.icp->jtj : d_jtj;
+    }
     a.depth = d_depth;
     a.tri_id = d_id;
     a.bary = d_bary;
@@ -561,7 +579,13 @@ rm_status run_eval(rm_map *m, const EvalReq &r, cudaStream_t s) {
       if (!dev_depth) RM_TRY(copy_out(r.depth, d_depth, sizeof(float) * P * r.n, s, &host_out));
       if (r.tri_id && !dev_id) RM_TRY(copy_out(r.tri_id, d_id, sizeof(int) * P * r.n, s, &host_out));
       if (r.bary && !dev_bary) RM_TRY(copy_out(r.bary, d_bary, sizeof(float) * 2 * P * r.n, s, &host_out));
-    } else if (r.out) {
+    } else if (icp_mode) {
+      if (!dev_n) RM_TRY(copy_out(r.icp->n_assoc, d_counts, sizeof(long long) * r.n, s, &host_out));
+      if (!dev_l1) RM_TRY(copy_out(r.icp->cost_l1, d_l1, sizeof(double) * r.n, s, &host_out));
+      if (!dev_e2) RM_TRY(copy_out(r.icp->e2, d_els, sizeof(double) * r.n, s, &host_out));
+      if (!dev_jte) RM_TRY(copy_out(r.icp->jte, d_grad, sizeof(double) * 6 * r.n, s, &host_out));
+      if (!dev_ijtj) RM_TRY(copy_out(r.icp->jtj, d_jtj, sizeof(double) * 21 * r.n, s, &host_out));
+    } else if (r.mode != rmk::kIcp && r.out) {
       if (!dev_counts) RM_TRY(copy_out(r.out->counts, d_counts, sizeof(long long) * 6 * r.n, s, &host_out));
       if (!dev_etable) RM_TRY(copy_out(r.out->e_table, d_etable, sizeof(long long) * r.n, s, &host_out));
       if (!dev_els) RM_TRY(copy_out(r.out->e_ls, d_els, sizeof(double) * r.n, s, &host_out));
@@ -1087,7 +1111,7 @@ rm_status rm_render_depth(rm_map *m, const double *poses, int32_t n, const rm_in
                           float *depth, int32_t *tri_id, float *bary, void *stream) {
   if (!m) return fail(RM_EINVAL, "map is NULL");
   std::lock_guard<std::mutex> lk(m->mu);
-  EvalReq r{intr, nullptr, poses, n, nullptr, rmk::kRender, nullptr, depth, tri_id, bary};
+  EvalReq r{intr, nullptr, poses, n, nullptr, rmk::kRender, nullptr, nullptr, depth, tri_id, bary};
   return run_eval(m, r, (cudaStream_t)stream);
 }
 
@@ -1096,7 +1120,7 @@ rm_status rm_cost(rm_map *m, const rm_scan *scan, const double *poses, int32_t n
   if (!m) return fail(RM_EINVAL, "map is NULL");
   if (!scan) return fail(RM_EINVAL, "scan is NULL");
   std::lock_guard<std::mutex> lk(m->mu);
-  EvalReq r{&scan->intr, scan, poses, n, prm, rmk::kCost, out, nullptr, nullptr, nullptr};
+  EvalReq r{&scan->intr, scan, poses, n, prm, rmk::kCost, out, nullptr, nullptr, nullptr, nullptr};
   return run_eval(m, r, (cudaStream_t)stream);
 }
 
@@ -1105,7 +1129,18 @@ rm_status rm_cost_grad(rm_map *m, const rm_scan *scan, const double *poses, int3
   if (!m) return fail(RM_EINVAL, "map is NULL");
   if (!scan) return fail(RM_EINVAL, "scan is NULL");
   std::lock_guard<std::mutex> lk(m->mu);
-  EvalReq r{&scan->intr, scan, poses, n, prm, rmk::kCostGrad, out, nullptr, nullptr, nullptr};
+  EvalReq r{&scan->intr, scan, poses, n, prm, rmk::kCostGrad, out, nullptr, nullptr, nullptr, nullptr};
+  return run_eval(m, r, (cudaStream_t)stream);
+}
+
+rm_status rm_icp_terms(rm_map *m, const rm_scan *scan, const double *poses, int32_t n, float tol,
+                       const rm_icp_out *out, void *stream) {
+  if (!m) return fail(RM_EINVAL, "map is NULL");
+  if (!scan) return fail(RM_EINVAL, "scan is NULL");
+  if (!(tol >= 0.0f)) return fail(RM_EINVAL, "tol must be >= 0");
+  std::lock_guard<std::mutex> lk(m->mu);
+  const rm_cost_params prm{tol, 0.0f, 0.0f, 0.0f};
+  EvalReq r{&scan->intr, scan, poses, n, &prm, rmk::kIcp, nullptr, out, nullptr, nullptr, nullptr};
   return run_eval(m, r, (cudaStream_t)stream);
 }
 
@@ -1315,6 +1350,119 @@ rm_status rm_align(rm_map *m, const rm_scan *scan, const double *init_pose,
       rep->e_table_final = hs.e_table;
     }
     return hs.converged ? RM_OK : fail(RM_ENOTCONV, "max_iters reached before step_tol");
+  }
+}
+
+rm_status rm_icp_align(rm_map *m, const rm_scan *scan, const double *init_pose,
+                       const rm_icp_params *prm, double *pose_out, rm_icp_report *rep,
+                       void *stream) {
+  if (!m) return fail(RM_EINVAL, "map is NULL");
+  if (!scan || !scan->depth || !scan->cls) return fail(RM_EINVAL, "scan or its arrays NULL");
+  if (!init_pose || !pose_out || !prm) return fail(RM_EINVAL, "NULL argument");
+  if (prm->max_iters < 0 || prm->max_iters > 100000) return fail(RM_EINVAL, "max_iters out of range");
+  if (!(prm->tol >= 0.0f)) return fail(RM_EINVAL, "tol must be >= 0");
+  std::lock_guard<std::mutex> lk(m->mu);
+  cudaStream_t s = (cudaStream_t)stream;
+  const rm_intrinsics *in = &scan->intr;
+  RM_TRY(check_intr(in));
+  RM_CK(cudaSetDevice(m->device));
+  const long long P = (long long)in->width * in->height;
+  const bool host_scan = !on_device(scan->depth), host_cls = !on_device(scan->cls);
+  const bool host_rays = in->model == RM_RAYTABLE && !on_device(in->rays);
+  for (int attempt = 0;; ++attempt) {
+    TileGeom tg = make_tiles(m, in);
+    Carver plan{nullptr};
+    plan.take<rmk::IcpState>(1);
+    if (host_rays) plan.take<float>(3 * P);
+    plan.take<double>(16);
+    plan.take<float>(12);
+    plan.take<int>(1);
+    if (host_scan) plan.take<float>(P);
+    if (host_cls) plan.take<uint8_t>(P);
+    plan.take<long long>(1);
+    plan.take<double>(1);
+    plan.take<double>(1);
+    plan.take<double>(6);
+    plan.take<double>(21);
+    plan.take<int4>(m->n_clusters);
+    plan.take<int>(1);
+    plan.take<int>(tg.ntiles);
+    plan.take<unsigned char>((size_t)tg.ntiles * tg.cap * tg.rec_bytes);
+    plan.take<double>((size_t)tg.ntiles * rmk::kNumVals);
+    RM_TRY(ensure_arena(m, plan.off, s));
+    m->batch_inputs_valid = false;
+    Carver cv{m->arena};
+    rmk::IcpState *d_st = cv.take<rmk::IcpState>(1);
+    const float *d_rays = host_rays ? cv.take<float>(3 * P) : in->rays;
+    double *d_T0 = cv.take<double>(16);
+    float *d_M = cv.take<float>(12);
+    int *d_skip = cv.take<int>(1);
+    const float *d_sd = host_scan ? cv.take<float>(P) : scan->depth;
+    const uint8_t *d_sc = host_cls ? cv.take<uint8_t>(P) : scan->cls;
+    long long *d_n = cv.take<long long>(1);
+    double *d_l1 = cv.take<double>(1);
+    double *d_e2 = cv.take<double>(1);
+    double *d_g = cv.take<double>(6);
+    double *d_H = cv.take<double>(21);
+    WaveArgs a{};
+    a.cam = make_cam(in, d_rays);
+    a.tg = tg;
+    a.V = (int)m->V;
+    a.T = m->T;
+    a.n_poses = 1;
+    a.wave_base = 0;
+    a.v = m->d_v;
+    a.faces = m->d_faces;
+    a.planes = m->d_planes;
+    a.Ms = d_M;
+    set_clusters(m, a);
+    a.vis = cv.take<int4>(m->n_clusters);
+    a.vis_count = cv.take<int>(1);
+    a.counts = cv.take<int>(tg.ntiles);
+    a.bins = cv.take<unsigned char>((size_t)tg.ntiles * tg.cap * tg.rec_bytes);
+    a.partial = cv.take<double>((size_t)tg.ntiles * rmk::kNumVals);
+    a.status = m->d_status;
+    a.skip = d_skip;
+    a.scan_depth = d_sd;
+    a.scan_cls = d_sc;
+    a.prm = {prm->tol, 0.0f, 0.0f, 0.0f};
+    a.res_n = d_n;
+    a.res_l1 = d_l1;
+    a.res_els = d_e2;
+    a.res_grad = d_g;
+    a.res_jtj = d_H;
+    RM_CK(cudaMemcpyAsync(d_T0, init_pose, sizeof(double) * 16,
+                          on_device(init_pose) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    if (host_rays) RM_CK(cudaMemcpyAsync((void *)d_rays, in->rays, sizeof(float) * 3 * P, cudaMemcpyHostToDevice, s));
+    if (host_scan) RM_CK(cudaMemcpyAsync((void *)d_sd, scan->depth, sizeof(float) * P, cudaMemcpyHostToDevice, s));
+    if (host_cls) RM_CK(cudaMemcpyAsync((void *)d_sc, scan->cls, P, cudaMemcpyHostToDevice, s));
+    const rmk::IcpArgs ia{prm->step_tol, m->centre[0], m->centre[1], m->centre[2]};
+    RM_CK(rmk::launch_icp_init(d_st, d_T0, ia, d_M, d_skip, s));
+    m->launches += 1;
+    for (int it = 0; it < prm->max_iters; ++it) {
+      RM_TRY(wave(m, a, rmk::kIcp, s));
+      RM_CK(rmk::launch_icp_step(d_st, ia, d_n, d_l1, d_g, d_H, d_M, d_skip, s));
+      m->launches += 1;
+    }
+    rmk::IcpState hs;
+    RM_CK(cudaMemcpyAsync(&hs, d_st, sizeof(hs), cudaMemcpyDeviceToHost, s));
+    unsigned st = 0;
+    RM_TRY(read_status(m, s, &st));  // synchronises the stream
+    if (st & rmk::kStatusTimeout) return fail(RM_ETIMEOUT, "a device-side wait ran out of time");
+    if (st & (rmk::kStatusOverflow | rmk::kStatusOverflowRay)) {
+      RM_TRY(grow_bins(m, st, attempt));
+      continue;
+    }
+    if (on_device(pose_out)) RM_CK(cudaMemcpy(pose_out, hs.T, sizeof(double) * 16, cudaMemcpyHostToDevice));
+    else std::memcpy(pose_out, hs.T, sizeof(double) * 16);
+    if (rep) {
+      rep->iters = hs.iters;
+      rep->converged = hs.converged;
+      rep->n_assoc = hs.n_assoc;
+      rep->cost_l1_initial = hs.l1_0;
+      rep->cost_l1_final = hs.l1;
+    }
+    return hs.converged ? RM_OK : fail(RM_ENOTCONV, "no ICP step fell below step_tol");
   }
 }
 

@@ -10,8 +10,11 @@
 //                 copies, integer edge functions with the top-left rule, 64-bit
 //                 depth|id z-test by shared-memory atomicMin (the z-buffer R(Y) of Sec. III);
 //                 then the fused epilogue: Table I per pixel (Sec. III.B), the truncated
-//                 least-squares residual, its pose Jacobian, and a fixed-order reduction
+//                 least-squares residual, its pose Jacobian, and a fixed-order reduction;
+//                 in ICP mode instead the projective association of each pixel's map
+//                 surface with its scan return and the point-to-plane terms (Sec. IV)
 //   k_reduce      per pose: fixed-order sum of the per-tile partials
+// k_lm_* and k_icp_* take the Levenberg-Marquardt and ICP steps between evaluations.
 // k_persist runs the same phases for a batch of problems (and LM iterations) in one launch.
 #include <cfloat>
 #include <cmath>
@@ -994,6 +997,65 @@ __device__ __forceinline__ void raster_block(const WaveArgs &a, int tile, int q,
   }
   const float eps = a.prm.eps;
   const float ifx = 1.0f / a.cam.fx, ify = 1.0f / a.cam.fy;
+  float l1 = 0.0f;  // ICP: sum |Z_M - Z_1| over the associated pixels
+  if (MODE == kIcp) {
+    // ---- point-to-plane ICP epilogue (Sec. IV): projective association of the pixel's map
+    // surface with its scan return, residual e = (d - t)(n . r), J = (n, p x n), p = d r.
+    // Counts field 0 holds the associations; eps is the association tolerance.
+#pragma unroll 1
+    for (int p = tid; p < NP; p += kThreads) {
+      const int i = ox + p % TW, j = oy + p / TW;
+      if (i > xe || j > ye) continue;
+      const unsigned long long key = zk[p];
+      if (key == kKeyEmpty) continue;
+      const long long pix = (long long)j * W + i;
+      const float sd = a.scan_depth[pix];
+      if (a.scan_cls[pix] != 0 || !(fabsf(sd) <= FLT_MAX)) continue;  // FO returns only
+      const float4 pl = a.planes[(unsigned)key];
+      if (__float_as_int(pl.w) != 0) continue;                         // FO surfaces only
+      const float dz = __fsub_rn(key_depth(key), sd);
+      if (!(fabsf(dz) < eps)) continue;
+      float nx = R[0] * pl.x + R[1] * pl.y + R[2] * pl.z;
+      float ny = R[3] * pl.x + R[4] * pl.y + R[5] * pl.z;
+      float nz = R[6] * pl.x + R[7] * pl.y + R[8] * pl.z;
+      const float nn = nx * nx + ny * ny + nz * nz;
+      if (!(nn > 0.0f)) continue;  // degenerate face: no plane
+      const float u = rsqrtf(nn);
+      nx *= u;
+      ny *= u;
+      nz *= u;
+      float rx, ry, rz;
+      if (MODEL == 0) {
+        rx = (i + 0.5f - a.cam.cx) * ifx;
+        ry = (j + 0.5f - a.cam.cy) * ify;
+        rz = 1.0f;
+      } else {
+        const float *rr = a.cam.rays + 3 * pix;
+        rx = rr[0];
+        ry = rr[1];
+        rz = rr[2];
+      }
+      const float e = -dz * (nx * rx + ny * ry + nz * rz);
+      const float px = sd * rx, py = sd * ry, pz = sd * rz;
+      float J[6];
+      J[0] = nx;
+      J[1] = ny;
+      J[2] = nz;
+      J[3] = py * nz - pz * ny;
+      J[4] = pz * nx - px * nz;
+      J[5] = px * ny - py * nx;
+      cnt6 += 1u;
+      l1 += fabsf(dz);
+      acc[0] += e * e;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) acc[1 + k] += J[k] * e;
+      int qk = 7;
+#pragma unroll
+      for (int u2 = 0; u2 < 6; ++u2)
+#pragma unroll
+        for (int v2 = u2; v2 < 6; ++v2) acc[qk++] += J[u2] * J[v2];
+    }
+  } else {
 #pragma unroll 1
   for (int p = tid; p < NP; p += kThreads) {
     const int i = ox + p % TW, j = oy + p / TW;
@@ -1065,6 +1127,7 @@ __device__ __forceinline__ void raster_block(const WaveArgs &a, int tile, int q,
         for (int v = u; v < 6; ++v) acc[qk++] += w * J[u] * J[v];
     }
   }
+  }
   // fixed-order reduction: a reduce-scatter butterfly over the warp (lane L ends with the
   // warp's sum of value L), integer counts by warp reduction, then over the warps in order
   // (FP32, then one conversion to the FP64 tile partial)
@@ -1091,8 +1154,19 @@ __device__ __forceinline__ void raster_block(const WaveArgs &a, int tile, int q,
     const unsigned c = __reduce_add_sync(0xffffffffu, (cnt6 >> (5 * k)) & 31u);
     if (lane == 0) redc[warp][k] = (int)c;
   }
+  if (MODE == kIcp) {
+    // the warp's C in counts field 1 (unused by ICP), as FP32 bits
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) l1 += __shfl_xor_sync(0xffffffffu, l1, off);
+    if (lane == 0) redc[warp][1] = __float_as_int(l1);
+  }
   __syncthreads();
-  if (tid < 6) {
+  if (MODE == kIcp && tid == 1) {
+    float f = 0.0f;
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) f = __fadd_rn(f, __int_as_float(redc[w][1]));
+    a.partial[bin * kNumVals + 1] = (double)f;
+  } else if (tid < 6) {
     int c = 0;
 #pragma unroll
     for (int w = 0; w < kThreads / 32; ++w) c += redc[w][tid];
@@ -1131,6 +1205,8 @@ __device__ __forceinline__ void reduce_block(const WaveArgs &a, int q, double *v
   if (k == 6 && a.res_els) a.res_els[g] = vals[6];
   if (k >= 7 && k < 13 && a.res_grad) a.res_grad[6 * (long long)g + (k - 7)] = vals[k];
   if (k >= 13 && k < kNumVals && a.res_jtj) a.res_jtj[21 * (long long)g + (k - 13)] = vals[k];
+  if (k == 0 && a.res_n) a.res_n[g] = (long long)vals[0];
+  if (k == 1 && a.res_l1) a.res_l1[g] = vals[1];
   if (k == 0 && a.res_etable)
     a.res_etable[g] = (long long)(vals[1] + vals[3] + vals[5]) - (long long)(vals[0] + vals[2] + vals[4]);
 }
@@ -1148,6 +1224,7 @@ static cudaError_t launch_raster_m(const WaveArgs &a, int mode, cudaStream_t s) 
   dim3 grid(a.tg.ntiles, a.n_poses);
   if (mode == kRender) k_raster<TW, TH, kRender, MODEL><<<grid, kThreads, 0, s>>>(a);
   else if (mode == kCost) k_raster<TW, TH, kCost, MODEL><<<grid, kThreads, 0, s>>>(a);
+  else if (mode == kIcp) k_raster<TW, TH, kIcp, MODEL><<<grid, kThreads, 0, s>>>(a);
   else k_raster<TW, TH, kCostGrad, MODEL><<<grid, kThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
@@ -1449,6 +1526,65 @@ __global__ void k_lm_propose(LMState *st, LMArgs a, float *M, int *skip) {
 __global__ void k_lm_accept(LMState *st, LMArgs a, const long long *counts, const double *els,
                             const double *grad, const double *jtj, int *skip) {
   lm_accept_dev(*st, a, counts, els, grad, jtj, *skip != 0);
+}
+
+// ------------------------------------------------------------------ point-to-plane ICP
+
+__global__ void k_icp_init(IcpState *st, const double *T0, IcpArgs a, float *M, int *skip) {
+  for (int k = 0; k < 16; ++k) st->T[k] = T0[k];
+  st->l1_0 = st->l1 = 0.0;
+  st->n_assoc = 0;
+  st->iters = st->converged = st->done = st->evals = 0;
+  pose_to_m(T0, a.cx, a.cy, a.cz, M);
+  *skip = 0;
+}
+
+// Gauss-Newton step of point-to-plane ICP: J^T J dx = -J^T e (Cholesky, no damping), then
+// T <- T exp(dx^). A system that is not positive definite ends the iterations unconverged.
+__global__ void k_icp_step(IcpState *st, IcpArgs a, const long long *n, const double *l1,
+                           const double *g, const double *H, float *M, int *skip) {
+  IcpState &s = *st;
+  if (s.done) {
+    *skip = 1;
+    return;
+  }
+  s.n_assoc = n[0];
+  s.l1 = l1[0];
+  if (s.evals == 0) s.l1_0 = l1[0];
+  s.evals += 1;
+  double dx[6];
+  if (!lm_solve_dev(H, g, 0.0, dx)) {
+    s.done = 1;
+    *skip = 1;
+    return;
+  }
+  double Tn[16];
+  se3_right_dev(s.T, dx, Tn);
+  for (int k = 0; k < 16; ++k) s.T[k] = Tn[k];
+  s.iters += 1;
+  double nrm = 0.0;
+  for (int k = 0; k < 6; ++k) nrm += dx[k] * dx[k];
+  if (sqrt(nrm) < a.step_tol) {
+    s.converged = 1;
+    s.done = 1;
+    *skip = 1;
+    return;
+  }
+  pose_to_m(s.T, a.cx, a.cy, a.cz, M);
+  *skip = 0;
+}
+
+cudaError_t launch_icp_init(IcpState *st, const double *T0, const IcpArgs &a, float *M,
+                            int *skip, cudaStream_t s) {
+  k_icp_init<<<1, 1, 0, s>>>(st, T0, a, M, skip);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_icp_step(IcpState *st, const IcpArgs &a, const long long *n,
+                            const double *l1, const double *g, const double *H, float *M,
+                            int *skip, cudaStream_t s) {
+  k_icp_step<<<1, 1, 0, s>>>(st, a, n, l1, g, H, M, skip);
+  return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ persistent batch kernel

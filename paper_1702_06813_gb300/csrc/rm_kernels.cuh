@@ -50,13 +50,17 @@ struct WaveArgs {
   double *res_els;
   double *res_grad;
   double *res_jtj;
+  // ICP mode (the tolerance travels in prm.eps; e2, J^T e and J^T J in res_els, res_grad and
+  // res_jtj): associated pixels and C = sum |Z_M - Z_1|
+  long long *res_n;
+  double *res_l1;
   // render outputs (global pose index)
   float *depth;
   int *tri_id;
   float *bary;
 };
 
-enum Mode { kRender = 0, kCost = 1, kCostGrad = 2 };
+enum Mode { kRender = 0, kCost = 1, kCostGrad = 2, kIcp = 3 };
 
 cudaError_t launch_pose_to_m(const double *poses, int n, double cx, double cy, double cz,
                              float *Ms, cudaStream_t s);
@@ -88,6 +92,27 @@ struct LMArgs {
   double lambda0, lambda_up, lambda_down, step_tol;
   double cx, cy, cz;   // map centre
 };
+
+// Point-to-plane ICP state on the device (one pose).
+struct IcpState {
+  double T[16];        // current pose
+  double l1_0, l1;     // C at the first and at the last evaluation
+  long long n_assoc;   // associated pixels at the last evaluation
+  int iters, converged, done, evals;
+};
+
+struct IcpArgs {
+  double step_tol;
+  double cx, cy, cz;   // map centre
+};
+
+cudaError_t launch_icp_init(IcpState *st, const double *T0, const IcpArgs &a, float *M,
+                            int *skip, cudaStream_t s);
+// After an evaluation at the state's pose (outputs n, l1, g = J^T e, H = J^T J): record it,
+// solve, move the pose and write its matrix, or set *skip when the iterations are over.
+cudaError_t launch_icp_step(IcpState *st, const IcpArgs &a, const long long *n,
+                            const double *l1, const double *g, const double *H, float *M,
+                            int *skip, cudaStream_t s);
 
 // Batch of problems (each its own camera, scan and scratch) run by one persistent kernel.
 constexpr int kPersistCull = 4;   // 256-cluster chunks per cull item

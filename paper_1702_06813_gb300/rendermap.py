@@ -245,6 +245,38 @@ def align(m: Map, scan: Scan, init_pose, params=None, max_iters=50, lambda0=1e-3
     return out.reshape(4, 4), report
 
 
+def icp_terms(m: Map, scan: Scan, poses, tol=0.1):
+    """Point-to-plane ICP terms with projective association (Sec. IV) for each pose:
+    n_assoc (N,) int64, cost_l1 = C (N,), e2 (N,), jte (N,6) and jtj (N,21) float64."""
+    p, n = _poses(poses)
+    na = torch.empty(n, dtype=torch.int64, device="cuda")
+    l1 = torch.empty(n, dtype=torch.float64, device="cuda")
+    e2 = torch.empty(n, dtype=torch.float64, device="cuda")
+    g = torch.empty((n, 6), dtype=torch.float64, device="cuda")
+    h = torch.empty((n, 21), dtype=torch.float64, device="cuda")
+    out = N.rm_icp_out(na.data_ptr(), l1.data_ptr(), e2.data_ptr(), g.data_ptr(), h.data_ptr())
+    cs = scan.c()
+    check(lib().rm_icp_terms(m.handle, ctypes.byref(cs), _ptr(p), n, float(tol), ctypes.byref(out),
+                             _stream()))
+    return {"n_assoc": na, "cost_l1": l1, "e2": e2, "jte": g, "jtj": h}
+
+
+def icp_align(m: Map, scan: Scan, init_pose, tol=0.1, max_iters=30, step_tol=1e-5):
+    """Point-to-plane ICP on the device; returns (pose 4x4 float64 numpy, report)."""
+    p, _ = _poses(init_pose)
+    out = np.empty(16)
+    rep = N.rm_icp_report()
+    prm = N.rm_icp_params(float(tol), int(max_iters), float(step_tol))
+    cs = scan.c()
+    st = lib().rm_icp_align(m.handle, ctypes.byref(cs), _ptr(p), ctypes.byref(prm),
+                            out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(rep), _stream())
+    if st not in (N.RM_OK, N.RM_ENOTCONV):
+        check(st)
+    report = {f: getattr(rep, f) for f, _ in N.rm_icp_report._fields_}
+    report["status"] = N.STATUS_NAMES[st]
+    return out.reshape(4, 4), report
+
+
 class RenderMapCost(torch.autograd.Function):
     """e_ls(pose * exp(xi^)) as a differentiable function of the twist xi (6,) float64.
 

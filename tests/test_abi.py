@@ -48,6 +48,8 @@ def test_argument_errors_without_gpu(lib):
     assert lib.rm_cost(None, None, None, 0, None, None, None) == N.RM_EINVAL
     assert lib.rm_pose_retract(None, None, -1, None, None, None) == N.RM_EINVAL
     assert lib.rm_map_info(None, None, None, None) == N.RM_EINVAL
+    assert lib.rm_icp_terms(None, None, None, 0, 0.1, None, None) == N.RM_EINVAL
+    assert lib.rm_icp_align(None, None, None, None, None, None, None) == N.RM_EINVAL
 
 
 def test_abi_struct_sizes_match_header():
@@ -60,9 +62,10 @@ def test_abi_struct_sizes_match_header():
 #include <stddef.h>
 #include "rendermap.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(rm_intrinsics), offsetof(rm_intrinsics, rays),
-         sizeof(rm_scan), sizeof(rm_cost_params), sizeof(rm_cost_out), sizeof(rm_tuning),
-         sizeof(rm_align_params), sizeof(rm_align_report));
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(rm_intrinsics),
+         offsetof(rm_intrinsics, rays), sizeof(rm_scan), sizeof(rm_cost_params), sizeof(rm_cost_out),
+         sizeof(rm_tuning), sizeof(rm_align_params), sizeof(rm_align_report), sizeof(rm_icp_out),
+         sizeof(rm_icp_params), sizeof(rm_icp_report), offsetof(rm_icp_report, n_assoc));
   return 0;
 }'''
     with tempfile.TemporaryDirectory() as d:
@@ -73,5 +76,7 @@ int main(void) {
         got = [int(x) for x in subprocess.run([exe], capture_output=True, text=True).stdout.split()]
     want = [ctypes.sizeof(N.rm_intrinsics), N.rm_intrinsics.rays.offset, ctypes.sizeof(N.rm_scan),
             ctypes.sizeof(N.rm_cost_params), ctypes.sizeof(N.rm_cost_out), ctypes.sizeof(N.rm_tuning),
-            ctypes.sizeof(N.rm_align_params), ctypes.sizeof(N.rm_align_report)]
+            ctypes.sizeof(N.rm_align_params), ctypes.sizeof(N.rm_align_report),
+            ctypes.sizeof(N.rm_icp_out), ctypes.sizeof(N.rm_icp_params), ctypes.sizeof(N.rm_icp_report),
+            N.rm_icp_report.n_assoc.offset]
     assert got == want

@@ -212,3 +212,21 @@ def test_icp_empty_and_degenerate():
     pose, rep = om.icp_align(np.eye(4), cam, sd, sc, tol=0.1, max_iters=5)
     assert rep["converged"] == 0 and rep["iters"] == 0
     assert np.array_equal(pose, np.eye(4))
+
+
+def test_icp_single_wall_is_degenerate():
+    """Fig. 2's failure of point-only alignment: a view of one plane constrains only the
+    depth and the two tilts, so J^T J is singular (rank 3) and no Gauss-Newton step is
+    taken; the pose stays where it started."""
+    cam, om = _wall()
+    sd = np.full((cam.height, cam.width), 2.03, np.float32)
+    sc = np.zeros_like(sd, np.uint8)
+    out = om.icp_terms(np.eye(4), cam, sd, sc, tol=0.1)
+    H = np.zeros((6, 6))
+    for a in range(6):
+        for b in range(a, 6):
+            H[a, b] = H[b, a] = out["jtj"][packed(a, b)]
+    assert np.linalg.matrix_rank(H) == 3
+    pose, rep = om.icp_align(np.eye(4), cam, sd, sc, tol=0.1, max_iters=10)
+    assert rep["converged"] == 0 and rep["iters"] == 0
+    assert np.array_equal(pose, np.eye(4))
