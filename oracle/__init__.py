@@ -20,7 +20,10 @@ Parity status of each function (what pins it, see ``tests/test_oracle_pins.py``)
   * point-to-plane ICP terms: closed forms for a fronto-parallel wall (association count,
     C, residuals, J^T e, J^T J), the association rules (tolerance, labels, scan classes),
     finite differences of the frozen point-to-plane cost (J^T e; J^T J where the residuals
-    vanish); ICP alignment: convergence to the true pose on noise-free scans.
+    vanish); ICP alignment: convergence to the true pose on noise-free scans;
+  * depth-image normals (Eq. 2): closed forms for linear and quadratic depth images, a constant
+    image with holes (values, and the invalid set as a dilation of the holes), the metric
+    normal of a tilted plane at the principal point.
 """
 from __future__ import annotations
 
@@ -179,6 +182,20 @@ def decode(keys):
     ids = (keys & np.uint64(0xFFFFFFFF)).astype(np.int64).astype(np.int32)
     ids[empty] = -1
     return depth, ids
+
+
+def depth_normals(depth, cls, sigma=1.0, metric=False, fx=1.0, fy=1.0):
+    """Eq. 2 surface normals of a depth image: (normals (H, W, 3), smoothed depth (H, W))."""
+    d = _f32(depth)
+    c = np.ascontiguousarray(cls, np.uint8)
+    H, W = d.shape
+    n = np.empty((H, W, 3))
+    s = np.empty((H, W))
+    st = lib().orc_depth_normals(_p(d), _p(c), W, H, ctypes.c_double(sigma), int(metric),
+                                 ctypes.c_double(fx), ctypes.c_double(fy), _p(n), _p(s))
+    if st != 0:
+        raise ValueError("bad sigma")
+    return n, s
 
 
 class OracleMap:

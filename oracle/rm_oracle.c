@@ -959,3 +959,62 @@ int orc_icp_align(const float *v, const float *vr, int64_t V, const double centr
   memcpy(Twc_out, Tc, sizeof(Tc));
   return 0;
 }
+
+/* ------------------------------------------------------------------------------------- */
+/* Depth-image surface normals (Eq. 2)                                                     */
+/* ------------------------------------------------------------------------------------- */
+
+static int depth_valid(const float *depth, const uint8_t *cls, int64_t p) {
+  return cls[p] == 0 && fabsf(depth[p]) <= FLT_MAX;
+}
+
+int orc_depth_normals(const float *depth, const uint8_t *cls, int W, int H, double sigma,
+                      int metric, double fx, double fy, double *normals, double *smoothed) {
+  if (W < 0 || H < 0 || !(sigma >= 0.0) || sigma > 5.0) return -1;
+  const int r = sigma > 0.0 ? (int)ceil(3.0 * sigma) : 0;
+  double g[17];
+  for (int k = 0; k <= r; ++k) g[k] = sigma > 0.0 ? exp(-(double)(k * k) / (2.0 * sigma * sigma)) : 1.0;
+  const int64_t P = (int64_t)W * H;
+  double *S = smoothed ? smoothed : (double *)malloc(sizeof(double) * (P > 0 ? P : 1));
+  if (!S) return -1;
+  /* Gaussian smoothing of the valid depths (weights renormalised over the valid ones) */
+  for (int y = 0; y < H; ++y)
+    for (int x = 0; x < W; ++x) {
+      const int64_t p = (int64_t)y * W + x;
+      if (!depth_valid(depth, cls, p)) {
+        S[p] = NAN;
+        continue;
+      }
+      double num = 0.0, den = 0.0;
+      for (int dy = -r; dy <= r; ++dy)
+        for (int dx = -r; dx <= r; ++dx) {
+          const int xx = x + dx, yy = y + dy;
+          if (xx < 0 || xx >= W || yy < 0 || yy >= H) continue;
+          const int64_t q = (int64_t)yy * W + xx;
+          if (!depth_valid(depth, cls, q)) continue;
+          const double wgt = g[abs(dx)] * g[abs(dy)];
+          num += wgt * (double)depth[q];
+          den += wgt;
+        }
+      S[p] = num / den;
+    }
+  /* central differences across and down, then N = a x b with a = (0, s_y, dz/dy) and
+   * b = (s_x, 0, dz/dx): s = 1 pixel, or the pixel's footprint S/f at its depth (metric) */
+  for (int y = 0; y < H; ++y)
+    for (int x = 0; x < W; ++x) {
+      const int64_t p = (int64_t)y * W + x;
+      double *n = normals + 3 * p;
+      n[0] = n[1] = n[2] = NAN;
+      if (x < 1 || x + 1 >= W || y < 1 || y + 1 >= H) continue;
+      if (isnan(S[p]) || isnan(S[p - 1]) || isnan(S[p + 1]) || isnan(S[p - W]) || isnan(S[p + W])) continue;
+      const double zx = 0.5 * (S[p + 1] - S[p - 1]);
+      const double zy = 0.5 * (S[p + W] - S[p - W]);
+      const double sx = metric ? S[p] / fx : 1.0, sy = metric ? S[p] / fy : 1.0;
+      const double a[3] = {0.0, sy, zy}, b[3] = {sx, 0.0, zx};
+      const double c[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
+      const double nn = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+      for (int k = 0; k < 3; ++k) n[k] = c[k] / nn;
+    }
+  if (!smoothed) free(S);
+  return 0;
+}

@@ -148,6 +148,18 @@ int orc_icp_align(const float *v, const float *vr, int64_t V, const double centr
                   float tol, int max_iters, double step_tol, double Twc_out[16], int *iters,
                   int *converged, int64_t *n_assoc, double *cost_l1);
 
+/* Surface normals of a depth image (Eq. 2, Sec. IV). A pixel is valid when its class is FO
+ * (0) and its depth finite. The valid depths are smoothed with a Gaussian of standard
+ * deviation sigma pixels (0 <= sigma <= 5; radius ceil(3 sigma); weights renormalised over
+ * the valid pixels in the window; invalid pixels stay invalid), then differentiated by central
+ * differences across (x) and down (y): dz/dx = (S(x+1) - S(x-1)) / 2 and likewise in y. The
+ * normal is N = a x b with a = (0, s_y, dz/dy) and b = (s_x, 0, dz/dx), normalised, where
+ * s = 1 (pixel units, metric = 0; then N ~ (dz/dx, dz/dy, -1)) or the pixel's footprint at
+ * its depth s_x = S/fx, s_y = S/fy (metric = 1). Border pixels and pixels with an invalid
+ * 4-neighbour get NaN. normals: H*W*3; smoothed (optional): H*W. Returns -1 on a bad sigma. */
+int orc_depth_normals(const float *depth, const uint8_t *cls, int W, int H, double sigma,
+                      int metric, double fx, double fy, double *normals, double *smoothed);
+
 #ifdef __cplusplus
 }
 #endif
