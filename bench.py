@@ -412,9 +412,35 @@ def run_icp(a):
     lidar_align = align_stats(gl, sl, wl["start"], wl["gt"], 0.5, 1e-4)
     gl.close()
 
+    # Eq. 2 normals of 64 depth images (the room scan with per-image noise), sigma 1.5 px,
+    # metric: HBM-bound, 17 algorithmic bytes per pixel (depth, class, normal)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(a.seed)
+    d0 = torch.as_tensor(w["scan"][0], device="cuda")
+    dimg = (d0[None] * (1 + 0.005 * torch.randn((64,) + d0.shape, device="cuda", generator=gen))).contiguous()
+    cimg = torch.as_tensor(w["scan"][1], device="cuda")[None].expand(64, -1, -1).contiguous()
+    nrm = torch.empty(dimg.shape + (3,), dtype=torch.float32, device="cuda")
+    ci = intr.c()
+
+    def normals_step():
+        N.check(N.lib().rm_depth_normals(ctypes.byref(ci), 64, ctypes.c_void_p(dimg.data_ptr()),
+                                         ctypes.c_void_p(cimg.data_ptr()), 1.5, 1,
+                                         ctypes.c_void_p(nrm.data_ptr()), None, sp))
+
+    for _ in range(3):
+        normals_step()
+    ms_n, _ = timed(normals_step, 20)
+    pk, pk_kind = peaks()
+    nb = 17 * dimg.numel()
+    normals_gbs = nb * 20 / (ms_n * 1e-3) / 1e9
+    normals_line = {"images": 64, "image": [cam.width, cam.height], "sigma_px": 1.5, "metric": True,
+                    "us_per_launch": ms_n / 20 * 1e3, "images_per_s": 64 * 20 / (ms_n * 1e-3),
+                    "algorithmic_bytes_per_launch": nb, "achieved_gbs": normals_gbs,
+                    "hbm_frac": normals_gbs / pk["hbm_gbs"],
+                    "l2": "flushed between launches (256 MiB write)"}
+
     P = cam.width * cam.height
     ab = algorithmic_bytes(mesh.n_verts, mesh.n_tris, P)
-    pk, pk_kind = peaks()
     kern = prof["kernels"]
     dom = max(kern, key=lambda k: kern[k][1])
     launches, tot = kern[dom]
@@ -433,6 +459,7 @@ def run_icp(a):
                    "wave_poses": min(n, 128), "l2": "flushed between timed steps (256 MiB write)",
                    "kernel_share": share, "e2e_matches_device": ok,
                    "align_room_1M_640x480": room_align, "align_lidar_2M_1024x64": lidar_align,
+                   "depth_normals_eq2": normals_line,
                    "step_hbm_roofline_frac": ab["total"] * n * a.steps / (ms * 1e-3) / 1e9 / pk["hbm_gbs"]},
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": "pose evals/s",

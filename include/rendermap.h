@@ -244,6 +244,23 @@ rm_status rm_icp_align(rm_map *map, const rm_scan *scan, const double *init_pose
                        const rm_icp_params *params, double *pose_out, rm_icp_report *rep,
                        void *stream);
 
+/* Surface normals of depth images (Eq. 2, Sec. IV), n images of one camera (intr: width,
+ * height, and fx, fy for metric normals), each H*W float depth plus H*W uint8 RM_SCAN_* class,
+ * host or device. A pixel is valid when its class is FO and its depth finite. The valid depths
+ * are smoothed with a Gaussian of sigma pixels (0 <= sigma <= 5, radius ceil(3 sigma), weights
+ * renormalised over the valid pixels of the window; invalid pixels stay invalid), then
+ * differentiated by central differences across and down the image; the normal is
+ * N = a x b, a = (0, s_y, dz/dy), b = (s_x, 0, dz/dx), normalised (it faces the camera: N_z < 0).
+ * metric = 0: s = 1 pixel (N ~ (dz/dx, dz/dy, -1), the paper's image-space form); metric = 1:
+ * s_x = S/fx, s_y = S/fy, the pixel's footprint at its smoothed depth S (pinhole only).
+ * normals: n*H*W*3 float (NaN on the border and where the pixel or a 4-neighbour is invalid);
+ * smoothed (optional): n*H*W float S (NaN where invalid). Host outputs are complete on return;
+ * device outputs are ordered on `stream`. Host arrays are staged through stream-ordered
+ * allocations. Errors: RM_EINVAL (sizes, sigma, metric without a pinhole), RM_ECUDA. */
+rm_status rm_depth_normals(const rm_intrinsics *intr, int32_t n_images, const float *depth,
+                           const uint8_t *cls, float sigma, int32_t metric, float *normals,
+                           float *smoothed, void *stream);
+
 /* Per-kernel timing, recorded with CUDA events on the launch stream around every kernel
  * the map launches while enabled. rm_profile(map, 1) clears the record and starts, 0 stops.
  * rm_profile_read waits for the recorded events and fills up to `cap` entries (one per

@@ -104,6 +104,8 @@ _SIGS = {
                                     ctypes.POINTER(rm_icp_out), _P]),
     "rm_icp_align": (ctypes.c_int, [_P, ctypes.POINTER(rm_scan), _P, ctypes.POINTER(rm_icp_params), _P,
                                     ctypes.POINTER(rm_icp_report), _P]),
+    "rm_depth_normals": (ctypes.c_int, [ctypes.POINTER(rm_intrinsics), ctypes.c_int32, _P, _P, ctypes.c_float,
+                                        ctypes.c_int32, _P, _P, _P]),
     "rm_cost_grad_noalloc": (ctypes.c_int, [_P, ctypes.POINTER(rm_scan), _P,
                                             ctypes.POINTER(rm_cost_params), ctypes.POINTER(rm_cost_out), _P]),
     "rm_status_sync": (ctypes.c_int, [_P, _P]),

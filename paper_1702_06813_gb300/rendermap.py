@@ -277,6 +277,28 @@ def icp_align(m: Map, scan: Scan, init_pose, tol=0.1, max_iters=30, step_tol=1e-
     return out.reshape(4, 4), report
 
 
+def depth_normals(intr: Intrinsics, depth, cls, sigma=1.0, metric=False, want_smoothed=False):
+    """Surface normals of depth images (Eq. 2): depth (N,H,W) or (H,W) float32 and class uint8
+    -> normals (..., H, W, 3) float32, NaN where undefined (and the smoothed depth)."""
+    d = _dev_tensor(depth, torch.float32)
+    c = _dev_tensor(cls, torch.uint8)
+    single = d.dim() == 2
+    d = d.reshape(-1, intr.height, intr.width)
+    c = c.reshape(-1, intr.height, intr.width)
+    if c.shape != d.shape:
+        raise ValueError("one class per depth pixel")
+    n = d.shape[0]
+    nrm = torch.empty((n, intr.height, intr.width, 3), dtype=torch.float32, device="cuda")
+    sm = torch.empty((n, intr.height, intr.width), dtype=torch.float32, device="cuda") if want_smoothed else None
+    ci = intr.c()
+    check(lib().rm_depth_normals(ctypes.byref(ci), n, _ptr(d), _ptr(c), float(sigma), int(bool(metric)),
+                                 _ptr(nrm), _ptr(sm), _stream()))
+    if single:
+        nrm = nrm[0]
+        sm = sm[0] if sm is not None else None
+    return (nrm, sm) if want_smoothed else nrm
+
+
 class RenderMapCost(torch.autograd.Function):
     """e_ls(pose * exp(xi^)) as a differentiable function of the twist xi (6,) float64.
 
