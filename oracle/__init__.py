@@ -23,7 +23,10 @@ Parity status of each function (what pins it, see ``tests/test_oracle_pins.py``)
     vanish); ICP alignment: convergence to the true pose on noise-free scans;
   * depth-image normals (Eq. 2): closed forms for linear and quadratic depth images, a constant
     image with holes (values, and the invalid set as a dilation of the holes), the metric
-    normal of a tilted plane at the principal point.
+    normal of a tilted plane at the principal point;
+  * meshification: closed-form vertices and labels of a fronto-parallel wall, depth steps,
+    no-return and dead pixels, face counts; rendering the mesh of a scan from the scan's own
+    pose reproduces the scan's depths.
 """
 from __future__ import annotations
 
@@ -196,6 +199,28 @@ def depth_normals(depth, cls, sigma=1.0, metric=False, fx=1.0, fy=1.0):
     if st != 0:
         raise ValueError("bad sigma")
     return n, s
+
+
+def meshify(cam, depth, cls, pose, max_range, max_edge=0.1, step=1):
+    """Labelled mesh of a range image (Sec. III.A): (vertices (Hs*Ws, 3) float32, faces (F, 3)
+    int32, labels (F,) uint8)."""
+    c, keep = make_cam(cam)
+    d = _f32(depth)
+    cl = np.ascontiguousarray(cls, np.uint8)
+    Ws = (cam.width - 1) // step + 1 if cam.width > 0 else 0
+    Hs = (cam.height - 1) // step + 1 if cam.height > 0 else 0
+    v = np.empty((Hs * Ws, 3), np.float32)
+    cap = max(2 * max(Hs - 1, 0) * max(Ws - 1, 0), 1)
+    f = np.empty((cap, 3), np.int32)
+    lab = np.empty(cap, np.uint8)
+    nf = ctypes.c_int64()
+    st = lib().orc_meshify(ctypes.byref(c), _p(d), _p(cl), _p(_f64(pose).reshape(16)),
+                           ctypes.c_float(max_range), ctypes.c_float(max_edge), int(step), _p(v), _p(f),
+                           _p(lab), ctypes.byref(nf))
+    del keep
+    if st != 0:
+        raise ValueError("bad meshify parameters")
+    return v, f[:nf.value].copy(), lab[:nf.value].copy()
 
 
 class OracleMap:

@@ -1018,3 +1018,95 @@ int orc_depth_normals(const float *depth, const uint8_t *cls, int W, int H, doub
   if (!smoothed) free(S);
   return 0;
 }
+
+/* ------------------------------------------------------------------------------------- */
+/* Meshification of a range image (Sec. III.A, Fig. 5)                                     */
+/* ------------------------------------------------------------------------------------- */
+
+/* Camera-frame point of pixel (x, y) at range d along its ray, in FP32 (the label test is an
+ * integer decision taken in FP32 on both sides). */
+static void mesh_point32(const orc_cam *cam, int x, int y, float d, float p[3]) {
+  float rx, ry, rz;
+  if (cam->model == 0) {
+    rx = ((float)x + 0.5f - cam->cx) / cam->fx;
+    ry = ((float)y + 0.5f - cam->cy) / cam->fy;
+    rz = 1.0f;
+  } else {
+    const float *q = cam->rays + 3 * ((int64_t)y * cam->width + x);
+    rx = q[0];
+    ry = q[1];
+    rz = q[2];
+  }
+  p[0] = d * rx;
+  p[1] = d * ry;
+  p[2] = d * rz;
+}
+
+static float edge2_32(const float a[3], const float b[3]) {
+  float dx = a[0] - b[0], dy = a[1] - b[1], dz = a[2] - b[2];
+  float xx = dx * dx, yy = dy * dy, zz = dz * dz;
+  float s = xx + yy;
+  return s + zz;
+}
+
+int orc_meshify(const orc_cam *cam, const float *depth, const uint8_t *cls, const double Twc[16],
+                float max_range, float max_edge, int step, float *vertices, int32_t *faces,
+                uint8_t *labels, int64_t *n_faces) {
+  if (step < 1 || !(max_range > 0.0f) || !(max_edge >= 0.0f)) return -1;
+  const int W = cam->width, H = cam->height;
+  const int Ws = W > 0 ? (W - 1) / step + 1 : 0, Hs = H > 0 ? (H - 1) / step + 1 : 0;
+  const int64_t NV = (int64_t)Ws * Hs;
+  /* per grid vertex: kind 0 return (FO), 1 no return (FU, drawn at max_range), 2 dead */
+  uint8_t *kind = (uint8_t *)malloc(NV > 0 ? NV : 1);
+  float *pc = (float *)malloc(sizeof(float) * 3 * (NV > 0 ? NV : 1));
+  if (!kind || !pc) {
+    free(kind);
+    free(pc);
+    return -1;
+  }
+  for (int j = 0; j < Hs; ++j)
+    for (int i = 0; i < Ws; ++i) {
+      const int x = i * step, y = j * step;
+      const int64_t p = (int64_t)y * W + x, v = (int64_t)j * Ws + i;
+      const int c = scan_class_of(depth, cls, p);
+      float d = 0.0f;
+      kind[v] = (uint8_t)c;
+      if (c == 0) d = depth[p];
+      else if (c == 1) d = max_range;
+      mesh_point32(cam, x, y, d, pc + 3 * v);
+      double w[3];
+      for (int a = 0; a < 3; ++a) {
+        if (c == 2) {
+          w[a] = Twc[4 * a + 3];  /* unreferenced: parked at the sensor origin */
+        } else {
+          w[a] = Twc[4 * a] * (double)pc[3 * v] + Twc[4 * a + 1] * (double)pc[3 * v + 1] +
+                 Twc[4 * a + 2] * (double)pc[3 * v + 2] + Twc[4 * a + 3];
+        }
+        vertices[3 * v + a] = (float)w[a];
+      }
+    }
+  const float lim = max_edge * max_edge;
+  int64_t nf = 0;
+  for (int j = 0; j + 1 < Hs; ++j)
+    for (int i = 0; i + 1 < Ws; ++i) {
+      const int64_t v00 = (int64_t)j * Ws + i, v10 = v00 + 1, v01 = v00 + Ws, v11 = v01 + 1;
+      if (kind[v00] == 2 || kind[v10] == 2 || kind[v01] == 2 || kind[v11] == 2) continue;
+      int fu = kind[v00] == 1 || kind[v10] == 1 || kind[v01] == 1 || kind[v11] == 1;
+      const float *a = pc + 3 * v00, *b = pc + 3 * v10, *c = pc + 3 * v11, *d = pc + 3 * v01;
+      if (edge2_32(a, b) > lim || edge2_32(b, c) > lim || edge2_32(c, d) > lim ||
+          edge2_32(d, a) > lim || edge2_32(a, c) > lim)
+        fu = 1;
+      const int32_t t0[3] = {(int32_t)v00, (int32_t)v10, (int32_t)v11};
+      const int32_t t1[3] = {(int32_t)v00, (int32_t)v11, (int32_t)v01};
+      for (int k = 0; k < 3; ++k) {
+        faces[3 * nf + k] = t0[k];
+        faces[3 * nf + 3 + k] = t1[k];
+      }
+      labels[nf] = labels[nf + 1] = (uint8_t)(fu ? 1 : 0);
+      nf += 2;
+    }
+  *n_faces = nf;
+  free(kind);
+  free(pc);
+  return 0;
+}

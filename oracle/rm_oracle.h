@@ -160,6 +160,19 @@ int orc_icp_align(const float *v, const float *vr, int64_t V, const double centr
 int orc_depth_normals(const float *depth, const uint8_t *cls, int W, int H, double sigma,
                       int metric, double fx, double fy, double *normals, double *smoothed);
 
+/* Meshification of a range image (Sec. III.A, Fig. 5). The grid takes every step-th pixel
+ * across and down (step 2 = the factor-2 downsampling of Sec. IV). Each grid pixel is a
+ * vertex at its range along its ray, transformed to the world by Twc: returns (FO) at their
+ * depth, no-return pixels (FU) at max_range; dead pixels (scan class NaN) are parked at the
+ * sensor origin and unreferenced. Each 2x2 block of adjacent grid vertices with no dead pixel
+ * gives two triangles (v00, v10, v11) and (v00, v11, v01), labelled FU when a vertex is a
+ * no-return or a side or the diagonal is longer than max_edge (squared lengths compared in
+ * FP32 in the camera frame), else FO. Faces come in row-major block order. vertices: Hs*Ws*3
+ * with Ws = (W-1)/step + 1; faces: capacity 2*(Hs-1)*(Ws-1)*3; labels likewise. */
+int orc_meshify(const orc_cam *cam, const float *depth, const uint8_t *cls, const double Twc[16],
+                float max_range, float max_edge, int step, float *vertices, int32_t *faces,
+                uint8_t *labels, int64_t *n_faces);
+
 #ifdef __cplusplus
 }
 #endif
