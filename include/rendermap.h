@@ -261,6 +261,31 @@ rm_status rm_depth_normals(const rm_intrinsics *intr, int32_t n_images, const fl
                            const uint8_t *cls, float sigma, int32_t metric, float *normals,
                            float *smoothed, void *stream);
 
+/* ---- Meshification of a range image (Sec. III.A, Fig. 5) ------------------------------ */
+typedef struct {
+  float max_range;          /* no-return pixels are drawn at this range (4 m for Kinect-class) */
+  float max_edge;           /* quads with a side or diagonal longer than this are FU (0.1 m) */
+  int32_t step;             /* grid stride in pixels (1; 2 = the factor-2 downsampling of Sec. IV) */
+  int32_t reserved;
+} rm_meshify_params;
+
+/* The labelled interface mesh of one range image seen from `pose` (16 doubles camera-to-world,
+ * host or device). Grid pixels (every step-th across and down: Ws = (W-1)/step + 1 by
+ * Hs = (H-1)/step + 1) become vertices in the world frame (vertex j*Ws + i for grid pixel
+ * (i, j)): returns (scan class FO, finite depth) at their depth along the pixel's ray,
+ * no-returns (FU) at max_range; dead pixels (class NaN, or a non-finite depth) are parked at
+ * the sensor origin and used by no face. Each 2x2 block of adjacent grid vertices without a
+ * dead pixel gives two triangles (v00, v10, v11), (v00, v11, v01), labelled RM_LABEL FU when a
+ * vertex is a no-return or when a side or the diagonal v00-v11 is longer than max_edge
+ * (squared camera-frame lengths compared in FP32), else FO; faces are in row-major block
+ * order. Outputs (host or device): vertices Ws*Hs*3 float; faces and labels with room for
+ * 2*(Ws-1)*(Hs-1) triangles; *n_faces (host or device) the count. The result feeds
+ * rm_map_create. Host outputs are complete on return. Errors: RM_EINVAL (arguments, as
+ * rm_cost for the intrinsics; step 1..64), RM_ENOMEM, RM_ECUDA. */
+rm_status rm_meshify(const rm_scan *scan, const double *pose, const rm_meshify_params *params,
+                     float *vertices, int32_t *faces, uint8_t *labels, int64_t *n_faces,
+                     void *stream);
+
 /* Per-kernel timing, recorded with CUDA events on the launch stream around every kernel
  * the map launches while enabled. rm_profile(map, 1) clears the record and starts, 0 stops.
  * rm_profile_read waits for the recorded events and fills up to `cap` entries (one per

@@ -76,6 +76,11 @@ class rm_icp_report(ctypes.Structure):
                 ("cost_l1_initial", ctypes.c_double), ("cost_l1_final", ctypes.c_double)]
 
 
+class rm_meshify_params(ctypes.Structure):
+    _fields_ = [("max_range", ctypes.c_float), ("max_edge", ctypes.c_float), ("step", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
 class rm_kernel_time(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
@@ -106,6 +111,8 @@ _SIGS = {
                                     ctypes.POINTER(rm_icp_report), _P]),
     "rm_depth_normals": (ctypes.c_int, [ctypes.POINTER(rm_intrinsics), ctypes.c_int32, _P, _P, ctypes.c_float,
                                         ctypes.c_int32, _P, _P, _P]),
+    "rm_meshify": (ctypes.c_int, [ctypes.POINTER(rm_scan), _P, ctypes.POINTER(rm_meshify_params), _P, _P, _P,
+                                  _P, _P]),
     "rm_cost_grad_noalloc": (ctypes.c_int, [_P, ctypes.POINTER(rm_scan), _P,
                                             ctypes.POINTER(rm_cost_params), ctypes.POINTER(rm_cost_out), _P]),
     "rm_status_sync": (ctypes.c_int, [_P, _P]),

@@ -960,6 +960,10 @@ rm_status wave_inputs(const rm_map *m, const rm_intrinsics *in, WaveArgs *a, dou
 
 void set_error(const std::string &msg) { g_err = msg; }
 
+rm_status check_intrinsics(const rm_intrinsics *in) { return check_intr(in); }
+
+bool is_device_pointer(const void *p) { return on_device(p); }
+
 }  // namespace rmapi
 
 extern "C" {

@@ -176,4 +176,8 @@ rm_status wave_inputs(const rm_map *map, const rm_intrinsics *intr, rmk::WaveArg
                       double centre[3]);
 // Sets the calling thread's rm_last_error message.
 void set_error(const std::string &msg);
+// Checks the intrinsics as every evaluation entry point does (RM_EINVAL with a message).
+rm_status check_intrinsics(const rm_intrinsics *in);
+// True for device (or managed) memory.
+bool is_device_pointer(const void *p);
 }  // namespace rmapi

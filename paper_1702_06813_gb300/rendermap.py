@@ -299,6 +299,27 @@ def depth_normals(intr: Intrinsics, depth, cls, sigma=1.0, metric=False, want_sm
     return (nrm, sm) if want_smoothed else nrm
 
 
+def meshify(scan: Scan, pose, max_range, max_edge=0.1, step=1):
+    """Labelled interface mesh of a range image seen from `pose` (Sec. III.A): vertices
+    (Hs*Ws, 3) float32, faces (F, 3) int32 and labels (F,) uint8, on the device."""
+    p, n = _poses(pose)
+    if n != 1:
+        raise ValueError("one pose")
+    intr = scan.intr
+    st = max(int(step), 1)  # the library rejects step < 1
+    Ws, Hs = (intr.width - 1) // st + 1, (intr.height - 1) // st + 1
+    cap = 2 * (Ws - 1) * (Hs - 1)
+    v = torch.empty((Ws * Hs, 3), dtype=torch.float32, device="cuda")
+    f = torch.empty((max(cap, 1), 3), dtype=torch.int32, device="cuda")
+    lab = torch.empty(max(cap, 1), dtype=torch.uint8, device="cuda")
+    nf = ctypes.c_int64()
+    prm = N.rm_meshify_params(float(max_range), float(max_edge), int(step), 0)
+    cs = scan.c()
+    check(lib().rm_meshify(ctypes.byref(cs), _ptr(p), ctypes.byref(prm), _ptr(v), _ptr(f), _ptr(lab),
+                           ctypes.byref(nf), _stream()))
+    return {"vertices": v, "faces": f[:nf.value], "labels": lab[:nf.value]}
+
+
 class RenderMapCost(torch.autograd.Function):
     """e_ls(pose * exp(xi^)) as a differentiable function of the twist xi (6,) float64.
 
