@@ -94,6 +94,48 @@ class _LMReport(ctypes.Structure):
                 ("e_table_initial", ctypes.c_int64), ("e_table_final", ctypes.c_int64)]
 
 
+class _DfoParams(ctypes.Structure):
+    _fields_ = [("nm_iters", ctypes.c_int32), ("cd_iters", ctypes.c_int32), ("nm_step", ctypes.c_double),
+                ("nm_tol", ctypes.c_double), ("cd_step", ctypes.c_double), ("cd_tol", ctypes.c_double),
+                ("scale_t", ctypes.c_double), ("scale_r", ctypes.c_double)]
+
+
+class _DfoReport(ctypes.Structure):
+    _fields_ = [("evals", ctypes.c_int32), ("nm_iters", ctypes.c_int32), ("nm_shrinks", ctypes.c_int32),
+                ("cd_iters", ctypes.c_int32), ("converged", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+
+
+_BATCH_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                             ctypes.POINTER(ctypes.c_double))
+
+
+def dfo_params(nm_iters=60, cd_iters=60, nm_step=1.0, nm_tol=0.05, cd_step=0.25, cd_tol=0.01,
+               scale_t=0.05, scale_r=0.0349):
+    return _DfoParams(nm_iters, cd_iters, nm_step, nm_tol, cd_step, cd_tol, scale_t, scale_r)
+
+
+def dfo_minimise(f, scale, params=None):
+    """The derivative-free search on a Python function of a (n, 6) batch of twists."""
+    prm = params or dfo_params()
+
+    def cb(_ctx, n, xi, out):
+        x = np.ctypeslib.as_array(xi, shape=(n, 6)).copy()
+        vals = np.asarray(f(x), dtype=np.float64)
+        for i in range(n):
+            out[i] = vals[i]
+        return 0
+
+    fn = _BATCH_FN(cb)
+    x = np.zeros(6)
+    fb = ctypes.c_double()
+    rep = _DfoReport()
+    st = lib().orc_dfo_core(fn, None, _p(_f64(scale)), ctypes.byref(prm), _p(x), ctypes.byref(fb),
+                            ctypes.byref(rep))
+    if st != 0:
+        raise RuntimeError("orc_dfo_core failed")
+    return x, fb.value, {f_: getattr(rep, f_) for f_, _ in _DfoReport._fields_ if f_ != "pad_"}
+
+
 _lib = None
 
 
@@ -339,6 +381,26 @@ class OracleMap:
                                        ctypes.byref(prm), _p(counts), _p(e), _p(g), _p(h))
         del keep
         return {"counts": counts, "e_ls": e, "grad": g, "jtj": h, "threads": threads}
+
+    def dfo_align(self, pose0, cam, scan_depth, scan_class, params=None, dfo=None):
+        """Nelder-Mead then coordinate descent on the Table I cost (Sec. III.C)."""
+        c, keep = make_cam(cam)
+        prm = params or make_params()
+        d = dfo or dfo_params()
+        out = np.empty(16)
+        et = ctypes.c_int64()
+        rep = _DfoReport()
+        st = lib().orc_dfo_align(_p(self.v), _p(self.vr), self.V, _p(self.centre), _p(self.faces),
+                                 _p(self.labels), self.T, _p(_f64(pose0).reshape(16)), ctypes.byref(c),
+                                 _p(_f32(scan_depth)), _p(np.ascontiguousarray(scan_class, np.uint8)),
+                                 ctypes.byref(prm), ctypes.byref(d), _p(out), ctypes.byref(et),
+                                 ctypes.byref(rep))
+        del keep
+        if st != 0:
+            raise RuntimeError("orc_dfo_align failed")
+        r = {f_: getattr(rep, f_) for f_, _ in _DfoReport._fields_ if f_ != "pad_"}
+        r["e_table"] = et.value
+        return out.reshape(4, 4), r
 
     def icp_terms(self, pose, cam, scan_depth, scan_class, tol):
         """Point-to-plane ICP terms with projective association (Sec. IV)."""

@@ -1110,3 +1110,172 @@ int orc_meshify(const orc_cam *cam, const float *depth, const uint8_t *cls, cons
   free(pc);
   return 0;
 }
+
+/* ------------------------------------------------------------------------------------- */
+/* Derivative-free search on the Table I cost (Sec. III.C): Nelder-Mead, then coordinate  */
+/* (compass) descent near the minimum                                                      */
+/* ------------------------------------------------------------------------------------- */
+
+/* The order of simplex vertices: by value, ties by slot index. */
+static void nm_order(const double f[7], int ord[7]) {
+  for (int i = 0; i < 7; ++i) ord[i] = i;
+  for (int i = 1; i < 7; ++i) /* insertion sort, stable */
+    for (int j = i; j > 0 && f[ord[j]] < f[ord[j - 1]]; --j) {
+      int t = ord[j];
+      ord[j] = ord[j - 1];
+      ord[j - 1] = t;
+    }
+}
+
+int orc_dfo_core(orc_batch_fn fn, void *ctx, const double scale[6], const orc_dfo_params *p,
+                 double x_out[6], double *f_out, orc_dfo_report *rep) {
+  double x[7][6], f[7], cand[12][6], fc[12];
+  int evals = 0, nm_iters = 0, shrinks = 0, cd_iters = 0;
+  /* initial simplex: the origin and one step along each axis */
+  for (int i = 0; i < 7; ++i)
+    for (int k = 0; k < 6; ++k) x[i][k] = (i >= 1 && k == i - 1) ? p->nm_step * scale[k] : 0.0;
+  if (fn(ctx, 7, &x[0][0], f)) return -1;
+  evals += 7;
+  while (nm_iters < p->nm_iters) {
+    int o[7];
+    nm_order(f, o);
+    /* stop when every vertex is within nm_tol (in units of scale) of the best */
+    double diam = 0.0;
+    for (int i = 1; i < 7; ++i)
+      for (int k = 0; k < 6; ++k) {
+        double d = fabs(x[o[i]][k] - x[o[0]][k]) / scale[k];
+        if (d > diam) diam = d;
+      }
+    if (diam < p->nm_tol) break;
+    const int h = o[6];
+    double c[6];
+    for (int k = 0; k < 6; ++k) {
+      double s = 0.0;
+      for (int i = 0; i < 6; ++i) s += x[o[i]][k];
+      c[k] = s / 6.0;
+    }
+    /* reflection, expansion, outside and inside contraction, evaluated together */
+    for (int k = 0; k < 6; ++k) {
+      double dk = c[k] - x[h][k];
+      cand[0][k] = c[k] + dk;
+      cand[1][k] = c[k] + 2.0 * dk;
+      cand[2][k] = c[k] + 0.5 * dk;
+      cand[3][k] = c[k] - 0.5 * dk;
+    }
+    if (fn(ctx, 4, &cand[0][0], fc)) return -1;
+    evals += 4;
+    ++nm_iters;
+    const double fb = f[o[0]], fs = f[o[5]], fh = f[h];
+    int take = -1;
+    if (fc[0] < fb) take = fc[1] < fc[0] ? 1 : 0;
+    else if (fc[0] < fs) take = 0;
+    else if (fc[0] < fh) take = fc[2] <= fc[0] ? 2 : -1;
+    else take = fc[3] < fh ? 3 : -1;
+    if (take >= 0) {
+      for (int k = 0; k < 6; ++k) x[h][k] = cand[take][k];
+      f[h] = fc[take];
+    } else {
+      /* shrink toward the best vertex */
+      const int b = o[0];
+      int m = 0;
+      for (int i = 0; i < 7; ++i) {
+        if (i == b) continue;
+        for (int k = 0; k < 6; ++k) cand[m][k] = x[b][k] + 0.5 * (x[i][k] - x[b][k]);
+        ++m;
+      }
+      if (fn(ctx, 6, &cand[0][0], fc)) return -1;
+      evals += 6;
+      ++shrinks;
+      m = 0;
+      for (int i = 0; i < 7; ++i) {
+        if (i == b) continue;
+        for (int k = 0; k < 6; ++k) x[i][k] = cand[m][k];
+        f[i] = fc[m];
+        ++m;
+      }
+    }
+  }
+  int o[7];
+  nm_order(f, o);
+  double xc[6], fcur = f[o[0]], st[6];
+  for (int k = 0; k < 6; ++k) {
+    xc[k] = x[o[0]][k];
+    st[k] = p->cd_step * scale[k];
+  }
+  /* coordinate descent: the best of the 12 moves +-step along each axis, else halve */
+  int converged = 0;
+  while (cd_iters < p->cd_iters) {
+    double smax = 0.0;
+    for (int k = 0; k < 6; ++k)
+      if (st[k] / scale[k] > smax) smax = st[k] / scale[k];
+    if (smax < p->cd_tol) {
+      converged = 1;
+      break;
+    }
+    for (int a = 0; a < 12; ++a)
+      for (int k = 0; k < 6; ++k) cand[a][k] = xc[k] + (k == a / 2 ? (a % 2 ? -st[k] : st[k]) : 0.0);
+    if (fn(ctx, 12, &cand[0][0], fc)) return -1;
+    evals += 12;
+    ++cd_iters;
+    int best = 0;
+    for (int a = 1; a < 12; ++a)
+      if (fc[a] < fc[best]) best = a;
+    if (fc[best] < fcur) {
+      for (int k = 0; k < 6; ++k) xc[k] = cand[best][k];
+      fcur = fc[best];
+    } else {
+      for (int k = 0; k < 6; ++k) st[k] *= 0.5;
+    }
+  }
+  for (int k = 0; k < 6; ++k) x_out[k] = xc[k];
+  *f_out = fcur;
+  if (rep) {
+    rep->evals = evals;
+    rep->nm_iters = nm_iters;
+    rep->nm_shrinks = shrinks;
+    rep->cd_iters = cd_iters;
+    rep->converged = converged;
+  }
+  return 0;
+}
+
+/* The Table I cost of T0 exp(xi^) for a batch of twists. */
+typedef struct {
+  const float *v, *vr;
+  int64_t V, T;
+  const double *centre, *T0;
+  const int32_t *faces;
+  const uint8_t *labels;
+  const orc_cam *cam;
+  const float *sd;
+  const uint8_t *sc;
+  const orc_params *prm;
+} etable_ctx;
+
+static int etable_batch(void *vctx, int n, const double *xi, double *f) {
+  etable_ctx *c = (etable_ctx *)vctx;
+  for (int i = 0; i < n; ++i) {
+    double T[16], g[6], h[21], e;
+    int64_t counts[6];
+    orc_se3_right(c->T0, xi + 6 * i, T);
+    if (orc_cost(c->v, c->vr, c->V, c->centre, c->faces, c->labels, c->T, T, c->cam, c->sd, c->sc,
+                 c->prm, 0, counts, &e, g, h, NULL, NULL))
+      return -1;
+    f[i] = (double)((counts[1] + counts[3] + counts[5]) - (counts[0] + counts[2] + counts[4]));
+  }
+  return 0;
+}
+
+int orc_dfo_align(const float *v, const float *vr, int64_t V, const double centre[3],
+                  const int32_t *faces, const uint8_t *labels, int64_t T, const double Twc0[16],
+                  const orc_cam *cam, const float *scan_depth, const uint8_t *scan_class,
+                  const orc_params *prm, const orc_dfo_params *p, double Twc_out[16],
+                  int64_t *e_table, orc_dfo_report *rep) {
+  etable_ctx c = {v, vr, V, T, centre, Twc0, faces, labels, cam, scan_depth, scan_class, prm};
+  const double scale[6] = {p->scale_t, p->scale_t, p->scale_t, p->scale_r, p->scale_r, p->scale_r};
+  double xi[6], fb;
+  if (orc_dfo_core(etable_batch, &c, scale, p, xi, &fb, rep)) return -1;
+  orc_se3_right(Twc0, xi, Twc_out);
+  *e_table = (int64_t)fb;
+  return 0;
+}

@@ -173,6 +173,43 @@ int orc_meshify(const orc_cam *cam, const float *depth, const uint8_t *cls, cons
                 float max_range, float max_edge, int step, float *vertices, int32_t *faces,
                 uint8_t *labels, int64_t *n_faces);
 
+/* Derivative-free search (Sec. III.C): Nelder-Mead iterations, then coordinate descent once
+ * near the minimum. The search runs over twists xi (rho in metres, phi in radians) scaled
+ * per axis by `scale`; each step evaluates its candidates as one batch.
+ *  - Simplex: the origin and nm_step * scale_k along each axis k. Per iteration the vertices
+ *    are ordered by value (ties by slot), c is the mean of the best six (summed in that
+ *    order, divided by 6), and four candidates c + d, c + 2d, c + d/2, c - d/2 with
+ *    d = c - x_worst are evaluated together; the usual rules pick one (reflect: f_r below
+ *    the second worst; expand: f_e < f_r < f_best; outside contraction: f_oc <= f_r < f_worst;
+ *    inside contraction: f_ic < f_worst <= f_r) or shrink every vertex halfway toward the
+ *    best (a batch of six). Ends after nm_iters iterations or when every vertex lies within
+ *    nm_tol (scaled, per axis) of the best.
+ *  - Coordinate descent from the best vertex with steps cd_step * scale: the 12 moves +-step
+ *    along each axis as one batch; the lowest (ties: the first, +axis0, -axis0, +axis1, ...)
+ *    is taken if it is below the current value, else every step is halved. Converged when the
+ *    largest scaled step is below cd_tol; ends after cd_iters iterations otherwise. */
+typedef int (*orc_batch_fn)(void *ctx, int n, const double *xi, double *f);
+
+typedef struct {
+  int32_t nm_iters, cd_iters;
+  double nm_step, nm_tol, cd_step, cd_tol;
+  double scale_t, scale_r;   /* metres and radians per unit of the scaled twist */
+} orc_dfo_params;
+
+typedef struct {
+  int32_t evals, nm_iters, nm_shrinks, cd_iters, converged, pad_;
+} orc_dfo_report;
+
+int orc_dfo_core(orc_batch_fn fn, void *ctx, const double scale[6], const orc_dfo_params *p,
+                 double x_out[6], double *f_out, orc_dfo_report *rep);
+
+/* The search above on f(xi) = E_table(Twc0 exp(xi^)), the Table I cost (integer valued). */
+int orc_dfo_align(const float *v, const float *vr, int64_t V, const double centre[3],
+                  const int32_t *faces, const uint8_t *labels, int64_t T, const double Twc0[16],
+                  const orc_cam *cam, const float *scan_depth, const uint8_t *scan_class,
+                  const orc_params *prm, const orc_dfo_params *p, double Twc_out[16],
+                  int64_t *e_table, orc_dfo_report *rep);
+
 #ifdef __cplusplus
 }
 #endif
