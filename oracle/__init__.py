@@ -265,6 +265,23 @@ def meshify(cam, depth, cls, pose, max_range, max_edge=0.1, step=1):
     return v, f[:nf.value].copy(), lab[:nf.value].copy()
 
 
+def scan_from_range(rng, range_min, range_max):
+    """(depth, class) of a raw range image by the no-return / dead-pixel rules."""
+    r = _f32(rng)
+    d = np.empty_like(r)
+    c = np.empty(r.shape, np.uint8)
+    lib().orc_scan_from_range(_p(r), ctypes.c_int64(r.size), ctypes.c_float(range_min),
+                              ctypes.c_float(range_max), _p(d), _p(c))
+    return d, c
+
+
+def pose_from_x(X):
+    """4x4 camera-to-world pose of X = (x, y, z, theta_x, theta_y, theta_z), R = Rz Ry Rx."""
+    T = np.empty(16)
+    lib().orc_pose_from_x(_p(_f64(X).reshape(6)), _p(T))
+    return T.reshape(4, 4)
+
+
 class OracleMap:
     """The oracle's copy of a labelled triangle-mesh map (Sec. III.A)."""
 

@@ -1279,3 +1279,45 @@ int orc_dfo_align(const float *v, const float *vr, int64_t V, const double centr
   *e_table = (int64_t)fb;
   return 0;
 }
+
+/* ------------------------------------------------------------------------------------- */
+/* Scan classes from a raw range image (Sec. III.A, III.B); pose from X (Eq. 1)             */
+/* ------------------------------------------------------------------------------------- */
+
+void orc_scan_from_range(const float *range, int64_t n, float range_min, float range_max,
+                         float *depth, uint8_t *cls) {
+  for (int64_t i = 0; i < n; ++i) {
+    const float r = range[i];
+    if (isnan(r) || (r > 0.0f && r < range_min)) {
+      /* dead pixel, or a return closer than the sensor can measure */
+      depth[i] = NAN;
+      cls[i] = 2;
+    } else if (r <= 0.0f || r > range_max) {
+      /* no reading: free space up to the maximal range */
+      depth[i] = range_max;
+      cls[i] = 1;
+    } else {
+      depth[i] = r;
+      cls[i] = 0;
+    }
+  }
+}
+
+void orc_pose_from_x(const double X[6], double T[16]) {
+  const double cx = cos(X[3]), sx = sin(X[3]), cy = cos(X[4]), sy = sin(X[4]);
+  const double cz = cos(X[5]), sz = sin(X[5]);
+  const double Rx[9] = {1, 0, 0, 0, cx, -sx, 0, sx, cx};
+  const double Ry[9] = {cy, 0, sy, 0, 1, 0, -sy, 0, cy};
+  const double Rz[9] = {cz, -sz, 0, sz, cz, 0, 0, 0, 1};
+  double A[9], R[9];
+  for (int i = 0; i < 3; ++i) /* A = Rz Ry */
+    for (int j = 0; j < 3; ++j) A[3 * i + j] = Rz[3 * i] * Ry[j] + Rz[3 * i + 1] * Ry[3 + j] + Rz[3 * i + 2] * Ry[6 + j];
+  for (int i = 0; i < 3; ++i) /* R = A Rx */
+    for (int j = 0; j < 3; ++j) R[3 * i + j] = A[3 * i] * Rx[j] + A[3 * i + 1] * Rx[3 + j] + A[3 * i + 2] * Rx[6 + j];
+  for (int i = 0; i < 3; ++i) {
+    for (int j = 0; j < 3; ++j) T[4 * i + j] = R[3 * i + j];
+    T[4 * i + 3] = X[i];
+  }
+  T[12] = T[13] = T[14] = 0.0;
+  T[15] = 1.0;
+}

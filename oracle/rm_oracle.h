@@ -210,6 +210,17 @@ int orc_dfo_align(const float *v, const float *vr, int64_t V, const double centr
                   const orc_params *prm, const orc_dfo_params *p, double Twc_out[16],
                   int64_t *e_table, orc_dfo_report *rep);
 
+/* Depth and class of each pixel of a raw range image (Sec. III.A, III.B): NaN, or a return
+ * closer than range_min (and above 0), is dead (NaN class, NaN depth); no reading (<= 0,
+ * above range_max, +inf) is free space up to the maximal range (FU, depth range_max); the rest
+ * are returns (FO, their range). */
+void orc_scan_from_range(const float *range, int64_t n, float range_min, float range_max,
+                         float *depth, uint8_t *cls);
+
+/* Camera-to-world pose from the paper's X = (x, y, z, theta_x, theta_y, theta_z) (Eq. 1),
+ * read as R = Rz(theta_z) Ry(theta_y) Rx(theta_x) and translation (x, y, z). */
+void orc_pose_from_x(const double X[6], double T[16]);
+
 #ifdef __cplusplus
 }
 #endif
