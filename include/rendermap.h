@@ -194,6 +194,21 @@ rm_status rm_align(rm_map *map, const rm_scan *scan, const double *init_pose,
                    const rm_cost_params *params, const rm_align_params *lm, double *pose_out,
                    rm_align_report *rep, void *stream);
 
+/* ---- Input helpers ----------------------------------------------------------------------
+ * Depth and class of n pixels of raw range images (Sec. III.A, III.B): a NaN reading, or a
+ * return closer than range_min (and above 0), is a dead pixel (RM_SCAN_NAN, depth NaN); no
+ * reading (<= 0, above range_max, +inf) is free space up to the sensor's maximal range
+ * (RM_SCAN_FU, depth range_max); the rest are returns (RM_SCAN_FO, their range). Arrays host
+ * or device (host outputs complete on return). RM_EINVAL unless 0 <= range_min < range_max
+ * < inf. */
+rm_status rm_scan_from_range(const float *range, int64_t n_pixels, float range_min,
+                             float range_max, float *depth, uint8_t *cls, void *stream);
+
+/* Camera-to-world poses (n*16 doubles) from the paper's pose vectors X = (x, y, z, theta_x,
+ * theta_y, theta_z) (n*6 doubles, Eq. 1), read as R = Rz(theta_z) Ry(theta_y) Rx(theta_x)
+ * (the paper does not state the order) and translation (x, y, z). Host or device. */
+rm_status rm_pose_from_x(const double *X, int32_t n, double *poses, void *stream);
+
 /* ---- Render-accelerated point-to-plane ICP (Sec. IV) ----------------------------------
  * Projective association: the map is rendered at the pose and each pixel's winning surface is
  * paired with the scan return of the same pixel when the surface is FO, the scan pixel is an
@@ -261,6 +276,39 @@ rm_status rm_depth_normals(const rm_intrinsics *intr, int32_t n_images, const fl
                            const uint8_t *cls, float sigma, int32_t metric, float *normals,
                            float *smoothed, void *stream);
 
+/* ---- Derivative-free search on the Table I cost (Sec. III.C) ---------------------------
+ * The paper minimises its piecewise-constant cost with Nelder-Mead and coordinate descent.
+ * Here both run on the device over twists xi of the start pose (pose = T0 exp(xi^)), scaled
+ * per axis by scale_t (metres) and scale_r (radians); each step's candidates are rendered and
+ * scored together as one batch of 12 poses:
+ *  - Nelder-Mead: simplex = origin plus nm_step * scale on each axis; per iteration the four
+ *    points c + d, c + 2d, c + d/2, c - d/2 (c the centroid of the best six, d = c - worst)
+ *    are scored together and the usual reflect / expand / contract / shrink rules applied
+ *    (ties in value: the lower slot ranks first); ends after nm_iters iterations or when every
+ *    vertex is within nm_tol (scaled) of the best;
+ *  - coordinate descent from the best vertex with steps cd_step * scale: the 12 moves +-step
+ *    along each axis scored together; the best move is taken if it lowers the cost, else all
+ *    steps halve; converged when the largest scaled step is below cd_tol. */
+typedef struct {
+  int32_t nm_iters, cd_iters;
+  double nm_step, nm_tol, cd_step, cd_tol;
+  double scale_t, scale_r;
+} rm_dfo_params;
+
+typedef struct {
+  int32_t evals;            /* poses scored (candidates only) */
+  int32_t nm_iters, nm_shrinks, cd_iters, converged, reserved;
+  int64_t e_table_initial, e_table_final;
+} rm_dfo_report;
+
+/* Derivative-free alignment of one scan from init_pose (16 doubles, host or device) on the
+ * Table I cost with parameters `params` (the cost's eps and weights; the weights do not enter
+ * E_table). pose_out (host or device) and rep (optional, host) are written in every case;
+ * returns RM_ENOTCONV when coordinate descent ran out of iterations. */
+rm_status rm_dfo_align(rm_map *map, const rm_scan *scan, const double *init_pose,
+                       const rm_cost_params *params, const rm_dfo_params *dfo, double *pose_out,
+                       rm_dfo_report *rep, void *stream);
+
 /* ---- Meshification of a range image (Sec. III.A, Fig. 5) ------------------------------ */
 typedef struct {
   float max_range;          /* no-return pixels are drawn at this range (4 m for Kinect-class) */
@@ -280,8 +328,10 @@ typedef struct {
  * (squared camera-frame lengths compared in FP32), else FO; faces are in row-major block
  * order. Outputs (host or device): vertices Ws*Hs*3 float; faces and labels with room for
  * 2*(Ws-1)*(Hs-1) triangles; *n_faces (host or device) the count. The result feeds
- * rm_map_create. Host outputs are complete on return. Errors: RM_EINVAL (arguments, as
- * rm_cost for the intrinsics; step 1..64), RM_ENOMEM, RM_ECUDA. */
+ * rm_map_create. Host outputs are complete on return; with device outputs and a device pose
+ * the call does not wait for the GPU. A host pose must be finite (RM_EINVAL); a device pose
+ * is not checked. Errors: RM_EINVAL (arguments, as rm_cost for the intrinsics; step
+ * 1..64), RM_ENOMEM, RM_ECUDA. */
 rm_status rm_meshify(const rm_scan *scan, const double *pose, const rm_meshify_params *params,
                      float *vertices, int32_t *faces, uint8_t *labels, int64_t *n_faces,
                      void *stream);

@@ -81,6 +81,18 @@ class rm_meshify_params(ctypes.Structure):
                 ("reserved", ctypes.c_int32)]
 
 
+class rm_dfo_params(ctypes.Structure):
+    _fields_ = [("nm_iters", ctypes.c_int32), ("cd_iters", ctypes.c_int32), ("nm_step", ctypes.c_double),
+                ("nm_tol", ctypes.c_double), ("cd_step", ctypes.c_double), ("cd_tol", ctypes.c_double),
+                ("scale_t", ctypes.c_double), ("scale_r", ctypes.c_double)]
+
+
+class rm_dfo_report(ctypes.Structure):
+    _fields_ = [("evals", ctypes.c_int32), ("nm_iters", ctypes.c_int32), ("nm_shrinks", ctypes.c_int32),
+                ("cd_iters", ctypes.c_int32), ("converged", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("e_table_initial", ctypes.c_int64), ("e_table_final", ctypes.c_int64)]
+
+
 class rm_kernel_time(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
@@ -113,6 +125,10 @@ _SIGS = {
                                         ctypes.c_int32, _P, _P, _P]),
     "rm_meshify": (ctypes.c_int, [ctypes.POINTER(rm_scan), _P, ctypes.POINTER(rm_meshify_params), _P, _P, _P,
                                   _P, _P]),
+    "rm_dfo_align": (ctypes.c_int, [_P, ctypes.POINTER(rm_scan), _P, ctypes.POINTER(rm_cost_params),
+                                    ctypes.POINTER(rm_dfo_params), _P, ctypes.POINTER(rm_dfo_report), _P]),
+    "rm_scan_from_range": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_float, ctypes.c_float, _P, _P, _P]),
+    "rm_pose_from_x": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),
     "rm_cost_grad_noalloc": (ctypes.c_int, [_P, ctypes.POINTER(rm_scan), _P,
                                             ctypes.POINTER(rm_cost_params), ctypes.POINTER(rm_cost_out), _P]),
     "rm_status_sync": (ctypes.c_int, [_P, _P]),

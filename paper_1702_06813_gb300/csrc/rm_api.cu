@@ -1357,6 +1357,144 @@ rm_status rm_align(rm_map *m, const rm_scan *scan, const double *init_pose,
   }
 }
 
+rm_status rm_dfo_align(rm_map *m, const rm_scan *scan, const double *init_pose,
+                       const rm_cost_params *prm, const rm_dfo_params *dp, double *pose_out,
+                       rm_dfo_report *rep, void *stream) {
+  if (!m) return fail(RM_EINVAL, "map is NULL");
+  if (!scan || !scan->depth || !scan->cls) return fail(RM_EINVAL, "scan or its arrays NULL");
+  if (!init_pose || !pose_out || !prm || !dp) return fail(RM_EINVAL, "NULL argument");
+  if (!(prm->eps >= 0.0f)) return fail(RM_EINVAL, "eps must be >= 0");
+  if (dp->nm_iters < 0 || dp->cd_iters < 0 || dp->nm_iters > 100000 || dp->cd_iters > 100000)
+    return fail(RM_EINVAL, "iteration counts out of range");
+  if (!(dp->scale_t > 0.0) || !(dp->scale_r > 0.0) || !(dp->nm_step > 0.0) || !(dp->cd_step > 0.0) ||
+      !(dp->nm_tol >= 0.0) || !(dp->cd_tol >= 0.0) || !std::isfinite(dp->scale_t) ||
+      !std::isfinite(dp->scale_r) || !std::isfinite(dp->nm_step) || !std::isfinite(dp->cd_step))
+    return fail(RM_EINVAL, "scales and steps must be finite and > 0, tolerances >= 0");
+  std::lock_guard<std::mutex> lk(m->mu);
+  cudaStream_t s = (cudaStream_t)stream;
+  const rm_intrinsics *in = &scan->intr;
+  RM_TRY(check_intr(in));
+  RM_CK(cudaSetDevice(m->device));
+  const long long P = (long long)in->width * in->height;
+  const bool host_scan = !on_device(scan->depth), host_cls = !on_device(scan->cls);
+  const bool host_rays = in->model == RM_RAYTABLE && !on_device(in->rays);
+  const int S = rmk::kDfoSlots;
+  for (int attempt = 0;; ++attempt) {
+    TileGeom tg = make_tiles(m, in);
+    Carver plan{nullptr};
+    plan.take<rmk::DfoState>(1);
+    if (host_rays) plan.take<float>(3 * P);
+    plan.take<double>(16);
+    plan.take<float>(12 * S);
+    plan.take<int>(1);
+    if (host_scan) plan.take<float>(P);
+    if (host_cls) plan.take<uint8_t>(P);
+    plan.take<long long>(6 * S);
+    plan.take<long long>(S);
+    plan.take<double>(S);
+    plan.take<int4>((size_t)m->n_clusters * S);
+    plan.take<int>(S);
+    plan.take<int>((size_t)tg.ntiles * S);
+    plan.take<unsigned char>((size_t)tg.ntiles * tg.cap * tg.rec_bytes * S);
+    plan.take<double>((size_t)tg.ntiles * rmk::kNumVals * S);
+    RM_TRY(ensure_arena(m, plan.off, s));
+    m->batch_inputs_valid = false;
+    Carver cv{m->arena};
+    rmk::DfoState *d_st = cv.take<rmk::DfoState>(1);
+    const float *d_rays = host_rays ? cv.take<float>(3 * P) : in->rays;
+    double *d_T0 = cv.take<double>(16);
+    float *d_M = cv.take<float>(12 * S);
+    int *d_skip = cv.take<int>(1);
+    const float *d_sd = host_scan ? cv.take<float>(P) : scan->depth;
+    const uint8_t *d_sc = host_cls ? cv.take<uint8_t>(P) : scan->cls;
+    long long *d_counts = cv.take<long long>(6 * S);
+    long long *d_et = cv.take<long long>(S);
+    double *d_els = cv.take<double>(S);
+    WaveArgs a{};
+    a.cam = make_cam(in, d_rays);
+    a.tg = tg;
+    a.V = (int)m->V;
+    a.T = m->T;
+    a.n_poses = S;
+    a.wave_base = 0;
+    a.v = m->d_v;
+    a.faces = m->d_faces;
+    a.planes = m->d_planes;
+    a.Ms = d_M;
+    set_clusters(m, a);
+    a.vis = cv.take<int4>((size_t)m->n_clusters * S);
+    a.vis_count = cv.take<int>(S);
+    a.counts = cv.take<int>((size_t)tg.ntiles * S);
+    a.bins = cv.take<unsigned char>((size_t)tg.ntiles * tg.cap * tg.rec_bytes * S);
+    a.partial = cv.take<double>((size_t)tg.ntiles * rmk::kNumVals * S);
+    a.status = m->d_status;
+    a.skip = d_skip;
+    a.scan_depth = d_sd;
+    a.scan_cls = d_sc;
+    a.prm = {prm->eps, prm->w_fofo, prm->w_fofu, prm->w_fufo};
+    a.res_counts = d_counts;
+    a.res_etable = d_et;
+    a.res_els = d_els;
+    RM_CK(cudaMemcpyAsync(d_T0, init_pose, sizeof(double) * 16,
+                          on_device(init_pose) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    if (host_rays) RM_CK(cudaMemcpyAsync((void *)d_rays, in->rays, sizeof(float) * 3 * P, cudaMemcpyHostToDevice, s));
+    if (host_scan) RM_CK(cudaMemcpyAsync((void *)d_sd, scan->depth, sizeof(float) * P, cudaMemcpyHostToDevice, s));
+    if (host_cls) RM_CK(cudaMemcpyAsync((void *)d_sc, scan->cls, P, cudaMemcpyHostToDevice, s));
+    rmk::DfoArgs da{};
+    da.nm_iters = dp->nm_iters;
+    da.cd_iters = dp->cd_iters;
+    da.nm_step = dp->nm_step;
+    da.nm_tol = dp->nm_tol;
+    da.cd_step = dp->cd_step;
+    da.cd_tol = dp->cd_tol;
+    for (int k = 0; k < 3; ++k) {
+      da.scale[k] = dp->scale_t;
+      da.scale[3 + k] = dp->scale_r;
+    }
+    da.cx = m->centre[0];
+    da.cy = m->centre[1];
+    da.cz = m->centre[2];
+    RM_CK(rmk::launch_dfo_init(d_st, d_T0, da, d_M, d_skip, s));
+    m->launches += 1;
+    // at most: the simplex, two batches per Nelder-Mead iteration, one per descent step
+    const int max_steps = 1 + 2 * dp->nm_iters + dp->cd_iters;
+    for (int it = 0; it < max_steps; ++it) {
+      RM_TRY(wave(m, a, rmk::kCost, s));
+      RM_CK(rmk::launch_dfo_step(d_st, da, d_et, d_M, d_skip, s));
+      m->launches += 1;
+    }
+    rmk::DfoState hs;
+    RM_CK(cudaMemcpyAsync(&hs, d_st, sizeof(hs), cudaMemcpyDeviceToHost, s));
+    unsigned stw = 0;
+    RM_TRY(read_status(m, s, &stw));  // synchronises the stream
+    if (stw & rmk::kStatusTimeout) return fail(RM_ETIMEOUT, "a device-side wait ran out of time");
+    if (stw & (rmk::kStatusOverflow | rmk::kStatusOverflowRay)) {
+      RM_TRY(grow_bins(m, stw, attempt));
+      continue;
+    }
+    // the final pose T0 exp(xc^) on the device, through the library's retraction
+    double *d_xi = reinterpret_cast<double *>(d_counts);  // 6 doubles of scratch
+    double *d_out = d_xi + 6;
+    RM_CK(cudaMemcpyAsync(d_xi, hs.xc, sizeof(double) * 6, cudaMemcpyHostToDevice, s));
+    RM_CK(rmk::launch_retract(d_T0, d_xi, 1, d_out, nullptr, s));
+    m->launches += 1;
+    RM_CK(cudaMemcpyAsync(pose_out, d_out, sizeof(double) * 16,
+                          on_device(pose_out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    RM_CK(cudaStreamSynchronize(s));
+    if (rep) {
+      rep->evals = hs.evals;
+      rep->nm_iters = hs.nm_iters;
+      rep->nm_shrinks = hs.nm_shrinks;
+      rep->cd_iters = hs.cd_iters;
+      rep->converged = hs.converged;
+      rep->reserved = 0;
+      rep->e_table_initial = (long long)hs.f_init;
+      rep->e_table_final = (long long)hs.fcur;
+    }
+    return hs.converged ? RM_OK : fail(RM_ENOTCONV, "coordinate descent ran out of iterations");
+  }
+}
+
 rm_status rm_icp_align(rm_map *m, const rm_scan *scan, const double *init_pose,
                        const rm_icp_params *prm, double *pose_out, rm_icp_report *rep,
                        void *stream) {

@@ -1251,7 +1251,10 @@ cudaError_t launch_wave(const WaveArgs &a, int mode, cudaStream_t s, cudaEvent_t
   }
   if (ev && (e = cudaEventRecord(ev[1], s)) != cudaSuccess) return e;
   if (a.n_clusters > 0) {
-    const int blocks = min(max(a.n_clusters / 64, 1), 96);
+    // up to 96 CTAs per pose; waves of few poses (single-pose alignment) get up to about six
+    // CTAs per SM in total so that their setup spreads over the GPU
+    const int per_pose = max(96, (kSetupCtasPerGpu + a.n_poses - 1) / a.n_poses);
+    const int blocks = min(max(a.n_clusters / 64, 1), per_pose);
     dim3 gs(blocks, a.n_poses);
     if (a.cam.model == 0) k_setup<0><<<gs, 256, 0, s>>>(a);
     else k_setup<1><<<gs, 256, 0, s>>>(a);
@@ -1584,6 +1587,175 @@ cudaError_t launch_icp_step(IcpState *st, const IcpArgs &a, const long long *n,
                             const double *l1, const double *g, const double *H, float *M,
                             int *skip, cudaStream_t s) {
   k_icp_step<<<1, 1, 0, s>>>(st, a, n, l1, g, H, M, skip);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ derivative-free search
+
+// Vertex order by value, ties by slot (stable insertion sort).
+__device__ void dfo_order(const double *f, int *o) {
+  for (int i = 0; i < 7; ++i) o[i] = i;
+  for (int i = 1; i < 7; ++i)
+    for (int j = i; j > 0 && f[o[j]] < f[o[j - 1]]; --j) {
+      const int t = o[j];
+      o[j] = o[j - 1];
+      o[j - 1] = t;
+    }
+}
+
+// Coordinate descent: converged, out of iterations, or the 12 moves +-step per axis.
+__device__ void dfo_next_cd(DfoState &s, const DfoArgs &a) {
+  if (s.cd_iters >= a.cd_iters) {
+    s.phase = 4;
+    return;
+  }
+  double smax = 0.0;
+  for (int k = 0; k < 6; ++k) smax = fmax(smax, s.st[k] / a.scale[k]);
+  if (smax < a.cd_tol) {
+    s.converged = 1;
+    s.phase = 4;
+    return;
+  }
+  for (int m = 0; m < 12; ++m)
+    for (int k = 0; k < 6; ++k)
+      s.cand[m][k] = s.xc[k] + (k == m / 2 ? (m % 2 ? -s.st[k] : s.st[k]) : 0.0);
+  s.n_cand = 12;
+  s.phase = 3;
+}
+
+// Next Nelder-Mead iteration (the four candidates), or the switch to coordinate descent.
+__device__ void dfo_next_nm(DfoState &s, const DfoArgs &a) {
+  int o[7];
+  dfo_order(s.f, o);
+  double diam = 0.0;
+  for (int i = 1; i < 7; ++i)
+    for (int k = 0; k < 6; ++k) diam = fmax(diam, fabs(s.x[o[i]][k] - s.x[o[0]][k]) / a.scale[k]);
+  if (s.nm_iters >= a.nm_iters || diam < a.nm_tol) {
+    for (int k = 0; k < 6; ++k) {
+      s.xc[k] = s.x[o[0]][k];
+      s.st[k] = a.cd_step * a.scale[k];
+    }
+    s.fcur = s.f[o[0]];
+    dfo_next_cd(s, a);
+    return;
+  }
+  const int h = o[6];
+  for (int k = 0; k < 6; ++k) {
+    double sum = 0.0;
+    for (int i = 0; i < 6; ++i) sum += s.x[o[i]][k];
+    const double c = sum / 6.0, d = c - s.x[h][k];
+    s.cand[0][k] = c + d;
+    s.cand[1][k] = c + 2.0 * d;
+    s.cand[2][k] = c + 0.5 * d;
+    s.cand[3][k] = c - 0.5 * d;
+  }
+  s.n_cand = 4;
+  s.phase = 1;
+}
+
+__device__ void dfo_write_candidates(DfoState &s, const DfoArgs &a, float *Ms) {
+  for (int m = 0; m < kDfoSlots; ++m) {
+    double T[16];
+    se3_right_dev(s.T0, s.cand[m < s.n_cand ? m : 0], T);
+    pose_to_m(T, a.cx, a.cy, a.cz, Ms + 12 * m);
+  }
+}
+
+__global__ void k_dfo_init(DfoState *st, const double *T0, DfoArgs a, float *Ms, int *skip) {
+  DfoState &s = *st;
+  for (int k = 0; k < 16; ++k) s.T0[k] = T0[k];
+  for (int i = 0; i < 7; ++i)
+    for (int k = 0; k < 6; ++k) s.cand[i][k] = (i >= 1 && k == i - 1) ? a.nm_step * a.scale[k] : 0.0;
+  s.n_cand = 7;
+  s.phase = 0;
+  s.evals = s.nm_iters = s.nm_shrinks = s.cd_iters = s.converged = s.shrink_best = 0;
+  dfo_write_candidates(s, a, Ms);
+  *skip = 0;
+}
+
+__global__ void k_dfo_step(DfoState *st, DfoArgs a, const long long *et, float *Ms, int *skip) {
+  DfoState &s = *st;
+  if (s.phase == 4) {
+    *skip = 1;
+    return;
+  }
+  double fc[kDfoSlots];
+  for (int m = 0; m < s.n_cand; ++m) fc[m] = (double)et[m];
+  s.evals += s.n_cand;
+  if (s.phase == 0) {
+    s.f_init = fc[0];
+    for (int i = 0; i < 7; ++i) {
+      for (int k = 0; k < 6; ++k) s.x[i][k] = s.cand[i][k];
+      s.f[i] = fc[i];
+    }
+    dfo_next_nm(s, a);
+  } else if (s.phase == 1) {
+    s.nm_iters += 1;
+    int o[7];
+    dfo_order(s.f, o);
+    const int h = o[6];
+    const double fb = s.f[o[0]], fs = s.f[o[5]], fh = s.f[h];
+    int take;
+    if (fc[0] < fb) take = fc[1] < fc[0] ? 1 : 0;
+    else if (fc[0] < fs) take = 0;
+    else if (fc[0] < fh) take = fc[2] <= fc[0] ? 2 : -1;
+    else take = fc[3] < fh ? 3 : -1;
+    if (take >= 0) {
+      for (int k = 0; k < 6; ++k) s.x[h][k] = s.cand[take][k];
+      s.f[h] = fc[take];
+      dfo_next_nm(s, a);
+    } else {
+      const int b = o[0];
+      int m = 0;
+      for (int i = 0; i < 7; ++i) {
+        if (i == b) continue;
+        for (int k = 0; k < 6; ++k) s.cand[m][k] = s.x[b][k] + 0.5 * (s.x[i][k] - s.x[b][k]);
+        ++m;
+      }
+      s.shrink_best = b;
+      s.n_cand = 6;
+      s.phase = 2;
+    }
+  } else if (s.phase == 2) {
+    s.nm_shrinks += 1;
+    int m = 0;
+    for (int i = 0; i < 7; ++i) {
+      if (i == s.shrink_best) continue;
+      for (int k = 0; k < 6; ++k) s.x[i][k] = s.cand[m][k];
+      s.f[i] = fc[m];
+      ++m;
+    }
+    dfo_next_nm(s, a);
+  } else {
+    s.cd_iters += 1;
+    int best = 0;
+    for (int m = 1; m < 12; ++m)
+      if (fc[m] < fc[best]) best = m;
+    if (fc[best] < s.fcur) {
+      for (int k = 0; k < 6; ++k) s.xc[k] = s.cand[best][k];
+      s.fcur = fc[best];
+    } else {
+      for (int k = 0; k < 6; ++k) s.st[k] *= 0.5;
+    }
+    dfo_next_cd(s, a);
+  }
+  if (s.phase == 4) {
+    *skip = 1;
+    return;
+  }
+  dfo_write_candidates(s, a, Ms);
+  *skip = 0;
+}
+
+cudaError_t launch_dfo_init(DfoState *st, const double *T0, const DfoArgs &a, float *Ms,
+                            int *skip, cudaStream_t s) {
+  k_dfo_init<<<1, 1, 0, s>>>(st, T0, a, Ms, skip);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dfo_step(DfoState *st, const DfoArgs &a, const long long *e_table, float *Ms,
+                            int *skip, cudaStream_t s) {
+  k_dfo_step<<<1, 1, 0, s>>>(st, a, e_table, Ms, skip);
   return cudaGetLastError();
 }
 

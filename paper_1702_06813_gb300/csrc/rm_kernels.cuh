@@ -114,6 +114,35 @@ cudaError_t launch_icp_step(IcpState *st, const IcpArgs &a, const long long *n,
                             const double *l1, const double *g, const double *H, float *M,
                             int *skip, cudaStream_t s);
 
+// Derivative-free search state on the device (one pose): Nelder-Mead over scaled twists,
+// then coordinate descent, on the Table I cost of T0 exp(xi^); candidates are evaluated as
+// one wave of kDfoSlots poses.
+constexpr int kDfoSlots = 12;
+struct DfoState {
+  double T0[16];
+  double x[7][6], f[7];       // simplex vertices and values
+  double cand[kDfoSlots][6];  // candidates of the pending evaluation
+  double xc[6], fcur, st[6];  // coordinate descent: point, value, steps
+  double f_init;              // the cost at the start pose
+  int phase;                  // 0 simplex, 1 NM step, 2 NM shrink, 3 coordinate step, 4 done
+  int n_cand;
+  int evals, nm_iters, nm_shrinks, cd_iters, converged, shrink_best;
+};
+
+struct DfoArgs {
+  int nm_iters, cd_iters;
+  double nm_step, nm_tol, cd_step, cd_tol;
+  double scale[6];
+  double cx, cy, cz;  // map centre
+};
+
+cudaError_t launch_dfo_init(DfoState *st, const double *T0, const DfoArgs &a, float *Ms,
+                            int *skip, cudaStream_t s);
+// Takes the Table I costs of the pending candidates (e_table per slot), advances the search
+// and writes the next candidates' matrices, or sets *skip when the search is over.
+cudaError_t launch_dfo_step(DfoState *st, const DfoArgs &a, const long long *e_table, float *Ms,
+                            int *skip, cudaStream_t s);
+
 // Batch of problems (each its own camera, scan and scratch) run by one persistent kernel.
 constexpr int kPersistCull = 4;   // 256-cluster chunks per cull item
 // Persistent kernel screen tiles: pinhole problems use 64x32 tiles, one per raster item;
@@ -145,6 +174,7 @@ struct BatchArgs {
 };
 
 constexpr int kSetupClusters = 64;  // visible clusters per setup item (eight per warp)
+constexpr int kSetupCtasPerGpu = 912;  // setup CTAs a small wave may spread over (152 SMs x 6)
 
 // Every slot unpublished except the evaluation-0 cull items of every problem at the head of
 // the cull/setup queue; sets that queue's tail.

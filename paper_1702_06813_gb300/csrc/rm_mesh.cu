@@ -30,7 +30,8 @@ struct MeshArgs {
   const float *rays;
   const float *depth;
   const uint8_t *cls;
-  double T[12];         // camera-to-world rows (R | t)
+  double T[12];         // camera-to-world rows (R | t) of a host pose
+  const double *Tdev;   // or the pose in device memory (16 doubles)
   float max_range, lim;  // lim = max_edge^2 (FP32)
   float *vertices;
   float4 *pc;           // camera-frame points
@@ -69,7 +70,7 @@ __global__ void __launch_bounds__(256) k_mesh_points(MeshArgs a) {
   a.pc[v] = make_float4(px, py, pz, 0.0f);
   a.kind[v] = (uint8_t)k;
   for (int q = 0; q < 3; ++q) {
-    const double *m = a.T + 4 * q;
+    const double *m = (a.Tdev ? a.Tdev : a.T) + 4 * q;
     double w = m[3];  // dead pixels stay at the sensor origin (unreferenced)
     if (k != 2)
       w = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(m[0], (double)px), __dmul_rn(m[1], (double)py)),
@@ -192,16 +193,12 @@ extern "C" rm_status rm_meshify(const rm_scan *scan, const double *pose,
   if (!(prm->max_edge >= 0.0f) || !(prm->max_edge <= FLT_MAX))
     return mf_fail(RM_EINVAL, "max_edge must be finite and >= 0");
   cudaStream_t s = (cudaStream_t)stream;
-  double T[16];  // the pose on the host (it may live in device memory)
-  if (rmapi::is_device_pointer(pose)) {
-    cudaError_t e0 = cudaMemcpyAsync(T, pose, sizeof(T), cudaMemcpyDeviceToHost, s);
-    if (e0 == cudaSuccess) e0 = cudaStreamSynchronize(s);
-    if (e0 != cudaSuccess) return mf_fail(RM_ECUDA, std::string("rm_meshify: ") + cudaGetErrorString(e0));
-  } else {
-    for (int k = 0; k < 16; ++k) T[k] = pose[k];
-  }
-  for (int k = 0; k < 12; ++k)
-    if (!std::isfinite(T[k])) return mf_fail(RM_EINVAL, "pose must be finite");
+  // a host pose is checked here and passed by value; a device pose is read by the kernel in
+  // place (no host round trip; a non-finite one gives non-finite vertices)
+  const bool dev_pose = rmapi::is_device_pointer(pose);
+  if (!dev_pose)
+    for (int k = 0; k < 12; ++k)
+      if (!std::isfinite(pose[k])) return mf_fail(RM_EINVAL, "pose must be finite");
   const rm_intrinsics &in = scan->intr;
   const int Ws = (in.width - 1) / prm->step + 1, Hs = (in.height - 1) / prm->step + 1;
   const long long NV = (long long)Ws * Hs, NQ = (long long)(Ws - 1) * (Hs - 1);
@@ -249,7 +246,8 @@ extern "C" rm_status rm_meshify(const rm_scan *scan, const double *pose,
   a.depth = host_d ? reinterpret_cast<float *>(buf + o_d) : scan->depth;
   a.cls = host_c ? buf + o_c : scan->cls;
   a.rays = host_r ? reinterpret_cast<float *>(buf + o_r) : in.rays;
-  for (int k = 0; k < 12; ++k) a.T[k] = T[k];
+  for (int k = 0; k < 12; ++k) a.T[k] = dev_pose ? 0.0 : pose[k];
+  a.Tdev = dev_pose ? pose : nullptr;
   a.max_range = prm->max_range;
   a.lim = prm->max_edge * prm->max_edge;
   a.vertices = host_v ? reinterpret_cast<float *>(buf + o_v) : vertices;

@@ -1,9 +1,11 @@
 // rm_normals.cu -- rm_depth_normals: surface normals of depth images (Eq. 2, Sec. IV).
 //
-// One CTA per (32x16 output tile, image), fused: the tile's depths with a halo of r + 1
-// pixels are staged in shared memory (invalid pixels as NaN), smoothed with the separable
-// Gaussian as a normalised convolution (a horizontal pass of weighted sums and weight sums,
-// then a vertical pass), and the smoothed depth S over the tile plus a one-pixel ring feeds
+// One CTA per (64x16 output tile, image), fused: the tile's depths with a halo of r + 1
+// pixels are staged in shared memory as (depth, validity) pairs (invalid pixels contribute
+// neither), smoothed with the separable Gaussian as a normalised convolution (a horizontal
+// pass of weighted sums and weight sums, then a vertical pass; one instantiation per radius,
+// so the taps unroll with their weights in registers), and the smoothed depth S over the
+// tile plus a one-pixel ring feeds
 // the central differences and the normal N = a x b with a = (0, s_y, dz/dy) and
 // b = (s_x, 0, dz/dx). Each depth and class byte is read once from HBM and each normal
 // written once (17 bytes per pixel); the kernel is bound by HBM bandwidth.
@@ -16,12 +18,11 @@
 
 namespace {
 
-constexpr int kTW = 32, kTH = 16;      // output tile
+constexpr int kTW = 64, kTH = 16;      // output tile
 constexpr int kMaxR = 16;              // Gaussian radius ceil(3 sigma) for sigma <= 5
 constexpr int kSW = kTW + 2;           // smoothed region (tile plus a one-pixel ring)
 constexpr int kSH = kTH + 2;
-constexpr int kDW = kSW + 2 * kMaxR;   // staged depth region
-constexpr int kDH = kSH + 2 * kMaxR;
+constexpr int kThreadsN = 256;
 
 struct NormalArgs {
   const float *depth;
@@ -33,76 +34,106 @@ struct NormalArgs {
   float g[kMaxR + 1];
 };
 
-__global__ void __launch_bounds__(256) k_depth_normals(NormalArgs a) {
-  __shared__ float sz[kDH][kDW + 1];
-  __shared__ float snum[kDH][kSW];
-  __shared__ float sden[kDH][kSW];
-  __shared__ float sS[kSH][kSW];
-  __shared__ float sg[kMaxR + 1];
+// Dynamic shared memory: the staged (depth, validity) pairs of the tile plus its halo, the
+// horizontal sums (weighted depth, weight) of each staged row over the smoothed columns, and
+// the smoothed depth S of the tile plus a one-pixel ring.
+__host__ __device__ inline int staged_w(int r) { return kSW + 2 * r; }
+__host__ __device__ inline int staged_h(int r) { return kSH + 2 * r; }
+inline size_t normals_smem(int r) {
+  return sizeof(float2) * ((size_t)staged_h(r) * staged_w(r) + (size_t)staged_h(r) * kSW) +
+         sizeof(float) * kSH * kSW;
+}
+
+template <int R>
+__global__ void __launch_bounds__(kThreadsN) k_depth_normals(NormalArgs a) {
+  extern __shared__ float4 smem_raw[];
+  constexpr int dw = kSW + 2 * R, dh = kSH + 2 * R;
+  float2 *sz = reinterpret_cast<float2 *>(smem_raw);  // [dh][dw]: (valid ? z : 0, valid)
+  float2 *sh = sz + dh * dw;                           // [dh][kSW]
+  float *sS = reinterpret_cast<float *>(sh + dh * kSW); // [kSH][kSW]
   const int tid = threadIdx.x;
-  if (tid <= kMaxR) sg[tid] = a.g[tid];
+  float g[R + 1];
+#pragma unroll
+  for (int k = 0; k <= R; ++k) g[k] = a.g[k];
   const int img = blockIdx.y;
   const int ntx = (a.W + kTW - 1) / kTW;
   const int ox = (blockIdx.x % ntx) * kTW, oy = (blockIdx.x / ntx) * kTH;
-  const int r = a.r;
-  const int dw = kSW + 2 * r, dh = kSH + 2 * r;  // staged region actually used
-  const int x0 = ox - 1 - r, y0 = oy - 1 - r;    // image coordinates of sz[0][0]
+  const int x0 = ox - 1 - R, y0 = oy - 1 - R;  // image coordinates of sz[0][0]
   const long long P = (long long)a.W * a.H;
   const float *dimg = a.depth + img * P;
   const uint8_t *cimg = a.cls + img * P;
-  for (int k = tid; k < dw * dh; k += blockDim.x) {
-    const int u = k % dw, v = k / dw;
-    const int x = x0 + u, y = y0 + v;
-    float z = __int_as_float(0x7fc00000);
-    if (x >= 0 && x < a.W && y >= 0 && y < a.H) {
-      const long long p = (long long)y * a.W + x;
-      const float d = dimg[p];
-      if (cimg[p] == 0 && fabsf(d) <= FLT_MAX) z = d;
+  constexpr int n_st = dw * dh;
+  // stage: independent loads, four per thread in flight
+  for (int k0 = tid; k0 < n_st; k0 += 4 * kThreadsN) {
+    float dv[4];
+    int cv[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int k = k0 + m * kThreadsN;
+      dv[m] = 0.0f;
+      cv[m] = 1;
+      if (k < n_st) {
+        const int x = x0 + k % dw, y = y0 + k / dw;
+        if (x >= 0 && x < a.W && y >= 0 && y < a.H) {
+          const long long p = (long long)y * a.W + x;
+          dv[m] = __ldg(dimg + p);
+          cv[m] = __ldg(cimg + p);
+        }
+      }
     }
-    sz[v][u] = z;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int k = k0 + m * kThreadsN;
+      if (k < n_st) {
+        const bool ok = cv[m] == 0 && fabsf(dv[m]) <= FLT_MAX;
+        sz[k] = ok ? make_float2(dv[m], 1.0f) : make_float2(0.0f, 0.0f);
+      }
+    }
   }
   __syncthreads();
   // horizontal pass: weighted sums of the valid depths and of their weights
-  for (int k = tid; k < dh * kSW; k += blockDim.x) {
-    const int u = k % kSW, v = k / kSW;
+  for (int k = tid; k < dh * kSW; k += kThreadsN) {
+    const int v = k / kSW, u = k % kSW;
+    const float2 *row = sz + v * dw + u;  // output u: staged columns u .. u + 2R
     float num = 0.0f, den = 0.0f;
-    for (int dx = -r; dx <= r; ++dx) {
-      const float z = sz[v][u + r + dx];
-      if (!isnan(z)) {
-        const float w = sg[abs(dx)];
-        num = fmaf(w, z, num);
-        den += w;
-      }
+#pragma unroll
+    for (int t = 0; t <= 2 * R; ++t) {
+      const float2 zv = row[t];
+      const float w = g[t < R ? R - t : t - R];
+      num = fmaf(w, zv.x, num);
+      den = fmaf(w, zv.y, den);
     }
-    snum[v][u] = num;
-    sden[v][u] = den;
+    sh[k] = make_float2(num, den);
   }
   __syncthreads();
   // vertical pass: the smoothed depth where the centre pixel is valid
-  for (int k = tid; k < kSH * kSW; k += blockDim.x) {
-    const int u = k % kSW, v = k / kSW;
+  for (int k = tid; k < kSH * kSW; k += kThreadsN) {
+    const int v = k / kSW, u = k % kSW;
     float s = __int_as_float(0x7fc00000);
-    if (!isnan(sz[v + r][u + r])) {
+    if (sz[(v + R) * dw + (u + R)].y != 0.0f) {
       float num = 0.0f, den = 0.0f;
-      for (int dy = -r; dy <= r; ++dy) {
-        const float w = sg[abs(dy)];
-        num = fmaf(w, snum[v + r + dy][u], num);
-        den = fmaf(w, sden[v + r + dy][u], den);
+#pragma unroll
+      for (int t = 0; t <= 2 * R; ++t) {
+        const float2 hv = sh[(v + t) * kSW + u];
+        const float w = g[t < R ? R - t : t - R];
+        num = fmaf(w, hv.x, num);
+        den = fmaf(w, hv.y, den);
       }
       s = num / den;
     }
-    sS[v][u] = s;
+    sS[k] = s;
   }
   __syncthreads();
-  for (int k = tid; k < kTW * kTH; k += blockDim.x) {
+  for (int k = tid; k < kTW * kTH; k += kThreadsN) {
     const int u = k % kTW + 1, v = k / kTW + 1;
     const int x = ox + u - 1, y = oy + v - 1;
     if (x >= a.W || y >= a.H) continue;
     const long long p = img * P + (long long)y * a.W + x;
-    const float s = sS[v][u];
+    const float s = sS[v * kSW + u];
     if (a.smoothed) a.smoothed[p] = s;
     float n0 = __int_as_float(0x7fc00000), n1 = n0, n2 = n0;
-    const float sl = sS[v][u - 1], sr = sS[v][u + 1], su = sS[v - 1][u], sd = sS[v + 1][u];
+    const float sl = sS[v * kSW + u - 1], sr = sS[v * kSW + u + 1];
+    const float su = sS[(v - 1) * kSW + u], sd = sS[(v + 1) * kSW + u];
     if (x >= 1 && x + 1 < a.W && y >= 1 && y + 1 < a.H && !isnan(s) && !isnan(sl) && !isnan(sr) &&
         !isnan(su) && !isnan(sd)) {
       const float zx = 0.5f * (sr - sl), zy = 0.5f * (sd - su);
@@ -118,6 +149,23 @@ __global__ void __launch_bounds__(256) k_depth_normals(NormalArgs a) {
     a.normals[3 * p + 1] = n1;
     a.normals[3 * p + 2] = n2;
   }
+}
+
+template <int R>
+cudaError_t launch_normals_r(const NormalArgs &a, int tiles, int n, cudaStream_t s) {
+  const size_t sm = normals_smem(R);
+  // radii above about 7 need more than the default 48 KB (set on the current device)
+  cudaError_t e = cudaFuncSetAttribute(k_depth_normals<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k_depth_normals<R><<<dim3(tiles, n), kThreadsN, sm, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int R>
+cudaError_t launch_normals(const NormalArgs &a, int tiles, int n, cudaStream_t s) {
+  if (a.r == R) return launch_normals_r<R>(a, tiles, n, s);
+  if constexpr (R < kMaxR) return launch_normals<R + 1>(a, tiles, n, s);
+  return cudaErrorInvalidValue;
 }
 
 bool dn_on_device(const void *p) {
@@ -185,8 +233,7 @@ extern "C" rm_status rm_depth_normals(const rm_intrinsics *intr, int32_t n, cons
     for (int k = 0; k <= kMaxR; ++k)
       a.g[k] = sigma > 0.0f ? (float)std::exp(-(double)(k * k) / (2.0 * (double)sigma * sigma)) : 1.0f;
     const int tiles = ((a.W + kTW - 1) / kTW) * ((a.H + kTH - 1) / kTH);
-    k_depth_normals<<<dim3(tiles, n), 256, 0, s>>>(a);
-    ck(cudaGetLastError());
+    ck(launch_normals<0>(a, tiles, n, s));
   }
   if (e == cudaSuccess && host_n) ck(cudaMemcpyAsync(normals, d_n, sizeof(float) * 3 * np, cudaMemcpyDeviceToHost, s));
   if (e == cudaSuccess && host_s) ck(cudaMemcpyAsync(smoothed, d_s, sizeof(float) * np, cudaMemcpyDeviceToHost, s));

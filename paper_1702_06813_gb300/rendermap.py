@@ -245,6 +245,56 @@ def align(m: Map, scan: Scan, init_pose, params=None, max_iters=50, lambda0=1e-3
     return out.reshape(4, 4), report
 
 
+def dfo_params(nm_iters=60, cd_iters=60, nm_step=1.0, nm_tol=0.05, cd_step=0.25, cd_tol=0.01,
+               scale_t=0.05, scale_r=0.0349) -> N.rm_dfo_params:
+    """Nelder-Mead / coordinate-descent settings; scales: 5 cm and 2 deg per unit."""
+    return N.rm_dfo_params(nm_iters, cd_iters, nm_step, nm_tol, cd_step, cd_tol, scale_t, scale_r)
+
+
+def dfo_align(m: Map, scan: Scan, init_pose, params=None, dfo=None, gd_iters=0):
+    """The paper's hybrid derivative-free alignment on the Table I cost (Sec. III.C): optional
+    initial gradient steps (Levenberg-Marquardt on the surrogate), then Nelder-Mead and
+    coordinate descent, all on the device. Returns (pose 4x4 float64 numpy, report)."""
+    start = init_pose
+    gd = None
+    if gd_iters > 0:
+        start, gd = align(m, scan, init_pose, params=params, max_iters=gd_iters)
+    p, _ = _poses(start)
+    out = np.empty(16)
+    rep = N.rm_dfo_report()
+    prm = params if params is not None else _DEFAULT_PARAMS
+    d = dfo if dfo is not None else dfo_params()
+    cs = scan.c()
+    st = lib().rm_dfo_align(m.handle, ctypes.byref(cs), _ptr(p), ctypes.byref(prm), ctypes.byref(d),
+                            out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(rep), _stream())
+    if st not in (N.RM_OK, N.RM_ENOTCONV):
+        check(st)
+    report = {f: getattr(rep, f) for f, _ in N.rm_dfo_report._fields_ if f != "reserved"}
+    report["status"] = N.STATUS_NAMES[st]
+    if gd is not None:
+        report["gd"] = gd
+    return out.reshape(4, 4), report
+
+
+def scan_from_range(intr: Intrinsics, rng, range_min, range_max) -> Scan:
+    """A Scan from raw range images by the paper's rules: no reading -> FU at range_max,
+    NaN or closer than range_min -> dead (Sec. III.A, III.B)."""
+    r = _dev_tensor(rng, torch.float32)
+    d = torch.empty_like(r)
+    c = torch.empty(r.shape, dtype=torch.uint8, device="cuda")
+    check(lib().rm_scan_from_range(_ptr(r), r.numel(), float(range_min), float(range_max), _ptr(d), _ptr(c),
+                                   _stream()))
+    return Scan(intr, d, c)
+
+
+def pose_from_x(X):
+    """(N, 4, 4) camera-to-world poses of X = (x, y, z, theta_x, theta_y, theta_z), R = Rz Ry Rx."""
+    x = _dev_tensor(X, torch.float64).reshape(-1, 6)
+    out = torch.empty((x.shape[0], 16), dtype=torch.float64, device="cuda")
+    check(lib().rm_pose_from_x(_ptr(x), x.shape[0], _ptr(out), _stream()))
+    return out.reshape(-1, 4, 4)
+
+
 def icp_terms(m: Map, scan: Scan, poses, tol=0.1):
     """Point-to-plane ICP terms with projective association (Sec. IV) for each pose:
     n_assoc (N,) int64, cost_l1 = C (N,), e2 (N,), jte (N,6) and jtj (N,21) float64."""
