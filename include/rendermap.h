@@ -276,6 +276,13 @@ rm_status rm_depth_normals(const rm_intrinsics *intr, int32_t n_images, const fl
                            const uint8_t *cls, float sigma, int32_t metric, float *normals,
                            float *smoothed, void *stream);
 
+/* Gaussian blur of depth images for cost smoothing (Sec. III.C): the smoothing above alone.
+ * out (n*H*W float, host or device) holds each FO return's smoothed depth and every other
+ * pixel's input depth unchanged (FU pixels stay at their maximal range, dead pixels NaN), so
+ * the result pairs with the same class image as a scan. Errors as rm_depth_normals. */
+rm_status rm_depth_blur(const rm_intrinsics *intr, int32_t n_images, const float *depth,
+                        const uint8_t *cls, float sigma, float *out, void *stream);
+
 /* ---- Derivative-free search on the Table I cost (Sec. III.C) ---------------------------
  * The paper minimises its piecewise-constant cost with Nelder-Mead and coordinate descent.
  * Here both run on the device over twists xi of the start pose (pose = T0 exp(xi^)), scaled

@@ -282,6 +282,15 @@ def pose_from_x(X):
     return T.reshape(4, 4)
 
 
+def depth_blur(depth, cls, sigma=1.0):
+    """Cost smoothing: FO returns get their Eq. 2 smoothed depth, other pixels keep theirs."""
+    _, s = depth_normals(depth, cls, sigma=sigma)
+    d = np.array(depth, np.float32, copy=True)
+    ok = ~np.isnan(s)
+    d[ok] = s[ok]
+    return d, s
+
+
 class OracleMap:
     """The oracle's copy of a labelled triangle-mesh map (Sec. III.A)."""
 

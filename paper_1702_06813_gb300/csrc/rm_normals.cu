@@ -29,6 +29,7 @@ struct NormalArgs {
   const uint8_t *cls;
   float *normals;
   float *smoothed;   // optional
+  float *blur;       // optional: S where valid, else the input depth
   int W, H, r, metric;
   float fx, fy;
   float g[kMaxR + 1];
@@ -131,6 +132,8 @@ __global__ void __launch_bounds__(kThreadsN) k_depth_normals(NormalArgs a) {
     const long long p = img * P + (long long)y * a.W + x;
     const float s = sS[v * kSW + u];
     if (a.smoothed) a.smoothed[p] = s;
+    if (a.blur) a.blur[p] = isnan(s) ? a.depth[p] : s;
+    if (!a.normals) continue;
     float n0 = __int_as_float(0x7fc00000), n1 = n0, n2 = n0;
     const float sl = sS[v * kSW + u - 1], sr = sS[v * kSW + u + 1];
     const float su = sS[(v - 1) * kSW + u], sd = sS[(v + 1) * kSW + u];
@@ -183,11 +186,10 @@ rm_status dn_fail(rm_status s, const std::string &m) {
   return s;
 }
 
-}  // namespace
-
-extern "C" rm_status rm_depth_normals(const rm_intrinsics *intr, int32_t n, const float *depth,
-                                      const uint8_t *cls, float sigma, int32_t metric,
-                                      float *normals, float *smoothed, void *stream) {
+// Shared driver of rm_depth_normals and rm_depth_blur; any of the three outputs may be NULL.
+rm_status run_normals(const rm_intrinsics *intr, int32_t n, const float *depth, const uint8_t *cls,
+                      float sigma, int32_t metric, float *normals, float *smoothed, float *blur,
+                      void *stream) {
   if (!intr) return dn_fail(RM_EINVAL, "intrinsics are NULL");
   if (n < 0 || intr->width < 0 || intr->height < 0) return dn_fail(RM_EINVAL, "negative size");
   if (!(sigma >= 0.0f) || sigma > 5.0f) return dn_fail(RM_EINVAL, "sigma must be in [0, 5]");
@@ -197,16 +199,18 @@ extern "C" rm_status rm_depth_normals(const rm_intrinsics *intr, int32_t n, cons
     return dn_fail(RM_EINVAL, "metric normals need a pinhole camera with finite fx, fy > 0");
   const long long P = (long long)intr->width * intr->height;
   if (n == 0 || P == 0) return RM_OK;
-  if (!depth || !cls || !normals) return dn_fail(RM_EINVAL, "NULL array");
+  if (!depth || !cls) return dn_fail(RM_EINVAL, "NULL array");
   if ((long long)n * P > (1LL << 40)) return dn_fail(RM_EINVAL, "too many pixels");
   cudaStream_t s = (cudaStream_t)stream;
   const bool host_d = !dn_on_device(depth), host_c = !dn_on_device(cls);
-  const bool host_n = !dn_on_device(normals), host_s = smoothed && !dn_on_device(smoothed);
+  const bool host_n = normals && !dn_on_device(normals), host_s = smoothed && !dn_on_device(smoothed);
+  const bool host_b = blur && !dn_on_device(blur);
   const size_t np = (size_t)n * P;
   // host arrays are staged through stream-ordered device allocations
   float *d_d = host_d ? nullptr : const_cast<float *>(depth);
   float *d_n = host_n ? nullptr : normals;
   float *d_s = host_s ? nullptr : smoothed;
+  float *d_b = host_b ? nullptr : blur;
   uint8_t *d_c = host_c ? nullptr : const_cast<uint8_t *>(cls);
   cudaError_t e = cudaSuccess;
   auto ck = [&](cudaError_t x) {
@@ -216,6 +220,7 @@ extern "C" rm_status rm_depth_normals(const rm_intrinsics *intr, int32_t n, cons
   if (host_c) ck(cudaMallocAsync((void **)&d_c, np, s));
   if (host_n) ck(cudaMallocAsync((void **)&d_n, sizeof(float) * 3 * np, s));
   if (host_s) ck(cudaMallocAsync((void **)&d_s, sizeof(float) * np, s));
+  if (host_b) ck(cudaMallocAsync((void **)&d_b, sizeof(float) * np, s));
   if (e == cudaSuccess && host_d) ck(cudaMemcpyAsync(d_d, depth, sizeof(float) * np, cudaMemcpyHostToDevice, s));
   if (e == cudaSuccess && host_c) ck(cudaMemcpyAsync(d_c, cls, np, cudaMemcpyHostToDevice, s));
   if (e == cudaSuccess) {
@@ -224,6 +229,7 @@ extern "C" rm_status rm_depth_normals(const rm_intrinsics *intr, int32_t n, cons
     a.cls = d_c;
     a.normals = d_n;
     a.smoothed = d_s;
+    a.blur = d_b;
     a.W = intr->width;
     a.H = intr->height;
     a.r = sigma > 0.0f ? (int)std::ceil(3.0 * (double)sigma) : 0;
@@ -237,11 +243,28 @@ extern "C" rm_status rm_depth_normals(const rm_intrinsics *intr, int32_t n, cons
   }
   if (e == cudaSuccess && host_n) ck(cudaMemcpyAsync(normals, d_n, sizeof(float) * 3 * np, cudaMemcpyDeviceToHost, s));
   if (e == cudaSuccess && host_s) ck(cudaMemcpyAsync(smoothed, d_s, sizeof(float) * np, cudaMemcpyDeviceToHost, s));
+  if (e == cudaSuccess && host_b) ck(cudaMemcpyAsync(blur, d_b, sizeof(float) * np, cudaMemcpyDeviceToHost, s));
   if (host_d && d_d) cudaFreeAsync(d_d, s);
   if (host_c && d_c) cudaFreeAsync(d_c, s);
   if (host_n && d_n) cudaFreeAsync(d_n, s);
   if (host_s && d_s) cudaFreeAsync(d_s, s);
-  if (e == cudaSuccess && (host_n || host_s)) ck(cudaStreamSynchronize(s));
+  if (host_b && d_b) cudaFreeAsync(d_b, s);
+  if (e == cudaSuccess && (host_n || host_s || host_b)) ck(cudaStreamSynchronize(s));
   if (e != cudaSuccess) return dn_fail(RM_ECUDA, std::string("rm_depth_normals: ") + cudaGetErrorString(e));
   return RM_OK;
+}
+
+}  // namespace
+
+extern "C" rm_status rm_depth_normals(const rm_intrinsics *intr, int32_t n, const float *depth,
+                                      const uint8_t *cls, float sigma, int32_t metric,
+                                      float *normals, float *smoothed, void *stream) {
+  if (!normals && n > 0) return dn_fail(RM_EINVAL, "normals is NULL");
+  return run_normals(intr, n, depth, cls, sigma, metric, normals, smoothed, nullptr, stream);
+}
+
+extern "C" rm_status rm_depth_blur(const rm_intrinsics *intr, int32_t n, const float *depth,
+                                   const uint8_t *cls, float sigma, float *out, void *stream) {
+  if (!out && n > 0) return dn_fail(RM_EINVAL, "out is NULL");
+  return run_normals(intr, n, depth, cls, sigma, 0, nullptr, nullptr, out, stream);
 }

@@ -245,6 +245,17 @@ def align(m: Map, scan: Scan, init_pose, params=None, max_iters=50, lambda0=1e-3
     return out.reshape(4, 4), report
 
 
+def blur_scan(scan: Scan, sigma=1.0) -> Scan:
+    """The scan with its FO returns' depths Gaussian-smoothed (sigma pixels, over FO returns
+    only) and every other pixel unchanged: cost smoothing (Sec. III.C)."""
+    intr = scan.intr
+    out = torch.empty_like(scan.depth)
+    ci = intr.c()
+    check(lib().rm_depth_blur(ctypes.byref(ci), 1, _ptr(scan.depth), _ptr(scan.cls), float(sigma), _ptr(out),
+                              _stream()))
+    return Scan(intr, out, scan.cls)
+
+
 def dfo_params(nm_iters=60, cd_iters=60, nm_step=1.0, nm_tol=0.05, cd_step=0.25, cd_tol=0.01,
                scale_t=0.05, scale_r=0.0349) -> N.rm_dfo_params:
     """Nelder-Mead / coordinate-descent settings; scales: 5 cm and 2 deg per unit."""

@@ -51,6 +51,7 @@ def test_argument_errors_without_gpu(lib):
     assert lib.rm_icp_terms(None, None, None, 0, 0.1, None, None) == N.RM_EINVAL
     assert lib.rm_icp_align(None, None, None, None, None, None, None) == N.RM_EINVAL
     assert lib.rm_meshify(None, None, None, None, None, None, None, None) == N.RM_EINVAL
+    assert lib.rm_dfo_align(None, None, None, None, None, None, None, None) == N.RM_EINVAL
     assert lib.rm_depth_normals(None, 1, None, None, 1.0, 0, None, None, None) == N.RM_EINVAL
 
 
@@ -68,7 +69,7 @@ int main(void) {
          offsetof(rm_intrinsics, rays), sizeof(rm_scan), sizeof(rm_cost_params), sizeof(rm_cost_out),
          sizeof(rm_tuning), sizeof(rm_align_params), sizeof(rm_align_report), sizeof(rm_icp_out),
          sizeof(rm_icp_params), sizeof(rm_icp_report), offsetof(rm_icp_report, n_assoc));
-  printf("%zu\n", sizeof(rm_meshify_params));
+  printf("%zu %zu %zu\n", sizeof(rm_meshify_params), sizeof(rm_dfo_params), sizeof(rm_dfo_report));
   return 0;
 }'''
     with tempfile.TemporaryDirectory() as d:
@@ -81,5 +82,6 @@ int main(void) {
             ctypes.sizeof(N.rm_cost_params), ctypes.sizeof(N.rm_cost_out), ctypes.sizeof(N.rm_tuning),
             ctypes.sizeof(N.rm_align_params), ctypes.sizeof(N.rm_align_report),
             ctypes.sizeof(N.rm_icp_out), ctypes.sizeof(N.rm_icp_params), ctypes.sizeof(N.rm_icp_report),
-            N.rm_icp_report.n_assoc.offset, ctypes.sizeof(N.rm_meshify_params)]
+            N.rm_icp_report.n_assoc.offset, ctypes.sizeof(N.rm_meshify_params),
+            ctypes.sizeof(N.rm_dfo_params), ctypes.sizeof(N.rm_dfo_report)]
     assert got == want

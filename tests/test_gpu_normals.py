@@ -106,3 +106,22 @@ def test_depth_normals_host_buffers(scans):
     g = _np(rm.depth_normals(intr, d, c, sigma=1.5, metric=True))
     assert np.array_equal(np.isnan(out), np.isnan(g))
     assert np.array_equal(out[~np.isnan(out)], g[~np.isnan(g)])
+
+
+@pytest.mark.parametrize("sigma", [0.0, 1.0, 3.0])
+def test_depth_blur_parity(scans, sigma):
+    """Cost smoothing: FO returns take the smoothed depth (within 1e-5 relative of the
+    oracle's), every other pixel keeps its input depth bit for bit; the blurred scan scores
+    like any scan."""
+    cam, sc = scans
+    intr = rm.Intrinsics.from_camera(cam)
+    for d, c in sc:
+        g = rm.blur_scan(rm.Scan.make(intr, d, c), sigma=sigma)
+        od, _ = oracle.depth_blur(d, c, sigma=sigma)
+        gd = _np(g.depth)
+        fo = (c == 0) & np.isfinite(d)
+        assert np.all(np.abs(gd[fo] - od[fo]) <= 1e-5 * np.abs(od[fo]))
+        assert np.array_equal(gd[~fo].view(np.uint32), d[~fo].view(np.uint32))
+        assert torch.equal(g.cls, torch.as_tensor(c, device="cuda"))
+        if sigma == 0.0:
+            assert np.array_equal(gd.view(np.uint32), np.asarray(d, np.float32).view(np.uint32))

@@ -102,3 +102,24 @@ def test_sigma_bounds():
         oracle.depth_normals(z, c, sigma=-1.0)
     n, s = oracle.depth_normals(z, c, sigma=0.0)
     assert np.all(s == 1.0)
+
+
+def test_blur_keeps_other_pixels_and_linear_interior():
+    """Cost smoothing keeps FU and dead pixels as they are and, away from the border and the
+    holes, leaves a linear depth image unchanged."""
+    H, W = 30, 40
+    y, x = np.mgrid[0:H, 0:W].astype(np.float64)
+    z = (2.0 + 0.0625 * x - 0.03125 * y).astype(np.float32)
+    c = np.zeros((H, W), np.uint8)
+    c[10:12, 5:8] = 1
+    z[10:12, 5:8] = 4.0
+    c[20, 30] = 2
+    d, _ = oracle.depth_blur(z, c, sigma=1.0)
+    assert np.array_equal(d[c != 0], z[c != 0])
+    far = np.ones((H, W), bool)
+    far[6:16, 1:12] = False  # within reach of the FU block
+    far[16:25, 26:35] = False
+    inner = np.zeros((H, W), bool)
+    inner[4:-4, 4:-4] = True
+    sel = far & inner & (c == 0)
+    assert np.allclose(d[sel], z[sel], rtol=1e-6, atol=0)
