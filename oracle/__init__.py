@@ -145,6 +145,7 @@ def lib():
         _lib = ctypes.CDLL(build())
         _lib.orc_cost_frozen.restype = ctypes.c_double
         _lib.orc_icp_frozen.restype = ctypes.c_double
+        _lib.orc_cost_frozen_vertex.restype = ctypes.c_double
     return _lib
 
 
@@ -407,6 +408,29 @@ class OracleMap:
                                        ctypes.byref(prm), _p(counts), _p(e), _p(g), _p(h))
         del keep
         return {"counts": counts, "e_ls": e, "grad": g, "jtj": h, "threads": threads}
+
+    def vertex_grad(self, pose, cam, scan_depth, scan_class, params=None):
+        """d e_ls / d (world vertex positions), (V, 3)."""
+        c, keep = make_cam(cam)
+        prm = params or make_params()
+        g = np.zeros((self.v.shape[0], 3))
+        lib().orc_cost_vertex_grad(_p(self.v), _p(self.vr), self.V, _p(self.centre), _p(self.faces),
+                                   _p(self.labels), self.T, _p(_f64(pose).reshape(16)), ctypes.byref(c),
+                                   _p(_f32(scan_depth)), _p(np.ascontiguousarray(scan_class, np.uint8)),
+                                   ctypes.byref(prm), _p(g))
+        del keep
+        return g
+
+    def cost_frozen_vertex(self, pose, cam, scan_depth, scan_class, vk, delta, params=None):
+        c, keep = make_cam(cam)
+        prm = params or make_params()
+        r = lib().orc_cost_frozen_vertex(_p(self.v), _p(self.vr), self.V, _p(self.centre), _p(self.faces),
+                                         _p(self.labels), self.T, _p(_f64(pose).reshape(16)),
+                                         ctypes.byref(c), _p(_f32(scan_depth)),
+                                         _p(np.ascontiguousarray(scan_class, np.uint8)), ctypes.byref(prm),
+                                         ctypes.c_int64(vk), _p(_f64(delta)))
+        del keep
+        return r
 
     def dfo_align(self, pose0, cam, scan_depth, scan_class, params=None, dfo=None):
         """Nelder-Mead then coordinate descent on the Table I cost (Sec. III.C)."""

@@ -1321,3 +1321,122 @@ void orc_pose_from_x(const double X[6], double T[16]) {
   T[12] = T[13] = T[14] = 0.0;
   T[15] = 1.0;
 }
+
+/* ------------------------------------------------------------------------------------- */
+/* Vertex-position gradient of the least-squares surrogate (map refinement)               */
+/* ------------------------------------------------------------------------------------- */
+
+/* Camera-frame plane of the triangle (a, b, c) given in FP64 world coordinates: unnormalised
+ * camera-frame normal n_c, world normal n_w, offset d with n_c . (t r) = d on the plane. */
+static void plane64d(const double a[3], const double b[3], const double c[3], const double T[16],
+                     double nc[3], double nw[3], double *d) {
+  double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+  double e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+  nw[0] = e1[1] * e2[2] - e1[2] * e2[1];
+  nw[1] = e1[2] * e2[0] - e1[0] * e2[2];
+  nw[2] = e1[0] * e2[1] - e1[1] * e2[0];
+  double q[3] = {a[0] - T[3], a[1] - T[7], a[2] - T[11]};
+  *d = nw[0] * q[0] + nw[1] * q[1] + nw[2] * q[2];
+  for (int i = 0; i < 3; ++i) nc[i] = T[0 * 4 + i] * nw[0] + T[1 * 4 + i] * nw[1] + T[2 * 4 + i] * nw[2];
+}
+
+static void face_vertices64(const float *v, const int32_t *faces, int64_t k, int64_t vk,
+                            const double delta[3], double P[3][3]) {
+  for (int m = 0; m < 3; ++m) {
+    const int64_t id = faces[3 * k + m];
+    for (int a = 0; a < 3; ++a) P[m][a] = (double)v[3 * id + a] + (id == vk && delta ? delta[a] : 0.0);
+  }
+}
+
+int orc_cost_vertex_grad(const float *v, const float *vr, int64_t V, const double centre[3],
+                         const int32_t *faces, const uint8_t *labels, int64_t T,
+                         const double Twc[16], const orc_cam *cam, const float *scan_depth,
+                         const uint8_t *scan_class, const orc_params *prm, double *gV) {
+  int64_t P = (int64_t)cam->width * cam->height;
+  uint64_t *keys = (uint64_t *)malloc(sizeof(uint64_t) * (P > 0 ? P : 1));
+  if (!keys) return -1;
+  orc_render(vr, V, centre, faces, T, Twc, cam, keys, NULL, 0, NULL);
+  for (int64_t i = 0; i < 3 * V; ++i) gV[i] = 0.0;
+  for (int j = 0; j < cam->height; ++j)
+    for (int i = 0; i < cam->width; ++i) {
+      int64_t p = (int64_t)j * cam->width + i;
+      uint64_t key = keys[p];
+      if (key == KEY_EMPTY) continue;
+      const int64_t k = (int64_t)(key & 0xFFFFFFFFu);
+      int mc = (int)labels[k];
+      int sc = scan_class_of(scan_depth, scan_class, p);
+      if (sc == 2) continue;
+      float t32 = key_depth(key);
+      float dz32 = t32 - scan_depth[p];
+      int oc = orc_table1(mc, sc, dz32, prm->eps);
+      if (oc < 0) continue;
+      int active;
+      double sgn, w;
+      double res = ls_residual(oc, dz32, (double)t32 - (double)scan_depth[p], prm->eps, prm, &active, &sgn, &w);
+      if (!active) continue;
+      double Pv[3][3], nc[3], nw[3], d, r[3];
+      face_vertices64(v, faces, k, -1, NULL, Pv);
+      plane64d(Pv[0], Pv[1], Pv[2], Twc, nc, nw, &d);
+      ray64(cam, i, j, r);
+      const double nr = nc[0] * r[0] + nc[1] * r[1] + nc[2] * r[2];
+      const double t = d / nr;
+      /* the hit point in the world and its barycentrics (sub-triangle areas along n_w) */
+      double dir[3], h[3];
+      for (int a = 0; a < 3; ++a) dir[a] = Twc[4 * a] * r[0] + Twc[4 * a + 1] * r[1] + Twc[4 * a + 2] * r[2];
+      for (int a = 0; a < 3; ++a) h[a] = Twc[4 * a + 3] + t * dir[a];
+      const double nn = nw[0] * nw[0] + nw[1] * nw[1] + nw[2] * nw[2];
+      double b[3];
+      for (int m = 0; m < 3; ++m) {
+        const double *A = Pv[(m + 1) % 3], *B = Pv[(m + 2) % 3];
+        double e1[3] = {B[0] - A[0], B[1] - A[1], B[2] - A[2]};
+        double e2[3] = {h[0] - A[0], h[1] - A[1], h[2] - A[2]};
+        double cr[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+        b[m] = (cr[0] * nw[0] + cr[1] * nw[1] + cr[2] * nw[2]) / nn;
+      }
+      /* d t / d v_m = b_m n_w / (n_c . r) */
+      for (int m = 0; m < 3; ++m) {
+        const int64_t id = faces[3 * k + m];
+        for (int a = 0; a < 3; ++a) gV[3 * id + a] += w * res * sgn * b[m] * nw[a] / nr;
+      }
+    }
+  free(keys);
+  return 0;
+}
+
+double orc_cost_frozen_vertex(const float *v, const float *vr, int64_t V, const double centre[3],
+                              const int32_t *faces, const uint8_t *labels, int64_t T,
+                              const double Twc[16], const orc_cam *cam, const float *scan_depth,
+                              const uint8_t *scan_class, const orc_params *prm, int64_t vk,
+                              const double delta[3]) {
+  int64_t P = (int64_t)cam->width * cam->height;
+  uint64_t *keys = (uint64_t *)malloc(sizeof(uint64_t) * (P > 0 ? P : 1));
+  if (!keys) return NAN;
+  orc_render(vr, V, centre, faces, T, Twc, cam, keys, NULL, 0, NULL);
+  double E = 0.0;
+  for (int j = 0; j < cam->height; ++j)
+    for (int i = 0; i < cam->width; ++i) {
+      int64_t p = (int64_t)j * cam->width + i;
+      uint64_t key = keys[p];
+      if (key == KEY_EMPTY) continue;
+      const int64_t k = (int64_t)(key & 0xFFFFFFFFu);
+      int mc = (int)labels[k];
+      int sc = scan_class_of(scan_depth, scan_class, p);
+      if (sc == 2) continue;
+      float t32 = key_depth(key);
+      float dz32 = t32 - scan_depth[p];
+      int oc = orc_table1(mc, sc, dz32, prm->eps);
+      if (oc < 0) continue;
+      double Pv[3][3], nc[3], nw[3], d, r[3];
+      face_vertices64(v, faces, k, vk, delta, Pv);
+      plane64d(Pv[0], Pv[1], Pv[2], Twc, nc, nw, &d);
+      ray64(cam, i, j, r);
+      double dz = d / (nc[0] * r[0] + nc[1] * r[1] + nc[2] * r[2]) - (double)scan_depth[p];
+      int active;
+      double sgn, w;
+      /* cells and activity frozen at the unperturbed map */
+      double res = ls_residual(oc, dz32, dz, prm->eps, prm, &active, &sgn, &w);
+      E += 0.5 * w * res * res;
+    }
+  free(keys);
+  return E;
+}

@@ -221,6 +221,23 @@ void orc_scan_from_range(const float *range, int64_t n, float range_min, float r
  * read as R = Rz(theta_z) Ry(theta_y) Rx(theta_x) and translation (x, y, z). */
 void orc_pose_from_x(const double X[6], double T[16]);
 
+/* Gradient of e_ls w.r.t. the world positions of the map's vertices at pose Twc (V*3, map
+ * refinement): each active pixel adds w r sgn b_m n_w / (n_c . r) to the vertices m of its
+ * winning triangle, with b_m the barycentrics of the FP64 hit point. The residual r is the
+ * cost's (FP32 z-buffer depth), the geometry FP64. */
+int orc_cost_vertex_grad(const float *v, const float *vr, int64_t V, const double centre[3],
+                         const int32_t *faces, const uint8_t *labels, int64_t T,
+                         const double Twc[16], const orc_cam *cam, const float *scan_depth,
+                         const uint8_t *scan_class, const orc_params *prm, double *gV);
+
+/* The frozen-cell e_ls of pose Twc (winners, cells and activity of the unmoved map) with
+ * vertex vk moved by delta (world) and the depths re-intersected in FP64. */
+double orc_cost_frozen_vertex(const float *v, const float *vr, int64_t V, const double centre[3],
+                              const int32_t *faces, const uint8_t *labels, int64_t T,
+                              const double Twc[16], const orc_cam *cam, const float *scan_depth,
+                              const uint8_t *scan_class, const orc_params *prm, int64_t vk,
+                              const double delta[3]);
+
 #ifdef __cplusplus
 }
 #endif
