@@ -194,6 +194,18 @@ rm_status rm_align(rm_map *map, const rm_scan *scan, const double *init_pose,
                    const rm_cost_params *params, const rm_align_params *lm, double *pose_out,
                    rm_align_report *rep, void *stream);
 
+/* ---- Vertex-position gradient (map refinement) ----------------------------------------
+ * grad_v (V*3 doubles, host or device, overwritten) = the sum over the n poses of
+ * d e_ls / d (world vertex positions) against one scan: each pixel with an active residual r
+ * (the cells and thresholds of rm_cost_grad) adds w r sgn b_m n / (n_c . ray) to vertex m of
+ * its winning triangle (b_m its barycentric, n the unit world normal, n_c the camera-frame
+ * one). Renders each pose's visibility buffer (ids, depths, barycentrics), then scatters with
+ * FP64 atomics, so the summation order (and the last bits) vary from run to run. Errors as
+ * rm_cost_grad. */
+rm_status rm_cost_grad_vertices(rm_map *map, const rm_scan *scan, const double *poses,
+                                int32_t n_poses, const rm_cost_params *params, double *grad_v,
+                                void *stream);
+
 /* ---- Input helpers ----------------------------------------------------------------------
  * Depth and class of n pixels of raw range images (Sec. III.A, III.B): a NaN reading, or a
  * return closer than range_min (and above 0), is a dead pixel (RM_SCAN_NAN, depth NaN); no

@@ -131,6 +131,8 @@ _SIGS = {
     "rm_pose_from_x": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),
     "rm_depth_blur": (ctypes.c_int, [ctypes.POINTER(rm_intrinsics), ctypes.c_int32, _P, _P, ctypes.c_float, _P,
                                      _P]),
+    "rm_cost_grad_vertices": (ctypes.c_int, [_P, ctypes.POINTER(rm_scan), _P, ctypes.c_int32,
+                                             ctypes.POINTER(rm_cost_params), _P, _P]),
     "rm_cost_grad_noalloc": (ctypes.c_int, [_P, ctypes.POINTER(rm_scan), _P,
                                             ctypes.POINTER(rm_cost_params), ctypes.POINTER(rm_cost_out), _P]),
     "rm_status_sync": (ctypes.c_int, [_P, _P]),

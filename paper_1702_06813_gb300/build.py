@@ -11,7 +11,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "librendermap.so")
-SOURCES = ["rm_api.cu", "rm_kernels.cu", "rm_noalloc.cu", "rm_normals.cu", "rm_mesh.cu", "rm_util.cu"]
+SOURCES = ["rm_api.cu", "rm_kernels.cu", "rm_noalloc.cu", "rm_normals.cu", "rm_mesh.cu", "rm_util.cu", "rm_vgrad.cu"]
 HEADERS = ["rm_internal.cuh", "rm_kernels.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off",

@@ -1148,6 +1148,91 @@ rm_status rm_icp_terms(rm_map *m, const rm_scan *scan, const double *poses, int3
   return run_eval(m, r, (cudaStream_t)stream);
 }
 
+rm_status rm_cost_grad_vertices(rm_map *m, const rm_scan *scan, const double *poses, int32_t n,
+                                const rm_cost_params *prm, double *grad_v, void *stream) {
+  if (!m) return fail(RM_EINVAL, "map is NULL");
+  if (!scan || !scan->depth || !scan->cls) return fail(RM_EINVAL, "scan or its arrays NULL");
+  if (!prm || !grad_v) return fail(RM_EINVAL, "NULL argument");
+  if (!(prm->eps >= 0.0f)) return fail(RM_EINVAL, "eps must be >= 0");
+  if (n < 0) return fail(RM_EINVAL, "n_poses < 0");
+  if (n > 0 && !poses) return fail(RM_EINVAL, "poses is NULL");
+  std::lock_guard<std::mutex> lk(m->mu);
+  const rm_intrinsics *in = &scan->intr;
+  RM_TRY(check_intr(in));
+  RM_CK(cudaSetDevice(m->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long P = (long long)in->width * in->height;
+  const int chunk = (int)std::max<long long>(1, std::min<long long>(16, (1LL << 28) / std::max<long long>(P, 1)));
+  const bool host_g = !on_device(grad_v), host_p = n > 0 && !on_device(poses);
+  const bool host_sd = !on_device(scan->depth), host_sc = !on_device(scan->cls);
+  const bool host_rays = in->model == RM_RAYTABLE && !on_device(in->rays);
+  // stream-ordered scratch (the map's arena is reused by the render calls below)
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = off;
+    off += (bytes + 255) / 256 * 256;
+    return at;
+  };
+  const size_t o_g = host_g ? take(sizeof(double) * 3 * (size_t)m->V) : 0;
+  const size_t o_p = take(sizeof(double) * 16 * (size_t)std::max(n, 1));
+  const size_t o_sd = host_sd ? take(sizeof(float) * P) : 0, o_sc = host_sc ? take(P) : 0;
+  const size_t o_r = host_rays ? take(sizeof(float) * 3 * P) : 0;
+  const size_t o_m = take(sizeof(float) * 12 * chunk);
+  const size_t o_id = take(sizeof(int) * P * chunk), o_d = take(sizeof(float) * P * chunk);
+  const size_t o_b = take(sizeof(float) * 2 * P * chunk);
+  unsigned char *buf = nullptr;
+  RM_CK(cudaMallocAsync((void **)&buf, off, s));
+  double *d_g = host_g ? reinterpret_cast<double *>(buf + o_g) : grad_v;
+  double *d_p = reinterpret_cast<double *>(buf + o_p);
+  const float *d_sd = host_sd ? reinterpret_cast<float *>(buf + o_sd) : scan->depth;
+  const uint8_t *d_sc = host_sc ? buf + o_sc : scan->cls;
+  const float *d_rays = host_rays ? reinterpret_cast<float *>(buf + o_r) : in->rays;
+  float *d_M = reinterpret_cast<float *>(buf + o_m);
+  int *d_id = reinterpret_cast<int *>(buf + o_id);
+  float *d_d = reinterpret_cast<float *>(buf + o_d);
+  float *d_b = reinterpret_cast<float *>(buf + o_b);
+  auto body = [&]() -> rm_status {
+    RM_CK(cudaMemsetAsync(d_g, 0, sizeof(double) * 3 * (size_t)m->V, s));
+    if (n > 0)
+      RM_CK(cudaMemcpyAsync(d_p, poses, sizeof(double) * 16 * n,
+                            host_p ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+    if (host_sd) RM_CK(cudaMemcpyAsync((void *)d_sd, scan->depth, sizeof(float) * P, cudaMemcpyHostToDevice, s));
+    if (host_sc) RM_CK(cudaMemcpyAsync((void *)d_sc, scan->cls, P, cudaMemcpyHostToDevice, s));
+    if (host_rays) RM_CK(cudaMemcpyAsync((void *)d_rays, in->rays, sizeof(float) * 3 * P, cudaMemcpyHostToDevice, s));
+    rm_intrinsics ind = *in;
+    ind.rays = d_rays;
+    for (int p0 = 0; p0 < n; p0 += chunk) {
+      const int c = std::min(chunk, n - p0);
+      EvalReq r{&ind, nullptr, d_p + 16 * (size_t)p0, c, nullptr, rmk::kRender, nullptr, nullptr, d_d, d_id, d_b};
+      RM_TRY(run_eval(m, r, s));
+      RM_CK(rmk::launch_pose_to_m(d_p + 16 * (size_t)p0, c, m->centre[0], m->centre[1], m->centre[2], d_M, s));
+      rmk::VGradArgs a{};
+      a.cam = make_cam(&ind, d_rays);
+      a.W = in->width;
+      a.n_poses = c;
+      a.P = P;
+      a.Ms = d_M;
+      a.planes = m->d_planes;
+      a.faces = m->d_faces;
+      a.tri_id = d_id;
+      a.depth = d_d;
+      a.bary = d_b;
+      a.scan_depth = d_sd;
+      a.scan_cls = d_sc;
+      a.prm = {prm->eps, prm->w_fofo, prm->w_fofu, prm->w_fufo};
+      a.grad = d_g;
+      RM_CK(rmk::launch_vertex_grad(a, s));
+      m->launches += 2;
+    }
+    if (host_g) RM_CK(cudaMemcpyAsync(grad_v, d_g, sizeof(double) * 3 * (size_t)m->V, cudaMemcpyDeviceToHost, s));
+    return RM_OK;
+  };
+  rm_status st = body();
+  cudaFreeAsync(buf, s);
+  if (st == RM_OK && host_g) RM_CK(cudaStreamSynchronize(s));
+  return st;
+}
+
 rm_status rm_pose_retract(const double *poses, const double *twists, int32_t n, double *out,
                           double *jr, void *stream) {
   if (n < 0) return fail(RM_EINVAL, "n < 0");

@@ -114,6 +114,24 @@ cudaError_t launch_icp_step(IcpState *st, const IcpArgs &a, const long long *n,
                             const double *l1, const double *g, const double *H, float *M,
                             int *skip, cudaStream_t s);
 
+// Vertex-position gradient of the surrogate from a rendered visibility buffer.
+struct VGradArgs {
+  DevCam cam;
+  int W, n_poses;
+  long long P;            // pixels per pose
+  const float *Ms;        // 12 floats per pose
+  const float4 *planes;   // unit world normal, label bits in w
+  const int4 *faces;      // i0, i1, i2, label
+  const int *tri_id;      // n_poses * P
+  const float *depth;     // n_poses * P (the z-buffer depth)
+  const float *bary;      // n_poses * P * 2
+  const float *scan_depth;
+  const uint8_t *scan_cls;
+  CostParams prm;
+  double *grad;           // V * 3, accumulated
+};
+cudaError_t launch_vertex_grad(const VGradArgs &a, cudaStream_t s);
+
 // Derivative-free search state on the device (one pose): Nelder-Mead over scaled twists,
 // then coordinate descent, on the Table I cost of T0 exp(xi^); candidates are evaluated as
 // one wave of kDfoSlots poses.

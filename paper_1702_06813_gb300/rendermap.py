@@ -214,6 +214,17 @@ def cost_grad(m: Map, scan: Scan, poses, params=None):
     return _cost(lib().rm_cost_grad, m, scan, poses, params, True)
 
 
+def cost_grad_vertices(m: Map, scan: Scan, poses, params=None):
+    """d e_ls / d (world vertex positions), summed over the poses: (V, 3) float64 on the device."""
+    p, n = _poses(poses)
+    g = torch.empty((m.n_vertices, 3), dtype=torch.float64, device="cuda")
+    cs = scan.c()
+    prm = params if params is not None else _DEFAULT_PARAMS
+    check(lib().rm_cost_grad_vertices(m.handle, ctypes.byref(cs), _ptr(p), n, ctypes.byref(prm), _ptr(g),
+                                      _stream()))
+    return g
+
+
 def pose_retract(poses, twists, with_jacobian=False):
     """poses * exp(twists^) (and the SE(3) right Jacobians), computed on the device."""
     p, n = _poses(poses)
