@@ -5,8 +5,9 @@ pose is scored by rendering the map's z-buffer from it and comparing it per pixe
 observed range image by Table I (Sec. III.B, Eq. 1). All of it runs in hand-written sm_103a
 CUDA kernels behind the C ABI of include/rendermap.h; this package is the thin binding.
 """
-from .rendermap import (Intrinsics, Map, RenderMapCost, Scan, align, align_batch, blur_scan, cost,  # noqa: F401
-                        cost_grad, cost_grad_batch, cost_grad_vertices, cost_params, depth_normals, dfo_align, dfo_params, icp_align,
-                        icp_terms, meshify, pose_from_x, scan_from_range,
-                        pose_retract, render_depth, OUTCOMES, RM_PINHOLE, RM_RAYTABLE)
+from .rendermap import (OUTCOMES, RM_PINHOLE, RM_RAYTABLE, Intrinsics, Map, RenderMapCost,  # noqa: F401
+                        Scan, align, align_batch, blur_scan, cost, cost_grad, cost_grad_batch,
+                        cost_grad_vertices, cost_params, depth_normals, dfo_align, dfo_params,
+                        icp_align, icp_terms, meshify, pose_from_x, pose_retract, render_depth,
+                        scan_from_range)
 from ._native import RenderMapError, exported_symbols  # noqa: F401
