@@ -47,6 +47,8 @@ def args_():
     ap.add_argument("--frames", type=int, default=200, help="tracking: frames of the trajectory")
     ap.add_argument("--agents", type=int, default=64, help="tracking: agents (scans per frame)")
     ap.add_argument("--triangles", type=int, default=2_000_000, help="tracking: map size")
+    ap.add_argument("--method", choices=["lm", "icp"], default="lm",
+                    help="tracking: LM on the Table I surrogate, or point-to-plane ICP (Sec. IV)")
     return ap.parse_args()
 
 
@@ -242,7 +244,12 @@ def run_tracking(a):
     est = np.stack([synth.perturb_fixed(truth[0, i], rng, 0.10, 1.0) for i in range(n_agents)])
     prev = est.copy()
     scans0 = scans_for(0)
-    rm.align_batch(gm, [(scans0[i], est[i]) for i in range(n_agents)], max_iters=5)  # warm
+    def step_batch(pairs):
+        if a.method == "icp":
+            return rm.icp_align_batch(gm, pairs, tol=0.3, max_iters=5, step_tol=1e-4)
+        return rm.align_batch(gm, pairs, max_iters=5)
+
+    step_batch([(scans0[i], est[i]) for i in range(n_agents)])  # warm
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
     total_ms, evals = 0.0, 0
@@ -256,11 +263,11 @@ def run_tracking(a):
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        out, reps, _ = rm.align_batch(gm, [(scans[i], init[i]) for i in range(n_agents)], max_iters=5)
+        out, reps, _ = step_batch([(scans[i], init[i]) for i in range(n_agents)])
         e1.record(stream)
         torch.cuda.synchronize()
         total_ms += e0.elapsed_time(e1)
-        evals += sum(1 + r["iters"] for r in reps)
+        evals += sum(1 + r["iters"] if a.method == "lm" else min(5, r["iters"] + 1) for r in reps)
         prev, est = est, out
         errs.append(np.linalg.norm(est[:, :3, 3] - truth[f, :, :3, 3], axis=1))
     value = n_agents * a.frames / (total_ms * 1e-3)
@@ -272,17 +279,21 @@ def run_tracking(a):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for i in range(n_agents):
-            rm.align(gm, scans[i], truth[f, i], max_iters=5)
+            if a.method == "icp":
+                rm.icp_align(gm, scans[i], truth[f, i], tol=0.3, max_iters=5, step_tol=1e-4)
+            else:
+                rm.align(gm, scans[i], truth[f, i], max_iters=5)
         torch.cuda.synchronize()
         plain_ms += (time.perf_counter() - t0) * 1e3
     plain_value = n_agents * n_plain / (plain_ms * 1e-3)
     errs = np.array(errs)
     print(json.dumps({
-        "metric": "tracking frames/s (64 mixed scans, 5 LM iterations each, 2M-triangle map)",
+        "metric": ("tracking frames/s (64 mixed scans, 5 LM iterations each, 2M-triangle map)" if a.method == "lm"
+                   else "tracking frames/s (64 mixed scans, 5 point-to-plane ICP iterations each, 2M-triangle map)"),
         "value": value, "unit": "scan frames/s", "n_gpus": 1, "steps": a.frames, "warmup": 1,
         "ms_per_step": total_ms / a.frames, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": w["name"], "agents": n_agents, "frames": a.frames,
+        "config": {"workload": w["name"], "method": a.method, "agents": n_agents, "frames": a.frames,
                    "triangles": mesh.n_tris, "sensors": ["160x120", "640x480", "1024x64 lidar"],
                    "pose_evals": evals, "pose_evals_per_s": evals / (total_ms * 1e-3),
                    "plain_per_pose_frames_per_s": plain_value, "batched_over_plain": value / plain_value,
@@ -410,6 +421,8 @@ def run_icp(a):
     gl = rm.Map(wl["mesh"].vertices, wl["mesh"].faces, wl["mesh"].labels)
     sl = rm.Scan.make(rm.Intrinsics.from_camera(wl["cam"]), *wl["scan"])
     lidar_align = align_stats(gl, sl, wl["start"], wl["gt"], 0.5, 1e-4)
+    gl.set_tuning(tile=(16, 16))  # one pose: 4x the tiles of the default 32x32 spread it wider
+    lidar_align["tile16x16"] = align_stats(gl, sl, wl["start"], wl["gt"], 0.5, 1e-4)
     gl.close()
 
     # Eq. 2 normals of 64 depth images (the room scan with per-image noise), sigma 1.5 px,
@@ -439,6 +452,56 @@ def run_icp(a):
                     "hbm_frac": normals_gbs / pk["hbm_gbs"],
                     "l2": "flushed between launches (256 MiB write)"}
 
+    # meshification of the room scan (Sec. III.A): 640x480 -> 306k vertices, 612k faces
+    P_img = cam.width * cam.height
+    mv = torch.empty((P_img, 3), dtype=torch.float32, device="cuda")
+    mf = torch.empty((2 * (cam.width - 1) * (cam.height - 1), 3), dtype=torch.int32, device="cuda")
+    ml = torch.empty(mf.shape[0], dtype=torch.uint8, device="cuda")
+    mn = torch.empty(1, dtype=torch.int64, device="cuda")
+    dscan = rm.Scan.make(intr, *w["scan"])
+    dcs = dscan.c()
+    gt_dev = torch.as_tensor(w["gt"].reshape(16), dtype=torch.float64, device="cuda")
+    mprm = N.rm_meshify_params(cam.range_max, 0.1, 1, 0)
+
+    def mesh_step():
+        N.check(N.lib().rm_meshify(ctypes.byref(dcs), ctypes.c_void_p(gt_dev.data_ptr()), ctypes.byref(mprm),
+                                   ctypes.c_void_p(mv.data_ptr()), ctypes.c_void_p(mf.data_ptr()),
+                                   ctypes.c_void_p(ml.data_ptr()), ctypes.c_void_p(mn.data_ptr()), sp))
+
+    for _ in range(3):
+        mesh_step()
+    ms_m, _ = timed(mesh_step, 20)
+    nfaces = int(mn.item())
+    mbytes = 5 * P_img + 12 * P_img + 13 * nfaces
+    mesh_line = {"image": [cam.width, cam.height], "faces": nfaces, "us_per_call": ms_m / 20 * 1e3,
+                 "algorithmic_bytes": mbytes, "achieved_gbs": mbytes * 20 / (ms_m * 1e-3) / 1e9,
+                 "kernels_per_call": 4}
+
+    # derivative-free alignment on the Table I cost (Sec. III.C), room scan from 3 cm / 1.5 deg
+    rng2 = np.random.Generator(np.random.PCG64(a.seed + 9))
+    dstart = synth.perturb_fixed(w["gt"], rng2, 0.03, 1.5)
+    dpar = rm.dfo_params(nm_iters=60, cd_iters=40)
+    rm.dfo_align(gm, scan, dstart, dfo=dpar)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    reps_d = 3
+    for _ in range(reps_d):
+        dpose, drep = rm.dfo_align(gm, scan, dstart, dfo=dpar)
+    dfo_ms = (time.perf_counter() - t0) / reps_d * 1e3
+    dfo_line = {"ms_per_alignment": dfo_ms, "evals": drep["evals"], "us_per_eval": dfo_ms * 1e3 / drep["evals"],
+                "nm_iters": drep["nm_iters"], "cd_iters": drep["cd_iters"], "converged": drep["converged"],
+                "e_table_initial": drep["e_table_initial"], "e_table_final": drep["e_table_final"],
+                "pos_err_m": float(np.linalg.norm(dpose[:3, 3] - w["gt"][:3, 3])),
+                "batch_slots": 12}
+
+    # vertex-position gradient summed over 16 candidate poses (map refinement)
+    vposes = poses[:16]
+    rm.cost_grad_vertices(gm, scan, vposes)
+    ms_v, _ = timed(lambda: rm.cost_grad_vertices(gm, scan, vposes), 5)
+    vgrad_line = {"poses": 16, "vertices": mesh.n_verts, "ms_per_call": ms_v / 5,
+                  "pose_evals_per_s": 16 * 5 / (ms_v * 1e-3),
+                  "note": "render with ids and barycentrics, then FP64 atomics per active pixel"}
+
     P = cam.width * cam.height
     ab = algorithmic_bytes(mesh.n_verts, mesh.n_tris, P)
     kern = prof["kernels"]
@@ -459,7 +522,8 @@ def run_icp(a):
                    "wave_poses": min(n, 128), "l2": "flushed between timed steps (256 MiB write)",
                    "kernel_share": share, "e2e_matches_device": ok,
                    "align_room_1M_640x480": room_align, "align_lidar_2M_1024x64": lidar_align,
-                   "depth_normals_eq2": normals_line,
+                   "depth_normals_eq2": normals_line, "meshify_sec3a": mesh_line,
+                   "dfo_align_table1_room": dfo_line, "vertex_grad": vgrad_line,
                    "step_hbm_roofline_frac": ab["total"] * n * a.steps / (ms * 1e-3) / 1e9 / pk["hbm_gbs"]},
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": "pose evals/s",

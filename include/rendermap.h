@@ -271,6 +271,7 @@ rm_status rm_icp_align(rm_map *map, const rm_scan *scan, const double *init_pose
                        const rm_icp_params *params, double *pose_out, rm_icp_report *rep,
                        void *stream);
 
+
 /* Surface normals of depth images (Eq. 2, Sec. IV), n images of one camera (intr: width,
  * height, and fx, fy for metric normals), each H*W float depth plus H*W uint8 RM_SCAN_* class,
  * host or device. A pixel is valid when its class is FO and its depth finite. The valid depths
@@ -398,6 +399,15 @@ rm_status rm_cost_grad_batch(rm_map *map, const rm_problem *problems, int32_t n,
 rm_status rm_align_batch(rm_map *map, const rm_problem *problems, int32_t n,
                          const rm_cost_params *params, const rm_align_params *lm,
                          double *poses_out, rm_align_report *reports, void *stream);
+
+/* rm_icp_align for a batch of problems (each its own scan and start pose; pinhole and
+ * ray-table problems mixed), every evaluation and step of every problem in one persistent
+ * kernel (as rm_align_batch): params->max_iters evaluations per problem (1..100000), each
+ * followed by its Gauss-Newton step on the device. poses_out: n*16 doubles (host or device);
+ * reps: n reports (optional, host). Returns RM_ENOTCONV when a problem did not converge. */
+rm_status rm_icp_align_batch(rm_map *map, const rm_problem *problems, int32_t n,
+                             const rm_icp_params *params, double *poses_out, rm_icp_report *reps,
+                             void *stream);
 
 /* Cost and gradient of ONE pose without allocating (the paper has no counterpart; this is a
  * deployment variant of rm_cost_grad). For callers that must not allocate device memory

@@ -619,23 +619,26 @@ int raster_items(const TileGeom &tg, int model) {
   return (tg.ntiles + per - 1) / per;
 }
 
-// Shared driver of rm_cost_grad_batch (lm == nullptr) and rm_align_batch.
+// Shared driver of rm_cost_grad_batch (lm == icp == nullptr), rm_align_batch (lm) and
+// rm_icp_align_batch (icp; prm->eps then carries the association tolerance).
 rm_status run_batch(rm_map *m, const rm_problem *probs, int n, const rm_cost_params *prm,
                     const rm_align_params *lm, const rm_cost_out *out, double *poses_out,
-                    rm_align_report *reps, cudaStream_t s) {
+                    rm_align_report *reps, cudaStream_t s, const rm_icp_params *icp = nullptr,
+                    rm_icp_report *ireps = nullptr) {
   if (n < 0) return fail(RM_EINVAL, "n < 0");
   if (n == 0) return RM_OK;
   if (!probs || !prm) return fail(RM_EINVAL, "NULL argument");
   if (!(prm->eps >= 0.0f)) return fail(RM_EINVAL, "eps must be >= 0");
   if (lm && (lm->max_iters < 0 || lm->max_iters > 100000)) return fail(RM_EINVAL, "max_iters out of range");
-  if (lm && !poses_out) return fail(RM_EINVAL, "poses_out is NULL");
+  if (icp && (icp->max_iters < 1 || icp->max_iters > 100000)) return fail(RM_EINVAL, "max_iters out of range (1..100000)");
+  if ((lm || icp) && !poses_out) return fail(RM_EINVAL, "poses_out is NULL");
   for (int p = 0; p < n; ++p) {
     RM_TRY(check_intr(&probs[p].scan.intr));
     if (!probs[p].scan.depth || !probs[p].scan.cls || !probs[p].pose)
       return fail(RM_EINVAL, "problem " + std::to_string(p) + ": NULL scan array or pose");
   }
   RM_CK(cudaSetDevice(m->device));
-  const int K = lm ? lm->max_iters : 0;
+  const int K = lm ? lm->max_iters : (icp ? icp->max_iters - 1 : 0);
   const int nc = m->n_clusters;
   // at least one item per phase, so that every phase completes and publishes the next
   const int ncull = std::max(1, ((nc + 255) / 256 + rmk::kPersistCull - 1) / rmk::kPersistCull);
@@ -697,7 +700,7 @@ rm_status run_batch(rm_map *m, const rm_problem *probs, int n, const rm_cost_par
                       rmk::LMState **d_lm, int **d_vcount, int4 **d_vis, int **d_counts,
                       double **d_partial, unsigned char **d_bins, float **d_sd, uint8_t **d_sc,
                       float **d_rays, long long **r_counts, long long **r_et, double **r_els,
-                      double **r_grad, double **r_jtj) {
+                      double **r_grad, double **r_jtj, rmk::IcpState **d_icp, double **r_l1) {
       (void)carve;
       *d_args = cv.take<WaveArgs>(n);
       *d_items = cv.take<int4>(cap_hi + cap_lo);
@@ -721,19 +724,22 @@ rm_status run_batch(rm_map *m, const rm_problem *probs, int n, const rm_cost_par
       *r_els = cv.take<double>(n);
       *r_grad = cv.take<double>(6 * (size_t)n);
       *r_jtj = cv.take<double>(21 * (size_t)n);
+      *d_icp = cv.take<rmk::IcpState>(n);
+      *r_l1 = cv.take<double>(n);
     };
     WaveArgs *d_args; int4 *d_items, *d_vis; int *d_next, *d_done, *d_need, *d_skip, *d_vcount, *d_counts;
     float *d_M, *d_sd, *d_rays; double *d_poses, *d_partial, *r_els, *r_grad, *r_jtj; rmk::LMState *d_lm;
     unsigned char *d_bins; uint8_t *d_sc; long long *r_counts, *r_et;
+    rmk::IcpState *d_icp; double *r_l1;
     Carver plan{nullptr};
     layout(plan, false, &d_args, &d_items, &d_next, &d_done, &d_need, &d_M, &d_skip, &d_poses, &d_lm,
            &d_vcount, &d_vis, &d_counts, &d_partial, &d_bins, &d_sd, &d_sc, &d_rays, &r_counts, &r_et,
-           &r_els, &r_grad, &r_jtj);
+           &r_els, &r_grad, &r_jtj, &d_icp, &r_l1);
     RM_TRY(ensure_arena(m, plan.off, s));
     Carver cv{m->arena};
     layout(cv, true, &d_args, &d_items, &d_next, &d_done, &d_need, &d_M, &d_skip, &d_poses, &d_lm,
            &d_vcount, &d_vis, &d_counts, &d_partial, &d_bins, &d_sd, &d_sc, &d_rays, &r_counts, &r_et,
-           &r_els, &r_grad, &r_jtj);
+           &r_els, &r_grad, &r_jtj, &d_icp, &r_l1);
     // ---- per-problem arguments and inputs
     // poses laid out back to back (one n x 16 array) are copied in one call
     bool poses_contiguous = true;
@@ -800,6 +806,12 @@ rm_status run_batch(rm_map *m, const rm_problem *probs, int n, const rm_cost_par
       a.res_els = r_els + p;
       a.res_grad = r_grad + 6 * (size_t)p;
       a.res_jtj = r_jtj + 21 * (size_t)p;
+      if (icp) {  // ICP terms: associations, C, e^2, J^T e, J^T J
+        a.res_counts = nullptr;
+        a.res_etable = nullptr;
+        a.res_n = r_counts + p;
+        a.res_l1 = r_l1 + p;
+      }
       t_off += tg[p].ntiles;
       b_off += align_up((size_t)tg[p].ntiles * tg[p].cap * tg[p].rec_bytes, 256);
     }
@@ -839,6 +851,9 @@ rm_status run_batch(rm_map *m, const rm_problem *probs, int n, const rm_cost_par
     b.done = d_done;
     b.need = d_need;
     b.lm = lm ? d_lm : nullptr;
+    b.icp = icp ? d_icp : nullptr;
+    rmk::IcpArgs ia{icp ? icp->step_tol : 0.0, m->centre[0], m->centre[1], m->centre[2]};
+    b.icpargs = ia;
     b.Ms = d_M;
     b.skip = d_skip;
     b.lmargs = la;
@@ -850,9 +865,9 @@ rm_status run_batch(rm_map *m, const rm_problem *probs, int n, const rm_cost_par
     // counters to zero, LM state / pose matrices, the persistent kernel: one captured graph
     // per batch shape (the arena layout is a function of the shape), replayed every call
     char sig[512];
-    std::snprintf(sig, sizeof(sig), "%p|%d|%d|%zu|%d|%d|%a|%a|%a|%a|%zu|%zu|%zu|%d", (void *)m->arena, n,
-                  K, cap_hi + cap_lo, grid, lm ? 1 : 0, la.lambda0, la.lambda_up, la.lambda_down,
-                  la.step_tol, tiles_total, px_total, rays_total, m->cap * 4096 + m->cap_ray);
+    std::snprintf(sig, sizeof(sig), "%p|%d|%d|%zu|%d|%d|%a|%a|%a|%a|%zu|%zu|%zu|%d|%a", (void *)m->arena, n,
+                  K, cap_hi + cap_lo, grid, lm ? 1 : (icp ? 2 : 0), la.lambda0, la.lambda_up, la.lambda_down,
+                  la.step_tol, tiles_total, px_total, rays_total, m->cap * 4096 + m->cap_ray, ia.step_tol);
     std::string key(sig);
     for (int p = 0; p < n; ++p) key += "|" + std::to_string(probs[p].scan.intr.model) + "x" +
                                         std::to_string(probs[p].scan.intr.width) + "x" +
@@ -877,6 +892,7 @@ rm_status run_batch(rm_map *m, const rm_problem *probs, int n, const rm_cost_par
       rec(cudaMemsetAsync(d_vcount, 0, sizeof(int) * n, c));
       rec(cudaMemsetAsync(d_counts, 0, sizeof(int) * tiles_total, c));
       if (lm) rec(rmk::launch_lm_init_batch(d_lm, d_poses, n, la, d_M, d_skip, c));
+      else if (icp) rec(rmk::launch_icp_init_batch(d_icp, d_poses, n, ia, d_M, d_skip, c));
       else rec(rmk::launch_pose_to_m(d_poses, n, m->centre[0], m->centre[1], m->centre[2], d_M, c));
       rec(rmk::launch_persist(b, grid, c));
       cudaGraph_t graph = nullptr;
@@ -894,9 +910,13 @@ rm_status run_batch(rm_map *m, const rm_problem *probs, int n, const rm_cost_par
     m->launches += 2;
     bool host_out = false;
     std::vector<rmk::LMState> hs;
+    std::vector<rmk::IcpState> his;
     if (lm) {
       hs.resize(n);
       RM_CK(cudaMemcpyAsync(hs.data(), d_lm, sizeof(rmk::LMState) * n, cudaMemcpyDeviceToHost, s));
+    } else if (icp) {
+      his.resize(n);
+      RM_CK(cudaMemcpyAsync(his.data(), d_icp, sizeof(rmk::IcpState) * n, cudaMemcpyDeviceToHost, s));
     } else if (out) {
       RM_TRY(copy_out(out->counts, r_counts, sizeof(long long) * 6 * n, s, &host_out));
       RM_TRY(copy_out(out->e_table, r_et, sizeof(long long) * n, s, &host_out));
@@ -911,6 +931,26 @@ rm_status run_batch(rm_map *m, const rm_problem *probs, int n, const rm_cost_par
     if (st & (rmk::kStatusOverflow | rmk::kStatusOverflowRay)) {
       RM_TRY(grow_bins(m, st, attempt));
       continue;
+    }
+    if (icp) {
+      bool all_conv = true;
+      std::vector<double> pout(16 * (size_t)n);
+      for (int p = 0; p < n; ++p) {
+        std::memcpy(&pout[16 * (size_t)p], his[p].T, sizeof(double) * 16);
+        all_conv = all_conv && his[p].converged;
+        if (ireps) {
+          ireps[p].iters = his[p].iters;
+          ireps[p].converged = his[p].converged;
+          ireps[p].n_assoc = his[p].n_assoc;
+          ireps[p].cost_l1_initial = his[p].l1_0;
+          ireps[p].cost_l1_final = his[p].l1;
+        }
+      }
+      if (on_device(poses_out))
+        RM_CK(cudaMemcpy(poses_out, pout.data(), sizeof(double) * 16 * n, cudaMemcpyHostToDevice));
+      else
+        std::memcpy(poses_out, pout.data(), sizeof(double) * 16 * n);
+      return all_conv ? RM_OK : fail(RM_ENOTCONV, "a problem's ICP steps did not fall below step_tol");
     }
     if (!lm) return RM_OK;
     bool all_conv = true;
@@ -1313,6 +1353,16 @@ rm_status rm_align_batch(rm_map *m, const rm_problem *probs, int32_t n, const rm
   if (!lm) return fail(RM_EINVAL, "lm is NULL");
   std::lock_guard<std::mutex> lk(m->mu);
   return run_batch(m, probs, n, prm, lm, nullptr, poses_out, reps, (cudaStream_t)stream);
+}
+
+rm_status rm_icp_align_batch(rm_map *m, const rm_problem *probs, int32_t n, const rm_icp_params *icp,
+                             double *poses_out, rm_icp_report *reps, void *stream) {
+  if (!m) return fail(RM_EINVAL, "map is NULL");
+  if (!icp) return fail(RM_EINVAL, "params is NULL");
+  if (!(icp->tol >= 0.0f)) return fail(RM_EINVAL, "tol must be >= 0");
+  std::lock_guard<std::mutex> lk(m->mu);
+  const rm_cost_params prm{icp->tol, 0.0f, 0.0f, 0.0f};
+  return run_batch(m, probs, n, &prm, nullptr, nullptr, poses_out, nullptr, (cudaStream_t)stream, icp, reps);
 }
 
 rm_status rm_status_sync(rm_map *m, void *stream) {

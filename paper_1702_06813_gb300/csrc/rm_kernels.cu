@@ -1533,20 +1533,24 @@ __global__ void k_lm_accept(LMState *st, LMArgs a, const long long *counts, cons
 
 // ------------------------------------------------------------------ point-to-plane ICP
 
-__global__ void k_icp_init(IcpState *st, const double *T0, IcpArgs a, float *M, int *skip) {
-  for (int k = 0; k < 16; ++k) st->T[k] = T0[k];
-  st->l1_0 = st->l1 = 0.0;
-  st->n_assoc = 0;
-  st->iters = st->converged = st->done = st->evals = 0;
+__device__ void icp_init_dev(IcpState &st, const double *T0, const IcpArgs &a, float *M, int *skip) {
+  for (int k = 0; k < 16; ++k) st.T[k] = T0[k];
+  st.l1_0 = st.l1 = 0.0;
+  st.n_assoc = 0;
+  st.iters = st.converged = st.done = st.evals = 0;
   pose_to_m(T0, a.cx, a.cy, a.cz, M);
   *skip = 0;
 }
 
+__global__ void k_icp_init(IcpState *st, const double *T0, IcpArgs a, float *M, int *skip) {
+  icp_init_dev(*st, T0, a, M, skip);
+}
+
 // Gauss-Newton step of point-to-plane ICP: J^T J dx = -J^T e (Cholesky, no damping), then
 // T <- T exp(dx^). A system that is not positive definite ends the iterations unconverged.
-__global__ void k_icp_step(IcpState *st, IcpArgs a, const long long *n, const double *l1,
-                           const double *g, const double *H, float *M, int *skip) {
-  IcpState &s = *st;
+__device__ __noinline__ void icp_step_dev(IcpState &s, const IcpArgs &a, const long long *n,
+                                          const double *l1, const double *g, const double *H,
+                                          float *M, int *skip) {
   if (s.done) {
     *skip = 1;
     return;
@@ -1575,6 +1579,24 @@ __global__ void k_icp_step(IcpState *st, IcpArgs a, const long long *n, const do
   }
   pose_to_m(s.T, a.cx, a.cy, a.cz, M);
   *skip = 0;
+}
+
+__global__ void k_icp_step(IcpState *st, IcpArgs a, const long long *n, const double *l1,
+                           const double *g, const double *H, float *M, int *skip) {
+  icp_step_dev(*st, a, n, l1, g, H, M, skip);
+}
+
+__global__ void k_icp_init_batch(IcpState *st, const double *T0, int n, IcpArgs a, float *Ms,
+                                 int *skip) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) icp_init_dev(st[k], T0 + 16 * (long long)k, a, Ms + 12 * (long long)k, skip + k);
+}
+
+cudaError_t launch_icp_init_batch(IcpState *st, const double *T0, int n, const IcpArgs &a,
+                                  float *Ms, int *skip, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_icp_init_batch<<<(n + 63) / 64, 64, 0, s>>>(st, T0, n, a, Ms, skip);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_icp_init(IcpState *st, const double *T0, const IcpArgs &a, float *M,
@@ -1793,6 +1815,16 @@ __device__ __noinline__ void persist_raster(
   }
 }
 
+template <int MODEL>
+__device__ __noinline__ void persist_raster_icp(
+    const WaveArgs &a, int item, RasterSmem<kPersistTileW[MODEL] * kPersistTileH[MODEL], MODEL> &sm) {
+  const int t1 = min((item + 1) * kPersistTiles[MODEL], a.tg.ntiles);
+  for (int t = item * kPersistTiles[MODEL]; t < t1; ++t) {
+    raster_block<kPersistTileW[MODEL], kPersistTileH[MODEL], kIcp, MODEL>(a, t, 0, sm);
+    __syncthreads();
+  }
+}
+
 __device__ __noinline__ void persist_reduce(const WaveArgs &a, double *vals) {
   reduce_block(a, 0, vals);
 }
@@ -1903,10 +1935,30 @@ __global__ void __launch_bounds__(kThreads, RM_PERSIST_MIN_BLOCKS) k_persist(Bat
           else persist_setup<1>(a, item.z, __ldcg(b.need + 3 * item.x + 1), u.su);
           break;
         case 2:
-          if (a.cam.model == 0) persist_raster<0>(a, item.z, u.r0);
-          else persist_raster<1>(a, item.z, u.r1);
+          if (b.icp) {
+            if (a.cam.model == 0) persist_raster_icp<0>(a, item.z, u.r0);
+            else persist_raster_icp<1>(a, item.z, u.r1);
+          } else {
+            if (a.cam.model == 0) persist_raster<0>(a, item.z, u.r0);
+            else persist_raster<1>(a, item.z, u.r1);
+          }
           break;
         default: persist_reduce(a, u.vals); break;
+      }
+    }
+    if (item.y == 3 && b.icp) {
+      // ICP: every evaluation is followed by a Gauss-Newton step (a no-op once done)
+      __syncthreads();
+      const int p = item.x, it = item.w;
+      if (threadIdx.x == 0) {
+        IcpState st = b.icp[p];
+        icp_step_dev(st, b.icpargs, a.res_n, a.res_l1, a.res_grad, a.res_jtj, b.Ms + 12 * (long long)p,
+                     b.skip + p);
+        b.icp[p] = st;
+      }
+      if (it < b.lm_iters) {
+        for (int t = threadIdx.x; t < a.tg.ntiles; t += blockDim.x) a.counts[t] = 0;
+        if (threadIdx.x == 0) a.vis_count[0] = 0;
       }
     }
     if (item.y == 3 && b.lm) {
@@ -1946,7 +1998,7 @@ __global__ void __launch_bounds__(kThreads, RM_PERSIST_MIN_BLOCKS) k_persist(Bat
             eq = make_int4(3, 1, 0, it);
           }
         }
-      } else if (b.lm && it < b.lm_iters) {
+      } else if ((b.lm || b.icp) && it < b.lm_iters) {
         b.done[4 * p + 0] = 0;
         b.done[4 * p + 1] = 0;
         b.done[4 * p + 2] = 0;

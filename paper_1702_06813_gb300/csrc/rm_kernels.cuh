@@ -108,6 +108,8 @@ struct IcpArgs {
 
 cudaError_t launch_icp_init(IcpState *st, const double *T0, const IcpArgs &a, float *M,
                             int *skip, cudaStream_t s);
+cudaError_t launch_icp_init_batch(IcpState *st, const double *T0, int n, const IcpArgs &a,
+                                  float *Ms, int *skip, cudaStream_t s);
 // After an evaluation at the state's pose (outputs n, l1, g = J^T e, H = J^T J): record it,
 // solve, move the pose and write its matrix, or set *skip when the iterations are over.
 cudaError_t launch_icp_step(IcpState *st, const IcpArgs &a, const long long *n,
@@ -183,10 +185,13 @@ struct BatchArgs {
   int *need;               // per problem: cull items, setup items (set by the kernel each
                            // evaluation from the visible-cluster count), raster items
   LMState *lm;             // per problem, or null for a plain evaluation
+  IcpState *icp;           // per problem for ICP alignment (raster in ICP mode), else null
+  IcpArgs icpargs;
   float *Ms;               // 12 floats per problem (the problems' a.Ms point here)
   int *skip;               // one flag per problem (the problems' a.skip point here)
   LMArgs lmargs;
-  int lm_iters;            // LM iterations (evaluations 0..lm_iters)
+  int lm_iters;            // LM (or ICP) iterations after the first evaluation (evaluations
+                           // 0..lm_iters)
   unsigned *status;
   long long spin_limit;    // cycles a CTA may go without finding work before it gives up
 };

@@ -3,9 +3,10 @@
 // One CTA per (64x16 output tile, image), fused: the tile's depths with a halo of r + 1
 // pixels are staged in shared memory as (depth, validity) pairs (invalid pixels contribute
 // neither), smoothed with the separable Gaussian as a normalised convolution (a horizontal
-// pass of weighted sums and weight sums, then a vertical pass; one instantiation per radius,
-// so the taps unroll with their weights in registers), and the smoothed depth S over the
-// tile plus a one-pixel ring feeds
+// pass of weighted sums and weight sums, four outputs per thread sliding along a row, then a
+// vertical pass, six per thread down a column; one instantiation per radius, so the taps
+// unroll with their weights in registers), and the smoothed depth S over the tile plus a
+// one-pixel ring feeds
 // the central differences and the normal N = a x b with a = (0, s_y, dz/dy) and
 // b = (s_x, 0, dz/dx). Each depth and class byte is read once from HBM and each normal
 // written once (17 bytes per pixel); the kernel is bound by HBM bandwidth.
@@ -23,6 +24,8 @@ constexpr int kMaxR = 16;              // Gaussian radius ceil(3 sigma) for sigm
 constexpr int kSW = kTW + 2;           // smoothed region (tile plus a one-pixel ring)
 constexpr int kSH = kTH + 2;
 constexpr int kThreadsN = 256;
+constexpr int kHG = 4;                 // horizontal pass: outputs per thread along a row
+constexpr int kVG = 6;                 // vertical pass: outputs per thread down a column
 
 struct NormalArgs {
   const float *depth;
@@ -92,37 +95,66 @@ __global__ void __launch_bounds__(kThreadsN) k_depth_normals(NormalArgs a) {
     }
   }
   __syncthreads();
-  // horizontal pass: weighted sums of the valid depths and of their weights
-  for (int k = tid; k < dh * kSW; k += kThreadsN) {
-    const int v = k / kSW, u = k % kSW;
-    const float2 *row = sz + v * dw + u;  // output u: staged columns u .. u + 2R
-    float num = 0.0f, den = 0.0f;
+  // horizontal pass: weighted sums of the valid depths and of their weights, kHG adjacent
+  // outputs per thread: each staged value is loaded once and added to every output whose
+  // window holds it (the taps unroll: R is a template parameter)
+  {
+    constexpr int groups = (kSW + kHG - 1) / kHG;
+    for (int it = tid; it < dh * groups; it += kThreadsN) {
+      const int v = it / groups, u0 = (it % groups) * kHG;
+      float num[kHG], den[kHG];
 #pragma unroll
-    for (int t = 0; t <= 2 * R; ++t) {
-      const float2 zv = row[t];
-      const float w = g[t < R ? R - t : t - R];
-      num = fmaf(w, zv.x, num);
-      den = fmaf(w, zv.y, den);
+      for (int j = 0; j < kHG; ++j) num[j] = den[j] = 0.0f;
+      const float2 *row = sz + v * dw + u0;  // output u0 + j: staged columns u0 + j .. + 2R
+#pragma unroll
+      for (int t = 0; t < 2 * R + kHG; ++t) {
+        const float2 zv = (u0 + t < dw) ? row[t] : make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int j = 0; j < kHG; ++j) {
+          const int d = t - j;
+          if (d >= 0 && d <= 2 * R) {
+            const float w = g[d < R ? R - d : d - R];
+            num[j] = fmaf(w, zv.x, num[j]);
+            den[j] = fmaf(w, zv.y, den[j]);
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < kHG; ++j)
+        if (u0 + j < kSW) sh[v * kSW + u0 + j] = make_float2(num[j], den[j]);
     }
-    sh[k] = make_float2(num, den);
   }
   __syncthreads();
-  // vertical pass: the smoothed depth where the centre pixel is valid
-  for (int k = tid; k < kSH * kSW; k += kThreadsN) {
-    const int v = k / kSW, u = k % kSW;
-    float s = __int_as_float(0x7fc00000);
-    if (sz[(v + R) * dw + (u + R)].y != 0.0f) {
-      float num = 0.0f, den = 0.0f;
+  // vertical pass: kVG outputs per thread down a column; S where the centre pixel is valid
+  {
+    constexpr int groups = (kSH + kVG - 1) / kVG;
+    for (int it = tid; it < kSW * groups; it += kThreadsN) {
+      const int u = it % kSW, v0 = (it / kSW) * kVG;
+      float num[kVG], den[kVG];
 #pragma unroll
-      for (int t = 0; t <= 2 * R; ++t) {
-        const float2 hv = sh[(v + t) * kSW + u];
-        const float w = g[t < R ? R - t : t - R];
-        num = fmaf(w, hv.x, num);
-        den = fmaf(w, hv.y, den);
+      for (int j = 0; j < kVG; ++j) num[j] = den[j] = 0.0f;
+#pragma unroll
+      for (int t = 0; t < 2 * R + kVG; ++t) {
+        const float2 hv = (v0 + t < dh) ? sh[(v0 + t) * kSW + u] : make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int j = 0; j < kVG; ++j) {
+          const int d = t - j;
+          if (d >= 0 && d <= 2 * R) {
+            const float w = g[d < R ? R - d : d - R];
+            num[j] = fmaf(w, hv.x, num[j]);
+            den[j] = fmaf(w, hv.y, den[j]);
+          }
+        }
       }
-      s = num / den;
+#pragma unroll
+      for (int j = 0; j < kVG; ++j) {
+        const int v = v0 + j;
+        if (v < kSH) {
+          const bool centre = sz[(v + R) * dw + (u + R)].y != 0.0f;
+          sS[v * kSW + u] = centre ? num[j] / den[j] : __int_as_float(0x7fc00000);
+        }
+      }
     }
-    sS[k] = s;
   }
   __syncthreads();
   for (int k = tid; k < kTW * kTH; k += kThreadsN) {

@@ -491,3 +491,20 @@ def align_batch(m: Map, problems=None, params=None, max_iters=5, lambda0=1e-3, l
     del keep
     reports = [{f: getattr(r, f) for f, _ in N.rm_align_report._fields_ if f != "reserved"} for r in reps]
     return out.reshape(n, 4, 4), reports, N.STATUS_NAMES[st]
+
+
+def icp_align_batch(m: Map, problems=None, tol=0.1, max_iters=10, step_tol=1e-5, *, scans=None, poses=None):
+    """Point-to-plane ICP for [(Scan, start pose), ...] with every evaluation and step of every
+    problem in one persistent kernel launch. Returns (poses (n,4,4) numpy, reports, status)."""
+    arr, keep = _problems(problems, scans, poses)
+    n = len(arr)
+    out = np.empty((n, 16))
+    reps = (N.rm_icp_report * n)()
+    prm = N.rm_icp_params(float(tol), int(max_iters), float(step_tol))
+    st = lib().rm_icp_align_batch(m.handle, arr, n, ctypes.byref(prm), out.ctypes.data_as(ctypes.c_void_p),
+                                  reps, _stream())
+    if st not in (N.RM_OK, N.RM_ENOTCONV):
+        check(st)
+    del keep
+    reports = [{f: getattr(r, f) for f, _ in N.rm_icp_report._fields_} for r in reps]
+    return out.reshape(n, 4, 4), reports, N.STATUS_NAMES[st]

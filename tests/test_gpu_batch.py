@@ -150,3 +150,26 @@ def test_batch_empty_map_and_nothing_visible():
         assert status in ("RM_OK", "RM_ENOTCONV")
         assert np.allclose(poses, np.eye(4)[None])
         gm.close()
+
+
+def test_batch_icp_equals_single_calls(mixed):
+    """ICP alignment of the mixed batch in one persistent launch: every problem's pose and
+    report equal its rm_icp_align call bit for bit, and the Lidar problems end near the truth."""
+    gm = mixed["gm"]
+    gm.set_tuning()
+    probs = mixed["probs"]
+    poses, reps, status = rm.icp_align_batch(gm, [(pr["gscan"], pr["start"]) for pr in probs], tol=0.5,
+                                             max_iters=8, step_tol=1e-4)
+    for k, pr in enumerate(probs):
+        ps, rs = rm.icp_align(gm, pr["gscan"], pr["start"], tol=0.5, max_iters=8, step_tol=1e-4)
+        assert np.array_equal(poses[k], ps), k
+        for f in ("iters", "converged", "n_assoc", "cost_l1_initial", "cost_l1_final"):
+            assert reps[k][f] == rs[f], (k, f, reps[k][f], rs[f])
+    for k, pr in enumerate(probs):
+        if pr["cam"].model == "spherical":
+            assert reps[k]["converged"] == 1
+            assert np.linalg.norm(poses[k][:3, 3] - pr["gt"][:3, 3]) < 0.02
+    # repeated call (replayed graph) gives the same poses
+    poses2, _, _ = rm.icp_align_batch(gm, [(pr["gscan"], pr["start"]) for pr in probs], tol=0.5,
+                                      max_iters=8, step_tol=1e-4)
+    assert np.array_equal(poses, poses2)
