@@ -52,6 +52,35 @@ def args_():
     return ap.parse_args()
 
 
+# ---- multi-rank plumbing (one process per GPU; each rank evaluates its own batch of poses, so
+# the data path has no collective; only the timing is reduced, max over ranks)
+
+def rank_info():
+    """(world, rank, local rank) from the launcher's environment (1, 0, 0 without one)."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def rank_seed(seed, rank):
+    """Each rank's synthetic batch: the same workload shape, its own candidate poses and scan."""
+    return seed + 17 * rank
+
+
+def max_over_ranks(x, world, device):
+    """The largest of every rank's x (a time): all ranks wait for the slowest."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, units_per_rank, seconds):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -172,7 +201,7 @@ def cpu_baseline(w, min_seconds=1.5):
 
 def run_reference(a):
     """The oracle timed as it stands, same workload and metric (rank 0 only)."""
-    rank = int(os.environ.get("RANK", "0"))
+    rank = rank_info()[1]
     if rank != 0:
         return
     import synth
@@ -566,9 +595,7 @@ def main():
     import torch
     import torch.distributed as dist
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = rank_info()
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -585,7 +612,7 @@ def main():
     from paper_1702_06813_gb300 import _native as N
     import synth
 
-    w = synth.workload_headline(a.seed + 17 * rank, a.poses)
+    w = synth.workload_headline(rank_seed(a.seed, rank), a.poses)
     mesh, cam = w["mesh"], w["cam"]
     gm = rm.Map(mesh.vertices, mesh.faces, mesh.labels)
     intr = rm.Intrinsics.from_camera(cam)
@@ -645,12 +672,9 @@ def main():
         if not bad:
             break
     clocks["remeasured"] = attempt > 0
-    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms = float(ms_t.item())
+    ms = max_over_ranks(ms, world, "cuda")
     ms_per_step = ms / a.steps
-    value = world * n * a.steps / (ms * 1e-3)
+    value = job_rate(world, n * a.steps, ms * 1e-3)
     # per-kernel durations: the same steps again with the library's event profiler on (its
     # waves then run on one stream, so each kernel's interval is its own)
     _, prof = timed(step, a.steps, profile=True)
@@ -696,10 +720,7 @@ def main():
         e2e_step()
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_value = world * n * a.steps / float(e2e_t.item())
+    e2e_value = job_rate(world, n * a.steps, max_over_ranks(e2e_s, world, "cuda"))
     h2d = hp.numel() * 8 + hd.numel() * 4 + hc.numel()
     d2h = n * (6 * 8 + 8 + 8 + 6 * 8 + 21 * 8)
     # sanity: the e2e numbers equal the device path's
