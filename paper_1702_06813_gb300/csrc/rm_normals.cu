@@ -34,7 +34,8 @@ struct NormalArgs {
   float *smoothed;   // optional
   float *blur;       // optional: S where valid, else the input depth
   int W, H, r, metric;
-  float fx, fy;
+  float ifx, ify;    // 1 / fx, 1 / fy
+  float inv_g2;      // 1 / (sum of the taps)^2: the weight sum when every staged pixel is valid
   float g[kMaxR + 1];
 };
 
@@ -66,8 +67,10 @@ __global__ void __launch_bounds__(kThreadsN) k_depth_normals(NormalArgs a) {
   const long long P = (long long)a.W * a.H;
   const float *dimg = a.depth + img * P;
   const uint8_t *cimg = a.cls + img * P;
+  // stage: independent loads, four per thread in flight; note whether every staged pixel is
+  // valid, the common case away from holes and the image border
   constexpr int n_st = dw * dh;
-  // stage: independent loads, four per thread in flight
+  bool mine_valid = true;
   for (int k0 = tid; k0 < n_st; k0 += 4 * kThreadsN) {
     float dv[4];
     int cv[4];
@@ -90,14 +93,16 @@ __global__ void __launch_bounds__(kThreadsN) k_depth_normals(NormalArgs a) {
       const int k = k0 + m * kThreadsN;
       if (k < n_st) {
         const bool ok = cv[m] == 0 && fabsf(dv[m]) <= FLT_MAX;
+        mine_valid = mine_valid && ok;
         sz[k] = ok ? make_float2(dv[m], 1.0f) : make_float2(0.0f, 0.0f);
       }
     }
   }
-  __syncthreads();
-  // horizontal pass: weighted sums of the valid depths and of their weights, kHG adjacent
-  // outputs per thread: each staged value is loaded once and added to every output whose
-  // window holds it (the taps unroll: R is a template parameter)
+  const bool all_valid = __syncthreads_and(mine_valid);
+  // horizontal pass: weighted sums of the valid depths (and of their weights, unless every
+  // staged pixel is valid), kHG adjacent outputs per thread: each staged value is loaded once
+  // and added to every output whose window holds it (the taps unroll: R is a template
+  // parameter)
   {
     constexpr int groups = (kSW + kHG - 1) / kHG;
     for (int it = tid; it < dh * groups; it += kThreadsN) {
@@ -106,16 +111,28 @@ __global__ void __launch_bounds__(kThreadsN) k_depth_normals(NormalArgs a) {
 #pragma unroll
       for (int j = 0; j < kHG; ++j) num[j] = den[j] = 0.0f;
       const float2 *row = sz + v * dw + u0;  // output u0 + j: staged columns u0 + j .. + 2R
+      if (all_valid) {
 #pragma unroll
-      for (int t = 0; t < 2 * R + kHG; ++t) {
-        const float2 zv = (u0 + t < dw) ? row[t] : make_float2(0.0f, 0.0f);
+        for (int t = 0; t < 2 * R + kHG; ++t) {
+          const float z = (u0 + t < dw) ? row[t].x : 0.0f;
 #pragma unroll
-        for (int j = 0; j < kHG; ++j) {
-          const int d = t - j;
-          if (d >= 0 && d <= 2 * R) {
-            const float w = g[d < R ? R - d : d - R];
-            num[j] = fmaf(w, zv.x, num[j]);
-            den[j] = fmaf(w, zv.y, den[j]);
+          for (int j = 0; j < kHG; ++j) {
+            const int d = t - j;
+            if (d >= 0 && d <= 2 * R) num[j] = fmaf(g[d < R ? R - d : d - R], z, num[j]);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int t = 0; t < 2 * R + kHG; ++t) {
+          const float2 zv = (u0 + t < dw) ? row[t] : make_float2(0.0f, 0.0f);
+#pragma unroll
+          for (int j = 0; j < kHG; ++j) {
+            const int d = t - j;
+            if (d >= 0 && d <= 2 * R) {
+              const float w = g[d < R ? R - d : d - R];
+              num[j] = fmaf(w, zv.x, num[j]);
+              den[j] = fmaf(w, zv.y, den[j]);
+            }
           }
         }
       }
@@ -133,25 +150,40 @@ __global__ void __launch_bounds__(kThreadsN) k_depth_normals(NormalArgs a) {
       float num[kVG], den[kVG];
 #pragma unroll
       for (int j = 0; j < kVG; ++j) num[j] = den[j] = 0.0f;
+      if (all_valid) {
 #pragma unroll
-      for (int t = 0; t < 2 * R + kVG; ++t) {
-        const float2 hv = (v0 + t < dh) ? sh[(v0 + t) * kSW + u] : make_float2(0.0f, 0.0f);
+        for (int t = 0; t < 2 * R + kVG; ++t) {
+          const float h = (v0 + t < dh) ? sh[(v0 + t) * kSW + u].x : 0.0f;
 #pragma unroll
-        for (int j = 0; j < kVG; ++j) {
-          const int d = t - j;
-          if (d >= 0 && d <= 2 * R) {
-            const float w = g[d < R ? R - d : d - R];
-            num[j] = fmaf(w, hv.x, num[j]);
-            den[j] = fmaf(w, hv.y, den[j]);
+          for (int j = 0; j < kVG; ++j) {
+            const int d = t - j;
+            if (d >= 0 && d <= 2 * R) num[j] = fmaf(g[d < R ? R - d : d - R], h, num[j]);
           }
         }
-      }
 #pragma unroll
-      for (int j = 0; j < kVG; ++j) {
-        const int v = v0 + j;
-        if (v < kSH) {
-          const bool centre = sz[(v + R) * dw + (u + R)].y != 0.0f;
-          sS[v * kSW + u] = centre ? num[j] / den[j] : __int_as_float(0x7fc00000);
+        for (int j = 0; j < kVG; ++j)
+          if (v0 + j < kSH) sS[(v0 + j) * kSW + u] = num[j] * a.inv_g2;
+      } else {
+#pragma unroll
+        for (int t = 0; t < 2 * R + kVG; ++t) {
+          const float2 hv = (v0 + t < dh) ? sh[(v0 + t) * kSW + u] : make_float2(0.0f, 0.0f);
+#pragma unroll
+          for (int j = 0; j < kVG; ++j) {
+            const int d = t - j;
+            if (d >= 0 && d <= 2 * R) {
+              const float w = g[d < R ? R - d : d - R];
+              num[j] = fmaf(w, hv.x, num[j]);
+              den[j] = fmaf(w, hv.y, den[j]);
+            }
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < kVG; ++j) {
+          const int v = v0 + j;
+          if (v < kSH) {
+            const bool centre = sz[(v + R) * dw + (u + R)].y != 0.0f;
+            sS[v * kSW + u] = centre ? num[j] / den[j] : __int_as_float(0x7fc00000);
+          }
         }
       }
     }
@@ -172,7 +204,7 @@ __global__ void __launch_bounds__(kThreadsN) k_depth_normals(NormalArgs a) {
     if (x >= 1 && x + 1 < a.W && y >= 1 && y + 1 < a.H && !isnan(s) && !isnan(sl) && !isnan(sr) &&
         !isnan(su) && !isnan(sd)) {
       const float zx = 0.5f * (sr - sl), zy = 0.5f * (sd - su);
-      const float sx = a.metric ? s / a.fx : 1.0f, sy = a.metric ? s / a.fy : 1.0f;
+      const float sx = a.metric ? s * a.ifx : 1.0f, sy = a.metric ? s * a.ify : 1.0f;
       // a = (0, sy, zy), b = (sx, 0, zx), N = a x b
       const float c0 = sy * zx, c1 = zy * sx, c2 = -sy * sx;
       const float inv = rsqrtf(c0 * c0 + c1 * c1 + c2 * c2);
@@ -266,10 +298,13 @@ rm_status run_normals(const rm_intrinsics *intr, int32_t n, const float *depth, 
     a.H = intr->height;
     a.r = sigma > 0.0f ? (int)std::ceil(3.0 * (double)sigma) : 0;
     a.metric = metric;
-    a.fx = intr->fx;
-    a.fy = intr->fy;
+    a.ifx = metric ? 1.0f / intr->fx : 1.0f;
+    a.ify = metric ? 1.0f / intr->fy : 1.0f;
     for (int k = 0; k <= kMaxR; ++k)
       a.g[k] = sigma > 0.0f ? (float)std::exp(-(double)(k * k) / (2.0 * (double)sigma * sigma)) : 1.0f;
+    double gs = a.g[0];
+    for (int k = 1; k <= a.r; ++k) gs += 2.0 * a.g[k];
+    a.inv_g2 = (float)(1.0 / (gs * gs));
     const int tiles = ((a.W + kTW - 1) / kTW) * ((a.H + kTH - 1) / kTH);
     ck(launch_normals<0>(a, tiles, n, s));
   }

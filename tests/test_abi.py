@@ -52,6 +52,19 @@ def test_argument_errors_without_gpu(lib):
     assert lib.rm_icp_align(None, None, None, None, None, None, None) == N.RM_EINVAL
     assert lib.rm_meshify(None, None, None, None, None, None, None, None) == N.RM_EINVAL
     assert lib.rm_dfo_align(None, None, None, None, None, None, None, None) == N.RM_EINVAL
+    assert lib.rm_icp_align_batch(None, None, 1, None, None, None, None) == N.RM_EINVAL
+    assert lib.rm_cost_grad_vertices(None, None, None, 1, None, None, None) == N.RM_EINVAL
+    assert lib.rm_depth_blur(None, 1, None, None, 1.0, None, None) == N.RM_EINVAL
+    assert lib.rm_scan_from_range(None, 10, 4.0, 0.5, None, None, None) == N.RM_EINVAL   # min > max
+    assert lib.rm_scan_from_range(None, -1, 0.5, 4.0, None, None, None) == N.RM_EINVAL
+    assert lib.rm_scan_from_range(None, 0, 0.5, 4.0, None, None, None) == N.RM_OK        # nothing to do
+    assert lib.rm_pose_from_x(None, -1, None, None) == N.RM_EINVAL
+    assert lib.rm_pose_from_x(None, 0, None, None) == N.RM_OK
+    intr = N.rm_intrinsics()
+    intr.width, intr.height = 8, 8
+    assert lib.rm_depth_normals(ctypes.byref(intr), 1, None, None, 9.0, 0, None, None, None) == N.RM_EINVAL
+    assert lib.rm_depth_normals(ctypes.byref(intr), 1, None, None, 1.0, 1, None, None, None) == N.RM_EINVAL
+    assert lib.rm_depth_normals(ctypes.byref(intr), 0, None, None, 1.0, 0, None, None, None) == N.RM_OK
     assert lib.rm_depth_normals(None, 1, None, None, 1.0, 0, None, None, None) == N.RM_EINVAL
 
 
