@@ -977,6 +977,105 @@ rm_status run_batch(rm_map *m, const rm_problem *probs, int n, const rm_cost_par
   }
 }
 
+// ---- single-pose device loops (rm_align, rm_icp_align, rm_dfo_align)
+
+// The arrays every such loop carves after its own state and results: the start pose, the
+// matrices of its S poses per evaluation, a skip flag, the staged scan and rays (host inputs
+// only) and the wave scratch for S poses. Planned and carved by the same function, so the
+// two passes agree.
+struct LoopBufs {
+  double *T0;
+  float *M;
+  int *skip;
+  const float *sd, *rays;
+  const uint8_t *sc;
+  int4 *vis;
+  int *vis_count, *counts;
+  unsigned char *bins;
+  double *partial;
+};
+
+void loop_arrays(Carver &cv, const rm_map *m, const rm_scan *scan, const TileGeom &tg, int S,
+                 LoopBufs *b) {
+  const rm_intrinsics *in = &scan->intr;
+  const long long P = (long long)in->width * in->height;
+  b->T0 = cv.take<double>(16);
+  b->M = cv.take<float>(12 * (size_t)S);
+  b->skip = cv.take<int>(1);
+  b->sd = on_device(scan->depth) ? scan->depth : cv.take<float>(P);
+  b->sc = on_device(scan->cls) ? scan->cls : cv.take<uint8_t>(P);
+  b->rays = (in->model != RM_RAYTABLE || on_device(in->rays)) ? in->rays : cv.take<float>(3 * P);
+  b->vis = cv.take<int4>((size_t)m->n_clusters * S);
+  b->vis_count = cv.take<int>(S);
+  b->counts = cv.take<int>((size_t)tg.ntiles * S);
+  b->bins = cv.take<unsigned char>((size_t)tg.ntiles * tg.cap * tg.rec_bytes * S);
+  b->partial = cv.take<double>((size_t)tg.ntiles * rmk::kNumVals * S);
+}
+
+// The loop's wave over its S poses (result pointers are the caller's), and the copies of its
+// host inputs (start pose, scan, rays) into the staged arrays.
+WaveArgs loop_wave(const rm_map *m, const rm_scan *scan, const TileGeom &tg, int S, const LoopBufs &b,
+                   const rm_cost_params &prm) {
+  WaveArgs a{};
+  a.cam = make_cam(&scan->intr, b.rays);
+  a.tg = tg;
+  a.V = (int)m->V;
+  a.T = m->T;
+  a.n_poses = S;
+  a.wave_base = 0;
+  a.v = m->d_v;
+  a.faces = m->d_faces;
+  a.planes = m->d_planes;
+  a.Ms = b.M;
+  set_clusters(m, a);
+  a.vis = b.vis;
+  a.vis_count = b.vis_count;
+  a.counts = b.counts;
+  a.bins = b.bins;
+  a.partial = b.partial;
+  a.status = m->d_status;
+  a.skip = b.skip;
+  a.scan_depth = b.sd;
+  a.scan_cls = b.sc;
+  a.prm = {prm.eps, prm.w_fofo, prm.w_fofu, prm.w_fufo};
+  return a;
+}
+
+rm_status loop_inputs(const rm_scan *scan, const double *init_pose, const LoopBufs &b, cudaStream_t s) {
+  const rm_intrinsics *in = &scan->intr;
+  const long long P = (long long)in->width * in->height;
+  RM_CK(cudaMemcpyAsync(b.T0, init_pose, sizeof(double) * 16,
+                        on_device(init_pose) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  if (b.rays != in->rays)
+    RM_CK(cudaMemcpyAsync((void *)b.rays, in->rays, sizeof(float) * 3 * P, cudaMemcpyHostToDevice, s));
+  if (b.sd != scan->depth)
+    RM_CK(cudaMemcpyAsync((void *)b.sd, scan->depth, sizeof(float) * P, cudaMemcpyHostToDevice, s));
+  if (b.sc != scan->cls) RM_CK(cudaMemcpyAsync((void *)b.sc, scan->cls, P, cudaMemcpyHostToDevice, s));
+  return RM_OK;
+}
+
+// After a loop: read its state back (synchronising), and map the status word to the call's
+// result: RM_OK, an error, or "grow the bins and run again" (*retry).
+rm_status loop_finish(rm_map *m, cudaStream_t s, void *host_state, const void *dev_state, size_t bytes,
+                      int attempt, bool *retry) {
+  *retry = false;
+  RM_CK(cudaMemcpyAsync(host_state, dev_state, bytes, cudaMemcpyDeviceToHost, s));
+  unsigned st = 0;
+  RM_TRY(read_status(m, s, &st));  // synchronises the stream
+  if (st & rmk::kStatusTimeout) return fail(RM_ETIMEOUT, "a device-side wait ran out of time");
+  if (st & (rmk::kStatusOverflow | rmk::kStatusOverflowRay)) {
+    RM_TRY(grow_bins(m, st, attempt));
+    *retry = true;
+  }
+  return RM_OK;
+}
+
+rm_status write_pose(double *pose_out, const double *T) {
+  if (on_device(pose_out)) RM_CK(cudaMemcpy(pose_out, T, sizeof(double) * 16, cudaMemcpyHostToDevice));
+  else std::memcpy(pose_out, T, sizeof(double) * 16);
+  return RM_OK;
+}
+
 }  // namespace
 
 namespace rmapi {
@@ -1387,97 +1486,50 @@ rm_status rm_align(rm_map *m, const rm_scan *scan, const double *init_pose,
   const rm_intrinsics *in = &scan->intr;
   RM_TRY(check_intr(in));
   RM_CK(cudaSetDevice(m->device));
-  const long long P = (long long)in->width * in->height;
-  const bool host_scan = !on_device(scan->depth), host_cls = !on_device(scan->cls);
-  const bool host_rays = in->model == RM_RAYTABLE && !on_device(in->rays);
   for (int attempt = 0;; ++attempt) {
     TileGeom tg = make_tiles(m, in);
+    LoopBufs lb;
+    auto arrays = [&](Carver &cv, rmk::LMState **st, long long **counts, long long **et, double **els,
+                      double **grad, double **jtj) {
+      *st = cv.take<rmk::LMState>(1);
+      *counts = cv.take<long long>(6);
+      *et = cv.take<long long>(1);
+      *els = cv.take<double>(1);
+      *grad = cv.take<double>(6);
+      *jtj = cv.take<double>(21);
+      loop_arrays(cv, m, scan, tg, 1, &lb);
+    };
+    rmk::LMState *d_st;
+    long long *d_counts, *d_etable;
+    double *d_els, *d_grad, *d_jtj;
     Carver plan{nullptr};
-    plan.take<rmk::LMState>(1);
-    if (host_rays) plan.take<float>(3 * P);
-    plan.take<double>(16);
-    plan.take<float>(12);
-    plan.take<int>(1);
-    if (host_scan) plan.take<float>(P);
-    if (host_cls) plan.take<uint8_t>(P);
-    plan.take<long long>(6);
-    plan.take<long long>(1);
-    plan.take<double>(1);
-    plan.take<double>(6);
-    plan.take<double>(21);
-    plan.take<int4>(m->n_clusters);
-    plan.take<int>(1);
-    plan.take<int>(tg.ntiles);
-    plan.take<unsigned char>((size_t)tg.ntiles * tg.cap * tg.rec_bytes);
-    plan.take<double>((size_t)tg.ntiles * rmk::kNumVals);
+    arrays(plan, &d_st, &d_counts, &d_etable, &d_els, &d_grad, &d_jtj);
     RM_TRY(ensure_arena(m, plan.off, s));
     m->batch_inputs_valid = false;
     Carver cv{m->arena};
-    rmk::LMState *d_st = cv.take<rmk::LMState>(1);
-    const float *d_rays = host_rays ? cv.take<float>(3 * P) : in->rays;
-    double *d_T0 = cv.take<double>(16);
-    float *d_M = cv.take<float>(12);
-    int *d_skip = cv.take<int>(1);
-    const float *d_sd = host_scan ? cv.take<float>(P) : scan->depth;
-    const uint8_t *d_sc = host_cls ? cv.take<uint8_t>(P) : scan->cls;
-    long long *d_counts = cv.take<long long>(6);
-    long long *d_etable = cv.take<long long>(1);
-    double *d_els = cv.take<double>(1);
-    double *d_grad = cv.take<double>(6);
-    double *d_jtj = cv.take<double>(21);
-    WaveArgs a{};
-    a.cam = make_cam(in, d_rays);
-    a.tg = tg;
-    a.V = (int)m->V;
-    a.T = m->T;
-    a.n_poses = 1;
-    a.wave_base = 0;
-    a.v = m->d_v;
-    a.faces = m->d_faces;
-    a.planes = m->d_planes;
-    a.Ms = d_M;
-    set_clusters(m, a);
-    a.vis = cv.take<int4>(m->n_clusters);
-    a.vis_count = cv.take<int>(1);
-    a.counts = cv.take<int>(tg.ntiles);
-    a.bins = cv.take<unsigned char>((size_t)tg.ntiles * tg.cap * tg.rec_bytes);
-    a.partial = cv.take<double>((size_t)tg.ntiles * rmk::kNumVals);
-    a.status = m->d_status;
-    a.skip = d_skip;
-    a.scan_depth = d_sd;
-    a.scan_cls = d_sc;
-    a.prm = {prm->eps, prm->w_fofo, prm->w_fofu, prm->w_fufo};
+    arrays(cv, &d_st, &d_counts, &d_etable, &d_els, &d_grad, &d_jtj);
+    WaveArgs a = loop_wave(m, scan, tg, 1, lb, *prm);
     a.res_counts = d_counts;
     a.res_etable = d_etable;
     a.res_els = d_els;
     a.res_grad = d_grad;
     a.res_jtj = d_jtj;
-    RM_CK(cudaMemcpyAsync(d_T0, init_pose, sizeof(double) * 16,
-                          on_device(init_pose) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
-    if (host_rays) RM_CK(cudaMemcpyAsync((void *)d_rays, in->rays, sizeof(float) * 3 * P, cudaMemcpyHostToDevice, s));
-    if (host_scan) RM_CK(cudaMemcpyAsync((void *)d_sd, scan->depth, sizeof(float) * P, cudaMemcpyHostToDevice, s));
-    if (host_cls) RM_CK(cudaMemcpyAsync((void *)d_sc, scan->cls, P, cudaMemcpyHostToDevice, s));
+    RM_TRY(loop_inputs(scan, init_pose, lb, s));
     rmk::LMArgs la{lm->lambda0, lm->lambda_up, lm->lambda_down, lm->step_tol,
                    m->centre[0], m->centre[1], m->centre[2]};
-    RM_CK(rmk::launch_lm_init(d_st, d_T0, la, d_M, d_skip, s));
+    RM_CK(rmk::launch_lm_init(d_st, lb.T0, la, lb.M, lb.skip, s));
     RM_TRY(wave(m, a, rmk::kCostGrad, s));
     RM_CK(rmk::launch_lm_take_initial(d_st, d_counts, d_els, d_grad, d_jtj, s));
     for (int it = 0; it < lm->max_iters; ++it) {
-      RM_CK(rmk::launch_lm_propose(d_st, la, d_M, d_skip, s));
+      RM_CK(rmk::launch_lm_propose(d_st, la, lb.M, lb.skip, s));
       RM_TRY(wave(m, a, rmk::kCostGrad, s));
-      RM_CK(rmk::launch_lm_accept(d_st, la, d_counts, d_els, d_grad, d_jtj, d_skip, s));
+      RM_CK(rmk::launch_lm_accept(d_st, la, d_counts, d_els, d_grad, d_jtj, lb.skip, s));
     }
     rmk::LMState hs;
-    RM_CK(cudaMemcpyAsync(&hs, d_st, sizeof(hs), cudaMemcpyDeviceToHost, s));
-    unsigned st = 0;
-    RM_TRY(read_status(m, s, &st));  // synchronises the stream
-    if (st & rmk::kStatusTimeout) return fail(RM_ETIMEOUT, "a device-side wait ran out of time");
-    if (st & (rmk::kStatusOverflow | rmk::kStatusOverflowRay)) {
-      RM_TRY(grow_bins(m, st, attempt));
-      continue;
-    }
-    if (on_device(pose_out)) RM_CK(cudaMemcpy(pose_out, hs.T, sizeof(double) * 16, cudaMemcpyHostToDevice));
-    else std::memcpy(pose_out, hs.T, sizeof(double) * 16);
+    bool retry;
+    RM_TRY(loop_finish(m, s, &hs, d_st, sizeof(hs), attempt, &retry));
+    if (retry) continue;
+    RM_TRY(write_pose(pose_out, hs.T));
     if (rep) {
       rep->iters = hs.iters;
       rep->accepted = hs.accepted;
@@ -1510,71 +1562,31 @@ rm_status rm_dfo_align(rm_map *m, const rm_scan *scan, const double *init_pose,
   const rm_intrinsics *in = &scan->intr;
   RM_TRY(check_intr(in));
   RM_CK(cudaSetDevice(m->device));
-  const long long P = (long long)in->width * in->height;
-  const bool host_scan = !on_device(scan->depth), host_cls = !on_device(scan->cls);
-  const bool host_rays = in->model == RM_RAYTABLE && !on_device(in->rays);
   const int S = rmk::kDfoSlots;
   for (int attempt = 0;; ++attempt) {
     TileGeom tg = make_tiles(m, in);
+    LoopBufs lb;
+    auto arrays = [&](Carver &cv, rmk::DfoState **st, long long **counts, long long **et, double **els) {
+      *st = cv.take<rmk::DfoState>(1);
+      *counts = cv.take<long long>(6 * S);
+      *et = cv.take<long long>(S);
+      *els = cv.take<double>(S);
+      loop_arrays(cv, m, scan, tg, S, &lb);
+    };
+    rmk::DfoState *d_st;
+    long long *d_counts, *d_et;
+    double *d_els;
     Carver plan{nullptr};
-    plan.take<rmk::DfoState>(1);
-    if (host_rays) plan.take<float>(3 * P);
-    plan.take<double>(16);
-    plan.take<float>(12 * S);
-    plan.take<int>(1);
-    if (host_scan) plan.take<float>(P);
-    if (host_cls) plan.take<uint8_t>(P);
-    plan.take<long long>(6 * S);
-    plan.take<long long>(S);
-    plan.take<double>(S);
-    plan.take<int4>((size_t)m->n_clusters * S);
-    plan.take<int>(S);
-    plan.take<int>((size_t)tg.ntiles * S);
-    plan.take<unsigned char>((size_t)tg.ntiles * tg.cap * tg.rec_bytes * S);
-    plan.take<double>((size_t)tg.ntiles * rmk::kNumVals * S);
+    arrays(plan, &d_st, &d_counts, &d_et, &d_els);
     RM_TRY(ensure_arena(m, plan.off, s));
     m->batch_inputs_valid = false;
     Carver cv{m->arena};
-    rmk::DfoState *d_st = cv.take<rmk::DfoState>(1);
-    const float *d_rays = host_rays ? cv.take<float>(3 * P) : in->rays;
-    double *d_T0 = cv.take<double>(16);
-    float *d_M = cv.take<float>(12 * S);
-    int *d_skip = cv.take<int>(1);
-    const float *d_sd = host_scan ? cv.take<float>(P) : scan->depth;
-    const uint8_t *d_sc = host_cls ? cv.take<uint8_t>(P) : scan->cls;
-    long long *d_counts = cv.take<long long>(6 * S);
-    long long *d_et = cv.take<long long>(S);
-    double *d_els = cv.take<double>(S);
-    WaveArgs a{};
-    a.cam = make_cam(in, d_rays);
-    a.tg = tg;
-    a.V = (int)m->V;
-    a.T = m->T;
-    a.n_poses = S;
-    a.wave_base = 0;
-    a.v = m->d_v;
-    a.faces = m->d_faces;
-    a.planes = m->d_planes;
-    a.Ms = d_M;
-    set_clusters(m, a);
-    a.vis = cv.take<int4>((size_t)m->n_clusters * S);
-    a.vis_count = cv.take<int>(S);
-    a.counts = cv.take<int>((size_t)tg.ntiles * S);
-    a.bins = cv.take<unsigned char>((size_t)tg.ntiles * tg.cap * tg.rec_bytes * S);
-    a.partial = cv.take<double>((size_t)tg.ntiles * rmk::kNumVals * S);
-    a.status = m->d_status;
-    a.skip = d_skip;
-    a.scan_depth = d_sd;
-    a.scan_cls = d_sc;
-    a.prm = {prm->eps, prm->w_fofo, prm->w_fofu, prm->w_fufo};
+    arrays(cv, &d_st, &d_counts, &d_et, &d_els);
+    WaveArgs a = loop_wave(m, scan, tg, S, lb, *prm);
     a.res_counts = d_counts;
     a.res_etable = d_et;
     a.res_els = d_els;
-    RM_CK(cudaMemcpyAsync(d_T0, init_pose, sizeof(double) * 16,
-                          on_device(init_pose) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
-    if (host_rays) RM_CK(cudaMemcpyAsync((void *)d_rays, in->rays, sizeof(float) * 3 * P, cudaMemcpyHostToDevice, s));
-    if (host_scan) RM_CK(cudaMemcpyAsync((void *)d_sd, scan->depth, sizeof(float) * P, cudaMemcpyHostToDevice, s));
-    if (host_cls) RM_CK(cudaMemcpyAsync((void *)d_sc, scan->cls, P, cudaMemcpyHostToDevice, s));
+    RM_TRY(loop_inputs(scan, init_pose, lb, s));
     rmk::DfoArgs da{};
     da.nm_iters = dp->nm_iters;
     da.cd_iters = dp->cd_iters;
@@ -1589,29 +1601,24 @@ rm_status rm_dfo_align(rm_map *m, const rm_scan *scan, const double *init_pose,
     da.cx = m->centre[0];
     da.cy = m->centre[1];
     da.cz = m->centre[2];
-    RM_CK(rmk::launch_dfo_init(d_st, d_T0, da, d_M, d_skip, s));
+    RM_CK(rmk::launch_dfo_init(d_st, lb.T0, da, lb.M, lb.skip, s));
     m->launches += 1;
     // at most: the simplex, two batches per Nelder-Mead iteration, one per descent step
     const int max_steps = 1 + 2 * dp->nm_iters + dp->cd_iters;
     for (int it = 0; it < max_steps; ++it) {
       RM_TRY(wave(m, a, rmk::kCost, s));
-      RM_CK(rmk::launch_dfo_step(d_st, da, d_et, d_M, d_skip, s));
+      RM_CK(rmk::launch_dfo_step(d_st, da, d_et, lb.M, lb.skip, s));
       m->launches += 1;
     }
     rmk::DfoState hs;
-    RM_CK(cudaMemcpyAsync(&hs, d_st, sizeof(hs), cudaMemcpyDeviceToHost, s));
-    unsigned stw = 0;
-    RM_TRY(read_status(m, s, &stw));  // synchronises the stream
-    if (stw & rmk::kStatusTimeout) return fail(RM_ETIMEOUT, "a device-side wait ran out of time");
-    if (stw & (rmk::kStatusOverflow | rmk::kStatusOverflowRay)) {
-      RM_TRY(grow_bins(m, stw, attempt));
-      continue;
-    }
+    bool retry;
+    RM_TRY(loop_finish(m, s, &hs, d_st, sizeof(hs), attempt, &retry));
+    if (retry) continue;
     // the final pose T0 exp(xc^) on the device, through the library's retraction
     double *d_xi = reinterpret_cast<double *>(d_counts);  // 6 doubles of scratch
     double *d_out = d_xi + 6;
     RM_CK(cudaMemcpyAsync(d_xi, hs.xc, sizeof(double) * 6, cudaMemcpyHostToDevice, s));
-    RM_CK(rmk::launch_retract(d_T0, d_xi, 1, d_out, nullptr, s));
+    RM_CK(rmk::launch_retract(lb.T0, d_xi, 1, d_out, nullptr, s));
     m->launches += 1;
     RM_CK(cudaMemcpyAsync(pose_out, d_out, sizeof(double) * 16,
                           on_device(pose_out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
@@ -1643,95 +1650,49 @@ rm_status rm_icp_align(rm_map *m, const rm_scan *scan, const double *init_pose,
   const rm_intrinsics *in = &scan->intr;
   RM_TRY(check_intr(in));
   RM_CK(cudaSetDevice(m->device));
-  const long long P = (long long)in->width * in->height;
-  const bool host_scan = !on_device(scan->depth), host_cls = !on_device(scan->cls);
-  const bool host_rays = in->model == RM_RAYTABLE && !on_device(in->rays);
   for (int attempt = 0;; ++attempt) {
     TileGeom tg = make_tiles(m, in);
+    LoopBufs lb;
+    auto arrays = [&](Carver &cv, rmk::IcpState **st, long long **n, double **l1, double **e2,
+                      double **g, double **H) {
+      *st = cv.take<rmk::IcpState>(1);
+      *n = cv.take<long long>(1);
+      *l1 = cv.take<double>(1);
+      *e2 = cv.take<double>(1);
+      *g = cv.take<double>(6);
+      *H = cv.take<double>(21);
+      loop_arrays(cv, m, scan, tg, 1, &lb);
+    };
+    rmk::IcpState *d_st;
+    long long *d_n;
+    double *d_l1, *d_e2, *d_g, *d_H;
     Carver plan{nullptr};
-    plan.take<rmk::IcpState>(1);
-    if (host_rays) plan.take<float>(3 * P);
-    plan.take<double>(16);
-    plan.take<float>(12);
-    plan.take<int>(1);
-    if (host_scan) plan.take<float>(P);
-    if (host_cls) plan.take<uint8_t>(P);
-    plan.take<long long>(1);
-    plan.take<double>(1);
-    plan.take<double>(1);
-    plan.take<double>(6);
-    plan.take<double>(21);
-    plan.take<int4>(m->n_clusters);
-    plan.take<int>(1);
-    plan.take<int>(tg.ntiles);
-    plan.take<unsigned char>((size_t)tg.ntiles * tg.cap * tg.rec_bytes);
-    plan.take<double>((size_t)tg.ntiles * rmk::kNumVals);
+    arrays(plan, &d_st, &d_n, &d_l1, &d_e2, &d_g, &d_H);
     RM_TRY(ensure_arena(m, plan.off, s));
     m->batch_inputs_valid = false;
     Carver cv{m->arena};
-    rmk::IcpState *d_st = cv.take<rmk::IcpState>(1);
-    const float *d_rays = host_rays ? cv.take<float>(3 * P) : in->rays;
-    double *d_T0 = cv.take<double>(16);
-    float *d_M = cv.take<float>(12);
-    int *d_skip = cv.take<int>(1);
-    const float *d_sd = host_scan ? cv.take<float>(P) : scan->depth;
-    const uint8_t *d_sc = host_cls ? cv.take<uint8_t>(P) : scan->cls;
-    long long *d_n = cv.take<long long>(1);
-    double *d_l1 = cv.take<double>(1);
-    double *d_e2 = cv.take<double>(1);
-    double *d_g = cv.take<double>(6);
-    double *d_H = cv.take<double>(21);
-    WaveArgs a{};
-    a.cam = make_cam(in, d_rays);
-    a.tg = tg;
-    a.V = (int)m->V;
-    a.T = m->T;
-    a.n_poses = 1;
-    a.wave_base = 0;
-    a.v = m->d_v;
-    a.faces = m->d_faces;
-    a.planes = m->d_planes;
-    a.Ms = d_M;
-    set_clusters(m, a);
-    a.vis = cv.take<int4>(m->n_clusters);
-    a.vis_count = cv.take<int>(1);
-    a.counts = cv.take<int>(tg.ntiles);
-    a.bins = cv.take<unsigned char>((size_t)tg.ntiles * tg.cap * tg.rec_bytes);
-    a.partial = cv.take<double>((size_t)tg.ntiles * rmk::kNumVals);
-    a.status = m->d_status;
-    a.skip = d_skip;
-    a.scan_depth = d_sd;
-    a.scan_cls = d_sc;
-    a.prm = {prm->tol, 0.0f, 0.0f, 0.0f};
+    arrays(cv, &d_st, &d_n, &d_l1, &d_e2, &d_g, &d_H);
+    const rm_cost_params cp{prm->tol, 0.0f, 0.0f, 0.0f};
+    WaveArgs a = loop_wave(m, scan, tg, 1, lb, cp);
     a.res_n = d_n;
     a.res_l1 = d_l1;
     a.res_els = d_e2;
     a.res_grad = d_g;
     a.res_jtj = d_H;
-    RM_CK(cudaMemcpyAsync(d_T0, init_pose, sizeof(double) * 16,
-                          on_device(init_pose) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
-    if (host_rays) RM_CK(cudaMemcpyAsync((void *)d_rays, in->rays, sizeof(float) * 3 * P, cudaMemcpyHostToDevice, s));
-    if (host_scan) RM_CK(cudaMemcpyAsync((void *)d_sd, scan->depth, sizeof(float) * P, cudaMemcpyHostToDevice, s));
-    if (host_cls) RM_CK(cudaMemcpyAsync((void *)d_sc, scan->cls, P, cudaMemcpyHostToDevice, s));
+    RM_TRY(loop_inputs(scan, init_pose, lb, s));
     const rmk::IcpArgs ia{prm->step_tol, m->centre[0], m->centre[1], m->centre[2]};
-    RM_CK(rmk::launch_icp_init(d_st, d_T0, ia, d_M, d_skip, s));
+    RM_CK(rmk::launch_icp_init(d_st, lb.T0, ia, lb.M, lb.skip, s));
     m->launches += 1;
     for (int it = 0; it < prm->max_iters; ++it) {
       RM_TRY(wave(m, a, rmk::kIcp, s));
-      RM_CK(rmk::launch_icp_step(d_st, ia, d_n, d_l1, d_g, d_H, d_M, d_skip, s));
+      RM_CK(rmk::launch_icp_step(d_st, ia, d_n, d_l1, d_g, d_H, lb.M, lb.skip, s));
       m->launches += 1;
     }
     rmk::IcpState hs;
-    RM_CK(cudaMemcpyAsync(&hs, d_st, sizeof(hs), cudaMemcpyDeviceToHost, s));
-    unsigned st = 0;
-    RM_TRY(read_status(m, s, &st));  // synchronises the stream
-    if (st & rmk::kStatusTimeout) return fail(RM_ETIMEOUT, "a device-side wait ran out of time");
-    if (st & (rmk::kStatusOverflow | rmk::kStatusOverflowRay)) {
-      RM_TRY(grow_bins(m, st, attempt));
-      continue;
-    }
-    if (on_device(pose_out)) RM_CK(cudaMemcpy(pose_out, hs.T, sizeof(double) * 16, cudaMemcpyHostToDevice));
-    else std::memcpy(pose_out, hs.T, sizeof(double) * 16);
+    bool retry;
+    RM_TRY(loop_finish(m, s, &hs, d_st, sizeof(hs), attempt, &retry));
+    if (retry) continue;
+    RM_TRY(write_pose(pose_out, hs.T));
     if (rep) {
       rep->iters = hs.iters;
       rep->converged = hs.converged;
