@@ -332,6 +332,36 @@ def run_tracking(a):
         "gpu_launches": a.frames}))
 
 
+def oracle_row_timings(w, dstart, tol=0.1):
+    """The oracle, as it stands, on one unit of each widened row of the 1M-triangle room
+    (single thread; a bounded sample each): ICP terms of one pose, the derivative-free search
+    from dstart, one meshification, the Eq. 2 normals of one image, the vertex gradient of one
+    pose. Seconds per unit."""
+    import oracle
+    oracle.build()
+    mesh, cam = w["mesh"], w["cam"]
+    sd, sc = w["scan"]
+    om = oracle.OracleMap(mesh.vertices, mesh.faces, mesh.labels)
+    out = {}
+
+    def clock(fn):
+        t0 = time.perf_counter()
+        r = fn()
+        return time.perf_counter() - t0, r
+
+    out["icp_terms_s_per_pose"], _ = clock(lambda: om.icp_terms(w["poses"][0], cam, sd, sc, tol))
+    dt, (_, rep) = clock(lambda: om.dfo_align(dstart, cam, sd, sc, dfo=oracle.dfo_params(nm_iters=60, cd_iters=40)))
+    out["dfo_align_s"] = dt
+    out["dfo_evals"] = rep["evals"]
+    out["dfo_e_table_final"] = rep["e_table"]
+    out["meshify_s_per_image"], _ = clock(lambda: oracle.meshify(cam, sd, sc, w["gt"], cam.range_max, 0.1, 1))
+    out["normals_s_per_image"], _ = clock(lambda: oracle.depth_normals(sd, sc, sigma=1.5, metric=True,
+                                                                        fx=cam.fx, fy=cam.fy))
+    out["vertex_grad_s_per_pose"], _ = clock(lambda: om.vertex_grad(w["poses"][0], cam, sd, sc))
+    out["cores"] = 1
+    return out
+
+
 def run_icp(a):
     """Render-accelerated point-to-plane ICP (Sec. IV). Value: ICP term evaluations per second
     (render + projective association + J^T e, J^T J) for the 256 candidate poses of the
@@ -577,6 +607,7 @@ def run_icp(a):
         dt = time.perf_counter() - t0
         line["cpu_baseline"] = {"value": done / dt, "unit": "pose evals/s", "cores": 1, "kind": "oracle",
                                 "sample": f"{done} of the candidate poses, one thread, {dt:.1f} s wall"}
+        line["config"]["oracle_per_row"] = oracle_row_timings(w, dstart, tol)
     print(json.dumps(line))
     gm.close()
 
