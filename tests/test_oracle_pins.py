@@ -447,3 +447,23 @@ def test_lm_converges_noise_free(pitch_deg):
     assert np.linalg.norm(pose[:3, 3] - gt[:3, 3]) < 1e-6
     ang = Rotation.from_matrix(gt[:3, :3].T @ pose[:3, :3]).magnitude()
     assert math.degrees(ang) < 1e-4
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_rigid_invariance_of_depth(seed):
+    """Moving the world and the pose together by one rigid motion G leaves the depth image
+    unchanged, up to the FP32 rounding of the moved vertices (the same surfaces are seen)."""
+    c = cases.config1(seed=2100 + seed)
+    mesh, cam = c["mesh"], c["cam"]
+    r = cases.rng(2200 + seed)
+    G = synth.pose_from(r.uniform(-20, 20, 3), r.uniform(-math.pi, math.pi), r.uniform(-0.5, 0.5),
+                        r.uniform(-0.5, 0.5))
+    v2 = (mesh.vertices.astype(np.float64) @ G[:3, :3].T + G[:3, 3]).astype(np.float32)
+    pose = c["start"]
+    a = oracle.OracleMap(mesh.vertices, mesh.faces, mesh.labels).render(pose, cam)
+    b = oracle.OracleMap(v2, mesh.faces, mesh.labels).render(G @ pose, cam)
+    hit = ~np.isnan(a["depth"])
+    assert np.array_equal(hit, ~np.isnan(b["depth"]))
+    same = a["tri_id"] == b["tri_id"]
+    assert same.mean() > 0.995   # ties at shared edges may go either way after rounding
+    assert np.all(np.abs(b["depth"][hit & same] - a["depth"][hit & same]) <= 1e-5 * a["depth"][hit & same])
