@@ -108,3 +108,33 @@ def test_fullsize_lidar_render_and_cost():
     assert np.linalg.norm(_np(g["grad"])[0] - oc["grad"]) <= EPS_REL_GRAD * np.linalg.norm(oc["grad"])
     assert np.linalg.norm(_np(g["jtj"])[0] - oc["jtj"]) <= EPS_REL_GRAD * np.linalg.norm(oc["jtj"])
     gm.close()
+
+
+def test_fullsize_icp_terms_sampled_poses(head):
+    """ICP terms of the 256 poses in the benchmark's launch configuration (64x32 tiles, two
+    128-pose waves), checked on the first and last pose of each wave: association counts
+    exact, sums within the ICP parity tolerances."""
+    w = head["w"]
+    g = rm.icp_terms(head["gm"], head["scan"], head["poses"], tol=0.1)
+    for k in SAMPLED:
+        o = head["om"].icp_terms(w["poses"][k], w["cam"], *w["scan"], 0.1)
+        assert int(_np(g["n_assoc"])[k]) == o["n_assoc"], k
+        for key in ("cost_l1", "e2"):
+            assert abs(float(_np(g[key])[k]) - o[key]) <= 1e-5 * abs(o[key]), (k, key)
+        assert np.linalg.norm(_np(g["jte"])[k] - o["jte"]) <= 1e-3 * np.linalg.norm(o["jte"]), k
+        assert np.linalg.norm(_np(g["jtj"])[k] - o["jtj"]) <= 1e-4 * np.linalg.norm(o["jtj"]), k
+        assert o["n_assoc"] > 0
+
+
+def test_fullsize_dfo_same_search_as_oracle(head):
+    """The derivative-free search on the full-size room from 3 cm / 1.5 deg (the benchmark's
+    start): the same scored poses, iterations and final Table I cost as the oracle's search."""
+    w = head["w"]
+    r = np.random.Generator(np.random.PCG64(3000 + 9))
+    start = synth.perturb_fixed(w["gt"], r, 0.03, 1.5)
+    pg, rep = rm.dfo_align(head["gm"], head["scan"], start, dfo=rm.dfo_params(nm_iters=60, cd_iters=40))
+    po, orep = head["om"].dfo_align(start, w["cam"], *w["scan"], dfo=oracle.dfo_params(nm_iters=60, cd_iters=40))
+    for key in ("evals", "nm_iters", "nm_shrinks", "cd_iters", "converged"):
+        assert rep[key] == orep[key], (key, rep, orep)
+    assert rep["e_table_final"] == orep["e_table"]
+    assert np.allclose(pg, po, rtol=0, atol=1e-9)
