@@ -284,7 +284,8 @@ rm_status rm_icp_align(rm_map *map, const rm_scan *scan, const double *init_pose
  * normals: n*H*W*3 float (NaN on the border and where the pixel or a 4-neighbour is invalid);
  * smoothed (optional): n*H*W float S (NaN where invalid). Host outputs are complete on return;
  * device outputs are ordered on `stream`. Host arrays are staged through stream-ordered
- * allocations. Errors: RM_EINVAL (sizes, sigma, metric without a pinhole), RM_ECUDA. */
+ * allocations. Errors: RM_EINVAL (sizes, more than 65535 images, sigma, metric without a
+ * pinhole), RM_ECUDA. */
 rm_status rm_depth_normals(const rm_intrinsics *intr, int32_t n_images, const float *depth,
                            const uint8_t *cls, float sigma, int32_t metric, float *normals,
                            float *smoothed, void *stream);

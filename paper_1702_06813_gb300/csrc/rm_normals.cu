@@ -256,6 +256,7 @@ rm_status run_normals(const rm_intrinsics *intr, int32_t n, const float *depth, 
                       void *stream) {
   if (!intr) return dn_fail(RM_EINVAL, "intrinsics are NULL");
   if (n < 0 || intr->width < 0 || intr->height < 0) return dn_fail(RM_EINVAL, "negative size");
+  if (n > 65535) return dn_fail(RM_EINVAL, "at most 65535 images per call");
   if (!(sigma >= 0.0f) || sigma > 5.0f) return dn_fail(RM_EINVAL, "sigma must be in [0, 5]");
   if (metric != 0 && metric != 1) return dn_fail(RM_EINVAL, "metric must be 0 or 1");
   if (metric && (intr->model != RM_PINHOLE || !(intr->fx > 0.0f) || !(intr->fy > 0.0f) ||

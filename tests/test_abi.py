@@ -65,6 +65,7 @@ def test_argument_errors_without_gpu(lib):
     assert lib.rm_depth_normals(ctypes.byref(intr), 1, None, None, 9.0, 0, None, None, None) == N.RM_EINVAL
     assert lib.rm_depth_normals(ctypes.byref(intr), 1, None, None, 1.0, 1, None, None, None) == N.RM_EINVAL
     assert lib.rm_depth_normals(ctypes.byref(intr), 0, None, None, 1.0, 0, None, None, None) == N.RM_OK
+    assert lib.rm_depth_normals(ctypes.byref(intr), 70000, None, None, 1.0, 0, None, None, None) == N.RM_EINVAL
     assert lib.rm_depth_normals(None, 1, None, None, 1.0, 0, None, None, None) == N.RM_EINVAL
 
 
