@@ -553,6 +553,15 @@ def run_icp(a):
                 "pos_err_m": float(np.linalg.norm(dpose[:3, 3] - w["gt"][:3, 3])),
                 "batch_slots": 12}
 
+    # Fig. 7's cost landscape: 101-sample sweeps along each of the six twist axes
+    def sweeps():
+        return [rm.cost_sweep(gm, scan, w["gt"], ax, 0.3 if ax < 3 else 0.1, 101) for ax in range(6)]
+
+    sweeps()
+    ms_s, _ = timed(sweeps, 3)
+    sweep_line = {"axes": 6, "samples_per_axis": 101, "span": [0.3, 0.3, 0.3, 0.1, 0.1, 0.1],
+                  "ms_per_six_sweeps": ms_s / 3, "pose_evals_per_s": 606 * 3 / (ms_s * 1e-3)}
+
     # vertex-position gradient summed over 16 candidate poses (map refinement)
     vposes = poses[:16]
     rm.cost_grad_vertices(gm, scan, vposes)
@@ -582,7 +591,7 @@ def run_icp(a):
                    "kernel_share": share, "e2e_matches_device": ok,
                    "align_room_1M_640x480": room_align, "align_lidar_2M_1024x64": lidar_align,
                    "depth_normals_eq2": normals_line, "meshify_sec3a": mesh_line,
-                   "dfo_align_table1_room": dfo_line, "vertex_grad": vgrad_line,
+                   "dfo_align_table1_room": dfo_line, "vertex_grad": vgrad_line, "cost_sweep_fig7": sweep_line,
                    "step_hbm_roofline_frac": ab["total"] * n * a.steps / (ms * 1e-3) / 1e9 / pk["hbm_gbs"]},
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": "pose evals/s",

@@ -330,6 +330,14 @@ rm_status rm_dfo_align(rm_map *map, const rm_scan *scan, const double *init_pose
                        const rm_cost_params *params, const rm_dfo_params *dfo, double *pose_out,
                        rm_dfo_report *rep, void *stream);
 
+/* Fig. 7's cost landscape: the Table I cost and surrogate at the n poses pose exp(t_i e_axis^)
+ * with t_i = -span + 2 span i / (n - 1) (t = 0 for n = 1), i.e. a sweep along one twist axis
+ * of the camera frame: axis 0..2 translation (metres), 3..5 rotation (radians). Evaluated as
+ * one batch; pose (16 doubles) host or device; outputs as rm_cost (n per-pose entries). */
+rm_status rm_cost_sweep(rm_map *map, const rm_scan *scan, const double *pose, int32_t axis,
+                        double span, int32_t n, const rm_cost_params *params,
+                        const rm_cost_out *out, void *stream);
+
 /* ---- Meshification of a range image (Sec. III.A, Fig. 5) ------------------------------ */
 typedef struct {
   float max_range;          /* no-return pixels are drawn at this range (4 m for Kinect-class) */

@@ -392,6 +392,16 @@ class OracleMap:
         del keep
         return out.reshape(4, 4), {f: getattr(rep, f) for f, _ in _LMReport._fields_ if f != "pad_"}
 
+    def cost_sweep(self, pose, cam, scan_depth, scan_class, axis, span, n, params=None):
+        """Fig. 7: the cost at pose exp(t_i e_axis^), t_i = -span + 2 span i / (n - 1)."""
+        ts = [-span + 2.0 * span * i / (n - 1) for i in range(n)] if n > 1 else [0.0]
+        out = []
+        for t in ts:
+            xi = np.zeros(6)
+            xi[axis] = t
+            out.append(self.cost(se3_right(pose, xi), cam, scan_depth, scan_class, params))
+        return ts, out
+
     def cost_batch(self, poses, cam, scan_depth, scan_class, params=None):
         c, keep = make_cam(cam)
         prm = params or make_params()

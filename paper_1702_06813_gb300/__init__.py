@@ -7,7 +7,7 @@ CUDA kernels behind the C ABI of include/rendermap.h; this package is the thin b
 """
 from .rendermap import (OUTCOMES, RM_PINHOLE, RM_RAYTABLE, Intrinsics, Map, RenderMapCost,  # noqa: F401
                         Scan, align, align_batch, blur_scan, cost, cost_grad, cost_grad_batch,
-                        cost_grad_vertices, cost_params, depth_normals, dfo_align, dfo_params,
+                        cost_grad_vertices, cost_params, cost_sweep, depth_normals, dfo_align, dfo_params,
                         icp_align, icp_align_batch, icp_terms, meshify, pose_from_x, pose_retract, render_depth,
                         scan_from_range)
 from ._native import RenderMapError, exported_symbols  # noqa: F401

@@ -135,6 +135,8 @@ _SIGS = {
                                              ctypes.POINTER(rm_cost_params), _P, _P]),
     "rm_icp_align_batch": (ctypes.c_int, [_P, ctypes.POINTER(rm_problem), ctypes.c_int32,
                                           ctypes.POINTER(rm_icp_params), _P, ctypes.POINTER(rm_icp_report), _P]),
+    "rm_cost_sweep": (ctypes.c_int, [_P, ctypes.POINTER(rm_scan), _P, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
+                                     ctypes.POINTER(rm_cost_params), ctypes.POINTER(rm_cost_out), _P]),
     "rm_cost_grad_noalloc": (ctypes.c_int, [_P, ctypes.POINTER(rm_scan), _P,
                                             ctypes.POINTER(rm_cost_params), ctypes.POINTER(rm_cost_out), _P]),
     "rm_status_sync": (ctypes.c_int, [_P, _P]),

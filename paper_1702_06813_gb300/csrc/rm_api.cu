@@ -1372,6 +1372,35 @@ rm_status rm_cost_grad_vertices(rm_map *m, const rm_scan *scan, const double *po
   return st;
 }
 
+rm_status rm_cost_sweep(rm_map *m, const rm_scan *scan, const double *pose, int32_t axis, double span,
+                        int32_t n, const rm_cost_params *prm, const rm_cost_out *out, void *stream) {
+  if (!m) return fail(RM_EINVAL, "map is NULL");
+  if (!scan) return fail(RM_EINVAL, "scan is NULL");
+  if (!pose) return fail(RM_EINVAL, "pose is NULL");
+  if (axis < 0 || axis > 5) return fail(RM_EINVAL, "axis must be 0..5");
+  if (!(span >= 0.0) || !std::isfinite(span)) return fail(RM_EINVAL, "span must be finite and >= 0");
+  if (n < 0) return fail(RM_EINVAL, "n < 0");
+  if (n == 0) return RM_OK;
+  std::lock_guard<std::mutex> lk(m->mu);
+  RM_CK(cudaSetDevice(m->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  double *buf = nullptr;
+  RM_CK(cudaMallocAsync((void **)&buf, sizeof(double) * (16 + 38 * (size_t)n), s));
+  double *d_base = buf, *d_rep = buf + 16, *d_tw = d_rep + 16 * (size_t)n, *d_poses = d_tw + 6 * (size_t)n;
+  auto body = [&]() -> rm_status {
+    RM_CK(cudaMemcpyAsync(d_base, pose, sizeof(double) * 16,
+                          on_device(pose) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    RM_CK(rmk::launch_sweep_inputs(d_base, axis, span, n, d_rep, d_tw, s));
+    RM_CK(rmk::launch_retract(d_rep, d_tw, n, d_poses, nullptr, s));
+    m->launches += 2;
+    EvalReq r{&scan->intr, scan, d_poses, n, prm, rmk::kCost, out, nullptr, nullptr, nullptr, nullptr};
+    return run_eval(m, r, s);
+  };
+  const rm_status st = body();
+  cudaFreeAsync(buf, s);
+  return st;
+}
+
 rm_status rm_pose_retract(const double *poses, const double *twists, int32_t n, double *out,
                           double *jr, void *stream) {
   if (n < 0) return fail(RM_EINVAL, "n < 0");

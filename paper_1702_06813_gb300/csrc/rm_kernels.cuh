@@ -73,6 +73,9 @@ cudaError_t launch_wave(const WaveArgs &a, int mode, cudaStream_t s, cudaEvent_t
 int wave_kernel_launches(const WaveArgs &a, int mode);
 cudaError_t launch_retract(const double *T, const double *xi, int n, double *out, double *jr,
                            cudaStream_t s);
+// n copies of `pose` (device, 16 doubles) and the twists t_i e_axis of a sweep (rm_util.cu).
+cudaError_t launch_sweep_inputs(const double *pose, int axis, double span, int n, double *poses,
+                                double *twists, cudaStream_t s);
 
 // Levenberg-Marquardt state on the device (one pose).
 struct LMState {

@@ -51,12 +51,32 @@ __global__ void k_pose_from_x(const double *X, int n, double *T) {
   t[15] = 1.0;
 }
 
+// Inputs of a cost sweep along one twist axis: n copies of the base pose and the twists
+// t_i e_axis with t_i = -span + 2 span i / (n - 1) (t = 0 when n = 1).
+__global__ void k_sweep_inputs(const double *pose, int axis, double span, int n, double *poses,
+                               double *twists) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int k = 0; k < 16; ++k) poses[16 * (long long)i + k] = pose[k];
+  const double t = n > 1 ? -span + 2.0 * span * (double)i / (double)(n - 1) : 0.0;
+  for (int k = 0; k < 6; ++k) twists[6 * (long long)i + k] = k == axis ? t : 0.0;
+}
+
 rm_status ut_fail(rm_status s, const std::string &m) {
   rmapi::set_error(m);
   return s;
 }
 
 }  // namespace
+
+namespace rmk {
+cudaError_t launch_sweep_inputs(const double *pose, int axis, double span, int n, double *poses,
+                                double *twists, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_sweep_inputs<<<(n + 63) / 64, 64, 0, s>>>(pose, axis, span, n, poses, twists);
+  return cudaGetLastError();
+}
+}  // namespace rmk
 
 extern "C" rm_status rm_scan_from_range(const float *range, int64_t n, float range_min,
                                         float range_max, float *depth, uint8_t *cls, void *stream) {

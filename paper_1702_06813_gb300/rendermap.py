@@ -225,6 +225,23 @@ def cost_grad_vertices(m: Map, scan: Scan, poses, params=None):
     return g
 
 
+def cost_sweep(m: Map, scan: Scan, pose, axis, span, n, params=None):
+    """Fig. 7's cost landscape along one camera-frame twist axis (0-2 metres, 3-5 radians):
+    the Table I cost and the surrogate at n evenly spaced displacements in [-span, span]."""
+    p, k = _poses(pose)
+    if k != 1:
+        raise ValueError("one pose")
+    counts = torch.empty((n, 6), dtype=torch.int64, device="cuda")
+    etab = torch.empty(n, dtype=torch.int64, device="cuda")
+    els = torch.empty(n, dtype=torch.float64, device="cuda")
+    out = N.rm_cost_out(counts.data_ptr(), etab.data_ptr(), els.data_ptr(), None, None)
+    cs = scan.c()
+    prm = params if params is not None else _DEFAULT_PARAMS
+    check(lib().rm_cost_sweep(m.handle, ctypes.byref(cs), _ptr(p), int(axis), float(span), int(n), ctypes.byref(prm),
+                              ctypes.byref(out), _stream()))
+    return {"counts": counts, "e_table": etab, "e_ls": els}
+
+
 def pose_retract(poses, twists, with_jacobian=False):
     """poses * exp(twists^) (and the SE(3) right Jacobians), computed on the device."""
     p, n = _poses(poses)

@@ -401,3 +401,18 @@ def test_raytable_align_matches_oracle(lidar):
     assert dt < 1e-3 and da < 1e-2, (dt, da, rep, orep)
     dgt, agt = _pose_gap(pg, lidar["gt"])
     assert dgt < 0.05 and agt < 0.5, (dgt, agt)
+
+
+@pytest.mark.parametrize("axis,span", [(0, 0.2), (2, 0.15), (5, 0.05)])
+def test_cost_sweep_matches_oracle(c1, axis, span):
+    """Fig. 7's sweep along one twist axis, evaluated as one batch on the device: Table I
+    counts exact and the surrogate within 1e-5 at every sample."""
+    c1["gm"].set_tuning()
+    sd, sc = c1["scan"]
+    g = rm.cost_sweep(c1["gm"], c1["gscan"], c1["start"], axis, span, 11)
+    ts, outs = c1["om"].cost_sweep(c1["start"], c1["cam"], sd, sc, axis, span, 11)
+    for k, o in enumerate(outs):
+        _check_cost(g, o, k, grad=False)
+    # the sweep's samples are the same poses as separate evaluations
+    single = rm.cost(c1["gm"], c1["gscan"], rm.pose_retract(c1["start"][None], np.eye(6)[axis][None] * ts[0]))
+    assert torch.equal(single["counts"][0], g["counts"][0])

@@ -467,3 +467,40 @@ def test_rigid_invariance_of_depth(seed):
     same = a["tri_id"] == b["tri_id"]
     assert same.mean() > 0.995   # ties at shared edges may go either way after rounding
     assert np.all(np.abs(b["depth"][hit & same] - a["depth"][hit & same]) <= 1e-5 * a["depth"][hit & same])
+
+
+def test_cost_sweep_wall_closed_form():
+    """Fig. 7-style sweep along the optical axis in front of a wall seen at its true distance:
+    at displacement t the map is t nearer, so every pixel has dz = -t: rewarded with
+    E_ls = N t^2 / 2 while |t| <= eps, penalised with N eps^2 / 2 beyond."""
+    cam = cases.small_pinhole(w=32, h=24, f=30.0)
+    v, f = cases.plane_grid(5, 5, (-20, -20, 2.0), (40, 0, 0), (0, 40, 0))
+    om = oracle.OracleMap(v, f, np.zeros(len(f), np.uint8))
+    sd = np.full((cam.height, cam.width), 2.0, np.float32)
+    sc = np.zeros_like(sd, np.uint8)
+    N = cam.width * cam.height
+    ts, outs = om.cost_sweep(np.eye(4), cam, sd, sc, axis=2, span=0.33, n=12)
+    assert ts[0] == -0.33 and ts[-1] == 0.33
+    for t, o in zip(ts, outs):
+        if abs(t) < 0.1:
+            assert o["e_table"] == -N, t
+            assert o["e_ls"] == pytest.approx(0.5 * N * t * t, rel=1e-5), t
+        else:
+            assert o["e_table"] == N, t
+            assert o["e_ls"] == pytest.approx(0.5 * N * np.float32(0.1) ** 2, rel=1e-6), t
+
+
+def test_cost_sweep_minimum_at_true_pose():
+    """On a noise-free scan the sweep's Table I cost is lowest at zero displacement, where every
+    compared pixel is rewarded, along translation and rotation axes alike."""
+    c = cases.config1(seed=2300, noise=0.0, dropout=0.0)
+    mesh, cam = c["mesh"], c["cam"]
+    fo = mesh.labels == 0
+    om = oracle.OracleMap(mesh.vertices, mesh.faces, mesh.labels)
+    sd, sc = cases.scan_from_render(oracle.OracleMap(mesh.vertices, mesh.faces[fo], mesh.labels[fo])
+                                    .render(c["gt"], cam)["depth"], cam)
+    for axis, span in ((0, 0.3), (4, 0.1)):
+        ts, outs = om.cost_sweep(c["gt"], cam, sd, sc, axis=axis, span=span, n=9)
+        e = [o["e_table"] for o in outs]
+        assert ts[4] == 0.0 and e[4] == min(e) and e[4] == -int(np.sum(outs[4]["counts"]))
+        assert e[0] > e[4] and e[-1] > e[4]
