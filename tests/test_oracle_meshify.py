@@ -156,3 +156,25 @@ def test_render_of_meshed_scan_reproduces_scan(seed):
     assert nr.sum() > 100
     assert np.all(np.abs(t[nr] - R) <= 2e-6 * R)
     assert 0.05 < lab.mean() < 0.9
+
+
+def test_raytable_vertices_lie_on_their_rays():
+    """Panoramic (ray-table) scan at a constant range R: every vertex is R along its pixel's
+    unit ray (so |v| = R), and no-returns sit at the maximal range along theirs."""
+    cam = cases.small_spherical(w=64, h=12)
+    R = 7.5
+    d = np.full((cam.height, cam.width), R, np.float32)
+    c = np.zeros_like(d, np.uint8)
+    c[3, 10:20] = 1
+    v, f, lab = oracle.meshify(cam, d, c, np.eye(4), max_range=40.0, max_edge=10.0)
+    rays = cam.ray_table_f32().reshape(-1, 3).astype(np.float64)
+    rng = np.where(c.ravel() == 1, 40.0, R)
+    want = (np.float32(rng)[:, None] * rays.astype(np.float32)).astype(np.float32)
+    assert np.array_equal(v, want)
+    assert np.allclose(np.linalg.norm(v, axis=1), rng, rtol=1e-6)
+    # every 2x2 block is kept (no dead pixels); only the blocks touching a no-return are FU
+    assert f.shape[0] == 2 * (cam.width - 1) * (cam.height - 1)
+    blk = lab[0::2].reshape(cam.height - 1, cam.width - 1)
+    nr = c == 1
+    touch = nr[:-1, :-1] | nr[1:, :-1] | nr[:-1, 1:] | nr[1:, 1:]
+    assert np.array_equal(blk, touch.astype(np.uint8))
