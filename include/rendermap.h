@@ -293,7 +293,8 @@ rm_status rm_depth_normals(const rm_intrinsics *intr, int32_t n_images, const fl
 /* Gaussian blur of depth images for cost smoothing (Sec. III.C): the smoothing above alone.
  * out (n*H*W float, host or device) holds each FO return's smoothed depth and every other
  * pixel's input depth unchanged (FU pixels stay at their maximal range, dead pixels NaN), so
- * the result pairs with the same class image as a scan. Errors as rm_depth_normals. */
+ * the result pairs with the same class image as a scan. out must not overlap depth (other
+ * tiles still read the input while one writes). Errors as rm_depth_normals. */
 rm_status rm_depth_blur(const rm_intrinsics *intr, int32_t n_images, const float *depth,
                         const uint8_t *cls, float sigma, float *out, void *stream);
 
