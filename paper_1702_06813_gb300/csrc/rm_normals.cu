@@ -334,5 +334,10 @@ extern "C" rm_status rm_depth_normals(const rm_intrinsics *intr, int32_t n, cons
 extern "C" rm_status rm_depth_blur(const rm_intrinsics *intr, int32_t n, const float *depth,
                                    const uint8_t *cls, float sigma, float *out, void *stream) {
   if (!out && n > 0) return dn_fail(RM_EINVAL, "out is NULL");
+  if (intr && depth && out && n > 0 && intr->width > 0 && intr->height > 0) {
+    const size_t bytes = sizeof(float) * (size_t)n * intr->width * intr->height;
+    const char *a0 = reinterpret_cast<const char *>(depth), *b0 = reinterpret_cast<const char *>(out);
+    if (a0 < b0 + bytes && b0 < a0 + bytes) return dn_fail(RM_EINVAL, "out overlaps depth");
+  }
   return run_normals(intr, n, depth, cls, sigma, 0, nullptr, nullptr, out, stream);
 }

@@ -66,6 +66,13 @@ def test_argument_errors_without_gpu(lib):
     assert lib.rm_depth_normals(ctypes.byref(intr), 1, None, None, 1.0, 1, None, None, None) == N.RM_EINVAL
     assert lib.rm_depth_normals(ctypes.byref(intr), 0, None, None, 1.0, 0, None, None, None) == N.RM_OK
     assert lib.rm_depth_normals(ctypes.byref(intr), 70000, None, None, 1.0, 0, None, None, None) == N.RM_EINVAL
+    import numpy as np
+    buf = np.zeros(2 * 64, np.float32)
+    cls = np.zeros(64, np.uint8)
+    # the blur's output may not overlap its input (checked before any device work)
+    assert lib.rm_depth_blur(ctypes.byref(intr), 1, buf.ctypes.data, cls.ctypes.data, 1.0,
+                             buf.ctypes.data + 4 * 10, None) == N.RM_EINVAL
+    assert b"overlaps" in lib.rm_last_error()
     assert lib.rm_depth_normals(None, 1, None, None, 1.0, 0, None, None, None) == N.RM_EINVAL
 
 
