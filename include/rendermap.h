@@ -13,6 +13,11 @@
  * On top of the paper's cost the library computes a truncated least-squares surrogate with
  * the same cells and thresholds, its derivative with respect to a pose twist, and
  * Levenberg-Marquardt steps on it (the paper's Sec. III.C optimiser is derivative-free).
+ * Around that path: render-accelerated point-to-plane ICP (Sec. IV), the derivative-free
+ * search of Sec. III.C on the exact Table I cost, Fig. 7's cost sweeps, depth-image normals
+ * (Eq. 2) and blur, the meshification of range images (Sec. III.A), the cost's gradient with
+ * respect to the map's vertices, and input helpers for raw range images and the paper's pose
+ * vector.
  *
  * All work runs in CUDA kernels for sm_103a on the calling thread's current device.
  *
