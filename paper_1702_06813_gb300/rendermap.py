@@ -284,6 +284,27 @@ def blur_scan(scan: Scan, sigma=1.0) -> Scan:
     return Scan(intr, out, scan.cls)
 
 
+def sequential_icp(scans, first_pose, max_range, step=2, max_edge=0.1, tol=0.2, max_iters=20,
+                   step_tol=1e-5):
+    """Sequential depth-image alignment (Sec. IV): each scan, downsampled by `step` and meshed
+    at its pose, becomes the map the next scan is aligned to by point-to-plane ICP, starting
+    from the previous pose. Returns the (n, 4, 4) poses (the first is `first_pose`) and the
+    per-step ICP reports. The meshes are built on the device; each becomes a Map through the
+    host (rm_map_create)."""
+    poses = [np.asarray(first_pose, dtype=np.float64).reshape(4, 4)]
+    reports = []
+    for k in range(1, len(scans)):
+        mesh = meshify(scans[k - 1], poses[-1], max_range, max_edge=max_edge, step=step)
+        m = Map(mesh["vertices"], mesh["faces"], mesh["labels"])
+        try:
+            pose, rep = icp_align(m, scans[k], poses[-1], tol=tol, max_iters=max_iters, step_tol=step_tol)
+        finally:
+            m.close()
+        poses.append(pose)
+        reports.append(rep)
+    return np.stack(poses), reports
+
+
 def dfo_params(nm_iters=60, cd_iters=60, nm_step=1.0, nm_tol=0.05, cd_step=0.25, cd_tol=0.01,
                scale_t=0.05, scale_r=0.0349) -> N.rm_dfo_params:
     """Nelder-Mead / coordinate-descent settings; scales: 5 cm and 2 deg per unit."""
