@@ -14,7 +14,16 @@
  *    all pixels (Sec. III.B).
  *  - Sec. III.C names derivative-based and derivative-free optimisers; this oracle adds the
  *    least-squares surrogate whose Levenberg-Marquardt step the library runs (a reading, not
- *    the paper's own optimiser), with the pose derivative of the ray-plane depth.
+ *    the paper's own optimiser), with the pose derivative of the ray-plane depth, and the
+ *    paper's own derivative-free search (Nelder-Mead, then coordinate descent) on Table I.
+ *  - Sec. IV: render-accelerated point-to-plane ICP (projective association with a depth
+ *    tolerance, point-to-plane residual and its 6x6 normal equations) and the depth-image
+ *    normals of Eq. 2.
+ *  - Sec. III.A / Fig. 5: meshification of a range image into FO / FU quads; Sec. III.A-B:
+ *    the classes of raw range readings; Eq. 1: the pose of the vector X.
+ *  - Map refinement: the surrogate's gradient with respect to the vertex positions.
+ * Every function is pinned by tests against closed forms, invariants, brute force or finite
+ * differences (see the tests named in oracle/__init__.py); no function is unpinned.
  *
  * The z-buffer follows a written FP32 arithmetic contract so that the CPU and the GPU pick
  * the same triangle for every pixel: fixed operation order, IEEE add / mul / div / fma,
