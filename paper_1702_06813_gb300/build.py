@@ -48,16 +48,21 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
         o = os.path.join(build_dir, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _stale(o, [s] + hdrs):
-            cmd = [nvcc, *ARCH, *FLAGS, *(extra or []), "-c", s, "-o", o]
-            jobs.append(cmd)
+            # each object goes to a private file first: processes that build at the same time
+            # (one per GPU) never link a half-written object
+            tmp_o = o + f".{os.getpid()}.tmp"
+            cmd = [nvcc, *ARCH, *FLAGS, *(extra or []), "-c", s, "-o", tmp_o]
+            jobs.append((cmd, tmp_o, o))
     if jobs:
         with concurrent.futures.ThreadPoolExecutor(len(jobs)) as ex:
-            for cmd, res in zip(jobs, ex.map(lambda c: subprocess.run(c, capture_output=True, text=True), jobs)):
+            runs = ex.map(lambda j: subprocess.run(j[0], capture_output=True, text=True), jobs)
+            for (cmd, tmp_o, o), res in zip(jobs, runs):
                 if verbose or res.returncode != 0:
                     print(" ".join(cmd))
                     print(res.stdout + res.stderr)
                 if res.returncode != 0:
                     raise RuntimeError(f"nvcc failed for {cmd[-3]}")
+                os.replace(tmp_o, o)
     if force or jobs or _stale(lib, objs):
         tmp = lib + f".{os.getpid()}.tmp"
         res = subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"],
