@@ -90,3 +90,19 @@ def test_table1_search_reaches_true_pose_noise_free():
     assert rep["e_table"] <= e_gt + 0.005 * abs(e_gt)
     assert np.linalg.norm(pose[:3, 3] - gt[:3, 3]) < 0.05
     assert math.degrees(Rotation.from_matrix(gt[:3, :3].T @ pose[:3, :3]).magnitude()) < 1.0
+
+
+def test_search_depends_only_on_the_order_of_values():
+    """Nelder-Mead and coordinate descent compare values only: adding a constant to the
+    objective or scaling it by a positive factor leaves the whole search path unchanged. The
+    objective is integer valued, like the Table I cost, so both changes are exact."""
+    a = np.array([0.02, -0.01, 0.015, -0.02, 0.01, 0.005])
+    w = np.array([1.0, 2.0, 0.5, 3.0, 1.0, 2.0])
+    base = lambda X: np.floor(1e7 * ((X - a) ** 2 * w).sum(1))  # noqa: E731
+    prm = oracle.dfo_params(nm_iters=40, cd_iters=30)
+    x0, f0, r0 = oracle.dfo_minimise(base, SCALE, prm)
+    x1, f1, r1 = oracle.dfo_minimise(lambda X: base(X) + 7.0, SCALE, prm)
+    x2, f2, r2 = oracle.dfo_minimise(lambda X: 3.0 * base(X), SCALE, prm)
+    assert np.array_equal(x0, x1) and np.array_equal(x0, x2)
+    assert r0 == r1 == r2
+    assert f1 == pytest.approx(f0 + 7.0) and f2 == pytest.approx(3.0 * f0)

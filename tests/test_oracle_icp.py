@@ -230,3 +230,19 @@ def test_icp_single_wall_is_degenerate():
     pose, rep = om.icp_align(np.eye(4), cam, sd, sc, tol=0.1, max_iters=10)
     assert rep["converged"] == 0 and rep["iters"] == 0
     assert np.array_equal(pose, np.eye(4))
+
+
+def test_icp_terms_are_rigidly_invariant():
+    """Moving the world and the pose together by one rigid motion leaves the associations and
+    the terms (all in the camera frame) unchanged, up to the FP32 rounding of the moved
+    vertices."""
+    c = cases.config1(seed=2400)
+    mesh, cam = c["mesh"], c["cam"]
+    sd, sc = c["scan"]
+    G = synth.pose_from(np.array([12.0, -7.0, 3.0]), 1.1, 0.3, -0.2)
+    v2 = (mesh.vertices.astype(np.float64) @ G[:3, :3].T + G[:3, 3]).astype(np.float32)
+    a = oracle.OracleMap(mesh.vertices, mesh.faces, mesh.labels).icp_terms(c["start"], cam, sd, sc, 0.1)
+    b = oracle.OracleMap(v2, mesh.faces, mesh.labels).icp_terms(G @ c["start"], cam, sd, sc, 0.1)
+    assert abs(a["n_assoc"] - b["n_assoc"]) <= 1e-3 * a["n_assoc"]
+    assert np.linalg.norm(a["jte"] - b["jte"]) <= 1e-3 * np.linalg.norm(a["jte"])
+    assert np.linalg.norm(a["jtj"] - b["jtj"]) <= 1e-3 * np.linalg.norm(a["jtj"])
