@@ -123,3 +123,17 @@ def test_blur_keeps_other_pixels_and_linear_interior():
     inner[4:-4, 4:-4] = True
     sel = far & inner & (c == 0)
     assert np.allclose(d[sel], z[sel], rtol=1e-6, atol=0)
+
+
+def test_transpose_swaps_the_in_plane_components():
+    """In pixel units, transposing a depth image transposes its normal field and swaps the
+    x and y components (a mixed-up axis in either difference or in the cross product fails)."""
+    r = np.random.Generator(np.random.PCG64(9))
+    z = (2.0 + 0.3 * r.random((23, 31))).astype(np.float32)
+    c = (r.random(z.shape) < 0.05).astype(np.uint8)
+    n, _ = oracle.depth_normals(z, c, sigma=1.3)
+    nt, _ = oracle.depth_normals(np.ascontiguousarray(z.T), np.ascontiguousarray(c.T), sigma=1.3)
+    want = np.transpose(n, (1, 0, 2))[..., [1, 0, 2]]
+    assert np.array_equal(np.isnan(nt), np.isnan(want))
+    ok = ~np.isnan(want)
+    assert np.allclose(nt[ok], want[ok], rtol=0, atol=1e-12)
