@@ -97,7 +97,13 @@ int main(void) {
         c = os.path.join(d, "s.c")
         open(c, "w").write(code)
         exe = os.path.join(d, "s")
-        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), c, "-o", exe],
+                       check=True)
+        # the header is also valid C++ (its declarations sit in an extern "C" block)
+        cc = os.path.join(d, "s.cc")
+        open(cc, "w").write(code)
+        subprocess.run(["g++", "-std=c++17", "-Wall", "-Werror", "-fsyntax-only", "-I", os.path.join(ROOT, "include"),
+                        cc], check=True)
         got = [int(x) for x in subprocess.run([exe], capture_output=True, text=True).stdout.split()]
     want = [ctypes.sizeof(N.rm_intrinsics), N.rm_intrinsics.rays.offset, ctypes.sizeof(N.rm_scan),
             ctypes.sizeof(N.rm_cost_params), ctypes.sizeof(N.rm_cost_out), ctypes.sizeof(N.rm_tuning),
