@@ -178,3 +178,20 @@ def test_raytable_vertices_lie_on_their_rays():
     nr = c == 1
     touch = nr[:-1, :-1] | nr[1:, :-1] | nr[:-1, 1:] | nr[1:, 1:]
     assert np.array_equal(blk, touch.astype(np.uint8))
+
+
+def test_step_equals_meshing_the_subsampled_image():
+    """Meshing with step 2 is meshing the image of every other pixel with a camera whose
+    pixels are twice as large (the same rays), face for face and label for label."""
+    import dataclasses
+    c = cases.config1(seed=1750, noise=0.005, dropout=0.05)
+    cam = c["cam"]
+    sd, sc = c["scan"]
+    v2, f2, l2 = oracle.meshify(cam, sd, sc, c["gt"], cam.range_max, 0.1, 2)
+    # the subsampled camera: pixel (i, j) of it is pixel (2i, 2j) of the original
+    sub = dataclasses.replace(cam, width=(cam.width - 1) // 2 + 1, height=(cam.height - 1) // 2 + 1,
+                              fx=cam.fx / 2, fy=cam.fy / 2, cx=(cam.cx + 0.5) / 2, cy=(cam.cy + 0.5) / 2)
+    vs, fs, ls = oracle.meshify(sub, np.ascontiguousarray(sd[::2, ::2]), np.ascontiguousarray(sc[::2, ::2]),
+                                c["gt"], cam.range_max, 0.1, 1)
+    assert np.array_equal(f2, fs) and np.array_equal(l2, ls)
+    assert np.allclose(v2, vs, rtol=0, atol=1e-5)
