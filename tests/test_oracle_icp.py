@@ -246,3 +246,18 @@ def test_icp_terms_are_rigidly_invariant():
     assert abs(a["n_assoc"] - b["n_assoc"]) <= 1e-3 * a["n_assoc"]
     assert np.linalg.norm(a["jte"] - b["jte"]) <= 1e-3 * np.linalg.norm(a["jte"])
     assert np.linalg.norm(a["jtj"] - b["jtj"]) <= 1e-3 * np.linalg.norm(a["jtj"])
+
+
+def test_associations_grow_with_the_tolerance():
+    """A larger tolerance keeps every pair a smaller one makes (|Z_M - Z_1| < tol is monotone),
+    and C grows with the pairs it adds."""
+    c = cases.config1(seed=2500)
+    om = oracle.OracleMap(c["mesh"].vertices, c["mesh"].faces, c["mesh"].labels)
+    sd, sc = c["scan"]
+    prev = None
+    for tol in (0.0, 0.01, 0.03, 0.1, 0.3, 1.0):
+        o = om.icp_terms(c["start"], c["cam"], sd, sc, tol)
+        if prev is not None:
+            assert o["n_assoc"] >= prev["n_assoc"] and o["cost_l1"] >= prev["cost_l1"]
+        prev = o
+    assert om.icp_terms(c["start"], c["cam"], sd, sc, 0.0)["n_assoc"] == 0
