@@ -123,7 +123,12 @@ typedef struct {
   int32_t wave_poses;       /* poses processed together per kernel wave */
   int32_t async_status;     /* 1: do not read the device status back (graph capture);
                                check it later with rm_status_sync */
-  int32_t reserved[3];
+  int32_t wait_log2;        /* 0: default budgets of the bounded device waits (about 2^31
+                               cycles for a bulk copy, 2^32 for the batch kernel's work
+                               queue); 1..40: every such wait gives up after 2^wait_log2
+                               cycles and the call returns RM_ETIMEOUT (a copy still in
+                               flight is drained with the default budget first) */
+  int32_t reserved[2];
 } rm_tuning;
 
 typedef struct {
@@ -189,6 +194,14 @@ rm_status rm_cost_grad(rm_map *map, const rm_scan *scan, const double *poses,
  * Uses stream-ordered device scratch when any pointer is on the host, and then waits. */
 rm_status rm_pose_retract(const double *poses, const double *twists, int32_t n_poses,
                           double *out, double *jr, void *stream);
+
+/* The same chain rule applied on the device: out_k = scale_k J_r(twists_k)^T grads_k, the
+ * derivative of e(T exp(xi^)) with respect to xi from the adjoint gradient at the retracted
+ * pose (rm_cost_grad), scaled by an upstream derivative (autograd's grad_output). twists and
+ * grads N*6, scale N (optional: 1), out N*6 doubles; all host or device. Uses stream-ordered
+ * device scratch when any pointer is on the host, and then waits. */
+rm_status rm_twist_grad(const double *twists, const double *grads, const double *scale,
+                        int32_t n, double *out, void *stream);
 
 /* Levenberg-Marquardt alignment of one scan from init_pose (16 doubles, host or device):
  * each iteration renders, evaluates the surrogate and its gradient, solves
@@ -289,8 +302,9 @@ rm_status rm_icp_align(rm_map *map, const rm_scan *scan, const double *init_pose
  * normals: n*H*W*3 float (NaN on the border and where the pixel or a 4-neighbour is invalid);
  * smoothed (optional): n*H*W float S (NaN where invalid). Host outputs are complete on return;
  * device outputs are ordered on `stream`. Host arrays are staged through stream-ordered
- * allocations. Errors: RM_EINVAL (sizes, more than 65535 images, sigma, metric without a
- * pinhole), RM_ECUDA. */
+ * allocations. Neither output may overlap depth, cls or the other output (other tiles still
+ * read the inputs' halos while one writes). Errors: RM_EINVAL (sizes, more than 65535
+ * images, sigma, metric without a pinhole, overlapping outputs), RM_ECUDA. */
 rm_status rm_depth_normals(const rm_intrinsics *intr, int32_t n_images, const float *depth,
                            const uint8_t *cls, float sigma, int32_t metric, float *normals,
                            float *smoothed, void *stream);
@@ -298,8 +312,8 @@ rm_status rm_depth_normals(const rm_intrinsics *intr, int32_t n_images, const fl
 /* Gaussian blur of depth images for cost smoothing (Sec. III.C): the smoothing above alone.
  * out (n*H*W float, host or device) holds each FO return's smoothed depth and every other
  * pixel's input depth unchanged (FU pixels stay at their maximal range, dead pixels NaN), so
- * the result pairs with the same class image as a scan. out must not overlap depth (other
- * tiles still read the input while one writes). Errors as rm_depth_normals. */
+ * the result pairs with the same class image as a scan. out must not overlap depth or cls
+ * (other tiles still read the inputs while one writes). Errors as rm_depth_normals. */
 rm_status rm_depth_blur(const rm_intrinsics *intr, int32_t n_images, const float *depth,
                         const uint8_t *cls, float sigma, float *out, void *stream);
 
@@ -432,16 +446,19 @@ rm_status rm_icp_align_batch(rm_map *map, const rm_problem *problems, int32_t n,
  * matrix, visible-cluster list, screen-tile bins, per-tile partial sums, status word) comes
  * from one array of RM_NOALLOC_SCRATCH_BYTES in device global memory that belongs to the
  * library: every GPU that loads the library holds it until the process exits.
- *  - map: created earlier with rm_map_create (read only here); its tile size is used, and
- *    the bin capacity is whatever fits in the array (at most 4096 records per tile).
- *  - scan: depth and cls in DEVICE memory; pose: 16 doubles, host or device.
- *  - out: DEVICE pointers (any may be NULL), one pose's values as for rm_cost_grad.
+ *  - map: created earlier with rm_map_create (read only here) on the device that is current
+ *    for this call (the call does not switch devices); its tile size is used, and the bin
+ *    capacity is whatever fits in the array (at most 4096 records per tile).
+ *  - scan: depth and cls in DEVICE memory of that device; pose: 16 doubles, host or device.
+ *  - out: DEVICE pointers of that device (any may be NULL), one pose's values as for
+ *    rm_cost_grad.
  * The call waits for `stream` to read its status. The first call on each device looks up
  * the array's device address (cudaGetSymbolAddress, with that device current); make that
  * first call before any stream capture. Every call shares the one array and leaves its
  * contents behind; the call clears what must start at zero. Calls whose GPU work overlaps
  * (other streams, unordered threads) race on the array and give wrong results.
- * Errors: RM_EINVAL for host scan/output pointers, or when the cluster list and tile arrays
+ * Errors: RM_EINVAL when the map, the scan or an output is not on the current device (host
+ * scan/output pointers included), or when the cluster list and tile arrays
  * leave room for fewer than 256 records per tile; RM_EOVERFLOW when a tile's bin overflows
  * (no growth is possible); RM_ECUDA, RM_ETIMEOUT as elsewhere. */
 #define RM_NOALLOC_SCRATCH_BYTES (48u << 20)

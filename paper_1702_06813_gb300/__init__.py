@@ -9,5 +9,6 @@ from .rendermap import (OUTCOMES, RM_PINHOLE, RM_RAYTABLE, Intrinsics, Map, Rend
                         Scan, align, align_batch, blur_scan, cost, cost_grad, cost_grad_batch,
                         cost_grad_vertices, cost_params, cost_sweep, depth_normals, dfo_align, dfo_params,
                         icp_align, icp_align_batch, icp_terms, meshify, pose_from_x, pose_retract, render_depth,
+                        twist_grad,
                         scan_from_range, sequential_icp)
 from ._native import RenderMapError, exported_symbols  # noqa: F401

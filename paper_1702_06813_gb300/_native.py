@@ -46,7 +46,8 @@ class rm_cost_out(ctypes.Structure):
 class rm_tuning(ctypes.Structure):
     _fields_ = [("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32),
                 ("bin_capacity", ctypes.c_int32), ("wave_poses", ctypes.c_int32),
-                ("async_status", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("async_status", ctypes.c_int32), ("wait_log2", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class rm_align_params(ctypes.Structure):
@@ -110,6 +111,7 @@ _SIGS = {
     "rm_cost_grad": (ctypes.c_int, [_P, ctypes.POINTER(rm_scan), _P, ctypes.c_int32,
                                     ctypes.POINTER(rm_cost_params), ctypes.POINTER(rm_cost_out), _P]),
     "rm_pose_retract": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P, _P, _P]),
+    "rm_twist_grad": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, _P, _P]),
     "rm_cost_grad_batch": (ctypes.c_int, [_P, ctypes.POINTER(rm_problem), ctypes.c_int32,
                                           ctypes.POINTER(rm_cost_params), ctypes.POINTER(rm_cost_out), _P]),
     "rm_align_batch": (ctypes.c_int, [_P, ctypes.POINTER(rm_problem), ctypes.c_int32,

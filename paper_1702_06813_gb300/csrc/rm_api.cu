@@ -316,7 +316,14 @@ int wave_size(const rm_map *m, int n, const TileGeom &tg) {
   return (int)std::min<size_t>(std::min<size_t>(w, 128), (size_t)n);
 }
 
-void set_clusters(const rm_map *m, WaveArgs &a) {
+// Budget of the map's bounded device waits in cycles (dflt unless the tuning sets wait_log2).
+long long wait_budget(const rm_map *m, long long dflt) {
+  return m->tuning.wait_log2 > 0 ? (1ll << m->tuning.wait_log2) : dflt;
+}
+
+// The map's clusters and its wait budget in a wave's arguments.
+void set_map_fields(const rm_map *m, WaveArgs &a) {
+  a.wait_cycles = wait_budget(m, 0);
   a.n_clusters = m->n_clusters;
   a.cl_info = m->d_cl_info;
   a.cl_sphere = m->d_cl_sphere;
@@ -523,7 +530,7 @@ rm_status run_eval(rm_map *m, const EvalReq &r, cudaStream_t s) {
     a.faces = m->d_faces;
     a.planes = m->d_planes;
     a.Ms = d_M;
-    set_clusters(m, a);
+    set_map_fields(m, a);
     a.vis = d_vis;
     a.vis_count = d_vcount;
     a.counts = d_bcount;
@@ -789,7 +796,7 @@ rm_status run_batch(rm_map *m, const rm_problem *probs, int n, const rm_cost_par
       a.v = m->d_v;
       a.faces = m->d_faces;
       a.planes = m->d_planes;
-      set_clusters(m, a);
+      set_map_fields(m, a);
       a.Ms = d_M + 12 * (size_t)p;
       a.vis = d_vis + (size_t)p * std::max(nc, 1);
       a.vis_count = d_vcount + p;
@@ -859,15 +866,16 @@ rm_status run_batch(rm_map *m, const rm_problem *probs, int n, const rm_cost_par
     b.lmargs = la;
     b.lm_iters = K;
     b.status = m->d_status;
-    b.spin_limit = 1ll << 32;
+    b.spin_limit = wait_budget(m, 1ll << 32);
     const int grid = rmk::persist_grid(m->device);
     if (grid <= 0) return fail(RM_ECUDA, "could not size the persistent grid");
     // counters to zero, LM state / pose matrices, the persistent kernel: one captured graph
     // per batch shape (the arena layout is a function of the shape), replayed every call
     char sig[512];
-    std::snprintf(sig, sizeof(sig), "%p|%d|%d|%zu|%d|%d|%a|%a|%a|%a|%zu|%zu|%zu|%d|%a", (void *)m->arena, n,
+    std::snprintf(sig, sizeof(sig), "%p|%d|%d|%zu|%d|%d|%a|%a|%a|%a|%zu|%zu|%zu|%d|%a|%lld", (void *)m->arena, n,
                   K, cap_hi + cap_lo, grid, lm ? 1 : (icp ? 2 : 0), la.lambda0, la.lambda_up, la.lambda_down,
-                  la.step_tol, tiles_total, px_total, rays_total, m->cap * 4096 + m->cap_ray, ia.step_tol);
+                  la.step_tol, tiles_total, px_total, rays_total, m->cap * 4096 + m->cap_ray, ia.step_tol,
+                  b.spin_limit);
     std::string key(sig);
     for (int p = 0; p < n; ++p) key += "|" + std::to_string(probs[p].scan.intr.model) + "x" +
                                         std::to_string(probs[p].scan.intr.width) + "x" +
@@ -1027,7 +1035,7 @@ WaveArgs loop_wave(const rm_map *m, const rm_scan *scan, const TileGeom &tg, int
   a.faces = m->d_faces;
   a.planes = m->d_planes;
   a.Ms = b.M;
-  set_clusters(m, a);
+  set_map_fields(m, a);
   a.vis = b.vis;
   a.vis_count = b.vis_count;
   a.counts = b.counts;
@@ -1080,6 +1088,8 @@ rm_status write_pose(double *pose_out, const double *T) {
 
 namespace rmapi {
 
+int map_device(const rm_map *m) { return m->device; }
+
 rm_status wave_inputs(const rm_map *m, const rm_intrinsics *in, WaveArgs *a, double centre[3]) {
   if (!m) return fail(RM_EINVAL, "map is NULL");
   RM_TRY(check_intr(in));
@@ -1092,7 +1102,7 @@ rm_status wave_inputs(const rm_map *m, const rm_intrinsics *in, WaveArgs *a, dou
   a->v = m->d_v;
   a->faces = m->d_faces;
   a->planes = m->d_planes;
-  set_clusters(m, *a);
+  set_map_fields(m, *a);
   for (int k = 0; k < 3; ++k) centre[k] = m->centre[k];
   return RM_OK;
 }
@@ -1238,6 +1248,7 @@ rm_status rm_map_set_tuning(rm_map *m, const rm_tuning *t) {
                  (u.tile_w == 16 && u.tile_h == 16);
   if (!ok_tile) return fail(RM_EINVAL, "tile must be 16x16, 32x16, 32x32 or 64x32");
   if (u.bin_capacity < 0 || u.wave_poses < 0) return fail(RM_EINVAL, "negative tuning value");
+  if (u.wait_log2 < 0 || u.wait_log2 > 40) return fail(RM_EINVAL, "wait_log2 must be 0..40");
   m->tuning = u;
   if (u.bin_capacity > 0) m->cap = m->cap_ray = u.bin_capacity;
   return RM_OK;
@@ -1428,6 +1439,36 @@ rm_status rm_pose_retract(const double *poses, const double *twists, int32_t n, 
     return RM_OK;
   };
   st = run();
+  cudaFreeAsync(buf, s);
+  return st;
+}
+
+rm_status rm_twist_grad(const double *twists, const double *grads, const double *scale, int32_t n,
+                        double *out, void *stream) {
+  if (n < 0) return fail(RM_EINVAL, "n < 0");
+  if (n == 0) return RM_OK;
+  if (!twists || !grads || !out) return fail(RM_EINVAL, "NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool dt = on_device(twists), dg = on_device(grads), ds = !scale || on_device(scale);
+  const bool dout = on_device(out);
+  if (dt && dg && ds && dout) {
+    RM_CK(rmk::launch_twist_grad(twists, grads, scale, n, out, s));
+    return RM_OK;
+  }
+  double *buf = nullptr;
+  RM_CK(cudaMallocAsync((void **)&buf, sizeof(double) * 19 * (size_t)n, s));
+  double *bt = buf, *bg = bt + 6 * (size_t)n, *bs = bg + 6 * (size_t)n, *bo = bs + (size_t)n;
+  auto run = [&]() -> rm_status {
+    RM_CK(cudaMemcpyAsync(bt, twists, sizeof(double) * 6 * n, dt ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    RM_CK(cudaMemcpyAsync(bg, grads, sizeof(double) * 6 * n, dg ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    if (scale)
+      RM_CK(cudaMemcpyAsync(bs, scale, sizeof(double) * n, on_device(scale) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    RM_CK(rmk::launch_twist_grad(bt, bg, scale ? bs : nullptr, n, bo, s));
+    RM_CK(cudaMemcpyAsync(out, bo, sizeof(double) * 6 * n, dout ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    RM_CK(cudaStreamSynchronize(s));
+    return RM_OK;
+  };
+  const rm_status st = run();
   cudaFreeAsync(buf, s);
   return st;
 }

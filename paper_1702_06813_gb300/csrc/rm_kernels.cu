@@ -66,11 +66,15 @@ __device__ __forceinline__ bool mbar_try(unsigned long long *bar, unsigned parit
   return ok != 0;
 }
 
-// Bounded wait on a phase of `bar`: gives up after about 2^31 cycles (~1 s).
-__device__ __noinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
+// Default budget of a bounded device wait: about 2^31 cycles (~1 s at 2 GHz).
+constexpr long long kWaitCycles = 1ll << 31;
+
+// Bounded wait on a phase of `bar`: gives up after `budget` cycles (kWaitCycles when <= 0).
+__device__ __noinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, long long budget) {
+  if (budget <= 0) budget = kWaitCycles;
   long long t0 = clock64();
   while (!mbar_try(bar, parity)) {
-    if (clock64() - t0 > (1ll << 31)) return false;
+    if (clock64() - t0 > budget) return false;
   }
   return true;
 }
@@ -638,7 +642,7 @@ template <int TW, int TH>
 __device__ __forceinline__ bool raster_tile(unsigned long long *zk, TriRec *stage, int4 *hdr,
                                             int *S, int *wtot, unsigned long long *bar,
                                             const TriRec *recs, int n, int ox, int oy, int xe,
-                                            int ye, const DevCam &cam) {
+                                            int ye, const DevCam &cam, long long budget) {
   constexpr int kRecMax = kRecMaxPinhole;
   static_assert(kRecMax <= kThreads, "one record per thread");
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -653,10 +657,11 @@ __device__ __forceinline__ bool raster_tile(unsigned long long *zk, TriRec *stag
       fence_async_smem();
       bulk_g2s(stage, recs + r0, (unsigned)(cnt * sizeof(TriRec)), bar);
     }
-    bool ok = mbar_wait(bar, phase);
+    bool ok = mbar_wait(bar, phase, budget);
     ok = __syncthreads_and(ok);
     if (!ok) {
-      if (tid == 0) mbar_wait(bar, phase);
+      // the copy may still be in flight: drain it (default budget) before the CTA leaves
+      if (tid == 0) mbar_wait(bar, phase, kWaitCycles);
       return false;
     }
     phase ^= 1u;
@@ -764,7 +769,8 @@ __device__ __forceinline__ bool raster_tile_ray(unsigned long long *zk, RayRec *
                                                 const float *rx, const float *ry, const float *rz,
                                                 int *S, int *wtot, unsigned long long *bar,
                                                 const RayRec *recs, int n, int ox, int oy,
-                                                int xe, int ye, const DevCam &cam) {
+                                                int xe, int ye, const DevCam &cam,
+                                                long long budget) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int NW = kThreads / 32;
   constexpr int kRecMax = kRecMaxRay;
@@ -777,10 +783,11 @@ __device__ __forceinline__ bool raster_tile_ray(unsigned long long *zk, RayRec *
       fence_async_smem();
       bulk_g2s(stage, recs + r0, (unsigned)(cnt * sizeof(RayRec)), bar);
     }
-    bool ok = mbar_wait(bar, phase);
+    bool ok = mbar_wait(bar, phase, budget);
     ok = __syncthreads_and(ok);
     if (!ok) {
-      if (tid == 0) mbar_wait(bar, phase);
+      // the copy may still be in flight: drain it (default budget) before the CTA leaves
+      if (tid == 0) mbar_wait(bar, phase, kWaitCycles);
       return false;
     }
     phase ^= 1u;
@@ -918,11 +925,11 @@ __device__ __forceinline__ void raster_block(const WaveArgs &a, int tile, int q,
     ok = raster_tile<TW, TH>(zk, reinterpret_cast<TriRec *>(sbuf),
                              reinterpret_cast<int4 *>(sbuf + kRecMaxPinhole * 48), S, wtot, bar,
                              reinterpret_cast<const TriRec *>(a.bins) + bin * a.tg.cap, n, ox, oy,
-                             xe, ye, a.cam);
+                             xe, ye, a.cam, a.wait_cycles);
   else
     ok = raster_tile_ray<TW, TH>(zk, reinterpret_cast<RayRec *>(sbuf), rx, ry, rz, S, wtot, bar,
                                  reinterpret_cast<const RayRec *>(a.bins) + bin * a.tg.cap, n, ox,
-                                 oy, xe, ye, a.cam);
+                                 oy, xe, ye, a.cam, a.wait_cycles);
   if (!ok) {
     if (tid == 0) atomicOr(a.status, kStatusTimeout);
     return;
@@ -1408,6 +1415,29 @@ cudaError_t launch_retract(const double *T, const double *xi, int n, double *out
                            cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   k_retract<<<(n + 63) / 64, 64, 0, s>>>(T, xi, n, out, jr);
+  return cudaGetLastError();
+}
+
+// out_k = scale_k J_r(xi_k)^T g_k: the chain rule from a gradient at T exp(xi^) to xi.
+__global__ void k_twist_grad(const double *xi, const double *g, const double *scale, int n,
+                             double *out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  double m[6], J[36];
+  for (int u = 0; u < 6; ++u) m[u] = -xi[6 * (long long)k + u];
+  se3_left_jacobian(m, J);
+  const double sc = scale ? scale[k] : 1.0;
+  for (int c = 0; c < 6; ++c) {
+    double acc = 0.0;
+    for (int r = 0; r < 6; ++r) acc += J[6 * r + c] * g[6 * (long long)k + r];
+    out[6 * (long long)k + c] = sc * acc;
+  }
+}
+
+cudaError_t launch_twist_grad(const double *xi, const double *g, const double *scale, int n,
+                              double *out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_twist_grad<<<(n + 63) / 64, 64, 0, s>>>(xi, g, scale, n, out);
   return cudaGetLastError();
 }
 

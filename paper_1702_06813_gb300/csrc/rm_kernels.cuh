@@ -40,6 +40,7 @@ struct WaveArgs {
   double *partial;    // wave: ntiles * kNumVals per pose
   unsigned *status;   // device status word
   const int *skip;    // optional: non-zero means "skip this evaluation" (LM control)
+  long long wait_cycles;  // budget of each bounded device wait, cycles (<= 0: about 2^31)
   // cost inputs
   const float *scan_depth;
   const uint8_t *scan_cls;
@@ -73,6 +74,9 @@ cudaError_t launch_wave(const WaveArgs &a, int mode, cudaStream_t s, cudaEvent_t
 int wave_kernel_launches(const WaveArgs &a, int mode);
 cudaError_t launch_retract(const double *T, const double *xi, int n, double *out, double *jr,
                            cudaStream_t s);
+// out_k = scale_k J_r(xi_k)^T g_k (scale optional: 1), device arrays.
+cudaError_t launch_twist_grad(const double *xi, const double *g, const double *scale, int n,
+                              double *out, cudaStream_t s);
 // n copies of `pose` (device, 16 doubles) and the twists t_i e_axis of a sweep (rm_util.cu).
 cudaError_t launch_sweep_inputs(const double *pose, int axis, double span, int n, double *poses,
                                 double *twists, cudaStream_t s);
@@ -236,4 +240,6 @@ void set_error(const std::string &msg);
 rm_status check_intrinsics(const rm_intrinsics *in);
 // True for device (or managed) memory.
 bool is_device_pointer(const void *p);
+// The device the map's arrays live on (the device current at rm_map_create).
+int map_device(const rm_map *map);
 }  // namespace rmapi

@@ -34,13 +34,15 @@ rm_status na_fail(rm_status s, const std::string &m) {
   return s;
 }
 
-bool na_on_device(const void *p) {
+// True when p is device (or managed) memory; *dev receives its device.
+bool na_on_device(const void *p, int *dev = nullptr) {
   if (!p) return false;
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
+  if (dev) *dev = at.device;
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
@@ -53,18 +55,25 @@ extern "C" rm_status rm_cost_grad_noalloc(const rm_map *map, const rm_scan *scan
                                           const rm_cost_out *out, void *stream) {
   if (!map || !scan || !pose || !params || !out) return na_fail(RM_EINVAL, "NULL argument");
   if (!scan->depth || !scan->cls) return na_fail(RM_EINVAL, "scan arrays are NULL");
-  if (!na_on_device(scan->depth) || !na_on_device(scan->cls))
-    return na_fail(RM_EINVAL, "rm_cost_grad_noalloc needs the scan in device memory");
-  const void *outs[5] = {out->counts, out->e_table, out->e_ls, out->grad, out->jtj};
-  for (const void *p : outs)
-    if (p && !na_on_device(p))
-      return na_fail(RM_EINVAL, "rm_cost_grad_noalloc writes device outputs only");
-  if (!(params->eps >= 0.0f)) return na_fail(RM_EINVAL, "eps must be >= 0");
-  cudaStream_t s = (cudaStream_t)stream;
-
+  // The kernels run on the current device and read the map's arrays there, so the map, the
+  // scan and the outputs must all live on the current device (the call never switches).
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
     return na_fail(RM_ECUDA, "no usable current device");
+  if (rmapi::map_device(map) != dev)
+    return na_fail(RM_EINVAL, "rm_cost_grad_noalloc: the map lives on device " +
+                                  std::to_string(rmapi::map_device(map)) + ", the current device is " +
+                                  std::to_string(dev));
+  int pd = -1;
+  if (!na_on_device(scan->depth, &pd) || pd != dev || !na_on_device(scan->cls, &pd) || pd != dev)
+    return na_fail(RM_EINVAL, "rm_cost_grad_noalloc needs the scan in device memory of the current device");
+  const void *outs[5] = {out->counts, out->e_table, out->e_ls, out->grad, out->jtj};
+  for (const void *p : outs)
+    if (p && (!na_on_device(p, &pd) || pd != dev))
+      return na_fail(RM_EINVAL, "rm_cost_grad_noalloc writes device outputs of the current device only");
+  if (!(params->eps >= 0.0f)) return na_fail(RM_EINVAL, "eps must be >= 0");
+  cudaStream_t s = (cudaStream_t)stream;
+
   unsigned char *base;
   {
     std::lock_guard<std::mutex> lk(g_scratch_mu);

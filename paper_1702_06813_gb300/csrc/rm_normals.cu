@@ -322,22 +322,40 @@ rm_status run_normals(const rm_intrinsics *intr, int32_t n, const float *depth, 
   return RM_OK;
 }
 
+// True when the byte ranges [a, a + na) and [b, b + nb) share a byte (NULL overlaps nothing).
+bool overlaps(const void *a, size_t na, const void *b, size_t nb) {
+  if (!a || !b) return false;
+  const char *a0 = static_cast<const char *>(a), *b0 = static_cast<const char *>(b);
+  return a0 < b0 + nb && b0 < a0 + na;
+}
+
 }  // namespace
 
 extern "C" rm_status rm_depth_normals(const rm_intrinsics *intr, int32_t n, const float *depth,
                                       const uint8_t *cls, float sigma, int32_t metric,
                                       float *normals, float *smoothed, void *stream) {
   if (!normals && n > 0) return dn_fail(RM_EINVAL, "normals is NULL");
+  // neighbouring tiles read the inputs' halos while a tile writes its outputs, so no output
+  // may share memory with an input or with the other output
+  if (intr && n > 0 && intr->width > 0 && intr->height > 0) {
+    const size_t np = (size_t)n * intr->width * intr->height;
+    const size_t bd = sizeof(float) * np, bc = np, bn = 3 * sizeof(float) * np, bs = sizeof(float) * np;
+    if (overlaps(normals, bn, depth, bd) || overlaps(normals, bn, cls, bc))
+      return dn_fail(RM_EINVAL, "normals overlaps an input");
+    if (overlaps(smoothed, bs, depth, bd) || overlaps(smoothed, bs, cls, bc))
+      return dn_fail(RM_EINVAL, "smoothed overlaps an input");
+    if (overlaps(normals, bn, smoothed, bs)) return dn_fail(RM_EINVAL, "normals overlaps smoothed");
+  }
   return run_normals(intr, n, depth, cls, sigma, metric, normals, smoothed, nullptr, stream);
 }
 
 extern "C" rm_status rm_depth_blur(const rm_intrinsics *intr, int32_t n, const float *depth,
                                    const uint8_t *cls, float sigma, float *out, void *stream) {
   if (!out && n > 0) return dn_fail(RM_EINVAL, "out is NULL");
-  if (intr && depth && out && n > 0 && intr->width > 0 && intr->height > 0) {
-    const size_t bytes = sizeof(float) * (size_t)n * intr->width * intr->height;
-    const char *a0 = reinterpret_cast<const char *>(depth), *b0 = reinterpret_cast<const char *>(out);
-    if (a0 < b0 + bytes && b0 < a0 + bytes) return dn_fail(RM_EINVAL, "out overlaps depth");
+  if (intr && n > 0 && intr->width > 0 && intr->height > 0) {
+    const size_t np = (size_t)n * intr->width * intr->height;
+    if (overlaps(out, sizeof(float) * np, depth, sizeof(float) * np)) return dn_fail(RM_EINVAL, "out overlaps depth");
+    if (overlaps(out, sizeof(float) * np, cls, np)) return dn_fail(RM_EINVAL, "out overlaps cls");
   }
   return run_normals(intr, n, depth, cls, sigma, 0, nullptr, nullptr, out, stream);
 }

@@ -139,8 +139,8 @@ class Map:
         check(lib().rm_map_info(self.handle, None, None, c.ctypes.data_as(ctypes.c_void_p)))
         return c
 
-    def set_tuning(self, tile=(0, 0), bin_capacity=0, wave_poses=0, async_status=False):
-        t = N.rm_tuning(tile[0], tile[1], bin_capacity, wave_poses, int(async_status))
+    def set_tuning(self, tile=(0, 0), bin_capacity=0, wave_poses=0, async_status=False, wait_log2=0):
+        t = N.rm_tuning(tile[0], tile[1], bin_capacity, wave_poses, int(async_status), int(wait_log2))
         check(lib().rm_map_set_tuning(self.handle, ctypes.byref(t)))
 
     def profile(self, enable: bool):
@@ -160,7 +160,8 @@ class Map:
         t = N.rm_tuning()
         check(lib().rm_map_get_tuning(self.handle, ctypes.byref(t)))
         return {"tile": (t.tile_w, t.tile_h), "bin_capacity": t.bin_capacity,
-                "wave_poses": t.wave_poses, "async_status": bool(t.async_status)}
+                "wave_poses": t.wave_poses, "async_status": bool(t.async_status),
+                "wait_log2": t.wait_log2}
 
 
 def _poses(poses, device="cuda"):
@@ -434,25 +435,40 @@ class RenderMapCost(torch.autograd.Function):
     """e_ls(pose * exp(xi^)) as a differentiable function of the twist xi (6,) float64.
 
     forward: retraction and the fused render + Table I + least-squares + adjoint kernels;
-    backward: grad_output * J_r(xi)^T g, g the adjoint gradient at the retracted pose.
-    Usage: RenderMapCost.apply(xi, pose, map, scan, params) -> scalar tensor.
+    backward: grad_output * J_r(xi)^T g (rm_twist_grad), g the adjoint gradient at the
+    retracted pose. Usage: RenderMapCost.apply(xi, pose, map, scan, params) -> scalar tensor.
     """
 
     @staticmethod
     def forward(ctx, xi, pose, m, scan, params=None):
         pose_t = _dev_tensor(pose, torch.float64).reshape(1, 16)
-        xi_d = xi.detach().to(device="cuda", dtype=torch.float64).reshape(1, 6)
-        p, jr = pose_retract(pose_t, xi_d, with_jacobian=True)
+        xi_d = xi.detach().to(device="cuda", dtype=torch.float64).reshape(1, 6).contiguous()
+        p = pose_retract(pose_t, xi_d)
         res = cost_grad(m, scan, p.reshape(1, 16), params)
-        ctx.save_for_backward(res["grad"][0], jr[0])
+        ctx.save_for_backward(res["grad"], xi_d)
         ctx.xi_device = xi.device
         return res["e_ls"][0].to(xi.device)
 
     @staticmethod
     def backward(ctx, grad_out):
-        g, jr = ctx.saved_tensors
-        gx = jr.transpose(0, 1) @ g
-        return (grad_out.to(gx.device) * gx).to(ctx.xi_device), None, None, None, None
+        g, xi_d = ctx.saved_tensors
+        return twist_grad(xi_d, g, grad_out)[0].to(ctx.xi_device), None, None, None, None
+
+
+def twist_grad(twists, grads, scale=None):
+    """scale_k * J_r(twists_k)^T grads_k on the device (rm_twist_grad): (n, 6) float64."""
+    t = _dev_tensor(twists, torch.float64).reshape(-1, 6).contiguous()
+    g = _dev_tensor(grads, torch.float64).reshape(-1, 6).contiguous()
+    n = t.shape[0]
+    if g.shape[0] != n:
+        raise ValueError("one gradient per twist")
+    sc = None
+    if scale is not None:
+        sc = _dev_tensor(scale, torch.float64).reshape(-1)
+        sc = (sc.expand(n) if sc.numel() == 1 else sc).contiguous()
+    out = torch.empty((n, 6), dtype=torch.float64, device="cuda")
+    check(lib().rm_twist_grad(_ptr(t), _ptr(g), _ptr(sc), n, _ptr(out), _stream()))
+    return out
 
 
 def _problems(problems=None, scans=None, poses=None):

@@ -73,6 +73,17 @@ def test_argument_errors_without_gpu(lib):
     assert lib.rm_depth_blur(ctypes.byref(intr), 1, buf.ctypes.data, cls.ctypes.data, 1.0,
                              buf.ctypes.data + 4 * 10, None) == N.RM_EINVAL
     assert b"overlaps" in lib.rm_last_error()
+    # nor may the normals' outputs overlap an input or each other
+    big = np.zeros(4 * 64 * 3, np.float32)
+    assert lib.rm_depth_normals(ctypes.byref(intr), 1, buf.ctypes.data, cls.ctypes.data, 1.0, 0,
+                                buf.ctypes.data + 4 * 8, None, None) == N.RM_EINVAL
+    assert b"normals overlaps" in lib.rm_last_error()
+    assert lib.rm_depth_normals(ctypes.byref(intr), 1, buf.ctypes.data, cls.ctypes.data, 1.0, 0,
+                                big.ctypes.data, cls.ctypes.data, None) == N.RM_EINVAL
+    assert b"smoothed overlaps" in lib.rm_last_error()
+    assert lib.rm_depth_normals(ctypes.byref(intr), 1, buf.ctypes.data, cls.ctypes.data, 1.0, 0,
+                                big.ctypes.data, big.ctypes.data + 4 * 100, None) == N.RM_EINVAL
+    assert b"normals overlaps smoothed" in lib.rm_last_error()
     assert lib.rm_depth_normals(None, 1, None, None, 1.0, 0, None, None, None) == N.RM_EINVAL
 
 
