@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 
 import cases
+import checks
 import oracle
 import synth
 
@@ -73,8 +74,8 @@ def test_batch_cost_grad_equals_single_calls(mixed):
         o = mixed["om"].cost(pr["start"], pr["cam"], *pr["scan"])
         assert np.array_equal(_np(b["counts"][k]), o["counts"])
         assert abs(float(b["e_ls"][k]) - o["e_ls"]) <= 1e-5 * abs(o["e_ls"])
-        g = _np(b["grad"][k])
-        assert np.linalg.norm(g - o["grad"]) <= 1e-3 * np.linalg.norm(o["grad"])
+        checks.close_elementwise(_np(b["grad"][k]), o["grad"], 1e-3, f"batch_grad[{k}]")
+        checks.close_elementwise(_np(b["jtj"][k]), o["jtj"], 1e-3, f"batch_jtj[{k}]")
 
 
 def test_batch_align_equals_single_calls(mixed):

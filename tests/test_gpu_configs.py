@@ -1,0 +1,274 @@
+"""Parity at each workload's stated size, through the C ABI, against the FP64 oracle.
+
+- C1: 160x120, ~20k triangles, sigma 1 cm, 5% dropout: one cost evaluation, then LM from
+  5 cm / 2 deg to the oracle's pose within 1 mm / 0.01 deg.
+- C2: 640x480 Kinect camera, ~500k triangles (20% FU interfaces), noise 0.5% of depth:
+  cost and adjoint gradient against the oracle's FP64 values, against central finite
+  differences at h = 1e-4 of the oracle's frozen-visibility cost, and through the
+  torch.autograd.Function (RenderMapCost) backward.
+- C3: 256 candidate poses (10 cm / 5 deg) at 320x240 on the 1M-triangle room, all in one
+  persistent launch (and in waves): every pose against the oracle.
+- C4: 1024x64 panoramic Lidar on the 2M-triangle terrain: LM from 30 cm / 3 deg lands within
+  1 mm / 0.01 deg of the oracle's LM.
+- C5: the 64-agent mixed-sensor tracking batch on the 2M-triangle terrain, 5 LM iterations
+  per agent in one persistent launch: on two sampled frames, every agent's pose against the
+  oracle's 5-iteration LM from the same start.
+
+Tolerances: Table I counts bit for bit, E_ls 1e-5 relative, gradients and J^T J 1e-3
+element by element (tests/checks.py), poses 1 mm / 0.01 deg.
+"""
+from __future__ import annotations
+
+import math
+import os
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+import pytest
+from scipy.spatial.transform import Rotation
+
+import cases
+import checks
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - the gpu marker is deselected on CPU
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1702_06813_gb300 as rm  # noqa: E402
+from paper_1702_06813_gb300 import build as rmbuild  # noqa: E402
+
+rmbuild.build()
+
+EPS_REL_COST = 1e-5
+EPS_REL_GRAD = 1e-3
+POOL = ThreadPoolExecutor(max_workers=os.cpu_count() or 4)  # the oracle's C calls drop the GIL
+
+
+def _np(t):
+    return t.detach().cpu().numpy() if torch.is_tensor(t) else np.asarray(t)
+
+
+def _pose_gap(a, b):
+    dt = float(np.linalg.norm(a[:3, 3] - b[:3, 3]))
+    da = math.degrees(Rotation.from_matrix(a[:3, :3].T @ b[:3, :3]).magnitude())
+    return dt, da
+
+
+def _check_cost(g, k, o, grad=True, what=""):
+    assert np.array_equal(_np(g["counts"])[k], o["counts"]), (what, k)
+    assert int(_np(g["e_table"])[k]) == int(o["counts"][1] + o["counts"][3] + o["counts"][5]
+                                            - o["counts"][0] - o["counts"][2] - o["counts"][4])
+    e = float(_np(g["e_ls"])[k])
+    assert abs(e - o["e_ls"]) <= EPS_REL_COST * abs(o["e_ls"]) + 1e-12, (what, k, e, o["e_ls"])
+    if grad:
+        checks.close_elementwise(_np(g["grad"])[k], o["grad"], EPS_REL_GRAD, f"{what}_grad[{k}]", floor=1e-9)
+        checks.close_elementwise(_np(g["jtj"])[k], o["jtj"], EPS_REL_GRAD, f"{what}_jtj[{k}]", floor=1e-9)
+
+
+def _batch_rows(b, k):
+    return {"counts": b["counts"][k], "e_ls": b["e_ls"][k], "grad": b["grad"][k], "jtj": b["jtj"][k]}
+
+
+# ---------------------------------------------------------------------------------------
+# C1
+# ---------------------------------------------------------------------------------------
+
+def test_c1_cost_then_lm():
+    c = cases.config1(seed=1000)
+    mesh, cam = c["mesh"], c["cam"]
+    assert 19_000 <= mesh.n_tris <= 21_000
+    om = oracle.OracleMap(mesh.vertices, mesh.faces, mesh.labels)
+    gm = rm.Map(mesh.vertices, mesh.faces, mesh.labels)
+    scan = rm.Scan.make(rm.Intrinsics.from_camera(cam), *c["scan"])
+    g = rm.cost_grad(gm, scan, c["start"][None])
+    _check_cost(g, 0, om.cost(c["start"], cam, *c["scan"]), what="c1")
+    pg, rep = rm.align(gm, scan, c["start"], max_iters=50, step_tol=1e-7)
+    po, orep = om.align(c["start"], cam, *c["scan"], max_iters=50, step_tol=1e-7)
+    dt, da = _pose_gap(pg, po)
+    assert dt < 1e-3 and da < 1e-2, (dt, da, rep, orep)
+    gm.close()
+
+
+# ---------------------------------------------------------------------------------------
+# C2
+# ---------------------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def c2():
+    c = cases.config2()  # 400k FO + 100k FU triangles, 640x480, noise 0.5% of depth
+    mesh, cam = c["mesh"], c["cam"]
+    om = oracle.OracleMap(mesh.vertices, mesh.faces, mesh.labels)
+    gm = rm.Map(mesh.vertices, mesh.faces, mesh.labels)
+    scan = rm.Scan.make(rm.Intrinsics.from_camera(cam), *c["scan"])
+    yield dict(c, om=om, gm=gm, gscan=scan)
+    gm.close()
+
+
+def test_c2_size(c2):
+    mesh = c2["mesh"]
+    assert 475_000 <= mesh.n_tris <= 525_000
+    fu = float(np.mean(mesh.labels == 1))
+    assert 0.18 <= fu <= 0.22, fu
+    assert (c2["cam"].width, c2["cam"].height, c2["cam"].fx) == (640, 480, 525.0)
+
+
+def test_c2_cost_and_gradient_against_oracle(c2):
+    r = cases.rng(2101)
+    poses = [c2["gt"], c2["start"]] + [synth.perturb_fixed(c2["gt"], r, 0.1, 3.0) for _ in range(2)]
+    g = rm.cost_grad(c2["gm"], c2["gscan"], np.stack(poses))
+    outs = list(POOL.map(lambda P: c2["om"].cost(P, c2["cam"], *c2["scan"]), poses))
+    for k, o in enumerate(outs):
+        _check_cost(g, k, o, what="c2")
+    # every Table I outcome of the FU interfaces shows up
+    assert np.all(_np(g["counts"]).sum(0)[[0, 1, 4, 5]] > 0)
+
+
+def test_c2_gradient_against_central_fd_h1e4(c2):
+    """Central differences (h = 1e-4) of the oracle's FP64 frozen-visibility cost, the
+    quantity the adjoint differentiates."""
+    P = c2["start"]
+    g = _np(rm.cost_grad(c2["gm"], c2["gscan"], P[None])["grad"])[0]
+    h = 1e-4
+
+    def fd(a):
+        xi = np.zeros(6)
+        xi[a] = h
+        return (c2["om"].cost_frozen(P, c2["cam"], *c2["scan"], xi)
+                - c2["om"].cost_frozen(P, c2["cam"], *c2["scan"], -xi)) / (2 * h)
+
+    d = np.array(list(POOL.map(fd, range(6))))
+    checks.close_elementwise(g, d, EPS_REL_GRAD, "c2_grad_vs_fd_h1e-4")
+
+
+def test_c2_autograd_backward(c2):
+    """RenderMapCost (torch.autograd.Function): forward equals the oracle's E_ls at the
+    retracted pose; backward equals the chain rule J_r(xi)^T grad of the oracle, and central
+    differences (h = 1e-4) of the oracle's frozen cost in xi."""
+    P = c2["start"]
+    xi0 = np.array([0.004, -0.006, 0.003, 0.002, -0.001, 0.003])
+    xi = torch.tensor(xi0, dtype=torch.float64, requires_grad=True)
+    e = rm.RenderMapCost.apply(xi, P, c2["gm"], c2["gscan"], None)
+    e.backward()
+    Pr = oracle.se3_right(P, xi0)
+    o = c2["om"].cost(Pr, c2["cam"], *c2["scan"])
+    assert abs(e.item() - o["e_ls"]) <= EPS_REL_COST * o["e_ls"]
+    _, jr = rm.pose_retract(P[None], xi0[None], with_jacobian=True)
+    checks.close_elementwise(_np(xi.grad), _np(jr[0]).T @ o["grad"], EPS_REL_GRAD, "c2_autograd")
+    # the same derivative by differences in xi, through the frozen cost at P exp(xi +- h e_a)
+    h = 1e-4
+
+    def fd(a):
+        d = np.zeros(6)
+        d[a] = h
+        # frozen cells of the retracted pose; the perturbation is applied on the right of it
+        Jp = oracle.se3_right(np.eye(4), xi0 + d)
+        Jm = oracle.se3_right(np.eye(4), xi0 - d)
+        E0 = oracle.se3_right(np.eye(4), xi0)
+        xp = _log_se3(np.linalg.inv(E0) @ Jp)
+        xm = _log_se3(np.linalg.inv(E0) @ Jm)
+        return (c2["om"].cost_frozen(Pr, c2["cam"], *c2["scan"], xp)
+                - c2["om"].cost_frozen(Pr, c2["cam"], *c2["scan"], xm)) / (2 * h)
+
+    d = np.array(list(POOL.map(fd, range(6))))
+    checks.close_elementwise(_np(xi.grad), d, EPS_REL_GRAD, "c2_autograd_vs_fd")
+
+
+def _log_se3(T):
+    """Twist (rho, phi) with se3_right(I, xi) == T (small rotations; inverse of the SE(3)
+    exponential by the left Jacobian's inverse)."""
+    R = T[:3, :3]
+    phi = Rotation.from_matrix(R).as_rotvec()
+    th = np.linalg.norm(phi)
+    K = np.array([[0, -phi[2], phi[1]], [phi[2], 0, -phi[0]], [-phi[1], phi[0], 0]])
+    if th < 1e-12:
+        Jinv = np.eye(3) - 0.5 * K
+    else:
+        a = (1 - th * math.sin(th) / (2 * (1 - math.cos(th)))) / th ** 2
+        Jinv = np.eye(3) - 0.5 * K + a * K @ K
+    return np.concatenate([Jinv @ T[:3, 3], phi])
+
+
+# ---------------------------------------------------------------------------------------
+# C3
+# ---------------------------------------------------------------------------------------
+
+def test_c3_256_poses_320x240_persistent_and_waves():
+    w = synth.workload_headline(3000, 256)  # 800k FO + 200k FU; poses 10 cm / 5 deg around GT
+    mesh = w["mesh"]
+    assert 990_000 <= mesh.n_tris <= 1_010_000
+    cam = synth.cam_320x240()
+    scan_np = synth.synth_scan(mesh, cam, w["gt"], cases.rng(3301), sigma_rel=0.005)
+    gm = rm.Map(mesh.vertices, mesh.faces, mesh.labels)
+    om = oracle.OracleMap(mesh.vertices, mesh.faces, mesh.labels)
+    scan = rm.Scan.make(rm.Intrinsics.from_camera(cam), *scan_np)
+    poses = torch.as_tensor(w["poses"].reshape(-1, 16), dtype=torch.float64, device="cuda")
+    b = rm.cost_grad_batch(gm, scans=scan, poses=poses)   # one persistent launch (CUDA graph)
+    waves = rm.cost_grad(gm, scan, poses)
+    o = om.cost_batch(w["poses"], cam, *scan_np)
+    for k in range(256):
+        ok = {"counts": o["counts"][k], "e_ls": o["e_ls"][k], "grad": o["grad"][k], "jtj": o["jtj"][k]}
+        _check_cost(b, k, ok, what="c3")
+    for key in ("counts", "e_table", "e_ls", "grad", "jtj"):
+        assert torch.equal(b[key], waves[key]), key
+    gm.close()
+
+
+# ---------------------------------------------------------------------------------------
+# C4, C5: the 2M-triangle terrain
+# ---------------------------------------------------------------------------------------
+
+def test_c4_lidar_lm_full_size():
+    w = synth.workload_lidar()  # 1.4M FO + 0.6M FU, 1024x64, sigma 2 cm, start 30 cm / 3 deg
+    mesh, cam = w["mesh"], w["cam"]
+    assert 1_900_000 <= mesh.n_tris <= 2_100_000
+    fu = float(np.mean(mesh.labels == 1))
+    assert 0.27 <= fu <= 0.33, fu
+    gm = rm.Map(mesh.vertices, mesh.faces, mesh.labels)
+    om = oracle.OracleMap(mesh.vertices, mesh.faces, mesh.labels)
+    scan = rm.Scan.make(rm.Intrinsics.from_camera(cam), *w["scan"])
+    pg, rep = rm.align(gm, scan, w["start"], max_iters=200, step_tol=1e-7)
+    po, orep = om.align(w["start"], cam, *w["scan"], max_iters=200, step_tol=1e-7)
+    dt, da = _pose_gap(pg, po)
+    assert dt < 1e-3 and da < 1e-2, (dt, da, rep, orep)
+    assert rep["e_ls_final"] < rep["e_ls_initial"]
+    gm.close()
+
+
+def test_c5_tracking_batch_sampled_frames():
+    w = synth.workload_tracking(5000, n_agents=64, n_frames=200)
+    mesh, cams, kinds, truth = w["mesh"], w["cams"], w["kinds"], w["poses"]
+    assert 1_900_000 <= mesh.n_tris <= 2_100_000
+    gm = rm.Map(mesh.vertices, mesh.faces, mesh.labels)
+    om = oracle.OracleMap(mesh.vertices, mesh.faces, mesh.labels)
+    fo = mesh.labels == 0
+    om_fo = oracle.OracleMap(mesh.vertices, mesh.faces[fo], mesh.labels[fo])
+    intr = [rm.Intrinsics.from_camera(c) for c in cams]
+    n = truth.shape[1]
+    for f in (0, 120):
+        r = cases.rng(5100 + f)
+        starts = np.stack([synth.perturb_fixed(truth[f, a], r, 0.10, 1.0) for a in range(n)])
+        noise = [r.normal(size=(cams[kinds[a]].height, cams[kinds[a]].width)) for a in range(n)]
+
+        def scan_of(a):
+            cam = cams[kinds[a]]
+            d = om_fo.render(truth[f, a], cam)["depth"].astype(np.float64)
+            sig = 0.02 if cam.model != "pinhole" else 0.005 * np.nan_to_num(d, nan=0.0)
+            d = d + sig * noise[a]
+            far = ~(d <= cam.range_max)
+            d[far] = cam.range_max
+            return d.astype(np.float32), far.astype(np.uint8)
+
+        scans = list(POOL.map(scan_of, range(n)))
+        gscans = [rm.Scan.make(intr[kinds[a]], *scans[a]) for a in range(n)]
+        pg, reps, status = rm.align_batch(gm, [(gscans[a], starts[a]) for a in range(n)], max_iters=5)
+        outs = list(POOL.map(lambda a: om.align(starts[a], cams[kinds[a]], *scans[a], max_iters=5), range(n)))
+        for a in range(n):
+            po, orep = outs[a]
+            dt, da = _pose_gap(pg[a], po)
+            assert dt < 1e-3 and da < 1e-2, (f, a, kinds[a], dt, da, reps[a], orep)
+            assert reps[a]["iters"] == orep["iters"], (f, a, reps[a], orep)
+    gm.close()

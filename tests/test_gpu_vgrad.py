@@ -1,6 +1,7 @@
 """Vertex-position gradient (map refinement) on the GPU vs the CPU oracle, through the C ABI:
-within 1e-3 of the oracle's FP64 gradient (norm over all vertices; FP32 barycentrics and
-normals), summed over poses, for both camera models."""
+vertex by vertex within 1e-3 of the oracle's FP64 gradient (floor 1e-2 of the largest
+vertex's, tests/checks.py; FP32 barycentrics and normals), summed over poses, for both camera
+models; vertices the oracle leaves at zero are exactly zero."""
 from __future__ import annotations
 
 import dataclasses
@@ -9,6 +10,7 @@ import numpy as np
 import pytest
 
 import cases
+import checks
 import oracle
 import synth
 
@@ -25,7 +27,8 @@ rmbuild.build()
 
 
 def _close(g, o, rel=1e-3):
-    assert np.linalg.norm(g - o) <= rel * np.linalg.norm(o), (np.linalg.norm(g - o), np.linalg.norm(o))
+    assert (np.linalg.norm(o, axis=1) > 0).sum() > 100
+    checks.close_rows(g, o, rel, "vertex_grad")
 
 
 def test_vertex_grad_parity_pinhole():
