@@ -127,6 +127,13 @@ def algorithmic_bytes(V, T, P):
             "total": 12 * V + 13 * T + 5 * P}
 
 
+def step_algorithmic_bytes(V, T, P, n_poses, wave_poses):
+    """Bytes one batched step must move from HBM: the map once per wave of poses (every pose
+    of a wave shares it) and the scan comparison once per pose."""
+    waves = -(-n_poses // max(1, wave_poses))
+    return (12 * V + 13 * T) * waves + 5 * P * n_poses
+
+
 class Clocks:
     """nvidia-smi clock / throttle sampling while the timed region runs."""
 
@@ -200,7 +207,9 @@ def cpu_baseline(w, min_seconds=1.5):
 
 
 def run_reference(a):
-    """The oracle timed as it stands, same workload and metric (rank 0 only)."""
+    """The oracle timed as it stands on the host cores (OpenMP over poses), on the same
+    workload, batch, metric and step count as the GPU arm (rank 0 only): each step is one
+    pass over the candidate-pose batch (about 0.3 s on 16 cores for 256 poses)."""
     rank = rank_info()[1]
     if rank != 0:
         return
@@ -210,24 +219,24 @@ def run_reference(a):
     oracle.build()
     om = oracle.OracleMap(w["mesh"].vertices, w["mesh"].faces, w["mesh"].labels)
     sd, sc = w["scan"]
-    per_step = max(1, a.cpu_sample)
-    steps = max(1, min(a.steps, 5))
-    for k in range(max(0, min(a.warmup, 1))):
-        om.cost_batch(w["poses"][:per_step], w["cam"], sd, sc)
+    poses = w["poses"]
+    for k in range(max(1, a.warmup)):
+        om.cost_batch(poses, w["cam"], sd, sc)
     t0 = time.perf_counter()
     threads = 1
-    for k in range(steps):
-        sel = w["poses"][(k * per_step) % len(w["poses"]):][:per_step]
-        threads = om.cost_batch(sel, w["cam"], sd, sc)["threads"]
+    for k in range(a.steps):
+        threads = om.cost_batch(poses, w["cam"], sd, sc)["threads"]
     dt = time.perf_counter() - t0
-    v = steps * per_step / dt
+    v = a.steps * len(poses) / dt
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus,
-        "steps": steps, "warmup": a.warmup, "ms_per_step": 1e3 * dt / steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w["name"], "poses_per_step": per_step},
+        "steps": a.steps, "warmup": max(1, a.warmup), "ms_per_step": 1e3 * dt / a.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": w["name"], "poses_per_gpu": len(poses), "triangles": w["mesh"].n_tris,
+                   "image": [w["cam"].width, w["cam"].height]},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": int(threads), "kind": "oracle",
-                         "sample": f"{per_step} poses per step of the {len(w['poses'])}-pose batch"},
+                         "sample": f"{a.steps} passes over the {len(poses)}-pose batch, OpenMP over poses"},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
@@ -316,6 +325,43 @@ def run_tracking(a):
         plain_ms += (time.perf_counter() - t0) * 1e3
     plain_value = n_agents * n_plain / (plain_ms * 1e-3)
     errs = np.array(errs)
+    # roofline of the one kernel of a frame (the persistent batch kernel): algorithmic bytes per
+    # launch = the map once plus the scan comparison of every evaluation of every agent
+    pk, pk_kind = peaks()
+    p_img = [c.width * c.height for c in cams]
+    evals_per_agent = 1 + 5 if a.method == "lm" else 5
+    launch_bytes = 12 * mesh.n_verts + 13 * mesh.n_tris + sum(5 * p_img[k] * evals_per_agent for k in kinds)
+    achieved = launch_bytes / (total_ms / a.frames * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "k_persist", "achieved": achieved, "peak": pk["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "traffic": None, "peak_kind": pk_kind,
+                "avg_launch_ms": total_ms / a.frames, "algorithmic_bytes_per_launch": launch_bytes}
+    cpu = None
+    if not a.no_cpu_baseline:
+        # the oracle's LM (or ICP) of each agent from the same starts, one agent per host thread,
+        # on the first frame (a bounded sample: every agent once)
+        import oracle
+        from concurrent.futures import ThreadPoolExecutor
+        oracle.build()
+        om = oracle.OracleMap(mesh.vertices, mesh.faces, mesh.labels)
+        sc0 = scans_for(0)
+        host = [(sc0[i].depth.cpu().numpy(), sc0[i].cls.cpu().numpy()) for i in range(n_agents)]
+        start0 = np.stack([synth.perturb_fixed(truth[0, i], np.random.Generator(np.random.PCG64(a.seed + 11 + i)),
+                                               0.10, 1.0) for i in range(n_agents)])
+
+        def orc(i):
+            cam = cams[kinds[i]]
+            if a.method == "icp":
+                return om.icp_align(start0[i], cam, *host[i], 0.3, max_iters=5, step_tol=1e-4)
+            return om.align(start0[i], cam, *host[i], max_iters=5)
+
+        cores = os.cpu_count() or 1
+        with ThreadPoolExecutor(max_workers=cores) as pool:
+            t0 = time.perf_counter()
+            list(pool.map(orc, range(n_agents)))
+            dt = time.perf_counter() - t0
+        cpu = {"value": n_agents / dt, "unit": "scan frames/s", "cores": cores, "kind": "oracle",
+               "sample": f"one frame of {n_agents} agents (each 5 iterations), one agent per host thread, "
+                         f"{dt:.1f} s wall"}
     print(json.dumps({
         "metric": ("tracking frames/s (64 mixed scans, 5 LM iterations each, 2M-triangle map)" if a.method == "lm"
                    else "tracking frames/s (64 mixed scans, 5 point-to-plane ICP iterations each, 2M-triangle map)"),
@@ -329,6 +375,7 @@ def run_tracking(a):
                    "median_pos_err_m_all_frames": float(np.median(errs)),
                    "agents_within_0.1m_last_frame": float(np.mean(errs[-1] < 0.1)),
                    "agents_within_0.1m_all_frames": float(np.mean(np.all(errs < 0.1, axis=0)))},
+        "roofline": roofline, "cpu_baseline": cpu,
         "gpu_launches": a.frames}))
 
 
@@ -592,7 +639,8 @@ def run_icp(a):
                    "align_room_1M_640x480": room_align, "align_lidar_2M_1024x64": lidar_align,
                    "depth_normals_eq2": normals_line, "meshify_sec3a": mesh_line,
                    "dfo_align_table1_room": dfo_line, "vertex_grad": vgrad_line, "cost_sweep_fig7": sweep_line,
-                   "step_hbm_roofline_frac": ab["total"] * n * a.steps / (ms * 1e-3) / 1e9 / pk["hbm_gbs"]},
+                   "step_hbm_roofline_frac": step_algorithmic_bytes(mesh.n_verts, mesh.n_tris, P, n, min(n, 128))
+                   * a.steps / (ms * 1e-3) / 1e9 / pk["hbm_gbs"]},
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": "pose evals/s",
                 "h2d_bytes_per_step": int(hp.numel() * 8 + hd.numel() * 4 + hc.numel()),
@@ -608,14 +656,18 @@ def run_icp(a):
         om = oracle.OracleMap(mesh.vertices, mesh.faces, mesh.labels)
         sd, sc = w["scan"]
         om.icp_terms(w["poses"][0], cam, sd, sc, tol)
-        done = 0
-        t0 = time.perf_counter()
-        while time.perf_counter() - t0 < 3.0:
-            om.icp_terms(w["poses"][done % n], cam, sd, sc, tol)
-            done += 1
-        dt = time.perf_counter() - t0
-        line["cpu_baseline"] = {"value": done / dt, "unit": "pose evals/s", "cores": 1, "kind": "oracle",
-                                "sample": f"{done} of the candidate poses, one thread, {dt:.1f} s wall"}
+        from concurrent.futures import ThreadPoolExecutor
+        cores = os.cpu_count() or 1
+        with ThreadPoolExecutor(max_workers=cores) as pool:  # the oracle's C calls drop the GIL
+            done = 0
+            t0 = time.perf_counter()
+            while time.perf_counter() - t0 < 2.0:
+                list(pool.map(lambda k: om.icp_terms(w["poses"][k], cam, sd, sc, tol), range(n)))
+                done += n
+            dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": done / dt, "unit": "pose evals/s", "cores": cores, "kind": "oracle",
+                                "sample": f"{done // n} pass(es) over the {n} candidate poses, one pose per "
+                                          f"host thread, {dt:.1f} s wall"}
         line["config"]["oracle_per_row"] = oracle_row_timings(w, dstart, tol)
     print(json.dumps(line))
     gm.close()
@@ -777,7 +829,9 @@ def main():
     avg_s = tot * 1e-3 / launches
     achieved = ab[dom] * per_launch_poses / avg_s / 1e9
     share = {k: round(v[1] / sum(x[1] for x in kern.values()), 4) for k, v in kern.items()}
-    step_frac = ab["total"] * (n * a.steps) / (ms * 1e-3) / 1e9 / pk["hbm_gbs"]
+    step_bytes = step_algorithmic_bytes(mesh.n_verts, mesh.n_tris, P, n, tune["wave_poses"])
+    step_frac = step_bytes * a.steps / (ms * 1e-3) / 1e9 / pk["hbm_gbs"]
+    dram_raster = measured_traffic(dom, per_launch_poses, mesh.n_tris)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
@@ -792,14 +846,17 @@ def main():
                    "persistent_graph_evals_per_s": pers_value,
                    "batched_over_plain": value / plain_value,
                    "algorithmic_mb_per_eval": ab["total"] / 1e6,
+                   "step_algorithmic_mb_map_once_per_wave": step_bytes / 1e6,
                    "step_hbm_roofline_frac": step_frac,
+                   "raster_dram_mb_per_eval_ncu": (dram_raster / per_launch_poses / 1e6
+                                                   if dram_raster else None),
                    "kernel_share": share, "e2e_matches_device": ok},
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(prof["launches"] // a.steps) * a.steps,
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": pk["hbm_gbs"],
                      "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
-                     "traffic": measured_traffic(dom, per_launch_poses, mesh.n_tris),
+                     "traffic": dram_raster,
                      "peak_kind": pk_kind, "avg_launch_ms": avg_s * 1e3,
                      "poses_per_launch": per_launch_poses},
     }
