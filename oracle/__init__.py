@@ -20,7 +20,12 @@ Parity status of each function (what pins it, see ``tests/test_oracle_pins.py``)
   * point-to-plane ICP terms: closed forms for a fronto-parallel wall (association count,
     C, residuals, J^T e, J^T J), the association rules (tolerance, labels, scan classes),
     finite differences of the frozen point-to-plane cost (J^T e; J^T J where the residuals
-    vanish); ICP alignment: convergence to the true pose on noise-free scans;
+    vanish); ICP alignment: convergence to the true pose on noise-free scans; with vertex
+    normals: equal to the face-normal terms when every vertex carries its plane's normal,
+    the blended normal at a single associated pixel against perspective-correct screen-space
+    barycentrics, NaN normals removing exactly their triangles' pixels, finite differences;
+  * barycentrics: the reconstructed hit lies on the pixel's ray, unit coordinates at the
+    vertices, perspective-correct screen-space barycentrics (``tests/test_oracle_bary.py``);
   * depth-image normals (Eq. 2): closed forms for linear and quadratic depth images, a constant
     image with holes (values, and the invalid set as a dilation of the holes), the metric
     normal of a tilted plane at the principal point;
@@ -151,6 +156,11 @@ def lib():
 
 def _p(a):
     return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _pn(a):
+    """Pointer of an optional array (NULL for None)."""
+    return None if a is None else _p(a)
 
 
 def _f32(a):
@@ -462,41 +472,46 @@ class OracleMap:
         r["e_table"] = et.value
         return out.reshape(4, 4), r
 
-    def icp_terms(self, pose, cam, scan_depth, scan_class, tol):
-        """Point-to-plane ICP terms with projective association (Sec. IV)."""
+    def icp_terms(self, pose, cam, scan_depth, scan_class, tol, vnormals=None):
+        """Point-to-plane ICP terms with projective association (Sec. IV); vnormals (V, 3)
+        world-frame vertex normals select the normal-coloured map (Sec. IV step 3)."""
         c, keep = make_cam(cam)
+        vn = None if vnormals is None else _f64(vnormals).reshape(-1, 3)
         na = ctypes.c_int64()
         l1 = ctypes.c_double()
         e2 = ctypes.c_double()
         g = np.zeros(6)
         h = np.zeros(21)
         lib().orc_icp_terms(_p(self.v), _p(self.vr), self.V, _p(self.centre), _p(self.faces),
-                            _p(self.labels), self.T, _p(_f64(pose).reshape(16)), ctypes.byref(c),
+                            _p(self.labels), _pn(vn), self.T, _p(_f64(pose).reshape(16)), ctypes.byref(c),
                             _p(_f32(scan_depth)), _p(np.ascontiguousarray(scan_class, np.uint8)),
                             ctypes.c_float(tol), ctypes.byref(na), ctypes.byref(l1),
                             ctypes.byref(e2), _p(g), _p(h))
         del keep
         return {"n_assoc": na.value, "cost_l1": l1.value, "e2": e2.value, "jte": g, "jtj": h}
 
-    def icp_frozen(self, pose, cam, scan_depth, scan_class, tol, xi):
+    def icp_frozen(self, pose, cam, scan_depth, scan_class, tol, xi, vnormals=None):
         c, keep = make_cam(cam)
+        vn = None if vnormals is None else _f64(vnormals).reshape(-1, 3)
         r = lib().orc_icp_frozen(_p(self.v), _p(self.vr), self.V, _p(self.centre), _p(self.faces),
-                                 _p(self.labels), self.T, _p(_f64(pose).reshape(16)),
+                                 _p(self.labels), _pn(vn), self.T, _p(_f64(pose).reshape(16)),
                                  ctypes.byref(c), _p(_f32(scan_depth)),
                                  _p(np.ascontiguousarray(scan_class, np.uint8)),
                                  ctypes.c_float(tol), _p(_f64(xi)))
         del keep
         return r
 
-    def icp_align(self, pose0, cam, scan_depth, scan_class, tol, max_iters=30, step_tol=1e-8):
+    def icp_align(self, pose0, cam, scan_depth, scan_class, tol, max_iters=30, step_tol=1e-8,
+                  vnormals=None):
         c, keep = make_cam(cam)
+        vn = None if vnormals is None else _f64(vnormals).reshape(-1, 3)
         out = np.empty(16)
         it = ctypes.c_int()
         conv = ctypes.c_int()
         na = ctypes.c_int64()
         l1 = ctypes.c_double()
         lib().orc_icp_align(_p(self.v), _p(self.vr), self.V, _p(self.centre), _p(self.faces),
-                            _p(self.labels), self.T, _p(_f64(pose0).reshape(16)), ctypes.byref(c),
+                            _p(self.labels), _pn(vn), self.T, _p(_f64(pose0).reshape(16)), ctypes.byref(c),
                             _p(_f32(scan_depth)), _p(np.ascontiguousarray(scan_class, np.uint8)),
                             ctypes.c_float(tol), int(max_iters), ctypes.c_double(step_tol), _p(out),
                             ctypes.byref(it), ctypes.byref(conv), ctypes.byref(na),

@@ -480,6 +480,37 @@ void orc_depth_exact(const float *v, const int32_t *faces, const double Twc[16],
     }
 }
 
+/* Barycentrics (b1, b2) of pixel (i, j)'s ray-plane hit on triangle k at pose T: the hit is
+ * (1 - b1 - b2) w0 + b1 w1 + b2 w2 with w the triangle's camera-frame vertices, in face
+ * order (FP64 throughout). */
+static void bary_px(const float *v, const int32_t *faces, const double T[16], const orc_cam *cam,
+                    int64_t k, int i, int j, double *b1, double *b2) {
+  double w[3][3];
+  for (int m = 0; m < 3; ++m) { /* vertices in the camera frame */
+    const float *a = v + 3 * (int64_t)faces[3 * k + m];
+    double q[3] = {(double)a[0] - T[3], (double)a[1] - T[7], (double)a[2] - T[11]};
+    for (int c = 0; c < 3; ++c) w[m][c] = T[0 * 4 + c] * q[0] + T[1 * 4 + c] * q[1] + T[2 * 4 + c] * q[2];
+  }
+  double r[3];
+  ray64(cam, i, j, r);
+  double e1[3], e2[3], n[3];
+  for (int c = 0; c < 3; ++c) {
+    e1[c] = w[1][c] - w[0][c];
+    e2[c] = w[2][c] - w[0][c];
+  }
+  n[0] = e1[1] * e2[2] - e1[2] * e2[1];
+  n[1] = e1[2] * e2[0] - e1[0] * e2[2];
+  n[2] = e1[0] * e2[1] - e1[1] * e2[0];
+  double t = (n[0] * w[0][0] + n[1] * w[0][1] + n[2] * w[0][2]) /
+             (n[0] * r[0] + n[1] * r[1] + n[2] * r[2]);
+  double h[3] = {t * r[0] - w[0][0], t * r[1] - w[0][1], t * r[2] - w[0][2]};
+  double nn = n[0] * n[0] + n[1] * n[1] + n[2] * n[2];
+  double c1[3] = {h[1] * e2[2] - h[2] * e2[1], h[2] * e2[0] - h[0] * e2[2], h[0] * e2[1] - h[1] * e2[0]};
+  double c2[3] = {e1[1] * h[2] - e1[2] * h[1], e1[2] * h[0] - e1[0] * h[2], e1[0] * h[1] - e1[1] * h[0]};
+  *b1 = (c1[0] * n[0] + c1[1] * n[1] + c1[2] * n[2]) / nn;
+  *b2 = (c2[0] * n[0] + c2[1] * n[1] + c2[2] * n[2]) / nn;
+}
+
 void orc_barycentrics(const float *v, const int32_t *faces, const double T[16],
                       const orc_cam *cam, const uint64_t *keys, double *bary) {
   for (int j = 0; j < cam->height; ++j)
@@ -489,31 +520,7 @@ void orc_barycentrics(const float *v, const int32_t *faces, const double T[16],
         bary[2 * p] = bary[2 * p + 1] = NAN;
         continue;
       }
-      int64_t k = (int64_t)(keys[p] & 0xFFFFFFFFu);
-      double w[3][3];
-      for (int m = 0; m < 3; ++m) { /* vertices in the camera frame */
-        const float *a = v + 3 * (int64_t)faces[3 * k + m];
-        double q[3] = {(double)a[0] - T[3], (double)a[1] - T[7], (double)a[2] - T[11]};
-        for (int c = 0; c < 3; ++c) w[m][c] = T[0 * 4 + c] * q[0] + T[1 * 4 + c] * q[1] + T[2 * 4 + c] * q[2];
-      }
-      double r[3];
-      ray64(cam, i, j, r);
-      double e1[3], e2[3], n[3];
-      for (int c = 0; c < 3; ++c) {
-        e1[c] = w[1][c] - w[0][c];
-        e2[c] = w[2][c] - w[0][c];
-      }
-      n[0] = e1[1] * e2[2] - e1[2] * e2[1];
-      n[1] = e1[2] * e2[0] - e1[0] * e2[2];
-      n[2] = e1[0] * e2[1] - e1[1] * e2[0];
-      double t = (n[0] * w[0][0] + n[1] * w[0][1] + n[2] * w[0][2]) /
-                 (n[0] * r[0] + n[1] * r[1] + n[2] * r[2]);
-      double h[3] = {t * r[0] - w[0][0], t * r[1] - w[0][1], t * r[2] - w[0][2]};
-      double nn = n[0] * n[0] + n[1] * n[1] + n[2] * n[2];
-      double c1[3] = {h[1] * e2[2] - h[2] * e2[1], h[2] * e2[0] - h[0] * e2[2], h[0] * e2[1] - h[1] * e2[0]};
-      double c2[3] = {e1[1] * h[2] - e1[2] * h[1], e1[2] * h[0] - e1[0] * h[2], e1[0] * h[1] - e1[1] * h[0]};
-      bary[2 * p] = (c1[0] * n[0] + c1[1] * n[1] + c1[2] * n[2]) / nn;
-      bary[2 * p + 1] = (c2[0] * n[0] + c2[1] * n[1] + c2[2] * n[2]) / nn;
+      bary_px(v, faces, T, cam, (int64_t)(keys[p] & 0xFFFFFFFFu), i, j, &bary[2 * p], &bary[2 * p + 1]);
     }
 }
 
@@ -839,9 +846,10 @@ int orc_cost_batch(const float *v, const float *vr, int64_t V, const double cent
  * 1 with the unit camera-frame normal of the map surface nu, the ray r, the map depth t and
  * the scan depth d (both as FP64 from the FP32 values) and the FP32 difference. */
 static int icp_pair(const float *v, const int32_t *faces, const uint8_t *labels,
-                    const double Twc[16], const orc_cam *cam, const float *scan_depth,
-                    const uint8_t *scan_class, float tol, const uint64_t *keys, int i, int j,
-                    double nu[3], double r[3], double *t, double *d, float *dz_out) {
+                    const double *vnormals, const double Twc[16], const orc_cam *cam,
+                    const float *scan_depth, const uint8_t *scan_class, float tol,
+                    const uint64_t *keys, int i, int j, double nu[3], double r[3], double *t,
+                    double *d, float *dz_out) {
   int64_t p = (int64_t)j * cam->width + i;
   uint64_t key = keys[p];
   if (key == KEY_EMPTY) return 0;
@@ -852,7 +860,23 @@ static int icp_pair(const float *v, const int32_t *faces, const uint8_t *labels,
   float dz32 = t32 - scan_depth[p];
   if (!(fabsf(dz32) < tol)) return 0;
   double n[3], dc;
-  plane64(v, faces, id, Twc, n, &dc);
+  if (vnormals) {
+    /* the map's points coloured by their normals (Sec. IV, step 3): the normal seen at the
+     * pixel blends the triangle's three vertex normals by the hit's barycentrics, as a
+     * rasteriser interpolates a vertex attribute; a vertex without a normal (NaN) leaves the
+     * pixel unassociated */
+    double b1, b2, nw[3];
+    bary_px(v, faces, Twc, cam, id, i, j, &b1, &b2);
+    const double b[3] = {1.0 - b1 - b2, b1, b2};
+    for (int c = 0; c < 3; ++c) {
+      nw[c] = 0.0;
+      for (int m = 0; m < 3; ++m) nw[c] += b[m] * vnormals[3 * (int64_t)faces[3 * id + m] + c];
+    }
+    if (!(isfinite(nw[0]) && isfinite(nw[1]) && isfinite(nw[2]))) return 0;
+    for (int c = 0; c < 3; ++c) n[c] = Twc[0 * 4 + c] * nw[0] + Twc[1 * 4 + c] * nw[1] + Twc[2 * 4 + c] * nw[2];
+  } else {
+    plane64(v, faces, id, Twc, n, &dc);
+  }
   double nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
   if (!(nn > 0)) return 0;
   for (int a = 0; a < 3; ++a) nu[a] = n[a] / nn;
@@ -864,10 +888,10 @@ static int icp_pair(const float *v, const int32_t *faces, const uint8_t *labels,
 }
 
 int orc_icp_terms(const float *v, const float *vr, int64_t V, const double centre[3],
-                  const int32_t *faces, const uint8_t *labels, int64_t T, const double Twc[16],
-                  const orc_cam *cam, const float *scan_depth, const uint8_t *scan_class,
-                  float tol, int64_t *n_assoc, double *cost_l1, double *e2, double jte[6],
-                  double jtj[21]) {
+                  const int32_t *faces, const uint8_t *labels, const double *vnormals, int64_t T,
+                  const double Twc[16], const orc_cam *cam, const float *scan_depth,
+                  const uint8_t *scan_class, float tol, int64_t *n_assoc, double *cost_l1,
+                  double *e2, double jte[6], double jtj[21]) {
   int64_t P = (int64_t)cam->width * cam->height;
   uint64_t *keys = (uint64_t *)malloc(sizeof(uint64_t) * (P > 0 ? P : 1));
   if (!keys) return -1;
@@ -878,8 +902,8 @@ int orc_icp_terms(const float *v, const float *vr, int64_t V, const double centr
     for (int i = 0; i < cam->width; ++i) {
       double nu[3], r[3], t, d;
       float dz32;
-      if (!icp_pair(v, faces, labels, Twc, cam, scan_depth, scan_class, tol, keys, i, j, nu, r, &t,
-                    &d, &dz32))
+      if (!icp_pair(v, faces, labels, vnormals, Twc, cam, scan_depth, scan_class, tol, keys, i, j,
+                    nu, r, &t, &d, &dz32))
         continue;
       /* scan point p = d r and map point q = t r on the same ray; residual (p - q) . nu */
       double pnt[3] = {d * r[0], d * r[1], d * r[2]};
@@ -908,9 +932,10 @@ int orc_icp_terms(const float *v, const float *vr, int64_t V, const double centr
 }
 
 double orc_icp_frozen(const float *v, const float *vr, int64_t V, const double centre[3],
-                      const int32_t *faces, const uint8_t *labels, int64_t T,
-                      const double Twc[16], const orc_cam *cam, const float *scan_depth,
-                      const uint8_t *scan_class, float tol, const double xi[6]) {
+                      const int32_t *faces, const uint8_t *labels, const double *vnormals,
+                      int64_t T, const double Twc[16], const orc_cam *cam,
+                      const float *scan_depth, const uint8_t *scan_class, float tol,
+                      const double xi[6]) {
   int64_t P = (int64_t)cam->width * cam->height;
   uint64_t *keys = (uint64_t *)malloc(sizeof(uint64_t) * (P > 0 ? P : 1));
   if (!keys) return NAN;
@@ -923,8 +948,8 @@ double orc_icp_frozen(const float *v, const float *vr, int64_t V, const double c
     for (int i = 0; i < cam->width; ++i) {
       double nu[3], r[3], t, d;
       float dz32;
-      if (!icp_pair(v, faces, labels, Twc, cam, scan_depth, scan_class, tol, keys, i, j, nu, r, &t,
-                    &d, &dz32))
+      if (!icp_pair(v, faces, labels, vnormals, Twc, cam, scan_depth, scan_class, tol, keys, i, j,
+                    nu, r, &t, &d, &dz32))
         continue;
       double p[3] = {d * r[0], d * r[1], d * r[2]}, q[3] = {t * r[0], t * r[1], t * r[2]};
       double pm[3];
@@ -937,10 +962,11 @@ double orc_icp_frozen(const float *v, const float *vr, int64_t V, const double c
 }
 
 int orc_icp_align(const float *v, const float *vr, int64_t V, const double centre[3],
-                  const int32_t *faces, const uint8_t *labels, int64_t T, const double Twc0[16],
-                  const orc_cam *cam, const float *scan_depth, const uint8_t *scan_class,
-                  float tol, int max_iters, double step_tol, double Twc_out[16], int *iters,
-                  int *converged, int64_t *n_assoc, double *cost_l1) {
+                  const int32_t *faces, const uint8_t *labels, const double *vnormals, int64_t T,
+                  const double Twc0[16], const orc_cam *cam, const float *scan_depth,
+                  const uint8_t *scan_class, float tol, int max_iters, double step_tol,
+                  double Twc_out[16], int *iters, int *converged, int64_t *n_assoc,
+                  double *cost_l1) {
   double Tc[16], Tn[16];
   memcpy(Tc, Twc0, sizeof(Tc));
   *converged = 0;
@@ -949,8 +975,8 @@ int orc_icp_align(const float *v, const float *vr, int64_t V, const double centr
   double C = 0.0;
   for (it = 0; it < max_iters; ++it) {
     double e2, g[6], H[21], dx[6];
-    orc_icp_terms(v, vr, V, centre, faces, labels, T, Tc, cam, scan_depth, scan_class, tol, &na,
-                  &C, &e2, g, H);
+    orc_icp_terms(v, vr, V, centre, faces, labels, vnormals, T, Tc, cam, scan_depth, scan_class,
+                  tol, &na, &C, &e2, g, H);
     if (!lm_solve(H, g, 0.0, dx)) break; /* Gauss-Newton: J^T J dx = -J^T e */
     double nrm = 0;
     for (int a = 0; a < 6; ++a) nrm += dx[a] * dx[a];

@@ -126,27 +126,34 @@ int orc_cost_batch(const float *v, const float *vr, int64_t V, const double cent
  * camera-frame normal n, the residual is e = (p - q) . n and its Jacobian w.r.t. the right-
  * perturbation twist (rho, phi) of Twc is J = (n, p x n). n_assoc counts the associations,
  * cost_l1 = sum |Z_M - Z_1| over them (the paper's C), e2 = sum e^2, jte = sum J e,
- * jtj = upper triangle of sum J J^T. */
+ * jtj = upper triangle of sum J J^T.
+ * vnormals (V*3 world-frame vectors, or NULL): when given, n is not the face plane's normal
+ * but the map's points coloured by their normals (Sec. IV, sequential alignment step 3): the
+ * three vertex normals of the seen triangle blended by the hit's barycentrics, rotated into
+ * the camera frame and normalised; a pixel whose blend is not finite (a vertex without a
+ * normal, NaN) is not associated. */
 int orc_icp_terms(const float *v, const float *vr, int64_t V, const double centre[3],
-                  const int32_t *faces, const uint8_t *labels, int64_t T, const double Twc[16],
-                  const orc_cam *cam, const float *scan_depth, const uint8_t *scan_class,
-                  float tol, int64_t *n_assoc, double *cost_l1, double *e2, double jte[6],
-                  double jtj[21]);
+                  const int32_t *faces, const uint8_t *labels, const double *vnormals, int64_t T,
+                  const double Twc[16], const orc_cam *cam, const float *scan_depth,
+                  const uint8_t *scan_class, float tol, int64_t *n_assoc, double *cost_l1,
+                  double *e2, double jte[6], double jtj[21]);
 
 /* 1/2 sum e^2 with the associations, map points and normals of pose Twc frozen and the scan
  * points moved by exp(xi^) in its camera frame (for finite-difference checks of jte). */
 double orc_icp_frozen(const float *v, const float *vr, int64_t V, const double centre[3],
-                      const int32_t *faces, const uint8_t *labels, int64_t T,
-                      const double Twc[16], const orc_cam *cam, const float *scan_depth,
-                      const uint8_t *scan_class, float tol, const double xi[6]);
+                      const int32_t *faces, const uint8_t *labels, const double *vnormals,
+                      int64_t T, const double Twc[16], const orc_cam *cam,
+                      const float *scan_depth, const uint8_t *scan_class, float tol,
+                      const double xi[6]);
 
 /* ICP iterations: re-render and re-associate, solve J^T J dx = -J^T e (Cholesky), Twc <-
  * Twc exp(dx^), until |dx| < step_tol (converged = 1) or max_iters iterations. */
 int orc_icp_align(const float *v, const float *vr, int64_t V, const double centre[3],
-                  const int32_t *faces, const uint8_t *labels, int64_t T, const double Twc0[16],
-                  const orc_cam *cam, const float *scan_depth, const uint8_t *scan_class,
-                  float tol, int max_iters, double step_tol, double Twc_out[16], int *iters,
-                  int *converged, int64_t *n_assoc, double *cost_l1);
+                  const int32_t *faces, const uint8_t *labels, const double *vnormals, int64_t T,
+                  const double Twc0[16], const orc_cam *cam, const float *scan_depth,
+                  const uint8_t *scan_class, float tol, int max_iters, double step_tol,
+                  double Twc_out[16], int *iters, int *converged, int64_t *n_assoc,
+                  double *cost_l1);
 
 /* Surface normals of a depth image (Eq. 2, Sec. IV). A pixel is valid when its class is FO
  * (0) and its depth finite. The valid depths are smoothed with a Gaussian of standard
