@@ -66,13 +66,33 @@ __device__ __forceinline__ bool mbar_try(unsigned long long *bar, unsigned parit
   return ok != 0;
 }
 
+// Non-blocking test of a phase of `bar`.
+__device__ __forceinline__ bool mbar_test(unsigned long long *bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
 // Default budget of a bounded device wait: about 2^31 cycles (~1 s at 2 GHz).
 constexpr long long kWaitCycles = 1ll << 31;
 
 // Bounded wait on a phase of `bar`: gives up after `budget` cycles (kWaitCycles when <= 0).
+// try_wait may suspend the thread for a hardware-defined window, longer than a short budget;
+// a shorter budget therefore polls with the non-blocking test instead.
 __device__ __noinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, long long budget) {
   if (budget <= 0) budget = kWaitCycles;
-  long long t0 = clock64();
+  const long long t0 = clock64();
+  if (budget < kWaitCycles) {
+    while (!mbar_test(bar, parity)) {
+      if (clock64() - t0 > budget) return false;
+    }
+    return true;
+  }
   while (!mbar_try(bar, parity)) {
     if (clock64() - t0 > budget) return false;
   }
