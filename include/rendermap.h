@@ -161,6 +161,21 @@ void rm_map_destroy(rm_map *map);
 rm_status rm_map_info(const rm_map *map, int64_t *n_vertices, int64_t *n_faces,
                       double centre[3]);
 rm_status rm_map_set_tuning(rm_map *map, const rm_tuning *tuning);
+
+/* Attaches per-vertex normals to the map for the point-to-plane ICP entry points (Sec. IV,
+ * sequential depth-image alignment, steps 2-3: the normals of D_i by Eq. 2, then the points of
+ * D_i rendered coloured by their normals). Afterwards the normal of an associated pixel is the
+ * blend of the seen triangle's three vertex normals by the hit's barycentrics (a rasteriser
+ * interpolating a vertex attribute), rotated into the current camera frame and normalised;
+ * a pixel whose blend is not finite (a vertex with a NaN normal) is not associated. Without
+ * vertex normals the ICP uses each triangle's plane normal.
+ *  - normals: V*3 floats, host or device, in the frame of `pose`; NULL detaches the normals;
+ *  - pose: 16 doubles (host), the camera-to-world pose of the frame the normals are given in
+ *    (e.g. the pose of the depth image whose Eq. 2 normals they are), or NULL for world-frame
+ *    normals. The library stores the normals rotated into the world frame (FP32).
+ * Waits for `stream`. Errors: RM_EINVAL, RM_ENOMEM/RM_ECUDA. */
+rm_status rm_map_set_vertex_normals(rm_map *map, const float *normals, const double *pose,
+                                    void *stream);
 rm_status rm_map_get_tuning(const rm_map *map, rm_tuning *tuning);
 
 /* R(Y) of Eq. 1: the z-buffer of the map seen from each of N poses. The z-buffer keeps, per

@@ -104,6 +104,7 @@ _SIGS = {
     "rm_map_destroy": (None, [_P]),
     "rm_map_info": (ctypes.c_int, [_P, _P, _P, _P]),
     "rm_map_set_tuning": (ctypes.c_int, [_P, ctypes.POINTER(rm_tuning)]),
+    "rm_map_set_vertex_normals": (ctypes.c_int, [_P, _P, _P, _P]),
     "rm_map_get_tuning": (ctypes.c_int, [_P, ctypes.POINTER(rm_tuning)]),
     "rm_render_depth": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.POINTER(rm_intrinsics), _P, _P, _P, _P]),
     "rm_cost": (ctypes.c_int, [_P, ctypes.POINTER(rm_scan), _P, ctypes.c_int32,

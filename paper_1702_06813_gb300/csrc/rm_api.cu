@@ -79,6 +79,7 @@ struct rm_map {
   float4 *d_v = nullptr;
   int4 *d_faces = nullptr;
   float4 *d_planes = nullptr;
+  float4 *d_vn = nullptr;  // optional world-frame vertex normals for the ICP
   int n_clusters = 0;
   int4 *d_cl_info = nullptr;
   float4 *d_cl_sphere = nullptr;
@@ -324,6 +325,7 @@ long long wait_budget(const rm_map *m, long long dflt) {
 // The map's clusters and its wait budget in a wave's arguments.
 void set_map_fields(const rm_map *m, WaveArgs &a) {
   a.wait_cycles = wait_budget(m, 0);
+  a.vnormals = m->d_vn;
   a.n_clusters = m->n_clusters;
   a.cl_info = m->d_cl_info;
   a.cl_sphere = m->d_cl_sphere;
@@ -1211,6 +1213,7 @@ void rm_map_destroy(rm_map *m) {
   cudaFree(m->d_v);
   cudaFree(m->d_faces);
   cudaFree(m->d_planes);
+  cudaFree(m->d_vn);
   cudaFree(m->d_cl_info);
   cudaFree(m->d_cl_sphere);
   cudaFree(m->d_cl_pos);
@@ -1252,6 +1255,43 @@ rm_status rm_map_set_tuning(rm_map *m, const rm_tuning *t) {
   m->tuning = u;
   if (u.bin_capacity > 0) m->cap = m->cap_ray = u.bin_capacity;
   return RM_OK;
+}
+
+rm_status rm_map_set_vertex_normals(rm_map *m, const float *normals, const double *pose, void *stream) {
+  if (!m) return fail(RM_EINVAL, "map is NULL");
+  std::lock_guard<std::mutex> lk(m->mu);
+  RM_CK(cudaSetDevice(m->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!normals) {
+    if (m->d_vn) {
+      RM_CK(cudaStreamSynchronize(s));
+      RM_CK(cudaFree(m->d_vn));
+      m->d_vn = nullptr;
+    }
+    return RM_OK;
+  }
+  if (pose && on_device(pose)) return fail(RM_EINVAL, "pose must be a host array");
+  float R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+  if (pose)
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) R[3 * r + c] = (float)pose[4 * r + c];
+  const int V = (int)m->V;
+  if (V == 0) return RM_OK;
+  if (!m->d_vn) RM_CK(cudaMalloc((void **)&m->d_vn, sizeof(float4) * (size_t)V));
+  float *buf = nullptr;
+  const size_t nb = sizeof(float) * 3 * (size_t)V;
+  RM_CK(cudaMallocAsync((void **)&buf, nb + sizeof(R), s));
+  rm_status st = RM_OK;
+  auto run = [&]() -> rm_status {
+    RM_CK(cudaMemcpyAsync(buf, normals, nb, on_device(normals) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    RM_CK(cudaMemcpyAsync(buf + 3 * (size_t)V, R, sizeof(R), cudaMemcpyHostToDevice, s));
+    RM_CK(rmk::launch_rotate_normals(buf, V, buf + 3 * (size_t)V, m->d_vn, s));
+    RM_CK(cudaStreamSynchronize(s));
+    return RM_OK;
+  };
+  st = run();
+  cudaFreeAsync(buf, s);
+  return st;
 }
 
 rm_status rm_map_get_tuning(const rm_map *m, rm_tuning *t) {

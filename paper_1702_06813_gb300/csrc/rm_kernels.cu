@@ -631,7 +631,9 @@ __device__ __forceinline__ int derive_rect(TriRec *rec, int4 *hdr, int k, int cn
     }
   }
   const int qw = (bw + 1) >> 1, qh = (bh + 1) >> 1;  // 2x2 pixel quads over the rectangle
-  hdr[k] = make_int4(e0[0], e0[1], e0[2], __float_as_int(__frcp_rn(__int2float_rn(qw))));
+  // quad row of quad index l: __umulhi(2 l, m) = floor(l / qw) exactly for l < 2^10 with
+  // m = ceil(2^31 / qw) (the error 2 l / 2^32 stays below 1 / qw)
+  hdr[k] = make_int4(e0[0], e0[1], e0[2], (int)((2147483647u + (unsigned)qw) / (unsigned)qw));
   if (!fallback) {
     r.x0 = sx[0]; r.y0 = sy[0]; r.x1 = sx[1]; r.y1 = sy[1]; r.x2 = sx[2]; r.y2 = sy[2];
   }
@@ -652,6 +654,13 @@ __device__ __forceinline__ bool covers_exact(const TriRec &q, int i, int j) {
 __device__ __forceinline__ bool inner3(int a, int b, int c) { return (a | b | c) >= 0; }
 
 __device__ __forceinline__ int wadd(int a, int b) { return (int)((unsigned)a + (unsigned)b); }
+
+// (float)i + 0.5f for 0 <= i < 2^23 without the conversion pipe: 2^23 + i is exact in the
+// mantissa, and subtracting 2^23 - 0.5 (representable) leaves i + 0.5 exactly.
+__device__ __forceinline__ float px_centre(int i) {
+  return __fsub_rn(__int_as_float(0x4B000000 | i), 8388607.5f);
+}
+
 
 // Rasterise every record of one (pose, tile) bin into the shared z-buffer. Records are staged
 // with one bulk copy per round; a block-wide scan of their per-tile rectangle sizes lays all
@@ -726,7 +735,7 @@ __device__ __forceinline__ bool raster_tile(unsigned long long *zk, TriRec *stag
         const int pad = q.pad;
         const int bw = ((pad >> 16) & 0x3f) + 1, bh = ((pad >> 22) & 0x3f) + 1;
         const int qw = (bw + 1) >> 1;
-        const int qj = __float2int_rz(__fmul_rn(__int2float_rn(l) + 0.5f, __int_as_float(h.w)));
+        const int qj = (int)__umulhi(2u * (unsigned)l, (unsigned)h.w);
         const int di = 2 * (l - qj * qw), dj = 2 * qj;
         const int li = (pad & 0xff) + di, lj = ((pad >> 8) & 0xff) + dj;
         const int i = ox + li, j = oy + lj;
@@ -749,7 +758,7 @@ __device__ __forceinline__ bool raster_tile(unsigned long long *zk, TriRec *stag
         }
         // inverse depth at the four samples, each exactly inv_depth_pinhole's expression
         // (i + 1.5 = (i + .5) + 1 and j + 1.5 are exact in FP32)
-        const float fi = __fadd_rn(__int2float_rn(i), 0.5f), fj = __fadd_rn(__int2float_rn(j), 0.5f);
+        const float fi = px_centre(i), fj = px_centre(j);
         const float fi1 = __fadd_rn(fi, 1.0f), fj1 = __fadd_rn(fj, 1.0f);
         const float row0 = __fmaf_rn(q.Bi, fj, q.Ci), row1 = __fmaf_rn(q.Bi, fj1, q.Ci);
         const float w00 = __fmaf_rn(q.Ai, fi, row0), w10 = __fmaf_rn(q.Ai, fi1, row0);
@@ -892,6 +901,54 @@ struct RasterSmem {
   float red[NW][28];
   int redc[NW][6];
 };
+
+// Camera-frame normal at a pixel of triangle `id` from the map's vertex normals (Sec. IV,
+// sequential alignment: the map's points rendered coloured by their normals): the hit t r on
+// the triangle's camera-frame plane, its barycentrics (as the visibility buffer's), the three
+// world-frame vertex normals blended by them as a rasteriser interpolates a vertex attribute,
+// and the blend rotated into the camera frame (unnormalised). False when the blend is not
+// finite: a vertex without a normal (NaN) leaves the pixel unassociated.
+__device__ __noinline__ bool vertex_normal(const WaveArgs &a, const float *M, unsigned id, float t,
+                                           float rx, float ry, float rz, float &nx, float &ny,
+                                           float &nz) {
+  const int4 f = a.faces[id];
+  const float4 p0 = a.v[f.x], p1 = a.v[f.y], p2 = a.v[f.z];
+  float Mr[12];
+  for (int k = 0; k < 12; ++k) Mr[k] = M[k];
+  const float3 v0 = xform(Mr, p0.x, p0.y, p0.z), v1 = xform(Mr, p1.x, p1.y, p1.z),
+               v2 = xform(Mr, p2.x, p2.y, p2.z);
+  const float hx = t * rx - v0.x, hy = t * ry - v0.y, hz = t * rz - v0.z;
+  const float e1x = v1.x - v0.x, e1y = v1.y - v0.y, e1z = v1.z - v0.z;
+  const float e2x = v2.x - v0.x, e2y = v2.y - v0.y, e2z = v2.z - v0.z;
+  const float cx = e1y * e2z - e1z * e2y, cy = e1z * e2x - e1x * e2z, cz = e1x * e2y - e1y * e2x;
+  const float inn = 1.0f / (cx * cx + cy * cy + cz * cz);
+  const float b1 = ((hy * e2z - hz * e2y) * cx + (hz * e2x - hx * e2z) * cy + (hx * e2y - hy * e2x) * cz) * inn;
+  const float b2 = ((e1y * hz - e1z * hy) * cx + (e1z * hx - e1x * hz) * cy + (e1x * hy - e1y * hx) * cz) * inn;
+  const float b0 = 1.0f - b1 - b2;
+  const float4 N0 = a.vnormals[f.x], N1 = a.vnormals[f.y], N2 = a.vnormals[f.z];
+  const float wx = b0 * N0.x + b1 * N1.x + b2 * N2.x;
+  const float wy = b0 * N0.y + b1 * N1.y + b2 * N2.y;
+  const float wz = b0 * N0.z + b1 * N1.z + b2 * N2.z;
+  if (!(isfinite(wx) && isfinite(wy) && isfinite(wz))) return false;
+  nx = M[0] * wx + M[1] * wy + M[2] * wz;
+  ny = M[4] * wx + M[5] * wy + M[6] * wz;
+  nz = M[8] * wx + M[9] * wy + M[10] * wz;
+  return true;
+}
+
+__global__ void k_rotate_normals(const float *n, int V, const float *R, float4 *out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= V) return;
+  const float x = n[3 * (long long)k], y = n[3 * (long long)k + 1], z = n[3 * (long long)k + 2];
+  out[k] = make_float4(R[0] * x + R[1] * y + R[2] * z, R[3] * x + R[4] * y + R[5] * z,
+                       R[6] * x + R[7] * y + R[8] * z, 0.0f);
+}
+
+cudaError_t launch_rotate_normals(const float *n, int V, const float *R, float4 *out, cudaStream_t s) {
+  if (V <= 0) return cudaSuccess;
+  k_rotate_normals<<<(V + 255) / 256, 256, 0, s>>>(n, V, R, out);
+  return cudaGetLastError();
+}
 
 // One (pose q, tile) of the z-buffer and its fused epilogue. Returns false on a timed-out wait.
 template <int TW, int TH, int MODE, int MODEL>
@@ -1040,17 +1097,9 @@ __device__ __forceinline__ void raster_block(const WaveArgs &a, int tile, int q,
       if (a.scan_cls[pix] != 0 || !(fabsf(sd) <= FLT_MAX)) continue;  // FO returns only
       const float4 pl = a.planes[(unsigned)key];
       if (__float_as_int(pl.w) != 0) continue;                         // FO surfaces only
-      const float dz = __fsub_rn(key_depth(key), sd);
+      const float t = key_depth(key);
+      const float dz = __fsub_rn(t, sd);
       if (!(fabsf(dz) < eps)) continue;
-      float nx = R[0] * pl.x + R[1] * pl.y + R[2] * pl.z;
-      float ny = R[3] * pl.x + R[4] * pl.y + R[5] * pl.z;
-      float nz = R[6] * pl.x + R[7] * pl.y + R[8] * pl.z;
-      const float nn = nx * nx + ny * ny + nz * nz;
-      if (!(nn > 0.0f)) continue;  // degenerate face: no plane
-      const float u = rsqrtf(nn);
-      nx *= u;
-      ny *= u;
-      nz *= u;
       float rx, ry, rz;
       if (MODEL == 0) {
         rx = (i + 0.5f - a.cam.cx) * ifx;
@@ -1062,6 +1111,20 @@ __device__ __forceinline__ void raster_block(const WaveArgs &a, int tile, int q,
         ry = rr[1];
         rz = rr[2];
       }
+      float nx, ny, nz;
+      if (a.vnormals) {
+        if (!vertex_normal(a, sm.M, (unsigned)key, t, rx, ry, rz, nx, ny, nz)) continue;
+      } else {
+        nx = R[0] * pl.x + R[1] * pl.y + R[2] * pl.z;
+        ny = R[3] * pl.x + R[4] * pl.y + R[5] * pl.z;
+        nz = R[6] * pl.x + R[7] * pl.y + R[8] * pl.z;
+      }
+      const float nn = nx * nx + ny * ny + nz * nz;
+      if (!(nn > 0.0f)) continue;  // degenerate face: no plane
+      const float u = rsqrtf(nn);
+      nx *= u;
+      ny *= u;
+      nz *= u;
       const float e = -dz * (nx * rx + ny * ry + nz * rz);
       const float px = sd * rx, py = sd * ry, pz = sd * rz;
       float J[6];

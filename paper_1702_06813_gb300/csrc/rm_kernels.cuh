@@ -41,6 +41,7 @@ struct WaveArgs {
   unsigned *status;   // device status word
   const int *skip;    // optional: non-zero means "skip this evaluation" (LM control)
   long long wait_cycles;  // budget of each bounded device wait, cycles (<= 0: about 2^31)
+  const float4 *vnormals;  // optional world-frame vertex normals (ICP's normal-coloured map)
   // cost inputs
   const float *scan_depth;
   const uint8_t *scan_cls;
@@ -74,6 +75,8 @@ cudaError_t launch_wave(const WaveArgs &a, int mode, cudaStream_t s, cudaEvent_t
 int wave_kernel_launches(const WaveArgs &a, int mode);
 cudaError_t launch_retract(const double *T, const double *xi, int n, double *out, double *jr,
                            cudaStream_t s);
+// out_k = R n_k for V vertex normals (n: V*3 device floats, R row major): world-frame float4.
+cudaError_t launch_rotate_normals(const float *n, int V, const float *R, float4 *out, cudaStream_t s);
 // out_k = scale_k J_r(xi_k)^T g_k (scale optional: 1), device arrays.
 cudaError_t launch_twist_grad(const double *xi, const double *g, const double *scale, int n,
                               double *out, cudaStream_t s);

@@ -143,6 +143,20 @@ class Map:
         t = N.rm_tuning(tile[0], tile[1], bin_capacity, wave_poses, int(async_status), int(wait_log2))
         check(lib().rm_map_set_tuning(self.handle, ctypes.byref(t)))
 
+    def set_vertex_normals(self, normals, pose=None):
+        """Per-vertex normals for the point-to-plane ICP (Sec. IV step 3), (V, 3) in the frame of
+        `pose` (camera-to-world, 4x4), or world-frame when pose is None; None detaches them."""
+        if normals is None:
+            check(lib().rm_map_set_vertex_normals(self.handle, None, None, _stream()))
+            return
+        n = _dev_tensor(normals, torch.float32).reshape(-1, 3).contiguous()
+        if n.shape[0] != self.n_vertices:
+            raise ValueError("one normal per map vertex")
+        P = None if pose is None else np.ascontiguousarray(np.asarray(pose, np.float64).reshape(16))
+        check(lib().rm_map_set_vertex_normals(self.handle, _ptr(n),
+                                              None if P is None else P.ctypes.data_as(ctypes.c_void_p),
+                                              _stream()))
+
     def profile(self, enable: bool):
         """Start (clearing the record) or stop per-kernel event timing on this map."""
         check(lib().rm_profile(self.handle, int(enable)))
@@ -286,18 +300,28 @@ def blur_scan(scan: Scan, sigma=1.0) -> Scan:
 
 
 def sequential_icp(scans, first_pose, max_range, step=2, max_edge=0.1, tol=0.2, max_iters=20,
-                   step_tol=1e-5):
+                   step_tol=1e-5, normals="face", sigma=1.0):
     """Sequential depth-image alignment (Sec. IV): each scan, downsampled by `step` and meshed
     at its pose, becomes the map the next scan is aligned to by point-to-plane ICP, starting
-    from the previous pose. Returns the (n, 4, 4) poses (the first is `first_pose`) and the
-    per-step ICP reports. The meshes are built on the device; each becomes a Map through the
-    host (rm_map_create)."""
+    from the previous pose. normals="eq2" takes the point-to-plane normals from the previous
+    scan's Eq. 2 normals (metric, Gaussian sigma in pixels, pinhole scans) at the mesh's grid
+    pixels, blended over each rendered triangle (the points rendered coloured by their normals,
+    steps 2-3); normals="face" uses each mesh triangle's plane. Returns the (n, 4, 4) poses (the
+    first is `first_pose`) and the per-step ICP reports. The meshes are built on the device;
+    each becomes a Map through the host (rm_map_create)."""
+    if normals not in ("face", "eq2"):
+        raise ValueError("normals must be 'face' or 'eq2'")
     poses = [np.asarray(first_pose, dtype=np.float64).reshape(4, 4)]
     reports = []
     for k in range(1, len(scans)):
-        mesh = meshify(scans[k - 1], poses[-1], max_range, max_edge=max_edge, step=step)
+        prev = scans[k - 1]
+        mesh = meshify(prev, poses[-1], max_range, max_edge=max_edge, step=step)
         m = Map(mesh["vertices"], mesh["faces"], mesh["labels"])
         try:
+            if normals == "eq2":
+                nrm = depth_normals(prev.intr, prev.depth, prev.cls, sigma=sigma, metric=True)
+                st = max(int(step), 1)
+                m.set_vertex_normals(nrm[::st, ::st].reshape(-1, 3), pose=poses[-1])
             pose, rep = icp_align(m, scans[k], poses[-1], tol=tol, max_iters=max_iters, step_tol=step_tol)
         finally:
             m.close()
