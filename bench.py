@@ -9,6 +9,8 @@ least-squares residual, and reduce the adjoint gradient and Gauss-Newton matrix 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
   python bench.py --workload tracking     # 64 mixed-sensor agents, rm_align_batch per frame
   python bench.py --workload icp          # point-to-plane ICP terms and alignments (Sec. IV)
+  python bench.py --workload normals      # Eq. 2 normals of 64 depth images per step
+  python bench.py --workload vgrad        # vertex-position gradient of 16 poses per step
 """
 from __future__ import annotations
 
@@ -43,7 +45,7 @@ def args_():
     ap.add_argument("--cpu-sample", type=int, default=64, help="poses per step of the reference arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile", default=None, help="WxH screen tile (e.g. 64x32): skip the autotuner")
-    ap.add_argument("--workload", choices=["headline", "tracking", "icp"], default="headline")
+    ap.add_argument("--workload", choices=["headline", "tracking", "icp", "normals", "vgrad"], default="headline")
     ap.add_argument("--frames", type=int, default=200, help="tracking: frames of the trajectory")
     ap.add_argument("--agents", type=int, default=64, help="tracking: agents (scans per frame)")
     ap.add_argument("--triangles", type=int, default=2_000_000, help="tracking: map size")
@@ -673,6 +675,135 @@ def run_icp(a):
     gm.close()
 
 
+def _timed_events(fn, steps, flush):
+    """Total milliseconds of `steps` calls of fn on the current stream, the L2 flushed (a
+    256 MiB write) before each, CUDA events around each call."""
+    import torch
+    stream = torch.cuda.current_stream()
+    tot = 0.0
+    for k in range(steps):
+        flush.fill_(k & 0xFF)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tot += e0.elapsed_time(e1)
+    return tot
+
+
+def _small_line(a, metric, unit, value, ms, config, roofline, cpu, launches):
+    print(json.dumps({
+        "metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": a.steps,
+        "warmup": max(3, a.warmup), "ms_per_step": ms / a.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
+        "roofline": roofline, "cpu_baseline": cpu, "gpu_launches": launches}))
+
+
+def run_normals(a):
+    """Eq. 2 surface normals (Sec. IV) of 64 noisy copies of the 640x480 room scan per step
+    (sigma 1.5 px, metric), one rm_depth_normals call. Algorithmic bytes: depth and class in,
+    the normal out, 17 per pixel. CPU baseline: the oracle on one image per host thread."""
+    import torch
+    import paper_1702_06813_gb300 as rm
+    import synth
+    import __graft_entry__
+    __graft_entry__.build_library()
+    torch.cuda.set_device(0)
+    w = synth.workload_headline(a.seed, 1)
+    cam = w["cam"]
+    intr = rm.Intrinsics.from_camera(cam)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(a.seed)
+    d0 = torch.as_tensor(w["scan"][0], device="cuda")
+    D = (d0[None] * (1 + 0.005 * torch.randn((64,) + d0.shape, device="cuda", generator=gen))).contiguous()
+    C = torch.as_tensor(w["scan"][1], device="cuda")[None].expand(64, -1, -1).contiguous()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(max(3, a.warmup)):
+        rm.depth_normals(intr, D, C, sigma=1.5, metric=True)
+    torch.cuda.synchronize()
+    ms = _timed_events(lambda: rm.depth_normals(intr, D, C, sigma=1.5, metric=True), a.steps, flush)
+    pk, pk_kind = peaks()
+    nb = 17 * D.numel()
+    achieved = nb * a.steps / (ms * 1e-3) / 1e9
+    cpu = None
+    if not a.no_cpu_baseline:
+        import oracle
+        from concurrent.futures import ThreadPoolExecutor
+        oracle.build()
+        Dh, Ch = D[:16].cpu().numpy(), C[:16].cpu().numpy()
+        cores = os.cpu_count() or 1
+        with ThreadPoolExecutor(max_workers=cores) as pool:
+            t0 = time.perf_counter()
+            list(pool.map(lambda k: oracle.depth_normals(Dh[k], Ch[k], sigma=1.5, metric=True, fx=cam.fx,
+                                                         fy=cam.fy), range(16)))
+            dt = time.perf_counter() - t0
+        cpu = {"value": 16 / dt, "unit": "images/s", "cores": cores, "kind": "oracle",
+               "sample": f"16 of the 64 images, one per host thread, {dt:.1f} s wall"}
+    _small_line(a, "Eq. 2 depth-image normals/s (640x480, sigma 1.5 px, metric)", "images/s",
+                64 * a.steps / (ms * 1e-3), ms,
+                {"workload": "room-scan-640x480-x64-normals", "images_per_step": 64, "sigma_px": 1.5,
+                 "l2": "flushed between timed steps (256 MiB write)"},
+                {"bound": "hbm", "kernel": "k_depth_normals", "achieved": achieved, "peak": pk["hbm_gbs"],
+                 "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "traffic": None, "peak_kind": pk_kind,
+                 "avg_launch_ms": ms / a.steps, "algorithmic_bytes_per_launch": nb},
+                cpu, a.steps)
+
+
+def run_vgrad(a):
+    """Vertex-position gradient (map refinement) of 16 candidate poses of the 1M-triangle room
+    per step, one rm_cost_grad_vertices call: visibility-buffer render, then the per-pixel
+    scatter kernel. Algorithmic bytes per pose: the map (12 V + 13 T, once per call), the scan
+    (5 P) and the FP64 gradient (24 V, once per call). CPU baseline: the oracle, one pose per
+    host thread."""
+    import torch
+    import paper_1702_06813_gb300 as rm
+    import synth
+    import __graft_entry__
+    __graft_entry__.build_library()
+    torch.cuda.set_device(0)
+    w = synth.workload_headline(a.seed, 16)
+    mesh, cam = w["mesh"], w["cam"]
+    gm = rm.Map(mesh.vertices, mesh.faces, mesh.labels)
+    scan = rm.Scan.make(rm.Intrinsics.from_camera(cam), *w["scan"])
+    poses = torch.as_tensor(w["poses"].reshape(-1, 16), dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(max(3, a.warmup)):
+        rm.cost_grad_vertices(gm, scan, poses)
+    torch.cuda.synchronize()
+    gm.profile(True)
+    ms = _timed_events(lambda: rm.cost_grad_vertices(gm, scan, poses), a.steps, flush)
+    prof = gm.profile_read()
+    gm.profile(False)
+    pk, pk_kind = peaks()
+    P = cam.width * cam.height
+    nb = 12 * mesh.n_verts + 13 * mesh.n_tris + 24 * mesh.n_verts + 16 * 5 * P
+    achieved = nb * a.steps / (ms * 1e-3) / 1e9
+    cpu = None
+    if not a.no_cpu_baseline:
+        import oracle
+        from concurrent.futures import ThreadPoolExecutor
+        oracle.build()
+        om = oracle.OracleMap(mesh.vertices, mesh.faces, mesh.labels)
+        cores = os.cpu_count() or 1
+        with ThreadPoolExecutor(max_workers=cores) as pool:
+            t0 = time.perf_counter()
+            list(pool.map(lambda k: om.vertex_grad(w["poses"][k], cam, *w["scan"]), range(16)))
+            dt = time.perf_counter() - t0
+        cpu = {"value": 16 / dt, "unit": "pose evals/s", "cores": cores, "kind": "oracle",
+               "sample": f"the 16 poses, one per host thread, {dt:.1f} s wall"}
+    _small_line(a, "vertex-gradient pose evals/s (640x480, 1M tris, d e_ls / d vertices)", "pose evals/s",
+                16 * a.steps / (ms * 1e-3), ms,
+                {"workload": w["name"] + "-vgrad16", "poses_per_step": 16, "vertices": mesh.n_verts,
+                 "kernel_ms_per_step": {k: v[1] / a.steps for k, v in prof["kernels"].items()},
+                 "l2": "flushed between timed steps (256 MiB write)"},
+                {"bound": "hbm", "kernel": "whole call", "achieved": achieved, "peak": pk["hbm_gbs"],
+                 "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "traffic": None, "peak_kind": pk_kind,
+                 "avg_launch_ms": ms / a.steps, "algorithmic_bytes_per_call": nb},
+                cpu, int(prof["launches"]))
+    gm.close()
+
+
 def main():
     a = args_()
     if a.impl == "reference":
@@ -683,6 +814,12 @@ def main():
         return
     if a.workload == "icp":
         run_icp(a)
+        return
+    if a.workload == "normals":
+        run_normals(a)
+        return
+    if a.workload == "vgrad":
+        run_vgrad(a)
         return
     import torch
     import torch.distributed as dist

@@ -1162,9 +1162,12 @@ rm_status rm_map_create(const float *vertices, int64_t n_vertices, const int32_t
   for (int64_t k = 0; k < n_faces; ++k) {
     int i0 = faces[3 * k], i1 = faces[3 * k + 1], i2 = faces[3 * k + 2];
     hf[k] = make_int4(i0, i1, i2, labels[k]);
-    const float4 &a = hv[i0], &b = hv[i1], &c = hv[i2];
-    double e1[3] = {(double)b.x - a.x, (double)b.y - a.y, (double)b.z - a.z};
-    double e2[3] = {(double)c.x - a.x, (double)c.y - a.y, (double)c.z - a.z};
+    // the unit normal in FP64 from the caller's FP32 vertices (not the re-centred copies,
+    // whose rounding far from the centre would tilt small triangles)
+    const float *a = vertices + 3 * (int64_t)i0, *b = vertices + 3 * (int64_t)i1,
+                *c = vertices + 3 * (int64_t)i2;
+    double e1[3] = {(double)b[0] - a[0], (double)b[1] - a[1], (double)b[2] - a[2]};
+    double e2[3] = {(double)c[0] - a[0], (double)c[1] - a[1], (double)c[2] - a[2]};
     double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
     double nn = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
     if (nn > 0) for (double &x : n) x /= nn;

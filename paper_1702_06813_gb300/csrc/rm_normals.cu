@@ -41,21 +41,26 @@ struct NormalArgs {
 
 // Dynamic shared memory: the staged (depth, validity) pairs of the tile plus its halo, the
 // horizontal sums (weighted depth, weight) of each staged row over the smoothed columns, and
-// the smoothed depth S of the tile plus a one-pixel ring.
+// the smoothed depth S of the tile plus a one-pixel ring. The two float2 tables are read down
+// their columns by consecutive threads, so their row strides are padded to 1 mod 16 float2:
+// consecutive rows then start two banks apart and a warp's 8-byte reads take two wavefronts.
+__host__ __device__ constexpr int pad16p1(int n) { return n + ((17 - n % 16) % 16); }
 __host__ __device__ inline int staged_w(int r) { return kSW + 2 * r; }
 __host__ __device__ inline int staged_h(int r) { return kSH + 2 * r; }
+__host__ __device__ inline int staged_stride(int r) { return pad16p1(staged_w(r)); }
+constexpr int kSWP = pad16p1(kSW);  // row stride of the horizontal sums
 inline size_t normals_smem(int r) {
-  return sizeof(float2) * ((size_t)staged_h(r) * staged_w(r) + (size_t)staged_h(r) * kSW) +
+  return sizeof(float2) * ((size_t)staged_h(r) * staged_stride(r) + (size_t)staged_h(r) * kSWP) +
          sizeof(float) * kSH * kSW;
 }
 
 template <int R>
 __global__ void __launch_bounds__(kThreadsN) k_depth_normals(NormalArgs a) {
   extern __shared__ float4 smem_raw[];
-  constexpr int dw = kSW + 2 * R, dh = kSH + 2 * R;
-  float2 *sz = reinterpret_cast<float2 *>(smem_raw);  // [dh][dw]: (valid ? z : 0, valid)
-  float2 *sh = sz + dh * dw;                           // [dh][kSW]
-  float *sS = reinterpret_cast<float *>(sh + dh * kSW); // [kSH][kSW]
+  constexpr int dw = kSW + 2 * R, dh = kSH + 2 * R, dws = pad16p1(dw);
+  float2 *sz = reinterpret_cast<float2 *>(smem_raw);   // [dh][dws]: (valid ? z : 0, valid)
+  float2 *sh = sz + dh * dws;                           // [dh][kSWP]
+  float *sS = reinterpret_cast<float *>(sh + dh * kSWP); // [kSH][kSW]
   const int tid = threadIdx.x;
   float g[R + 1];
 #pragma unroll
@@ -94,7 +99,7 @@ __global__ void __launch_bounds__(kThreadsN) k_depth_normals(NormalArgs a) {
       if (k < n_st) {
         const bool ok = cv[m] == 0 && fabsf(dv[m]) <= FLT_MAX;
         mine_valid = mine_valid && ok;
-        sz[k] = ok ? make_float2(dv[m], 1.0f) : make_float2(0.0f, 0.0f);
+        sz[(k / dw) * dws + k % dw] = ok ? make_float2(dv[m], 1.0f) : make_float2(0.0f, 0.0f);
       }
     }
   }
@@ -102,15 +107,15 @@ __global__ void __launch_bounds__(kThreadsN) k_depth_normals(NormalArgs a) {
   // horizontal pass: weighted sums of the valid depths (and of their weights, unless every
   // staged pixel is valid), kHG adjacent outputs per thread: each staged value is loaded once
   // and added to every output whose window holds it (the taps unroll: R is a template
-  // parameter)
+  // parameter); consecutive threads take consecutive rows
   {
     constexpr int groups = (kSW + kHG - 1) / kHG;
     for (int it = tid; it < dh * groups; it += kThreadsN) {
-      const int v = it / groups, u0 = (it % groups) * kHG;
+      const int v = it % dh, u0 = (it / dh) * kHG;
       float num[kHG], den[kHG];
 #pragma unroll
       for (int j = 0; j < kHG; ++j) num[j] = den[j] = 0.0f;
-      const float2 *row = sz + v * dw + u0;  // output u0 + j: staged columns u0 + j .. + 2R
+      const float2 *row = sz + v * dws + u0;  // output u0 + j: staged columns u0 + j .. + 2R
       if (all_valid) {
 #pragma unroll
         for (int t = 0; t < 2 * R + kHG; ++t) {
@@ -138,7 +143,7 @@ __global__ void __launch_bounds__(kThreadsN) k_depth_normals(NormalArgs a) {
       }
 #pragma unroll
       for (int j = 0; j < kHG; ++j)
-        if (u0 + j < kSW) sh[v * kSW + u0 + j] = make_float2(num[j], den[j]);
+        if (u0 + j < kSW) sh[v * kSWP + u0 + j] = make_float2(num[j], den[j]);
     }
   }
   __syncthreads();
@@ -153,7 +158,7 @@ __global__ void __launch_bounds__(kThreadsN) k_depth_normals(NormalArgs a) {
       if (all_valid) {
 #pragma unroll
         for (int t = 0; t < 2 * R + kVG; ++t) {
-          const float h = (v0 + t < dh) ? sh[(v0 + t) * kSW + u].x : 0.0f;
+          const float h = (v0 + t < dh) ? sh[(v0 + t) * kSWP + u].x : 0.0f;
 #pragma unroll
           for (int j = 0; j < kVG; ++j) {
             const int d = t - j;
@@ -166,7 +171,7 @@ __global__ void __launch_bounds__(kThreadsN) k_depth_normals(NormalArgs a) {
       } else {
 #pragma unroll
         for (int t = 0; t < 2 * R + kVG; ++t) {
-          const float2 hv = (v0 + t < dh) ? sh[(v0 + t) * kSW + u] : make_float2(0.0f, 0.0f);
+          const float2 hv = (v0 + t < dh) ? sh[(v0 + t) * kSWP + u] : make_float2(0.0f, 0.0f);
 #pragma unroll
           for (int j = 0; j < kVG; ++j) {
             const int d = t - j;
@@ -181,7 +186,7 @@ __global__ void __launch_bounds__(kThreadsN) k_depth_normals(NormalArgs a) {
         for (int j = 0; j < kVG; ++j) {
           const int v = v0 + j;
           if (v < kSH) {
-            const bool centre = sz[(v + R) * dw + (u + R)].y != 0.0f;
+            const bool centre = sz[(v + R) * dws + (u + R)].y != 0.0f;
             sS[v * kSW + u] = centre ? num[j] / den[j] : __int_as_float(0x7fc00000);
           }
         }

@@ -117,11 +117,15 @@ def fp32_bound(om, pose, cam, scan_depth, scan_class, eps=0.1, weights=(1.0, 1.0
     w = np.vectorize(wmap.get)(oc[jj, ii]).astype(np.float64)
     res = np.abs(o["resid"][jj, ii])
     aJ = np.abs(J)
-    delta = np.repeat(rel[:, None], 6, 1)
-    delta[:, 3:] += rel_t[:, None]
-    g_bound = (w * res)[:, None] * aJ * delta
-    g_bound = g_bound.sum(0)
-    H = np.einsum("p,pa,pb->ab", w, aJ * delta, aJ) + np.einsum("p,pa,pb->ab", w, aJ, aJ * delta)
+    # absolute error of each component: relative part, plus the rounding of the cross product
+    # r x n, whose components cancel where r and n are nearly parallel
+    crs = np.stack([np.abs(r[:, 1] * n[:, 2]) + np.abs(r[:, 2] * n[:, 1]),
+                    np.abs(r[:, 2] * n[:, 0]) + np.abs(r[:, 0] * n[:, 2]),
+                    np.abs(r[:, 0] * n[:, 1]) + np.abs(r[:, 1] * n[:, 0])], 1)
+    dJ = aJ * rel[:, None]
+    dJ[:, 3:] += aJ[:, 3:] * rel_t[:, None] + 4 * u * (t / np.abs(nr))[:, None] * crs
+    g_bound = ((w * res)[:, None] * dJ).sum(0)
+    H = np.einsum("p,pa,pb->ab", w, dJ, aJ) + np.einsum("p,pa,pb->ab", w, aJ, dJ)
     iu = np.triu_indices(6)
     return g_bound, H[iu]
 
