@@ -8,7 +8,7 @@ least-squares residual, and reduce the adjoint gradient and Gauss-Newton matrix 
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
   python bench.py --workload tracking     # 64 mixed-sensor agents, rm_align_batch per frame
-  python bench.py --workload icp          # point-to-plane ICP terms and alignments (Sec. IV)
+  python bench.py --workload icp          # point-to-plane ICP terms and alignments (Sec. V)
   python bench.py --workload normals      # Eq. 2 normals of 64 depth images per step
   python bench.py --workload vgrad        # vertex-position gradient of 16 poses per step
 """
@@ -50,7 +50,7 @@ def args_():
     ap.add_argument("--agents", type=int, default=64, help="tracking: agents (scans per frame)")
     ap.add_argument("--triangles", type=int, default=2_000_000, help="tracking: map size")
     ap.add_argument("--method", choices=["lm", "icp"], default="lm",
-                    help="tracking: LM on the Table I surrogate, or point-to-plane ICP (Sec. IV)")
+                    help="tracking: LM on the Table I surrogate, or point-to-plane ICP (Sec. V)")
     return ap.parse_args()
 
 
@@ -412,7 +412,7 @@ def oracle_row_timings(w, dstart, tol=0.1):
 
 
 def run_icp(a):
-    """Render-accelerated point-to-plane ICP (Sec. IV). Value: ICP term evaluations per second
+    """Render-accelerated point-to-plane ICP (Sec. V). Value: ICP term evaluations per second
     (render + projective association + J^T e, J^T J) for the 256 candidate poses of the
     1M-triangle 640x480 room, L2 flushed between steps. Alongside: rm_icp_align wall time on
     that room's scan from a 5 cm / 2 deg start and on the 2M-triangle 1024x64 lidar scan
@@ -560,7 +560,7 @@ def run_icp(a):
                     "hbm_frac": normals_gbs / pk["hbm_gbs"],
                     "l2": "flushed between launches (256 MiB write)"}
 
-    # meshification of the room scan (Sec. III.A): 640x480 -> 306k vertices, 612k faces
+    # meshification of the room scan (Sec. IV.A): 640x480 -> 306k vertices, 612k faces
     P_img = cam.width * cam.height
     mv = torch.empty((P_img, 3), dtype=torch.float32, device="cuda")
     mf = torch.empty((2 * (cam.width - 1) * (cam.height - 1), 3), dtype=torch.int32, device="cuda")
@@ -585,7 +585,7 @@ def run_icp(a):
                  "algorithmic_bytes": mbytes, "achieved_gbs": mbytes * 20 / (ms_m * 1e-3) / 1e9,
                  "kernels_per_call": 4}
 
-    # derivative-free alignment on the Table I cost (Sec. III.C), room scan from 3 cm / 1.5 deg
+    # derivative-free alignment on the Table I cost (Sec. IV.C), room scan from 3 cm / 1.5 deg
     rng2 = np.random.Generator(np.random.PCG64(a.seed + 9))
     dstart = synth.perturb_fixed(w["gt"], rng2, 0.03, 1.5)
     dpar = rm.dfo_params(nm_iters=60, cd_iters=40)
@@ -701,7 +701,7 @@ def _small_line(a, metric, unit, value, ms, config, roofline, cpu, launches):
 
 
 def run_normals(a):
-    """Eq. 2 surface normals (Sec. IV) of 64 noisy copies of the 640x480 room scan per step
+    """Eq. 2 surface normals (Sec. V) of 64 noisy copies of the 640x480 room scan per step
     (sigma 1.5 px, metric), one rm_depth_normals call. Algorithmic bytes: depth and class in,
     the normal out, 17 per pixel. CPU baseline: the oracle on one image per host thread."""
     import torch

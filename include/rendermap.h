@@ -5,17 +5,17 @@
  * labelled triangle-mesh map, following Ryde & Ding, "RenderMap: Exploiting the Link Between
  * Perception and Rendering for Dense Mapping" (arXiv 1702.06813):
  *   - the map is the mesh of the interfaces between free, occupied and unknown space, each
- *     face labelled free-occupied (FO), free-unknown (FU) or unknown-occupied (UO) (Sec. III.A,
+ *     face labelled free-occupied (FO), free-unknown (FU) or unknown-occupied (UO) (Sec. IV.A,
  *     Fig. 3);
  *   - E(X) = C(R(T(X)), Z_s) (Eq. 1): render the map's z-buffer R from the camera pose and
  *     compare it per pixel with the scan Z_s;
- *   - the comparison is Table I (Sec. III.B), summed over all pixels.
+ *   - the comparison is Table I (Sec. IV.B), summed over all pixels.
  * On top of the paper's cost the library computes a truncated least-squares surrogate with
  * the same cells and thresholds, its derivative with respect to a pose twist, and
- * Levenberg-Marquardt steps on it (the paper's Sec. III.C optimiser is derivative-free).
- * Around that path: render-accelerated point-to-plane ICP (Sec. IV), the derivative-free
- * search of Sec. III.C on the exact Table I cost, Fig. 7's cost sweeps, depth-image normals
- * (Eq. 2) and blur, the meshification of range images (Sec. III.A), the cost's gradient with
+ * Levenberg-Marquardt steps on it (the paper's Sec. IV.C optimiser is derivative-free).
+ * Around that path: render-accelerated point-to-plane ICP (Sec. V), the derivative-free
+ * search of Sec. IV.C on the exact Table I cost, Fig. 7's cost sweeps, depth-image normals
+ * (Eq. 2) and blur, the meshification of range images (Sec. IV.A), the cost's gradient with
  * respect to the map's vertices, and input helpers for raw range images and the paper's pose
  * vector.
  *
@@ -61,10 +61,10 @@ typedef enum {
   RM_ENOTCONV = 6    /* rm_align / rm_icp_align stopped without meeting step_tol */
 } rm_status;
 
-/* Face labels (Sec. III.A): the interface a map face lies on. */
+/* Face labels (Sec. IV.A): the interface a map face lies on. */
 enum { RM_LABEL_FO = 0, RM_LABEL_FU = 1, RM_LABEL_UO = 2 };
-/* Scan pixel classes (Sec. III.B): a return (FO), no return drawn at the sensor's maximum
- * range (FU, Sec. III.A), or a dead pixel (NaN). A scan pixel whose depth is not finite, or
+/* Scan pixel classes (Sec. IV.B): a return (FO), no return drawn at the sensor's maximum
+ * range (FU, Sec. IV.A), or a dead pixel (NaN). A scan pixel whose depth is not finite, or
  * whose class byte is above 2, counts as NaN. */
 enum { RM_SCAN_FO = 0, RM_SCAN_FU = 1, RM_SCAN_NAN = 2 };
 /* Table I outcomes, the index into every counts[6] array. */
@@ -108,7 +108,7 @@ typedef struct {
 /* Per-pose outputs of rm_cost / rm_cost_grad; any pointer may be NULL; host or device. */
 typedef struct {
   int64_t *counts;          /* N*6 pixels per Table I outcome (RM_FOFO_REWARD ...) */
-  int64_t *e_table;         /* N   Table I cost: penalties minus rewards (Sec. III.B) */
+  int64_t *e_table;         /* N   Table I cost: penalties minus rewards (Sec. IV.B) */
   double *e_ls;             /* N   1/2 sum w r^2 of the truncated least-squares surrogate */
   double *grad;             /* N*6 d e_ls / d xi = sum w r J (rm_cost_grad only) */
   double *jtj;              /* N*21 packed sum w J J^T (rm_cost_grad only) */
@@ -153,7 +153,7 @@ typedef struct rm_map rm_map;
  * FP32; poses are shifted to match) and precomputes unit face normals. Ownership: the
  * caller keeps its arrays; *out is released with rm_map_destroy.
  * Errors: RM_EINVAL for null pointers, negative sizes, T >= 2^31, an index outside [0, V),
- * a label above 2 or a non-finite vertex; RM_ENOMEM; RM_ECUDA. (Sec. III.A, Fig. 3.) */
+ * a label above 2 or a non-finite vertex; RM_ENOMEM; RM_ECUDA. (Sec. IV.A, Fig. 3.) */
 rm_status rm_map_create(const float *vertices, int64_t n_vertices, const int32_t *faces,
                         const uint8_t *labels, int64_t n_faces, rm_map **out);
 void rm_map_destroy(rm_map *map);
@@ -162,7 +162,7 @@ rm_status rm_map_info(const rm_map *map, int64_t *n_vertices, int64_t *n_faces,
                       double centre[3]);
 rm_status rm_map_set_tuning(rm_map *map, const rm_tuning *tuning);
 
-/* Attaches per-vertex normals to the map for the point-to-plane ICP entry points (Sec. IV,
+/* Attaches per-vertex normals to the map for the point-to-plane ICP entry points (Sec. V,
  * sequential depth-image alignment, steps 2-3: the normals of D_i by Eq. 2, then the points of
  * D_i rendered coloured by their normals). Afterwards the normal of an associated pixel is the
  * blend of the seen triangle's three vertex normals by the hit's barycentrics (a rasteriser
@@ -181,8 +181,8 @@ rm_status rm_map_get_tuning(const rm_map *map, rm_tuning *tuning);
 /* R(Y) of Eq. 1: the z-buffer of the map seen from each of N poses. The z-buffer keeps, per
  * pixel, the nearest triangle under the library's FP32 rasterisation contract (8-bit
  * sub-pixel snapping, top-left fill rule, one sample at the pixel centre, no anti-aliasing
- * as in Sec. V; ties go to the lower triangle id).
- * depth: N*H*W float32, NaN where the ray hits nothing (the paper's NaN, Sec. III.B);
+ * as in Sec. VI; ties go to the lower triangle id).
+ * depth: N*H*W float32, NaN where the ray hits nothing (the paper's NaN, Sec. IV.B);
  * tri_id: optional N*H*W int32, -1 where nothing is hit;
  * bary: optional N*H*W*2 float32 barycentrics (b1, b2) of the hit on that triangle.
  * All outputs host or device; `poses` host or device. stream: a cudaStream_t or NULL. */
@@ -190,7 +190,7 @@ rm_status rm_render_depth(rm_map *map, const double *poses, int32_t n_poses,
                           const rm_intrinsics *intr, float *depth, int32_t *tri_id,
                           float *bary, void *stream);
 
-/* E(X) of Eq. 1 with C from Table I (Sec. III.B) for N poses against one scan, plus the
+/* E(X) of Eq. 1 with C from Table I (Sec. IV.B) for N poses against one scan, plus the
  * least-squares surrogate: counts, e_table and e_ls in `out` (grad / jtj ignored). */
 rm_status rm_cost(rm_map *map, const rm_scan *scan, const double *poses, int32_t n_poses,
                   const rm_cost_params *params, const rm_cost_out *out, void *stream);
@@ -240,7 +240,7 @@ rm_status rm_cost_grad_vertices(rm_map *map, const rm_scan *scan, const double *
                                 void *stream);
 
 /* ---- Input helpers ----------------------------------------------------------------------
- * Depth and class of n pixels of raw range images (Sec. III.A, III.B): a NaN reading, or a
+ * Depth and class of n pixels of raw range images (Sec. IV.A, IV.B): a NaN reading, or a
  * return closer than range_min (and above 0), is a dead pixel (RM_SCAN_NAN, depth NaN); no
  * reading (<= 0, above range_max, +inf) is free space up to the sensor's maximal range
  * (RM_SCAN_FU, depth range_max); the rest are returns (RM_SCAN_FO, their range). Arrays host
@@ -254,11 +254,11 @@ rm_status rm_scan_from_range(const float *range, int64_t n_pixels, float range_m
  * (the paper does not state the order) and translation (x, y, z). Host or device. */
 rm_status rm_pose_from_x(const double *X, int32_t n, double *poses, void *stream);
 
-/* ---- Render-accelerated point-to-plane ICP (Sec. IV) ----------------------------------
+/* ---- Render-accelerated point-to-plane ICP (Sec. V) ----------------------------------
  * Projective association: the map is rendered at the pose and each pixel's winning surface is
  * paired with the scan return of the same pixel when the surface is FO, the scan pixel is an
  * FO return, and |Z_M - Z_1| < tol (decided in FP32 on the z-buffer depth and the scan depth,
- * the z-difference test of Sec. IV). For a pair, with r the pixel's ray, t the map depth, d
+ * the z-difference test of Sec. V). For a pair, with r the pixel's ray, t the map depth, d
  * the scan depth, p = d r the scan point and n the map surface's unit normal in the camera
  * frame, the residual is the point-to-plane distance e = (d - t) (n . r) and its Jacobian
  * with respect to the right-perturbation twist (rho, phi) of the pose (T <- T exp(xi^)) is
@@ -267,7 +267,7 @@ rm_status rm_pose_from_x(const double *X, int32_t n, double *poses, void *stream
 /* Per-pose outputs of rm_icp_terms; any pointer may be NULL; host or device. */
 typedef struct {
   int64_t *n_assoc;         /* N   associated pixels */
-  double *cost_l1;          /* N   C = sum |Z_M - Z_1| over the associated pixels (Sec. IV) */
+  double *cost_l1;          /* N   C = sum |Z_M - Z_1| over the associated pixels (Sec. V) */
   double *e2;               /* N   sum e^2 */
   double *jte;              /* N*6 sum J e */
   double *jtj;              /* N*21 packed sum J J^T (row-major upper triangle) */
@@ -305,7 +305,7 @@ rm_status rm_icp_align(rm_map *map, const rm_scan *scan, const double *init_pose
                        void *stream);
 
 
-/* Surface normals of depth images (Eq. 2, Sec. IV), n images of one camera (intr: width,
+/* Surface normals of depth images (Eq. 2, Sec. V), n images of one camera (intr: width,
  * height, and fx, fy for metric normals), each H*W float depth plus H*W uint8 RM_SCAN_* class,
  * host or device. A pixel is valid when its class is FO and its depth finite. The valid depths
  * are smoothed with a Gaussian of sigma pixels (0 <= sigma <= 5, radius ceil(3 sigma), weights
@@ -324,7 +324,7 @@ rm_status rm_depth_normals(const rm_intrinsics *intr, int32_t n_images, const fl
                            const uint8_t *cls, float sigma, int32_t metric, float *normals,
                            float *smoothed, void *stream);
 
-/* Gaussian blur of depth images for cost smoothing (Sec. III.C): the smoothing above alone.
+/* Gaussian blur of depth images for cost smoothing (Sec. IV.C): the smoothing above alone.
  * out (n*H*W float, host or device) holds each FO return's smoothed depth and every other
  * pixel's input depth unchanged (FU pixels stay at their maximal range, dead pixels NaN), so
  * the result pairs with the same class image as a scan. out must not overlap depth or cls
@@ -332,7 +332,7 @@ rm_status rm_depth_normals(const rm_intrinsics *intr, int32_t n_images, const fl
 rm_status rm_depth_blur(const rm_intrinsics *intr, int32_t n_images, const float *depth,
                         const uint8_t *cls, float sigma, float *out, void *stream);
 
-/* ---- Derivative-free search on the Table I cost (Sec. III.C) ---------------------------
+/* ---- Derivative-free search on the Table I cost (Sec. IV.C) ---------------------------
  * The paper minimises its piecewise-constant cost with Nelder-Mead and coordinate descent.
  * Here both run on the device over twists xi of the start pose (pose = T0 exp(xi^)), scaled
  * per axis by scale_t (metres) and scale_r (radians); each step's candidates are rendered and
@@ -373,11 +373,11 @@ rm_status rm_cost_sweep(rm_map *map, const rm_scan *scan, const double *pose, in
                         double span, int32_t n, const rm_cost_params *params,
                         const rm_cost_out *out, void *stream);
 
-/* ---- Meshification of a range image (Sec. III.A, Fig. 5) ------------------------------ */
+/* ---- Meshification of a range image (Sec. IV.A, Fig. 5) ------------------------------ */
 typedef struct {
   float max_range;          /* no-return pixels are drawn at this range (4 m for Kinect-class) */
   float max_edge;           /* quads with a side or diagonal longer than this are FU (0.1 m) */
-  int32_t step;             /* grid stride in pixels (1; 2 = the factor-2 downsampling of Sec. IV) */
+  int32_t step;             /* grid stride in pixels (1; 2 = the factor-2 downsampling of Sec. V) */
   int32_t reserved;
 } rm_meshify_params;
 
@@ -430,7 +430,7 @@ typedef struct {
  * (RM_ETIMEOUT). Outputs as for rm_cost_grad, per problem
  * (index k = problem). Screen tiles are 64x32 for pinhole problems and 32x32 for ray-table
  * problems, the per-call entry points' defaults, so a problem's results equal those of
- * rm_cost_grad with default tiles bit for bit. (Sec. III.C / Sec. V: many evaluations per
+ * rm_cost_grad with default tiles bit for bit. (Sec. IV.C / Sec. VI: many evaluations per
  * scan match; batching them is this library's extension.) */
 rm_status rm_cost_grad_batch(rm_map *map, const rm_problem *problems, int32_t n,
                              const rm_cost_params *params, const rm_cost_out *out, void *stream);

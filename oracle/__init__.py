@@ -255,7 +255,7 @@ def depth_normals(depth, cls, sigma=1.0, metric=False, fx=1.0, fy=1.0):
 
 
 def meshify(cam, depth, cls, pose, max_range, max_edge=0.1, step=1):
-    """Labelled mesh of a range image (Sec. III.A): (vertices (Hs*Ws, 3) float32, faces (F, 3)
+    """Labelled mesh of a range image (Sec. IV.A): (vertices (Hs*Ws, 3) float32, faces (F, 3)
     int32, labels (F,) uint8)."""
     c, keep = make_cam(cam)
     d = _f32(depth)
@@ -303,7 +303,7 @@ def depth_blur(depth, cls, sigma=1.0):
 
 
 class OracleMap:
-    """The oracle's copy of a labelled triangle-mesh map (Sec. III.A)."""
+    """The oracle's copy of a labelled triangle-mesh map (Sec. IV.A)."""
 
     def __init__(self, vertices, faces, labels):
         self.v = _f32(vertices).reshape(-1, 3)
@@ -453,7 +453,7 @@ class OracleMap:
         return r
 
     def dfo_align(self, pose0, cam, scan_depth, scan_class, params=None, dfo=None):
-        """Nelder-Mead then coordinate descent on the Table I cost (Sec. III.C)."""
+        """Nelder-Mead then coordinate descent on the Table I cost (Sec. IV.C)."""
         c, keep = make_cam(cam)
         prm = params or make_params()
         d = dfo or dfo_params()
@@ -473,8 +473,8 @@ class OracleMap:
         return out.reshape(4, 4), r
 
     def icp_terms(self, pose, cam, scan_depth, scan_class, tol, vnormals=None):
-        """Point-to-plane ICP terms with projective association (Sec. IV); vnormals (V, 3)
-        world-frame vertex normals select the normal-coloured map (Sec. IV step 3)."""
+        """Point-to-plane ICP terms with projective association (Sec. V); vnormals (V, 3)
+        world-frame vertex normals select the normal-coloured map (Sec. V step 3)."""
         c, keep = make_cam(cam)
         vn = None if vnormals is None else _f64(vnormals).reshape(-1, 3)
         na = ctypes.c_int64()

@@ -6,20 +6,20 @@
  * no fusion. It shares no code with the CUDA library.
  *
  * What it computes, and where the paper defines it:
- *  - Sec. III.A: the map is a triangle mesh of the interfaces between free, occupied and
+ *  - Sec. IV.A: the map is a triangle mesh of the interfaces between free, occupied and
  *    unknown space, each face labelled FO / FU / UO; it is rendered into a z-buffer image.
  *  - Eq. 1: E(X) = C(R(T(X)), Z_s), R(Y) the z-buffer rendered from camera pose Y.
  *  - Table I: the per-pixel reward / penalty from the map class, the scan class and
  *    dz = d(p_r) - d(p_s) with the inlier threshold eps = 0.1 m; the cost is the sum over
- *    all pixels (Sec. III.B).
- *  - Sec. III.C names derivative-based and derivative-free optimisers; this oracle adds the
+ *    all pixels (Sec. IV.B).
+ *  - Sec. IV.C names derivative-based and derivative-free optimisers; this oracle adds the
  *    least-squares surrogate whose Levenberg-Marquardt step the library runs (a reading, not
  *    the paper's own optimiser), with the pose derivative of the ray-plane depth, and the
  *    paper's own derivative-free search (Nelder-Mead, then coordinate descent) on Table I.
- *  - Sec. IV: render-accelerated point-to-plane ICP (projective association with a depth
+ *  - Sec. V: render-accelerated point-to-plane ICP (projective association with a depth
  *    tolerance, point-to-plane residual and its 6x6 normal equations) and the depth-image
  *    normals of Eq. 2.
- *  - Sec. III.A / Fig. 5: meshification of a range image into FO / FU quads; Sec. III.A-B:
+ *  - Sec. IV.A / Fig. 5: meshification of a range image into FO / FU quads; Sec. IV.A-B:
  *    the classes of raw range readings; Eq. 1: the pose of the vector X.
  *  - Map refinement: the surrogate's gradient with respect to the vertex positions.
  * Every function is pinned by tests against closed forms, invariants, brute force or finite
@@ -85,7 +85,7 @@ void orc_transform(const float M[12], const float *v, int64_t V, float *vc) {
 }
 
 /* ------------------------------------------------------------------------------------- */
-/* the z-buffer (Sec. III.A render; depth buffer as in Sec. III)                          */
+/* the z-buffer (Sec. IV.A render; depth buffer as in Sec. IV)                          */
 /* ------------------------------------------------------------------------------------- */
 
 /* Camera-space plane n . p = d of a triangle, and its inverse depth w = 1/t folded per pixel:
@@ -163,7 +163,7 @@ static int snap(const orc_cam *cam, float X, float Y, float Z, int32_t *xi, int3
 }
 
 /* One snapped triangle: integer edge functions, top-left fill rule, sample at pixel centres
- * (256 i + 128, 256 j + 128); single sample, no anti-aliasing (Sec. V renders with AA off). */
+ * (256 i + 128, 256 j + 128); single sample, no anti-aliasing (Sec. VI renders with AA off). */
 static void raster_snapped(int32_t x[3], int32_t y[3], const plane32 *pl, uint32_t id,
                            const orc_cam *cam, uint64_t *keys, int32_t *frags, int brute,
                            orc_stats *st) {
@@ -837,12 +837,12 @@ int orc_cost_batch(const float *v, const float *vr, int64_t V, const double cent
 }
 
 /* ------------------------------------------------------------------------------------- */
-/* Render-accelerated point-to-plane ICP (Sec. IV)                                         */
+/* Render-accelerated point-to-plane ICP (Sec. V)                                         */
 /* ------------------------------------------------------------------------------------- */
 
 /* One ICP association at pixel p of the render at Twc: the map surface seen at the pixel
  * must be occupied (FO), the scan pixel a return (FO), and |Z_M - Z_1| below the tolerance
- * (Sec. IV), decided on the FP32 z-buffer depth and the FP32 difference. On success returns
+ * (Sec. V), decided on the FP32 z-buffer depth and the FP32 difference. On success returns
  * 1 with the unit camera-frame normal of the map surface nu, the ray r, the map depth t and
  * the scan depth d (both as FP64 from the FP32 values) and the FP32 difference. */
 static int icp_pair(const float *v, const int32_t *faces, const uint8_t *labels,
@@ -861,7 +861,7 @@ static int icp_pair(const float *v, const int32_t *faces, const uint8_t *labels,
   if (!(fabsf(dz32) < tol)) return 0;
   double n[3], dc;
   if (vnormals) {
-    /* the map's points coloured by their normals (Sec. IV, step 3): the normal seen at the
+    /* the map's points coloured by their normals (Sec. V, step 3): the normal seen at the
      * pixel blends the triangle's three vertex normals by the hit's barycentrics, as a
      * rasteriser interpolates a vertex attribute; a vertex without a normal (NaN) leaves the
      * pixel unassociated */
@@ -1055,7 +1055,7 @@ int orc_depth_normals(const float *depth, const uint8_t *cls, int W, int H, doub
 }
 
 /* ------------------------------------------------------------------------------------- */
-/* Meshification of a range image (Sec. III.A, Fig. 5)                                     */
+/* Meshification of a range image (Sec. IV.A, Fig. 5)                                     */
 /* ------------------------------------------------------------------------------------- */
 
 /* Camera-frame point of pixel (x, y) at range d along its ray, in FP32 (the label test is an
@@ -1147,7 +1147,7 @@ int orc_meshify(const orc_cam *cam, const float *depth, const uint8_t *cls, cons
 }
 
 /* ------------------------------------------------------------------------------------- */
-/* Derivative-free search on the Table I cost (Sec. III.C): Nelder-Mead, then coordinate  */
+/* Derivative-free search on the Table I cost (Sec. IV.C): Nelder-Mead, then coordinate  */
 /* (compass) descent near the minimum                                                      */
 /* ------------------------------------------------------------------------------------- */
 
@@ -1316,7 +1316,7 @@ int orc_dfo_align(const float *v, const float *vr, int64_t V, const double centr
 }
 
 /* ------------------------------------------------------------------------------------- */
-/* Scan classes from a raw range image (Sec. III.A, III.B); pose from X (Eq. 1)             */
+/* Scan classes from a raw range image (Sec. IV.A, IV.B); pose from X (Eq. 1)             */
 /* ------------------------------------------------------------------------------------- */
 
 void orc_scan_from_range(const float *range, int64_t n, float range_min, float range_max,

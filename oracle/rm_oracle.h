@@ -119,16 +119,16 @@ int orc_cost_batch(const float *v, const float *vr, int64_t V, const double cent
                    const uint8_t *scan_class, const orc_params *prm, int64_t *counts,
                    double *e_ls, double *grad, double *jtj);
 
-/* Render-accelerated point-to-plane ICP (Sec. IV). One iteration's terms at pose Twc: a pixel
+/* Render-accelerated point-to-plane ICP (Sec. V). One iteration's terms at pose Twc: a pixel
  * is associated when the map surface it sees is FO, the scan pixel is an FO return and
- * |Z_M - Z_1| < tol (FP32 z-buffer depth, FP32 difference; Sec. IV's z-difference test). With
+ * |Z_M - Z_1| < tol (FP32 z-buffer depth, FP32 difference; Sec. V's z-difference test). With
  * the scan point p = d r, the map point q = t r on the same ray and the map surface's unit
  * camera-frame normal n, the residual is e = (p - q) . n and its Jacobian w.r.t. the right-
  * perturbation twist (rho, phi) of Twc is J = (n, p x n). n_assoc counts the associations,
  * cost_l1 = sum |Z_M - Z_1| over them (the paper's C), e2 = sum e^2, jte = sum J e,
  * jtj = upper triangle of sum J J^T.
  * vnormals (V*3 world-frame vectors, or NULL): when given, n is not the face plane's normal
- * but the map's points coloured by their normals (Sec. IV, sequential alignment step 3): the
+ * but the map's points coloured by their normals (Sec. V, sequential alignment step 3): the
  * three vertex normals of the seen triangle blended by the hit's barycentrics, rotated into
  * the camera frame and normalised; a pixel whose blend is not finite (a vertex without a
  * normal, NaN) is not associated. */
@@ -155,7 +155,7 @@ int orc_icp_align(const float *v, const float *vr, int64_t V, const double centr
                   double Twc_out[16], int *iters, int *converged, int64_t *n_assoc,
                   double *cost_l1);
 
-/* Surface normals of a depth image (Eq. 2, Sec. IV). A pixel is valid when its class is FO
+/* Surface normals of a depth image (Eq. 2, Sec. V). A pixel is valid when its class is FO
  * (0) and its depth finite. The valid depths are smoothed with a Gaussian of standard
  * deviation sigma pixels (0 <= sigma <= 5; radius ceil(3 sigma); weights renormalised over
  * the valid pixels in the window; invalid pixels stay invalid), then differentiated by central
@@ -167,8 +167,8 @@ int orc_icp_align(const float *v, const float *vr, int64_t V, const double centr
 int orc_depth_normals(const float *depth, const uint8_t *cls, int W, int H, double sigma,
                       int metric, double fx, double fy, double *normals, double *smoothed);
 
-/* Meshification of a range image (Sec. III.A, Fig. 5). The grid takes every step-th pixel
- * across and down (step 2 = the factor-2 downsampling of Sec. IV). Each grid pixel is a
+/* Meshification of a range image (Sec. IV.A, Fig. 5). The grid takes every step-th pixel
+ * across and down (step 2 = the factor-2 downsampling of Sec. V). Each grid pixel is a
  * vertex at its range along its ray, transformed to the world by Twc: returns (FO) at their
  * depth, no-return pixels (FU) at max_range; dead pixels (scan class NaN) are parked at the
  * sensor origin and unreferenced. Each 2x2 block of adjacent grid vertices with no dead pixel
@@ -180,7 +180,7 @@ int orc_meshify(const orc_cam *cam, const float *depth, const uint8_t *cls, cons
                 float max_range, float max_edge, int step, float *vertices, int32_t *faces,
                 uint8_t *labels, int64_t *n_faces);
 
-/* Derivative-free search (Sec. III.C): Nelder-Mead iterations, then coordinate descent once
+/* Derivative-free search (Sec. IV.C): Nelder-Mead iterations, then coordinate descent once
  * near the minimum. The search runs over twists xi (rho in metres, phi in radians) scaled
  * per axis by `scale`; each step evaluates its candidates as one batch.
  *  - Simplex: the origin and nm_step * scale_k along each axis k. Per iteration the vertices
@@ -217,7 +217,7 @@ int orc_dfo_align(const float *v, const float *vr, int64_t V, const double centr
                   const orc_params *prm, const orc_dfo_params *p, double Twc_out[16],
                   int64_t *e_table, orc_dfo_report *rep);
 
-/* Depth and class of each pixel of a raw range image (Sec. III.A, III.B): NaN, or a return
+/* Depth and class of each pixel of a raw range image (Sec. IV.A, IV.B): NaN, or a return
  * closer than range_min (and above 0), is dead (NaN class, NaN depth); no reading (<= 0,
  * above range_max, +inf) is free space up to the maximal range (FU, depth range_max); the rest
  * are returns (FO, their range). */

@@ -1,8 +1,8 @@
 """GB300-native RenderMap pose-cost engine (Ryde & Ding, arXiv 1702.06813).
 
-The map is a labelled triangle mesh of the free/occupied/unknown interfaces (Sec. III.A); a
+The map is a labelled triangle mesh of the free/occupied/unknown interfaces (Sec. IV.A); a
 pose is scored by rendering the map's z-buffer from it and comparing it per pixel with an
-observed range image by Table I (Sec. III.B, Eq. 1). All of it runs in hand-written sm_103a
+observed range image by Table I (Sec. IV.B, Eq. 1). All of it runs in hand-written sm_103a
 CUDA kernels behind the C ABI of include/rendermap.h; this package is the thin binding.
 """
 from .rendermap import (OUTCOMES, RM_PINHOLE, RM_RAYTABLE, Intrinsics, Map, RenderMapCost,  # noqa: F401

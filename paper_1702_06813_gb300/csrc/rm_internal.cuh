@@ -1,13 +1,13 @@
 // rm_internal.cuh -- device-side data layout and the FP32 rasterisation contract.
 //
-// The z-buffer of Sec. III (R(Y) in Eq. 1) must pick, for every pixel, exactly the triangle
+// The z-buffer of Sec. IV (R(Y) in Eq. 1) must pick, for every pixel, exactly the triangle
 // the CPU reference picks. Every step that feeds coverage or the depth key therefore uses
 // IEEE round-to-nearest intrinsics in a fixed order (no contraction left to the compiler):
 //   vertex:   X = fma(M00, x, fma(M01, y, fma(M02, z, M03)))        (rows 1, 2 alike)
 //   project:  xs = fma(fx, X / Z, cx); xi = rint(xs * 256)           (8 sub-pixel bits)
 //   near cut: s = (near - a.z) / (b.z - a.z), a = lower vertex index; P = a + s (b - a)
 //   plane:    n = (v1 - v0) x (v2 - v0), d = n . v0 (camera frame, stored vertex order)
-//   inverse depth (affine in the image, like a GPU z-buffer value, Sec. IV):
+//   inverse depth (affine in the image, like a GPU z-buffer value, Sec. V):
 //             pinhole  w = fma(Ai, i + .5, fma(Bi, j + .5, Ci)), Ai = A / d, Bi = B / d,
 //                      Ci = C / d with A = nx/fx, B = ny/fy, C = fma(-A, cx, fma(-B, cy, nz));
 //             ray table w = fma(nx/d, rx, fma(ny/d, ry, (nz/d) rz))

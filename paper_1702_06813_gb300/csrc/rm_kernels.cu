@@ -8,11 +8,11 @@
 //                 to the screen-tile bins
 //   k_raster      one CTA per (pose, tile): bins staged into shared memory with bulk (TMA)
 //                 copies, integer edge functions with the top-left rule, 64-bit
-//                 depth|id z-test by shared-memory atomicMin (the z-buffer R(Y) of Sec. III);
-//                 then the fused epilogue: Table I per pixel (Sec. III.B), the truncated
+//                 depth|id z-test by shared-memory atomicMin (the z-buffer R(Y) of Sec. IV);
+//                 then the fused epilogue: Table I per pixel (Sec. IV.B), the truncated
 //                 least-squares residual, its pose Jacobian, and a fixed-order reduction;
 //                 in ICP mode instead the projective association of each pixel's map
-//                 surface with its scan return and the point-to-plane terms (Sec. IV)
+//                 surface with its scan return and the point-to-plane terms (Sec. V)
 //   k_reduce      per pose: fixed-order sum of the per-tile partials
 // k_lm_* and k_icp_* take the Levenberg-Marquardt and ICP steps between evaluations.
 // k_persist runs the same phases for a batch of problems (and LM iterations) in one launch.
@@ -902,7 +902,7 @@ struct RasterSmem {
   int redc[NW][6];
 };
 
-// Camera-frame normal at a pixel of triangle `id` from the map's vertex normals (Sec. IV,
+// Camera-frame normal at a pixel of triangle `id` from the map's vertex normals (Sec. V,
 // sequential alignment: the map's points rendered coloured by their normals): the hit t r on
 // the triangle's camera-frame plane, its barycentrics (as the visibility buffer's), the three
 // world-frame vertex normals blended by them as a rasteriser interpolates a vertex attribute,
@@ -1083,7 +1083,7 @@ __device__ __forceinline__ void raster_block(const WaveArgs &a, int tile, int q,
   const float ifx = 1.0f / a.cam.fx, ify = 1.0f / a.cam.fy;
   float l1 = 0.0f;  // ICP: sum |Z_M - Z_1| over the associated pixels
   if (MODE == kIcp) {
-    // ---- point-to-plane ICP epilogue (Sec. IV): projective association of the pixel's map
+    // ---- point-to-plane ICP epilogue (Sec. V): projective association of the pixel's map
     // surface with its scan return, residual e = (d - t)(n . r), J = (n, p x n), p = d r.
     // Counts field 0 holds the associations; eps is the association tolerance.
 #pragma unroll 1

@@ -1,4 +1,4 @@
-// rm_mesh.cu -- rm_meshify: the labelled interface mesh of one range image (Sec. III.A, Fig. 5).
+// rm_mesh.cu -- rm_meshify: the labelled interface mesh of one range image (Sec. IV.A, Fig. 5).
 //
 // Four kernels, all elementwise or per-block, in a fixed order so that the output is the same
 // run to run (row-major block order, no atomics):

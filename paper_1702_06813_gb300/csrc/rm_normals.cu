@@ -1,4 +1,4 @@
-// rm_normals.cu -- rm_depth_normals: surface normals of depth images (Eq. 2, Sec. IV).
+// rm_normals.cu -- rm_depth_normals: surface normals of depth images (Eq. 2, Sec. V).
 //
 // One CTA per (64x16 output tile, image), fused: the tile's depths with a halo of r + 1
 // pixels are staged in shared memory as (depth, validity) pairs (invalid pixels contribute

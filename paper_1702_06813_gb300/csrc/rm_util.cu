@@ -1,4 +1,4 @@
-// rm_util.cu -- input helpers: scan classes of raw range images (Sec. III.A, III.B) and poses
+// rm_util.cu -- input helpers: scan classes of raw range images (Sec. IV.A, IV.B) and poses
 // from the paper's X = (x, y, z, theta_x, theta_y, theta_z) (Eq. 1). Elementwise kernels.
 #include <cfloat>
 #include <cmath>

@@ -98,7 +98,7 @@ _DEFAULT_PARAMS = cost_params()
 
 
 class Map:
-    """A labelled triangle-mesh map (Sec. III.A) resident on the GPU."""
+    """A labelled triangle-mesh map (Sec. IV.A) resident on the GPU."""
 
     def __init__(self, vertices, faces, labels):
         v = np.ascontiguousarray(vertices.cpu().numpy() if isinstance(vertices, torch.Tensor) else vertices,
@@ -144,7 +144,7 @@ class Map:
         check(lib().rm_map_set_tuning(self.handle, ctypes.byref(t)))
 
     def set_vertex_normals(self, normals, pose=None):
-        """Per-vertex normals for the point-to-plane ICP (Sec. IV step 3), (V, 3) in the frame of
+        """Per-vertex normals for the point-to-plane ICP (Sec. V step 3), (V, 3) in the frame of
         `pose` (camera-to-world, 4x4), or world-frame when pose is None; None detaches them."""
         if normals is None:
             check(lib().rm_map_set_vertex_normals(self.handle, None, None, _stream()))
@@ -290,7 +290,7 @@ def align(m: Map, scan: Scan, init_pose, params=None, max_iters=50, lambda0=1e-3
 
 def blur_scan(scan: Scan, sigma=1.0) -> Scan:
     """The scan with its FO returns' depths Gaussian-smoothed (sigma pixels, over FO returns
-    only) and every other pixel unchanged: cost smoothing (Sec. III.C)."""
+    only) and every other pixel unchanged: cost smoothing (Sec. IV.C)."""
     intr = scan.intr
     out = torch.empty_like(scan.depth)
     ci = intr.c()
@@ -301,7 +301,7 @@ def blur_scan(scan: Scan, sigma=1.0) -> Scan:
 
 def sequential_icp(scans, first_pose, max_range, step=2, max_edge=0.1, tol=0.2, max_iters=20,
                    step_tol=1e-5, normals="face", sigma=1.0):
-    """Sequential depth-image alignment (Sec. IV): each scan, downsampled by `step` and meshed
+    """Sequential depth-image alignment (Sec. V): each scan, downsampled by `step` and meshed
     at its pose, becomes the map the next scan is aligned to by point-to-plane ICP, starting
     from the previous pose. normals="eq2" takes the point-to-plane normals from the previous
     scan's Eq. 2 normals (metric, Gaussian sigma in pixels, pinhole scans) at the mesh's grid
@@ -337,7 +337,7 @@ def dfo_params(nm_iters=60, cd_iters=60, nm_step=1.0, nm_tol=0.05, cd_step=0.25,
 
 
 def dfo_align(m: Map, scan: Scan, init_pose, params=None, dfo=None, gd_iters=0):
-    """The paper's hybrid derivative-free alignment on the Table I cost (Sec. III.C): optional
+    """The paper's hybrid derivative-free alignment on the Table I cost (Sec. IV.C): optional
     initial gradient steps (Levenberg-Marquardt on the surrogate), then Nelder-Mead and
     coordinate descent, all on the device. Returns (pose 4x4 float64 numpy, report)."""
     start = init_pose
@@ -363,7 +363,7 @@ def dfo_align(m: Map, scan: Scan, init_pose, params=None, dfo=None, gd_iters=0):
 
 def scan_from_range(intr: Intrinsics, rng, range_min, range_max) -> Scan:
     """A Scan from raw range images by the paper's rules: no reading -> FU at range_max,
-    NaN or closer than range_min -> dead (Sec. III.A, III.B)."""
+    NaN or closer than range_min -> dead (Sec. IV.A, IV.B)."""
     r = _dev_tensor(rng, torch.float32)
     d = torch.empty_like(r)
     c = torch.empty(r.shape, dtype=torch.uint8, device="cuda")
@@ -381,7 +381,7 @@ def pose_from_x(X):
 
 
 def icp_terms(m: Map, scan: Scan, poses, tol=0.1):
-    """Point-to-plane ICP terms with projective association (Sec. IV) for each pose:
+    """Point-to-plane ICP terms with projective association (Sec. V) for each pose:
     n_assoc (N,) int64, cost_l1 = C (N,), e2 (N,), jte (N,6) and jtj (N,21) float64."""
     p, n = _poses(poses)
     na = torch.empty(n, dtype=torch.int64, device="cuda")
@@ -435,7 +435,7 @@ def depth_normals(intr: Intrinsics, depth, cls, sigma=1.0, metric=False, want_sm
 
 
 def meshify(scan: Scan, pose, max_range, max_edge=0.1, step=1):
-    """Labelled interface mesh of a range image seen from `pose` (Sec. III.A): vertices
+    """Labelled interface mesh of a range image seen from `pose` (Sec. IV.A): vertices
     (Hs*Ws, 3) float32, faces (F, 3) int32 and labels (F,) uint8, on the device."""
     p, n = _poses(pose)
     if n != 1:

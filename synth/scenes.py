@@ -7,10 +7,10 @@ Conventions shared by every consumer of these arrays:
   spherical (panoramic) model, where azimuth 0 / elevation 0 is +z, azimuth grows toward
   +x and elevation grows toward -y.
 * A pose is a 4x4 float64 camera-to-world matrix T_wc (p_w = R p_c + t), row major.
-* Face labels (Sec. III.A, Fig. 3): 0 = free-occupied (FO), 1 = free-unknown (FU),
+* Face labels (Sec. IV.A, Fig. 3): 0 = free-occupied (FO), 1 = free-unknown (FU),
   2 = unknown-occupied (UO).
-* Scan pixel classes (Sec. III.B): 0 = FO (a return), 1 = FU (no return, drawn at the
-  sensor's maximum range as Sec. III.A prescribes), 2 = NaN (dead pixel).
+* Scan pixel classes (Sec. IV.B): 0 = FO (a return), 1 = FU (no return, drawn at the
+  sensor's maximum range as Sec. IV.A prescribes), 2 = NaN (dead pixel).
 
 All randomness comes from numpy's PCG64 seeded per call.
 """
@@ -329,7 +329,7 @@ def synth_scan(mesh: Mesh, cam: Camera, pose: np.ndarray, rng, sigma_abs=0.0, si
                dropout=0.0, dropout_as_nan=False):
     """Observed range image of the world from `pose`: (depth float32 HxW, class uint8 HxW).
 
-    No return beyond range_max, and dropped-out pixels, become FU at range_max (Sec. III.A);
+    No return beyond range_max, and dropped-out pixels, become FU at range_max (Sec. IV.A);
     returns closer than range_min are dead pixels (NaN)."""
     rays = cam.rays()
     dirs = rays @ pose[:3, :3].T

@@ -37,7 +37,7 @@ def config2(seed=2000, target_fo=400_000, target_fu=100_000):
 
 def scan_from_render(depth32, cam, ids=None, labels=None):
     """Noise-free observed scan from a z-buffer depth image (FO where the hit is within range,
-    FU at range_max otherwise), as Sec. III.A draws no-return pixels."""
+    FU at range_max otherwise), as Sec. IV.A draws no-return pixels."""
     d = np.array(depth32, np.float32, copy=True)
     cls = np.zeros(d.shape, np.uint8)
     miss = ~(d <= cam.range_max)

@@ -1,4 +1,4 @@
-"""Derivative-free alignment on the Table I cost (Sec. III.C) on the GPU vs the CPU oracle,
+"""Derivative-free alignment on the Table I cost (Sec. IV.C) on the GPU vs the CPU oracle,
 through the C ABI.
 
 Table I counts are bit-exact between the two sides and both take the search's decisions on

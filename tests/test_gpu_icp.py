@@ -1,4 +1,4 @@
-"""Render-accelerated point-to-plane ICP (Sec. IV) on the GPU vs the CPU oracle, through the
+"""Render-accelerated point-to-plane ICP (Sec. V) on the GPU vs the CPU oracle, through the
 C ABI.
 
 The association (which pixels pair up) is decided in FP32 on both sides from the same z-buffer

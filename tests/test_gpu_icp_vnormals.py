@@ -1,4 +1,4 @@
-"""Point-to-plane ICP with the map's points coloured by their normals (Sec. IV, sequential
+"""Point-to-plane ICP with the map's points coloured by their normals (Sec. V, sequential
 depth-image alignment steps 2-3) on the GPU vs the CPU oracle, through the C ABI.
 
 With vertex normals attached (rm_map_set_vertex_normals), the normal of an associated pixel is
@@ -144,7 +144,7 @@ def test_vertex_normal_alignment_matches_oracle(room):
 
 
 def test_eq2_pipeline_step_matches_oracle():
-    """One step of Sec. IV's loop with Eq. 2 normals: scan A meshed at its pose (downsampled
+    """One step of Sec. V's loop with Eq. 2 normals: scan A meshed at its pose (downsampled
     by 2), its metric Eq. 2 normals at the mesh's grid pixels as vertex normals, and scan B
     aligned to that map by ICP, on the GPU and on the oracle."""
     c = cases.config1(seed=1810)

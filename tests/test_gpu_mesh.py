@@ -1,5 +1,5 @@
-"""Meshification of range images (Sec. III.A) on the GPU vs the CPU oracle, and scan-to-scan
-alignment against the mesh of a previous scan (Sec. IV), through the C ABI.
+"""Meshification of range images (Sec. IV.A) on the GPU vs the CPU oracle, and scan-to-scan
+alignment against the mesh of a previous scan (Sec. V), through the C ABI.
 
 Vertices, faces and labels must match the oracle bit for bit (the label decision is taken in
 FP32 with the same operation order on both sides; the world transform in FP64, rounded once).
@@ -153,7 +153,7 @@ def test_scan_to_scan_alignment():
 
 
 def test_sequential_depth_image_alignment():
-    """Sec. IV's loop over a short trajectory: each scan meshed (downsampled by 2) at its
+    """Sec. V's loop over a short trajectory: each scan meshed (downsampled by 2) at its
     estimated pose is the map for the next scan's ICP. Frames 1-3 move 4 cm / 1.5 deg each;
     the chained estimates stay within a few millimetres of the truth."""
     c = cases.config1(seed=1800)

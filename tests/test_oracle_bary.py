@@ -1,4 +1,4 @@
-"""Pins for the oracle's visibility-buffer barycentrics (Sec. III z-buffer; the per-pixel
+"""Pins for the oracle's visibility-buffer barycentrics (Sec. IV z-buffer; the per-pixel
 triangle id plus barycentrics of the visibility buffer).
 
 orc_barycentrics returns, per covered pixel, (b1, b2) such that the pixel's ray meets the

@@ -1,4 +1,4 @@
-"""Pins of the oracle's derivative-free search (Nelder-Mead, then coordinate descent; Sec. III.C),
+"""Pins of the oracle's derivative-free search (Nelder-Mead, then coordinate descent; Sec. IV.C),
 no GPU needed.
 
 The search is pinned on functions with known minima (a convex quadratic, an integer staircase

@@ -1,4 +1,4 @@
-"""Pins of the oracle's input helpers: scan classes from a raw range image (Sec. III.A, III.B;
+"""Pins of the oracle's input helpers: scan classes from a raw range image (Sec. IV.A, IV.B;
 the reading rules in tests/golden/scan_classes.txt) and the pose of the paper's X (Eq. 1, read
 as R = Rz Ry Rx), no GPU needed."""
 from __future__ import annotations

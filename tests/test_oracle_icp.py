@@ -1,4 +1,4 @@
-"""Pins of the oracle's render-accelerated point-to-plane ICP (Sec. IV) to things other than
+"""Pins of the oracle's render-accelerated point-to-plane ICP (Sec. V) to things other than
 itself (no GPU needed).
 
 The association is projective: the map surface rendered at a pixel and the scan return of the

@@ -1,5 +1,5 @@
 """Pins of the oracle's point-to-plane ICP with the map's points coloured by their normals
-(Sec. IV, sequential depth-image alignment, steps 2-3), no GPU needed.
+(Sec. V, sequential depth-image alignment, steps 2-3), no GPU needed.
 
 With vertex normals attached, the normal used at an associated pixel is the blend of the seen
 triangle's three vertex normals by the hit's barycentrics (a rasteriser interpolating a vertex

@@ -1,4 +1,4 @@
-"""Pins of the oracle's meshification of a range image (Sec. III.A, Fig. 5), no GPU needed.
+"""Pins of the oracle's meshification of a range image (Sec. IV.A, Fig. 5), no GPU needed.
 
 Closed forms: the vertices of a wall seen head-on, the labels that the edge threshold and the
 no-return rule give, the faces that dead pixels remove, the downsampled grid; and an invariant:

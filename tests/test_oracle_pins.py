@@ -24,7 +24,7 @@ VALUE_OF_OUTCOME = {-1: 0, 0: -1, 1: +1, 2: -1, 3: +1, 4: -1, 5: +1}
 
 
 # ---------------------------------------------------------------------------------------
-# Table I (Sec. III.B)
+# Table I (Sec. IV.B)
 # ---------------------------------------------------------------------------------------
 
 def _table1_rows():
