@@ -908,7 +908,7 @@ struct RasterSmem {
 // world-frame vertex normals blended by them as a rasteriser interpolates a vertex attribute,
 // and the blend rotated into the camera frame (unnormalised). False when the blend is not
 // finite: a vertex without a normal (NaN) leaves the pixel unassociated.
-__device__ __noinline__ bool vertex_normal(const WaveArgs &a, const float *M, unsigned id, float t,
+__device__ __forceinline__ bool vertex_normal(const WaveArgs &a, const float *M, unsigned id, float t,
                                            float rx, float ry, float rz, float &nx, float &ny,
                                            float &nz) {
   const int4 f = a.faces[id];
@@ -1082,7 +1082,7 @@ __device__ __forceinline__ void raster_block(const WaveArgs &a, int tile, int q,
   const float eps = a.prm.eps;
   const float ifx = 1.0f / a.cam.fx, ify = 1.0f / a.cam.fy;
   float l1 = 0.0f;  // ICP: sum |Z_M - Z_1| over the associated pixels
-  if (MODE == kIcp) {
+  if (is_icp(MODE)) {
     // ---- point-to-plane ICP epilogue (Sec. V): projective association of the pixel's map
     // surface with its scan return, residual e = (d - t)(n . r), J = (n, p x n), p = d r.
     // Counts field 0 holds the associations; eps is the association tolerance.
@@ -1112,7 +1112,7 @@ __device__ __forceinline__ void raster_block(const WaveArgs &a, int tile, int q,
         rz = rr[2];
       }
       float nx, ny, nz;
-      if (a.vnormals) {
+      if (MODE == kIcpVn) {
         if (!vertex_normal(a, sm.M, (unsigned)key, t, rx, ry, rz, nx, ny, nz)) continue;
       } else {
         nx = R[0] * pl.x + R[1] * pl.y + R[2] * pl.z;
@@ -1244,14 +1244,14 @@ __device__ __forceinline__ void raster_block(const WaveArgs &a, int tile, int q,
     const unsigned c = __reduce_add_sync(0xffffffffu, (cnt6 >> (5 * k)) & 31u);
     if (lane == 0) redc[warp][k] = (int)c;
   }
-  if (MODE == kIcp) {
+  if (is_icp(MODE)) {
     // the warp's C in counts field 1 (unused by ICP), as FP32 bits
 #pragma unroll
     for (int off = 16; off >= 1; off >>= 1) l1 += __shfl_xor_sync(0xffffffffu, l1, off);
     if (lane == 0) redc[warp][1] = __float_as_int(l1);
   }
   __syncthreads();
-  if (MODE == kIcp && tid == 1) {
+  if (is_icp(MODE) && tid == 1) {
     float f = 0.0f;
 #pragma unroll
     for (int w = 0; w < kThreads / 32; ++w) f = __fadd_rn(f, __int_as_float(redc[w][1]));
@@ -1314,6 +1314,7 @@ static cudaError_t launch_raster_m(const WaveArgs &a, int mode, cudaStream_t s) 
   dim3 grid(a.tg.ntiles, a.n_poses);
   if (mode == kRender) k_raster<TW, TH, kRender, MODEL><<<grid, kThreads, 0, s>>>(a);
   else if (mode == kCost) k_raster<TW, TH, kCost, MODEL><<<grid, kThreads, 0, s>>>(a);
+  else if (mode == kIcp && a.vnormals) k_raster<TW, TH, kIcpVn, MODEL><<<grid, kThreads, 0, s>>>(a);
   else if (mode == kIcp) k_raster<TW, TH, kIcp, MODEL><<<grid, kThreads, 0, s>>>(a);
   else k_raster<TW, TH, kCostGrad, MODEL><<<grid, kThreads, 0, s>>>(a);
   return cudaGetLastError();
@@ -1341,9 +1342,11 @@ cudaError_t launch_wave(const WaveArgs &a, int mode, cudaStream_t s, cudaEvent_t
   }
   if (ev && (e = cudaEventRecord(ev[1], s)) != cudaSuccess) return e;
   if (a.n_clusters > 0) {
-    // up to 96 CTAs per pose; waves of few poses (single-pose alignment) get up to about six
-    // CTAs per SM in total so that their setup spreads over the GPU
-    const int per_pose = max(96, (kSetupCtasPerGpu + a.n_poses - 1) / a.n_poses);
+    // 16 CTAs per pose in a large wave: each warp then sets up several clusters, and the next
+    // wave's setup (on the other stream) takes few enough SMs to run beside this wave's
+    // raster; waves of few poses (single-pose alignment) get up to about six CTAs per SM in
+    // total so that their setup spreads over the GPU
+    const int per_pose = max(16, (kSetupCtasPerGpu + a.n_poses - 1) / a.n_poses);
     const int blocks = min(max(a.n_clusters / 64, 1), per_pose);
     dim3 gs(blocks, a.n_poses);
     if (a.cam.model == 0) k_setup<0><<<gs, 256, 0, s>>>(a);
@@ -1904,7 +1907,8 @@ __global__ void k_lm_init_batch(LMState *st, const double *T0, int n, LMArgs a, 
 
 // Phase bodies of the persistent kernel, each compiled out of line so that its register
 // allocation is its own (as in the per-phase kernels) rather than the union of all phases.
-__device__ __noinline__ void persist_cull(const WaveArgs &a, int item, float *sM) {
+__device__ __noinline__ void persist_cull(const WaveArgs *__restrict__ pa, int item, float *sM) {
+  const WaveArgs &a = *pa;
   const int c1 = min((item + 1) * kPersistCull, (a.n_clusters + 255) / 256);
   for (int c = item * kPersistCull; c < c1; ++c) {
     cull_block(a, 0, c, sM);
@@ -1913,14 +1917,16 @@ __device__ __noinline__ void persist_cull(const WaveArgs &a, int item, float *sM
 }
 
 template <int MODEL>
-__device__ __noinline__ void persist_setup(const WaveArgs &a, int worker, int nworkers,
+__device__ __noinline__ void persist_setup(const WaveArgs *__restrict__ pa, int worker, int nworkers,
                                            SetupSmem &sm) {
+  const WaveArgs &a = *pa;
   setup_block<MODEL>(a, 0, worker, nworkers, sm);
 }
 
 template <int MODEL>
 __device__ __noinline__ void persist_raster(
-    const WaveArgs &a, int item, RasterSmem<kPersistTileW[MODEL] * kPersistTileH[MODEL], MODEL> &sm) {
+    const WaveArgs *__restrict__ pa, int item, RasterSmem<kPersistTileW[MODEL] * kPersistTileH[MODEL], MODEL> &sm) {
+  const WaveArgs &a = *pa;
   const int t1 = min((item + 1) * kPersistTiles[MODEL], a.tg.ntiles);
   for (int t = item * kPersistTiles[MODEL]; t < t1; ++t) {
     raster_block<kPersistTileW[MODEL], kPersistTileH[MODEL], kCostGrad, MODEL>(a, t, 0, sm);
@@ -1930,15 +1936,18 @@ __device__ __noinline__ void persist_raster(
 
 template <int MODEL>
 __device__ __noinline__ void persist_raster_icp(
-    const WaveArgs &a, int item, RasterSmem<kPersistTileW[MODEL] * kPersistTileH[MODEL], MODEL> &sm) {
+    const WaveArgs *__restrict__ pa, int item, RasterSmem<kPersistTileW[MODEL] * kPersistTileH[MODEL], MODEL> &sm) {
+  const WaveArgs &a = *pa;
   const int t1 = min((item + 1) * kPersistTiles[MODEL], a.tg.ntiles);
   for (int t = item * kPersistTiles[MODEL]; t < t1; ++t) {
-    raster_block<kPersistTileW[MODEL], kPersistTileH[MODEL], kIcp, MODEL>(a, t, 0, sm);
+    if (a.vnormals) raster_block<kPersistTileW[MODEL], kPersistTileH[MODEL], kIcpVn, MODEL>(a, t, 0, sm);
+    else raster_block<kPersistTileW[MODEL], kPersistTileH[MODEL], kIcp, MODEL>(a, t, 0, sm);
     __syncthreads();
   }
 }
 
-__device__ __noinline__ void persist_reduce(const WaveArgs &a, double *vals) {
+__device__ __noinline__ void persist_reduce(const WaveArgs *__restrict__ pa, double *vals) {
+  const WaveArgs &a = *pa;
   reduce_block(a, 0, vals);
 }
 
@@ -1976,11 +1985,9 @@ __global__ void __launch_bounds__(kThreads, RM_PERSIST_MIN_BLOCKS) k_persist(Bat
   };
   __shared__ PersistSmem u;
   __shared__ float s_M[12];
-  __shared__ WaveArgs s_args;  // the current item's problem, copied once per problem
   __shared__ int4 s_item;
   __shared__ int4 s_enq;       // successors to publish: phase, count, first slot, evaluation
   __shared__ int s_abort;
-  int loaded = -1;  // the problem whose arguments s_args holds
   for (;;) {
     if (threadIdx.x == 0) {
       int4 item = make_int4(-1, 0, 0, 0);
@@ -2031,32 +2038,28 @@ __global__ void __launch_bounds__(kThreads, RM_PERSIST_MIN_BLOCKS) k_persist(Bat
     __syncthreads();
     const int4 item = s_item;
     if (item.x < 0 || s_abort) break;
-    if (item.x != loaded) {  // consecutive items of one problem keep its arguments
-      const int *src = reinterpret_cast<const int *>(b.probs + item.x);
-      int *dst = reinterpret_cast<int *>(&s_args);
-      for (int k = threadIdx.x; k < (int)(sizeof(WaveArgs) / 4); k += blockDim.x) dst[k] = src[k];
-      loaded = item.x;
-      __syncthreads();
-    }
-    const WaveArgs &a = s_args;
+    // the problem's argument block: written before the launch and read-only during it, so
+    // the phases read it in place through the read-only data path
+    const WaveArgs *__restrict__ pa = b.probs + item.x;
+    const WaveArgs &a = *pa;
     const bool skip = skipped(a);
     if (!skip) {
       switch (item.y) {
-        case 0: persist_cull(a, item.z, s_M); break;
+        case 0: persist_cull(pa, item.z, s_M); break;
         case 1:
-          if (a.cam.model == 0) persist_setup<0>(a, item.z, __ldcg(b.need + 3 * item.x + 1), u.su);
-          else persist_setup<1>(a, item.z, __ldcg(b.need + 3 * item.x + 1), u.su);
+          if (a.cam.model == 0) persist_setup<0>(pa, item.z, __ldcg(b.need + 3 * item.x + 1), u.su);
+          else persist_setup<1>(pa, item.z, __ldcg(b.need + 3 * item.x + 1), u.su);
           break;
         case 2:
           if (b.icp) {
-            if (a.cam.model == 0) persist_raster_icp<0>(a, item.z, u.r0);
-            else persist_raster_icp<1>(a, item.z, u.r1);
+            if (a.cam.model == 0) persist_raster_icp<0>(pa, item.z, u.r0);
+            else persist_raster_icp<1>(pa, item.z, u.r1);
           } else {
-            if (a.cam.model == 0) persist_raster<0>(a, item.z, u.r0);
-            else persist_raster<1>(a, item.z, u.r1);
+            if (a.cam.model == 0) persist_raster<0>(pa, item.z, u.r0);
+            else persist_raster<1>(pa, item.z, u.r1);
           }
           break;
-        default: persist_reduce(a, u.vals); break;
+        default: persist_reduce(pa, u.vals); break;
       }
     }
     if (item.y == 3 && b.icp) {

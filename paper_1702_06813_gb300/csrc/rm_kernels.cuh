@@ -62,7 +62,10 @@ struct WaveArgs {
   float *bary;
 };
 
-enum Mode { kRender = 0, kCost = 1, kCostGrad = 2, kIcp = 3 };
+// kIcpVn: the ICP epilogue with the map's per-vertex normals; the raster launch picks it in
+// place of kIcp when the map carries vertex normals, so the face-normal form keeps its code.
+enum Mode { kRender = 0, kCost = 1, kCostGrad = 2, kIcp = 3, kIcpVn = 4 };
+__host__ __device__ constexpr bool is_icp(int mode) { return mode == kIcp || mode == kIcpVn; }
 
 cudaError_t launch_pose_to_m(const double *poses, int n, double cx, double cy, double cz,
                              float *Ms, cudaStream_t s);
