@@ -639,7 +639,7 @@ def run_icp(a):
                    "wave_poses": min(n, 128), "l2": "flushed between timed steps (256 MiB write)",
                    "kernel_share": share, "e2e_matches_device": ok,
                    "align_room_1M_640x480": room_align, "align_lidar_2M_1024x64": lidar_align,
-                   "depth_normals_eq2": normals_line, "meshify_sec3a": mesh_line,
+                   "depth_normals_eq2": normals_line, "meshify_sec4a": mesh_line,
                    "dfo_align_table1_room": dfo_line, "vertex_grad": vgrad_line, "cost_sweep_fig7": sweep_line,
                    "step_hbm_roofline_frac": step_algorithmic_bytes(mesh.n_verts, mesh.n_tris, P, n, min(n, 128))
                    * a.steps / (ms * 1e-3) / 1e9 / pk["hbm_gbs"]},

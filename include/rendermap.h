@@ -468,9 +468,9 @@ rm_status rm_icp_align_batch(rm_map *map, const rm_problem *problems, int32_t n,
  *  - out: DEVICE pointers of that device (any may be NULL), one pose's values as for
  *    rm_cost_grad.
  * The call waits for `stream` to read its status. The first call on each device looks up
- * the array's device address (cudaGetSymbolAddress, with that device current); make that
- * first call before any stream capture. Every call shares the one array and leaves its
- * contents behind; the call clears what must start at zero. Calls whose GPU work overlaps
+ * the array's device address (cudaGetSymbolAddress, with that device current). Every call
+ * shares the one array and leaves its contents behind; the call clears what must start at
+ * zero. Calls whose GPU work overlaps
  * (other streams, unordered threads) race on the array and give wrong results.
  * Errors: RM_EINVAL when the map, the scan or an output is not on the current device (host
  * scan/output pointers included), or when the cluster list and tile arrays

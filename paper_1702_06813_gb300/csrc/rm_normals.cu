@@ -1,15 +1,15 @@
 // rm_normals.cu -- rm_depth_normals: surface normals of depth images (Eq. 2, Sec. V).
 //
 // One CTA per (64x16 output tile, image), fused: the tile's depths with a halo of r + 1
-// pixels are staged in shared memory as (depth, validity) pairs (invalid pixels contribute
-// neither), smoothed with the separable Gaussian as a normalised convolution (a horizontal
-// pass of weighted sums and weight sums, four outputs per thread sliding along a row, then a
-// vertical pass, six per thread down a column; one instantiation per radius, so the taps
-// unroll with their weights in registers), and the smoothed depth S over the tile plus a
-// one-pixel ring feeds
-// the central differences and the normal N = a x b with a = (0, s_y, dz/dy) and
-// b = (s_x, 0, dz/dx). Each depth and class byte is read once from HBM and each normal
-// written once (17 bytes per pixel); the kernel is bound by HBM bandwidth.
+// pixels are staged in shared memory as depths and validity weights (invalid pixels
+// contribute neither), smoothed with the separable Gaussian as a normalised convolution (a
+// horizontal pass of weighted sums and weight sums, four outputs per thread sliding along a
+// row, then a vertical pass, six per thread down a column; one instantiation per radius, so
+// the taps unroll with their weights in registers), and the smoothed depth S over the tile
+// plus a one-pixel ring feeds the central differences and the normal N = a x b with
+// a = (0, s_y, dz/dy) and b = (s_x, 0, dz/dx). Each depth and class byte is read once from HBM
+// and each normal written once (17 bytes per pixel); the convolution's instructions and
+// shared-memory traffic, not HBM, set the kernel's time.
 #include <cfloat>
 #include <cmath>
 #include <string>
@@ -39,28 +39,31 @@ struct NormalArgs {
   float g[kMaxR + 1];
 };
 
-// Dynamic shared memory: the staged (depth, validity) pairs of the tile plus its halo, the
-// horizontal sums (weighted depth, weight) of each staged row over the smoothed columns, and
-// the smoothed depth S of the tile plus a one-pixel ring. The two float2 tables are read down
-// their columns by consecutive threads, so their row strides are padded to 1 mod 16 float2:
-// consecutive rows then start two banks apart and a warp's 8-byte reads take two wavefronts.
-__host__ __device__ constexpr int pad16p1(int n) { return n + ((17 - n % 16) % 16); }
+// Dynamic shared memory, all FP32 tables: the staged depths (0 where invalid) and validity
+// weights (1 or 0) of the tile plus its halo, the horizontal sums of each staged row over the
+// smoothed columns (weighted depths, weights), and the smoothed depth S of the tile plus a
+// one-pixel ring. The horizontal pass reads and writes the tables down their columns with
+// consecutive threads on consecutive rows, so every row stride is odd: 32 consecutive rows
+// then fall in 32 distinct banks and a warp's 4-byte access takes one wavefront.
+__host__ __device__ constexpr int odd_stride(int n) { return n | 1; }
 __host__ __device__ inline int staged_w(int r) { return kSW + 2 * r; }
 __host__ __device__ inline int staged_h(int r) { return kSH + 2 * r; }
-__host__ __device__ inline int staged_stride(int r) { return pad16p1(staged_w(r)); }
-constexpr int kSWP = pad16p1(kSW);  // row stride of the horizontal sums
+__host__ __device__ inline int staged_stride(int r) { return odd_stride(staged_w(r)); }
+constexpr int kSWP = odd_stride(kSW);  // row stride of the horizontal sums
 inline size_t normals_smem(int r) {
-  return sizeof(float2) * ((size_t)staged_h(r) * staged_stride(r) + (size_t)staged_h(r) * kSWP) +
-         sizeof(float) * kSH * kSW;
+  return sizeof(float) * (2 * (size_t)staged_h(r) * staged_stride(r) + 2 * (size_t)staged_h(r) * kSWP +
+                          (size_t)kSH * kSW);
 }
 
 template <int R>
 __global__ void __launch_bounds__(kThreadsN) k_depth_normals(NormalArgs a) {
   extern __shared__ float4 smem_raw[];
-  constexpr int dw = kSW + 2 * R, dh = kSH + 2 * R, dws = pad16p1(dw);
-  float2 *sz = reinterpret_cast<float2 *>(smem_raw);   // [dh][dws]: (valid ? z : 0, valid)
-  float2 *sh = sz + dh * dws;                           // [dh][kSWP]
-  float *sS = reinterpret_cast<float *>(sh + dh * kSWP); // [kSH][kSW]
+  constexpr int dw = kSW + 2 * R, dh = kSH + 2 * R, dws = odd_stride(dw);
+  float *zv = reinterpret_cast<float *>(smem_raw);  // [dh][dws]: valid ? z : 0
+  float *zw = zv + dh * dws;                          // [dh][dws]: valid ? 1 : 0
+  float *hn = zw + dh * dws;                          // [dh][kSWP]: horizontal sums of zv
+  float *hd = hn + dh * kSWP;                         // [dh][kSWP]: horizontal sums of zw
+  float *sS = hd + dh * kSWP;                         // [kSH][kSW]
   const int tid = threadIdx.x;
   float g[R + 1];
 #pragma unroll
@@ -68,7 +71,7 @@ __global__ void __launch_bounds__(kThreadsN) k_depth_normals(NormalArgs a) {
   const int img = blockIdx.y;
   const int ntx = (a.W + kTW - 1) / kTW;
   const int ox = (blockIdx.x % ntx) * kTW, oy = (blockIdx.x / ntx) * kTH;
-  const int x0 = ox - 1 - R, y0 = oy - 1 - R;  // image coordinates of sz[0][0]
+  const int x0 = ox - 1 - R, y0 = oy - 1 - R;  // image coordinates of zv[0][0]
   const long long P = (long long)a.W * a.H;
   const float *dimg = a.depth + img * P;
   const uint8_t *cimg = a.cls + img * P;
@@ -99,7 +102,9 @@ __global__ void __launch_bounds__(kThreadsN) k_depth_normals(NormalArgs a) {
       if (k < n_st) {
         const bool ok = cv[m] == 0 && fabsf(dv[m]) <= FLT_MAX;
         mine_valid = mine_valid && ok;
-        sz[(k / dw) * dws + k % dw] = ok ? make_float2(dv[m], 1.0f) : make_float2(0.0f, 0.0f);
+        const int at = (k / dw) * dws + k % dw;
+        zv[at] = ok ? dv[m] : 0.0f;
+        zw[at] = ok ? 1.0f : 0.0f;
       }
     }
   }
@@ -115,11 +120,12 @@ __global__ void __launch_bounds__(kThreadsN) k_depth_normals(NormalArgs a) {
       float num[kHG], den[kHG];
 #pragma unroll
       for (int j = 0; j < kHG; ++j) num[j] = den[j] = 0.0f;
-      const float2 *row = sz + v * dws + u0;  // output u0 + j: staged columns u0 + j .. + 2R
+      const float *row = zv + v * dws + u0;  // output u0 + j: staged columns u0 + j .. + 2R
+      const float *roww = zw + v * dws + u0;
       if (all_valid) {
 #pragma unroll
         for (int t = 0; t < 2 * R + kHG; ++t) {
-          const float z = (u0 + t < dw) ? row[t].x : 0.0f;
+          const float z = (u0 + t < dw) ? row[t] : 0.0f;
 #pragma unroll
           for (int j = 0; j < kHG; ++j) {
             const int d = t - j;
@@ -129,21 +135,25 @@ __global__ void __launch_bounds__(kThreadsN) k_depth_normals(NormalArgs a) {
       } else {
 #pragma unroll
         for (int t = 0; t < 2 * R + kHG; ++t) {
-          const float2 zv = (u0 + t < dw) ? row[t] : make_float2(0.0f, 0.0f);
+          const bool in = u0 + t < dw;
+          const float z = in ? row[t] : 0.0f, zok = in ? roww[t] : 0.0f;
 #pragma unroll
           for (int j = 0; j < kHG; ++j) {
             const int d = t - j;
             if (d >= 0 && d <= 2 * R) {
               const float w = g[d < R ? R - d : d - R];
-              num[j] = fmaf(w, zv.x, num[j]);
-              den[j] = fmaf(w, zv.y, den[j]);
+              num[j] = fmaf(w, z, num[j]);
+              den[j] = fmaf(w, zok, den[j]);
             }
           }
         }
       }
 #pragma unroll
       for (int j = 0; j < kHG; ++j)
-        if (u0 + j < kSW) sh[v * kSWP + u0 + j] = make_float2(num[j], den[j]);
+        if (u0 + j < kSW) {
+          hn[v * kSWP + u0 + j] = num[j];
+          hd[v * kSWP + u0 + j] = den[j];
+        }
     }
   }
   __syncthreads();
@@ -158,7 +168,7 @@ __global__ void __launch_bounds__(kThreadsN) k_depth_normals(NormalArgs a) {
       if (all_valid) {
 #pragma unroll
         for (int t = 0; t < 2 * R + kVG; ++t) {
-          const float h = (v0 + t < dh) ? sh[(v0 + t) * kSWP + u].x : 0.0f;
+          const float h = (v0 + t < dh) ? hn[(v0 + t) * kSWP + u] : 0.0f;
 #pragma unroll
           for (int j = 0; j < kVG; ++j) {
             const int d = t - j;
@@ -171,14 +181,15 @@ __global__ void __launch_bounds__(kThreadsN) k_depth_normals(NormalArgs a) {
       } else {
 #pragma unroll
         for (int t = 0; t < 2 * R + kVG; ++t) {
-          const float2 hv = (v0 + t < dh) ? sh[(v0 + t) * kSWP + u] : make_float2(0.0f, 0.0f);
+          const bool in = v0 + t < dh;
+          const float hz = in ? hn[(v0 + t) * kSWP + u] : 0.0f, hw = in ? hd[(v0 + t) * kSWP + u] : 0.0f;
 #pragma unroll
           for (int j = 0; j < kVG; ++j) {
             const int d = t - j;
             if (d >= 0 && d <= 2 * R) {
               const float w = g[d < R ? R - d : d - R];
-              num[j] = fmaf(w, hv.x, num[j]);
-              den[j] = fmaf(w, hv.y, den[j]);
+              num[j] = fmaf(w, hz, num[j]);
+              den[j] = fmaf(w, hw, den[j]);
             }
           }
         }
@@ -186,7 +197,7 @@ __global__ void __launch_bounds__(kThreadsN) k_depth_normals(NormalArgs a) {
         for (int j = 0; j < kVG; ++j) {
           const int v = v0 + j;
           if (v < kSH) {
-            const bool centre = sz[(v + R) * dws + (u + R)].y != 0.0f;
+            const bool centre = zw[(v + R) * dws + (u + R)] != 0.0f;
             sS[v * kSW + u] = centre ? num[j] / den[j] : __int_as_float(0x7fc00000);
           }
         }
