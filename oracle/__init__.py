@@ -102,12 +102,14 @@ class _LMReport(ctypes.Structure):
 class _DfoParams(ctypes.Structure):
     _fields_ = [("nm_iters", ctypes.c_int32), ("cd_iters", ctypes.c_int32), ("nm_step", ctypes.c_double),
                 ("nm_tol", ctypes.c_double), ("cd_step", ctypes.c_double), ("cd_tol", ctypes.c_double),
-                ("scale_t", ctypes.c_double), ("scale_r", ctypes.c_double)]
+                ("scale_t", ctypes.c_double), ("scale_r", ctypes.c_double), ("method", ctypes.c_int32),
+                ("powell_iters", ctypes.c_int32), ("powell_step", ctypes.c_double),
+                ("powell_tol", ctypes.c_double)]
 
 
 class _DfoReport(ctypes.Structure):
     _fields_ = [("evals", ctypes.c_int32), ("nm_iters", ctypes.c_int32), ("nm_shrinks", ctypes.c_int32),
-                ("cd_iters", ctypes.c_int32), ("converged", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+                ("cd_iters", ctypes.c_int32), ("converged", ctypes.c_int32), ("powell_iters", ctypes.c_int32)]
 
 
 _BATCH_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
@@ -115,8 +117,12 @@ _BATCH_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes
 
 
 def dfo_params(nm_iters=60, cd_iters=60, nm_step=1.0, nm_tol=0.05, cd_step=0.25, cd_tol=0.01,
-               scale_t=0.05, scale_r=0.0349):
-    return _DfoParams(nm_iters, cd_iters, nm_step, nm_tol, cd_step, cd_tol, scale_t, scale_r)
+               scale_t=0.05, scale_r=0.0349, method="nm", powell_iters=30, powell_step=1.0,
+               powell_tol=0.05):
+    """method: "nm" (Nelder-Mead) or "powell" (Powell's method), then coordinate descent."""
+    m = {"nm": 0, "powell": 1}[method]
+    return _DfoParams(nm_iters, cd_iters, nm_step, nm_tol, cd_step, cd_tol, scale_t, scale_r, m,
+                      powell_iters, powell_step, powell_tol)
 
 
 def dfo_minimise(f, scale, params=None):
@@ -138,7 +144,7 @@ def dfo_minimise(f, scale, params=None):
                             ctypes.byref(rep))
     if st != 0:
         raise RuntimeError("orc_dfo_core failed")
-    return x, fb.value, {f_: getattr(rep, f_) for f_, _ in _DfoReport._fields_ if f_ != "pad_"}
+    return x, fb.value, {f_: getattr(rep, f_) for f_, _ in _DfoReport._fields_}
 
 
 _lib = None
@@ -453,7 +459,8 @@ class OracleMap:
         return r
 
     def dfo_align(self, pose0, cam, scan_depth, scan_class, params=None, dfo=None):
-        """Nelder-Mead then coordinate descent on the Table I cost (Sec. IV.C)."""
+        """Nelder-Mead (or Powell's method) then coordinate descent on the Table I cost
+        (Sec. IV.C)."""
         c, keep = make_cam(cam)
         prm = params or make_params()
         d = dfo or dfo_params()
@@ -468,7 +475,7 @@ class OracleMap:
         del keep
         if st != 0:
             raise RuntimeError("orc_dfo_align failed")
-        r = {f_: getattr(rep, f_) for f_, _ in _DfoReport._fields_ if f_ != "pad_"}
+        r = {f_: getattr(rep, f_) for f_, _ in _DfoReport._fields_}
         r["e_table"] = et.value
         return out.reshape(4, 4), r
 

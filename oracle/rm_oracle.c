@@ -1162,71 +1162,149 @@ static void nm_order(const double f[7], int ord[7]) {
     }
 }
 
+/* Powell's line search: the 12 points x + (a s) d in the order of kPowellA, one batch; x and
+ * *f move to the lowest if it is below *f. *drop = how much the value fell (0: no move). */
+static const double kPowellA[12] = {0.25, -0.25, 0.5, -0.5, 1.0, -1.0, 2.0, -2.0, 4.0, -4.0, 8.0, -8.0};
+
+static int powell_line(orc_batch_fn fn, void *ctx, double x[6], double *f, const double d[6],
+                       double s, int *evals, double *drop) {
+  double cand[12][6], fc[12];
+  for (int m = 0; m < 12; ++m) {
+    const double a = kPowellA[m] * s;
+    for (int k = 0; k < 6; ++k) {
+      const double step = a * d[k];
+      cand[m][k] = x[k] + step;
+    }
+  }
+  if (fn(ctx, 12, &cand[0][0], fc)) return -1;
+  *evals += 12;
+  int best = 0;
+  for (int m = 1; m < 12; ++m)
+    if (fc[m] < fc[best]) best = m;
+  *drop = 0.0;
+  if (fc[best] < *f) {
+    *drop = *f - fc[best];
+    for (int k = 0; k < 6; ++k) x[k] = cand[best][k];
+    *f = fc[best];
+  }
+  return 0;
+}
+
+/* Powell's conjugate-direction search from the origin (see the header); x, *f: its end. */
+static int powell_search(orc_batch_fn fn, void *ctx, const double scale[6], const orc_dfo_params *p,
+                         double x[6], double *f, int *evals, int *iters) {
+  double D[6][6];
+  for (int i = 0; i < 6; ++i)
+    for (int k = 0; k < 6; ++k) D[i][k] = i == k ? scale[k] : 0.0;
+  for (int k = 0; k < 6; ++k) x[k] = 0.0;
+  if (fn(ctx, 1, x, f)) return -1;
+  *evals += 1;
+  double s = p->powell_step;
+  *iters = 0;
+  while (*iters < p->powell_iters && s >= p->powell_tol) {
+    double x0[6], best_drop = 0.0, drop;
+    int best_dir = 0;
+    for (int k = 0; k < 6; ++k) x0[k] = x[k];
+    for (int i = 0; i < 6; ++i) {
+      if (powell_line(fn, ctx, x, f, D[i], s, evals, &drop)) return -1;
+      if (drop > best_drop) {
+        best_drop = drop;
+        best_dir = i;
+      }
+    }
+    ++*iters;
+    double d[6], n2 = 0.0;
+    for (int k = 0; k < 6; ++k) {
+      d[k] = x[k] - x0[k];
+      const double u = d[k] / scale[k];
+      n2 = n2 + u * u;
+    }
+    if (n2 == 0.0) {
+      s = 0.5 * s;
+      continue;
+    }
+    if (powell_line(fn, ctx, x, f, d, 1.0, evals, &drop)) return -1;
+    const double n = sqrt(n2);
+    for (int k = 0; k < 6; ++k) D[best_dir][k] = d[k] / n;
+  }
+  return 0;
+}
+
 int orc_dfo_core(orc_batch_fn fn, void *ctx, const double scale[6], const orc_dfo_params *p,
                  double x_out[6], double *f_out, orc_dfo_report *rep) {
   double x[7][6], f[7], cand[12][6], fc[12];
-  int evals = 0, nm_iters = 0, shrinks = 0, cd_iters = 0;
-  /* initial simplex: the origin and one step along each axis */
-  for (int i = 0; i < 7; ++i)
-    for (int k = 0; k < 6; ++k) x[i][k] = (i >= 1 && k == i - 1) ? p->nm_step * scale[k] : 0.0;
-  if (fn(ctx, 7, &x[0][0], f)) return -1;
-  evals += 7;
-  while (nm_iters < p->nm_iters) {
-    int o[7];
-    nm_order(f, o);
-    /* stop when every vertex is within nm_tol (in units of scale) of the best */
-    double diam = 0.0;
-    for (int i = 1; i < 7; ++i)
+  int evals = 0, nm_iters = 0, shrinks = 0, cd_iters = 0, powell_iters = 0;
+  if (p->method == 1) {
+    /* Powell's method in place of Nelder-Mead: its end point becomes the best vertex */
+    double xp[6], fp;
+    if (powell_search(fn, ctx, scale, p, xp, &fp, &evals, &powell_iters)) return -1;
+    for (int i = 0; i < 7; ++i) {
+      for (int k = 0; k < 6; ++k) x[i][k] = xp[k];
+      f[i] = fp;
+    }
+  } else {
+    /* initial simplex: the origin and one step along each axis */
+    for (int i = 0; i < 7; ++i)
+      for (int k = 0; k < 6; ++k) x[i][k] = (i >= 1 && k == i - 1) ? p->nm_step * scale[k] : 0.0;
+    if (fn(ctx, 7, &x[0][0], f)) return -1;
+    evals += 7;
+    while (nm_iters < p->nm_iters) {
+      int o[7];
+      nm_order(f, o);
+      /* stop when every vertex is within nm_tol (in units of scale) of the best */
+      double diam = 0.0;
+      for (int i = 1; i < 7; ++i)
+        for (int k = 0; k < 6; ++k) {
+          double d = fabs(x[o[i]][k] - x[o[0]][k]) / scale[k];
+          if (d > diam) diam = d;
+        }
+      if (diam < p->nm_tol) break;
+      const int h = o[6];
+      double c[6];
       for (int k = 0; k < 6; ++k) {
-        double d = fabs(x[o[i]][k] - x[o[0]][k]) / scale[k];
-        if (d > diam) diam = d;
+        double s = 0.0;
+        for (int i = 0; i < 6; ++i) s += x[o[i]][k];
+        c[k] = s / 6.0;
       }
-    if (diam < p->nm_tol) break;
-    const int h = o[6];
-    double c[6];
-    for (int k = 0; k < 6; ++k) {
-      double s = 0.0;
-      for (int i = 0; i < 6; ++i) s += x[o[i]][k];
-      c[k] = s / 6.0;
-    }
-    /* reflection, expansion, outside and inside contraction, evaluated together */
-    for (int k = 0; k < 6; ++k) {
-      double dk = c[k] - x[h][k];
-      cand[0][k] = c[k] + dk;
-      cand[1][k] = c[k] + 2.0 * dk;
-      cand[2][k] = c[k] + 0.5 * dk;
-      cand[3][k] = c[k] - 0.5 * dk;
-    }
-    if (fn(ctx, 4, &cand[0][0], fc)) return -1;
-    evals += 4;
-    ++nm_iters;
-    const double fb = f[o[0]], fs = f[o[5]], fh = f[h];
-    int take = -1;
-    if (fc[0] < fb) take = fc[1] < fc[0] ? 1 : 0;
-    else if (fc[0] < fs) take = 0;
-    else if (fc[0] < fh) take = fc[2] <= fc[0] ? 2 : -1;
-    else take = fc[3] < fh ? 3 : -1;
-    if (take >= 0) {
-      for (int k = 0; k < 6; ++k) x[h][k] = cand[take][k];
-      f[h] = fc[take];
-    } else {
-      /* shrink toward the best vertex */
-      const int b = o[0];
-      int m = 0;
-      for (int i = 0; i < 7; ++i) {
-        if (i == b) continue;
-        for (int k = 0; k < 6; ++k) cand[m][k] = x[b][k] + 0.5 * (x[i][k] - x[b][k]);
-        ++m;
+      /* reflection, expansion, outside and inside contraction, evaluated together */
+      for (int k = 0; k < 6; ++k) {
+        double dk = c[k] - x[h][k];
+        cand[0][k] = c[k] + dk;
+        cand[1][k] = c[k] + 2.0 * dk;
+        cand[2][k] = c[k] + 0.5 * dk;
+        cand[3][k] = c[k] - 0.5 * dk;
       }
-      if (fn(ctx, 6, &cand[0][0], fc)) return -1;
-      evals += 6;
-      ++shrinks;
-      m = 0;
-      for (int i = 0; i < 7; ++i) {
-        if (i == b) continue;
-        for (int k = 0; k < 6; ++k) x[i][k] = cand[m][k];
-        f[i] = fc[m];
-        ++m;
+      if (fn(ctx, 4, &cand[0][0], fc)) return -1;
+      evals += 4;
+      ++nm_iters;
+      const double fb = f[o[0]], fs = f[o[5]], fh = f[h];
+      int take = -1;
+      if (fc[0] < fb) take = fc[1] < fc[0] ? 1 : 0;
+      else if (fc[0] < fs) take = 0;
+      else if (fc[0] < fh) take = fc[2] <= fc[0] ? 2 : -1;
+      else take = fc[3] < fh ? 3 : -1;
+      if (take >= 0) {
+        for (int k = 0; k < 6; ++k) x[h][k] = cand[take][k];
+        f[h] = fc[take];
+      } else {
+        /* shrink toward the best vertex */
+        const int b = o[0];
+        int m = 0;
+        for (int i = 0; i < 7; ++i) {
+          if (i == b) continue;
+          for (int k = 0; k < 6; ++k) cand[m][k] = x[b][k] + 0.5 * (x[i][k] - x[b][k]);
+          ++m;
+        }
+        if (fn(ctx, 6, &cand[0][0], fc)) return -1;
+        evals += 6;
+        ++shrinks;
+        m = 0;
+        for (int i = 0; i < 7; ++i) {
+          if (i == b) continue;
+          for (int k = 0; k < 6; ++k) x[i][k] = cand[m][k];
+          f[i] = fc[m];
+          ++m;
+        }
       }
     }
   }
@@ -1270,6 +1348,7 @@ int orc_dfo_core(orc_batch_fn fn, void *ctx, const double scale[6], const orc_df
     rep->nm_shrinks = shrinks;
     rep->cd_iters = cd_iters;
     rep->converged = converged;
+    rep->powell_iters = powell_iters;
   }
   return 0;
 }

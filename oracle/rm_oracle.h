@@ -191,6 +191,17 @@ int orc_meshify(const orc_cam *cam, const float *depth, const uint8_t *cls, cons
  *    inside contraction: f_ic < f_worst <= f_r) or shrink every vertex halfway toward the
  *    best (a batch of six). Ends after nm_iters iterations or when every vertex lies within
  *    nm_tol (scaled, per axis) of the best.
+ *  - Or, with method 1, Powell's conjugate-direction search in place of Nelder-Mead (the
+ *    paper names it beside Nelder-Mead; settings are not given, these are this oracle's):
+ *    directions start as scale_k e_k (unit scaled length), and the origin is evaluated
+ *    alone. A line search along d from x is one batch of the 12 points x + (a s) d,
+ *    a = +1/4, -1/4, +1/2, -1/2, +1, -1, +2, -2, +4, -4, +8, -8 (products and sums rounded
+ *    separately); the lowest (ties: the first) is taken if it is below f(x). An iteration
+ *    searches along the six directions in turn (s = the current step), then, if x moved, along
+ *    the displacement d = x - x0 of the iteration with s = 1, and replaces the direction
+ *    whose search lowered the value most by d divided by its scaled length
+ *    sqrt(sum_k (d_k / scale_k)^2). An iteration in which x did not move halves s. Ends after
+ *    powell_iters iterations or once s < powell_tol.
  *  - Coordinate descent from the best vertex with steps cd_step * scale: the 12 moves +-step
  *    along each axis as one batch; the lowest (ties: the first, +axis0, -axis0, +axis1, ...)
  *    is taken if it is below the current value, else every step is halved. Converged when the
@@ -201,10 +212,13 @@ typedef struct {
   int32_t nm_iters, cd_iters;
   double nm_step, nm_tol, cd_step, cd_tol;
   double scale_t, scale_r;   /* metres and radians per unit of the scaled twist */
+  int32_t method;            /* 0: Nelder-Mead, 1: Powell's method; then coordinate descent */
+  int32_t powell_iters;
+  double powell_step, powell_tol;
 } orc_dfo_params;
 
 typedef struct {
-  int32_t evals, nm_iters, nm_shrinks, cd_iters, converged, pad_;
+  int32_t evals, nm_iters, nm_shrinks, cd_iters, converged, powell_iters;
 } orc_dfo_report;
 
 int orc_dfo_core(orc_batch_fn fn, void *ctx, const double scale[6], const orc_dfo_params *p,
