@@ -601,6 +601,19 @@ def run_icp(a):
                 "e_table_initial": drep["e_table_initial"], "e_table_final": drep["e_table_final"],
                 "pos_err_m": float(np.linalg.norm(dpose[:3, 3] - w["gt"][:3, 3])),
                 "batch_slots": 12}
+    # the same search with Powell's method in place of Nelder-Mead
+    ppar = rm.dfo_params(method="powell", powell_iters=20, cd_iters=40)
+    rm.dfo_align(gm, scan, dstart, dfo=ppar)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps_d):
+        ppose, prep = rm.dfo_align(gm, scan, dstart, dfo=ppar)
+    pw_ms = (time.perf_counter() - t0) / reps_d * 1e3
+    dfo_line["powell"] = {"ms_per_alignment": pw_ms, "evals": prep["evals"],
+                          "us_per_eval": pw_ms * 1e3 / prep["evals"], "powell_iters": prep["powell_iters"],
+                          "cd_iters": prep["cd_iters"], "converged": prep["converged"],
+                          "e_table_final": prep["e_table_final"],
+                          "pos_err_m": float(np.linalg.norm(ppose[:3, 3] - w["gt"][:3, 3]))}
 
     # Fig. 7's cost landscape: 101-sample sweeps along each of the six twist axes
     def sweeps():

@@ -342,6 +342,14 @@ rm_status rm_depth_blur(const rm_intrinsics *intr, int32_t n_images, const float
  *    are scored together and the usual reflect / expand / contract / shrink rules applied
  *    (ties in value: the lower slot ranks first); ends after nm_iters iterations or when every
  *    vertex is within nm_tol (scaled) of the best;
+ *  - or, with method = 1, Powell's conjugate-direction search in place of Nelder-Mead (the
+ *    paper names it too, without settings): the directions start as the scaled axes; a line
+ *    search from x along d scores the 12 points x + (a s) d, a = +-1/4, +-1/2, +-1, +-2, +-4,
+ *    +-8 (in that order, + first; ties: the first), and moves to the lowest if it lowers the
+ *    cost. An iteration searches the six directions in turn with the step s (powell_step at
+ *    first), then the iteration's displacement d with s = 1, and replaces the direction that
+ *    lowered the cost most by d over its scaled length; an iteration that does not move halves
+ *    s. Ends after powell_iters iterations or once s < powell_tol;
  *  - coordinate descent from the best vertex with steps cd_step * scale: the 12 moves +-step
  *    along each axis scored together; the best move is taken if it lowers the cost, else all
  *    steps halve; converged when the largest scaled step is below cd_tol. */
@@ -349,11 +357,14 @@ typedef struct {
   int32_t nm_iters, cd_iters;
   double nm_step, nm_tol, cd_step, cd_tol;
   double scale_t, scale_r;
+  int32_t method;           /* 0: Nelder-Mead, 1: Powell's method; then coordinate descent */
+  int32_t powell_iters;
+  double powell_step, powell_tol;
 } rm_dfo_params;
 
 typedef struct {
   int32_t evals;            /* poses scored (candidates only) */
-  int32_t nm_iters, nm_shrinks, cd_iters, converged, reserved;
+  int32_t nm_iters, nm_shrinks, cd_iters, converged, powell_iters;
   int64_t e_table_initial, e_table_final;
 } rm_dfo_report;
 

@@ -85,12 +85,14 @@ class rm_meshify_params(ctypes.Structure):
 class rm_dfo_params(ctypes.Structure):
     _fields_ = [("nm_iters", ctypes.c_int32), ("cd_iters", ctypes.c_int32), ("nm_step", ctypes.c_double),
                 ("nm_tol", ctypes.c_double), ("cd_step", ctypes.c_double), ("cd_tol", ctypes.c_double),
-                ("scale_t", ctypes.c_double), ("scale_r", ctypes.c_double)]
+                ("scale_t", ctypes.c_double), ("scale_r", ctypes.c_double), ("method", ctypes.c_int32),
+                ("powell_iters", ctypes.c_int32), ("powell_step", ctypes.c_double),
+                ("powell_tol", ctypes.c_double)]
 
 
 class rm_dfo_report(ctypes.Structure):
     _fields_ = [("evals", ctypes.c_int32), ("nm_iters", ctypes.c_int32), ("nm_shrinks", ctypes.c_int32),
-                ("cd_iters", ctypes.c_int32), ("converged", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("cd_iters", ctypes.c_int32), ("converged", ctypes.c_int32), ("powell_iters", ctypes.c_int32),
                 ("e_table_initial", ctypes.c_int64), ("e_table_final", ctypes.c_int64)]
 
 

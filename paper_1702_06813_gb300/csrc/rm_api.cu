@@ -1670,6 +1670,10 @@ rm_status rm_dfo_align(rm_map *m, const rm_scan *scan, const double *init_pose,
       !(dp->nm_tol >= 0.0) || !(dp->cd_tol >= 0.0) || !std::isfinite(dp->scale_t) ||
       !std::isfinite(dp->scale_r) || !std::isfinite(dp->nm_step) || !std::isfinite(dp->cd_step))
     return fail(RM_EINVAL, "scales and steps must be finite and > 0, tolerances >= 0");
+  if (dp->method != 0 && dp->method != 1) return fail(RM_EINVAL, "method must be 0 or 1");
+  if (dp->method == 1 && (dp->powell_iters < 0 || dp->powell_iters > 100000 || !(dp->powell_step > 0.0) ||
+                          !std::isfinite(dp->powell_step) || !(dp->powell_tol >= 0.0)))
+    return fail(RM_EINVAL, "Powell: iterations 0..100000, a finite step > 0, a tolerance >= 0");
   std::lock_guard<std::mutex> lk(m->mu);
   cudaStream_t s = (cudaStream_t)stream;
   const rm_intrinsics *in = &scan->intr;
@@ -1703,6 +1707,10 @@ rm_status rm_dfo_align(rm_map *m, const rm_scan *scan, const double *init_pose,
     rmk::DfoArgs da{};
     da.nm_iters = dp->nm_iters;
     da.cd_iters = dp->cd_iters;
+    da.method = dp->method;
+    da.powell_iters = dp->method == 1 ? dp->powell_iters : 0;
+    da.powell_step = dp->powell_step;
+    da.powell_tol = dp->powell_tol;
     da.nm_step = dp->nm_step;
     da.nm_tol = dp->nm_tol;
     da.cd_step = dp->cd_step;
@@ -1716,8 +1724,10 @@ rm_status rm_dfo_align(rm_map *m, const rm_scan *scan, const double *init_pose,
     da.cz = m->centre[2];
     RM_CK(rmk::launch_dfo_init(d_st, lb.T0, da, lb.M, lb.skip, s));
     m->launches += 1;
-    // at most: the simplex, two batches per Nelder-Mead iteration, one per descent step
-    const int max_steps = 1 + 2 * dp->nm_iters + dp->cd_iters;
+    // at most: the simplex, two batches per Nelder-Mead iteration, one per descent step; or
+    // the origin and seven line searches per Powell iteration
+    const int max_steps = dp->method == 1 ? 1 + 7 * dp->powell_iters + dp->cd_iters
+                                          : 1 + 2 * dp->nm_iters + dp->cd_iters;
     for (int it = 0; it < max_steps; ++it) {
       RM_TRY(wave(m, a, rmk::kCost, s));
       RM_CK(rmk::launch_dfo_step(d_st, da, d_et, lb.M, lb.skip, s));
@@ -1742,7 +1752,7 @@ rm_status rm_dfo_align(rm_map *m, const rm_scan *scan, const double *init_pose,
       rep->nm_shrinks = hs.nm_shrinks;
       rep->cd_iters = hs.cd_iters;
       rep->converged = hs.converged;
-      rep->reserved = 0;
+      rep->powell_iters = hs.powell_iters;
       rep->e_table_initial = (long long)hs.f_init;
       rep->e_table_final = (long long)hs.fcur;
     }

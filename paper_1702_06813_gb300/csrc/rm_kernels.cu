@@ -1791,6 +1791,78 @@ __device__ void dfo_next_nm(DfoState &s, const DfoArgs &a) {
   s.phase = 1;
 }
 
+// Powell's line search from xc along d: the 12 points xc + (a step) d, products and sums
+// rounded separately (no contraction), so the candidates equal the oracle's bit for bit.
+__constant__ double kPowellA[12] = {0.25, -0.25, 0.5, -0.5, 1.0, -1.0, 2.0, -2.0, 4.0, -4.0, 8.0, -8.0};
+
+__device__ void powell_line(DfoState &s, const double *d, double step) {
+  for (int m = 0; m < 12; ++m) {
+    const double am = __dmul_rn(kPowellA[m], step);
+    for (int k = 0; k < 6; ++k) s.cand[m][k] = __dadd_rn(s.xc[k], __dmul_rn(am, d[k]));
+  }
+  s.n_cand = 12;
+  s.phase = 6;
+}
+
+// The next Powell iteration (its first axis search), or the switch to coordinate descent from
+// Powell's end point once out of iterations or below the step tolerance.
+__device__ void powell_next(DfoState &s, const DfoArgs &a) {
+  if (s.powell_iters >= a.powell_iters || !(s.ps >= a.powell_tol)) {
+    for (int k = 0; k < 6; ++k) s.st[k] = a.cd_step * a.scale[k];
+    dfo_next_cd(s, a);
+    return;
+  }
+  for (int k = 0; k < 6; ++k) s.x0[k] = s.xc[k];
+  s.best_drop = 0.0;
+  s.best_dir = 0;
+  s.pdir = 0;
+  powell_line(s, s.D[0], s.ps);
+}
+
+// One finished Powell line search: take its lowest point if it lowers the value, then the
+// next direction, the displacement search, or the next iteration.
+__device__ void powell_step(DfoState &s, const DfoArgs &a, const double *fc) {
+  int best = 0;
+  for (int m = 1; m < 12; ++m)
+    if (fc[m] < fc[best]) best = m;
+  double drop = 0.0;
+  if (fc[best] < s.fcur) {
+    drop = s.fcur - fc[best];
+    for (int k = 0; k < 6; ++k) s.xc[k] = s.cand[best][k];
+    s.fcur = fc[best];
+  }
+  if (s.pdir == 6) {  // the displacement search: replace the direction of largest decrease
+    const double n = __dsqrt_rn(s.n2);
+    for (int k = 0; k < 6; ++k) s.D[s.best_dir][k] = __ddiv_rn(s.disp[k], n);
+    powell_next(s, a);
+    return;
+  }
+  if (drop > s.best_drop) {
+    s.best_drop = drop;
+    s.best_dir = s.pdir;
+  }
+  s.pdir += 1;
+  if (s.pdir < 6) {
+    powell_line(s, s.D[s.pdir], s.ps);
+    return;
+  }
+  s.powell_iters += 1;
+  double n2 = 0.0;
+  for (int k = 0; k < 6; ++k) {
+    s.disp[k] = __dsub_rn(s.xc[k], s.x0[k]);
+    const double u = __ddiv_rn(s.disp[k], a.scale[k]);
+    n2 = __dadd_rn(n2, __dmul_rn(u, u));
+  }
+  if (n2 == 0.0) {
+    s.ps = 0.5 * s.ps;
+    powell_next(s, a);
+    return;
+  }
+  s.n2 = n2;
+  s.pdir = 6;
+  powell_line(s, s.disp, 1.0);
+}
+
 __device__ void dfo_write_candidates(DfoState &s, const DfoArgs &a, float *Ms) {
   for (int m = 0; m < kDfoSlots; ++m) {
     double T[16];
@@ -1802,11 +1874,23 @@ __device__ void dfo_write_candidates(DfoState &s, const DfoArgs &a, float *Ms) {
 __global__ void k_dfo_init(DfoState *st, const double *T0, DfoArgs a, float *Ms, int *skip) {
   DfoState &s = *st;
   for (int k = 0; k < 16; ++k) s.T0[k] = T0[k];
+  s.evals = s.nm_iters = s.nm_shrinks = s.cd_iters = s.converged = s.shrink_best = 0;
+  s.powell_iters = 0;
+  if (a.method == 1) {  // Powell: the origin first; directions are the scaled axes
+    for (int i = 0; i < 6; ++i)
+      for (int k = 0; k < 6; ++k) s.D[i][k] = i == k ? a.scale[k] : 0.0;
+    for (int k = 0; k < 6; ++k) s.cand[0][k] = s.xc[k] = 0.0;
+    s.ps = a.powell_step;
+    s.n_cand = 1;
+    s.phase = 5;
+    dfo_write_candidates(s, a, Ms);
+    *skip = 0;
+    return;
+  }
   for (int i = 0; i < 7; ++i)
     for (int k = 0; k < 6; ++k) s.cand[i][k] = (i >= 1 && k == i - 1) ? a.nm_step * a.scale[k] : 0.0;
   s.n_cand = 7;
   s.phase = 0;
-  s.evals = s.nm_iters = s.nm_shrinks = s.cd_iters = s.converged = s.shrink_best = 0;
   dfo_write_candidates(s, a, Ms);
   *skip = 0;
 }
@@ -1864,6 +1948,11 @@ __global__ void k_dfo_step(DfoState *st, DfoArgs a, const long long *et, float *
       ++m;
     }
     dfo_next_nm(s, a);
+  } else if (s.phase == 5) {
+    s.f_init = s.fcur = fc[0];
+    powell_next(s, a);
+  } else if (s.phase == 6) {
+    powell_step(s, a, fc);
   } else {
     s.cd_iters += 1;
     int best = 0;

@@ -157,13 +157,19 @@ struct DfoState {
   double cand[kDfoSlots][6];  // candidates of the pending evaluation
   double xc[6], fcur, st[6];  // coordinate descent: point, value, steps
   double f_init;              // the cost at the start pose
-  int phase;                  // 0 simplex, 1 NM step, 2 NM shrink, 3 coordinate step, 4 done
+  int phase;                  // 0 simplex, 1 NM step, 2 NM shrink, 3 coordinate step, 4 done,
+                              // 5 Powell start, 6 Powell line search
   int n_cand;
   int evals, nm_iters, nm_shrinks, cd_iters, converged, shrink_best;
+  // Powell's method: directions, the iteration's start and displacement, the line step
+  double D[6][6], x0[6], disp[6], n2, ps, best_drop;
+  int pdir, best_dir, powell_iters;
 };
 
 struct DfoArgs {
   int nm_iters, cd_iters;
+  int method, powell_iters;   // method 1: Powell's method in place of Nelder-Mead
+  double powell_step, powell_tol;
   double nm_step, nm_tol, cd_step, cd_tol;
   double scale[6];
   double cx, cy, cz;  // map centre

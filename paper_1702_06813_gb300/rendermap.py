@@ -331,15 +331,20 @@ def sequential_icp(scans, first_pose, max_range, step=2, max_edge=0.1, tol=0.2, 
 
 
 def dfo_params(nm_iters=60, cd_iters=60, nm_step=1.0, nm_tol=0.05, cd_step=0.25, cd_tol=0.01,
-               scale_t=0.05, scale_r=0.0349) -> N.rm_dfo_params:
-    """Nelder-Mead / coordinate-descent settings; scales: 5 cm and 2 deg per unit."""
-    return N.rm_dfo_params(nm_iters, cd_iters, nm_step, nm_tol, cd_step, cd_tol, scale_t, scale_r)
+               scale_t=0.05, scale_r=0.0349, method="nm", powell_iters=30, powell_step=1.0,
+               powell_tol=0.05) -> N.rm_dfo_params:
+    """Derivative-free search settings; scales: 5 cm and 2 deg per unit. method "nm"
+    (Nelder-Mead) or "powell" (Powell's method), then coordinate descent."""
+    m = {"nm": 0, "powell": 1}[method]
+    return N.rm_dfo_params(nm_iters, cd_iters, nm_step, nm_tol, cd_step, cd_tol, scale_t, scale_r, m,
+                           powell_iters, powell_step, powell_tol)
 
 
 def dfo_align(m: Map, scan: Scan, init_pose, params=None, dfo=None, gd_iters=0):
     """The paper's hybrid derivative-free alignment on the Table I cost (Sec. IV.C): optional
-    initial gradient steps (Levenberg-Marquardt on the surrogate), then Nelder-Mead and
-    coordinate descent, all on the device. Returns (pose 4x4 float64 numpy, report)."""
+    initial gradient steps (Levenberg-Marquardt on the surrogate), then Nelder-Mead (or Powell's
+    method, dfo_params(method="powell")) and coordinate descent, all on the device. Returns
+    (pose 4x4 float64 numpy, report)."""
     start = init_pose
     gd = None
     if gd_iters > 0:
@@ -354,7 +359,7 @@ def dfo_align(m: Map, scan: Scan, init_pose, params=None, dfo=None, gd_iters=0):
                             out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(rep), _stream())
     if st not in (N.RM_OK, N.RM_ENOTCONV):
         check(st)
-    report = {f: getattr(rep, f) for f, _ in N.rm_dfo_report._fields_ if f != "reserved"}
+    report = {f: getattr(rep, f) for f, _ in N.rm_dfo_report._fields_}
     report["status"] = N.STATUS_NAMES[st]
     if gd is not None:
         report["gd"] = gd
