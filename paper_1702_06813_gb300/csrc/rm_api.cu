@@ -869,7 +869,23 @@ rm_status run_batch(rm_map *m, const rm_problem *probs, int n, const rm_cost_par
     b.lm_iters = K;
     b.status = m->d_status;
     b.spin_limit = wait_budget(m, 1ll << 32);
-    const int grid = rmk::persist_grid(m->device);
+    // A homogeneous plain batch (one scan, camera and parameters for every problem, no LM or
+    // ICP) runs as the poses of one wave: its argument block is a kernel parameter. The
+    // problems' arrays are already laid out at the wave's per-pose offsets, provided each
+    // problem's bins end on the 256-byte boundary where the next one's start.
+    bool wave_form = !lm && !icp && nc >= 1 &&
+                     ((size_t)tg[0].ntiles * tg[0].cap * tg[0].rec_bytes) % 256 == 0;
+    for (int p = 1; p < n && wave_form; ++p)
+      wave_form = scan_of[p] == 0 && std::memcmp(&probs[p].scan.intr, &probs[0].scan.intr, sizeof(rm_intrinsics)) == 0;
+    WaveArgs w;
+    std::memset(&w, 0, sizeof(w));
+    if (wave_form) {
+      w = args[0];
+      w.n_poses = n;
+      w.wave_base = 0;
+      w.skip = nullptr;
+    }
+    const int grid = wave_form ? rmk::persist_wave_grid(m->device, w.cam.model) : rmk::persist_grid(m->device);
     if (grid <= 0) return fail(RM_ECUDA, "could not size the persistent grid");
     // counters to zero, LM state / pose matrices, the persistent kernel: one captured graph
     // per batch shape (the arena layout is a function of the shape), replayed every call
@@ -879,6 +895,15 @@ rm_status run_batch(rm_map *m, const rm_problem *probs, int n, const rm_cost_par
                   la.step_tol, tiles_total, px_total, rays_total, m->cap * 4096 + m->cap_ray, ia.step_tol,
                   b.spin_limit);
     std::string key(sig);
+    if (wave_form) {  // the graph holds w by value: a different w needs a new capture
+      key += "|wave:";
+      const unsigned char *wb = reinterpret_cast<const unsigned char *>(&w);
+      for (size_t k = 0; k < sizeof(w); ++k) {
+        static const char hex[] = "0123456789abcdef";
+        key += hex[wb[k] >> 4];
+        key += hex[wb[k] & 15];
+      }
+    }
     for (int p = 0; p < n; ++p) key += "|" + std::to_string(probs[p].scan.intr.model) + "x" +
                                         std::to_string(probs[p].scan.intr.width) + "x" +
                                         std::to_string(probs[p].scan.intr.height);
@@ -904,7 +929,7 @@ rm_status run_batch(rm_map *m, const rm_problem *probs, int n, const rm_cost_par
       if (lm) rec(rmk::launch_lm_init_batch(d_lm, d_poses, n, la, d_M, d_skip, c));
       else if (icp) rec(rmk::launch_icp_init_batch(d_icp, d_poses, n, ia, d_M, d_skip, c));
       else rec(rmk::launch_pose_to_m(d_poses, n, m->centre[0], m->centre[1], m->centre[2], d_M, c));
-      rec(rmk::launch_persist(b, grid, c));
+      rec(wave_form ? rmk::launch_persist_wave(b, w, grid, c) : rmk::launch_persist(b, grid, c));
       cudaGraph_t graph = nullptr;
       const cudaError_t ec = cudaStreamEndCapture(c, &graph);
       if (e == cudaSuccess) e = ec;

@@ -2065,6 +2065,111 @@ __device__ __forceinline__ int claim_slot(int *head, const int *tail) {
 // only slots that have been reserved by a publisher (whose write is then at most a few
 // instructions away) and exits once every problem has finished; with nothing to take it
 // sleeps and retries (bounded).
+// Thread 0 of a CTA: claims the next ready item of the batch's queues into *s_item (x < 0:
+// every problem has finished) and sets *s_abort when a wait ran out of its budget.
+__device__ __forceinline__ void persist_claim(const BatchArgs &b, int4 *s_item, int *s_abort) {
+  int4 item = make_int4(-1, 0, 0, 0);
+  int abort = 0;
+  const long long t0 = clock64();
+  unsigned ns = 32;
+  for (;;) {
+    // a claim past a queue's capacity (racing claims at its very end) holds no slot
+    int slot = claim_slot(b.qctl + 0, b.qctl + 1);
+    if (slot >= b.cap[0]) slot = -1;
+    if (slot < 0) {
+      slot = claim_slot(b.qctl + 2, b.qctl + 3);
+      slot = slot >= b.cap[1] ? -1 : (slot >= 0 ? slot + b.cap[0] : -1);
+    }
+    if (slot >= 0) {
+      int x;
+      bool finished = false;
+      while ((x = *(volatile const int *)&b.items[slot].x) < 0) {
+        if (*(volatile const int *)(b.qctl + 4) >= b.n_problems) {  // nothing more will come
+          finished = true;
+          break;
+        }
+        if (clock64() - t0 > b.spin_limit) break;
+        __nanosleep(64);
+      }
+      if (finished) break;
+      if (x < 0) {
+        atomicOr(b.status, kStatusTimeout);
+        abort = 1;
+        break;
+      }
+      __threadfence();
+      item = make_int4(x, __ldcg(&b.items[slot].y), __ldcg(&b.items[slot].z), __ldcg(&b.items[slot].w));
+      break;
+    }
+    if (*(volatile const int *)(b.qctl + 4) >= b.n_problems) break;  // all finished
+    if (clock64() - t0 > b.spin_limit) {
+      atomicOr(b.status, kStatusTimeout);
+      abort = 1;
+      break;
+    }
+    __nanosleep(ns);
+    if (ns < 1024) ns *= 2;
+  }
+  *s_item = item;
+  *s_abort = abort;
+}
+
+// Thread 0 of a CTA, after `item` is done: counts it, and when it was its problem's last item
+// of a phase, reserves the next phase's slots (the setup phase sized by *vis_count, the
+// problem's visible clusters). Returns (phase, count, first slot, evaluation); count 0: none.
+__device__ __forceinline__ int4 persist_complete(const BatchArgs &b, int4 item, const int *vis_count) {
+  __threadfence();
+  const int p = item.x, ph = item.y, it = item.w;
+  int4 eq = make_int4(0, 0, -1, it);  // phase, count, queue, evaluation
+  if (ph < 3) {
+    const int c = atomicAdd(b.done + 4 * p + ph, 1) + 1;
+    if (c == __ldcg(b.need + 3 * p + ph)) {
+      if (ph == 0) {
+        // all cull items are in: size the setup phase by the visible clusters
+        const int nv = __ldcg(vis_count);
+        const int nsetup = max(1, (nv + kSetupClusters - 1) / kSetupClusters);
+        b.need[3 * p + 1] = nsetup;
+        eq = make_int4(1, nsetup, 1, it);
+      } else if (ph == 1) {
+        eq = make_int4(2, b.need[3 * p + 2], 0, it);
+      } else {
+        eq = make_int4(3, 1, 0, it);
+      }
+    }
+  } else if ((b.lm || b.icp) && it < b.lm_iters) {
+    b.done[4 * p + 0] = 0;
+    b.done[4 * p + 1] = 0;
+    b.done[4 * p + 2] = 0;
+    eq = make_int4(0, b.need[3 * p], 1, it + 1);
+  } else {
+    atomicAdd(b.qctl + 4, 1);  // the problem is finished
+  }
+  if (eq.y > 0) {
+    const int q = eq.z;
+    const int first = atomicAdd(b.qctl + 2 * q + 1, eq.y);
+    if (first + eq.y > b.cap[q]) atomicOr(b.status, kStatusQueue);  // cannot happen
+    eq.z = (q == 0 ? 0 : b.cap[0]) + first;
+    eq.y = max(0, min(eq.y, b.cap[q] - first));
+  }
+  return eq;
+}
+
+// All threads of a CTA: write the reserved successor slots, then publish each one by setting
+// its problem field last (after a fence).
+__device__ __forceinline__ void persist_publish(const BatchArgs &b, int4 eq, int problem) {
+if (eq.y > 0) {
+  for (int k = threadIdx.x; k < eq.y; k += blockDim.x) {
+    int4 *slot = b.items + eq.z + k;
+    slot->y = eq.x;
+    slot->z = k;
+    slot->w = eq.w;
+  }
+  __threadfence();
+  __syncthreads();
+  for (int k = threadIdx.x; k < eq.y; k += blockDim.x) atomicExch(&b.items[eq.z + k].x, problem);
+}
+}
+
 __global__ void __launch_bounds__(kThreads, RM_PERSIST_MIN_BLOCKS) k_persist(BatchArgs b) {
   union PersistSmem {
     RasterSmem<kPersistTileW[0] * kPersistTileH[0], 0> r0;
@@ -2078,52 +2183,7 @@ __global__ void __launch_bounds__(kThreads, RM_PERSIST_MIN_BLOCKS) k_persist(Bat
   __shared__ int4 s_enq;       // successors to publish: phase, count, first slot, evaluation
   __shared__ int s_abort;
   for (;;) {
-    if (threadIdx.x == 0) {
-      int4 item = make_int4(-1, 0, 0, 0);
-      int abort = 0;
-      const long long t0 = clock64();
-      unsigned ns = 32;
-      for (;;) {
-        // a claim past a queue's capacity (racing claims at its very end) holds no slot
-        int slot = claim_slot(b.qctl + 0, b.qctl + 1);
-        if (slot >= b.cap[0]) slot = -1;
-        if (slot < 0) {
-          slot = claim_slot(b.qctl + 2, b.qctl + 3);
-          slot = slot >= b.cap[1] ? -1 : (slot >= 0 ? slot + b.cap[0] : -1);
-        }
-        if (slot >= 0) {
-          int x;
-          bool finished = false;
-          while ((x = *(volatile const int *)&b.items[slot].x) < 0) {
-            if (*(volatile const int *)(b.qctl + 4) >= b.n_problems) {  // nothing more will come
-              finished = true;
-              break;
-            }
-            if (clock64() - t0 > b.spin_limit) break;
-            __nanosleep(64);
-          }
-          if (finished) break;
-          if (x < 0) {
-            atomicOr(b.status, kStatusTimeout);
-            abort = 1;
-            break;
-          }
-          __threadfence();
-          item = make_int4(x, __ldcg(&b.items[slot].y), __ldcg(&b.items[slot].z), __ldcg(&b.items[slot].w));
-          break;
-        }
-        if (*(volatile const int *)(b.qctl + 4) >= b.n_problems) break;  // all finished
-        if (clock64() - t0 > b.spin_limit) {
-          atomicOr(b.status, kStatusTimeout);
-          abort = 1;
-          break;
-        }
-        __nanosleep(ns);
-        if (ns < 1024) ns *= 2;
-      }
-      s_item = item;
-      s_abort = abort;
-    }
+    if (threadIdx.x == 0) persist_claim(b, &s_item, &s_abort);
     __syncthreads();
     const int4 item = s_item;
     if (item.x < 0 || s_abort) break;
@@ -2184,55 +2244,65 @@ __global__ void __launch_bounds__(kThreads, RM_PERSIST_MIN_BLOCKS) k_persist(Bat
     }
     __syncthreads();
     // completion; the last item of the problem's phase publishes the successors
-    if (threadIdx.x == 0) {
-      __threadfence();
-      const int p = item.x, ph = item.y, it = item.w;
-      int4 eq = make_int4(0, 0, -1, it);  // phase, count, queue, evaluation
-      if (ph < 3) {
-        const int c = atomicAdd(b.done + 4 * p + ph, 1) + 1;
-        if (c == __ldcg(b.need + 3 * p + ph)) {
-          if (ph == 0) {
-            // all cull items are in: size the setup phase by the visible clusters
-            const int nv = __ldcg(a.vis_count);
-            const int nsetup = max(1, (nv + kSetupClusters - 1) / kSetupClusters);
-            b.need[3 * p + 1] = nsetup;
-            eq = make_int4(1, nsetup, 1, it);
-          } else if (ph == 1) {
-            eq = make_int4(2, b.need[3 * p + 2], 0, it);
-          } else {
-            eq = make_int4(3, 1, 0, it);
-          }
+    if (threadIdx.x == 0) s_enq = persist_complete(b, item, a.vis_count);
+    __syncthreads();
+    persist_publish(b, s_enq, item.x);
+  }
+}
+
+// The persistent kernel for a homogeneous batch (every problem the same camera, scan and
+// parameters, a plain evaluation): the problems are the poses of one wave, whose arguments
+// are a kernel parameter, so the phases (inlined) read them as the per-wave kernels do and the
+// kernel fits the per-wave raster's register budget. Same queue, items and results as
+// k_persist.
+#ifndef RM_PERSIST_WAVE_MIN_BLOCKS
+#define RM_PERSIST_WAVE_MIN_BLOCKS 5
+#endif
+
+template <int MODEL>
+__global__ void __launch_bounds__(kThreads, MODEL == 0 ? RM_PERSIST_WAVE_MIN_BLOCKS : 4)
+    k_persist_wave(BatchArgs b, WaveArgs w) {
+  constexpr int TW = kPersistTileW[MODEL], TH = kPersistTileH[MODEL];
+  union PersistWaveSmem {
+    RasterSmem<TW * TH, MODEL> r;
+    SetupSmem su;
+    double vals[kNumVals];
+  };
+  __shared__ PersistWaveSmem u;
+  __shared__ float s_M[12];
+  __shared__ int4 s_item;
+  __shared__ int4 s_enq;
+  __shared__ int s_abort;
+  for (;;) {
+    if (threadIdx.x == 0) persist_claim(b, &s_item, &s_abort);
+    __syncthreads();
+    const int4 item = s_item;
+    if (item.x < 0 || s_abort) break;
+    const int q = item.x;  // the problem is pose q of the wave
+    switch (item.y) {
+      case 0: {
+        const int c1 = min((item.z + 1) * kPersistCull, (w.n_clusters + 255) / 256);
+        for (int c = item.z * kPersistCull; c < c1; ++c) {
+          cull_block(w, q, c, s_M);
+          __syncthreads();
         }
-      } else if ((b.lm || b.icp) && it < b.lm_iters) {
-        b.done[4 * p + 0] = 0;
-        b.done[4 * p + 1] = 0;
-        b.done[4 * p + 2] = 0;
-        eq = make_int4(0, b.need[3 * p], 1, it + 1);
-      } else {
-        atomicAdd(b.qctl + 4, 1);  // the problem is finished
+        break;
       }
-      if (eq.y > 0) {
-        const int q = eq.z;
-        const int first = atomicAdd(b.qctl + 2 * q + 1, eq.y);
-        if (first + eq.y > b.cap[q]) atomicOr(b.status, kStatusQueue);  // cannot happen
-        eq.z = (q == 0 ? 0 : b.cap[0]) + first;
-        eq.y = max(0, min(eq.y, b.cap[q] - first));
+      case 1: setup_block<MODEL>(w, q, item.z, __ldcg(b.need + 3 * q + 1), u.su); break;
+      case 2: {
+        const int t1 = min((item.z + 1) * kPersistTiles[MODEL], w.tg.ntiles);
+        for (int t = item.z * kPersistTiles[MODEL]; t < t1; ++t) {
+          raster_block<TW, TH, kCostGrad, MODEL>(w, t, q, u.r);
+          __syncthreads();
+        }
+        break;
       }
-      s_enq = eq;
+      default: reduce_block(w, q, u.vals); break;
     }
     __syncthreads();
-    const int4 eq = s_enq;
-    if (eq.y > 0) {
-      for (int k = threadIdx.x; k < eq.y; k += blockDim.x) {
-        int4 *slot = b.items + eq.z + k;
-        slot->y = eq.x;
-        slot->z = k;
-        slot->w = eq.w;
-      }
-      __threadfence();
-      __syncthreads();
-      for (int k = threadIdx.x; k < eq.y; k += blockDim.x) atomicExch(&b.items[eq.z + k].x, item.x);
-    }
+    if (threadIdx.x == 0) s_enq = persist_complete(b, item, w.vis_count + q);
+    __syncthreads();
+    persist_publish(b, s_enq, item.x);
   }
 }
 
@@ -2264,6 +2334,21 @@ cudaError_t launch_lm_init_batch(LMState *st, const double *T0, int n, const LMA
 cudaError_t launch_persist(const BatchArgs &b, int grid, cudaStream_t s) {
   k_persist<<<grid, kThreads, 0, s>>>(b);
   return cudaGetLastError();
+}
+
+cudaError_t launch_persist_wave(const BatchArgs &b, const WaveArgs &w, int grid, cudaStream_t s) {
+  if (w.cam.model == 0) k_persist_wave<0><<<grid, kThreads, 0, s>>>(b, w);
+  else k_persist_wave<1><<<grid, kThreads, 0, s>>>(b, w);
+  return cudaGetLastError();
+}
+
+int persist_wave_grid(int device, int model) {
+  int sms = 0, per = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
+  const cudaError_t e = model == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_persist_wave<0>, kThreads, 0)
+                                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_persist_wave<1>, kThreads, 0);
+  if (e != cudaSuccess) return 0;
+  return sms * (per > 0 ? per : 1);
 }
 
 int persist_grid(int device) {

@@ -227,6 +227,10 @@ cudaError_t launch_lm_init_batch(LMState *st, const double *T0, int n, const LMA
                                  float *Ms, int *skip, cudaStream_t s);
 cudaError_t launch_persist(const BatchArgs &b, int grid, cudaStream_t s);
 int persist_grid(int device);
+// The persistent kernel for a homogeneous plain batch: the problems are the n_poses poses of
+// the one argument block w (pose q's arrays at the wave's per-pose offsets).
+cudaError_t launch_persist_wave(const BatchArgs &b, const WaveArgs &w, int grid, cudaStream_t s);
+int persist_wave_grid(int device, int model);
 
 cudaError_t launch_lm_init(LMState *st, const double *T0, const LMArgs &a, float *M,
                            int *skip, cudaStream_t s);
