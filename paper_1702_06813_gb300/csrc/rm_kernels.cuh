@@ -188,7 +188,7 @@ constexpr int kPersistCull = 4;   // 256-cluster chunks per cull item
 // ray-table problems use 32x32 tiles, two per raster item.
 constexpr int kPersistTileW[2] = {64, 32};
 constexpr int kPersistTileH[2] = {32, 32};
-constexpr int kPersistTiles[2] = {1, 2};
+constexpr int kPersistTiles[2] = {2, 2};
 struct BatchArgs {
   const WaveArgs *probs;   // one per problem (n_poses 1, wave_base 0)
   int n_problems;
