@@ -2116,8 +2116,10 @@ __device__ __forceinline__ void persist_claim(const BatchArgs &b, int4 *s_item, 
 
 // Thread 0 of a CTA, after `item` is done: counts it, and when it was its problem's last item
 // of a phase, reserves the next phase's slots (the setup phase sized by *vis_count, the
-// problem's visible clusters). Returns (phase, count, first slot, evaluation); count 0: none.
-__device__ __forceinline__ int4 persist_complete(const BatchArgs &b, int4 item, const int *vis_count) {
+// problem's visible clusters, clusters_per_item to an item). Returns (phase, count, first
+// slot, evaluation); count 0: none.
+__device__ __forceinline__ int4 persist_complete(const BatchArgs &b, int4 item, const int *vis_count,
+                                                 int clusters_per_item) {
   __threadfence();
   const int p = item.x, ph = item.y, it = item.w;
   int4 eq = make_int4(0, 0, -1, it);  // phase, count, queue, evaluation
@@ -2127,7 +2129,7 @@ __device__ __forceinline__ int4 persist_complete(const BatchArgs &b, int4 item, 
       if (ph == 0) {
         // all cull items are in: size the setup phase by the visible clusters
         const int nv = __ldcg(vis_count);
-        const int nsetup = max(1, (nv + kSetupClusters - 1) / kSetupClusters);
+        const int nsetup = max(1, (nv + clusters_per_item - 1) / clusters_per_item);
         b.need[3 * p + 1] = nsetup;
         eq = make_int4(1, nsetup, 1, it);
       } else if (ph == 1) {
@@ -2244,7 +2246,7 @@ __global__ void __launch_bounds__(kThreads, RM_PERSIST_MIN_BLOCKS) k_persist(Bat
     }
     __syncthreads();
     // completion; the last item of the problem's phase publishes the successors
-    if (threadIdx.x == 0) s_enq = persist_complete(b, item, a.vis_count);
+    if (threadIdx.x == 0) s_enq = persist_complete(b, item, a.vis_count, setup_clusters(a.cam.model));
     __syncthreads();
     persist_publish(b, s_enq, item.x);
   }
@@ -2300,7 +2302,7 @@ __global__ void __launch_bounds__(kThreads, MODEL == 0 ? RM_PERSIST_WAVE_MIN_BLO
       default: reduce_block(w, q, u.vals); break;
     }
     __syncthreads();
-    if (threadIdx.x == 0) s_enq = persist_complete(b, item, w.vis_count + q);
+    if (threadIdx.x == 0) s_enq = persist_complete(b, item, w.vis_count + q, setup_clusters(MODEL));
     __syncthreads();
     persist_publish(b, s_enq, item.x);
   }

@@ -215,7 +215,10 @@ struct BatchArgs {
   long long spin_limit;    // cycles a CTA may go without finding work before it gives up
 };
 
-constexpr int kSetupClusters = 64;  // visible clusters per setup item (eight per warp)
+constexpr int kSetupClusters = 64;  // visible clusters per setup item (eight per warp), at most
+// Visible clusters per persistent setup item by camera model: pinhole 64; ray-table views,
+// which see many more clusters, 128.
+__host__ __device__ constexpr int setup_clusters(int model) { return model != 0 ? 128 : kSetupClusters; }
 constexpr int kSetupCtasPerGpu = 912;  // setup CTAs a small wave may spread over (152 SMs x 6)
 
 // Every slot unpublished except the evaluation-0 cull items of every problem at the head of
