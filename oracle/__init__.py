@@ -31,7 +31,15 @@ Parity status of each function (what pins it, see ``tests/test_oracle_pins.py``)
     normal of a tilted plane at the principal point;
   * meshification: closed-form vertices and labels of a fronto-parallel wall, depth steps,
     no-return and dead pixels, face counts; rendering the mesh of a scan from the scan's own
-    pose reproduces the scan's depths.
+    pose reproduces the scan's depths;
+  * derivative-free search (Nelder-Mead or Powell's method, then coordinate descent): known
+    minima of a convex (rotated) quadratic and an integer staircase, the exact candidates of
+    the first steps, accounting, invariance under an added constant or a positive factor, a
+    noise-free Table I search (``tests/test_oracle_dfo.py``);
+  * vertex gradient: finite differences of the frozen cost with one vertex moved, the sum
+    identity with the pose gradient, a wall's closed form (``tests/test_oracle_vgrad.py``);
+  * input helpers: a golden table of raw readings, single-axis and Euler rotations
+    (``tests/test_oracle_helpers.py``).
 """
 from __future__ import annotations
 

@@ -15,9 +15,11 @@
  *  - Sec. IV.C names derivative-based and derivative-free optimisers; this oracle adds the
  *    least-squares surrogate whose Levenberg-Marquardt step the library runs (a reading, not
  *    the paper's own optimiser), with the pose derivative of the ray-plane depth, and the
- *    paper's own derivative-free search (Nelder-Mead, then coordinate descent) on Table I.
+ *    paper's own derivative-free search (Nelder-Mead or Powell's method, then coordinate
+ *    descent) on Table I.
  *  - Sec. V: render-accelerated point-to-plane ICP (projective association with a depth
- *    tolerance, point-to-plane residual and its 6x6 normal equations) and the depth-image
+ *    tolerance, point-to-plane residual and its 6x6 normal equations), with the map's face
+ *    normals or its vertex normals blended by the hit's barycentrics, and the depth-image
  *    normals of Eq. 2.
  *  - Sec. IV.A / Fig. 5: meshification of a range image into FO / FU quads; Sec. IV.A-B:
  *    the classes of raw range readings; Eq. 1: the pose of the vector X.
