@@ -11,6 +11,7 @@ least-squares residual, and reduce the adjoint gradient and Gauss-Newton matrix 
   python bench.py --workload icp          # point-to-plane ICP terms and alignments (Sec. V)
   python bench.py --workload normals      # Eq. 2 normals of 64 depth images per step
   python bench.py --workload vgrad        # vertex-position gradient of 16 poses per step
+  python bench.py --workload lidar        # 64 poses, 1024x64 Lidar, 2M-triangle terrain; LM
 """
 from __future__ import annotations
 
@@ -45,7 +46,8 @@ def args_():
     ap.add_argument("--cpu-sample", type=int, default=64, help="poses per step of the reference arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile", default=None, help="WxH screen tile (e.g. 64x32): skip the autotuner")
-    ap.add_argument("--workload", choices=["headline", "tracking", "icp", "normals", "vgrad"], default="headline")
+    ap.add_argument("--workload", choices=["headline", "tracking", "icp", "normals", "vgrad", "lidar"],
+                    default="headline")
     ap.add_argument("--frames", type=int, default=200, help="tracking: frames of the trajectory")
     ap.add_argument("--agents", type=int, default=64, help="tracking: agents (scans per frame)")
     ap.add_argument("--triangles", type=int, default=2_000_000, help="tracking: map size")
@@ -713,6 +715,74 @@ def _small_line(a, metric, unit, value, ms, config, roofline, cpu, launches):
         "roofline": roofline, "cpu_baseline": cpu, "gpu_launches": launches}))
 
 
+def run_lidar(a):
+    """The panoramic workload: cost and gradient of 64 candidate poses (30 cm / 3 deg around the
+    true pose) through the 1024 x 64 ray table on the 2M-triangle terrain (render + Table I +
+    surrogate + adjoint), one rm_cost_grad call per step; then LM alignment from the 30 cm /
+    3 deg start. The raster's algorithmic bytes are the scan's, 5 per ray per pose. CPU
+    baseline: the oracle over 16 of the poses on the host cores."""
+    import torch
+    import paper_1702_06813_gb300 as rm
+    import synth
+    import __graft_entry__
+    __graft_entry__.build_library()
+    torch.cuda.set_device(0)
+    w = synth.workload_lidar(a.seed + 4000)
+    mesh, cam = w["mesh"], w["cam"]
+    n = 64
+    r = np.random.Generator(np.random.PCG64(a.seed + 41))
+    poses_np = synth.perturb_gauss(w["gt"], r, 0.3, 3.0, n)
+    gm = rm.Map(mesh.vertices, mesh.faces, mesh.labels)
+    scan = rm.Scan.make(rm.Intrinsics.from_camera(cam), *w["scan"])
+    poses = torch.as_tensor(poses_np.reshape(-1, 16), dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(max(3, a.warmup)):
+        rm.cost_grad(gm, scan, poses)
+    torch.cuda.synchronize()
+    ms = _timed_events(lambda: rm.cost_grad(gm, scan, poses), a.steps, flush)
+    gm.profile(True)
+    _timed_events(lambda: rm.cost_grad(gm, scan, poses), a.steps, flush)
+    prof = gm.profile_read()
+    gm.profile(False)
+    tune = gm.get_tuning()
+    kms = {k: v[1] / a.steps for k, v in prof["kernels"].items()}
+    P = cam.width * cam.height
+    wave = tune["wave_poses"] if tune["wave_poses"] > 0 else n
+    waves = -(-n // wave)
+    rl_ms = kms.get("k_raster", 0.0) / waves
+    pk, pk_kind = peaks()
+    achieved = 5 * P * min(n, wave) / (rl_ms * 1e-3) / 1e9 if rl_ms > 0 else None
+    # LM alignment from the 30 cm / 3 deg start (the configuration's own task)
+    rm.align(gm, scan, w["start"], max_iters=50)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pose, rep_lm = rm.align(gm, scan, w["start"], max_iters=50)
+    lm_ms = (time.perf_counter() - t0) * 1e3
+    cpu = None
+    if not a.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        om = oracle.OracleMap(mesh.vertices, mesh.faces, mesh.labels)
+        t0 = time.perf_counter()
+        res = om.cost_batch(poses_np[:16], cam, *w["scan"])
+        dt = time.perf_counter() - t0
+        cpu = {"value": 16 / dt, "unit": "pose evals/s", "cores": int(res["threads"]), "kind": "oracle",
+               "sample": f"16 of the 64 poses, OpenMP over poses, {dt:.1f} s wall"}
+    _small_line(a, "Lidar pose evals/s (render+residual+grad) 1024x64 ray table, 2M tris", "pose evals/s",
+                n * a.steps / (ms * 1e-3), ms,
+                {"workload": w["name"] + "-64poses", "poses_per_step": n, "triangles": mesh.n_tris,
+                 "rays": [cam.width, cam.height], "tile": list(tune["tile"]), "wave_poses": tune["wave_poses"],
+                 "kernel_ms_per_step": kms, "l2": "flushed between timed steps (256 MiB write)",
+                 "lm_align_from_30cm_3deg": {"ms": lm_ms, "iters": rep_lm["iters"],
+                                             "converged": rep_lm["converged"],
+                                             "pos_err_m": float(np.linalg.norm(pose[:3, 3] - w["gt"][:3, 3]))}},
+                {"bound": "hbm", "kernel": "k_raster", "achieved": achieved, "peak": pk["hbm_gbs"],
+                 "unit": "GB/s", "frac": (achieved / pk["hbm_gbs"]) if achieved else None, "traffic": None,
+                 "peak_kind": pk_kind, "avg_launch_ms": rl_ms, "poses_per_launch": min(n, wave)},
+                cpu, int(prof["launches"]))
+    gm.close()
+
+
 def run_normals(a):
     """Eq. 2 surface normals (Sec. V) of 64 noisy copies of the 640x480 room scan per step
     (sigma 1.5 px, metric), one rm_depth_normals call. Algorithmic bytes: depth and class in,
@@ -833,6 +903,9 @@ def main():
         return
     if a.workload == "vgrad":
         run_vgrad(a)
+        return
+    if a.workload == "lidar":
+        run_lidar(a)
         return
     import torch
     import torch.distributed as dist
