@@ -335,26 +335,34 @@ __device__ __forceinline__ int setup_ray(const float3 v[3], const float4 u[3], c
     if (sg[k] > 0.0f) sig |= 1 << k;
   }
   // ---- conservative pixel rectangle (any rounding; margins absorb it)
+  // An edge plane keeps the up (down) direction out when sg side.y exceeds 1e-4 |side| (below
+  // minus that): compared squared, sy^2 > 1e-8 |side|^2 with the sign of sy, no square root.
   bool has_up = true, has_dn = true;  // up = (0,-1,0), down = (0,1,0)
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    const float nrm = sqrtf(side[k].x * side[k].x + side[k].y * side[k].y + side[k].z * side[k].z);
-    const float tol = 1e-4f * nrm;
-    if (-sg[k] * side[k].y < -tol) has_up = false;
-    if (sg[k] * side[k].y < -tol) has_dn = false;
+    const float n2 = side[k].x * side[k].x + side[k].y * side[k].y + side[k].z * side[k].z;
+    const float sy = sg[k] * side[k].y;
+    const bool clear = sy * sy > 1e-8f * n2;
+    if (clear && sy > 0.0f) has_up = false;
+    if (clear && sy < 0.0f) has_dn = false;
   }
   float zmax = fmaxf(-u[0].y, fmaxf(-u[1].y, -u[2].y)), zmin = fminf(-u[0].y, fminf(-u[1].y, -u[2].y));
   const float cmin = fminf(u[0].x * u[1].x + u[0].y * u[1].y + u[0].z * u[1].z,
                            fminf(u[1].x * u[2].x + u[1].y * u[2].y + u[1].z * u[2].z,
                                  u[2].x * u[0].x + u[2].y * u[0].y + u[2].z * u[0].z));
-  const float ch = sqrtf(fmaxf(0.0f, 0.5f * (1.0f + cmin)));
-  if (ch < 0.05f) {
+  // half-angle cosine of the longest edge; its reciprocal square root widens the elevation
+  // bounds (the directions are normalised approximately, which the margin absorbs)
+  const float h2 = fmaxf(0.0f, 0.5f * (1.0f + cmin));
+  if (h2 < 0.0025f) {
     zmax = 1.0f;
     zmin = -1.0f;
   } else {
-    if (zmax >= 0.0f) zmax = fminf(1.0f, zmax / ch);
-    if (zmin <= 0.0f) zmin = fmaxf(-1.0f, zmin / ch);
+    const float ich = rsqrtf(h2);
+    if (zmax >= 0.0f) zmax = zmax * ich;
+    if (zmin <= 0.0f) zmin = zmin * ich;
   }
+  zmax = fminf(1.0f, zmax);
+  zmin = fmaxf(-1.0f, zmin);
   if (has_up) zmax = 1.0f;
   if (has_dn) zmin = -1.0f;
   const float el_hi = asinf(zmax), el_lo = asinf(zmin);
@@ -451,8 +459,9 @@ __device__ __forceinline__ void setup_block(const WaveArgs &a, int q, int worker
       const float3 c = xform(M, v.x, v.y, v.z);
       int2 sv = make_int2(kSentinel, 1);  // behind the near plane
       if (raytable) {
-        const float nr = sqrtf(c.x * c.x + c.y * c.y + c.z * c.z);
-        const float inv = nr > 0.0f ? 1.0f / nr : 0.0f;
+        // the direction only bounds the rectangle: an approximate normalisation suffices
+        const float n2 = c.x * c.x + c.y * c.y + c.z * c.z;
+        const float inv = n2 > 0.0f ? rsqrtf(n2) : 0.0f;
         s_dir[warp][k] = make_float4(c.x * inv, c.y * inv, c.z * inv, atan2f(c.x, c.z));
       } else if (c.z >= near_m) {
         int xi, yi;
