@@ -74,6 +74,7 @@ struct Carver {
 
 struct rm_map {
   int device = 0;
+  size_t wave_budget = size_t(4) << 30;  // per-wave scratch bytes that decide the poses per wave
   int64_t V = 0, T = 0;
   double centre[3] = {0, 0, 0};
   float4 *d_v = nullptr;
@@ -311,9 +312,9 @@ DevCam make_cam(const rm_intrinsics *in, const float *d_rays) {
 
 int wave_size(const rm_map *m, int n, const TileGeom &tg) {
   if (m->tuning.wave_poses > 0) return std::min(n, m->tuning.wave_poses);
-  // up to 128 poses per wave, keeping the per-wave scratch near 4 GiB
+  // up to 128 poses per wave, keeping the per-wave scratch within the map's wave budget
   size_t per = (size_t)m->n_clusters * sizeof(int4) + (size_t)tg.ntiles * ((size_t)tg.cap * tg.rec_bytes + 8 * 40);
-  size_t w = std::max<size_t>(1, (size_t(4) << 30) / std::max<size_t>(per, 1));
+  size_t w = std::max<size_t>(1, m->wave_budget / std::max<size_t>(per, 1));
   return (int)std::min<size_t>(std::min<size_t>(w, 128), (size_t)n);
 }
 
@@ -1165,6 +1166,15 @@ rm_status rm_map_create(const float *vertices, int64_t n_vertices, const int32_t
 
   rm_map *m = new rm_map();
   cudaGetDevice(&m->device);
+  {
+    // a sixteenth of the device's memory (at least 4 GiB) for one wave's scratch: panoramic
+    // views need large bins, and every extra wave repeats the slowest tile's serial work
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess)
+      m->wave_budget = std::max(m->wave_budget, total_b / 16);
+    else
+      cudaGetLastError();
+  }
   m->V = n_vertices;
   m->T = n_faces;
   // re-centre on the FP64 bounding-box centre

@@ -366,8 +366,9 @@ __device__ __forceinline__ int setup_ray(const float3 v[3], const float4 u[3], c
   if (has_up) zmax = 1.0f;
   if (has_dn) zmin = -1.0f;
   const float el_hi = asinf(zmax), el_lo = asinf(zmin);
-  const int j0 = max(0, (int)ceilf((cam.el0 - el_hi) / cam.el_step - kRayMarginPx));
-  const int j1 = min(cam.H - 1, (int)floorf((cam.el0 - el_lo) / cam.el_step + kRayMarginPx));
+  // approximate divisions: the margin absorbs their few-ulp error
+  const int j0 = max(0, (int)ceilf(__fdividef(cam.el0 - el_hi, cam.el_step) - kRayMarginPx));
+  const int j1 = min(cam.H - 1, (int)floorf(__fdividef(cam.el0 - el_lo, cam.el_step) + kRayMarginPx));
   if (j0 > j1) return 0;
   int nrect;
   if (has_up || has_dn) {
@@ -384,8 +385,8 @@ __device__ __forceinline__ int setup_ray(const float3 v[3], const float4 u[3], c
     if (g20 >= g01 && g20 >= g12) { lo = s0; hi = s2; }
     else if (g01 >= g12) { lo = s1; hi = s0 + twopi; }
     else { lo = s2; hi = s1 + twopi; }
-    const int ilo = (int)ceilf((lo - cam.az0) / cam.az_step - 0.5f - kRayMarginPx);
-    const int ihi = (int)floorf((hi - cam.az0) / cam.az_step - 0.5f + kRayMarginPx);
+    const int ilo = (int)ceilf(__fdividef(lo - cam.az0, cam.az_step) - 0.5f - kRayMarginPx);
+    const int ihi = (int)floorf(__fdividef(hi - cam.az0, cam.az_step) - 0.5f + kRayMarginPx);
     const int n = ihi - ilo + 1;
     if (n <= 0) return 0;
     if (n >= cam.W) {
