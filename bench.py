@@ -718,8 +718,8 @@ def _small_line(a, metric, unit, value, ms, config, roofline, cpu, launches):
 def run_lidar(a):
     """The panoramic workload: cost and gradient of 64 candidate poses (30 cm / 3 deg around the
     true pose) through the 1024 x 64 ray table on the 2M-triangle terrain (render + Table I +
-    surrogate + adjoint), one rm_cost_grad call per step after autotuning; then LM alignment
-    from the 30 cm / 3 deg start with the same tuning. The raster's algorithmic bytes are the scan's, 5 per ray per pose. CPU
+    surrogate + adjoint), one rm_cost_grad call per step with the default tiles; then LM
+    alignment from the 30 cm / 3 deg start. The raster's algorithmic bytes are the scan's, 5 per ray per pose. CPU
     baseline: the oracle over 16 of the poses on the host cores."""
     import torch
     import paper_1702_06813_gb300 as rm
@@ -736,12 +736,9 @@ def run_lidar(a):
     scan = rm.Scan.make(rm.Intrinsics.from_camera(cam), *w["scan"])
     poses = torch.as_tensor(poses_np.reshape(-1, 16), dtype=torch.float64, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    from paper_1702_06813_gb300 import autotune
-    if a.tile:
+    if a.tile:  # default: the ray-table tile (16x16); large tiles grow panoramic bins a lot
         tw, th = (int(x) for x in a.tile.split("x"))
         gm.set_tuning(tile=(tw, th))
-    else:
-        autotune.autotune(gm, scan, poses, cache=None, reps=2)  # untimed: part of warm-up
     for _ in range(max(3, a.warmup)):
         rm.cost_grad(gm, scan, poses)
     torch.cuda.synchronize()

@@ -118,7 +118,7 @@ typedef struct {
 typedef struct {
   int32_t tile_w, tile_h;   /* screen tile, pixels: 16x16, 32x16, 32x32 or 64x32; 0 = per
                                camera model as in the batched entry points (64x32 pinhole,
-                               32x32 ray table) */
+                               16x16 ray table) */
   int32_t bin_capacity;     /* triangle records per tile bin (grown on overflow) */
   int32_t wave_poses;       /* poses processed together per kernel wave */
   int32_t async_status;     /* 1: do not read the device status back (graph capture);
@@ -439,7 +439,7 @@ typedef struct {
  * triangle setup -> tile raster -> reduction per problem), the number of setup items follows
  * the visible clusters, and raster/reduction items are served first. Every wait is bounded
  * (RM_ETIMEOUT). Outputs as for rm_cost_grad, per problem
- * (index k = problem). Screen tiles are 64x32 for pinhole problems and 32x32 for ray-table
+ * (index k = problem). Screen tiles are 64x32 for pinhole problems and 16x16 for ray-table
  * problems, the per-call entry points' defaults, so a problem's results equal those of
  * rm_cost_grad with default tiles bit for bit. (Sec. IV.C / Sec. VI: many evaluations per
  * scan match; batching them is this library's extension.) */

@@ -276,7 +276,7 @@ rm_status check_intr(const rm_intrinsics *in) {
 
 TileGeom make_tiles(const rm_map *m, const rm_intrinsics *in) {
   TileGeom tg;
-  // default: the persistent kernel's tile for the camera model (64x32 pinhole, 32x32 ray table)
+  // default: the persistent kernel's tile for the camera model (64x32 pinhole, 16x16 ray table)
   const int md = in->model == RM_RAYTABLE ? 1 : 0;
   tg.tw = m->tuning.tile_w > 0 ? m->tuning.tile_w : rmk::kPersistTileW[md];
   tg.th = m->tuning.tile_h > 0 ? m->tuning.tile_h : rmk::kPersistTileH[md];

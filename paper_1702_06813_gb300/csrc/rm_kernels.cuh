@@ -184,10 +184,11 @@ cudaError_t launch_dfo_step(DfoState *st, const DfoArgs &a, const long long *e_t
 
 // Batch of problems (each its own camera, scan and scratch) run by one persistent kernel.
 constexpr int kPersistCull = 4;   // 256-cluster chunks per cull item
-// Persistent kernel screen tiles: pinhole problems use 64x32 tiles, one per raster item;
-// ray-table problems use 32x32 tiles, two per raster item.
-constexpr int kPersistTileW[2] = {64, 32};
-constexpr int kPersistTileH[2] = {32, 32};
+// Persistent kernel screen tiles, two per raster item: 64x32 for pinhole problems, 16x16 for
+// ray-table problems (a panoramic tile can hold thousands of bin records, and smaller tiles
+// split that serial work over more CTAs).
+constexpr int kPersistTileW[2] = {64, 16};
+constexpr int kPersistTileH[2] = {32, 16};
 constexpr int kPersistTiles[2] = {2, 2};
 struct BatchArgs {
   const WaveArgs *probs;   // one per problem (n_poses 1, wave_base 0)
