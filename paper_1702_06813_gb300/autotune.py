@@ -63,9 +63,13 @@ def autotune(m: rm.Map, scan: rm.Scan, poses, params=None, tiles=TILES, waves=WA
         _apply(m, best)
         return best
     results = []
+    # every (tile, wave) candidate starts from the same capacity: a capacity that a larger tile
+    # grew (panoramic tiles can hold thousands of records) would otherwise carry over to the
+    # smaller tiles and their waves, whose scratch it sizes
+    cap0 = m.get_tuning()["bin_capacity"]
     for tile in tiles:
         for wave in [w for w in waves if w <= max(n, waves[0])]:
-            m.set_tuning(tile=tile, wave_poses=wave)
+            m.set_tuning(tile=tile, wave_poses=wave, bin_capacity=cap0)
             ms = _time(m, scan, poses, params, reps)
             results.append({"tile": list(tile), "wave_poses": wave,
                             "bin_capacity": m.get_tuning()["bin_capacity"], "ms": ms})
