@@ -637,6 +637,7 @@ rm_status run_batch(rm_map *m, const rm_problem *probs, int n, const rm_cost_par
                     rm_icp_report *ireps = nullptr) {
   if (n < 0) return fail(RM_EINVAL, "n < 0");
   if (n == 0) return RM_OK;
+  if (n >= (1 << rmk::kItemProblemBits)) return fail(RM_EINVAL, "too many problems in one batch");
   if (!probs || !prm) return fail(RM_EINVAL, "NULL argument");
   if (!(prm->eps >= 0.0f)) return fail(RM_EINVAL, "eps must be >= 0");
   if (lm && (lm->max_iters < 0 || lm->max_iters > 100000)) return fail(RM_EINVAL, "max_iters out of range");
@@ -654,6 +655,7 @@ rm_status run_batch(rm_map *m, const rm_problem *probs, int n, const rm_cost_par
   const int ncull = std::max(1, ((nc + 255) / 256 + rmk::kPersistCull - 1) / rmk::kPersistCull);
   // setup items per evaluation are set on the device from the visible clusters; at most
   const int max_setup = std::max(1, (nc + rmk::kSetupClusters - 1) / rmk::kSetupClusters);
+  if (max_setup >= (1 << rmk::kItemIndexBits)) return fail(RM_EINVAL, "map has too many clusters for a batch");
   for (int attempt = 0;; ++attempt) {
     std::vector<TileGeom> tg(n);
     std::vector<long long> P(n);
@@ -705,7 +707,7 @@ rm_status run_batch(rm_map *m, const rm_problem *probs, int n, const rm_cost_par
       need[3 * p + 2] = raster_items(tg[p], probs[p].scan.intr.model);
     }
     // ---- plan and carve the arena
-    auto layout = [&](Carver &cv, bool carve, WaveArgs **d_args, int4 **d_items, int **d_next,
+    auto layout = [&](Carver &cv, bool carve, WaveArgs **d_args, long long **d_items, int **d_next,
                       int **d_done, int **d_need, float **d_M, int **d_skip, double **d_poses,
                       rmk::LMState **d_lm, int **d_vcount, int4 **d_vis, int **d_counts,
                       double **d_partial, unsigned char **d_bins, float **d_sd, uint8_t **d_sc,
@@ -713,7 +715,7 @@ rm_status run_batch(rm_map *m, const rm_problem *probs, int n, const rm_cost_par
                       double **r_grad, double **r_jtj, rmk::IcpState **d_icp, double **r_l1) {
       (void)carve;
       *d_args = cv.take<WaveArgs>(n);
-      *d_items = cv.take<int4>(cap_hi + cap_lo);
+      *d_items = cv.take<long long>(cap_hi + cap_lo);
       *d_next = cv.take<int>(8);  // queue heads and tails, finished problems
       *d_done = cv.take<int>(4 * (size_t)n);
       *d_need = cv.take<int>(3 * (size_t)n);
@@ -737,7 +739,7 @@ rm_status run_batch(rm_map *m, const rm_problem *probs, int n, const rm_cost_par
       *d_icp = cv.take<rmk::IcpState>(n);
       *r_l1 = cv.take<double>(n);
     };
-    WaveArgs *d_args; int4 *d_items, *d_vis; int *d_next, *d_done, *d_need, *d_skip, *d_vcount, *d_counts;
+    WaveArgs *d_args; long long *d_items; int4 *d_vis; int *d_next, *d_done, *d_need, *d_skip, *d_vcount, *d_counts;
     float *d_M, *d_sd, *d_rays; double *d_poses, *d_partial, *r_els, *r_grad, *r_jtj; rmk::LMState *d_lm;
     unsigned char *d_bins; uint8_t *d_sc; long long *r_counts, *r_et;
     rmk::IcpState *d_icp; double *r_l1;

@@ -2057,6 +2057,22 @@ __device__ __noinline__ void lm_load_cg(const LMState *src, LMState &dst) {
   for (int k = 0; k < (int)(sizeof(LMState) / 8); ++k) d[k] = __ldcg(s + k);
 }
 
+// A load with acquire semantics at GPU scope: later loads see what the writer released.
+__device__ __forceinline__ long long ld_acquire_gpu(const long long *p) {
+  long long v;
+  asm volatile("ld.acquire.gpu.global.s64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Orders this thread's earlier memory operations before its later ones at GPU scope (with a
+// relaxed write after it: a release; with a relaxed read before it: an acquire).
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
+__device__ __forceinline__ int4 unpack_item(long long v) {
+  return make_int4((int)(v >> 40), (int)(v >> 21) & 3, (int)v & ((1 << kItemIndexBits) - 1),
+                   (int)(v >> 23) & ((1 << kItemEvalBits) - 1));
+}
+
 // Claims the next slot of a queue that looks non-empty (one atomic add), or returns -1. Two
 // CTAs racing for its last item can both claim; the later one then waits for the queue's next
 // publication, or for the end of the batch.
@@ -2091,9 +2107,9 @@ __device__ __forceinline__ void persist_claim(const BatchArgs &b, int4 *s_item, 
       slot = slot >= b.cap[1] ? -1 : (slot >= 0 ? slot + b.cap[0] : -1);
     }
     if (slot >= 0) {
-      int x;
+      long long x;
       bool finished = false;
-      while ((x = *(volatile const int *)&b.items[slot].x) < 0) {
+      while ((x = ld_acquire_gpu(b.items + slot)) < 0) {
         if (*(volatile const int *)(b.qctl + 4) >= b.n_problems) {  // nothing more will come
           finished = true;
           break;
@@ -2107,8 +2123,7 @@ __device__ __forceinline__ void persist_claim(const BatchArgs &b, int4 *s_item, 
         abort = 1;
         break;
       }
-      __threadfence();
-      item = make_int4(x, __ldcg(&b.items[slot].y), __ldcg(&b.items[slot].z), __ldcg(&b.items[slot].w));
+      item = unpack_item(x);
       break;
     }
     if (*(volatile const int *)(b.qctl + 4) >= b.n_problems) break;  // all finished
@@ -2130,7 +2145,7 @@ __device__ __forceinline__ void persist_claim(const BatchArgs &b, int4 *s_item, 
 // slot, evaluation); count 0: none.
 __device__ __forceinline__ int4 persist_complete(const BatchArgs &b, int4 item, const int *vis_count,
                                                  int clusters_per_item) {
-  __threadfence();
+  fence_acq_rel_gpu();  // the CTA's results (after its barrier) before the count
   const int p = item.x, ph = item.y, it = item.w;
   int4 eq = make_int4(0, 0, -1, it);  // phase, count, queue, evaluation
   if (ph < 3) {
@@ -2166,20 +2181,16 @@ __device__ __forceinline__ int4 persist_complete(const BatchArgs &b, int4 item, 
   return eq;
 }
 
-// All threads of a CTA: write the reserved successor slots, then publish each one by setting
-// its problem field last (after a fence).
+// All threads of a CTA: publish the reserved successor slots, each with one 64-bit write after
+// a fence (which also orders what thread 0 observed of the completion counts).
 __device__ __forceinline__ void persist_publish(const BatchArgs &b, int4 eq, int problem) {
-if (eq.y > 0) {
-  for (int k = threadIdx.x; k < eq.y; k += blockDim.x) {
-    int4 *slot = b.items + eq.z + k;
-    slot->y = eq.x;
-    slot->z = k;
-    slot->w = eq.w;
+  if (eq.y > 0) {
+    fence_acq_rel_gpu();
+    __syncthreads();
+    for (int k = threadIdx.x; k < eq.y; k += blockDim.x)
+      atomicExch(reinterpret_cast<unsigned long long *>(b.items + eq.z + k),
+                 (unsigned long long)pack_item(problem, eq.x, k, eq.w));
   }
-  __threadfence();
-  __syncthreads();
-  for (int k = threadIdx.x; k < eq.y; k += blockDim.x) atomicExch(&b.items[eq.z + k].x, problem);
-}
 }
 
 __global__ void __launch_bounds__(kThreads, RM_PERSIST_MIN_BLOCKS) k_persist(BatchArgs b) {
@@ -2318,18 +2329,18 @@ __global__ void __launch_bounds__(kThreads, MODEL == 0 ? RM_PERSIST_WAVE_MIN_BLO
   }
 }
 
-__global__ void k_queue_init(int4 *items, int n_slots, int first_low, int n_problems,
+__global__ void k_queue_init(long long *items, int n_slots, int first_low, int n_problems,
                              int cull_items, int *qctl) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   const int n0 = n_problems * cull_items;
   if (k < n_slots) {
     const int c = k - first_low;
-    items[k] = c >= 0 && c < n0 ? make_int4(c / cull_items, 0, c % cull_items, 0) : make_int4(-1, 0, 0, 0);
+    items[k] = c >= 0 && c < n0 ? pack_item(c / cull_items, 0, c % cull_items, 0) : -1ll;
   }
   if (k == 0) qctl[3] = n0;
 }
 
-cudaError_t launch_queue_init(int4 *items, int n_slots, int first_low, int n_problems,
+cudaError_t launch_queue_init(long long *items, int n_slots, int first_low, int n_problems,
                               int cull_items, int *qctl, cudaStream_t s) {
   k_queue_init<<<(n_slots + 255) / 256, 256, 0, s>>>(items, n_slots, first_low, n_problems,
                                                      cull_items, qctl);

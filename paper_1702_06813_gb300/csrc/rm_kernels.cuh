@@ -195,9 +195,10 @@ struct BatchArgs {
   int n_problems;
   // Two ready queues in one slot array: slots [0, cap[0]) take raster and reduce items, slots
   // [cap[0], cap[0] + cap[1]) cull and setup items. An item is (problem, phase (0 cull,
-  // 1 setup, 2 raster, 3 reduce+LM), index within the phase, evaluation number); a slot's
-  // problem field is -1 until the slot is published.
-  int4 *items;
+  // 1 setup, 2 raster, 3 reduce+LM), index within the phase, evaluation number), packed into
+  // one 64-bit word by pack_item so that a claim reads it with a single load; a slot holds -1
+  // until it is published.
+  long long *items;
   int cap[2];
   int *qctl;               // head (claimed) and tail (reserved) of each queue, then the number
                            // of finished problems; zero before launch except the first tail
@@ -216,6 +217,16 @@ struct BatchArgs {
   long long spin_limit;    // cycles a CTA may go without finding work before it gives up
 };
 
+// Queue item fields: index within the phase (21 bits), phase (2), evaluation (17), problem
+// (23). The host checks the limits before a launch.
+constexpr int kItemIndexBits = 21, kItemEvalBits = 17, kItemProblemBits = 23;
+static_assert(kItemIndexBits + 2 + kItemEvalBits + kItemProblemBits == 63, "item fields fill 63 bits");
+// Evaluations (at most 100001) and raster items (at most 16384^2 / 256 / 2) always fit their
+// fields; the host checks the problem count and the setup items per evaluation.
+__host__ __device__ constexpr long long pack_item(int problem, int phase, int index, int eval) {
+  return ((long long)problem << 40) | ((long long)eval << 23) | ((long long)phase << 21) | (long long)index;
+}
+
 constexpr int kSetupClusters = 64;  // visible clusters per setup item (eight per warp), at most
 // Visible clusters per persistent setup item by camera model: pinhole 64; ray-table views,
 // which see many more clusters, 128.
@@ -224,7 +235,7 @@ constexpr int kSetupCtasPerGpu = 912;  // setup CTAs a small wave may spread ove
 
 // Every slot unpublished except the evaluation-0 cull items of every problem at the head of
 // the cull/setup queue; sets that queue's tail.
-cudaError_t launch_queue_init(int4 *items, int n_slots, int first_low, int n_problems,
+cudaError_t launch_queue_init(long long *items, int n_slots, int first_low, int n_problems,
                               int cull_items, int *qctl, cudaStream_t s);
 
 cudaError_t launch_lm_init_batch(LMState *st, const double *T0, int n, const LMArgs &a,
