@@ -97,6 +97,45 @@ def test_render_bit_exact_triangle_soup_with_near_cuts(seed):
     _same_render({"tri_id": g["tri_id"][0], "depth": g["depth"][0]}, o)
 
 
+@pytest.mark.parametrize("shape", [(16384, 3), (3, 16384)])
+def test_render_and_cost_at_the_largest_image_side(shape):
+    """The largest image side the ABI accepts (16384 pixels): one row of 256 tiles, or one
+    column of 512. A tilted, jittered grid of 80k triangles (about 450 visible along the
+    strip, FU faces among them) renders bit for bit and gives the oracle's Table I counts and
+    adjoint at two poses; a wide-angle soup with near cuts renders bit for bit too."""
+    w, h = shape
+    cam = cases.small_pinhole(w=w, h=h, f=1500.0)
+    intr = rm.Intrinsics.from_camera(cam)
+    vg, fg = cases.plane_grid(200, 200, (-20.0, -20.0, 2.0), (40.0, 0.0, 3.0), (0.0, 40.0, 1.0),
+                              jitter=0.3, seed=5)
+    labels = (np.arange(len(fg)) % 4 == 0).astype(np.uint8)
+    om = oracle.OracleMap(vg, fg, labels)
+    gm = rm.Map(vg, fg, labels)
+    o = om.render(np.eye(4), cam)
+    hit = ~np.isnan(o["depth"])
+    assert len(np.unique(o["tri_id"][hit])) > 300
+    g = rm.render_depth(gm, np.eye(4)[None], intr)
+    _same_render({"tri_id": g["tri_id"][0], "depth": g["depth"][0]}, o)
+    r = cases.rng(22)
+    sd = np.where(hit, o["depth"] * (1.0 + 0.01 * r.standard_normal(o["depth"].shape)), 4.0).astype(np.float32)
+    sc = np.where(hit, (r.uniform(size=sd.shape) < 0.2).astype(np.uint8), np.uint8(1))
+    sc[r.uniform(size=sd.shape) < 0.05] = 2
+    scan = rm.Scan.make(intr, sd, sc)
+    poses = [np.eye(4), synth.perturb_fixed(np.eye(4), r, 0.05, 2.0)]
+    gc = rm.cost_grad(gm, scan, np.stack(poses))
+    for k, P in enumerate(poses):
+        _check_cost(gc, om.cost(P, cam, sd, sc), k)
+    gm.close()
+    vs, fs = cases.random_tris(21, 600)
+    om = oracle.OracleMap(vs, fs, np.zeros(len(fs), np.uint8))
+    o = om.render(np.eye(4), cam)
+    assert o["stats"]["clipped"] > 0
+    gm = rm.Map(vs, fs, np.zeros(len(fs), np.uint8))
+    g = rm.render_depth(gm, np.eye(4)[None], intr)
+    _same_render({"tri_id": g["tri_id"][0], "depth": g["depth"][0]}, o)
+    gm.close()
+
+
 def test_render_watertight_plane_gpu():
     cam = cases.small_pinhole(w=96, h=72, f=70.0)
     v, f = cases.plane_grid(41, 29, (-4, -4, 1.0), (8, 0, 3.0), (0, 8, 2.0), jitter=0.2, seed=9)
@@ -225,6 +264,19 @@ def test_cost_parity_with_fu_faces_and_nan_scan():
         _check_cost(g, o, k)
         tot += o["counts"]
     assert np.all(tot > 0)   # every Table I outcome was exercised
+
+
+def test_cost_grad_empty_batch_and_batch_of_one(c1):
+    """No poses: empty outputs and no launch failure; a batch of one equals that pose inside a
+    larger batch bit for bit."""
+    g = rm.cost_grad(c1["gm"], c1["gscan"], np.zeros((0, 4, 4)))
+    assert g["counts"].shape[0] == 0 and g["grad"].shape[0] == 0
+    poses = np.stack([c1["gt"], c1["start"], c1["gt"]])
+    gb = rm.cost_grad(c1["gm"], c1["gscan"], poses)
+    g1 = rm.cost_grad(c1["gm"], c1["gscan"], poses[1:2])
+    for key in ("counts", "e_table", "e_ls", "grad", "jtj"):
+        assert torch.equal(gb[key][1:2], g1[key]), key
+    assert torch.equal(gb["grad"][0], gb["grad"][2])
 
 
 def test_cost_host_buffers_match_device(c1):
