@@ -136,6 +136,23 @@ def test_render_and_cost_at_the_largest_image_side(shape):
     gm.close()
 
 
+@pytest.mark.parametrize("tile", [(64, 32), (32, 32), (32, 16), (16, 16)])
+def test_render_exact_ties_lower_id_wins(tile):
+    """Duplicated faces (same vertex order: equal inverse depth bit for bit) under shuffled ids,
+    plus copies with rotated vertex order (near ties): ids and depth bit-exact, so the lower id
+    wins every exact tie as in the oracle."""
+    cam = cases.small_pinhole(w=75, h=53, f=50.0)
+    v, f = cases.plane_grid(12, 9, (-2.0, -1.5, 3.0), (4.0, 0.0, 1.0), (0.0, 3.0, 0.5), jitter=0.3, seed=3)
+    ff = np.concatenate([f, f, f[:, [1, 2, 0]]])[cases.rng(5).permutation(3 * len(f))]
+    lab = np.zeros(len(ff), np.uint8)
+    o = oracle.OracleMap(v, ff, lab).render(np.eye(4), cam)
+    gm = rm.Map(v, ff, lab)
+    gm.set_tuning(tile=tile)
+    g = rm.render_depth(gm, np.eye(4)[None], rm.Intrinsics.from_camera(cam))
+    _same_render({"tri_id": g["tri_id"][0], "depth": g["depth"][0]}, o)
+    gm.close()
+
+
 def test_render_watertight_plane_gpu():
     cam = cases.small_pinhole(w=96, h=72, f=70.0)
     v, f = cases.plane_grid(41, 29, (-4, -4, 1.0), (8, 0, 3.0), (0, 8, 2.0), jitter=0.2, seed=9)

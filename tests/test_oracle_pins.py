@@ -103,6 +103,29 @@ def test_zbuffer_bbox_equals_brute_force_pinhole(seed):
     assert np.array_equal(fb, fr)
 
 
+def test_zbuffer_exact_ties_lower_id_wins():
+    """Every face of a jittered grid twice, with the same vertex order (so both copies give the
+    same inverse depth bit for bit at every sample), under shuffled ids: the visible surface is
+    the single mesh's, and at every pixel the lower of the two ids wins (the raster rule of
+    equal depths)."""
+    cam = cases.small_pinhole(w=75, h=53, f=50.0)
+    v, f = cases.plane_grid(12, 9, (-2.0, -1.5, 3.0), (4.0, 0.0, 1.0), (0.0, 3.0, 0.5), jitter=0.3, seed=3)
+    perm = cases.rng(5).permutation(2 * len(f))
+    ff = np.concatenate([f, f])[perm]
+    orig = perm % len(f)  # geometric face of each id
+    one = oracle.OracleMap(v, f, np.zeros(len(f), np.uint8)).render(np.eye(4), cam)
+    two = oracle.OracleMap(v, ff, np.zeros(len(ff), np.uint8)).render(np.eye(4), cam)
+    hit = one["tri_id"] >= 0
+    assert hit.sum() > 1000
+    assert np.array_equal(two["tri_id"] >= 0, hit)
+    assert np.array_equal(two["depth"][hit].view(np.uint32), one["depth"][hit].view(np.uint32))
+    won = two["tri_id"][hit]
+    assert np.array_equal(orig[won], one["tri_id"][hit])
+    lower = np.full(len(f), np.iinfo(np.int64).max)
+    np.minimum.at(lower, orig, np.arange(len(ff)))
+    assert np.array_equal(won, lower[orig[won]])
+
+
 @pytest.mark.parametrize("seed", [5, 6, 7])
 def test_zbuffer_bounds_equal_brute_force_raytable(seed):
     cam = cases.small_spherical()
