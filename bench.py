@@ -210,6 +210,20 @@ def cpu_baseline(w, min_seconds=1.5):
                       f"640x480 render + Table I + FP64 gradient, OpenMP over poses, {dt:.1f} s wall"}
 
 
+def oracle_single_thread(w, n=4):
+    """The oracle as it stands on one host thread, one pose at a time (the plain CPU form):
+    evaluations per second over the first n candidate poses."""
+    import oracle
+    oracle.build()
+    om = oracle.OracleMap(w["mesh"].vertices, w["mesh"].faces, w["mesh"].labels)
+    sd, sc = w["scan"]
+    om.cost(w["poses"][0], w["cam"], sd, sc)  # page in
+    t0 = time.perf_counter()
+    for P in w["poses"][:n]:
+        om.cost(P, w["cam"], sd, sc)
+    return n / (time.perf_counter() - t0)
+
+
 def run_reference(a):
     """The oracle timed as it stands on the host cores (OpenMP over poses), on the same
     workload, batch, metric and step count as the GPU arm (rank 0 only): each step is one
@@ -1088,6 +1102,7 @@ def main():
     }
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
+        line["config"]["oracle_single_thread_evals_per_s"] = oracle_single_thread(w)
     if rank == 0:
         print(json.dumps(line))
     gm.close()
